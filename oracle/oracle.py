@@ -1,0 +1,341 @@
+"""ctypes binding of the FP64 CPU oracle (lqcd_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by ``__graft_entry__.smoke()``
+and by the CPU-baseline / reference legs of ``bench.py``.  The product library
+never loads it.
+
+Array conventions (numpy, C order, lexicographic site i = x + Lx(y + Ly(z + Lz t))):
+  U    complex128 (V, 4, 3, 3)   link U_mu(x)[row][col]
+  psi  complex128 (V, 4, 3)      spinor [spin][color]; even/odd fields are
+                                 full-lattice arrays with the other parity zero
+  P    float64    (V, 4, 8)      momentum Gell-Mann coefficients p_a
+dims = (Lx, Ly, Lz, Lt), t_bc = -1 (antiperiodic fermions in t) or +1.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lqcd_oracle.c")
+_LIB = os.path.join(_HERE, "liblqcd_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-O2", "-fPIC", "-shared", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math"]
+
+
+def build(force: bool = False) -> str:
+    """Compile lqcd_oracle.c into liblqcd_oracle.so next to it (gcc)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = ctypes.CDLL(_LIB)
+            _declare(_lib)
+    return _lib
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_lp = ctypes.POINTER(ctypes.c_long)
+_up = ctypes.POINTER(ctypes.c_uint32)
+_i, _d, _u32, _l = ctypes.c_int, ctypes.c_double, ctypes.c_uint32, ctypes.c_long
+
+
+def _declare(L):
+    sig = {
+        "or_gamma": (None, [_i, _dp]),
+        "or_philox4x32_10": (None, [_up, _up, _up]),
+        "or_uniform2": (None, [_u32] * 6 + [_dp]),
+        "or_gauss2": (None, [_u32] * 6 + [_dp]),
+        "or_plaquette": (_i, [_ip, _dp, _dp]),
+        "or_gauge_action": (_i, [_ip, _dp, _d, _dp]),
+        "or_dslash": (_i, [_ip, _i, _dp, _dp, _dp, _i, _i]),
+        "or_dslash_at": (_i, [_ip, _i, _dp, _dp, _i, _l, _lp, _dp]),
+        "or_mhat": (_i, [_ip, _i, _dp, _d, _dp, _dp, _i]),
+        "or_mdagm": (_i, [_ip, _i, _dp, _d, _dp, _dp]),
+        "or_cg": (_i, [_ip, _i, _dp, _d, _dp, _dp, _d, _i, _ip, _dp]),
+        "or_gauge_force": (_i, [_ip, _dp, _d, _dp]),
+        "or_gauge_force_at": (_i, [_ip, _dp, _d, _l, _lp, _dp]),
+        "or_fermion_force": (_i, [_ip, _i, _dp, _d, _dp, _l, _lp, _dp]),
+        "or_fermion_action": (_i, [_ip, _i, _dp, _d, _dp, _d, _i, _dp, _ip]),
+        "or_su3_expi": (None, [_dp, _d, _dp]),
+        "or_algebra_to_mat": (None, [_dp, _dp]),
+        "or_reunit_mat": (None, [_dp, _dp]),
+        "or_gauge_start": (_i, [_ip, _u32, _u32, _d, _dp]),
+        "or_momentum_refresh": (_i, [_ip, _u32, _u32, _u32, _dp]),
+        "or_eta_refresh": (_i, [_ip, _u32, _u32, _u32, _dp]),
+        "or_link_update": (_i, [_ip, _dp, _dp, _d]),
+        "or_reunitarize": (_i, [_ip, _dp, _dp]),
+        "or_kinetic": (_d, [_ip, _dp]),
+        "or_md_integrate": (_i, [_ip, _i, _dp, _dp, _dp, _d, _d, _d, _i, _i, _i, _d, _i, _dp]),
+        "or_hamiltonian": (_i, [_ip, _i, _dp, _dp, _dp, _d, _d, _i, _d, _i, _dp]),
+        "or_hmc_trajectory": (_i, [_ip, _i, _dp, _d, _d, _d, _i, _i, _i, _d, _i,
+                                   _u32, _u32, _u32, _i, _i, _dp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+# ----------------------------------------------------------------- helpers
+
+def _dims(dims):
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    return d
+
+
+def _vol(dims):
+    return int(np.prod(dims))
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    if a.dtype == np.complex128:
+        return a.view(np.float64).ctypes.data_as(_dp)
+    assert a.dtype == np.float64, a.dtype
+    return a.ctypes.data_as(_dp)
+
+
+def _check(rc):
+    if rc < 0:
+        raise ValueError("oracle: invalid lattice geometry (dims must be positive and even)")
+    return rc
+
+
+def new_gauge(dims):
+    return np.zeros((_vol(dims), 4, 3, 3), np.complex128)
+
+
+def new_spinor(dims):
+    return np.zeros((_vol(dims), 4, 3), np.complex128)
+
+
+def new_momentum(dims):
+    return np.zeros((_vol(dims), 4, 8), np.float64)
+
+
+def parity(dims) -> np.ndarray:
+    """parity (x+y+z+t) % 2 of every lexicographic site"""
+    Lx, Ly, Lz, Lt = dims
+    t, z, y, x = np.meshgrid(np.arange(Lt), np.arange(Lz), np.arange(Ly), np.arange(Lx), indexing="ij")
+    return ((x + y + z + t) % 2).reshape(-1)
+
+
+# ----------------------------------------------------------------- API
+
+def gamma(which: int) -> np.ndarray:
+    out = np.zeros((4, 4), np.complex128)
+    lib().or_gamma(which, _ptr(out))
+    return out
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = (ctypes.c_uint32 * 4)(*ctr)
+    k = (ctypes.c_uint32 * 2)(*key)
+    o = (ctypes.c_uint32 * 4)()
+    lib().or_philox4x32_10(c, k, o)
+    return np.array(list(o), np.uint32)
+
+
+def uniform2(seed, chain, site, j, purpose, traj):
+    o = np.zeros(2)
+    lib().or_uniform2(seed, chain, site, j, purpose, traj, _ptr(o))
+    return o
+
+
+def gauss2(seed, chain, site, j, purpose, traj):
+    o = np.zeros(2)
+    lib().or_gauss2(seed, chain, site, j, purpose, traj, _ptr(o))
+    return o
+
+
+def plaquette(dims, U) -> float:
+    o = ctypes.c_double()
+    _check(lib().or_plaquette(_dims(dims), _ptr(U), ctypes.byref(o)))
+    return o.value
+
+
+def gauge_action(dims, U, beta) -> float:
+    o = ctypes.c_double()
+    _check(lib().or_gauge_action(_dims(dims), _ptr(U), beta, ctypes.byref(o)))
+    return o.value
+
+
+def dslash(dims, U, psi, dagger=False, out_parity=-1, t_bc=-1) -> np.ndarray:
+    out = new_spinor(dims)
+    _check(lib().or_dslash(_dims(dims), t_bc, _ptr(U), _ptr(psi), _ptr(out), int(dagger), out_parity))
+    return out
+
+
+def dslash_at(dims, U, psi, sites, dagger=False, t_bc=-1) -> np.ndarray:
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.zeros((len(sites), 4, 3), np.complex128)
+    _check(lib().or_dslash_at(_dims(dims), t_bc, _ptr(U), _ptr(psi), int(dagger), len(sites),
+                              sites.ctypes.data_as(_lp), _ptr(out)))
+    return out
+
+
+def mhat(dims, U, kappa, psi, dagger=False, t_bc=-1) -> np.ndarray:
+    out = new_spinor(dims)
+    _check(lib().or_mhat(_dims(dims), t_bc, _ptr(U), kappa, _ptr(psi), _ptr(out), int(dagger)))
+    return out
+
+
+def mdagm(dims, U, kappa, psi, t_bc=-1) -> np.ndarray:
+    out = new_spinor(dims)
+    _check(lib().or_mdagm(_dims(dims), t_bc, _ptr(U), kappa, _ptr(psi), _ptr(out)))
+    return out
+
+
+def cg(dims, U, kappa, b, tol=1e-10, maxiter=10000, t_bc=-1):
+    """returns (x, converged, iters, true_rel_res)"""
+    x = new_spinor(dims)
+    it = ctypes.c_int()
+    rel = ctypes.c_double()
+    rc = _check(lib().or_cg(_dims(dims), t_bc, _ptr(U), kappa, _ptr(b), _ptr(x), tol, maxiter,
+                            ctypes.byref(it), ctypes.byref(rel)))
+    return x, rc == 0, it.value, rel.value
+
+
+def gauge_force(dims, U, beta, links=None) -> np.ndarray:
+    if links is None:
+        F = new_momentum(dims)
+        _check(lib().or_gauge_force(_dims(dims), _ptr(U), beta, _ptr(F)))
+        return F
+    links = np.ascontiguousarray(links, dtype=np.int64)
+    F = np.zeros((len(links), 8))
+    _check(lib().or_gauge_force_at(_dims(dims), _ptr(U), beta, len(links), links.ctypes.data_as(_lp), _ptr(F)))
+    return F
+
+
+def fermion_force(dims, U, kappa, X, links=None, t_bc=-1) -> np.ndarray:
+    if links is None:
+        F = new_momentum(dims)
+        _check(lib().or_fermion_force(_dims(dims), t_bc, _ptr(U), kappa, _ptr(X), -1, None, _ptr(F)))
+        return F
+    links = np.ascontiguousarray(links, dtype=np.int64)
+    F = np.zeros((len(links), 8))
+    _check(lib().or_fermion_force(_dims(dims), t_bc, _ptr(U), kappa, _ptr(X), len(links),
+                                  links.ctypes.data_as(_lp), _ptr(F)))
+    return F
+
+
+def fermion_action(dims, U, kappa, phi, tol=1e-12, maxiter=10000, t_bc=-1):
+    S = ctypes.c_double()
+    it = ctypes.c_int()
+    _check(lib().or_fermion_action(_dims(dims), t_bc, _ptr(U), kappa, _ptr(phi), tol, maxiter,
+                                   ctypes.byref(S), ctypes.byref(it)))
+    return S.value
+
+
+def su3_expi(H: np.ndarray, c: float) -> np.ndarray:
+    H = np.ascontiguousarray(H, np.complex128)
+    out = np.zeros((3, 3), np.complex128)
+    lib().or_su3_expi(_ptr(H), c, _ptr(out))
+    return out
+
+
+def algebra_to_mat(c8) -> np.ndarray:
+    c8 = np.ascontiguousarray(c8, np.float64)
+    out = np.zeros((3, 3), np.complex128)
+    lib().or_algebra_to_mat(_ptr(c8), _ptr(out))
+    return out
+
+
+def reunit_mat(m) -> np.ndarray:
+    m = np.ascontiguousarray(m, np.complex128)
+    out = np.zeros((3, 3), np.complex128)
+    lib().or_reunit_mat(_ptr(m), _ptr(out))
+    return out
+
+
+def gauge_start(dims, seed, eps, chain=0) -> np.ndarray:
+    U = new_gauge(dims)
+    _check(lib().or_gauge_start(_dims(dims), seed, chain, eps, _ptr(U)))
+    return U
+
+
+def momentum_refresh(dims, seed, traj, chain=0) -> np.ndarray:
+    P = new_momentum(dims)
+    _check(lib().or_momentum_refresh(_dims(dims), seed, chain, traj, _ptr(P)))
+    return P
+
+
+def eta_refresh(dims, seed, traj, chain=0) -> np.ndarray:
+    e = new_spinor(dims)
+    _check(lib().or_eta_refresh(_dims(dims), seed, chain, traj, _ptr(e)))
+    return e
+
+
+def link_update(dims, U, P, c) -> np.ndarray:
+    U = U.copy()
+    _check(lib().or_link_update(_dims(dims), _ptr(U), _ptr(P), c))
+    return U
+
+
+def reunitarize(dims, U):
+    U = U.copy()
+    m = ctypes.c_double()
+    _check(lib().or_reunitarize(_dims(dims), _ptr(U), ctypes.byref(m)))
+    return U, m.value
+
+
+def kinetic(dims, P) -> float:
+    return lib().or_kinetic(_dims(dims), _ptr(P))
+
+
+LEAPFROG, OMELYAN = 0, 1
+
+
+def md_integrate(dims, U, P, phi, beta, kappa, tau, nsteps, integrator=LEAPFROG, n_flavors=2,
+                 cg_tol=1e-10, cg_maxiter=10000, t_bc=-1):
+    """returns (U, P, stats) with stats = [cg_iters, n_solves, cg_failures]"""
+    U = U.copy()
+    P = P.copy()
+    if phi is None:
+        phi = new_spinor(dims)
+    st = np.zeros(3)
+    _check(lib().or_md_integrate(_dims(dims), t_bc, _ptr(U), _ptr(P), _ptr(phi), beta, kappa, tau, nsteps,
+                                 integrator, n_flavors, cg_tol, cg_maxiter, _ptr(st)))
+    return U, P, st
+
+
+def hamiltonian(dims, U, P, phi, beta, kappa, n_flavors=2, cg_tol=1e-12, cg_maxiter=10000, t_bc=-1):
+    if phi is None:
+        phi = new_spinor(dims)
+    H = ctypes.c_double()
+    _check(lib().or_hamiltonian(_dims(dims), t_bc, _ptr(U), _ptr(P), _ptr(phi), beta, kappa, n_flavors,
+                                cg_tol, cg_maxiter, ctypes.byref(H)))
+    return H.value
+
+
+TRAJ_KEYS = ("dH", "accepted", "plaq", "cg_iters", "H0", "H1", "u", "max_unitarity_dev", "n_solves",
+             "cg_failures")
+
+
+def hmc_trajectory(dims, U, beta, kappa, tau, nsteps, integrator=LEAPFROG, n_flavors=2, cg_tol=1e-10,
+                   cg_maxiter=10000, seed=1, chain=0, traj=0, reunit=True, metropolis=True, t_bc=-1):
+    """one full trajectory; returns (U_new, info dict)"""
+    U = U.copy()
+    info = np.zeros(10)
+    _check(lib().or_hmc_trajectory(_dims(dims), t_bc, _ptr(U), beta, kappa, tau, nsteps, integrator,
+                                   n_flavors, cg_tol, cg_maxiter, seed, chain, traj, int(reunit),
+                                   int(metropolis), _ptr(info)))
+    return U, dict(zip(TRAJ_KEYS, info.tolist()))
