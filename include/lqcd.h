@@ -1,0 +1,335 @@
+/*
+ * lqcd.h -- C ABI of a device-resident Hybrid Monte Carlo for SU(3) lattice
+ * gauge theory with two flavours of Wilson fermions on one NVIDIA GB300
+ * (sm_103a).
+ *
+ * The paper this follows (F. Winter, "Gauge Field Generation on Large-Scale
+ * GPU-Enabled Systems", Lattice 2012) argues that every part of an HMC
+ * trajectory must run on the accelerator, not only the solver (Sec. 1), and
+ * lists those parts: pseudofermion refresh, momentum updates, force terms,
+ * projection of fields, reunitarization of SU(3) matrices, a random number
+ * generator and the exponentiation of SU(3) matrices (Sec. 1), plus global
+ * reductions `sum`/`sumMulti` (Sec. 1) and the matrix inversions done by a
+ * Krylov solver (Sec. 6).  It ran Nf = 2 Wilson fermions (Sec. 6.2).  It gives
+ * no formulas; the conventions fixed here are:
+ *
+ *   Lattice      dims = (Lx, Ly, Lz, Lt), all even, V = LxLyLzLt, Vh = V/2.
+ *                Lexicographic site i = x + Lx(y + Ly(z + Lz t)); parity
+ *                (x+y+z+t) mod 2; checkerboard index cb = i/2 within a parity.
+ *   Gamma basis  DeGrand-Rossi (Hermitian), gamma_5 = diag(1, 1, -1, -1).
+ *   Hopping term (D psi)(x) = sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                                      + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu) ],
+ *                each hop across the t boundary multiplied by t_bc (fermions
+ *                antiperiodic in t by default; links periodic).
+ *   Wilson op.   M = 1 - kappa D; even-odd Mhat = 1 - kappa^2 Deo Doe on
+ *                even sites (det M = det Mhat).
+ *   Actions      S_g = beta sum_x sum_{mu<nu} (1 - Re Tr U_munu(x) / 3);
+ *                S_f = phi_e^dag (Mhat^dag Mhat)^-1 phi_e (two flavours);
+ *                T   = sum_links 1/2 sum_a p_a^2 with P = sum_a p_a T_a,
+ *                T_a = lambda_a / 2 (Gell-Mann).
+ *   MD           dU/dt = i P U, dP/dt = -F, F = sum_a T_a dS/de_a with
+ *                dS/de_a = d/de S(exp(i e T_a) U_mu(x)) at e = 0.
+ *   RNG          Philox4x32-10 (Salmon et al., SC'11), key (seed, chain),
+ *                counter (site, j, purpose, trajectory); purposes 0 gauge
+ *                start, 1 momenta, 2 pseudofermion eta, 3 Metropolis.
+ *
+ * Canonical HOST layouts (FP64, used by upload/download):
+ *   LQCD_GAUGE        [site][mu][row][col][re,im]   18 doubles / link
+ *   LQCD_MOMENTUM     [site][mu][a]                 8 doubles / link
+ *   LQCD_SPINOR_EVEN/ODD  [cb][spin][color][re,im]  24 doubles / site of that
+ *                     parity, cb ascending (= lexicographic order of the sites
+ *                     of that parity)
+ *   LQCD_SPINOR_FULL  [site][spin][color][re,im]    24 doubles / site
+ *
+ * Conventions of every call:
+ *   - The return value is an lqcd_status; on failure lqcd_last_error() gives a
+ *     message (thread-local, valid until the next failing call on that thread).
+ *     No call aborts the process or raises into the caller.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Kernels
+ *     are enqueued asynchronously on it; calls that return host scalars
+ *     synchronise that stream before returning.
+ *   - Device memory of fields and work buffers comes from the allocator set
+ *     by lqcd_set_allocator (default: cudaMalloc / cudaFree).
+ *   - Pointers named *_dev are device pointers owned by the caller; all other
+ *     pointers to numbers are host pointers owned by the caller.
+ *   - Fields are not thread-safe: one call at a time per field.
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LQCD_OK = 0,
+    LQCD_EINVAL = 1,   /* bad argument: null pointer, odd/zero dims, kind or precision mismatch */
+    LQCD_ENOMEM = 2,   /* the allocator returned NULL */
+    LQCD_ENOCONV = 3,  /* a solver reached maxiter; its info holds the true residual */
+    LQCD_ENUMERIC = 4, /* non-finite value in a reduction (dH, residual) */
+    LQCD_ECUDA = 5,    /* a CUDA runtime call failed; message from cudaGetErrorString */
+    LQCD_EAGAIN = 6,   /* result not ready yet (asynchronous solve) */
+    LQCD_ETIMEOUT = 7  /* a bounded device-side wait gave up */
+} lqcd_status;
+
+typedef struct {
+    int dims[4]; /* Lx, Ly, Lz, Lt: positive and even, V < 2^31 */
+    int t_bc;    /* fermion boundary factor in t: -1 antiperiodic, +1 periodic */
+} lqcd_lattice;
+
+typedef enum {
+    LQCD_GAUGE = 0,       /* 4 links per site */
+    LQCD_MOMENTUM = 1,    /* 8 su(3) coefficients per link, FP64 only */
+    LQCD_SPINOR_EVEN = 2, /* 4 spin x 3 colour on even sites */
+    LQCD_SPINOR_ODD = 3,  /* 4 spin x 3 colour on odd sites */
+    LQCD_SPINOR_FULL = 4  /* both parities, FP64 only */
+} lqcd_kind;
+
+typedef enum {
+    LQCD_F64 = 0,  /* FP64 storage and arithmetic */
+    LQCD_F32 = 1,  /* FP32 storage, FP32 arithmetic */
+    LQCD_F16N = 2, /* spinors: FP16 of value / site norm, FP32 norm = max |component|;
+                      links: FP16 (entries of SU(3) rows lie in [-1, 1]); FP32 arithmetic */
+    LQCD_BF16 = 3  /* BF16 storage, FP32 arithmetic */
+} lqcd_prec;
+
+typedef enum { LQCD_LEAPFROG = 0, LQCD_OMELYAN = 1 } lqcd_integrator;
+
+typedef struct lqcd_field lqcd_field;
+typedef struct lqcd_hmc_state lqcd_hmc_state;
+
+/* ------------------------------------------------------------ library */
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *lqcd_last_error(void);
+
+/* Version string of the library. */
+const char *lqcd_version(void);
+
+/* Number of kernels this library has launched in this process (all threads). */
+uint64_t lqcd_launch_count(void);
+
+/* Device allocator hook.  alloc(bytes, stream, ctx) returns device memory or
+ * NULL; free(ptr, stream, ctx) releases it.  Passing NULL for both restores
+ * cudaMalloc / cudaFree.  Fields remember the hook they were allocated with. */
+typedef void *(*lqcd_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*lqcd_free_fn)(void *ptr, void *stream, void *ctx);
+lqcd_status lqcd_set_allocator(lqcd_alloc_fn alloc, lqcd_free_fn free_fn, void *ctx);
+
+/* ------------------------------------------------------------ fields */
+
+/* Allocate a field on the current device (contents undefined).
+ *   kind/prec/link_recon combinations:
+ *     LQCD_GAUGE:       (F64, 18) master links; (F32|F16N|BF16, 12) compressed
+ *                       copies storing rows 0, 1 (row 2 = conj(row0 x row1)).
+ *     LQCD_MOMENTUM:    (F64, 0)
+ *     LQCD_SPINOR_EVEN/ODD: any precision, link_recon 0
+ *     LQCD_SPINOR_FULL: (F64, 0)
+ *   Device layout (structure of arrays, site index fastest, per parity):
+ *     gauge F64   double2 [mu][parity][row*3+col][Vh]
+ *     gauge 12    F32: float4 [mu][parity][3][Vh]; F16N/BF16: 4 halves [mu][parity][3][Vh]
+ *     momentum    double  [mu][parity][a][Vh]
+ *     spinor      F64: double2 [spin*3+col][Vh]; F32: float4 [6][Vh];
+ *                 F16N: 8 halves [3][Vh] + float norm [Vh]; BF16: 8 halves [3][Vh]
+ *     full spinor F64 [parity][12][Vh] double2
+ * Errors: LQCD_EINVAL (bad lattice / combination), LQCD_ENOMEM. */
+lqcd_status lqcd_field_alloc(const lqcd_lattice *lat, lqcd_kind kind, lqcd_prec prec, int link_recon,
+                             lqcd_field **out);
+lqcd_status lqcd_field_free(lqcd_field *f);
+
+/* Bytes of device memory the field holds. */
+lqcd_status lqcd_field_bytes(const lqcd_field *f, size_t *bytes);
+
+/* Device pointer of the field's main array (and of its norm array, NULL if
+ * none), for callers that share memory with another library. */
+lqcd_status lqcd_field_data(const lqcd_field *f, void **data_dev, void **norm_dev);
+
+/* Copy a host array in the canonical FP64 layout into the field (converting
+ * to the field's precision; gauge 12-real copies keep rows 0 and 1), or the
+ * field out to such an array (compressed gauge fields are expanded by
+ * reconstructing row 2).  Synchronous with respect to the host buffer: the
+ * call returns after the copy completed.  Uses a temporary device buffer of
+ * the host array's size. */
+lqcd_status lqcd_field_upload(lqcd_field *f, const double *host, void *stream);
+lqcd_status lqcd_field_download(const lqcd_field *f, double *host, void *stream);
+
+/* dst <- src for fields of the same kind and lattice, converting precision
+ * (e.g. FP64 master links -> 12-real FP16 copy, FP64 spinor -> FP16+norm). */
+lqcd_status lqcd_field_copy(lqcd_field *dst, const lqcd_field *src, void *stream);
+
+/* ------------------------------------------------------------ RNG and refresh */
+
+/* Raw Philox4x32-10 blocks: out_dev[4*i .. 4*i+3] = Philox(counter (c0 + i, c1,
+ * c2, c3), key (key0, key1)) for i < n_blocks.  out_dev: device, 4*n_blocks
+ * uint32. */
+lqcd_status lqcd_philox_blocks(uint32_t *out_dev, size_t n_blocks, uint32_t c0, uint32_t c1, uint32_t c2,
+                               uint32_t c3, uint32_t key0, uint32_t key1, void *stream);
+
+/* Start configuration U_mu(x) = exp(i eps sum_a h_a T_a), h_a ~ N(0,1) from
+ * Philox purpose 0 (counter (site, j, 0, 0), j = 0..15, Gaussians 2j, 2j+1 are
+ * coefficient k = mu*8 + a; uniforms from 52-bit words, Box-Muller).
+ * U: LQCD_GAUGE F64 18. */
+lqcd_status lqcd_gauge_start(lqcd_field *U, uint32_t seed, uint32_t chain, double eps, void *stream);
+
+/* Momentum refresh (paper Sec. 1, "momentum updates"): p_a ~ N(0,1), Philox
+ * purpose 1, counter (site, j, 1, traj), same coefficient order as the start.
+ * P: LQCD_MOMENTUM. */
+lqcd_status lqcd_momentum_refresh(lqcd_field *P, uint32_t seed, uint32_t chain, uint32_t traj, void *stream);
+
+/* Pseudofermion source eta on even sites (paper Sec. 1, "pseudofermion
+ * refresh"): each real ~ N(0, 1/2), Philox purpose 2, counter (site, j, 2,
+ * traj), j = 0..11, reals 2j, 2j+1 in [spin][colour][re,im] order.
+ * eta: LQCD_SPINOR_EVEN F64.  (phi = Mhat^dag eta is lqcd_mhat with dagger.) */
+lqcd_status lqcd_eta_refresh(lqcd_field *eta, uint32_t seed, uint32_t chain, uint32_t traj, void *stream);
+
+/* ------------------------------------------------------------ operators */
+
+/* Half hopping term: out = D_{p' p} in, p the parity of `in`, p' = 1 - p the
+ * parity of `out` (EVEN/ODD kinds).  dagger != 0 applies D^dag = gamma5 D gamma5.
+ * Precisions: U F64/18 with F64 spinors, or U 12-real of precision q with
+ * spinors of precision q (q in F32, F16N, BF16; FP32 arithmetic). */
+lqcd_status lqcd_dslash(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int dagger, void *stream);
+
+/* out_e = Mhat in_e = in_e - kappa^2 Deo Doe in_e (dagger: Mhat^dag).  EVEN
+ * spinors, precision rules as lqcd_dslash.  Uses one temporary odd spinor. */
+lqcd_status lqcd_mhat(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, double kappa, int dagger,
+                      void *stream);
+
+/* ------------------------------------------------------------ solver */
+
+typedef struct {
+    double tol;           /* stop when the true |r| <= tol |b| (r = b - Mhat^dag Mhat x) */
+    int maxiter;          /* total iteration cap (LQCD_ENOCONV when reached) */
+    lqcd_prec sloppy;     /* LQCD_F64: plain FP64 CG.  F32/F16N/BF16: reliable-update mixed
+                             CG with that sloppy storage (FP32 arithmetic, FP64 dot products,
+                             FP64 residual recomputation and solution accumulation) */
+    double delta;         /* reliable-update threshold: recompute the true residual when the
+                             sloppy |r| drops below delta * max |r| since the last update */
+    int max_restarts;     /* FP64 CG only: restarts allowed when the true residual fails */
+} lqcd_cg_params;
+
+typedef struct {
+    int iters;            /* CG iterations (sloppy iterations for the mixed solver) */
+    int restarts;         /* FP64 restarts / mixed reliable updates */
+    double true_rel_res;  /* |b - A x| / |b| in FP64 at exit */
+    double seconds;       /* wall time of the call */
+} lqcd_cg_info;
+
+/* Solve Mhat^dag Mhat x = b on the even sites (the matrix inversion of the
+ * paper's Sec. 6, done there by QUDA), x0 = 0.  x, b: EVEN F64 spinors.
+ * U: F64/18 master links; for a mixed solve also pass the sloppy 12-real
+ * copy U_sloppy in the matching precision (NULL for FP64).
+ * Returns LQCD_ENOCONV (x holds the last iterate) when maxiter is reached. */
+lqcd_status lqcd_cg_solve(lqcd_field *x, const lqcd_field *U, const lqcd_field *U_sloppy, const lqcd_field *b,
+                          double kappa, const lqcd_cg_params *params, lqcd_cg_info *info, void *stream);
+
+/* ------------------------------------------------------------ forces and updates */
+
+/* Gauge (staple) force with its traceless anti-Hermitian projection, fused
+ * with the momentum update (paper Sec. 1, "force term calculation",
+ * "projection of fields", "momentum updates"):
+ *   F = -(i beta / 12) TA(U_mu(x) A_mu(x)), A the staple sum,
+ *   TA(W) = (W - W^dag) - Tr(W - W^dag)/3,   P <- P - coeff * F (coefficients).
+ * P: MOMENTUM, U: GAUGE F64/18. */
+lqcd_status lqcd_gauge_force(lqcd_field *P, const lqcd_field *U, double beta, double coeff, void *stream);
+
+/* Two-flavour fermion force fused with the momentum update, given the even
+ * solution X_e = (Mhat^dag Mhat)^-1 phi_e:
+ *   Y_e = Mhat X_e, A = (X_e, Doe X_e), B = (Y_e, Deo^dag Y_e),
+ *   Q1 = sum_spin [s U A(x+mu)] [(1 - gamma_mu) B(x)]^dag,
+ *   Q2 = sum_spin A(x) [s U (1 + gamma_mu) B(x+mu)]^dag,
+ *   F = (i kappa^2 / 2) TA(Q1 - Q2),  P <- P - coeff * F.
+ * P: MOMENTUM, U: GAUGE F64/18, X_e: EVEN F64.  Uses three temporary spinors. */
+lqcd_status lqcd_fermion_force(lqcd_field *P, const lqcd_field *U, const lqcd_field *X_e, double kappa,
+                               double coeff, void *stream);
+
+/* SU(3) exponential link update (paper Sec. 1, "exponentiating of SU(3)
+ * matrices"): U_mu(x) <- exp(i c P_mu(x)) U_mu(x), exp by Cayley-Hamilton
+ * (Morningstar & Peardon 2004).  If U_sloppy is not NULL it receives the
+ * 12-real copy of the new links in its precision. */
+lqcd_status lqcd_link_update(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *U_sloppy, void *stream);
+
+/* Reunitarization (paper Sec. 1): rows 0, 1 by Gram-Schmidt, row 2 =
+ * conj(row0 x row1).  max_dev_out (host, may be NULL) receives the maximum
+ * over links of max_ij |(U U^dag - 1)_ij| before the projection. */
+lqcd_status lqcd_reunitarize(lqcd_field *U, double *max_dev_out, void *stream);
+
+/* ------------------------------------------------------------ reductions (Sec. 1, `sum`) */
+
+/* Mean plaquette (1/6V) sum_x sum_{mu<nu} Re Tr U_munu(x) / 3 (FP64,
+ * deterministic fixed-order reduction).  out: host. */
+lqcd_status lqcd_plaquette(const lqcd_field *U, double *out, void *stream);
+
+/* Kinetic energy 1/2 sum p_a^2.  out: host. */
+lqcd_status lqcd_kinetic_energy(const lqcd_field *P, double *out, void *stream);
+
+/* Re <a, b> = sum of products of the reals of two FP64 spinor fields of the
+ * same kind.  out: host. */
+lqcd_status lqcd_spinor_dot(const lqcd_field *a, const lqcd_field *b, double *out, void *stream);
+
+/* ------------------------------------------------------------ HMC driver */
+
+typedef struct {
+    double beta, kappa, tau;
+    int nsteps;
+    lqcd_integrator integrator; /* leapfrog or Omelyan 2MN (lambda = 0.1931833275037836) */
+    int n_flavors;              /* 0: pure gauge, 2: two Wilson flavours */
+    lqcd_cg_params cg;          /* solver of every force and action evaluation */
+    int reunitarize;            /* 1: reunitarize the links after the accept/reject */
+    int metropolis;             /* 1: accept iff u < exp(-dH); 0: always accept */
+} lqcd_hmc_params;
+
+typedef struct {
+    double dH, H0, H1;
+    double plaq;               /* after the trajectory (and reunitarization) */
+    double u;                  /* Metropolis uniform */
+    double max_unitarity_dev;  /* before reunitarization */
+    double seconds;
+    double cg_true_rel_res_max;
+    int accepted;
+    int cg_iters;              /* summed over all solves of the trajectory */
+    int n_solves;
+    int cg_failures;
+    uint32_t traj;             /* trajectory counter used for the random numbers */
+} lqcd_traj_info;
+
+/* State of one Markov chain on the device: borrows the caller's FP64 gauge
+ * field U (updated in place) and owns the momenta, pseudofermion fields, the
+ * backup of U, the sloppy link copy and the solver work space.
+ * seed/chain form the Philox key; traj0 is the first trajectory counter. */
+lqcd_status lqcd_hmc_state_create(lqcd_field *U, uint32_t seed, uint32_t chain, uint32_t traj0,
+                                  lqcd_hmc_state **out);
+lqcd_status lqcd_hmc_state_destroy(lqcd_hmc_state *s);
+
+/* Accessors for tests and checkpointing: the borrowed links, the momenta and
+ * phi_e; the trajectory counter (read, and set for resume). */
+lqcd_status lqcd_hmc_state_fields(lqcd_hmc_state *s, lqcd_field **U, lqcd_field **P, lqcd_field **phi);
+lqcd_status lqcd_hmc_state_traj(lqcd_hmc_state *s, uint32_t *traj_out, const uint32_t *traj_in);
+
+/* Refresh of the state for its current trajectory counter: momenta, eta and
+ * phi_e = Mhat^dag eta_e; H0 (host, may be NULL) = T + S_g + eta^dag eta. */
+lqcd_status lqcd_hmc_refresh(lqcd_hmc_state *s, const lqcd_hmc_params *p, double *H0, void *stream);
+
+/* H = T + S_g + S_f for the state's current (U, P, phi) (S_f by a CG solve). */
+lqcd_status lqcd_hmc_hamiltonian(lqcd_hmc_state *s, const lqcd_hmc_params *p, double *H, void *stream);
+
+/* One molecular-dynamics step of length tau/nsteps with the state's phi, as
+ * a whole step (leapfrog: kick dt/2, drift dt, kick dt/2; Omelyan:
+ * lambda dt, dt/2, (1-2 lambda) dt, dt/2, lambda dt). */
+lqcd_status lqcd_md_step(lqcd_hmc_state *s, const lqcd_hmc_params *p, void *stream);
+
+/* One full trajectory (paper Sec. 1 and 6.2): refresh, nsteps MD steps with
+ * adjacent kicks merged, H1, Metropolis with u from Philox purpose 3 counter
+ * (0, 0, 3, traj), restore U on reject, optional reunitarization, plaquette.
+ * Increments the state's trajectory counter.  info: host. */
+lqcd_status lqcd_hmc_trajectory(lqcd_hmc_state *s, const lqcd_hmc_params *p, lqcd_traj_info *info,
+                                void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LQCD_H */

@@ -1,0 +1,363 @@
+// cg.cu -- conjugate gradient on Mhat^dag Mhat (the matrix inversion the paper
+// hands to QUDA, Sec. 6).
+//
+// Plain FP64 CG, or reliable-update mixed precision (Clark, Babich, Barros,
+// Brower, Rebbi 2010): the iteration runs on sloppy fields (FP32, FP16+norm
+// or BF16 storage, FP32 arithmetic, FP64 dot products) and whenever the sloppy
+// residual has dropped by delta since the last update the solution increment
+// is folded into the FP64 solution and the residual recomputed in FP64.
+//
+// Every scalar (rr, pAp, alpha, beta) lives on the device: the reduction
+// kernels compute them in a fixed order and raise a pause flag when the host
+// must act, and every iteration kernel is a no-op while the flag is set.  The
+// host therefore synchronises only once per chunk of iterations, yet the
+// iteration count is exactly that of a per-iteration check.
+#include <chrono>
+#include <cmath>
+
+#include "cg.cuh"
+
+namespace lqcd {
+
+constexpr int BB = 256;
+constexpr int CG_CHUNK = 4;
+
+__global__ void cg_pap_kernel(const double *partials, int nb, CgScalars *sc)
+{
+    if (sc->pause) return;
+    double s[1];
+    final_sum_block<1>(partials, nb, s);
+    if (threadIdx.x == 0) {
+        double pAp = s[0];
+        sc->pAp = pAp;
+        if (!(pAp > 0.0) || !isfinite(pAp)) {
+            sc->alpha = 0.0;
+            sc->pause = 1;
+            sc->reason = PAUSE_NONFINITE;
+        } else {
+            sc->alpha = sc->rr / pAp;
+        }
+    }
+}
+
+__global__ void cg_rr_kernel(const double *partials, int nb, CgScalars *sc)
+{
+    if (sc->pause) return;
+    double s[1];
+    final_sum_block<1>(partials, nb, s);
+    if (threadIdx.x == 0) {
+        double rr_new = s[0];
+        sc->rr_new = rr_new;
+        sc->iter += 1;
+        int reason = PAUSE_NONE;
+        if (!isfinite(rr_new))
+            reason = PAUSE_NONFINITE;
+        else if (rr_new <= sc->stop2)
+            reason = PAUSE_CONVERGED;
+        else if (sc->delta2 > 0.0 && rr_new < sc->delta2 * sc->maxrr2)
+            reason = PAUSE_RELIABLE;
+        else if (sc->iter >= sc->maxiter)
+            reason = PAUSE_MAXITER;
+        if (reason != PAUSE_NONE) {
+            sc->pause = 1;
+            sc->reason = reason;
+        } else {
+            sc->beta = rr_new / sc->rr;
+            sc->rr = rr_new;
+            sc->maxrr2 = fmax(sc->maxrr2, rr_new);
+        }
+    }
+}
+
+__global__ void cg_set_kernel(CgScalars *sc, double rr, double beta, double maxrr2)
+{
+    sc->rr = rr;
+    sc->beta = beta;
+    sc->maxrr2 = maxrr2;
+    sc->pause = 0;
+    sc->reason = PAUSE_NONE;
+}
+
+template <lqcd_prec P>
+__global__ void p_update_kernel(SpinorRef<P> p, SpinorRef<P> r, const CgScalars *sc, int Vh)
+{
+    if (sc->pause) return;
+    int cb = blockIdx.x * BB + threadIdx.x;
+    if (cb >= Vh) return;
+    using R = typename std::conditional<P == LQCD_F64, double, float>::type;
+    R beta = (R)sc->beta;
+    Sp<R> pv = p.template load_rw<R>(cb);
+    Sp<R> rv = r.template load_rw<R>(cb);
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) pv.c[a][k] = rv.c[a][k] + beta * pv.c[a][k];
+    p.store(cb, pv);
+}
+
+// r = b - t and block partials of |r|^2
+__global__ void __launch_bounds__(BB) residual_kernel(SpinorRef<LQCD_F64> r, SpinorRef<LQCD_F64> b,
+                                                      SpinorRef<LQCD_F64> t, double *partials, int nb, int Vh)
+{
+    int cb = blockIdx.x * BB + threadIdx.x;
+    double n2[1] = {0.0};
+    if (cb < Vh) {
+        Sp<double> bv = b.load_rw<double>(cb), tv = t.load_rw<double>(cb);
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                bv.c[a][k] = bv.c[a][k] - tv.c[a][k];
+                n2[0] += norm2(bv.c[a][k]);
+            }
+        r.store(cb, bv);
+    }
+    block_sum_store<1, BB>(n2, partials, nb);
+}
+
+// x += xs; xs = 0
+__global__ void accum_zero_kernel(SpinorRef<LQCD_F64> x, SpinorRef<LQCD_F32> xs, int Vh)
+{
+    int cb = blockIdx.x * BB + threadIdx.x;
+    if (cb >= Vh) return;
+    Sp<double> xv = x.load_rw<double>(cb);
+    Sp<double> dv = xs.load_rw<double>(cb);
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) xv.c[a][k] = xv.c[a][k] + dv.c[a][k];
+    x.store(cb, xv);
+    xs.store(cb, sp_zero<double>());
+}
+
+// ---------------------------------------------------------------- pinned scalars
+
+struct Pinned {
+    CgScalars *sc = nullptr;
+    double *d = nullptr;
+    ~Pinned()
+    {
+        if (sc) cudaFreeHost(sc);
+        if (d) cudaFreeHost(d);
+    }
+};
+static thread_local Pinned g_pinned;
+
+static lqcd_status pinned()
+{
+    if (!g_pinned.sc) {
+        LQCD_CUDA(cudaMallocHost((void **)&g_pinned.sc, sizeof(CgScalars)));
+        LQCD_CUDA(cudaMallocHost((void **)&g_pinned.d, 8 * sizeof(double)));
+    }
+    return LQCD_OK;
+}
+
+// ---------------------------------------------------------------- work space
+
+lqcd_status CgWorkspace::ensure(const lqcd_lattice &l, lqcd_prec sl, cudaStream_t s)
+{
+    if (ready && same_lattice(lat, l) && sloppy == sl) return LQCD_OK;
+    ready = false;
+    for (FieldPtr *f : {&r64, &t64a, &t64b, &tmpo64, &p64, &xs, &rs, &ps, &ts, &tmpos}) {
+        if (f->f) lqcd_field_free(f->f);
+        f->f = nullptr;
+    }
+    lat = l;
+    sloppy = sl;
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &r64.f));
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &t64a.f));
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &t64b.f));
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F64, 0, &tmpo64.f));
+    if (sl == LQCD_F64) {
+        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &p64.f));
+    } else {
+        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F32, 0, &xs.f));
+        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, sl, 0, &rs.f));
+        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, sl, 0, &ps.f));
+        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, sl, 0, &ts.f));
+        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, sl, 0, &tmpos.f));
+    }
+    int Vh = make_geo(lat).Vh;
+    size_t np = (size_t)std::max(std::max(dslash_blocks(Vh), nblocks_for(Vh, BB)), 2048);
+    LQCD_TRY(sc.alloc(sizeof(CgScalars), s));
+    LQCD_TRY(partials.alloc(np * sizeof(double), s));
+    LQCD_TRY(scalars.alloc(8 * sizeof(double), s));
+    ready = true;
+    return LQCD_OK;
+}
+
+static lqcd_status launch_p_update(lqcd_field *p, lqcd_field *r, const CgScalars *sc, cudaStream_t s)
+{
+    int nb = nblocks_for(p->Vh, BB);
+    switch (p->prec) {
+    case LQCD_F64: p_update_kernel<LQCD_F64><<<nb, BB, 0, s>>>(spinor_ref<LQCD_F64>(p), spinor_ref<LQCD_F64>(r), sc, p->Vh); break;
+    case LQCD_F32: p_update_kernel<LQCD_F32><<<nb, BB, 0, s>>>(spinor_ref<LQCD_F32>(p), spinor_ref<LQCD_F32>(r), sc, p->Vh); break;
+    case LQCD_F16N: p_update_kernel<LQCD_F16N><<<nb, BB, 0, s>>>(spinor_ref<LQCD_F16N>(p), spinor_ref<LQCD_F16N>(r), sc, p->Vh); break;
+    case LQCD_BF16: p_update_kernel<LQCD_BF16><<<nb, BB, 0, s>>>(spinor_ref<LQCD_BF16>(p), spinor_ref<LQCD_BF16>(r), sc, p->Vh); break;
+    }
+    LQCD_LAUNCHED();
+    return LQCD_OK;
+}
+
+// true residual r64 = b - A x in FP64; |r64|^2 returned in *rr
+static lqcd_status true_residual(CgWorkspace &ws, const lqcd_field *x, const lqcd_field *U, const lqcd_field *b,
+                                 double kappa, double *rr, cudaStream_t s)
+{
+    LQCD_TRY(mhat_apply(ws.t64a.f, U, x, kappa, 0, ws.tmpo64.f, nullptr, s));
+    LQCD_TRY(mhat_apply(ws.t64b.f, U, ws.t64a.f, kappa, 1, ws.tmpo64.f, nullptr, s));
+    int Vh = x->Vh, nb = nblocks_for(Vh, BB);
+    residual_kernel<<<nb, BB, 0, s>>>(spinor_ref<LQCD_F64>(ws.r64.f), spinor_ref<LQCD_F64>(b),
+                                      spinor_ref<LQCD_F64>(ws.t64b.f), (double *)ws.partials.p, nb, Vh);
+    LQCD_LAUNCHED();
+    LQCD_TRY(reduce_partials((double *)ws.partials.p, nb, 1, (double *)ws.scalars.p, s));
+    LQCD_TRY(pinned());
+    LQCD_TRY(read_scalars((double *)ws.scalars.p, g_pinned.d, 1, s));
+    *rr = g_pinned.d[0];
+    return LQCD_OK;
+}
+
+lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, const lqcd_field *Us,
+                        const lqcd_field *b, double kappa, const lqcd_cg_params &prm, lqcd_cg_info *info,
+                        cudaStream_t s)
+{
+    auto t_start = std::chrono::steady_clock::now();
+    const bool mixed = prm.sloppy != LQCD_F64;
+    LQCD_TRY(ws.ensure(x->lat, prm.sloppy, s));
+    LQCD_TRY(pinned());
+    int Vh = x->Vh;
+    double k2 = kappa * kappa;
+
+    LQCD_TRY(spinor_dot_dev(b, b, (double *)ws.scalars.p, ws.partials, s));
+    LQCD_TRY(read_scalars((double *)ws.scalars.p, g_pinned.d, 1, s));
+    double bb = g_pinned.d[0];
+    LQCD_CUDA(cudaMemsetAsync(x->data, 0, x->bytes, s));
+    lqcd_cg_info inf{0, 0, 0.0, 0.0};
+    auto finish = [&](lqcd_status st) {
+        inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+        if (info) *info = inf;
+        return st;
+    };
+    if (!std::isfinite(bb)) {
+        set_error("cg: |b|^2 is not finite");
+        return finish(LQCD_ENUMERIC);
+    }
+    if (bb == 0.0) {
+        LQCD_CUDA(cudaStreamSynchronize(s));
+        return finish(LQCD_OK);
+    }
+
+    lqcd_field *P, *R, *T, *TMP, *XS;
+    const lqcd_field *UU;
+    LQCD_CUDA(cudaMemcpyAsync(ws.r64.f->data, b->data, b->bytes, cudaMemcpyDeviceToDevice, s));
+    if (mixed) {
+        LQCD_REQUIRE(Us && Us->kind == LQCD_GAUGE && Us->prec == prm.sloppy && Us->recon == 12,
+                     "cg: mixed solve needs a 12-real link copy in the sloppy precision");
+        LQCD_TRY(lqcd_field_copy(ws.rs.f, b, s));
+        LQCD_TRY(lqcd_field_copy(ws.ps.f, b, s));
+        LQCD_CUDA(cudaMemsetAsync(ws.xs.f->data, 0, ws.xs.f->bytes, s));
+        P = ws.ps.f, R = ws.rs.f, T = ws.ts.f, TMP = ws.tmpos.f, XS = ws.xs.f, UU = Us;
+    } else {
+        LQCD_CUDA(cudaMemcpyAsync(ws.p64.f->data, b->data, b->bytes, cudaMemcpyDeviceToDevice, s));
+        P = ws.p64.f, R = ws.r64.f, T = ws.t64a.f, TMP = ws.tmpo64.f, XS = x, UU = U;
+    }
+    CgScalars &h = *g_pinned.sc;
+    h = CgScalars{};
+    h.rr = bb;
+    h.stop2 = prm.tol * prm.tol * bb;
+    h.delta2 = mixed ? prm.delta * prm.delta : 0.0;
+    h.maxrr2 = bb;
+    h.maxiter = prm.maxiter;
+    CgScalars *sc = (CgScalars *)ws.sc.p;
+    LQCD_CUDA(cudaMemcpyAsync(sc, &h, sizeof(CgScalars), cudaMemcpyHostToDevice, s));
+    LQCD_CUDA(cudaStreamSynchronize(s)); // h is reused below
+
+    double *partials = (double *)ws.partials.p;
+    int nbd = dslash_blocks(Vh);
+    const int *skip = &sc->pause;
+    double rr_true = bb;
+    for (;;) {
+        for (int k = 0; k < CG_CHUNK; k++) {
+            LQCD_TRY(dslash_plain(TMP, UU, P, 0, skip, s));
+            LQCD_TRY(dslash_xpay(T, UU, TMP, 0, P, -k2, partials, skip, s));
+            cg_pap_kernel<<<1, 1024, 0, s>>>(partials, nbd, sc);
+            LQCD_LAUNCHED();
+            LQCD_TRY(dslash_plain(TMP, UU, T, 1, skip, s));
+            LQCD_TRY(dslash_cg(UU, TMP, 1, T, -k2, XS, R, P, partials, sc, s));
+            cg_rr_kernel<<<1, 1024, 0, s>>>(partials, nbd, sc);
+            LQCD_LAUNCHED();
+            LQCD_TRY(launch_p_update(P, R, sc, s));
+        }
+        LQCD_CUDA(cudaMemcpyAsync(&h, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+        LQCD_CUDA(cudaStreamSynchronize(s));
+        if (!h.pause) continue;
+        inf.iters = h.iter;
+        if (h.reason == PAUSE_NONFINITE) {
+            set_error("cg: non-finite value after %d iterations", h.iter);
+            return finish(LQCD_ENUMERIC);
+        }
+        if (mixed) {
+            accum_zero_kernel<<<nblocks_for(Vh, BB), BB, 0, s>>>(spinor_ref<LQCD_F64>(x), spinor_ref<LQCD_F32>(XS), Vh);
+            LQCD_LAUNCHED();
+        }
+        LQCD_TRY(true_residual(ws, x, U, b, kappa, &rr_true, s));
+        inf.true_rel_res = std::sqrt(rr_true / bb);
+        if (!std::isfinite(rr_true)) {
+            set_error("cg: non-finite true residual");
+            return finish(LQCD_ENUMERIC);
+        }
+        if (rr_true <= h.stop2) return finish(LQCD_OK);
+        if (h.reason == PAUSE_MAXITER || h.iter >= prm.maxiter) {
+            set_error("cg: no convergence in %d iterations (true |r|/|b| = %.3e)", h.iter, inf.true_rel_res);
+            return finish(LQCD_ENOCONV);
+        }
+        inf.restarts++;
+        double beta;
+        if (mixed) { // reliable update: continue with the FP64 residual
+            LQCD_TRY(lqcd_field_copy(ws.rs.f, ws.r64.f, s));
+            beta = rr_true / h.rr;
+        } else { // the iterated residual lied: restart from the true one
+            if (inf.restarts > prm.max_restarts) {
+                set_error("cg: true residual %.3e above tolerance after %d restarts", inf.true_rel_res,
+                          prm.max_restarts);
+                return finish(LQCD_ENOCONV);
+            }
+            beta = 0.0;
+        }
+        cg_set_kernel<<<1, 1, 0, s>>>(sc, rr_true, beta, rr_true);
+        LQCD_LAUNCHED();
+        LQCD_TRY(launch_p_update(P, R, sc, s));
+    }
+}
+
+} // namespace lqcd
+
+using namespace lqcd;
+
+extern "C" lqcd_status lqcd_cg_solve(lqcd_field *x, const lqcd_field *U, const lqcd_field *U_sloppy,
+                                     const lqcd_field *b, double kappa, const lqcd_cg_params *params,
+                                     lqcd_cg_info *info, void *stream)
+{
+    LQCD_REQUIRE(x && U && b && params, "cg_solve: NULL argument");
+    LQCD_REQUIRE(x->kind == LQCD_SPINOR_EVEN && b->kind == LQCD_SPINOR_EVEN && x->prec == LQCD_F64 &&
+                     b->prec == LQCD_F64,
+                 "cg_solve: x and b must be EVEN FP64 spinors");
+    LQCD_REQUIRE(x != b, "cg_solve: x must differ from b");
+    LQCD_REQUIRE(U->kind == LQCD_GAUGE && U->prec == LQCD_F64, "cg_solve: U must be the FP64 gauge field");
+    LQCD_REQUIRE(same_lattice(x->lat, U->lat) && same_lattice(b->lat, U->lat), "cg_solve: lattices differ");
+    LQCD_REQUIRE(params->tol > 0 && params->maxiter > 0, "cg_solve: tol and maxiter must be positive");
+    LQCD_REQUIRE(params->sloppy >= LQCD_F64 && params->sloppy <= LQCD_BF16, "cg_solve: bad sloppy precision");
+    LQCD_REQUIRE(params->sloppy == LQCD_F64 || (params->delta > 0 && params->delta < 1),
+                 "cg_solve: delta must lie in (0, 1)");
+    cudaStream_t s = (cudaStream_t)stream;
+    FieldPtr tmpU;
+    const lqcd_field *Us = U_sloppy;
+    if (params->sloppy != LQCD_F64 && !Us) {
+        LQCD_TRY(lqcd_field_alloc(&U->lat, LQCD_GAUGE, params->sloppy, 12, &tmpU.f));
+        LQCD_TRY(lqcd_field_copy(tmpU.f, U, s));
+        Us = tmpU.f;
+    }
+    CgWorkspace ws;
+    lqcd_status st = cg_solve_ws(ws, x, U, Us, b, kappa, *params, info, s);
+    cudaStreamSynchronize(s); // work space is released on return
+    return st;
+}

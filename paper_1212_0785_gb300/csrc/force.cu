@@ -1,0 +1,208 @@
+// force.cu -- gauge (staple) force and two-flavour Wilson fermion force, each
+// projected onto su(3) and fused with the momentum update P <- P - coeff F
+// (paper Sec. 1: "force term calculation", "projection of fields",
+// "momentum updates").  One thread per link, FP64.
+//
+// Both forces are written as f_a = Im Tr(lambda_a W) of one 3x3 matrix W per
+// link: for F = c TA(W) = c [(W - W^dag) - Tr(W - W^dag)/3] the Gell-Mann
+// coefficients are 2 Re Tr(T_a F) = Re(c Tr(lambda_a (W - W^dag)))
+// = Re(2 i c Im Tr(lambda_a W)), so
+//   gauge   F = -(i beta/12) TA(U A):  f_a = (beta / 6) Im Tr(lambda_a U A)
+//   fermion F = (i kappa^2/2) TA(Q):   f_a = -kappa^2 Im Tr(lambda_a Q).
+#include "dslash.cuh"
+#include "spin.cuh"
+#include "su3_device.cuh"
+
+namespace lqcd {
+
+constexpr int FB = 128;
+
+__device__ __forceinline__ void link_of_thread(long t, int Vh, int &mu, int &par, int &cb)
+{
+    cb = (int)(t % Vh);
+    int mp = (int)(t / Vh);
+    mu = mp >> 1;
+    par = mp & 1;
+}
+
+__device__ __forceinline__ int step_cb(const Geo &g, const int c[4], int dir, int s)
+{
+    int d[4] = {c[0], c[1], c[2], c[3]};
+    d[dir] += s;
+    if (d[dir] == g.L[dir]) d[dir] = 0;
+    if (d[dir] < 0) d[dir] = g.L[dir] - 1;
+    return coords_cb(g, d);
+}
+
+__device__ __forceinline__ void m3_acc(M3<double> &a, const M3<double> &b)
+{
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) a.e[i][j] = a.e[i][j] + b.e[i][j];
+}
+
+// staple sum A_mu(x): U_mu(x) A_mu(x) = sum of the 6 plaquettes starting with the link
+__global__ void __launch_bounds__(FB) gauge_force_kernel(MomRef P, GaugeRef<LQCD_F64> U, Geo g, double cf)
+{
+    long t = blockIdx.x * (long)FB + threadIdx.x;
+    if (t >= 8L * g.Vh) return;
+    int mu, par, cb;
+    link_of_thread(t, g.Vh, mu, par, cb);
+    int c[4];
+    cb_coords(g, cb, par, c);
+    int cpm[4] = {c[0], c[1], c[2], c[3]};
+    cpm[mu] = (c[mu] + 1 == g.L[mu]) ? 0 : c[mu] + 1;
+    int cb_pm = coords_cb(g, cpm);
+    M3<double> A;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) A.e[i][j] = cx<double>(0, 0);
+    for (int nu = 0; nu < 4; nu++) {
+        if (nu == mu) continue;
+        int cb_pn = step_cb(g, c, nu, +1);
+        int cb_mn = step_cb(g, c, nu, -1);
+        int cb_pmmn = step_cb(g, cpm, nu, -1);
+        // upper: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+        M3<double> up = m3_mul_dag(U.load<double>(nu, 1 - par, cb_pm), U.load<double>(mu, 1 - par, cb_pn));
+        up = m3_mul_dag(up, U.load<double>(nu, par, cb));
+        m3_acc(A, up);
+        // lower: U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu) = (U_mu(x-nu) U_nu(x+mu-nu))^dag U_nu(x-nu)
+        M3<double> lo = m3_mul(U.load<double>(mu, 1 - par, cb_mn), U.load<double>(nu, par, cb_pmmn));
+        lo = m3_dag_mul(lo, U.load<double>(nu, 1 - par, cb_mn));
+        m3_acc(A, lo);
+    }
+    M3<double> W = m3_mul(U.load<double>(mu, par, cb), A);
+    double gl[8];
+    im_tr_lambda(W, gl);
+#pragma unroll
+    for (int a = 0; a < 8; a++) P.d[P.idx(mu, par, a, cb)] -= cf * gl[a];
+}
+
+// Fermion force on link (x, mu), x of parity par:
+//   Q = sum_spin [s U A(x+mu)] [(1 - gamma_mu) B(x)]^dag - A(x) [s U (1 + gamma_mu) B(x+mu)]^dag
+// A = (A_e, A_o), B = (B_e, B_o) full-lattice spinors split by parity.
+template <int MU>
+__device__ __forceinline__ void fermion_force_link(MomRef &P, const GaugeRef<LQCD_F64> &U, const Geo &g, int par,
+                                                   int cb, const int c[4], const SpinorRef<LQCD_F64> (&A)[2],
+                                                   const SpinorRef<LQCD_F64> (&B)[2], double cf)
+{
+    int cy[4] = {c[0], c[1], c[2], c[3]};
+    bool wrap = (c[MU] + 1 == g.L[MU]);
+    cy[MU] = wrap ? 0 : c[MU] + 1;
+    int cby = coords_cb(g, cy);
+    double s = (MU == 3 && wrap && g.t_bc < 0) ? -1.0 : 1.0;
+    M3<double> u = U.load<double>(MU, par, cb);
+    Sp<double> Ay = A[1 - par].load_rw<double>(cby);
+    Sp<double> Ax = A[par].load_rw<double>(cb);
+    Sp<double> Bx = B[par].load_rw<double>(cb);
+    Sp<double> By = B[1 - par].load_rw<double>(cby);
+    // w1 = (1 - gamma) B(x) as a full spinor
+    Sp<double> w1 = sp_zero<double>();
+    accumulate<MU, -1>(w1, project<MU, -1>(Bx));
+    // w2 = s U (1 + gamma) B(y): project, multiply the two rows, reconstruct
+    Sp<double> w2 = sp_zero<double>();
+    {
+        Hs<double> h = mul_link(u, project<MU, +1>(By));
+        accumulate<MU, +1>(w2, h);
+    }
+    M3<double> Q;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) Q.e[a][b] = cx<double>(0, 0);
+#pragma unroll
+    for (int sp = 0; sp < 4; sp++) {
+        Cx<double> v1[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) v1[a] = u.e[a][0] * Ay.c[sp][0] + u.e[a][1] * Ay.c[sp][1] + u.e[a][2] * Ay.c[sp][2];
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int b = 0; b < 3; b++)
+                Q.e[a][b] = Q.e[a][b] + s * (v1[a] * conj(w1.c[sp][b]) - Ax.c[sp][a] * conj(w2.c[sp][b]));
+    }
+    double gl[8];
+    im_tr_lambda(Q, gl);
+    // P -= coeff * f with f_a = -kappa^2 g_a
+#pragma unroll
+    for (int a = 0; a < 8; a++) P.d[P.idx(MU, par, a, cb)] += cf * gl[a];
+}
+
+__global__ void __launch_bounds__(FB) fermion_force_kernel(MomRef P, GaugeRef<LQCD_F64> U, Geo g,
+                                                           SpinorRef<LQCD_F64> Ae, SpinorRef<LQCD_F64> Ao,
+                                                           SpinorRef<LQCD_F64> Be, SpinorRef<LQCD_F64> Bo, double cf)
+{
+    long t = blockIdx.x * (long)FB + threadIdx.x;
+    if (t >= 8L * g.Vh) return;
+    int mu, par, cb;
+    link_of_thread(t, g.Vh, mu, par, cb);
+    int c[4];
+    cb_coords(g, cb, par, c);
+    const SpinorRef<LQCD_F64> A[2] = {Ae, Ao};
+    const SpinorRef<LQCD_F64> B[2] = {Be, Bo};
+    switch (mu) {
+    case 0: fermion_force_link<0>(P, U, g, par, cb, c, A, B, cf); break;
+    case 1: fermion_force_link<1>(P, U, g, par, cb, c, A, B, cf); break;
+    case 2: fermion_force_link<2>(P, U, g, par, cb, c, A, B, cf); break;
+    default: fermion_force_link<3>(P, U, g, par, cb, c, A, B, cf); break;
+    }
+}
+
+lqcd_status gauge_force_dev(lqcd_field *P, const lqcd_field *U, double beta, double coeff, cudaStream_t s)
+{
+    Geo g = make_geo(U->lat);
+    gauge_force_kernel<<<nblocks_for(8L * g.Vh, FB), FB, 0, s>>>(mom_ref(P), gauge_ref<LQCD_F64>(U), g,
+                                                                   coeff * beta / 6.0);
+    LQCD_LAUNCHED();
+    return LQCD_OK;
+}
+
+// A_o = Doe X_e, Y_e = Mhat X_e = X_e - kappa^2 Deo A_o, B_o = Doe^dag-hop Y_e, then the link kernel
+lqcd_status fermion_force_dev(lqcd_field *P, const lqcd_field *U, const lqcd_field *X, double kappa, double coeff,
+                              lqcd_field *Ao, lqcd_field *Ye, lqcd_field *Bo, cudaStream_t s)
+{
+    LQCD_TRY(dslash_plain(Ao, U, X, 0, nullptr, s));
+    LQCD_TRY(dslash_xpay(Ye, U, Ao, 0, X, -kappa * kappa, nullptr, nullptr, s));
+    LQCD_TRY(dslash_plain(Bo, U, Ye, 1, nullptr, s));
+    Geo g = make_geo(U->lat);
+    fermion_force_kernel<<<nblocks_for(8L * g.Vh, FB), FB, 0, s>>>(
+        mom_ref(P), gauge_ref<LQCD_F64>(U), g, spinor_ref<LQCD_F64>(X), spinor_ref<LQCD_F64>(Ao),
+        spinor_ref<LQCD_F64>(Ye), spinor_ref<LQCD_F64>(Bo), coeff * kappa * kappa);
+    LQCD_LAUNCHED();
+    return LQCD_OK;
+}
+
+} // namespace lqcd
+
+using namespace lqcd;
+
+extern "C" {
+
+lqcd_status lqcd_gauge_force(lqcd_field *P, const lqcd_field *U, double beta, double coeff, void *stream)
+{
+    LQCD_REQUIRE(P && U && P->kind == LQCD_MOMENTUM && U->kind == LQCD_GAUGE && U->prec == LQCD_F64,
+                 "gauge_force needs a momentum field and an F64 gauge field");
+    LQCD_REQUIRE(same_lattice(P->lat, U->lat), "gauge_force: lattices differ");
+    return gauge_force_dev(P, U, beta, coeff, (cudaStream_t)stream);
+}
+
+lqcd_status lqcd_fermion_force(lqcd_field *P, const lqcd_field *U, const lqcd_field *X_e, double kappa, double coeff,
+                               void *stream)
+{
+    LQCD_REQUIRE(P && U && X_e && P->kind == LQCD_MOMENTUM && U->kind == LQCD_GAUGE && U->prec == LQCD_F64,
+                 "fermion_force needs a momentum field and an F64 gauge field");
+    LQCD_REQUIRE(X_e->kind == LQCD_SPINOR_EVEN && X_e->prec == LQCD_F64, "fermion_force: X_e must be EVEN F64");
+    LQCD_REQUIRE(same_lattice(P->lat, U->lat) && same_lattice(X_e->lat, U->lat), "fermion_force: lattices differ");
+    FieldPtr Ao, Ye, Bo;
+    LQCD_TRY(lqcd_field_alloc(&U->lat, LQCD_SPINOR_ODD, LQCD_F64, 0, &Ao.f));
+    LQCD_TRY(lqcd_field_alloc(&U->lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &Ye.f));
+    LQCD_TRY(lqcd_field_alloc(&U->lat, LQCD_SPINOR_ODD, LQCD_F64, 0, &Bo.f));
+    cudaStream_t s = (cudaStream_t)stream;
+    LQCD_TRY(fermion_force_dev(P, U, X_e, kappa, coeff, Ao.f, Ye.f, Bo.f, s));
+    LQCD_CUDA(cudaStreamSynchronize(s)); // temporaries are freed on return
+    return LQCD_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,336 @@
+// hmc.cu -- Hybrid Monte Carlo driver: refresh, molecular dynamics with merged
+// kicks (leapfrog or Omelyan 2MN), Hamiltonian, Metropolis and
+// reunitarization, every field operation on the device (paper Sec. 1: the
+// whole trajectory runs on the accelerator; Sec. 6.2: Nf = 2 Wilson HMC).
+//
+// The host only sequences kernels and reads back the scalars it must decide
+// on (solver convergence, dH and the Metropolis uniform, the plaquette).
+#include <chrono>
+#include <cmath>
+
+#include "cg.cuh"
+#include "su3_device.cuh"
+
+namespace lqcd {
+
+// defined in field.cu / force.cu
+lqcd_status plaquette_sum(const lqcd_field *U, double *dst_dev, DevBuf &part, cudaStream_t s);
+lqcd_status kinetic_sum(const lqcd_field *P, double *dst_dev, DevBuf &part, cudaStream_t s);
+lqcd_status reunitarize_dev(lqcd_field *U, double *dst_dev, DevBuf &part, cudaStream_t s);
+lqcd_status link_update_dev(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *Us, cudaStream_t s);
+lqcd_status momentum_refresh_dev(lqcd_field *P, uint32_t seed, uint32_t chain, uint32_t traj, cudaStream_t s);
+lqcd_status eta_refresh_dev(lqcd_field *E, uint32_t seed, uint32_t chain, uint32_t traj, cudaStream_t s);
+lqcd_status gauge_force_dev(lqcd_field *P, const lqcd_field *U, double beta, double coeff, cudaStream_t s);
+lqcd_status fermion_force_dev(lqcd_field *P, const lqcd_field *U, const lqcd_field *X, double kappa, double coeff,
+                              lqcd_field *Ao, lqcd_field *Ye, lqcd_field *Bo, cudaStream_t s);
+
+constexpr double OMELYAN_LAMBDA = 0.1931833275037836;
+
+// first uniform of Philox(counter (0, 0, 3, traj), key (seed, chain))
+__global__ void metropolis_uniform_kernel(double *out, uint32_t seed, uint32_t chain, uint32_t traj)
+{
+    uint4 x = philox4x32_10(make_uint4(0u, 0u, 3u, traj), make_uint2(seed, chain));
+    out[0] = u52(x.x, x.y);
+}
+
+} // namespace lqcd
+
+using namespace lqcd;
+
+struct lqcd_hmc_state {
+    lqcd_field *U = nullptr; // borrowed
+    uint32_t seed = 0, chain = 0, traj = 0;
+    FieldPtr P, eta, phi, X, Ao, Ye, Bo, Ubak, Us;
+    CgWorkspace ws;
+    DevBuf part, scal;
+    double H0 = 0;
+    // statistics of the current trajectory
+    int cg_iters = 0, n_solves = 0, cg_failures = 0;
+    double cg_res_max = 0;
+};
+
+namespace lqcd {
+
+static lqcd_status check_params(const lqcd_hmc_params *p)
+{
+    LQCD_REQUIRE(p != nullptr, "hmc: params is NULL");
+    LQCD_REQUIRE(p->nsteps > 0 && p->tau > 0, "hmc: nsteps and tau must be positive");
+    LQCD_REQUIRE(p->integrator == LQCD_LEAPFROG || p->integrator == LQCD_OMELYAN, "hmc: unknown integrator");
+    LQCD_REQUIRE(p->n_flavors == 0 || p->n_flavors == 2, "hmc: n_flavors must be 0 or 2");
+    if (p->n_flavors == 2) {
+        LQCD_REQUIRE(p->cg.tol > 0 && p->cg.maxiter > 0, "hmc: cg tol and maxiter must be positive");
+        LQCD_REQUIRE(p->cg.sloppy == LQCD_F64 || (p->cg.delta > 0 && p->cg.delta < 1),
+                     "hmc: cg delta must lie in (0, 1) for a mixed solve");
+    }
+    return LQCD_OK;
+}
+
+// sloppy link copy matching the solver precision (NULL for FP64)
+static lqcd_status ensure_sloppy(lqcd_hmc_state *st, const lqcd_hmc_params *p, cudaStream_t s)
+{
+    if (p->n_flavors == 0 || p->cg.sloppy == LQCD_F64) return LQCD_OK;
+    if (st->Us.f && st->Us.f->prec != p->cg.sloppy) {
+        lqcd_field_free(st->Us.f);
+        st->Us.f = nullptr;
+    }
+    if (!st->Us.f) LQCD_TRY(lqcd_field_alloc(&st->U->lat, LQCD_GAUGE, p->cg.sloppy, 12, &st->Us.f));
+    return lqcd_field_copy(st->Us.f, st->U, s);
+}
+
+static lqcd_field *sloppy_links(lqcd_hmc_state *st, const lqcd_hmc_params *p)
+{
+    return (p->n_flavors == 2 && p->cg.sloppy != LQCD_F64) ? st->Us.f : nullptr;
+}
+
+static lqcd_status solve(lqcd_hmc_state *st, const lqcd_hmc_params *p, cudaStream_t s)
+{
+    lqcd_cg_info info{};
+    lqcd_status rc = cg_solve_ws(st->ws, st->X.f, st->U, sloppy_links(st, p), st->phi.f, p->kappa, p->cg, &info, s);
+    st->cg_iters += info.iters;
+    st->n_solves++;
+    st->cg_res_max = std::max(st->cg_res_max, info.true_rel_res);
+    if (rc == LQCD_ENOCONV) {
+        st->cg_failures++;
+        return LQCD_OK; // the trajectory goes on; the failure is reported in its info
+    }
+    return rc;
+}
+
+// P <- P - c F(U)
+static lqcd_status kick(lqcd_hmc_state *st, const lqcd_hmc_params *p, double c, cudaStream_t s)
+{
+    LQCD_TRY(gauge_force_dev(st->P.f, st->U, p->beta, c, s));
+    if (p->n_flavors == 2) {
+        LQCD_TRY(solve(st, p, s));
+        LQCD_TRY(fermion_force_dev(st->P.f, st->U, st->X.f, p->kappa, c, st->Ao.f, st->Ye.f, st->Bo.f, s));
+    }
+    return LQCD_OK;
+}
+
+static lqcd_status drift(lqcd_hmc_state *st, const lqcd_hmc_params *p, double c, cudaStream_t s)
+{
+    return link_update_dev(st->U, st->P.f, c, sloppy_links(st, p), s);
+}
+
+// scalars[0] = plaquette sum, [1] = sum p^2, [2] = fermion term
+static lqcd_status hamiltonian_parts(lqcd_hmc_state *st, cudaStream_t s)
+{
+    double *d = (double *)st->scal.p;
+    LQCD_TRY(plaquette_sum(st->U, d + 0, st->part, s));
+    LQCD_TRY(kinetic_sum(st->P.f, d + 1, st->part, s));
+    return LQCD_OK;
+}
+
+static double hamiltonian_from(const lqcd_hmc_state *st, const lqcd_hmc_params *p, const double *h)
+{
+    double V = 2.0 * st->U->Vh;
+    return 0.5 * h[1] + p->beta * (6.0 * V - h[0]) + (p->n_flavors == 2 ? h[2] : 0.0);
+}
+
+static lqcd_status refresh(lqcd_hmc_state *st, const lqcd_hmc_params *p, double *H0, cudaStream_t s)
+{
+    LQCD_TRY(ensure_sloppy(st, p, s));
+    LQCD_TRY(momentum_refresh_dev(st->P.f, st->seed, st->chain, st->traj, s));
+    double *d = (double *)st->scal.p;
+    LQCD_TRY(hamiltonian_parts(st, s));
+    if (p->n_flavors == 2) {
+        LQCD_TRY(eta_refresh_dev(st->eta.f, st->seed, st->chain, st->traj, s));
+        LQCD_TRY(mhat_apply(st->phi.f, st->U, st->eta.f, p->kappa, 1, st->Ao.f, nullptr, s));
+        LQCD_TRY(spinor_dot_dev(st->eta.f, st->eta.f, d + 2, st->part, s));
+    }
+    double h[3] = {0, 0, 0};
+    LQCD_TRY(read_scalars(d, h, 3, s));
+    st->H0 = hamiltonian_from(st, p, h);
+    if (H0) *H0 = st->H0;
+    return LQCD_OK;
+}
+
+static lqcd_status hamiltonian(lqcd_hmc_state *st, const lqcd_hmc_params *p, double *H, cudaStream_t s)
+{
+    double *d = (double *)st->scal.p;
+    LQCD_TRY(hamiltonian_parts(st, s));
+    if (p->n_flavors == 2) {
+        LQCD_TRY(solve(st, p, s));
+        LQCD_TRY(spinor_dot_dev(st->phi.f, st->X.f, d + 2, st->part, s));
+    }
+    double h[3] = {0, 0, 0};
+    LQCD_TRY(read_scalars(d, h, 3, s));
+    *H = hamiltonian_from(st, p, h);
+    return LQCD_OK;
+}
+
+static lqcd_status integrate(lqcd_hmc_state *st, const lqcd_hmc_params *p, cudaStream_t s)
+{
+    double dt = p->tau / p->nsteps;
+    int n = p->nsteps;
+    if (p->integrator == LQCD_LEAPFROG) {
+        LQCD_TRY(kick(st, p, 0.5 * dt, s));
+        for (int k = 0; k < n; k++) {
+            LQCD_TRY(drift(st, p, dt, s));
+            LQCD_TRY(kick(st, p, k == n - 1 ? 0.5 * dt : dt, s));
+        }
+    } else {
+        const double lam = OMELYAN_LAMBDA;
+        LQCD_TRY(kick(st, p, lam * dt, s));
+        for (int k = 0; k < n; k++) {
+            LQCD_TRY(drift(st, p, 0.5 * dt, s));
+            LQCD_TRY(kick(st, p, (1.0 - 2.0 * lam) * dt, s));
+            LQCD_TRY(drift(st, p, 0.5 * dt, s));
+            LQCD_TRY(kick(st, p, k == n - 1 ? lam * dt : 2.0 * lam * dt, s));
+        }
+    }
+    return LQCD_OK;
+}
+
+static void reset_stats(lqcd_hmc_state *st)
+{
+    st->cg_iters = st->n_solves = st->cg_failures = 0;
+    st->cg_res_max = 0;
+}
+
+} // namespace lqcd
+
+extern "C" {
+
+lqcd_status lqcd_hmc_state_create(lqcd_field *U, uint32_t seed, uint32_t chain, uint32_t traj0, lqcd_hmc_state **out)
+{
+    LQCD_REQUIRE(U && out, "hmc_state_create: NULL argument");
+    LQCD_REQUIRE(U->kind == LQCD_GAUGE && U->prec == LQCD_F64, "hmc_state_create: U must be an F64 gauge field");
+    lqcd_hmc_state *st = new lqcd_hmc_state();
+    st->U = U;
+    st->seed = seed;
+    st->chain = chain;
+    st->traj = traj0;
+    const lqcd_lattice &lat = U->lat;
+    lqcd_status rc = LQCD_OK;
+    if (rc == LQCD_OK) rc = lqcd_field_alloc(&lat, LQCD_MOMENTUM, LQCD_F64, 0, &st->P.f);
+    if (rc == LQCD_OK) rc = lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->eta.f);
+    if (rc == LQCD_OK) rc = lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->phi.f);
+    if (rc == LQCD_OK) rc = lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->X.f);
+    if (rc == LQCD_OK) rc = lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F64, 0, &st->Ao.f);
+    if (rc == LQCD_OK) rc = lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->Ye.f);
+    if (rc == LQCD_OK) rc = lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F64, 0, &st->Bo.f);
+    if (rc == LQCD_OK) rc = lqcd_field_alloc(&lat, LQCD_GAUGE, LQCD_F64, 18, &st->Ubak.f);
+    if (rc == LQCD_OK) rc = st->scal.alloc(8 * sizeof(double), nullptr);
+    if (rc != LQCD_OK) {
+        delete st;
+        return rc;
+    }
+    *out = st;
+    return LQCD_OK;
+}
+
+lqcd_status lqcd_hmc_state_destroy(lqcd_hmc_state *s)
+{
+    cudaDeviceSynchronize();
+    delete s;
+    return LQCD_OK;
+}
+
+lqcd_status lqcd_hmc_state_fields(lqcd_hmc_state *s, lqcd_field **U, lqcd_field **P, lqcd_field **phi)
+{
+    LQCD_REQUIRE(s, "hmc_state_fields: NULL state");
+    if (U) *U = s->U;
+    if (P) *P = s->P.f;
+    if (phi) *phi = s->phi.f;
+    return LQCD_OK;
+}
+
+lqcd_status lqcd_hmc_state_traj(lqcd_hmc_state *s, uint32_t *traj_out, const uint32_t *traj_in)
+{
+    LQCD_REQUIRE(s, "hmc_state_traj: NULL state");
+    if (traj_in) s->traj = *traj_in;
+    if (traj_out) *traj_out = s->traj;
+    return LQCD_OK;
+}
+
+lqcd_status lqcd_hmc_refresh(lqcd_hmc_state *s, const lqcd_hmc_params *p, double *H0, void *stream)
+{
+    LQCD_REQUIRE(s, "hmc_refresh: NULL state");
+    LQCD_TRY(check_params(p));
+    return refresh(s, p, H0, (cudaStream_t)stream);
+}
+
+lqcd_status lqcd_hmc_hamiltonian(lqcd_hmc_state *s, const lqcd_hmc_params *p, double *H, void *stream)
+{
+    LQCD_REQUIRE(s && H, "hmc_hamiltonian: NULL argument");
+    LQCD_TRY(check_params(p));
+    LQCD_TRY(ensure_sloppy(s, p, (cudaStream_t)stream));
+    return hamiltonian(s, p, H, (cudaStream_t)stream);
+}
+
+lqcd_status lqcd_md_step(lqcd_hmc_state *s, const lqcd_hmc_params *p, void *stream)
+{
+    LQCD_REQUIRE(s, "md_step: NULL state");
+    LQCD_TRY(check_params(p));
+    cudaStream_t st = (cudaStream_t)stream;
+    LQCD_TRY(ensure_sloppy(s, p, st));
+    double dt = p->tau / p->nsteps;
+    if (p->integrator == LQCD_LEAPFROG) {
+        LQCD_TRY(kick(s, p, 0.5 * dt, st));
+        LQCD_TRY(drift(s, p, dt, st));
+        LQCD_TRY(kick(s, p, 0.5 * dt, st));
+    } else {
+        const double lam = OMELYAN_LAMBDA;
+        LQCD_TRY(kick(s, p, lam * dt, st));
+        LQCD_TRY(drift(s, p, 0.5 * dt, st));
+        LQCD_TRY(kick(s, p, (1.0 - 2.0 * lam) * dt, st));
+        LQCD_TRY(drift(s, p, 0.5 * dt, st));
+        LQCD_TRY(kick(s, p, lam * dt, st));
+    }
+    return LQCD_OK;
+}
+
+lqcd_status lqcd_hmc_trajectory(lqcd_hmc_state *s, const lqcd_hmc_params *p, lqcd_traj_info *info, void *stream)
+{
+    LQCD_REQUIRE(s, "hmc_trajectory: NULL state");
+    LQCD_TRY(check_params(p));
+    cudaStream_t st = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    reset_stats(s);
+    LQCD_CUDA(cudaMemcpyAsync(s->Ubak.f->data, s->U->data, s->U->bytes, cudaMemcpyDeviceToDevice, st));
+    double H0 = 0, H1 = 0;
+    lqcd_status rc = refresh(s, p, &H0, st);
+    if (rc == LQCD_OK) rc = integrate(s, p, st);
+    if (rc == LQCD_OK) rc = hamiltonian(s, p, &H1, st);
+    double dH = H1 - H0;
+    double *d = (double *)s->scal.p;
+    metropolis_uniform_kernel<<<1, 1, 0, st>>>(d + 3, s->seed, s->chain, s->traj);
+    LQCD_LAUNCHED();
+    double u = 0;
+    LQCD_TRY(read_scalars(d + 3, &u, 1, st));
+    bool accept = rc == LQCD_OK && std::isfinite(dH) && (!p->metropolis || u < std::exp(-dH));
+    if (!accept) LQCD_CUDA(cudaMemcpyAsync(s->U->data, s->Ubak.f->data, s->U->bytes, cudaMemcpyDeviceToDevice, st));
+    double maxdev = 0;
+    if (p->reunitarize) {
+        LQCD_TRY(reunitarize_dev(s->U, d + 4, s->part, st));
+        LQCD_TRY(read_scalars(d + 4, &maxdev, 1, st));
+    }
+    LQCD_TRY(plaquette_sum(s->U, d + 5, s->part, st));
+    double plaq_sum = 0;
+    LQCD_TRY(read_scalars(d + 5, &plaq_sum, 1, st));
+    if (info) {
+        info->dH = dH;
+        info->H0 = H0;
+        info->H1 = H1;
+        info->plaq = plaq_sum / (6.0 * 2.0 * s->U->Vh);
+        info->u = u;
+        info->max_unitarity_dev = maxdev;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        info->cg_true_rel_res_max = s->cg_res_max;
+        info->accepted = accept ? 1 : 0;
+        info->cg_iters = s->cg_iters;
+        info->n_solves = s->n_solves;
+        info->cg_failures = s->cg_failures;
+        info->traj = s->traj;
+    }
+    s->traj++;
+    if (rc != LQCD_OK) return rc;
+    if (!std::isfinite(dH)) {
+        set_error("hmc: dH is not finite; trajectory rejected");
+        return LQCD_ENUMERIC;
+    }
+    return LQCD_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,442 @@
+"""Thin ctypes binding of liblqcd.so (declared in include/lqcd.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  PyTorch supplies the device allocator (its caching allocator,
+installed as the library's allocator hook) and the CUDA stream.  There is no
+CPU fallback: if the library cannot be built or loaded, every call raises.
+
+Host arrays use the canonical layouts of include/lqcd.h as numpy arrays:
+  gauge    complex128 (V, 4, 3, 3)      momentum float64 (V, 4, 8)
+  half spinor (EVEN/ODD) complex128 (V/2, 4, 3) in checkerboard order
+  full spinor complex128 (V, 4, 3)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+# ---------------------------------------------------------------- constants
+
+OK, EINVAL, ENOMEM, ENOCONV, ENUMERIC, ECUDA, EAGAIN, ETIMEOUT = range(8)
+STATUS_NAMES = {0: "LQCD_OK", 1: "LQCD_EINVAL", 2: "LQCD_ENOMEM", 3: "LQCD_ENOCONV", 4: "LQCD_ENUMERIC",
+                5: "LQCD_ECUDA", 6: "LQCD_EAGAIN", 7: "LQCD_ETIMEOUT"}
+GAUGE, MOMENTUM, SPINOR_EVEN, SPINOR_ODD, SPINOR_FULL = range(5)
+F64, F32, F16N, BF16 = range(4)
+PREC_NAMES = {"f64": F64, "f32": F32, "f16n": F16N, "bf16": BF16}
+LEAPFROG, OMELYAN = 0, 1
+
+
+class LqcdError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+# ---------------------------------------------------------------- structs
+
+class Lattice(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 4), ("t_bc", ctypes.c_int)]
+
+
+class CgParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("sloppy", ctypes.c_int),
+                ("delta", ctypes.c_double), ("max_restarts", ctypes.c_int)]
+
+
+class CgInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("true_rel_res", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+
+class HmcParams(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("kappa", ctypes.c_double), ("tau", ctypes.c_double),
+                ("nsteps", ctypes.c_int), ("integrator", ctypes.c_int), ("n_flavors", ctypes.c_int),
+                ("cg", CgParams), ("reunitarize", ctypes.c_int), ("metropolis", ctypes.c_int)]
+
+
+class TrajInfo(ctypes.Structure):
+    _fields_ = [("dH", ctypes.c_double), ("H0", ctypes.c_double), ("H1", ctypes.c_double),
+                ("plaq", ctypes.c_double), ("u", ctypes.c_double), ("max_unitarity_dev", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("cg_true_rel_res_max", ctypes.c_double),
+                ("accepted", ctypes.c_int), ("cg_iters", ctypes.c_int), ("n_solves", ctypes.c_int),
+                ("cg_failures", ctypes.c_int), ("traj", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# ---------------------------------------------------------------- loading
+
+_vp, _sz, _u32, _i, _d = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_int, ctypes.c_double
+_dp = ctypes.POINTER(ctypes.c_double)
+_pp = ctypes.POINTER(ctypes.c_void_p)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+_SIGS = {
+    "lqcd_last_error": (ctypes.c_char_p, []),
+    "lqcd_version": (ctypes.c_char_p, []),
+    "lqcd_launch_count": (ctypes.c_uint64, []),
+    "lqcd_set_allocator": (_i, [ALLOC_FN, FREE_FN, _vp]),
+    "lqcd_field_alloc": (_i, [ctypes.POINTER(Lattice), _i, _i, _i, _pp]),
+    "lqcd_field_free": (_i, [_vp]),
+    "lqcd_field_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "lqcd_field_data": (_i, [_vp, _pp, _pp]),
+    "lqcd_field_upload": (_i, [_vp, _dp, _vp]),
+    "lqcd_field_download": (_i, [_vp, _dp, _vp]),
+    "lqcd_field_copy": (_i, [_vp, _vp, _vp]),
+    "lqcd_philox_blocks": (_i, [_vp, _sz, _u32, _u32, _u32, _u32, _u32, _u32, _vp]),
+    "lqcd_gauge_start": (_i, [_vp, _u32, _u32, _d, _vp]),
+    "lqcd_momentum_refresh": (_i, [_vp, _u32, _u32, _u32, _vp]),
+    "lqcd_eta_refresh": (_i, [_vp, _u32, _u32, _u32, _vp]),
+    "lqcd_dslash": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "lqcd_mhat": (_i, [_vp, _vp, _vp, _d, _i, _vp]),
+    "lqcd_cg_solve": (_i, [_vp, _vp, _vp, _vp, _d, ctypes.POINTER(CgParams), ctypes.POINTER(CgInfo), _vp]),
+    "lqcd_gauge_force": (_i, [_vp, _vp, _d, _d, _vp]),
+    "lqcd_fermion_force": (_i, [_vp, _vp, _vp, _d, _d, _vp]),
+    "lqcd_link_update": (_i, [_vp, _vp, _d, _vp, _vp]),
+    "lqcd_reunitarize": (_i, [_vp, _dp, _vp]),
+    "lqcd_plaquette": (_i, [_vp, _dp, _vp]),
+    "lqcd_kinetic_energy": (_i, [_vp, _dp, _vp]),
+    "lqcd_spinor_dot": (_i, [_vp, _vp, _dp, _vp]),
+    "lqcd_hmc_state_create": (_i, [_vp, _u32, _u32, _u32, _pp]),
+    "lqcd_hmc_state_destroy": (_i, [_vp]),
+    "lqcd_hmc_state_fields": (_i, [_vp, _pp, _pp, _pp]),
+    "lqcd_hmc_state_traj": (_i, [_vp, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
+    "lqcd_hmc_refresh": (_i, [_vp, ctypes.POINTER(HmcParams), _dp, _vp]),
+    "lqcd_hmc_hamiltonian": (_i, [_vp, ctypes.POINTER(HmcParams), _dp, _vp]),
+    "lqcd_md_step": (_i, [_vp, ctypes.POINTER(HmcParams), _vp]),
+    "lqcd_hmc_trajectory": (_i, [_vp, ctypes.POINTER(HmcParams), ctypes.POINTER(TrajInfo), _vp]),
+}
+
+_lock = threading.Lock()
+_lib = None
+_allocator_installed = False
+_alloc_keep = []
+
+
+def header_functions() -> list[str]:
+    """Names of every function declared in include/lqcd.h."""
+    txt = open(os.path.join(_build.INCLUDE, "lqcd.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lqcd_[a-z0-9_]+)\s*\(", txt)))
+
+
+def lib(build_if_needed: bool = True):
+    """The loaded library (built first if missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_needed:
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"{_build.LIB} is missing: run paper_1212_0785_gb300.build.build()")
+            L = ctypes.CDLL(_build.LIB)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise LqcdError(rc, where, lib().lqcd_last_error().decode())
+    return rc
+
+
+def version() -> str:
+    return lib().lqcd_version().decode()
+
+
+def launch_count() -> int:
+    return int(lib().lqcd_launch_count())
+
+
+# ---------------------------------------------------------------- torch plumbing
+
+def _torch():
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("liblqcd needs a CUDA device; none is visible")
+    return torch
+
+
+def install_torch_allocator():
+    """Point the library's allocator hook at PyTorch's caching allocator."""
+    global _allocator_installed
+    if _allocator_installed:
+        return
+    torch = _torch()
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0) or None)
+        except Exception:  # out of memory: the library reports LQCD_ENOMEM
+            return None
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+    _alloc_keep.extend([a, f])
+    _check(lib().lqcd_set_allocator(a, f, None), "set_allocator")
+    _allocator_installed = True
+
+
+def current_stream() -> int:
+    return _torch().cuda.current_stream().cuda_stream
+
+
+def _s(stream):
+    return ctypes.c_void_p(current_stream() if stream is None else int(stream))
+
+
+# ---------------------------------------------------------------- fields
+
+def lattice(dims, t_bc=-1) -> Lattice:
+    return Lattice((ctypes.c_int * 4)(*[int(d) for d in dims]), int(t_bc))
+
+
+class Field:
+    """A device field owned by the library (lqcd_field*)."""
+
+    def __init__(self, dims, kind, prec=F64, recon=None, t_bc=-1):
+        install_torch_allocator()
+        self.dims = tuple(int(d) for d in dims)
+        self.kind, self.prec, self.t_bc = kind, prec, t_bc
+        if recon is None:
+            recon = (18 if prec == F64 else 12) if kind == GAUGE else 0
+        self.recon = recon
+        h = ctypes.c_void_p()
+        _check(lib().lqcd_field_alloc(ctypes.byref(lattice(dims, t_bc)), kind, prec, recon, ctypes.byref(h)),
+               "field_alloc")
+        self.h = h
+        self._owned = True
+
+    @classmethod
+    def borrowed(cls, handle, dims, kind, prec=F64, t_bc=-1):
+        f = cls.__new__(cls)
+        f.dims, f.kind, f.prec, f.t_bc = tuple(dims), kind, prec, t_bc
+        f.recon = (18 if prec == F64 else 12) if kind == GAUGE else 0
+        f.h = ctypes.c_void_p(handle)
+        f._owned = False
+        return f
+
+    @property
+    def V(self):
+        return int(np.prod(self.dims))
+
+    def host_shape(self):
+        V = self.V
+        return {GAUGE: (V, 4, 3, 3), MOMENTUM: (V, 4, 8), SPINOR_EVEN: (V // 2, 4, 3),
+                SPINOR_ODD: (V // 2, 4, 3), SPINOR_FULL: (V, 4, 3)}[self.kind]
+
+    def host_dtype(self):
+        return np.float64 if self.kind == MOMENTUM else np.complex128
+
+    def upload(self, arr, stream=None):
+        a = np.ascontiguousarray(arr, dtype=self.host_dtype())
+        assert a.shape == self.host_shape(), (a.shape, self.host_shape())
+        buf = a.view(np.float64) if a.dtype == np.complex128 else a
+        _check(lib().lqcd_field_upload(self.h, buf.ctypes.data_as(_dp), _s(stream)), "field_upload")
+        return self
+
+    def download(self, stream=None, out=None):
+        a = out if out is not None else np.empty(self.host_shape(), self.host_dtype())
+        buf = a.view(np.float64) if a.dtype == np.complex128 else a
+        _check(lib().lqcd_field_download(self.h, buf.ctypes.data_as(_dp), _s(stream)), "field_download")
+        return a
+
+    def copy_from(self, src: "Field", stream=None):
+        _check(lib().lqcd_field_copy(self.h, src.h, _s(stream)), "field_copy")
+        return self
+
+    def nbytes(self) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().lqcd_field_bytes(self.h, ctypes.byref(n)), "field_bytes")
+        return n.value
+
+    def data_ptr(self) -> int:
+        p = ctypes.c_void_p()
+        _check(lib().lqcd_field_data(self.h, ctypes.byref(p), None), "field_data")
+        return p.value
+
+    def free(self):
+        if getattr(self, "_owned", False) and self.h:
+            lib().lqcd_field_free(self.h)
+            self.h = None
+            self._owned = False
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def gauge_field(dims, prec=F64, t_bc=-1):
+    return Field(dims, GAUGE, prec, t_bc=t_bc)
+
+
+def spinor_field(dims, parity, prec=F64, t_bc=-1):
+    return Field(dims, SPINOR_EVEN if parity == 0 else SPINOR_ODD, prec, t_bc=t_bc)
+
+
+def momentum_field(dims, t_bc=-1):
+    return Field(dims, MOMENTUM, F64, t_bc=t_bc)
+
+
+# ---------------------------------------------------------------- operations
+
+def philox_blocks(out_ptr: int, n_blocks: int, ctr, key, stream=None):
+    _check(lib().lqcd_philox_blocks(ctypes.c_void_p(out_ptr), n_blocks, *[int(c) for c in ctr],
+                                    int(key[0]), int(key[1]), _s(stream)), "philox_blocks")
+
+
+def gauge_start(U: Field, seed, eps, chain=0, stream=None):
+    _check(lib().lqcd_gauge_start(U.h, seed, chain, eps, _s(stream)), "gauge_start")
+
+
+def momentum_refresh(P: Field, seed, traj, chain=0, stream=None):
+    _check(lib().lqcd_momentum_refresh(P.h, seed, chain, traj, _s(stream)), "momentum_refresh")
+
+
+def eta_refresh(eta: Field, seed, traj, chain=0, stream=None):
+    _check(lib().lqcd_eta_refresh(eta.h, seed, chain, traj, _s(stream)), "eta_refresh")
+
+
+def dslash(out: Field, U: Field, inp: Field, dagger=False, stream=None):
+    _check(lib().lqcd_dslash(out.h, U.h, inp.h, int(dagger), _s(stream)), "dslash")
+
+
+def mhat(out: Field, U: Field, inp: Field, kappa, dagger=False, stream=None):
+    _check(lib().lqcd_mhat(out.h, U.h, inp.h, kappa, int(dagger), _s(stream)), "mhat")
+
+
+def cg_params(tol=1e-10, maxiter=10000, sloppy=F64, delta=0.1, max_restarts=3) -> CgParams:
+    return CgParams(tol, maxiter, sloppy, delta, max_restarts)
+
+
+def cg_solve(x: Field, U: Field, b: Field, kappa, params: CgParams | None = None, U_sloppy: Field | None = None,
+             stream=None, check=True):
+    """returns (status, CgInfo)"""
+    params = params or cg_params()
+    info = CgInfo()
+    rc = lib().lqcd_cg_solve(x.h, U.h, U_sloppy.h if U_sloppy is not None else None, b.h, kappa,
+                             ctypes.byref(params), ctypes.byref(info), _s(stream))
+    if check and rc not in (OK, ENOCONV):
+        _check(rc, "cg_solve")
+    return rc, info
+
+
+def gauge_force(P: Field, U: Field, beta, coeff, stream=None):
+    _check(lib().lqcd_gauge_force(P.h, U.h, beta, coeff, _s(stream)), "gauge_force")
+
+
+def fermion_force(P: Field, U: Field, X: Field, kappa, coeff, stream=None):
+    _check(lib().lqcd_fermion_force(P.h, U.h, X.h, kappa, coeff, _s(stream)), "fermion_force")
+
+
+def link_update(U: Field, P: Field, c, U_sloppy: Field | None = None, stream=None):
+    _check(lib().lqcd_link_update(U.h, P.h, c, U_sloppy.h if U_sloppy is not None else None, _s(stream)),
+           "link_update")
+
+
+def reunitarize(U: Field, stream=None) -> float:
+    d = ctypes.c_double()
+    _check(lib().lqcd_reunitarize(U.h, ctypes.byref(d), _s(stream)), "reunitarize")
+    return d.value
+
+
+def plaquette(U: Field, stream=None) -> float:
+    d = ctypes.c_double()
+    _check(lib().lqcd_plaquette(U.h, ctypes.byref(d), _s(stream)), "plaquette")
+    return d.value
+
+
+def kinetic_energy(P: Field, stream=None) -> float:
+    d = ctypes.c_double()
+    _check(lib().lqcd_kinetic_energy(P.h, ctypes.byref(d), _s(stream)), "kinetic_energy")
+    return d.value
+
+
+def spinor_dot(a: Field, b: Field, stream=None) -> float:
+    d = ctypes.c_double()
+    _check(lib().lqcd_spinor_dot(a.h, b.h, ctypes.byref(d), _s(stream)), "spinor_dot")
+    return d.value
+
+
+# ---------------------------------------------------------------- HMC
+
+def hmc_params(beta, kappa, tau=1.0, nsteps=10, integrator=LEAPFROG, n_flavors=2, cg=None, reunitarize=True,
+               metropolis=True) -> HmcParams:
+    return HmcParams(beta, kappa, tau, nsteps, integrator, n_flavors, cg or cg_params(), int(reunitarize),
+                     int(metropolis))
+
+
+class HmcState:
+    """One Markov chain on the device; borrows the FP64 gauge field U."""
+
+    def __init__(self, U: Field, seed, chain=0, traj0=0):
+        h = ctypes.c_void_p()
+        _check(lib().lqcd_hmc_state_create(U.h, seed, chain, traj0, ctypes.byref(h)), "hmc_state_create")
+        self.h, self.U = h, U
+
+    def fields(self):
+        u, p, phi = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().lqcd_hmc_state_fields(self.h, ctypes.byref(u), ctypes.byref(p), ctypes.byref(phi)),
+               "hmc_state_fields")
+        d, t = self.U.dims, self.U.t_bc
+        return (self.U, Field.borrowed(p.value, d, MOMENTUM, t_bc=t),
+                Field.borrowed(phi.value, d, SPINOR_EVEN, t_bc=t))
+
+    @property
+    def traj(self) -> int:
+        v = ctypes.c_uint32()
+        _check(lib().lqcd_hmc_state_traj(self.h, ctypes.byref(v), None), "hmc_state_traj")
+        return v.value
+
+    @traj.setter
+    def traj(self, value):
+        v = ctypes.c_uint32(value)
+        _check(lib().lqcd_hmc_state_traj(self.h, None, ctypes.byref(v)), "hmc_state_traj")
+
+    def refresh(self, params: HmcParams, stream=None) -> float:
+        H = ctypes.c_double()
+        _check(lib().lqcd_hmc_refresh(self.h, ctypes.byref(params), ctypes.byref(H), _s(stream)), "hmc_refresh")
+        return H.value
+
+    def hamiltonian(self, params: HmcParams, stream=None) -> float:
+        H = ctypes.c_double()
+        _check(lib().lqcd_hmc_hamiltonian(self.h, ctypes.byref(params), ctypes.byref(H), _s(stream)),
+               "hmc_hamiltonian")
+        return H.value
+
+    def md_step(self, params: HmcParams, stream=None):
+        _check(lib().lqcd_md_step(self.h, ctypes.byref(params), _s(stream)), "md_step")
+
+    def trajectory(self, params: HmcParams, stream=None) -> dict:
+        info = TrajInfo()
+        _check(lib().lqcd_hmc_trajectory(self.h, ctypes.byref(params), ctypes.byref(info), _s(stream)),
+               "hmc_trajectory")
+        return info.as_dict()
+
+    def close(self):
+        if self.h:
+            lib().lqcd_hmc_state_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

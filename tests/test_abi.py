@@ -1,0 +1,72 @@
+"""C-ABI checks that need no GPU: the library builds for sm_103a, loads, exports
+every function include/lqcd.h declares, and rejects bad arguments on the host
+before touching the device."""
+import ctypes
+
+import pytest
+
+from paper_1212_0785_gb300 import lqcd
+
+
+@pytest.fixture(scope="module")
+def L():
+    return lqcd.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    names = lqcd.header_functions()
+    assert len(names) >= 30
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # the binding marshals every declared function
+    assert set(names) <= set(lqcd._SIGS), set(names) - set(lqcd._SIGS)
+
+
+def test_version_and_error_string(L):
+    assert "sm_103a" in lqcd.version()
+    assert isinstance(L.lqcd_last_error(), bytes)
+    assert lqcd.launch_count() >= 0
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 3), (0, 4, 4, 4), (4, -2, 4, 4), (5, 4, 4, 4)])
+def test_field_alloc_rejects_bad_lattice(L, dims):
+    h = ctypes.c_void_p()
+    rc = L.lqcd_field_alloc(ctypes.byref(lqcd.lattice(dims)), lqcd.GAUGE, lqcd.F64, 18, ctypes.byref(h))
+    assert rc == lqcd.EINVAL
+    assert b"even" in L.lqcd_last_error() or b"positive" in L.lqcd_last_error()
+    assert not h.value
+
+
+@pytest.mark.parametrize("kind,prec,recon", [(lqcd.GAUGE, lqcd.F64, 12), (lqcd.GAUGE, lqcd.F16N, 18),
+                                             (lqcd.MOMENTUM, lqcd.F32, 0), (lqcd.SPINOR_FULL, lqcd.BF16, 0),
+                                             (lqcd.SPINOR_EVEN, lqcd.F64, 12), (7, lqcd.F64, 0)])
+def test_field_alloc_rejects_bad_combination(L, kind, prec, recon):
+    h = ctypes.c_void_p()
+    rc = L.lqcd_field_alloc(ctypes.byref(lqcd.lattice((4, 4, 4, 4))), kind, prec, recon, ctypes.byref(h))
+    assert rc == lqcd.EINVAL and not h.value
+
+
+def test_bad_boundary_and_huge_volume(L):
+    h = ctypes.c_void_p()
+    rc = L.lqcd_field_alloc(ctypes.byref(lqcd.lattice((4, 4, 4, 4), t_bc=0)), lqcd.GAUGE, lqcd.F64, 18,
+                            ctypes.byref(h))
+    assert rc == lqcd.EINVAL
+    rc = L.lqcd_field_alloc(ctypes.byref(lqcd.lattice((2048, 2048, 2048, 2))), lqcd.GAUGE, lqcd.F64, 18,
+                            ctypes.byref(h))
+    assert rc == lqcd.EINVAL and b"2^31" in L.lqcd_last_error()
+
+
+def test_null_arguments_are_rejected(L):
+    p = lqcd.cg_params()
+    info = lqcd.CgInfo()
+    assert L.lqcd_cg_solve(None, None, None, None, 0.1, ctypes.byref(p), ctypes.byref(info), None) == lqcd.EINVAL
+    assert L.lqcd_dslash(None, None, None, 0, None) == lqcd.EINVAL
+    assert L.lqcd_plaquette(None, None, None) == lqcd.EINVAL
+    assert L.lqcd_hmc_trajectory(None, None, None, None) == lqcd.EINVAL
+    assert L.lqcd_field_free(None) == lqcd.OK
+
+
+def test_allocator_hook_validation(L):
+    a = lqcd.ALLOC_FN(lambda n, s, c: None)
+    assert L.lqcd_set_allocator(a, lqcd.FREE_FN(), None) == lqcd.EINVAL
+    assert L.lqcd_set_allocator(lqcd.ALLOC_FN(), lqcd.FREE_FN(), None) == lqcd.OK

@@ -1,0 +1,125 @@
+"""GPU parity: Philox streams, start configuration, refreshes, host transfer
+and precision codecs, plaquette, kinetic energy, link update, reunitarize,
+against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as orc
+from paper_1212_0785_gb300 import inputs, lqcd
+from tests.gpu_util import PARITY_DIMS, half, rel_err, upload_gauge
+
+pytestmark = pytest.mark.gpu
+
+
+def test_philox_blocks_bit_exact():
+    n = 5000
+    out = torch.zeros(4 * n, dtype=torch.int32, device="cuda")
+    ctr, key = (7, 3, 1, 9), (12345, 6)
+    lqcd.philox_blocks(out.data_ptr(), n, ctr, key)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint32).reshape(n, 4)
+    for i in list(range(64)) + list(range(n - 64, n)) + [1000, 2500]:
+        assert np.array_equal(got[i], orc.philox4x32_10([ctr[0] + i, ctr[1], ctr[2], ctr[3]], key)), i
+    # counter words wrap at 2^32 like the oracle's
+    lqcd.philox_blocks(out.data_ptr(), 4, (0xFFFFFFFE, 0, 2, 0), (1, 2))
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint32).reshape(n, 4)
+    for i in range(4):
+        assert np.array_equal(got[i], orc.philox4x32_10([(0xFFFFFFFE + i) & 0xFFFFFFFF, 0, 2, 0], (1, 2)))
+
+
+@pytest.mark.parametrize("dims", PARITY_DIMS[:3])
+def test_gauge_start_matches_oracle(dims):
+    U = lqcd.gauge_field(dims)
+    lqcd.gauge_start(U, seed=2, eps=0.2, chain=1)
+    ref = orc.gauge_start(dims, seed=2, eps=0.2, chain=1)
+    assert rel_err(U.download(), ref) < 1e-13
+
+
+@pytest.mark.parametrize("dims", PARITY_DIMS[:3])
+def test_refresh_matches_oracle(dims):
+    P = lqcd.momentum_field(dims)
+    lqcd.momentum_refresh(P, seed=3, traj=5, chain=2)
+    assert np.max(np.abs(P.download() - orc.momentum_refresh(dims, 3, 5, chain=2))) < 1e-13
+    eta = lqcd.spinor_field(dims, 0)
+    lqcd.eta_refresh(eta, seed=3, traj=5, chain=2)
+    ref = half(orc.eta_refresh(dims, 3, 5, chain=2), dims, 0)
+    assert np.max(np.abs(eta.download() - ref)) < 1e-13
+
+
+def test_transfer_roundtrip_and_codecs():
+    dims = (6, 4, 2, 10)
+    Uh = inputs.random_gauge(dims, 1)
+    U = lqcd.gauge_field(dims).upload(Uh)
+    assert np.array_equal(U.download(), Uh)
+    for prec, tol in ((lqcd.F32, 1e-6), (lqcd.F16N, 2e-3), (lqcd.BF16, 1.6e-2)):
+        Us = lqcd.gauge_field(dims, prec).copy_from(U)
+        assert rel_err(Us.download(), Uh) < tol, prec  # row 2 reconstructed from rows 0, 1
+    P = inputs.random_momentum(dims, 2)
+    assert np.array_equal(lqcd.momentum_field(dims).upload(P).download(), P)
+    s = inputs.random_spinor(dims, 3)
+    for par in (0, 1):
+        h = half(s, dims, par)
+        f = lqcd.spinor_field(dims, par).upload(h)
+        assert np.array_equal(f.download(), h)
+        for prec, tol in ((lqcd.F32, 1e-6), (lqcd.F16N, 1e-3), (lqcd.BF16, 8e-3)):
+            g = lqcd.spinor_field(dims, par, prec).copy_from(f)
+            assert rel_err(g.download(), h) < tol
+    full = lqcd.Field(dims, lqcd.SPINOR_FULL).upload(s)
+    assert np.array_equal(full.download(), s)
+
+
+@pytest.mark.parametrize("dims", PARITY_DIMS)
+def test_plaquette_and_kinetic(dims):
+    Uh = orc.gauge_start(dims, seed=4, eps=0.4)
+    U = lqcd.gauge_field(dims).upload(Uh)
+    assert abs(lqcd.plaquette(U) - orc.plaquette(dims, Uh)) < 1e-14
+    Ph = inputs.random_momentum(dims, 5)
+    P = lqcd.momentum_field(dims).upload(Ph)
+    assert abs(lqcd.kinetic_energy(P) - orc.kinetic(dims, Ph)) < 1e-12 * orc.kinetic(dims, Ph)
+
+
+@pytest.mark.parametrize("dims", PARITY_DIMS[:3])
+def test_link_update_matches_oracle(dims):
+    Uh = orc.gauge_start(dims, seed=6, eps=0.3)
+    Ph = orc.momentum_refresh(dims, 6, 0)
+    U = lqcd.gauge_field(dims).upload(Uh)
+    P = lqcd.momentum_field(dims).upload(Ph)
+    Us = lqcd.gauge_field(dims, lqcd.F16N)
+    lqcd.link_update(U, P, 0.07, U_sloppy=Us)
+    ref = orc.link_update(dims, Uh, Ph, 0.07)
+    assert rel_err(U.download(), ref) < 1e-13
+    assert rel_err(Us.download(), ref) < 2e-3
+    # large steps take the Cayley-Hamilton exp through all its branches
+    for c in (1.5, -2.0, 1e-9):
+        U = lqcd.gauge_field(dims).upload(Uh)
+        lqcd.link_update(U, P, c)
+        assert rel_err(U.download(), orc.link_update(dims, Uh, Ph, c)) < 1e-12, c
+
+
+def test_link_update_degenerate_momenta():
+    """momenta with degenerate eigenvalues (single diagonal generators) and zero"""
+    dims = (4, 4, 4, 4)
+    V = 256
+    Uh = orc.gauge_start(dims, seed=7, eps=0.3)
+    Ph = np.zeros((V, 4, 8))
+    Ph[:, 0, 7] = 1.3   # lambda_8: eigenvalues (a, a, -2a)
+    Ph[:, 1, 2] = -0.8  # lambda_3: (a, -a, 0)
+    Ph[:, 2, 0] = 2.0   # lambda_1
+    U = lqcd.gauge_field(dims).upload(Uh)
+    P = lqcd.momentum_field(dims).upload(Ph)
+    lqcd.link_update(U, P, 0.5)
+    assert rel_err(U.download(), orc.link_update(dims, Uh, Ph, 0.5)) < 1e-13
+
+
+def test_reunitarize_matches_oracle():
+    dims = (6, 4, 2, 10)
+    Uh = orc.gauge_start(dims, seed=8, eps=0.3)
+    rng = np.random.default_rng(0)
+    noisy = Uh + 1e-4 * (rng.standard_normal(Uh.shape) + 1j * rng.standard_normal(Uh.shape))
+    U = lqcd.gauge_field(dims).upload(noisy)
+    dev = lqcd.reunitarize(U)
+    ref, ref_dev = orc.reunitarize(dims, noisy)
+    assert abs(dev - ref_dev) < 1e-12
+    assert rel_err(U.download(), ref) < 1e-14

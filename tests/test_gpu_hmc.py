@@ -1,0 +1,89 @@
+"""GPU parity of the whole trajectory against the oracle: dH to 1e-8, identical
+accept decisions, plaquette; and device-side reversibility and dH ~ dt^2."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1212_0785_gb300 import lqcd
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (4, 4, 4, 4)  # the 4^4 workload: seed 1, eps 0.3, beta 5.6, kappa 0.156
+
+
+def _run_gpu(Uh, params, seed, trajs):
+    U = lqcd.gauge_field(DIMS).upload(Uh)
+    st = lqcd.HmcState(U, seed=seed)
+    infos = [st.trajectory(params) for _ in range(trajs)]
+    out = U.download()
+    st.close()
+    return out, infos
+
+
+@pytest.mark.parametrize("integrator,tau,nsteps", [(lqcd.LEAPFROG, 1.0, 10), (lqcd.OMELYAN, 0.2, 10),
+                                                   (lqcd.LEAPFROG, 0.3, 6)])
+def test_trajectory_matches_oracle(integrator, tau, nsteps):
+    Uh = orc.gauge_start(DIMS, seed=1, eps=0.3)
+    params = lqcd.hmc_params(5.6, 0.156, tau, nsteps, integrator, cg=lqcd.cg_params(tol=1e-10))
+    Ug, infos = _run_gpu(Uh, params, 1, 2)
+    Uo = Uh
+    for traj, g in enumerate(infos):
+        Uo, o = orc.hmc_trajectory(DIMS, Uo, 5.6, 0.156, tau, nsteps, integrator=integrator, seed=1, traj=traj,
+                                   cg_tol=1e-10)
+        assert abs(g["dH"] - o["dH"]) < 1e-8, (g["dH"], o["dH"])
+        assert abs(g["H0"] - o["H0"]) < 1e-8 * abs(o["H0"])
+        assert g["u"] == o["u"]
+        marginal = abs(o["u"] - np.exp(-o["dH"])) < 1e-8
+        assert marginal or g["accepted"] == int(o["accepted"])
+        assert g["n_solves"] == o["n_solves"] and g["cg_failures"] == 0
+        assert abs(g["cg_iters"] - o["cg_iters"]) <= o["n_solves"]
+        assert abs(g["plaq"] - o["plaq"]) < 1e-10
+    assert np.max(np.abs(Ug - Uo)) < 1e-9
+
+
+def test_pure_gauge_trajectory_matches_oracle():
+    Uh = orc.gauge_start(DIMS, seed=1, eps=0.3)
+    params = lqcd.hmc_params(5.6, 0.0, 0.5, 8, lqcd.OMELYAN, n_flavors=0)
+    Ug, (g,) = _run_gpu(Uh, params, 4, 1)
+    Uo, o = orc.hmc_trajectory(DIMS, Uh, 5.6, 0.0, 0.5, 8, integrator=orc.OMELYAN, n_flavors=0, seed=4, traj=0)
+    assert abs(g["dH"] - o["dH"]) < 1e-9 and g["accepted"] == int(o["accepted"])
+    assert np.max(np.abs(Ug - Uo)) < 1e-11
+
+
+def test_mixed_trajectory_close_to_fp64():
+    Uh = orc.gauge_start(DIMS, seed=1, eps=0.3)
+    base = dict(beta=5.6, kappa=0.156, tau=0.2, nsteps=10, integrator=lqcd.OMELYAN)
+    _, (g64,) = _run_gpu(Uh, lqcd.hmc_params(**base, cg=lqcd.cg_params(tol=1e-10)), 1, 1)
+    for sl in (lqcd.F32, lqcd.F16N, lqcd.BF16):
+        _, (gm,) = _run_gpu(Uh, lqcd.hmc_params(**base, cg=lqcd.cg_params(tol=1e-10, sloppy=sl)), 1, 1)
+        assert abs(gm["dH"] - g64["dH"]) < 1e-6, (sl, gm["dH"], g64["dH"])
+        assert gm["cg_true_rel_res_max"] <= 1e-10
+
+
+def test_reversibility_on_device():
+    Uh = orc.gauge_start(DIMS, seed=1, eps=0.3)
+    U = lqcd.gauge_field(DIMS).upload(Uh)
+    st = lqcd.HmcState(U, seed=1)
+    params = lqcd.hmc_params(5.6, 0.156, 0.3, 3, lqcd.OMELYAN, cg=lqcd.cg_params(tol=1e-13))
+    st.refresh(params)
+    _, P, _ = st.fields()
+    P0 = P.download()
+    for _ in range(3):
+        st.md_step(params)
+    assert np.abs(U.download() - Uh).max() > 1e-2
+    P.upload(-P.download())
+    for _ in range(3):
+        st.md_step(params)
+    assert np.abs(U.download() - Uh).max() < 1e-10
+    assert np.abs(P.download() + P0).max() < 1e-10
+    st.close()
+
+
+def test_energy_conservation_dt_squared():
+    Uh = orc.gauge_start(DIMS, seed=1, eps=0.3)
+    dH = []
+    for n in (5, 10):
+        params = lqcd.hmc_params(5.6, 0.156, 0.25, n, lqcd.LEAPFROG, cg=lqcd.cg_params(tol=1e-12), metropolis=False)
+        _, (g,) = _run_gpu(Uh, params, 1, 1)
+        dH.append(g["dH"])
+    assert 3.5 < dH[0] / dH[1] < 4.5

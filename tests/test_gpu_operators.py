@@ -1,0 +1,138 @@
+"""GPU parity: even-odd dslash (every storage precision), Mhat, CG (FP64 and
+reliable-update mixed), gauge and fermion forces, against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1212_0785_gb300 import inputs, lqcd
+from tests.gpu_util import PARITY_DIMS, full_from_half, half, rel_err, upload_gauge, upload_half
+
+pytestmark = pytest.mark.gpu
+
+# relative error bounds of the low-precision dslash against FP64 (storage
+# rounding of links and spinors, FP32 arithmetic): see the derivation in the
+# design notes -- FP32 ~ 2^-24 x O(10), FP16+norm ~ 2^-11, BF16 ~ 2^-8
+LOWPREC_TOL = {lqcd.F32: 2e-6, lqcd.F16N: 3e-3, lqcd.BF16: 2.5e-2}
+
+
+@pytest.mark.parametrize("dims", PARITY_DIMS)
+@pytest.mark.parametrize("in_par", [0, 1])
+@pytest.mark.parametrize("dagger", [False, True])
+@pytest.mark.parametrize("t_bc", [-1, 1])
+def test_dslash_fp64_matches_oracle(dims, in_par, dagger, t_bc):
+    Uh = inputs.random_gauge(dims, 11)
+    s = inputs.random_spinor(dims, 12, parity=in_par)
+    ref = orc.dslash(dims, Uh, s, dagger=dagger, out_parity=1 - in_par, t_bc=t_bc)
+    U = lqcd.gauge_field(dims, t_bc=t_bc).upload(Uh)
+    inp = lqcd.spinor_field(dims, in_par, t_bc=t_bc).upload(half(s, dims, in_par))
+    out = lqcd.spinor_field(dims, 1 - in_par, t_bc=t_bc)
+    lqcd.dslash(out, U, inp, dagger)
+    assert rel_err(out.download(), half(ref, dims, 1 - in_par)) < 1e-13
+
+
+@pytest.mark.parametrize("prec", [lqcd.F32, lqcd.F16N, lqcd.BF16])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_dslash_low_precision(prec, dagger):
+    dims = (8, 6, 6, 12)
+    Uh = orc.gauge_start(dims, seed=3, eps=0.5)
+    s = inputs.random_spinor(dims, 13, parity=0)
+    ref = half(orc.dslash(dims, Uh, s, dagger=dagger, out_parity=1), dims, 1)
+    U, Us = upload_gauge(Uh, dims, prec)
+    inp = upload_half(s, dims, 0, prec)
+    out = lqcd.spinor_field(dims, 1, prec)
+    lqcd.dslash(out, Us, inp, dagger)
+    assert rel_err(out.download(), ref) < LOWPREC_TOL[prec]
+
+
+@pytest.mark.parametrize("dagger", [False, True])
+def test_mhat_matches_oracle(dagger):
+    dims = (6, 6, 10, 12)
+    kappa = 0.1575
+    Uh = orc.gauge_start(dims, seed=2, eps=0.2)
+    s = inputs.random_spinor(dims, 14, parity=0)
+    ref = half(orc.mhat(dims, Uh, kappa, s, dagger=dagger), dims, 0)
+    U = lqcd.gauge_field(dims).upload(Uh)
+    inp = upload_half(s, dims, 0)
+    out = lqcd.spinor_field(dims, 0)
+    lqcd.mhat(out, U, inp, kappa, dagger)
+    assert rel_err(out.download(), ref) < 1e-13
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 6, 10, 12)])
+def test_cg_fp64_matches_oracle(dims):
+    kappa = 0.156
+    Uh = orc.gauge_start(dims, seed=1, eps=0.3)
+    b = inputs.random_spinor(dims, 15, parity=0)
+    xr, conv, it_r, rel_r = orc.cg(dims, Uh, kappa, b, tol=1e-12)
+    assert conv
+    U = lqcd.gauge_field(dims).upload(Uh)
+    bf = upload_half(b, dims, 0)
+    x = lqcd.spinor_field(dims, 0)
+    rc, info = lqcd.cg_solve(x, U, bf, kappa, lqcd.cg_params(tol=1e-12))
+    assert rc == lqcd.OK and info.true_rel_res <= 1e-12
+    assert abs(info.iters - it_r) <= 2, (info.iters, it_r)
+    assert rel_err(x.download(), half(xr, dims, 0)) < 1e-9
+    # independent residual check with the oracle's operator
+    xf = full_from_half(x.download(), dims, 0)
+    r = b - orc.mdagm(dims, Uh, kappa, xf)
+    assert np.linalg.norm(r) <= 1.01e-12 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("sloppy", [lqcd.F32, lqcd.F16N, lqcd.BF16])
+def test_cg_mixed_reaches_fp64_tolerance(sloppy):
+    dims = (6, 6, 10, 12)
+    kappa = 0.156
+    Uh = orc.gauge_start(dims, seed=1, eps=0.3)
+    b = inputs.random_spinor(dims, 16, parity=0)
+    xr, conv, _, _ = orc.cg(dims, Uh, kappa, b, tol=1e-12)
+    U, Us = upload_gauge(Uh, dims, sloppy)
+    bf = upload_half(b, dims, 0)
+    x = lqcd.spinor_field(dims, 0)
+    rc, info = lqcd.cg_solve(x, U, bf, kappa, lqcd.cg_params(tol=1e-10, sloppy=sloppy, delta=0.1), U_sloppy=Us)
+    assert rc == lqcd.OK and info.true_rel_res <= 1e-10 and info.restarts >= 1
+    xf = full_from_half(x.download(), dims, 0)
+    r = b - orc.mdagm(dims, Uh, kappa, xf)
+    assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(b)
+    assert rel_err(x.download(), half(xr, dims, 0)) < 1e-8
+
+
+def test_cg_edge_cases():
+    dims = (4, 4, 4, 4)
+    Uh = orc.gauge_start(dims, seed=1, eps=0.3)
+    U = lqcd.gauge_field(dims).upload(Uh)
+    x = lqcd.spinor_field(dims, 0)
+    zero = lqcd.spinor_field(dims, 0).upload(np.zeros((128, 4, 3), complex))
+    rc, info = lqcd.cg_solve(x, U, zero, 0.156)
+    assert rc == lqcd.OK and info.iters == 0 and np.all(x.download() == 0)
+    b = upload_half(inputs.random_spinor(dims, 17, parity=0), dims, 0)
+    rc, info = lqcd.cg_solve(x, U, b, 0.156, lqcd.cg_params(tol=1e-12, maxiter=3), check=False)
+    assert rc == lqcd.ENOCONV and info.iters == 3 and info.true_rel_res > 1e-12
+    with pytest.raises(lqcd.LqcdError):
+        lqcd.cg_solve(x, U, x, 0.156)
+
+
+@pytest.mark.parametrize("dims", PARITY_DIMS[:3])
+def test_gauge_force_matches_oracle(dims):
+    beta, coeff = 5.6, 0.037
+    Uh = orc.gauge_start(dims, seed=5, eps=0.4)
+    Ph = inputs.random_momentum(dims, 18)
+    U = lqcd.gauge_field(dims).upload(Uh)
+    P = lqcd.momentum_field(dims).upload(Ph)
+    lqcd.gauge_force(P, U, beta, coeff)
+    F = orc.gauge_force(dims, Uh, beta)
+    assert np.max(np.abs(P.download() - (Ph - coeff * F))) < 1e-13 * max(1, np.abs(F).max())
+
+
+@pytest.mark.parametrize("dims", PARITY_DIMS[:3])
+@pytest.mark.parametrize("t_bc", [-1, 1])
+def test_fermion_force_matches_oracle(dims, t_bc):
+    kappa, coeff = 0.156, 0.05
+    Uh = orc.gauge_start(dims, seed=6, eps=0.4)
+    X = inputs.random_spinor(dims, 19, parity=0)
+    Ph = inputs.random_momentum(dims, 20)
+    U = lqcd.gauge_field(dims, t_bc=t_bc).upload(Uh)
+    P = lqcd.momentum_field(dims, t_bc=t_bc).upload(Ph)
+    Xf = lqcd.spinor_field(dims, 0, t_bc=t_bc).upload(half(X, dims, 0))
+    lqcd.fermion_force(P, U, Xf, kappa, coeff)
+    F = orc.fermion_force(dims, Uh, kappa, X, t_bc=t_bc)
+    assert np.max(np.abs(P.download() - (Ph - coeff * F))) < 1e-12 * max(1, np.abs(F).max())
