@@ -1,0 +1,442 @@
+#!/usr/bin/env python3
+"""Benchmark: two-flavour Wilson HMC trajectories per second on a 32^3x64
+lattice (beta 5.8, kappa 0.1570, synthetic start exp(i 0.15 H) from Philox
+seed 3, Omelyan 2MN with 16 steps, tau 1, CG true |r|/|b| <= 1e-10), mixed
+precision (FP16+norm spinors and 12-real FP16 links in the solver, FP32
+arithmetic, FP64 master fields, residuals, reductions and dH), with the plain
+FP64 GPU path timed beside it.
+
+One step = one full trajectory on the device.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (a bounded sample of the same
+workload, scaled to trajectories/s).  For N > 1 (torchrun) every rank runs its
+own independent chain (chain id = rank): the method has no exchange between
+chains, so there is no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+if HERE not in sys.path:
+    sys.path.insert(0, HERE)
+
+WORKLOAD = {
+    "workload": "nf2_wilson_hmc_32x32x32x64",
+    "dims": [32, 32, 32, 64],
+    "beta": 5.8,
+    "kappa": 0.1570,
+    "start": "exp(i*0.15*H), H Gell-Mann Gaussians from Philox seed 3",
+    "integrator": "omelyan_2mn",
+    "nsteps": 16,
+    "tau": 1.0,
+    "cg_tol": 1e-10,
+}
+SEED, EPS = 3, 0.15
+SLOPPY_BYTES = {"f64": 1536, "f32": 576, "f16n": 296, "bf16": 288}  # algorithmic bytes / half-dslash site
+ORACLE_SAMPLE_DIMS = (12, 12, 12, 24)
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world, use_cuda):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group("nccl" if use_cuda else "gloo")
+    return dist
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        reasons = sorted({name for r in rows for name, v in zip(self.REASONS, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(rows), "reasons": reasons}
+
+
+# ---------------------------------------------------------------- peaks, profiles
+
+def measured_peaks() -> dict:
+    p = os.path.join(HERE, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": d.get("hbm_gbs"), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def kernel_source_hash() -> str:
+    """hash of the hopping-term sources: a stored ncu traffic figure is only
+    valid for the kernel it was taken on"""
+    h = hashlib.sha256()
+    base = os.path.join(HERE, "paper_1212_0785_gb300", "csrc")
+    for name in ("dslash.cu", "spin.cuh", "lqcd_internal.cuh", "dslash.cuh"):
+        with open(os.path.join(base, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, or None if absent or stale"""
+    p = os.path.join(HERE, "profiles", f"traffic_{kernel}_32x32x32x64.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    with open(p) as fh:
+        for line in fh:
+            if "=" in line and not line.startswith("#"):
+                k, v = line.strip().split("=", 1)
+                kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- oracle baseline
+
+def oracle_sample(dims=ORACLE_SAMPLE_DIMS, wl=WORKLOAD):
+    """Time the FP64 CPU oracle on the operations of one MD force evaluation of
+    the workload at a reduced volume with the same recipe, and derive the time
+    of one full trajectory at the workload's volume:
+      t_traj = (2n+1) (t_solve + t_gauge_force + t_fermion_force) + t_solve
+               + 2n t_link_update,   scaled by V_workload / V_sample.
+    The CG iteration count of the sample solve is that of the oracle itself."""
+    from oracle import oracle as orc
+
+    beta, kappa, n = wl["beta"], wl["kappa"], wl["nsteps"]
+    U = orc.gauge_start(dims, SEED, EPS)
+    eta = orc.eta_refresh(dims, SEED, 0)
+    phi = orc.mhat(dims, U, kappa, eta, dagger=True)
+    P = orc.momentum_refresh(dims, SEED, 0)
+    t0 = time.perf_counter()
+    X, conv, iters, _ = orc.cg(dims, U, kappa, phi, tol=wl["cg_tol"])
+    t1 = time.perf_counter()
+    orc.gauge_force(dims, U, beta)
+    t2 = time.perf_counter()
+    orc.fermion_force(dims, U, kappa, X)
+    t3 = time.perf_counter()
+    orc.link_update(dims, U, P, 0.5 * wl["tau"] / n)
+    t4 = time.perf_counter()
+    t_solve, t_gf, t_ff, t_lu = t1 - t0, t2 - t1, t3 - t2, t4 - t3
+    scale = float(np.prod(wl["dims"])) / float(np.prod(dims))
+    t_traj = ((2 * n + 1) * (t_solve + t_gf + t_ff) + t_solve + 2 * n * t_lu) * scale
+    return {"t_traj_derived_s": t_traj, "sample_cpu_s": t4 - t0, "cg_iters": iters,
+            "parts_s": {"cg_solve": t_solve, "gauge_force": t_gf, "fermion_force": t_ff, "link_update": t_lu},
+            "scale": scale}
+
+
+def cpu_baseline_block(sample) -> dict:
+    d = "x".join(str(v) for v in ORACLE_SAMPLE_DIMS)
+    return {"value": 1.0 / sample["t_traj_derived_s"], "unit": "trajectories/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 oracle, single thread: one CG solve to 1e-10 ({sample['cg_iters']} iterations), "
+                       f"gauge force, fermion force and link update at {d} with the 32^3x64 recipe "
+                       f"({sample['sample_cpu_s']:.1f} s), derived to one 33-force-evaluation trajectory "
+                       f"and scaled by volume x{sample['scale']:.1f}"),
+            "parts_s": sample["parts_s"]}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    samples = []
+    for k in range(args.warmup + args.steps):
+        s = oracle_sample()
+        if k >= args.warmup:
+            samples.append(s)
+    t = float(np.mean([s["t_traj_derived_s"] for s in samples]))
+    value = 1.0 / t
+    cb = cpu_baseline_block(samples[-1])
+    cb["value"] = value
+    line = {"metric": "trajectories/s", "value": value, "unit": "trajectories/s", "impl": "reference",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_block(args, "f64"), "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "trajectories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def config_block(args, sloppy):
+    c = dict(WORKLOAD)
+    c["dims"] = list(args.dims)
+    c["solver"] = ("fp64 CG" if sloppy == "f64" else
+                   f"reliable-update mixed CG: {sloppy} spinors + 12-real {sloppy} links, fp32 math, "
+                   f"fp64 residual/dots, delta {args.delta}")
+    c["forces"] = f"{getattr(args, 'force_prec', 'f64')} arithmetic"
+    c["parallelism"] = f"replicas{args.gpus}" if args.gpus > 1 else "single_gpu"
+    c["l2"] = "inputs larger than L2 (FP64 links 1.21 GB, spinors 0.2 GB)"
+    return c
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+
+    from paper_1212_0785_gb300 import lqcd
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, True)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    dims = tuple(args.dims)
+    V = int(np.prod(dims))
+    sloppy = lqcd.PREC_NAMES[args.sloppy]
+    wl = WORKLOAD
+    cg = lqcd.cg_params(tol=wl["cg_tol"], maxiter=20000, sloppy=sloppy, delta=args.delta)
+    force_prec = lqcd.PREC_NAMES[args.force_prec]
+    params = lqcd.hmc_params(wl["beta"], wl["kappa"], wl["tau"], wl["nsteps"], lqcd.OMELYAN, n_flavors=2, cg=cg,
+                             force_prec=force_prec)
+
+    U = lqcd.gauge_field(dims)
+    lqcd.gauge_start(U, SEED, EPS, chain=rank)
+    state = lqcd.HmcState(U, seed=SEED, chain=rank)
+    for _ in range(args.warmup):
+        state.trajectory(params)
+    torch.cuda.synchronize()
+    barrier(dist, local)
+
+    gpu_index = int((os.environ.get("CUDA_VISIBLE_DEVICES") or str(local)).split(",")[local]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").replace(",", "").isdigit() else local
+    clocks = ClockSampler(gpu_index)
+    lqcd.kernel_timers(True)
+    launches0 = lqcd.launch_count()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    infos = [state.trajectory(params) for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist, local)
+    clk = clocks.stop()
+    launches = lqcd.launch_count() - launches0
+    t_local = ev0.elapsed_time(ev1) / 1e3
+    t_max = max_over_ranks(dist, t_local, dev)
+    total_traj = sum_over_ranks(dist, float(args.steps), dev)
+    value = total_traj / t_max
+
+    kclass = f"dslash_{args.sloppy}"
+    timers = {k: lqcd.kernel_timer_read(k) for k in lqcd.KERNEL_CLASSES}
+    lqcd.kernel_timers(False)
+    ms, n = timers[kclass]
+    Vh = V // 2
+    bytes_per_launch = SLOPPY_BYTES[args.sloppy] * Vh
+    peaks = measured_peaks()
+    achieved = bytes_per_launch / (ms / n * 1e-3) / 1e9 if n else None
+    traffic = stored_traffic(kclass) if tuple(dims) == (32, 32, 32, 64) else None
+    roofline = {"kernel": kclass, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"] if achieved else None, "traffic": traffic,
+                "peak_source": peaks["source"], "algorithmic_bytes_per_launch": bytes_per_launch,
+                "avg_launch_us": ms / n * 1e3 if n else None, "launches": n}
+    step_ms = t_max / args.steps * 1e3
+    kernel_share = {k: {"ms_per_traj": v[0] / args.steps, "launches_per_traj": v[1] / args.steps}
+                    for k, v in timers.items() if v[1]}
+
+    # FP64 GPU path beside it: same start, same chain, same trajectory counters
+    # as the first timed mixed trajectories, so dH differences measure the
+    # error of the mixed path
+    fp64 = None
+    if args.fp64_steps > 0:
+        U64 = lqcd.gauge_field(dims)
+        lqcd.gauge_start(U64, SEED, EPS, chain=rank)
+        st64 = lqcd.HmcState(U64, seed=SEED, chain=rank, traj0=args.warmup)
+        p64 = lqcd.hmc_params(wl["beta"], wl["kappa"], wl["tau"], wl["nsteps"], lqcd.OMELYAN, n_flavors=2,
+                              cg=lqcd.cg_params(tol=wl["cg_tol"], maxiter=20000, sloppy=lqcd.F64))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        i64 = [st64.trajectory(p64) for _ in range(args.fp64_steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        # the mixed chain's first timed trajectory against the FP64 chain's first
+        same_start = all(i["accepted"] == 0 for i in infos[:args.fp64_steps]) or args.warmup == 0
+        fp64 = {"trajectories_per_s": args.fp64_steps / t64, "s_per_traj": t64 / args.fp64_steps,
+                "cg_iters_per_traj": float(np.mean([i["cg_iters"] for i in i64])),
+                "dH": [i["dH"] for i in i64], "mixed_speedup": value / world / (args.fp64_steps / t64),
+                "mixed_minus_fp64_dH": ([m["dH"] - f["dH"] for m, f in zip(infos, i64)]
+                                        if same_start else None),
+                "mixed_minus_fp64_plaq": ([m["plaq"] - f["plaq"] for m, f in zip(infos, i64)]
+                                          if same_start else None)}
+        st64.close()
+        del U64
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        host_in = torch.empty(V * 4 * 9 * 2, dtype=torch.float64, pin_memory=True).numpy()
+        host_out = torch.empty(V * 4 * 9 * 2, dtype=torch.float64, pin_memory=True).numpy()
+        hin = host_in.view(np.complex128).reshape(V, 4, 3, 3)
+        hout = host_out.view(np.complex128).reshape(V, 4, 3, 3)
+        U.download(out=hin)
+        torch.cuda.synchronize()
+        barrier(dist, local)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            U.upload(hin)
+            info = state.trajectory(params)
+            U.download(out=hout)
+            hin, hout = hout, hin
+        e1.record(stream)
+        torch.cuda.synchronize()
+        te = max_over_ranks(dist, e0.elapsed_time(e1) / 1e3, dev)
+        nb = V * 4 * 18 * 8
+        e2e = {"value": sum_over_ranks(dist, float(args.e2e_steps), dev) / te, "unit": "trajectories/s",
+               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 96, "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_block(oracle_sample())
+
+    if rank == 0:
+        acc = [i["accepted"] for i in infos]
+        line = {
+            "metric": "trajectories/s", "value": value, "unit": "trajectories/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": (f"f32 math ({args.sloppy} storage in the solver, {args.force_prec} forces); f64 master "
+                      f"links/momenta, residuals, dots, link update, dH"),
+            "data": "synthetic", "config": config_block(args, args.sloppy), "gpu_launches": launches,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "fp64_gpu_path": fp64,
+            "physics": {"acceptance": float(np.mean(acc)), "dH": [i["dH"] for i in infos],
+                        "plaquette": [i["plaq"] for i in infos],
+                        "cg_iters_per_traj": float(np.mean([i["cg_iters"] for i in infos])),
+                        "solves_per_traj": float(np.mean([i["n_solves"] for i in infos])),
+                        "cg_true_rel_res_max": max(i["cg_true_rel_res_max"] for i in infos)},
+            "kernel_time_per_traj": kernel_share,
+        }
+        print(json.dumps(line))
+    state.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--sloppy", choices=("f32", "f16n", "bf16"), default="f16n")
+    ap.add_argument("--delta", type=float, default=0.003)
+    ap.add_argument("--force-prec", choices=("f64", "f32"), default="f32")
+    ap.add_argument("--dims", type=int, nargs=4, default=WORKLOAD["dims"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -112,6 +112,17 @@ const char *lqcd_version(void);
 /* Number of kernels this library has launched in this process (all threads). */
 uint64_t lqcd_launch_count(void);
 
+/* Kernel timers: while enabled, launches of the instrumented kernel classes
+ * are bracketed by CUDA events recorded on the launching stream.  Classes:
+ * "dslash_f64", "dslash_f32", "dslash_f16n", "dslash_bf16" (every half
+ * hopping-term launch of that storage precision, fused epilogues included),
+ * "dslash_df64" (the mixed solver's float-float residual products),
+ * "gauge_force", "fermion_force", "link_update".  Enabling clears the totals.
+ * lqcd_kernel_timer_read synchronises the device, then returns the summed
+ * event time in milliseconds and the number of launches of one class. */
+lqcd_status lqcd_kernel_timers(int enable);
+lqcd_status lqcd_kernel_timer_read(const char *kernel_class, double *total_ms, uint64_t *launches);
+
 /* Device allocator hook.  alloc(bytes, stream, ctx) returns device memory or
  * NULL; free(ptr, stream, ctx) releases it.  Passing NULL for both restores
  * cudaMalloc / cudaFree.  Fields remember the hook they were allocated with. */
@@ -236,6 +247,12 @@ lqcd_status lqcd_cg_solve(lqcd_field *x, const lqcd_field *U, const lqcd_field *
  * P: MOMENTUM, U: GAUGE F64/18. */
 lqcd_status lqcd_gauge_force(lqcd_field *P, const lqcd_field *U, double beta, double coeff, void *stream);
 
+/* The same with the arithmetic chosen: LQCD_F64, or LQCD_F32 (the links
+ * rounded once to an FP32 12-real copy, FP32 staples, the increment added to
+ * the FP64 momenta). */
+lqcd_status lqcd_gauge_force_ex(lqcd_field *P, const lqcd_field *U, double beta, double coeff, lqcd_prec arith,
+                                void *stream);
+
 /* Two-flavour fermion force fused with the momentum update, given the even
  * solution X_e = (Mhat^dag Mhat)^-1 phi_e:
  *   Y_e = Mhat X_e, A = (X_e, Doe X_e), B = (Y_e, Deo^dag Y_e),
@@ -245,6 +262,12 @@ lqcd_status lqcd_gauge_force(lqcd_field *P, const lqcd_field *U, double beta, do
  * P: MOMENTUM, U: GAUGE F64/18, X_e: EVEN F64.  Uses three temporary spinors. */
 lqcd_status lqcd_fermion_force(lqcd_field *P, const lqcd_field *U, const lqcd_field *X_e, double kappa,
                                double coeff, void *stream);
+
+/* The same with the arithmetic chosen (LQCD_F64 or LQCD_F32: X_e and the
+ * links rounded to FP32 (12-real links), the three hopping terms and the link
+ * kernel in FP32, the increment added to the FP64 momenta). */
+lqcd_status lqcd_fermion_force_ex(lqcd_field *P, const lqcd_field *U, const lqcd_field *X_e, double kappa,
+                                  double coeff, lqcd_prec arith, void *stream);
 
 /* SU(3) exponential link update (paper Sec. 1, "exponentiating of SU(3)
  * matrices"): U_mu(x) <- exp(i c P_mu(x)) U_mu(x), exp by Cayley-Hamilton
@@ -280,6 +303,11 @@ typedef struct {
     lqcd_cg_params cg;          /* solver of every force and action evaluation */
     int reunitarize;            /* 1: reunitarize the links after the accept/reject */
     int metropolis;             /* 1: accept iff u < exp(-dH); 0: always accept */
+    lqcd_prec force_prec;       /* arithmetic of the molecular dynamics: LQCD_F64, or LQCD_F32: both
+                                   forces in FP32 from an FP32 12-real copy of the links (increments
+                                   accumulated into the FP64 momenta) and the link update's
+                                   exponential by Cayley-Hamilton in FP32, re-unitarized in FP64
+                                   before the FP64 product with the FP64 links */
 } lqcd_hmc_params;
 
 typedef struct {

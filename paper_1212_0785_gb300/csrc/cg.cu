@@ -5,7 +5,12 @@
 // Brower, Rebbi 2010): the iteration runs on sloppy fields (FP32, FP16+norm
 // or BF16 storage, FP32 arithmetic, FP64 dot products) and whenever the sloppy
 // residual has dropped by delta since the last update the solution increment
-// is folded into the FP64 solution and the residual recomputed in FP64.
+// is folded into the accurate solution and the residual recomputed
+// accurately.  The accurate solution, source, links and residual of the mixed
+// solve are held in float-float storage and the residual is computed in
+// float-float arithmetic (about 48 significant bits, see df64.cuh): on GB300
+// that runs several times faster than FP64 and is far more accurate than the
+// 1e-10 tolerance needs.  The plain FP64 solve uses FP64 throughout.
 //
 // Every scalar (rr, pAp, alpha, beta) lives on the device: the reduction
 // kernels compute them in a fixed order and raise a pause flag when the host
@@ -16,6 +21,7 @@
 #include <cmath>
 
 #include "cg.cuh"
+#include "df64.cuh"
 
 namespace lqcd {
 
@@ -130,6 +136,84 @@ __global__ void accum_zero_kernel(SpinorRef<LQCD_F64> x, SpinorRef<LQCD_F32> xs,
     xs.store(cb, sp_zero<double>());
 }
 
+// ---------------------------------------------------------------- float-float helpers
+
+// x += xs (exact float-float sum); xs = 0
+__global__ void accum_df_kernel(SpinorRef<PREC_DF> x, SpinorRef<LQCD_F32> xs, int Vh)
+{
+    int cb = blockIdx.x * BB + threadIdx.x;
+    if (cb >= Vh) return;
+    Sp<Df> xv = x.load_rw<Df>(cb);
+    Sp<float> dv = xs.load_rw<float>(cb);
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            xv.c[a][k].re += Df(dv.c[a][k].re, 0.f);
+            xv.c[a][k].im += Df(dv.c[a][k].im, 0.f);
+        }
+    x.store(cb, xv);
+    xs.store(cb, sp_zero<float>());
+}
+
+// r = b - t in float-float; block partials of |r|^2 from the leading parts
+__global__ void __launch_bounds__(BB) residual_df_kernel(SpinorRef<PREC_DF> r, SpinorRef<PREC_DF> b,
+                                                         SpinorRef<PREC_DF> t, double *partials, int nb, int Vh)
+{
+    int cb = blockIdx.x * BB + threadIdx.x;
+    double n2[1] = {0.0};
+    if (cb < Vh) {
+        Sp<Df> bv = b.load_rw<Df>(cb), tv = t.load_rw<Df>(cb);
+        float acc = 0.f;
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                bv.c[a][k] = bv.c[a][k] - tv.c[a][k];
+                acc += bv.c[a][k].re.hi * bv.c[a][k].re.hi + bv.c[a][k].im.hi * bv.c[a][k].im.hi;
+            }
+        r.store(cb, bv);
+        n2[0] = acc;
+    }
+    block_sum_store<1, BB>(n2, partials, nb);
+}
+
+template <lqcd_prec PS, lqcd_prec PD, typename R>
+__global__ void convert_spinor_kernel(SpinorRef<PD> dst, SpinorRef<PS> src, int Vh)
+{
+    int cb = blockIdx.x * BB + threadIdx.x;
+    if (cb >= Vh) return;
+    dst.store(cb, src.template load_rw<R>(cb));
+}
+
+__global__ void split_gauge_kernel(GaugeRef<PREC_DF> dst, GaugeRef<LQCD_F64> src, int Vh)
+{
+    long t = blockIdx.x * (long)BB + threadIdx.x;
+    if (t >= 8L * Vh) return;
+    int cb = (int)(t % Vh), mp = (int)(t / Vh);
+    dst.store(mp >> 1, mp & 1, cb, src.load<double>(mp >> 1, mp & 1, cb));
+}
+
+template <lqcd_prec PS, lqcd_prec PD, typename R>
+static lqcd_status convert_spinor(lqcd_field *dst, const lqcd_field *src, cudaStream_t s)
+{
+    convert_spinor_kernel<PS, PD, R><<<nblocks_for(src->Vh, BB), BB, 0, s>>>(spinor_ref<PD>(dst), spinor_ref<PS>(src),
+                                                                             src->Vh);
+    LQCD_LAUNCHED();
+    return LQCD_OK;
+}
+
+// float-float residual -> sloppy residual
+static lqcd_status df_to_sloppy(lqcd_field *dst, const lqcd_field *src, cudaStream_t s)
+{
+    switch (dst->prec) {
+    case LQCD_F32: return convert_spinor<PREC_DF, LQCD_F32, float>(dst, src, s);
+    case LQCD_F16N: return convert_spinor<PREC_DF, LQCD_F16N, float>(dst, src, s);
+    case LQCD_BF16: return convert_spinor<PREC_DF, LQCD_BF16, float>(dst, src, s);
+    default: set_error("df_to_sloppy: bad precision"); return LQCD_EINVAL;
+    }
+}
+
 // ---------------------------------------------------------------- pinned scalars
 
 struct Pinned {
@@ -158,19 +242,27 @@ lqcd_status CgWorkspace::ensure(const lqcd_lattice &l, lqcd_prec sl, cudaStream_
 {
     if (ready && same_lattice(lat, l) && sloppy == sl) return LQCD_OK;
     ready = false;
-    for (FieldPtr *f : {&r64, &t64a, &t64b, &tmpo64, &p64, &xs, &rs, &ps, &ts, &tmpos}) {
+    for (FieldPtr *f : {&r64, &t64a, &t64b, &tmpo64, &p64, &xs, &rs, &ps, &ts, &tmpos, &Udf, &xdf, &bdf, &rdf,
+                        &t1df, &t2df, &tmpodf}) {
         if (f->f) lqcd_field_free(f->f);
         f->f = nullptr;
     }
     lat = l;
     sloppy = sl;
-    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &r64.f));
-    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &t64a.f));
-    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &t64b.f));
-    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F64, 0, &tmpo64.f));
     if (sl == LQCD_F64) {
+        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &r64.f));
+        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &t64a.f));
+        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &t64b.f));
+        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F64, 0, &tmpo64.f));
         LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &p64.f));
     } else {
+        LQCD_TRY(field_alloc_df(&lat, LQCD_GAUGE, &Udf.f));
+        LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &xdf.f));
+        LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &bdf.f));
+        LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &rdf.f));
+        LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &t1df.f));
+        LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &t2df.f));
+        LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_ODD, &tmpodf.f));
         LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F32, 0, &xs.f));
         LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, sl, 0, &rs.f));
         LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, sl, 0, &ps.f));
@@ -196,6 +288,26 @@ static lqcd_status launch_p_update(lqcd_field *p, lqcd_field *r, const CgScalars
     case LQCD_BF16: p_update_kernel<LQCD_BF16><<<nb, BB, 0, s>>>(spinor_ref<LQCD_BF16>(p), spinor_ref<LQCD_BF16>(r), sc, p->Vh); break;
     }
     LQCD_LAUNCHED();
+    return LQCD_OK;
+}
+
+// accurate residual r = b - A x of the mixed solve in float-float arithmetic
+// (x, b, links in float-float storage); |r|^2 in *rr
+static lqcd_status true_residual_df(CgWorkspace &ws, double kappa, double *rr, cudaStream_t s)
+{
+    double k2 = kappa * kappa;
+    LQCD_TRY(dslash_plain(ws.tmpodf.f, ws.Udf.f, ws.xdf.f, 0, nullptr, s));
+    LQCD_TRY(dslash_xpay(ws.t1df.f, ws.Udf.f, ws.tmpodf.f, 0, ws.xdf.f, -k2, nullptr, nullptr, s));
+    LQCD_TRY(dslash_plain(ws.tmpodf.f, ws.Udf.f, ws.t1df.f, 1, nullptr, s));
+    LQCD_TRY(dslash_xpay(ws.t2df.f, ws.Udf.f, ws.tmpodf.f, 1, ws.t1df.f, -k2, nullptr, nullptr, s));
+    int Vh = ws.xdf.f->Vh, nb = nblocks_for(Vh, BB);
+    residual_df_kernel<<<nb, BB, 0, s>>>(spinor_ref<PREC_DF>(ws.rdf.f), spinor_ref<PREC_DF>(ws.bdf.f),
+                                         spinor_ref<PREC_DF>(ws.t2df.f), (double *)ws.partials.p, nb, Vh);
+    LQCD_LAUNCHED();
+    LQCD_TRY(reduce_partials((double *)ws.partials.p, nb, 1, (double *)ws.scalars.p, s));
+    LQCD_TRY(pinned());
+    LQCD_TRY(read_scalars((double *)ws.scalars.p, g_pinned.d, 1, s));
+    *rr = g_pinned.d[0];
     return LQCD_OK;
 }
 
@@ -248,15 +360,20 @@ lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, con
 
     lqcd_field *P, *R, *T, *TMP, *XS;
     const lqcd_field *UU;
-    LQCD_CUDA(cudaMemcpyAsync(ws.r64.f->data, b->data, b->bytes, cudaMemcpyDeviceToDevice, s));
     if (mixed) {
         LQCD_REQUIRE(Us && Us->kind == LQCD_GAUGE && Us->prec == prm.sloppy && Us->recon == 12,
                      "cg: mixed solve needs a 12-real link copy in the sloppy precision");
+        split_gauge_kernel<<<nblocks_for(8L * Vh, BB), BB, 0, s>>>(gauge_ref<PREC_DF>(ws.Udf.f),
+                                                                   gauge_ref<LQCD_F64>(U), Vh);
+        LQCD_LAUNCHED();
+        LQCD_TRY((convert_spinor<LQCD_F64, PREC_DF, double>(ws.bdf.f, b, s)));
+        LQCD_CUDA(cudaMemsetAsync(ws.xdf.f->data, 0, ws.xdf.f->bytes, s));
         LQCD_TRY(lqcd_field_copy(ws.rs.f, b, s));
         LQCD_TRY(lqcd_field_copy(ws.ps.f, b, s));
         LQCD_CUDA(cudaMemsetAsync(ws.xs.f->data, 0, ws.xs.f->bytes, s));
         P = ws.ps.f, R = ws.rs.f, T = ws.ts.f, TMP = ws.tmpos.f, XS = ws.xs.f, UU = Us;
     } else {
+        LQCD_CUDA(cudaMemcpyAsync(ws.r64.f->data, b->data, b->bytes, cudaMemcpyDeviceToDevice, s));
         LQCD_CUDA(cudaMemcpyAsync(ws.p64.f->data, b->data, b->bytes, cudaMemcpyDeviceToDevice, s));
         P = ws.p64.f, R = ws.r64.f, T = ws.t64a.f, TMP = ws.tmpo64.f, XS = x, UU = U;
     }
@@ -296,10 +413,15 @@ lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, con
             return finish(LQCD_ENUMERIC);
         }
         if (mixed) {
-            accum_zero_kernel<<<nblocks_for(Vh, BB), BB, 0, s>>>(spinor_ref<LQCD_F64>(x), spinor_ref<LQCD_F32>(XS), Vh);
+            accum_df_kernel<<<nblocks_for(Vh, BB), BB, 0, s>>>(spinor_ref<PREC_DF>(ws.xdf.f), spinor_ref<LQCD_F32>(XS),
+                                                               Vh);
             LQCD_LAUNCHED();
+            LQCD_TRY(true_residual_df(ws, kappa, &rr_true, s));
+            // the FP64 solution is the float-float one rounded
+            LQCD_TRY((convert_spinor<PREC_DF, LQCD_F64, double>(x, ws.xdf.f, s)));
+        } else {
+            LQCD_TRY(true_residual(ws, x, U, b, kappa, &rr_true, s));
         }
-        LQCD_TRY(true_residual(ws, x, U, b, kappa, &rr_true, s));
         inf.true_rel_res = std::sqrt(rr_true / bb);
         if (!std::isfinite(rr_true)) {
             set_error("cg: non-finite true residual");
@@ -312,8 +434,8 @@ lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, con
         }
         inf.restarts++;
         double beta;
-        if (mixed) { // reliable update: continue with the FP64 residual
-            LQCD_TRY(lqcd_field_copy(ws.rs.f, ws.r64.f, s));
+        if (mixed) { // reliable update: continue with the accurate residual
+            LQCD_TRY(df_to_sloppy(ws.rs.f, ws.rdf.f, s));
             beta = rr_true / h.rr;
         } else { // the iterated residual lied: restart from the true one
             if (inf.restarts > prm.max_restarts) {

@@ -10,9 +10,12 @@ struct CgWorkspace {
     lqcd_lattice lat{};
     lqcd_prec sloppy = LQCD_F64;
     bool ready = false;
-    FieldPtr r64, t64a, t64b, tmpo64;  // FP64 residual and operator temporaries
+    FieldPtr r64, t64a, t64b, tmpo64;  // FP64 residual and operator temporaries (FP64 CG)
     FieldPtr p64;                      // FP64 search direction (plain FP64 CG)
     FieldPtr xs, rs, ps, ts, tmpos;    // sloppy fields (mixed CG)
+    // mixed CG: the accurate solution, source, residual and operator
+    // temporaries in float-float storage, and the float-float link copy
+    FieldPtr Udf, xdf, bdf, rdf, t1df, t2df, tmpodf;
     DevBuf sc, partials, scalars;
     lqcd_status ensure(const lqcd_lattice &lat, lqcd_prec sloppy, cudaStream_t s);
 };

@@ -11,6 +11,7 @@
 //
 // FP64 storage uses FP64 arithmetic; FP32, FP16+norm and BF16 storage use
 // FP32 arithmetic with 12-real links (row 2 = conj(row0 x row1)).
+#include "df64.cuh"
 #include "dslash.cuh"
 #include "spin.cuh"
 
@@ -164,8 +165,8 @@ static lqcd_status check_pair(const lqcd_field *out, const lqcd_field *U, const 
                  "dslash: in/out must be half spinors of opposite parity");
     LQCD_REQUIRE(same_lattice(U->lat, in->lat) && same_lattice(U->lat, out->lat), "dslash: lattices differ");
     LQCD_REQUIRE(in->prec == out->prec, "dslash: in/out precisions differ");
-    LQCD_REQUIRE(U->prec == in->prec, "dslash: link precision %d does not match spinor precision %d", (int)U->prec,
-                 (int)in->prec);
+    LQCD_REQUIRE(U->prec == in->prec || (U->prec == LQCD_F64 && in->prec == LQCD_F32),
+                 "dslash: link precision %d does not match spinor precision %d", (int)U->prec, (int)in->prec);
     return LQCD_OK;
 }
 
@@ -177,8 +178,12 @@ template <>
 struct ArithOf<LQCD_F64> {
     using type = double;
 };
+template <>
+struct ArithOf<PREC_DF> {
+    using type = Df;
+};
 
-template <lqcd_prec P>
+template <lqcd_prec P, lqcd_prec GP = P>
 static void launch_plain(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int dagger, const int *skip,
                          cudaStream_t s)
 {
@@ -186,14 +191,14 @@ static void launch_plain(lqcd_field *out, const lqcd_field *U, const lqcd_field 
     Geo g = make_geo(in->lat);
     int nb = dslash_blocks(g.Vh);
     if (dagger)
-        dslash_plain_kernel<R, P, P, true><<<nb, DS_BLOCK, 0, s>>>(spinor_ref<P>(out), spinor_ref<P>(in), gauge_ref<P>(U),
-                                                                   g, out_parity(out), skip);
+        dslash_plain_kernel<R, P, GP, true><<<nb, DS_BLOCK, 0, s>>>(spinor_ref<P>(out), spinor_ref<P>(in),
+                                                                    gauge_ref<GP>(U), g, out_parity(out), skip);
     else
-        dslash_plain_kernel<R, P, P, false><<<nb, DS_BLOCK, 0, s>>>(spinor_ref<P>(out), spinor_ref<P>(in),
-                                                                    gauge_ref<P>(U), g, out_parity(out), skip);
+        dslash_plain_kernel<R, P, GP, false><<<nb, DS_BLOCK, 0, s>>>(spinor_ref<P>(out), spinor_ref<P>(in),
+                                                                     gauge_ref<GP>(U), g, out_parity(out), skip);
 }
 
-template <lqcd_prec P>
+template <lqcd_prec P, lqcd_prec GP = P>
 static void launch_xpay(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int dagger, const lqcd_field *x,
                         double b, double *partials, const int *skip, cudaStream_t s)
 {
@@ -201,13 +206,13 @@ static void launch_xpay(lqcd_field *out, const lqcd_field *U, const lqcd_field *
     Geo g = make_geo(in->lat);
     int nb = dslash_blocks(g.Vh);
     if (dagger)
-        dslash_xpay_kernel<R, P, P, true><<<nb, DS_BLOCK, 0, s>>>(spinor_ref<P>(out), spinor_ref<P>(in), gauge_ref<P>(U),
-                                                                  g, out_parity(out), spinor_ref<P>(x), (R)b, partials,
-                                                                  nb, skip);
-    else
-        dslash_xpay_kernel<R, P, P, false><<<nb, DS_BLOCK, 0, s>>>(spinor_ref<P>(out), spinor_ref<P>(in),
-                                                                   gauge_ref<P>(U), g, out_parity(out),
+        dslash_xpay_kernel<R, P, GP, true><<<nb, DS_BLOCK, 0, s>>>(spinor_ref<P>(out), spinor_ref<P>(in),
+                                                                   gauge_ref<GP>(U), g, out_parity(out),
                                                                    spinor_ref<P>(x), (R)b, partials, nb, skip);
+    else
+        dslash_xpay_kernel<R, P, GP, false><<<nb, DS_BLOCK, 0, s>>>(spinor_ref<P>(out), spinor_ref<P>(in),
+                                                                    gauge_ref<GP>(U), g, out_parity(out),
+                                                                    spinor_ref<P>(x), (R)b, partials, nb, skip);
 }
 
 template <lqcd_prec P, lqcd_prec XP>
@@ -233,11 +238,18 @@ lqcd_status dslash_plain(lqcd_field *out, const lqcd_field *U, const lqcd_field 
                          cudaStream_t s)
 {
     LQCD_TRY(check_pair(out, U, in));
+    KernelTimer kt(dslash_class(in->prec), s);
     switch (in->prec) {
     case LQCD_F64: launch_plain<LQCD_F64>(out, U, in, dagger, skip, s); break;
-    case LQCD_F32: launch_plain<LQCD_F32>(out, U, in, dagger, skip, s); break;
+    case LQCD_F32:
+        if (U->prec == LQCD_F64)
+            launch_plain<LQCD_F32, LQCD_F64>(out, U, in, dagger, skip, s);
+        else
+            launch_plain<LQCD_F32>(out, U, in, dagger, skip, s);
+        break;
     case LQCD_F16N: launch_plain<LQCD_F16N>(out, U, in, dagger, skip, s); break;
     case LQCD_BF16: launch_plain<LQCD_BF16>(out, U, in, dagger, skip, s); break;
+    default: launch_plain<PREC_DF>(out, U, in, dagger, skip, s); break;
     }
     LQCD_LAUNCHED();
     return LQCD_OK;
@@ -248,11 +260,18 @@ lqcd_status dslash_xpay(lqcd_field *out, const lqcd_field *U, const lqcd_field *
 {
     LQCD_TRY(check_pair(out, U, in));
     LQCD_REQUIRE(x && x->kind == out->kind && x->prec == out->prec, "dslash_xpay: x must match out");
+    KernelTimer kt(dslash_class(in->prec), s);
     switch (in->prec) {
     case LQCD_F64: launch_xpay<LQCD_F64>(out, U, in, dagger, x, b, partials, skip, s); break;
-    case LQCD_F32: launch_xpay<LQCD_F32>(out, U, in, dagger, x, b, partials, skip, s); break;
+    case LQCD_F32:
+        if (U->prec == LQCD_F64)
+            launch_xpay<LQCD_F32, LQCD_F64>(out, U, in, dagger, x, b, partials, skip, s);
+        else
+            launch_xpay<LQCD_F32>(out, U, in, dagger, x, b, partials, skip, s);
+        break;
     case LQCD_F16N: launch_xpay<LQCD_F16N>(out, U, in, dagger, x, b, partials, skip, s); break;
     case LQCD_BF16: launch_xpay<LQCD_BF16>(out, U, in, dagger, x, b, partials, skip, s); break;
+    default: launch_xpay<PREC_DF>(out, U, in, dagger, x, b, partials, skip, s); break;
     }
     LQCD_LAUNCHED();
     return LQCD_OK;
@@ -262,6 +281,7 @@ lqcd_status dslash_cg(const lqcd_field *U, const lqcd_field *in, int dagger, con
                       lqcd_field *xs, lqcd_field *r, const lqcd_field *p, double *partials, const CgScalars *sc,
                       cudaStream_t s)
 {
+    KernelTimer kt(dslash_class(in->prec), s);
     switch (in->prec) {
     case LQCD_F64: launch_cg<LQCD_F64, LQCD_F64>(U, in, dagger, t, b, xs, r, p, partials, sc, s); break;
     case LQCD_F32: launch_cg<LQCD_F32, LQCD_F32>(U, in, dagger, t, b, xs, r, p, partials, sc, s); break;

@@ -2,8 +2,10 @@
 // precision conversion, Philox refresh kernels, start configuration, link
 // update, reunitarization and the FP64 reductions (plaquette, kinetic energy,
 // spinor dot products).
+#include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "lqcd_internal.cuh"
 #include "su3_device.cuh"
@@ -29,6 +31,70 @@ lqcd_status cuda_fail(cudaError_t e, const char *what, const char *file, int lin
 {
     set_error("%s failed at %s:%d: %s", what, file, line, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? LQCD_ENOMEM : LQCD_ECUDA;
+}
+
+// ------------------------------------------------------------------ kernel timers
+
+static const char *k_class_names[K_NCLASS] = {"dslash_f64",  "dslash_f32",  "dslash_f16n",   "dslash_bf16",
+                                              "dslash_df64", "gauge_force", "fermion_force", "link_update"};
+static std::mutex g_timer_mu;
+static std::atomic<bool> g_timers_on{false};
+static std::vector<cudaEvent_t> g_event_pool;
+struct PendingTiming {
+    int cls;
+    cudaEvent_t a, b;
+};
+static std::vector<PendingTiming> g_pending;
+static double g_timer_ms[K_NCLASS];
+static uint64_t g_timer_n[K_NCLASS];
+
+static cudaEvent_t pool_event()
+{
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+KernelTimer::KernelTimer(int c, cudaStream_t st) : cls(c), s(st)
+{
+    if (!g_timers_on.load(std::memory_order_relaxed)) return;
+    std::lock_guard<std::mutex> lk(g_timer_mu);
+    a = pool_event();
+    b = pool_event();
+    if (a && b) cudaEventRecord(a, s);
+}
+
+KernelTimer::~KernelTimer()
+{
+    if (!a || !b) return;
+    cudaEventRecord(b, s);
+    std::lock_guard<std::mutex> lk(g_timer_mu);
+    g_pending.push_back({cls, a, b});
+}
+
+// resolve pending event pairs (device synchronised by the caller)
+static void drain_timers_locked()
+{
+    for (auto &p : g_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            g_timer_ms[p.cls] += ms;
+            g_timer_n[p.cls] += 1;
+        } else {
+            cudaGetLastError();
+        }
+        g_event_pool.push_back(p.a);
+        g_event_pool.push_back(p.b);
+    }
+    g_pending.clear();
 }
 
 // ------------------------------------------------------------------ allocator
@@ -164,6 +230,7 @@ static bool valid_combo(lqcd_kind kind, lqcd_prec prec, int recon)
 static size_t field_data_bytes(lqcd_kind kind, lqcd_prec prec, int Vh)
 {
     size_t n = (size_t)Vh;
+    if (prec == (lqcd_prec)4) prec = LQCD_F64; // float-float pairs: as many bytes as FP64
     switch (kind) {
     case LQCD_GAUGE: return prec == LQCD_F64 ? n * 8 * 18 * 8 : (prec == LQCD_F32 ? n * 8 * 12 * 4 : n * 8 * 12 * 2);
     case LQCD_MOMENTUM: return n * 8 * 8 * 8;
@@ -177,6 +244,17 @@ static size_t field_data_bytes(lqcd_kind kind, lqcd_prec prec, int Vh)
 lqcd_status field_alloc_like(const lqcd_field *like, lqcd_kind kind, lqcd_prec prec, int recon, lqcd_field **out)
 {
     return lqcd_field_alloc(&like->lat, kind, prec, recon, out);
+}
+
+static lqcd_status field_alloc_impl(const lqcd_lattice *lat, lqcd_kind kind, lqcd_prec prec, int recon,
+                                    lqcd_field **out);
+
+// fields in the internal float-float precision (gauge with 18 reals, half spinors)
+lqcd_status field_alloc_df(const lqcd_lattice *lat, lqcd_kind kind, lqcd_field **out)
+{
+    LQCD_REQUIRE(kind == LQCD_GAUGE || kind == LQCD_SPINOR_EVEN || kind == LQCD_SPINOR_ODD,
+                 "float-float fields are gauge or half spinors");
+    return field_alloc_impl(lat, kind, (lqcd_prec)4, kind == LQCD_GAUGE ? 18 : 0, out);
 }
 
 // ------------------------------------------------------------------ host layout permutation kernels
@@ -489,22 +567,43 @@ __global__ void eta_refresh_kernel(SpinorRef<LQCD_F64> E, Geo g, uint32_t seed, 
 
 // ------------------------------------------------------------------ link update / reunitarize
 
-template <lqcd_prec PS>
-__global__ void link_update_kernel(GaugeRef<LQCD_F64> U, MomRef P, double c, GaugeRef<PS> Us, int Vh, int write_sloppy)
+// U <- exp(i c P) U.  FAST (the mixed-precision trajectory): the exponential
+// by Cayley-Hamilton in FP32, re-unitarized in FP64 so that the FP64 links
+// stay in SU(3) to FP64 rounding; otherwise everything in FP64.  The new links
+// are also written to the 12-real copies Us (solver precision) and Uf (FP32)
+// when those are given.
+template <lqcd_prec PS, bool FAST>
+__global__ void link_update_kernel(GaugeRef<LQCD_F64> U, MomRef P, double c, GaugeRef<PS> Us, GaugeRef<LQCD_F32> Uf,
+                                   int Vh, int write_sloppy, int write_f32)
 {
     long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (t >= 8L * Vh) return;
     int cb = (int)(t % Vh);
     int mp = (int)(t / Vh);
     int mu = mp >> 1, par = mp & 1;
-    double p[8];
-    for (int a = 0; a < 8; a++) p[a] = P.d[P.idx(mu, par, a, cb)];
-    M3<double> Q = herm_from_coeffs(p, c);
-    M3<double> E = expi_cayley_hamilton(Q);
+    M3<double> E;
+    if (FAST) {
+        float p[8];
+        for (int a = 0; a < 8; a++) p[a] = (float)P.d[P.idx(mu, par, a, cb)];
+        M3<float> Ef = expi_cayley_hamilton(herm_from_coeffs(p, (float)c));
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) E.e[i][j] = cx<double>(Ef.e[i][j].re, Ef.e[i][j].im);
+        reunit_rows(E);
+    } else {
+        double p[8];
+        for (int a = 0; a < 8; a++) p[a] = P.d[P.idx(mu, par, a, cb)];
+        E = expi_cayley_hamilton(herm_from_coeffs(p, c));
+    }
     M3<double> u = U.load<double>(mu, par, cb);
     M3<double> nu = m3_mul(E, u);
     U.store(mu, par, cb, nu);
-    if (write_sloppy) Us.store(mu, par, cb, nu);
+    if (write_sloppy || write_f32) {
+        M3<float> nf; // rows 0, 1 rounded once
+        for (int i = 0; i < 2; i++)
+            for (int j = 0; j < 3; j++) nf.e[i][j] = cx<float>((float)nu.e[i][j].re, (float)nu.e[i][j].im);
+        if (write_sloppy) Us.store(mu, par, cb, nf);
+        if (write_f32) Uf.store(mu, par, cb, nf);
+    }
 }
 
 __global__ void reunitarize_kernel(GaugeRef<LQCD_F64> U, int Vh, double *partials)
@@ -657,28 +756,38 @@ lqcd_status reunitarize_dev(lqcd_field *U, double *dst_dev, DevBuf &part, cudaSt
     return LQCD_OK;
 }
 
-lqcd_status link_update_dev(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *Us, cudaStream_t s)
+template <bool FAST>
+static lqcd_status launch_link_update(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *Us, lqcd_field *Uf,
+                                      cudaStream_t s)
 {
     long n = 8L * U->Vh;
     int nb = nblocks_for(n, 128);
-    if (!Us) {
-        link_update_kernel<LQCD_F64><<<nb, 128, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c, gauge_ref<LQCD_F64>(U), U->Vh, 0);
-    } else {
-        switch (Us->prec) {
-        case LQCD_F32:
-            link_update_kernel<LQCD_F32><<<nb, 128, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c, gauge_ref<LQCD_F32>(Us), U->Vh, 1);
-            break;
-        case LQCD_F16N:
-            link_update_kernel<LQCD_F16N><<<nb, 128, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c, gauge_ref<LQCD_F16N>(Us), U->Vh, 1);
-            break;
-        case LQCD_BF16:
-            link_update_kernel<LQCD_BF16><<<nb, 128, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c, gauge_ref<LQCD_BF16>(Us), U->Vh, 1);
-            break;
-        default: set_error("sloppy link copy must be 12-real F32/F16N/BF16"); return LQCD_EINVAL;
-        }
+    GaugeRef<LQCD_F32> uf = Uf ? gauge_ref<LQCD_F32>(Uf) : GaugeRef<LQCD_F32>{nullptr, U->Vh};
+    int wf = Uf ? 1 : 0;
+    switch (Us ? Us->prec : LQCD_F32) {
+    case LQCD_F32:
+        link_update_kernel<LQCD_F32, FAST><<<nb, 128, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c,
+                                                              Us ? gauge_ref<LQCD_F32>(Us) : uf, uf, U->Vh, Us ? 1 : 0, wf);
+        break;
+    case LQCD_F16N:
+        link_update_kernel<LQCD_F16N, FAST><<<nb, 128, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c,
+                                                               gauge_ref<LQCD_F16N>(Us), uf, U->Vh, 1, wf);
+        break;
+    case LQCD_BF16:
+        link_update_kernel<LQCD_BF16, FAST><<<nb, 128, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c,
+                                                               gauge_ref<LQCD_BF16>(Us), uf, U->Vh, 1, wf);
+        break;
+    default: set_error("sloppy link copy must be 12-real F32/F16N/BF16"); return LQCD_EINVAL;
     }
     LQCD_LAUNCHED();
     return LQCD_OK;
+}
+
+lqcd_status link_update_dev(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *Us, lqcd_field *Uf, bool fast,
+                            cudaStream_t s)
+{
+    KernelTimer kt(K_LINK_UPDATE, s);
+    return fast ? launch_link_update<true>(U, P, c, Us, Uf, s) : launch_link_update<false>(U, P, c, Us, Uf, s);
 }
 
 lqcd_status momentum_refresh_dev(lqcd_field *P, uint32_t seed, uint32_t chain, uint32_t traj, cudaStream_t s)
@@ -712,6 +821,34 @@ const char *lqcd_version(void) { return "lqcd-gb300 0.1 (sm_103a)"; }
 
 uint64_t lqcd_launch_count(void) { return g_launches.load(); }
 
+lqcd_status lqcd_kernel_timers(int enable)
+{
+    LQCD_CUDA(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> lk(g_timer_mu);
+    drain_timers_locked();
+    for (int k = 0; k < K_NCLASS; k++) {
+        g_timer_ms[k] = 0;
+        g_timer_n[k] = 0;
+    }
+    g_timers_on.store(enable != 0);
+    return LQCD_OK;
+}
+
+lqcd_status lqcd_kernel_timer_read(const char *kernel_class, double *total_ms, uint64_t *launches)
+{
+    LQCD_REQUIRE(kernel_class, "kernel_timer_read: NULL class");
+    int cls = -1;
+    for (int k = 0; k < K_NCLASS; k++)
+        if (std::strcmp(kernel_class, k_class_names[k]) == 0) cls = k;
+    LQCD_REQUIRE(cls >= 0, "kernel_timer_read: unknown class '%s'", kernel_class);
+    LQCD_CUDA(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> lk(g_timer_mu);
+    drain_timers_locked();
+    if (total_ms) *total_ms = g_timer_ms[cls];
+    if (launches) *launches = g_timer_n[cls];
+    return LQCD_OK;
+}
+
 lqcd_status lqcd_set_allocator(lqcd_alloc_fn alloc, lqcd_free_fn free_fn, void *ctx)
 {
     LQCD_REQUIRE((alloc == nullptr) == (free_fn == nullptr), "allocator: alloc and free must both be set or both NULL");
@@ -726,6 +863,18 @@ lqcd_status lqcd_field_alloc(const lqcd_lattice *lat, lqcd_kind kind, lqcd_prec 
     LQCD_REQUIRE(out != nullptr, "out is NULL");
     LQCD_REQUIRE(valid_combo(kind, prec, link_recon), "invalid field combination kind=%d prec=%d recon=%d", (int)kind,
                  (int)prec, link_recon);
+    return field_alloc_impl(lat, kind, prec, link_recon, out);
+}
+
+} // extern "C"
+
+namespace lqcd {
+
+static lqcd_status field_alloc_impl(const lqcd_lattice *lat, lqcd_kind kind, lqcd_prec prec, int link_recon,
+                                    lqcd_field **out)
+{
+    LQCD_TRY(check_lattice(lat));
+    LQCD_REQUIRE(out != nullptr, "out is NULL");
     lqcd_field *f = new lqcd_field();
     f->lat = *lat;
     f->kind = kind;
@@ -756,6 +905,10 @@ lqcd_status lqcd_field_alloc(const lqcd_lattice *lat, lqcd_kind kind, lqcd_prec 
     *out = f;
     return LQCD_OK;
 }
+
+} // namespace lqcd
+
+extern "C" {
 
 lqcd_status lqcd_field_free(lqcd_field *f)
 {
@@ -867,7 +1020,7 @@ lqcd_status lqcd_link_update(lqcd_field *U, const lqcd_field *P, double c, lqcd_
     if (U_sloppy)
         LQCD_REQUIRE(U_sloppy->kind == LQCD_GAUGE && U_sloppy->recon == 12 && same_lattice(U->lat, U_sloppy->lat),
                      "link_update: U_sloppy must be a 12-real gauge field on the same lattice");
-    return link_update_dev(U, P, c, U_sloppy, (cudaStream_t)stream);
+    return link_update_dev(U, P, c, U_sloppy, nullptr, false, (cudaStream_t)stream);
 }
 
 lqcd_status lqcd_reunitarize(lqcd_field *U, double *max_dev_out, void *stream)

@@ -1,7 +1,9 @@
 // force.cu -- gauge (staple) force and two-flavour Wilson fermion force, each
 // projected onto su(3) and fused with the momentum update P <- P - coeff F
 // (paper Sec. 1: "force term calculation", "projection of fields",
-// "momentum updates").  One thread per link, FP64.
+// "momentum updates").  One thread per link.  The arithmetic is FP64, or FP32
+// (links read from the FP64 master field, spinors in FP32, the increment
+// accumulated into the FP64 momenta) for the mixed-precision trajectory.
 //
 // Both forces are written as f_a = Im Tr(lambda_a W) of one 3x3 matrix W per
 // link: for F = c TA(W) = c [(W - W^dag) - Tr(W - W^dag)/3] the Gell-Mann
@@ -34,7 +36,8 @@ __device__ __forceinline__ int step_cb(const Geo &g, const int c[4], int dir, in
     return coords_cb(g, d);
 }
 
-__device__ __forceinline__ void m3_acc(M3<double> &a, const M3<double> &b)
+template <typename R>
+__device__ __forceinline__ void m3_acc(M3<R> &a, const M3<R> &b)
 {
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -43,7 +46,8 @@ __device__ __forceinline__ void m3_acc(M3<double> &a, const M3<double> &b)
 }
 
 // staple sum A_mu(x): U_mu(x) A_mu(x) = sum of the 6 plaquettes starting with the link
-__global__ void __launch_bounds__(FB) gauge_force_kernel(MomRef P, GaugeRef<LQCD_F64> U, Geo g, double cf)
+template <typename R, lqcd_prec GP>
+__global__ void __launch_bounds__(FB) gauge_force_kernel(MomRef P, GaugeRef<GP> U, Geo g, double cf)
 {
     long t = blockIdx.x * (long)FB + threadIdx.x;
     if (t >= 8L * g.Vh) return;
@@ -54,67 +58,67 @@ __global__ void __launch_bounds__(FB) gauge_force_kernel(MomRef P, GaugeRef<LQCD
     int cpm[4] = {c[0], c[1], c[2], c[3]};
     cpm[mu] = (c[mu] + 1 == g.L[mu]) ? 0 : c[mu] + 1;
     int cb_pm = coords_cb(g, cpm);
-    M3<double> A;
+    M3<R> A;
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) A.e[i][j] = cx<double>(0, 0);
+        for (int j = 0; j < 3; j++) A.e[i][j] = cx<R>(0, 0);
     for (int nu = 0; nu < 4; nu++) {
         if (nu == mu) continue;
         int cb_pn = step_cb(g, c, nu, +1);
         int cb_mn = step_cb(g, c, nu, -1);
         int cb_pmmn = step_cb(g, cpm, nu, -1);
         // upper: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
-        M3<double> up = m3_mul_dag(U.load<double>(nu, 1 - par, cb_pm), U.load<double>(mu, 1 - par, cb_pn));
-        up = m3_mul_dag(up, U.load<double>(nu, par, cb));
+        M3<R> up = m3_mul_dag(U.template load<R>(nu, 1 - par, cb_pm), U.template load<R>(mu, 1 - par, cb_pn));
+        up = m3_mul_dag(up, U.template load<R>(nu, par, cb));
         m3_acc(A, up);
         // lower: U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu) = (U_mu(x-nu) U_nu(x+mu-nu))^dag U_nu(x-nu)
-        M3<double> lo = m3_mul(U.load<double>(mu, 1 - par, cb_mn), U.load<double>(nu, par, cb_pmmn));
-        lo = m3_dag_mul(lo, U.load<double>(nu, 1 - par, cb_mn));
+        M3<R> lo = m3_mul(U.template load<R>(mu, 1 - par, cb_mn), U.template load<R>(nu, par, cb_pmmn));
+        lo = m3_dag_mul(lo, U.template load<R>(nu, 1 - par, cb_mn));
         m3_acc(A, lo);
     }
-    M3<double> W = m3_mul(U.load<double>(mu, par, cb), A);
-    double gl[8];
+    M3<R> W = m3_mul(U.template load<R>(mu, par, cb), A);
+    R gl[8];
     im_tr_lambda(W, gl);
 #pragma unroll
-    for (int a = 0; a < 8; a++) P.d[P.idx(mu, par, a, cb)] -= cf * gl[a];
+    for (int a = 0; a < 8; a++) P.d[P.idx(mu, par, a, cb)] -= cf * (double)gl[a];
 }
 
 // Fermion force on link (x, mu), x of parity par:
 //   Q = sum_spin [s U A(x+mu)] [(1 - gamma_mu) B(x)]^dag - A(x) [s U (1 + gamma_mu) B(x+mu)]^dag
 // A = (A_e, A_o), B = (B_e, B_o) full-lattice spinors split by parity.
-template <int MU>
-__device__ __forceinline__ void fermion_force_link(MomRef &P, const GaugeRef<LQCD_F64> &U, const Geo &g, int par,
-                                                   int cb, const int c[4], const SpinorRef<LQCD_F64> (&A)[2],
-                                                   const SpinorRef<LQCD_F64> (&B)[2], double cf)
+template <int MU, typename R, lqcd_prec SP, lqcd_prec GP>
+__device__ __forceinline__ void fermion_force_link(MomRef &P, const GaugeRef<GP> &U, const Geo &g, int par,
+                                                   int cb, const int c[4], const SpinorRef<SP> (&A)[2],
+                                                   const SpinorRef<SP> (&B)[2], double cf)
 {
     int cy[4] = {c[0], c[1], c[2], c[3]};
     bool wrap = (c[MU] + 1 == g.L[MU]);
     cy[MU] = wrap ? 0 : c[MU] + 1;
     int cby = coords_cb(g, cy);
-    double s = (MU == 3 && wrap && g.t_bc < 0) ? -1.0 : 1.0;
-    M3<double> u = U.load<double>(MU, par, cb);
-    Sp<double> Ay = A[1 - par].load_rw<double>(cby);
-    Sp<double> Ax = A[par].load_rw<double>(cb);
-    Sp<double> Bx = B[par].load_rw<double>(cb);
-    Sp<double> By = B[1 - par].load_rw<double>(cby);
+    R s = (MU == 3 && wrap && g.t_bc < 0) ? (R)-1 : (R)1;
+    M3<R> u = U.template load<R>(MU, par, cb);
+    Sp<R> Ay = A[1 - par].template load_rw<R>(cby);
+    Sp<R> Ax = A[par].template load_rw<R>(cb);
+    Sp<R> Bx = B[par].template load_rw<R>(cb);
+    Sp<R> By = B[1 - par].template load_rw<R>(cby);
     // w1 = (1 - gamma) B(x) as a full spinor
-    Sp<double> w1 = sp_zero<double>();
+    Sp<R> w1 = sp_zero<R>();
     accumulate<MU, -1>(w1, project<MU, -1>(Bx));
     // w2 = s U (1 + gamma) B(y): project, multiply the two rows, reconstruct
-    Sp<double> w2 = sp_zero<double>();
+    Sp<R> w2 = sp_zero<R>();
     {
-        Hs<double> h = mul_link(u, project<MU, +1>(By));
+        Hs<R> h = mul_link(u, project<MU, +1>(By));
         accumulate<MU, +1>(w2, h);
     }
-    M3<double> Q;
+    M3<R> Q;
 #pragma unroll
     for (int a = 0; a < 3; a++)
 #pragma unroll
-        for (int b = 0; b < 3; b++) Q.e[a][b] = cx<double>(0, 0);
+        for (int b = 0; b < 3; b++) Q.e[a][b] = cx<R>(0, 0);
 #pragma unroll
     for (int sp = 0; sp < 4; sp++) {
-        Cx<double> v1[3];
+        Cx<R> v1[3];
 #pragma unroll
         for (int a = 0; a < 3; a++) v1[a] = u.e[a][0] * Ay.c[sp][0] + u.e[a][1] * Ay.c[sp][1] + u.e[a][2] * Ay.c[sp][2];
 #pragma unroll
@@ -123,16 +127,17 @@ __device__ __forceinline__ void fermion_force_link(MomRef &P, const GaugeRef<LQC
             for (int b = 0; b < 3; b++)
                 Q.e[a][b] = Q.e[a][b] + s * (v1[a] * conj(w1.c[sp][b]) - Ax.c[sp][a] * conj(w2.c[sp][b]));
     }
-    double gl[8];
+    R gl[8];
     im_tr_lambda(Q, gl);
     // P -= coeff * f with f_a = -kappa^2 g_a
 #pragma unroll
-    for (int a = 0; a < 8; a++) P.d[P.idx(MU, par, a, cb)] += cf * gl[a];
+    for (int a = 0; a < 8; a++) P.d[P.idx(MU, par, a, cb)] += cf * (double)gl[a];
 }
 
-__global__ void __launch_bounds__(FB) fermion_force_kernel(MomRef P, GaugeRef<LQCD_F64> U, Geo g,
-                                                           SpinorRef<LQCD_F64> Ae, SpinorRef<LQCD_F64> Ao,
-                                                           SpinorRef<LQCD_F64> Be, SpinorRef<LQCD_F64> Bo, double cf)
+template <typename R, lqcd_prec SP, lqcd_prec GP>
+__global__ void __launch_bounds__(FB) fermion_force_kernel(MomRef P, GaugeRef<GP> U, Geo g, SpinorRef<SP> Ae,
+                                                           SpinorRef<SP> Ao, SpinorRef<SP> Be, SpinorRef<SP> Bo,
+                                                           double cf)
 {
     long t = blockIdx.x * (long)FB + threadIdx.x;
     if (t >= 8L * g.Vh) return;
@@ -140,36 +145,59 @@ __global__ void __launch_bounds__(FB) fermion_force_kernel(MomRef P, GaugeRef<LQ
     link_of_thread(t, g.Vh, mu, par, cb);
     int c[4];
     cb_coords(g, cb, par, c);
-    const SpinorRef<LQCD_F64> A[2] = {Ae, Ao};
-    const SpinorRef<LQCD_F64> B[2] = {Be, Bo};
+    const SpinorRef<SP> A[2] = {Ae, Ao};
+    const SpinorRef<SP> B[2] = {Be, Bo};
     switch (mu) {
-    case 0: fermion_force_link<0>(P, U, g, par, cb, c, A, B, cf); break;
-    case 1: fermion_force_link<1>(P, U, g, par, cb, c, A, B, cf); break;
-    case 2: fermion_force_link<2>(P, U, g, par, cb, c, A, B, cf); break;
-    default: fermion_force_link<3>(P, U, g, par, cb, c, A, B, cf); break;
+    case 0: fermion_force_link<0, R, SP, GP>(P, U, g, par, cb, c, A, B, cf); break;
+    case 1: fermion_force_link<1, R, SP, GP>(P, U, g, par, cb, c, A, B, cf); break;
+    case 2: fermion_force_link<2, R, SP, GP>(P, U, g, par, cb, c, A, B, cf); break;
+    default: fermion_force_link<3, R, SP, GP>(P, U, g, par, cb, c, A, B, cf); break;
     }
 }
 
-lqcd_status gauge_force_dev(lqcd_field *P, const lqcd_field *U, double beta, double coeff, cudaStream_t s)
+// Uf: the FP32 12-real link copy, used (and required) when arith is F32
+lqcd_status gauge_force_dev(lqcd_field *P, const lqcd_field *U, const lqcd_field *Uf, double beta, double coeff,
+                            lqcd_prec arith, cudaStream_t s)
 {
     Geo g = make_geo(U->lat);
-    gauge_force_kernel<<<nblocks_for(8L * g.Vh, FB), FB, 0, s>>>(mom_ref(P), gauge_ref<LQCD_F64>(U), g,
-                                                                   coeff * beta / 6.0);
+    KernelTimer kt(K_GAUGE_FORCE, s);
+    int nb = nblocks_for(8L * g.Vh, FB);
+    if (arith == LQCD_F32)
+        gauge_force_kernel<float, LQCD_F32><<<nb, FB, 0, s>>>(mom_ref(P), gauge_ref<LQCD_F32>(Uf), g, coeff * beta / 6.0);
+    else
+        gauge_force_kernel<double, LQCD_F64><<<nb, FB, 0, s>>>(mom_ref(P), gauge_ref<LQCD_F64>(U), g, coeff * beta / 6.0);
     LQCD_LAUNCHED();
     return LQCD_OK;
 }
 
-// A_o = Doe X_e, Y_e = Mhat X_e = X_e - kappa^2 Deo A_o, B_o = Doe^dag-hop Y_e, then the link kernel
-lqcd_status fermion_force_dev(lqcd_field *P, const lqcd_field *U, const lqcd_field *X, double kappa, double coeff,
-                              lqcd_field *Ao, lqcd_field *Ye, lqcd_field *Bo, cudaStream_t s)
+// A_o = Doe X_e, Y_e = Mhat X_e = X_e - kappa^2 Deo A_o, B_o = Doe^dag-hop Y_e, then the link kernel.
+// The temporaries' precision (F64 or F32) sets the arithmetic; for F32 the
+// links come from the FP32 12-real copy Uf and X is rounded into Xc first.
+lqcd_status fermion_force_dev(lqcd_field *P, const lqcd_field *U, const lqcd_field *Uf, const lqcd_field *X,
+                              double kappa, double coeff, lqcd_field *Ao, lqcd_field *Ye, lqcd_field *Bo, lqcd_field *Xc,
+                              cudaStream_t s)
 {
-    LQCD_TRY(dslash_plain(Ao, U, X, 0, nullptr, s));
-    LQCD_TRY(dslash_xpay(Ye, U, Ao, 0, X, -kappa * kappa, nullptr, nullptr, s));
-    LQCD_TRY(dslash_plain(Bo, U, Ye, 1, nullptr, s));
+    const lqcd_field *Xa = X;
+    const lqcd_field *L = Ao->prec == LQCD_F32 ? Uf : U;
+    if (Ao->prec != X->prec) {
+        LQCD_TRY(lqcd_field_copy(Xc, X, s));
+        Xa = Xc;
+    }
+    LQCD_TRY(dslash_plain(Ao, L, Xa, 0, nullptr, s));
+    LQCD_TRY(dslash_xpay(Ye, L, Ao, 0, Xa, -kappa * kappa, nullptr, nullptr, s));
+    LQCD_TRY(dslash_plain(Bo, L, Ye, 1, nullptr, s));
     Geo g = make_geo(U->lat);
-    fermion_force_kernel<<<nblocks_for(8L * g.Vh, FB), FB, 0, s>>>(
-        mom_ref(P), gauge_ref<LQCD_F64>(U), g, spinor_ref<LQCD_F64>(X), spinor_ref<LQCD_F64>(Ao),
-        spinor_ref<LQCD_F64>(Ye), spinor_ref<LQCD_F64>(Bo), coeff * kappa * kappa);
+    KernelTimer kt(K_FERMION_FORCE, s);
+    int nb = nblocks_for(8L * g.Vh, FB);
+    double cf = coeff * kappa * kappa;
+    if (Ao->prec == LQCD_F32)
+        fermion_force_kernel<float, LQCD_F32, LQCD_F32><<<nb, FB, 0, s>>>(
+            mom_ref(P), gauge_ref<LQCD_F32>(Uf), g, spinor_ref<LQCD_F32>(Xa), spinor_ref<LQCD_F32>(Ao),
+            spinor_ref<LQCD_F32>(Ye), spinor_ref<LQCD_F32>(Bo), cf);
+    else
+        fermion_force_kernel<double, LQCD_F64, LQCD_F64><<<nb, FB, 0, s>>>(
+            mom_ref(P), gauge_ref<LQCD_F64>(U), g, spinor_ref<LQCD_F64>(Xa), spinor_ref<LQCD_F64>(Ao),
+            spinor_ref<LQCD_F64>(Ye), spinor_ref<LQCD_F64>(Bo), cf);
     LQCD_LAUNCHED();
     return LQCD_OK;
 }
@@ -180,29 +208,56 @@ using namespace lqcd;
 
 extern "C" {
 
-lqcd_status lqcd_gauge_force(lqcd_field *P, const lqcd_field *U, double beta, double coeff, void *stream)
+lqcd_status lqcd_gauge_force_ex(lqcd_field *P, const lqcd_field *U, double beta, double coeff, lqcd_prec arith,
+                                void *stream)
 {
     LQCD_REQUIRE(P && U && P->kind == LQCD_MOMENTUM && U->kind == LQCD_GAUGE && U->prec == LQCD_F64,
                  "gauge_force needs a momentum field and an F64 gauge field");
     LQCD_REQUIRE(same_lattice(P->lat, U->lat), "gauge_force: lattices differ");
-    return gauge_force_dev(P, U, beta, coeff, (cudaStream_t)stream);
+    LQCD_REQUIRE(arith == LQCD_F64 || arith == LQCD_F32, "gauge_force: arithmetic must be F64 or F32");
+    cudaStream_t s = (cudaStream_t)stream;
+    FieldPtr Uf;
+    if (arith == LQCD_F32) {
+        LQCD_TRY(lqcd_field_alloc(&U->lat, LQCD_GAUGE, LQCD_F32, 12, &Uf.f));
+        LQCD_TRY(lqcd_field_copy(Uf.f, U, s));
+    }
+    LQCD_TRY(gauge_force_dev(P, U, Uf.f, beta, coeff, arith, s));
+    LQCD_CUDA(cudaStreamSynchronize(s)); // the temporary copy is freed on return
+    return LQCD_OK;
 }
 
-lqcd_status lqcd_fermion_force(lqcd_field *P, const lqcd_field *U, const lqcd_field *X_e, double kappa, double coeff,
-                               void *stream)
+lqcd_status lqcd_gauge_force(lqcd_field *P, const lqcd_field *U, double beta, double coeff, void *stream)
+{
+    return lqcd_gauge_force_ex(P, U, beta, coeff, LQCD_F64, stream);
+}
+
+lqcd_status lqcd_fermion_force_ex(lqcd_field *P, const lqcd_field *U, const lqcd_field *X_e, double kappa,
+                                  double coeff, lqcd_prec arith, void *stream)
 {
     LQCD_REQUIRE(P && U && X_e && P->kind == LQCD_MOMENTUM && U->kind == LQCD_GAUGE && U->prec == LQCD_F64,
                  "fermion_force needs a momentum field and an F64 gauge field");
     LQCD_REQUIRE(X_e->kind == LQCD_SPINOR_EVEN && X_e->prec == LQCD_F64, "fermion_force: X_e must be EVEN F64");
     LQCD_REQUIRE(same_lattice(P->lat, U->lat) && same_lattice(X_e->lat, U->lat), "fermion_force: lattices differ");
-    FieldPtr Ao, Ye, Bo;
-    LQCD_TRY(lqcd_field_alloc(&U->lat, LQCD_SPINOR_ODD, LQCD_F64, 0, &Ao.f));
-    LQCD_TRY(lqcd_field_alloc(&U->lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &Ye.f));
-    LQCD_TRY(lqcd_field_alloc(&U->lat, LQCD_SPINOR_ODD, LQCD_F64, 0, &Bo.f));
+    LQCD_REQUIRE(arith == LQCD_F64 || arith == LQCD_F32, "fermion_force: arithmetic must be F64 or F32");
+    FieldPtr Ao, Ye, Bo, Xc, Uf;
     cudaStream_t s = (cudaStream_t)stream;
-    LQCD_TRY(fermion_force_dev(P, U, X_e, kappa, coeff, Ao.f, Ye.f, Bo.f, s));
+    LQCD_TRY(lqcd_field_alloc(&U->lat, LQCD_SPINOR_ODD, arith, 0, &Ao.f));
+    LQCD_TRY(lqcd_field_alloc(&U->lat, LQCD_SPINOR_EVEN, arith, 0, &Ye.f));
+    LQCD_TRY(lqcd_field_alloc(&U->lat, LQCD_SPINOR_ODD, arith, 0, &Bo.f));
+    if (arith != LQCD_F64) {
+        LQCD_TRY(lqcd_field_alloc(&U->lat, LQCD_SPINOR_EVEN, arith, 0, &Xc.f));
+        LQCD_TRY(lqcd_field_alloc(&U->lat, LQCD_GAUGE, LQCD_F32, 12, &Uf.f));
+        LQCD_TRY(lqcd_field_copy(Uf.f, U, s));
+    }
+    LQCD_TRY(fermion_force_dev(P, U, Uf.f, X_e, kappa, coeff, Ao.f, Ye.f, Bo.f, Xc.f, s));
     LQCD_CUDA(cudaStreamSynchronize(s)); // temporaries are freed on return
     return LQCD_OK;
+}
+
+lqcd_status lqcd_fermion_force(lqcd_field *P, const lqcd_field *U, const lqcd_field *X_e, double kappa, double coeff,
+                               void *stream)
+{
+    return lqcd_fermion_force_ex(P, U, X_e, kappa, coeff, LQCD_F64, stream);
 }
 
 } // extern "C"

@@ -17,12 +17,15 @@ namespace lqcd {
 lqcd_status plaquette_sum(const lqcd_field *U, double *dst_dev, DevBuf &part, cudaStream_t s);
 lqcd_status kinetic_sum(const lqcd_field *P, double *dst_dev, DevBuf &part, cudaStream_t s);
 lqcd_status reunitarize_dev(lqcd_field *U, double *dst_dev, DevBuf &part, cudaStream_t s);
-lqcd_status link_update_dev(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *Us, cudaStream_t s);
+lqcd_status link_update_dev(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *Us, lqcd_field *Uf, bool fast,
+                            cudaStream_t s);
 lqcd_status momentum_refresh_dev(lqcd_field *P, uint32_t seed, uint32_t chain, uint32_t traj, cudaStream_t s);
 lqcd_status eta_refresh_dev(lqcd_field *E, uint32_t seed, uint32_t chain, uint32_t traj, cudaStream_t s);
-lqcd_status gauge_force_dev(lqcd_field *P, const lqcd_field *U, double beta, double coeff, cudaStream_t s);
-lqcd_status fermion_force_dev(lqcd_field *P, const lqcd_field *U, const lqcd_field *X, double kappa, double coeff,
-                              lqcd_field *Ao, lqcd_field *Ye, lqcd_field *Bo, cudaStream_t s);
+lqcd_status gauge_force_dev(lqcd_field *P, const lqcd_field *U, const lqcd_field *Uf, double beta, double coeff,
+                            lqcd_prec arith, cudaStream_t s);
+lqcd_status fermion_force_dev(lqcd_field *P, const lqcd_field *U, const lqcd_field *Uf, const lqcd_field *X,
+                              double kappa, double coeff, lqcd_field *Ao, lqcd_field *Ye, lqcd_field *Bo, lqcd_field *Xc,
+                              cudaStream_t s);
 
 constexpr double OMELYAN_LAMBDA = 0.1931833275037836;
 
@@ -41,6 +44,8 @@ struct lqcd_hmc_state {
     lqcd_field *U = nullptr; // borrowed
     uint32_t seed = 0, chain = 0, traj = 0;
     FieldPtr P, eta, phi, X, Ao, Ye, Bo, Ubak, Us;
+    FieldPtr Ao32, Ye32, Bo32, X32; // FP32 fermion-force temporaries (allocated on first use)
+    FieldPtr Uf;                    // FP32 12-real link copy for the FP32 molecular dynamics
     CgWorkspace ws;
     DevBuf part, scal;
     double H0 = 0;
@@ -62,12 +67,18 @@ static lqcd_status check_params(const lqcd_hmc_params *p)
         LQCD_REQUIRE(p->cg.sloppy == LQCD_F64 || (p->cg.delta > 0 && p->cg.delta < 1),
                      "hmc: cg delta must lie in (0, 1) for a mixed solve");
     }
+    LQCD_REQUIRE(p->force_prec == LQCD_F64 || p->force_prec == LQCD_F32, "hmc: force_prec must be F64 or F32");
     return LQCD_OK;
 }
 
-// sloppy link copy matching the solver precision (NULL for FP64)
+// sloppy link copy matching the solver precision (NULL for FP64), and the FP32
+// link copy of the FP32 molecular dynamics
 static lqcd_status ensure_sloppy(lqcd_hmc_state *st, const lqcd_hmc_params *p, cudaStream_t s)
 {
+    if (p->force_prec == LQCD_F32) {
+        if (!st->Uf.f) LQCD_TRY(lqcd_field_alloc(&st->U->lat, LQCD_GAUGE, LQCD_F32, 12, &st->Uf.f));
+        LQCD_TRY(lqcd_field_copy(st->Uf.f, st->U, s));
+    }
     if (p->n_flavors == 0 || p->cg.sloppy == LQCD_F64) return LQCD_OK;
     if (st->Us.f && st->Us.f->prec != p->cg.sloppy) {
         lqcd_field_free(st->Us.f);
@@ -96,20 +107,39 @@ static lqcd_status solve(lqcd_hmc_state *st, const lqcd_hmc_params *p, cudaStrea
     return rc;
 }
 
+static lqcd_status ensure_f32_temps(lqcd_hmc_state *st)
+{
+    if (st->Ao32.f) return LQCD_OK;
+    const lqcd_lattice &lat = st->U->lat;
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F32, 0, &st->Ao32.f));
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F32, 0, &st->Ye32.f));
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F32, 0, &st->Bo32.f));
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F32, 0, &st->X32.f));
+    return LQCD_OK;
+}
+
 // P <- P - c F(U)
 static lqcd_status kick(lqcd_hmc_state *st, const lqcd_hmc_params *p, double c, cudaStream_t s)
 {
-    LQCD_TRY(gauge_force_dev(st->P.f, st->U, p->beta, c, s));
+    LQCD_TRY(gauge_force_dev(st->P.f, st->U, st->Uf.f, p->beta, c, p->force_prec, s));
     if (p->n_flavors == 2) {
         LQCD_TRY(solve(st, p, s));
-        LQCD_TRY(fermion_force_dev(st->P.f, st->U, st->X.f, p->kappa, c, st->Ao.f, st->Ye.f, st->Bo.f, s));
+        if (p->force_prec == LQCD_F32) {
+            LQCD_TRY(ensure_f32_temps(st));
+            LQCD_TRY(fermion_force_dev(st->P.f, st->U, st->Uf.f, st->X.f, p->kappa, c, st->Ao32.f, st->Ye32.f,
+                                       st->Bo32.f, st->X32.f, s));
+        } else {
+            LQCD_TRY(fermion_force_dev(st->P.f, st->U, nullptr, st->X.f, p->kappa, c, st->Ao.f, st->Ye.f, st->Bo.f,
+                                       nullptr, s));
+        }
     }
     return LQCD_OK;
 }
 
 static lqcd_status drift(lqcd_hmc_state *st, const lqcd_hmc_params *p, double c, cudaStream_t s)
 {
-    return link_update_dev(st->U, st->P.f, c, sloppy_links(st, p), s);
+    bool fast = p->force_prec == LQCD_F32;
+    return link_update_dev(st->U, st->P.f, c, sloppy_links(st, p), fast ? st->Uf.f : nullptr, fast, s);
 }
 
 // scalars[0] = plaquette sum, [1] = sum p^2, [2] = fermion term

@@ -70,6 +70,27 @@ extern std::atomic<uint64_t> g_launches;
         LQCD_CUDA(cudaGetLastError());                                                                     \
     } while (0)
 
+// optional per-class kernel timing with CUDA events on the launching stream
+enum KernelClass {
+    K_DSLASH_F64 = 0,
+    K_DSLASH_F32,
+    K_DSLASH_F16N,
+    K_DSLASH_BF16,
+    K_DSLASH_DF64, // float-float arithmetic (internal storage precision)
+    K_GAUGE_FORCE,
+    K_FERMION_FORCE,
+    K_LINK_UPDATE,
+    K_NCLASS
+};
+struct KernelTimer { // RAII: events around the launches made while it lives
+    int cls;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    KernelTimer(int cls, cudaStream_t s);
+    ~KernelTimer();
+};
+inline int dslash_class(lqcd_prec p) { return K_DSLASH_F64 + (int)p; }
+
 // ------------------------------------------------------------------ memory
 
 // Allocation through the hook set by lqcd_set_allocator (cudaMalloc default).
@@ -590,11 +611,15 @@ struct GaugeRef<LQCD_F32> {
         reconstruct_row2(u);
         return u;
     }
-    __device__ __forceinline__ void store(int mu, int par, int cb, const M3<double> &u) const
+    template <typename R>
+    __device__ __forceinline__ void store(int mu, int par, int cb, const M3<R> &u) const
     {
-        d[idx(mu, par, 0, cb)] = make_float4(u.e[0][0].re, u.e[0][0].im, u.e[0][1].re, u.e[0][1].im);
-        d[idx(mu, par, 1, cb)] = make_float4(u.e[0][2].re, u.e[0][2].im, u.e[1][0].re, u.e[1][0].im);
-        d[idx(mu, par, 2, cb)] = make_float4(u.e[1][1].re, u.e[1][1].im, u.e[1][2].re, u.e[1][2].im);
+        d[idx(mu, par, 0, cb)] = make_float4((float)u.e[0][0].re, (float)u.e[0][0].im, (float)u.e[0][1].re,
+                                             (float)u.e[0][1].im);
+        d[idx(mu, par, 1, cb)] = make_float4((float)u.e[0][2].re, (float)u.e[0][2].im, (float)u.e[1][0].re,
+                                             (float)u.e[1][0].im);
+        d[idx(mu, par, 2, cb)] = make_float4((float)u.e[1][1].re, (float)u.e[1][1].im, (float)u.e[1][2].re,
+                                             (float)u.e[1][2].im);
     }
 };
 
@@ -607,7 +632,8 @@ struct GaugeRef16 {
         return ((size_t)((mu * 2 + par) * 3 + k)) * Vh + cb;
     }
     __device__ __forceinline__ float2 un(uint32_t w) const { return BF ? unpack_b2(w) : unpack_h2(w); }
-    __device__ __forceinline__ uint32_t pk(double a, double b) const
+    template <typename R>
+    __device__ __forceinline__ uint32_t pk(R a, R b) const
     {
         return BF ? pack_b2((float)a, (float)b) : pack_h2((float)a, (float)b);
     }
@@ -626,7 +652,8 @@ struct GaugeRef16 {
         reconstruct_row2(u);
         return u;
     }
-    __device__ __forceinline__ void store(int mu, int par, int cb, const M3<double> &u) const
+    template <typename R>
+    __device__ __forceinline__ void store(int mu, int par, int cb, const M3<R> &u) const
     {
         d[idx(mu, par, 0, cb)] = make_uint2(pk(u.e[0][0].re, u.e[0][0].im), pk(u.e[0][1].re, u.e[0][1].im));
         d[idx(mu, par, 1, cb)] = make_uint2(pk(u.e[0][2].re, u.e[0][2].im), pk(u.e[1][0].re, u.e[1][0].im));
@@ -732,6 +759,7 @@ inline int nblocks_for(long n, int block) { return (int)((n + block - 1) / block
 lqcd_status dslash_dispatch(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int dagger,
                             const lqcd_field *x, double a, double b, double *partials, cudaStream_t s);
 lqcd_status field_alloc_like(const lqcd_field *like, lqcd_kind kind, lqcd_prec prec, int recon, lqcd_field **out);
+lqcd_status field_alloc_df(const lqcd_lattice *lat, lqcd_kind kind, lqcd_field **out);
 lqcd_status mhat_apply(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, double kappa, int dagger,
                        lqcd_field *tmp_odd, double *partials, cudaStream_t s);
 

@@ -8,27 +8,30 @@
 namespace lqcd {
 
 // H = sum_a p_a lambda_a / 2 for the 8 coefficients p (Gell-Mann lambda_1..8).
-__device__ __forceinline__ M3<double> herm_from_coeffs(const double p[8], double scale)
+template <typename R>
+__device__ __forceinline__ M3<R> herm_from_coeffs(const R p[8], R scale)
 {
-    const double inv_sqrt3 = 0.57735026918962576451;
-    M3<double> h;
-    double s = 0.5 * scale;
-    h.e[0][0] = cx<double>(s * (p[2] + p[7] * inv_sqrt3), 0.0);
-    h.e[1][1] = cx<double>(s * (-p[2] + p[7] * inv_sqrt3), 0.0);
-    h.e[2][2] = cx<double>(-2.0 * s * p[7] * inv_sqrt3, 0.0);
-    h.e[0][1] = cx<double>(s * p[0], -s * p[1]);
-    h.e[1][0] = cx<double>(s * p[0], s * p[1]);
-    h.e[0][2] = cx<double>(s * p[3], -s * p[4]);
-    h.e[2][0] = cx<double>(s * p[3], s * p[4]);
-    h.e[1][2] = cx<double>(s * p[5], -s * p[6]);
-    h.e[2][1] = cx<double>(s * p[5], s * p[6]);
+    const R inv_sqrt3 = (R)0.57735026918962576451;
+    const R z = (R)0;
+    M3<R> h;
+    R s = (R)0.5 * scale;
+    h.e[0][0] = cx<R>(s * (p[2] + p[7] * inv_sqrt3), z);
+    h.e[1][1] = cx<R>(s * (-p[2] + p[7] * inv_sqrt3), z);
+    h.e[2][2] = cx<R>((R)-2 * s * p[7] * inv_sqrt3, z);
+    h.e[0][1] = cx<R>(s * p[0], -s * p[1]);
+    h.e[1][0] = cx<R>(s * p[0], s * p[1]);
+    h.e[0][2] = cx<R>(s * p[3], -s * p[4]);
+    h.e[2][0] = cx<R>(s * p[3], s * p[4]);
+    h.e[1][2] = cx<R>(s * p[5], -s * p[6]);
+    h.e[2][1] = cx<R>(s * p[5], s * p[6]);
     return h;
 }
 
 // g_a = Im Tr(lambda_a W) for a = 1..8.
-__device__ __forceinline__ void im_tr_lambda(const M3<double> &W, double g[8])
+template <typename R>
+__device__ __forceinline__ void im_tr_lambda(const M3<R> &W, R g[8])
 {
-    const double inv_sqrt3 = 0.57735026918962576451;
+    const R inv_sqrt3 = (R)0.57735026918962576451;
     g[0] = W.e[1][0].im + W.e[0][1].im;
     g[1] = W.e[0][1].re - W.e[1][0].re;
     g[2] = W.e[0][0].im - W.e[1][1].im;
@@ -36,7 +39,7 @@ __device__ __forceinline__ void im_tr_lambda(const M3<double> &W, double g[8])
     g[4] = W.e[0][2].re - W.e[2][0].re;
     g[5] = W.e[2][1].im + W.e[1][2].im;
     g[6] = W.e[1][2].re - W.e[2][1].re;
-    g[7] = (W.e[0][0].im + W.e[1][1].im - 2.0 * W.e[2][2].im) * inv_sqrt3;
+    g[7] = (W.e[0][0].im + W.e[1][1].im - (R)2 * W.e[2][2].im) * inv_sqrt3;
 }
 
 // exp(i Q) for Hermitian traceless Q by the Cayley-Hamilton theorem
@@ -49,52 +52,55 @@ __device__ __forceinline__ void im_tr_lambda(const M3<double> &W, double g[8])
 //   h1 = 2u e^{2iu} - e^{-iu} [2u cos w - i (3u^2 - w^2) xi0(w)]
 //   h2 = e^{2iu} - e^{-iu} [cos w + 3iu xi0(w)],   xi0(w) = sin(w)/w,
 // and f_j(-c0) = (-1)^j conj(f_j(c0)).
-__device__ __forceinline__ M3<double> expi_cayley_hamilton(const M3<double> &Q)
+template <typename R>
+__device__ __forceinline__ M3<R> expi_cayley_hamilton(const M3<R> &Q)
 {
-    M3<double> Q2 = m3_mul(Q, Q);
-    double c1 = 0.5 * (Q2.e[0][0].re + Q2.e[1][1].re + Q2.e[2][2].re);
+    const R one = (R)1, half = (R)0.5, third = (R)1 / (R)3;
+    M3<R> Q2 = m3_mul(Q, Q);
+    R c1 = half * (Q2.e[0][0].re + Q2.e[1][1].re + Q2.e[2][2].re);
     // det Q = Tr Q^3 / 3 (real for Hermitian Q)
-    double c0 = 0.0;
+    R c0 = (R)0;
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int k = 0; k < 3; k++) c0 += (Q.e[i][k] * Q2.e[k][i]).re;
-    c0 *= (1.0 / 3.0);
-    M3<double> r;
-    if (c1 < 1e-28) { // Q ~ 0: I + iQ - Q^2/2 is exact to double precision
+    c0 *= third;
+    M3<R> r;
+    // Q ~ 0: I + iQ - Q^2/2 is exact to working precision
+    if (c1 < (sizeof(R) == 8 ? (R)1e-28 : (R)1e-12)) {
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
             for (int j = 0; j < 3; j++)
-                r.e[i][j] = cx<double>((i == j ? 1.0 : 0.0) - 0.5 * Q2.e[i][j].re - Q.e[i][j].im,
-                                       Q.e[i][j].re - 0.5 * Q2.e[i][j].im);
+                r.e[i][j] = cx<R>((i == j ? one : (R)0) - half * Q2.e[i][j].re - Q.e[i][j].im,
+                                  Q.e[i][j].re - half * Q2.e[i][j].im);
         return r;
     }
-    bool neg = c0 < 0.0;
-    double ac0 = fabs(c0);
-    double c0max = 2.0 * c1 / 3.0 * sqrt(c1 / 3.0);
-    double ratio = fmin(ac0 / c0max, 1.0);
-    double theta = acos(ratio);
-    double u = sqrt(c1 / 3.0) * cos(theta / 3.0);
-    double w = sqrt(c1) * sin(theta / 3.0);
-    double u2 = u * u, w2 = w * w;
-    double cw = cos(w);
-    double xi0;
-    if (fabs(w) < 0.05) {
-        xi0 = 1.0 - w2 / 6.0 * (1.0 - w2 / 20.0 * (1.0 - w2 / 42.0 * (1.0 - w2 / 72.0)));
+    bool neg = c0 < (R)0;
+    R ac0 = fabs(c0);
+    R c0max = (R)2 * c1 * third * sqrt(c1 * third);
+    R ratio = fmin(ac0 / c0max, one);
+    R theta = acos(ratio);
+    R u = sqrt(c1 * third) * cos(theta * third);
+    R w = sqrt(c1) * sin(theta * third);
+    R u2 = u * u, w2 = w * w;
+    R cw = cos(w);
+    R xi0;
+    if (fabs(w) < (R)0.05) {
+        xi0 = one - w2 / (R)6 * (one - w2 / (R)20 * (one - w2 / (R)42 * (one - w2 / (R)72)));
     } else {
         xi0 = sin(w) / w;
     }
-    double s2u, c2u, su, cu;
-    sincos(2.0 * u, &s2u, &c2u);
+    R s2u, c2u, su, cu;
+    sincos((R)2 * u, &s2u, &c2u);
     sincos(u, &su, &cu);
-    Cx<double> e2iu = cx<double>(c2u, s2u);
-    Cx<double> emiu = cx<double>(cu, -su);
-    Cx<double> h0 = (u2 - w2) * e2iu + emiu * cx<double>(8.0 * u2 * cw, 2.0 * u * (3.0 * u2 + w2) * xi0);
-    Cx<double> h1 = (2.0 * u) * e2iu - emiu * cx<double>(2.0 * u * cw, -(3.0 * u2 - w2) * xi0);
-    Cx<double> h2 = e2iu - emiu * cx<double>(cw, 3.0 * u * xi0);
-    double inv = 1.0 / (9.0 * u2 - w2);
-    Cx<double> f0 = inv * h0, f1 = inv * h1, f2 = inv * h2;
+    Cx<R> e2iu = cx<R>(c2u, s2u);
+    Cx<R> emiu = cx<R>(cu, -su);
+    Cx<R> h0 = (u2 - w2) * e2iu + emiu * cx<R>((R)8 * u2 * cw, (R)2 * u * ((R)3 * u2 + w2) * xi0);
+    Cx<R> h1 = ((R)2 * u) * e2iu - emiu * cx<R>((R)2 * u * cw, -((R)3 * u2 - w2) * xi0);
+    Cx<R> h2 = e2iu - emiu * cx<R>(cw, (R)3 * u * xi0);
+    R inv = one / ((R)9 * u2 - w2);
+    Cx<R> f0 = inv * h0, f1 = inv * h1, f2 = inv * h2;
     if (neg) {
         f0 = conj(f0);
         f1 = -conj(f1);
@@ -104,11 +110,24 @@ __device__ __forceinline__ M3<double> expi_cayley_hamilton(const M3<double> &Q)
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            Cx<double> v = f1 * Q.e[i][j] + f2 * Q2.e[i][j];
+            Cx<R> v = f1 * Q.e[i][j] + f2 * Q2.e[i][j];
             if (i == j) v = v + f0;
             r.e[i][j] = v;
         }
     return r;
+}
+
+// Gram-Schmidt of rows 0 and 1, row 2 = conj(row0 x row1): the nearest
+// special-unitary matrix in the sense used by the reunitarization
+__device__ __forceinline__ void reunit_rows(M3<double> &u)
+{
+    double n0 = rsqrt(norm2(u.e[0][0]) + norm2(u.e[0][1]) + norm2(u.e[0][2]));
+    for (int b = 0; b < 3; b++) u.e[0][b] = n0 * u.e[0][b];
+    Cx<double> ov = cmul_conj(u.e[0][0], u.e[1][0]) + cmul_conj(u.e[0][1], u.e[1][1]) + cmul_conj(u.e[0][2], u.e[1][2]);
+    for (int b = 0; b < 3; b++) u.e[1][b] = u.e[1][b] - ov * u.e[0][b];
+    double n1 = rsqrt(norm2(u.e[1][0]) + norm2(u.e[1][1]) + norm2(u.e[1][2]));
+    for (int b = 0; b < 3; b++) u.e[1][b] = n1 * u.e[1][b];
+    reconstruct_row2(u);
 }
 
 // ------------------------------------------------------------------ Philox4x32-10

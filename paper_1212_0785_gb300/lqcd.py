@@ -57,7 +57,8 @@ class CgInfo(ctypes.Structure):
 class HmcParams(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("kappa", ctypes.c_double), ("tau", ctypes.c_double),
                 ("nsteps", ctypes.c_int), ("integrator", ctypes.c_int), ("n_flavors", ctypes.c_int),
-                ("cg", CgParams), ("reunitarize", ctypes.c_int), ("metropolis", ctypes.c_int)]
+                ("cg", CgParams), ("reunitarize", ctypes.c_int), ("metropolis", ctypes.c_int),
+                ("force_prec", ctypes.c_int)]
 
 
 class TrajInfo(ctypes.Structure):
@@ -84,6 +85,8 @@ _SIGS = {
     "lqcd_version": (ctypes.c_char_p, []),
     "lqcd_launch_count": (ctypes.c_uint64, []),
     "lqcd_set_allocator": (_i, [ALLOC_FN, FREE_FN, _vp]),
+    "lqcd_kernel_timers": (_i, [_i]),
+    "lqcd_kernel_timer_read": (_i, [ctypes.c_char_p, _dp, ctypes.POINTER(ctypes.c_uint64)]),
     "lqcd_field_alloc": (_i, [ctypes.POINTER(Lattice), _i, _i, _i, _pp]),
     "lqcd_field_free": (_i, [_vp]),
     "lqcd_field_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
@@ -99,7 +102,9 @@ _SIGS = {
     "lqcd_mhat": (_i, [_vp, _vp, _vp, _d, _i, _vp]),
     "lqcd_cg_solve": (_i, [_vp, _vp, _vp, _vp, _d, ctypes.POINTER(CgParams), ctypes.POINTER(CgInfo), _vp]),
     "lqcd_gauge_force": (_i, [_vp, _vp, _d, _d, _vp]),
+    "lqcd_gauge_force_ex": (_i, [_vp, _vp, _d, _d, _i, _vp]),
     "lqcd_fermion_force": (_i, [_vp, _vp, _vp, _d, _d, _vp]),
+    "lqcd_fermion_force_ex": (_i, [_vp, _vp, _vp, _d, _d, _i, _vp]),
     "lqcd_link_update": (_i, [_vp, _vp, _d, _vp, _vp]),
     "lqcd_reunitarize": (_i, [_vp, _dp, _vp]),
     "lqcd_plaquette": (_i, [_vp, _dp, _vp]),
@@ -158,6 +163,24 @@ def version() -> str:
 
 def launch_count() -> int:
     return int(lib().lqcd_launch_count())
+
+
+KERNEL_CLASSES = ("dslash_f64", "dslash_f32", "dslash_f16n", "dslash_bf16", "dslash_df64", "gauge_force",
+                  "fermion_force", "link_update")
+
+
+def kernel_timers(enable: bool):
+    """Enable (clearing the totals) or disable the library's per-class event timers."""
+    _check(lib().lqcd_kernel_timers(int(enable)), "kernel_timers")
+
+
+def kernel_timer_read(kernel_class: str):
+    """(total milliseconds, launches) of one kernel class since the timers were enabled"""
+    ms = ctypes.c_double()
+    n = ctypes.c_uint64()
+    _check(lib().lqcd_kernel_timer_read(kernel_class.encode(), ctypes.byref(ms), ctypes.byref(n)),
+           "kernel_timer_read")
+    return ms.value, n.value
 
 
 # ---------------------------------------------------------------- torch plumbing
@@ -338,12 +361,18 @@ def cg_solve(x: Field, U: Field, b: Field, kappa, params: CgParams | None = None
     return rc, info
 
 
-def gauge_force(P: Field, U: Field, beta, coeff, stream=None):
-    _check(lib().lqcd_gauge_force(P.h, U.h, beta, coeff, _s(stream)), "gauge_force")
+def gauge_force(P: Field, U: Field, beta, coeff, arith=None, stream=None):
+    if arith is None:
+        _check(lib().lqcd_gauge_force(P.h, U.h, beta, coeff, _s(stream)), "gauge_force")
+    else:
+        _check(lib().lqcd_gauge_force_ex(P.h, U.h, beta, coeff, arith, _s(stream)), "gauge_force_ex")
 
 
-def fermion_force(P: Field, U: Field, X: Field, kappa, coeff, stream=None):
-    _check(lib().lqcd_fermion_force(P.h, U.h, X.h, kappa, coeff, _s(stream)), "fermion_force")
+def fermion_force(P: Field, U: Field, X: Field, kappa, coeff, arith=None, stream=None):
+    if arith is None:
+        _check(lib().lqcd_fermion_force(P.h, U.h, X.h, kappa, coeff, _s(stream)), "fermion_force")
+    else:
+        _check(lib().lqcd_fermion_force_ex(P.h, U.h, X.h, kappa, coeff, arith, _s(stream)), "fermion_force_ex")
 
 
 def link_update(U: Field, P: Field, c, U_sloppy: Field | None = None, stream=None):
@@ -378,9 +407,9 @@ def spinor_dot(a: Field, b: Field, stream=None) -> float:
 # ---------------------------------------------------------------- HMC
 
 def hmc_params(beta, kappa, tau=1.0, nsteps=10, integrator=LEAPFROG, n_flavors=2, cg=None, reunitarize=True,
-               metropolis=True) -> HmcParams:
+               metropolis=True, force_prec=F64) -> HmcParams:
     return HmcParams(beta, kappa, tau, nsteps, integrator, n_flavors, cg or cg_params(), int(reunitarize),
-                     int(metropolis))
+                     int(metropolis), int(force_prec))
 
 
 class HmcState:

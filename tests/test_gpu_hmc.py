@@ -87,3 +87,17 @@ def test_energy_conservation_dt_squared():
         _, (g,) = _run_gpu(Uh, params, 1, 1)
         dH.append(g["dH"])
     assert 3.5 < dH[0] / dH[1] < 4.5
+
+
+def test_mixed_trajectory_fp32_forces_close_to_fp64():
+    """The benchmark's mixed configuration (FP16+norm solver, FP32 forces)
+    against the FP64 GPU trajectory from the same start and momenta."""
+    Uh = orc.gauge_start(DIMS, seed=1, eps=0.3)
+    base = dict(beta=5.6, kappa=0.156, tau=0.2, nsteps=10, integrator=lqcd.OMELYAN)
+    U64, (g64,) = _run_gpu(Uh, lqcd.hmc_params(**base, cg=lqcd.cg_params(tol=1e-10)), 1, 1)
+    Um, (gm,) = _run_gpu(Uh, lqcd.hmc_params(**base, cg=lqcd.cg_params(tol=1e-10, sloppy=lqcd.F16N, delta=0.003),
+                                             force_prec=lqcd.F32), 1, 1)
+    assert abs(gm["dH"] - g64["dH"]) < 1e-4, (gm["dH"], g64["dH"])
+    assert gm["accepted"] == g64["accepted"] == 1
+    assert np.max(np.abs(Um - U64)) < 1e-5
+    assert gm["cg_true_rel_res_max"] <= 1e-10

@@ -136,3 +136,27 @@ def test_fermion_force_matches_oracle(dims, t_bc):
     lqcd.fermion_force(P, U, Xf, kappa, coeff)
     F = orc.fermion_force(dims, Uh, kappa, X, t_bc=t_bc)
     assert np.max(np.abs(P.download() - (Ph - coeff * F))) < 1e-12 * max(1, np.abs(F).max())
+
+
+@pytest.mark.parametrize("which", ["gauge", "fermion"])
+def test_fp32_forces_close_to_oracle(which):
+    """FP32-arithmetic forces (the mixed trajectory's) against the FP64 oracle:
+    FP32 rounding of links, spinors and staple products bounds the error at a
+    few 1e-6 of the largest force component."""
+    dims = (8, 6, 6, 12)
+    kappa, beta, coeff = 0.156, 5.6, 0.05
+    Uh = orc.gauge_start(dims, seed=6, eps=0.4)
+    Ph = inputs.random_momentum(dims, 21)
+    U = lqcd.gauge_field(dims).upload(Uh)
+    P = lqcd.momentum_field(dims).upload(Ph)
+    if which == "gauge":
+        lqcd.gauge_force(P, U, beta, coeff, arith=lqcd.F32)
+        F = orc.gauge_force(dims, Uh, beta)
+    else:
+        X = inputs.random_spinor(dims, 22, parity=0)
+        Xf = lqcd.spinor_field(dims, 0).upload(half(X, dims, 0))
+        lqcd.fermion_force(P, U, Xf, kappa, coeff, arith=lqcd.F32)
+        F = orc.fermion_force(dims, Uh, kappa, X)
+    err = np.max(np.abs((Ph - P.download()) / coeff - F))
+    assert err < 5e-6 * np.abs(F).max(), err
+    assert err > 0  # it really ran in FP32
