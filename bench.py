@@ -324,18 +324,21 @@ def run_ours(args):
     kclass = f"dslash_{args.sloppy}"
     timers = {k: lqcd.kernel_timer_read(k) for k in lqcd.KERNEL_CLASSES}
     lqcd.kernel_timers(False)
-    ms, n = timers[kclass]
+    ms, n, nbytes = timers[kclass]
     Vh = V // 2
-    bytes_per_launch = SLOPPY_BYTES[args.sloppy] * Vh
     peaks = measured_peaks()
-    achieved = bytes_per_launch / (ms / n * 1e-3) / 1e9 if n else None
+    # achieved = algorithmic bytes of the timed launches (each launch's own
+    # fields: plain, axpy and CG-update variants) / their summed event time
+    achieved = nbytes / (ms * 1e-3) / 1e9 if n else None
     traffic = stored_traffic(kclass) if tuple(dims) == (32, 32, 32, 64) else None
     roofline = {"kernel": kclass, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"] if achieved else None, "traffic": traffic,
-                "peak_source": peaks["source"], "algorithmic_bytes_per_launch": bytes_per_launch,
+                "peak_source": peaks["source"], "algorithmic_bytes_per_launch": nbytes / n if n else None,
+                "plain_kernel_bytes_per_launch": SLOPPY_BYTES[args.sloppy] * Vh,
                 "avg_launch_us": ms / n * 1e3 if n else None, "launches": n}
     step_ms = t_max / args.steps * 1e3
-    kernel_share = {k: {"ms_per_traj": v[0] / args.steps, "launches_per_traj": v[1] / args.steps}
+    kernel_share = {k: {"ms_per_traj": v[0] / args.steps, "launches_per_traj": v[1] / args.steps,
+                        "GB_per_s": (v[2] / (v[0] * 1e-3) / 1e9) if v[2] else None}
                     for k, v in timers.items() if v[1]}
 
     # FP64 GPU path beside it: same start, same chain, same trajectory counters

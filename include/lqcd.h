@@ -119,9 +119,13 @@ uint64_t lqcd_launch_count(void);
  * "dslash_df64" (the mixed solver's float-float residual products),
  * "gauge_force", "fermion_force", "link_update".  Enabling clears the totals.
  * lqcd_kernel_timer_read synchronises the device, then returns the summed
- * event time in milliseconds and the number of launches of one class. */
+ * event time in milliseconds, the number of launches of one class and, for the
+ * hopping-term classes, the algorithmic bytes those launches move (every
+ * link, input, output and fused-epilogue field element counted once; 0 for
+ * the other classes).  Output pointers may be NULL. */
 lqcd_status lqcd_kernel_timers(int enable);
-lqcd_status lqcd_kernel_timer_read(const char *kernel_class, double *total_ms, uint64_t *launches);
+lqcd_status lqcd_kernel_timer_read(const char *kernel_class, double *total_ms, uint64_t *launches,
+                                   double *algorithmic_bytes);
 
 /* Device allocator hook.  alloc(bytes, stream, ctx) returns device memory or
  * NULL; free(ptr, stream, ctx) releases it.  Passing NULL for both restores

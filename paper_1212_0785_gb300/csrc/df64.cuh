@@ -68,6 +68,41 @@ __device__ __forceinline__ Df &operator+=(Df &a, Df b)
     return a;
 }
 
+// Accumulator of a sum of float-float products: the leading products are
+// added exactly (two-sum into s), all error terms and cross products are
+// summed in FP32 into c, and the pair is normalised once at the end.
+struct DfAcc {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add_prod(Df a, Df b)
+    {
+        float p = a.hi * b.hi;
+        float e = fmaf(a.hi, b.hi, -p);
+        e = fmaf(a.hi, b.lo, e);
+        e = fmaf(a.lo, b.hi, e);
+        float t = s + p;
+        float v = t - s;
+        c += ((s - (t - v)) + (p - v)) + e;
+        s = t;
+    }
+    __device__ __forceinline__ void sub_prod(Df a, Df b) { add_prod(Df(-a.hi, -a.lo), b); }
+    __device__ __forceinline__ void add(Df a)
+    {
+        float t = s + a.hi;
+        float v = t - s;
+        c += ((s - (t - v)) + (a.hi - v)) + a.lo;
+        s = t;
+    }
+    __device__ __forceinline__ Df value() const { return df_fast_two_sum_any(s, c); }
+    // |s| >= |c| holds unless the sum cancelled; normalise with a full two-sum
+    __device__ __forceinline__ static Df df_fast_two_sum_any(float a, float b)
+    {
+        float t = a + b;
+        float v = t - a;
+        float e = (a - (t - v)) + (b - v);
+        return Df(t, e);
+    }
+};
+
 // conversions used by the generic storage accessors
 template <typename R>
 __device__ __forceinline__ R df_to(float hi, float lo);
@@ -133,6 +168,13 @@ struct SpinorRef<PREC_DF> {
         }
         return s;
     }
+    template <typename R>
+    __device__ __forceinline__ Sp<R> load_scaled(int cb, R &scale) const
+    {
+        scale = R(1);
+        return load<R>(cb);
+    }
+    static constexpr bool has_norm = false;
     template <typename R>
     __device__ __forceinline__ void store(int cb, const Sp<R> &s) const
     {

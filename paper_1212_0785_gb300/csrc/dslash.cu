@@ -17,33 +17,46 @@
 
 namespace lqcd {
 
-// one direction: forward hop with (1 + FS gamma), backward with (1 + BS gamma)
+template <typename R>
+__device__ __forceinline__ void scale_hs(Hs<R> &h, R s)
+{
+#pragma unroll
+    for (int k = 0; k < 2; k++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) h.c[k][a] = s * h.c[k][a];
+}
+
+// One direction: forward hop U_mu(x) (1 + FS gamma_mu) psi(x + mu), backward
+// hop U_mu(x - mu)^dag (1 + BS gamma_mu) psi(x - mu).  A per-site norm of the
+// stored spinor and the fermion boundary sign multiply the 6 complex numbers
+// of the projected, link-multiplied half spinor rather than the 12 of the
+// spinor.
 template <int MU, int FS, int BS, typename R, lqcd_prec SP, lqcd_prec GP>
 __device__ __forceinline__ void hop_dir(Sp<R> &acc, const SpinorRef<SP> &in, const GaugeRef<GP> &U, const Geo &g,
-                                        const int c[4], int cb, int out_par)
+                                        int cb, int out_par, int nf, int nbk, bool wrap_f, bool wrap_b)
 {
-    const int in_par = 1 - out_par;
-    {   // forward: U_mu(x) psi(x + mu)
-        int cf[4] = {c[0], c[1], c[2], c[3]};
-        bool wrap = (c[MU] + 1 == g.L[MU]);
-        cf[MU] = wrap ? 0 : c[MU] + 1;
-        Sp<R> psi = in.template load<R>(coords_cb(g, cf));
-        Hs<R> h = project<MU, FS>(psi);
-        M3<R> u = U.template load<R>(MU, out_par, cb);
-        Hs<R> uh = mul_link(u, h);
-        if (MU == 3 && wrap && g.t_bc < 0) negate(uh);
+    constexpr bool NORM = SpinorRef<SP>::has_norm;
+    const bool antip = (MU == 3) && g.t_bc < 0;
+    {   // forward
+        R sc;
+        Sp<R> psi = in.template load_scaled<R>(nf, sc);
+        Hs<R> uh = mul_link(U.template load<R>(MU, out_par, cb), project<MU, FS>(psi));
+        if (NORM) {
+            scale_hs(uh, (antip && wrap_f) ? -sc : sc);
+        } else if (MU == 3) {
+            if (antip && wrap_f) negate(uh);
+        }
         accumulate<MU, FS>(acc, uh);
     }
-    {   // backward: U_mu(x - mu)^dag psi(x - mu)
-        int cbk[4] = {c[0], c[1], c[2], c[3]};
-        bool wrap = (c[MU] == 0);
-        cbk[MU] = wrap ? g.L[MU] - 1 : c[MU] - 1;
-        int nb = coords_cb(g, cbk);
-        Sp<R> psi = in.template load<R>(nb);
-        Hs<R> h = project<MU, BS>(psi);
-        M3<R> u = U.template load<R>(MU, in_par, nb);
-        Hs<R> uh = mul_link_dag(u, h);
-        if (MU == 3 && wrap && g.t_bc < 0) negate(uh);
+    {   // backward
+        R sc;
+        Sp<R> psi = in.template load_scaled<R>(nbk, sc);
+        Hs<R> uh = mul_link_dag(U.template load<R>(MU, 1 - out_par, nbk), project<MU, BS>(psi));
+        if (NORM) {
+            scale_hs(uh, (antip && wrap_b) ? -sc : sc);
+        } else if (MU == 3) {
+            if (antip && wrap_b) negate(uh);
+        }
         accumulate<MU, BS>(acc, uh);
     }
 }
@@ -52,16 +65,18 @@ template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
 __device__ __forceinline__ Sp<R> dslash_site(const SpinorRef<SP> &in, const GaugeRef<GP> &U, const Geo &g, int cb,
                                              int out_par)
 {
-    int c[4];
+    int c[4], nb[8];
+    bool tf, tb;
     cb_coords(g, cb, out_par, c);
+    cb_neighbours(g, cb, c, nb, tf, tb);
     Sp<R> acc = sp_zero<R>();
     // D: (1 - gamma) forward, (1 + gamma) backward; D^dag swaps them
     constexpr int FS = DAG ? +1 : -1;
     constexpr int BS = -FS;
-    hop_dir<0, FS, BS, R>(acc, in, U, g, c, cb, out_par);
-    hop_dir<1, FS, BS, R>(acc, in, U, g, c, cb, out_par);
-    hop_dir<2, FS, BS, R>(acc, in, U, g, c, cb, out_par);
-    hop_dir<3, FS, BS, R>(acc, in, U, g, c, cb, out_par);
+    hop_dir<0, FS, BS, R>(acc, in, U, g, cb, out_par, nb[0], nb[1], false, false);
+    hop_dir<1, FS, BS, R>(acc, in, U, g, cb, out_par, nb[2], nb[3], false, false);
+    hop_dir<2, FS, BS, R>(acc, in, U, g, cb, out_par, nb[4], nb[5], false, false);
+    hop_dir<3, FS, BS, R>(acc, in, U, g, cb, out_par, nb[6], nb[7], tf, tb);
     return acc;
 }
 
@@ -152,6 +167,174 @@ __global__ void __launch_bounds__(DS_BLOCK) dslash_cg_kernel(SpinorRef<SP> in, G
     block_sum_store<1, DS_BLOCK>(n2, partials, nblocks);
 }
 
+// ---------------------------------------------------------------- float-float kernel
+//
+// The float-float products of the mixed solver's accurate residual are long
+// chains of dependent FP32 operations, so this kernel spreads each output
+// site over three threads, one per colour row a of the result: every thread
+// projects the whole neighbour half spinor (L1 serves the repeated loads) and
+// multiplies it by row a of U (column a of U^dag), accumulating exact leading
+// products with a single normalisation per dot product.
+
+constexpr int DF_SITES = 64; // sites per block; blockDim = (64, 3)
+
+// acc += k v with k in {+1, -1, +i, -i} (kind 0..3)
+template <int KIND>
+__device__ __forceinline__ void acc_c(DfAcc &ar, DfAcc &ai, const Cx<Df> &v)
+{
+    if (KIND == 0) {
+        ar.add(v.re);
+        ai.add(v.im);
+    } else if (KIND == 1) {
+        ar.add(-v.re);
+        ai.add(-v.im);
+    } else if (KIND == 2) { // +i v = (-im, re)
+        ar.add(-v.im);
+        ai.add(v.re);
+    } else { // -i v = (im, -re)
+        ar.add(v.im);
+        ai.add(-v.re);
+    }
+}
+
+// rows 2, 3 of (1 + S gamma_mu) from the projected rows (v0, v1): see the table above project()
+template <int MU, int S>
+__device__ __forceinline__ void acc_hop(DfAcc (&ar)[4], DfAcc (&ai)[4], const Cx<Df> &v0, const Cx<Df> &v1)
+{
+    acc_c<0>(ar[0], ai[0], v0);
+    acc_c<0>(ar[1], ai[1], v1);
+    constexpr int MI = S > 0 ? 3 : 2; // -S i
+    constexpr int PI = S > 0 ? 2 : 3; // +S i
+    constexpr int P1 = S > 0 ? 0 : 1; // +S
+    constexpr int M1 = S > 0 ? 1 : 0; // -S
+    if (MU == 0) {
+        acc_c<MI>(ar[2], ai[2], v1);
+        acc_c<MI>(ar[3], ai[3], v0);
+    } else if (MU == 1) {
+        acc_c<P1>(ar[2], ai[2], v1);
+        acc_c<M1>(ar[3], ai[3], v0);
+    } else if (MU == 2) {
+        acc_c<MI>(ar[2], ai[2], v0);
+        acc_c<PI>(ar[3], ai[3], v1);
+    } else {
+        acc_c<P1>(ar[2], ai[2], v0);
+        acc_c<P1>(ar[3], ai[3], v1);
+    }
+}
+
+template <int MU, int FS, int BS>
+__device__ __forceinline__ void hop_dir_df(DfAcc (&ar)[4], DfAcc (&ai)[4], const SpinorRef<PREC_DF> &in,
+                                           const GaugeRef<PREC_DF> &U, const Geo &g, int cb, int out_par, int a,
+                                           int nf, int nbk, bool wrap_f, bool wrap_b)
+{
+    const bool antip = (MU == 3) && g.t_bc < 0;
+    { // forward: row a of U_mu(x)
+        Hs<Df> h = project<MU, FS>(in.template load<Df>(nf));
+        DfAcc r0, i0, r1, i1;
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            float4 w = ldg(U.d + U.idx(MU, out_par, a * 3 + b, cb));
+            Df ur(w.x, w.y), ui(w.z, w.w);
+            r0.add_prod(ur, h.c[0][b].re);
+            r0.sub_prod(ui, h.c[0][b].im);
+            i0.add_prod(ur, h.c[0][b].im);
+            i0.add_prod(ui, h.c[0][b].re);
+            r1.add_prod(ur, h.c[1][b].re);
+            r1.sub_prod(ui, h.c[1][b].im);
+            i1.add_prod(ur, h.c[1][b].im);
+            i1.add_prod(ui, h.c[1][b].re);
+        }
+        Cx<Df> v0{r0.value(), i0.value()}, v1{r1.value(), i1.value()};
+        if (antip && wrap_f) {
+            v0 = -v0;
+            v1 = -v1;
+        }
+        acc_hop<MU, FS>(ar, ai, v0, v1);
+    }
+    { // backward: column a of U_mu(x - mu), conjugated
+        Hs<Df> h = project<MU, BS>(in.template load<Df>(nbk));
+        DfAcc r0, i0, r1, i1;
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            float4 w = ldg(U.d + U.idx(MU, 1 - out_par, b * 3 + a, nbk));
+            Df ur(w.x, w.y), ui(w.z, w.w);
+            r0.add_prod(ur, h.c[0][b].re);
+            r0.add_prod(ui, h.c[0][b].im);
+            i0.add_prod(ur, h.c[0][b].im);
+            i0.sub_prod(ui, h.c[0][b].re);
+            r1.add_prod(ur, h.c[1][b].re);
+            r1.add_prod(ui, h.c[1][b].im);
+            i1.add_prod(ur, h.c[1][b].im);
+            i1.sub_prod(ui, h.c[1][b].re);
+        }
+        Cx<Df> v0{r0.value(), i0.value()}, v1{r1.value(), i1.value()};
+        if (antip && wrap_b) {
+            v0 = -v0;
+            v1 = -v1;
+        }
+        acc_hop<MU, BS>(ar, ai, v0, v1);
+    }
+}
+
+template <bool DAG, bool XPAY>
+__global__ void __launch_bounds__(DF_SITES * 3) dslash_df_kernel(SpinorRef<PREC_DF> out, SpinorRef<PREC_DF> in,
+                                                                 GaugeRef<PREC_DF> U, Geo g, int out_par,
+                                                                 SpinorRef<PREC_DF> x, Df b, const int *skip)
+{
+    if (skip && *skip) return;
+    const int a = threadIdx.y;
+    const int cb = blockIdx.x * DF_SITES + threadIdx.x;
+    if (cb >= g.Vh) return;
+    int c[4], nb[8];
+    bool tf, tb;
+    cb_coords(g, cb, out_par, c);
+    cb_neighbours(g, cb, c, nb, tf, tb);
+    DfAcc ar[4], ai[4];
+    constexpr int FS = DAG ? +1 : -1;
+    constexpr int BS = -FS;
+    hop_dir_df<0, FS, BS>(ar, ai, in, U, g, cb, out_par, a, nb[0], nb[1], false, false);
+    hop_dir_df<1, FS, BS>(ar, ai, in, U, g, cb, out_par, a, nb[2], nb[3], false, false);
+    hop_dir_df<2, FS, BS>(ar, ai, in, U, g, cb, out_par, a, nb[4], nb[5], false, false);
+    hop_dir_df<3, FS, BS>(ar, ai, in, U, g, cb, out_par, a, nb[6], nb[7], tf, tb);
+#pragma unroll
+    for (int sp = 0; sp < 4; sp++) {
+        Cx<Df> v{ar[sp].value(), ai[sp].value()};
+        size_t k = (size_t)(sp * 3 + a) * out.Vh + cb;
+        if (XPAY) {
+            float4 xv = x.d[k];
+            Cx<Df> xc{Df(xv.x, xv.y), Df(xv.z, xv.w)};
+            v = xc + b * v;
+        }
+        out.d[k] = df_from<Df>(v);
+    }
+}
+
+static lqcd_status launch_df(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int dagger,
+                             const lqcd_field *x, double b, const int *skip, cudaStream_t s)
+{
+    Geo g = make_geo(in->lat);
+    dim3 block(DF_SITES, 3), grid(nblocks_for(g.Vh, DF_SITES));
+    SpinorRef<PREC_DF> xr = x ? spinor_ref<PREC_DF>(x) : SpinorRef<PREC_DF>{nullptr, g.Vh};
+    int op = out->kind == LQCD_SPINOR_EVEN ? 0 : 1;
+    Df bd(b);
+    if (x) {
+        if (dagger)
+            dslash_df_kernel<true, true><<<grid, block, 0, s>>>(spinor_ref<PREC_DF>(out), spinor_ref<PREC_DF>(in),
+                                                                 gauge_ref<PREC_DF>(U), g, op, xr, bd, skip);
+        else
+            dslash_df_kernel<false, true><<<grid, block, 0, s>>>(spinor_ref<PREC_DF>(out), spinor_ref<PREC_DF>(in),
+                                                                  gauge_ref<PREC_DF>(U), g, op, xr, bd, skip);
+    } else {
+        if (dagger)
+            dslash_df_kernel<true, false><<<grid, block, 0, s>>>(spinor_ref<PREC_DF>(out), spinor_ref<PREC_DF>(in),
+                                                                  gauge_ref<PREC_DF>(U), g, op, xr, bd, skip);
+        else
+            dslash_df_kernel<false, false><<<grid, block, 0, s>>>(spinor_ref<PREC_DF>(out), spinor_ref<PREC_DF>(in),
+                                                                   gauge_ref<PREC_DF>(U), g, op, xr, bd, skip);
+    }
+    return LQCD_OK;
+}
+
 // ---------------------------------------------------------------- dispatch
 
 static int out_parity(const lqcd_field *f) { return f->kind == LQCD_SPINOR_EVEN ? 0 : 1; }
@@ -238,7 +421,8 @@ lqcd_status dslash_plain(lqcd_field *out, const lqcd_field *U, const lqcd_field 
                          cudaStream_t s)
 {
     LQCD_TRY(check_pair(out, U, in));
-    KernelTimer kt(dslash_class(in->prec), s);
+    double site = 8 * link_bytes(U->prec) + 2 * spinor_site_bytes(in->prec);
+    KernelTimer kt(dslash_class(in->prec), s, site * in->Vh);
     switch (in->prec) {
     case LQCD_F64: launch_plain<LQCD_F64>(out, U, in, dagger, skip, s); break;
     case LQCD_F32:
@@ -249,7 +433,7 @@ lqcd_status dslash_plain(lqcd_field *out, const lqcd_field *U, const lqcd_field 
         break;
     case LQCD_F16N: launch_plain<LQCD_F16N>(out, U, in, dagger, skip, s); break;
     case LQCD_BF16: launch_plain<LQCD_BF16>(out, U, in, dagger, skip, s); break;
-    default: launch_plain<PREC_DF>(out, U, in, dagger, skip, s); break;
+    default: launch_df(out, U, in, dagger, nullptr, 0.0, skip, s); break;
     }
     LQCD_LAUNCHED();
     return LQCD_OK;
@@ -260,7 +444,8 @@ lqcd_status dslash_xpay(lqcd_field *out, const lqcd_field *U, const lqcd_field *
 {
     LQCD_TRY(check_pair(out, U, in));
     LQCD_REQUIRE(x && x->kind == out->kind && x->prec == out->prec, "dslash_xpay: x must match out");
-    KernelTimer kt(dslash_class(in->prec), s);
+    double site = 8 * link_bytes(U->prec) + 3 * spinor_site_bytes(in->prec); // + read of x
+    KernelTimer kt(dslash_class(in->prec), s, site * in->Vh);
     switch (in->prec) {
     case LQCD_F64: launch_xpay<LQCD_F64>(out, U, in, dagger, x, b, partials, skip, s); break;
     case LQCD_F32:
@@ -271,7 +456,10 @@ lqcd_status dslash_xpay(lqcd_field *out, const lqcd_field *U, const lqcd_field *
         break;
     case LQCD_F16N: launch_xpay<LQCD_F16N>(out, U, in, dagger, x, b, partials, skip, s); break;
     case LQCD_BF16: launch_xpay<LQCD_BF16>(out, U, in, dagger, x, b, partials, skip, s); break;
-    default: launch_xpay<PREC_DF>(out, U, in, dagger, x, b, partials, skip, s); break;
+    default:
+        LQCD_REQUIRE(partials == nullptr, "float-float hopping term has no norm reduction");
+        launch_df(out, U, in, dagger, x, b, skip, s);
+        break;
     }
     LQCD_LAUNCHED();
     return LQCD_OK;
@@ -281,7 +469,10 @@ lqcd_status dslash_cg(const lqcd_field *U, const lqcd_field *in, int dagger, con
                       lqcd_field *xs, lqcd_field *r, const lqcd_field *p, double *partials, const CgScalars *sc,
                       cudaStream_t s)
 {
-    KernelTimer kt(dslash_class(in->prec), s);
+    // links, input; reads of t, p, r and xs; writes of r and xs (no output of the product)
+    double site = 8 * link_bytes(U->prec) + 4 * spinor_site_bytes(in->prec) + spinor_site_bytes(r->prec) +
+                  2 * spinor_site_bytes(xs->prec);
+    KernelTimer kt(dslash_class(in->prec), s, site * in->Vh);
     switch (in->prec) {
     case LQCD_F64: launch_cg<LQCD_F64, LQCD_F64>(U, in, dagger, t, b, xs, r, p, partials, sc, s); break;
     case LQCD_F32: launch_cg<LQCD_F32, LQCD_F32>(U, in, dagger, t, b, xs, r, p, partials, sc, s); break;

@@ -42,10 +42,12 @@ static std::atomic<bool> g_timers_on{false};
 static std::vector<cudaEvent_t> g_event_pool;
 struct PendingTiming {
     int cls;
+    double bytes;
     cudaEvent_t a, b;
 };
 static std::vector<PendingTiming> g_pending;
 static double g_timer_ms[K_NCLASS];
+static double g_timer_bytes[K_NCLASS];
 static uint64_t g_timer_n[K_NCLASS];
 
 static cudaEvent_t pool_event()
@@ -63,7 +65,7 @@ static cudaEvent_t pool_event()
     return e;
 }
 
-KernelTimer::KernelTimer(int c, cudaStream_t st) : cls(c), s(st)
+KernelTimer::KernelTimer(int c, cudaStream_t st, double nbytes) : cls(c), s(st), bytes(nbytes)
 {
     if (!g_timers_on.load(std::memory_order_relaxed)) return;
     std::lock_guard<std::mutex> lk(g_timer_mu);
@@ -77,7 +79,7 @@ KernelTimer::~KernelTimer()
     if (!a || !b) return;
     cudaEventRecord(b, s);
     std::lock_guard<std::mutex> lk(g_timer_mu);
-    g_pending.push_back({cls, a, b});
+    g_pending.push_back({cls, bytes, a, b});
 }
 
 // resolve pending event pairs (device synchronised by the caller)
@@ -87,6 +89,7 @@ static void drain_timers_locked()
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
             g_timer_ms[p.cls] += ms;
+            g_timer_bytes[p.cls] += p.bytes;
             g_timer_n[p.cls] += 1;
         } else {
             cudaGetLastError();
@@ -173,6 +176,12 @@ Geo make_geo(const lqcd_lattice &lat)
     g.Lxh = lat.dims[0] / 2;
     g.Vh = (int)((long long)lat.dims[0] * lat.dims[1] * lat.dims[2] * lat.dims[3] / 2);
     g.t_bc = lat.t_bc;
+    g.sY = g.Lxh;
+    g.sZ = g.Lxh * lat.dims[1];
+    g.sT = g.sZ * lat.dims[2];
+    g.dLxh = make_fastdiv((uint32_t)g.Lxh);
+    g.dLy = make_fastdiv((uint32_t)lat.dims[1]);
+    g.dLz = make_fastdiv((uint32_t)lat.dims[2]);
     return g;
 }
 
@@ -828,13 +837,15 @@ lqcd_status lqcd_kernel_timers(int enable)
     drain_timers_locked();
     for (int k = 0; k < K_NCLASS; k++) {
         g_timer_ms[k] = 0;
+        g_timer_bytes[k] = 0;
         g_timer_n[k] = 0;
     }
     g_timers_on.store(enable != 0);
     return LQCD_OK;
 }
 
-lqcd_status lqcd_kernel_timer_read(const char *kernel_class, double *total_ms, uint64_t *launches)
+lqcd_status lqcd_kernel_timer_read(const char *kernel_class, double *total_ms, uint64_t *launches,
+                                   double *algorithmic_bytes)
 {
     LQCD_REQUIRE(kernel_class, "kernel_timer_read: NULL class");
     int cls = -1;
@@ -846,6 +857,7 @@ lqcd_status lqcd_kernel_timer_read(const char *kernel_class, double *total_ms, u
     drain_timers_locked();
     if (total_ms) *total_ms = g_timer_ms[cls];
     if (launches) *launches = g_timer_n[cls];
+    if (algorithmic_bytes) *algorithmic_bytes = g_timer_bytes[cls];
     return LQCD_OK;
 }
 

@@ -85,11 +85,33 @@ enum KernelClass {
 struct KernelTimer { // RAII: events around the launches made while it lives
     int cls;
     cudaStream_t s;
+    double bytes; // algorithmic bytes the timed launches move (0: not counted)
     cudaEvent_t a = nullptr, b = nullptr;
-    KernelTimer(int cls, cudaStream_t s);
+    KernelTimer(int cls, cudaStream_t s, double bytes = 0.0);
     ~KernelTimer();
 };
 inline int dslash_class(lqcd_prec p) { return K_DSLASH_F64 + (int)p; }
+
+// algorithmic bytes of one half spinor site / one link in a storage precision
+// (each field element counted once; 12-real links for the low precisions)
+inline double spinor_site_bytes(lqcd_prec p)
+{
+    switch ((int)p) {
+    case LQCD_F32: return 96;
+    case LQCD_F16N: return 52; // 48 + 4-byte norm
+    case LQCD_BF16: return 48;
+    default: return 192; // F64, float-float
+    }
+}
+inline double link_bytes(lqcd_prec p)
+{
+    switch ((int)p) {
+    case LQCD_F32: return 48;
+    case LQCD_F16N:
+    case LQCD_BF16: return 24;
+    default: return 144;
+    }
+}
 
 // ------------------------------------------------------------------ memory
 
@@ -130,11 +152,31 @@ struct FieldPtr {
 
 // ------------------------------------------------------------------ geometry
 
+// Division by an invariant divisor d (Granlund-Montgomery): with l = ceil(log2 d)
+// and m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(m, n) + n) >> l for
+// every n < 2^31 (the sum cannot overflow 32 bits there).
+struct FastDiv {
+    uint32_t d, m, l;
+};
+inline FastDiv make_fastdiv(uint32_t d)
+{
+    uint32_t l = 0;
+    while ((1ull << l) < d) l++;
+    uint64_t m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+    return FastDiv{d, (uint32_t)m, l};
+}
+__device__ __forceinline__ int fdiv(int n, const FastDiv &f)
+{
+    return (int)((__umulhi((uint32_t)n, f.m) + (uint32_t)n) >> f.l);
+}
+
 struct Geo {
     int L[4];
     int Lxh; // Lx / 2
     int Vh;
     int t_bc; // +1 / -1
+    int sY, sZ, sT; // checkerboard strides of y, z, t
+    FastDiv dLxh, dLy, dLz;
 };
 
 lqcd_status check_lattice(const lqcd_lattice *lat);
@@ -144,13 +186,31 @@ bool same_lattice(const lqcd_lattice &a, const lqcd_lattice &b);
 // coordinates of checkerboard site cb of parity par
 __device__ __forceinline__ void cb_coords(const Geo &g, int cb, int par, int c[4])
 {
-    int xh = cb % g.Lxh;
-    int r = cb / g.Lxh;
-    c[1] = r % g.L[1];
-    r /= g.L[1];
-    c[2] = r % g.L[2];
-    c[3] = r / g.L[2];
+    int r = fdiv(cb, g.dLxh);
+    int xh = cb - r * g.Lxh;
+    int r2 = fdiv(r, g.dLy);
+    c[1] = r - r2 * g.L[1];
+    c[3] = fdiv(r2, g.dLz);
+    c[2] = r2 - c[3] * g.L[2];
     c[0] = 2 * xh + ((c[1] + c[2] + c[3] + par) & 1);
+}
+
+// checkerboard indices of the 8 neighbours of (cb, coordinates c) and the
+// wrap flags of the t hops: nb[2*mu] forward, nb[2*mu+1] backward
+__device__ __forceinline__ void cb_neighbours(const Geo &g, int cb, const int c[4], int nb[8], bool &twrap_f,
+                                              bool &twrap_b)
+{
+    int b = c[0] & 1, xh = c[0] >> 1;
+    nb[0] = (b && xh == g.Lxh - 1) ? cb - (g.Lxh - 1) : cb + b;
+    nb[1] = (!b && xh == 0) ? cb + (g.Lxh - 1) : cb - (1 - b);
+    nb[2] = (c[1] == g.L[1] - 1) ? cb - g.sY * (g.L[1] - 1) : cb + g.sY;
+    nb[3] = (c[1] == 0) ? cb + g.sY * (g.L[1] - 1) : cb - g.sY;
+    nb[4] = (c[2] == g.L[2] - 1) ? cb - g.sZ * (g.L[2] - 1) : cb + g.sZ;
+    nb[5] = (c[2] == 0) ? cb + g.sZ * (g.L[2] - 1) : cb - g.sZ;
+    twrap_f = (c[3] == g.L[3] - 1);
+    twrap_b = (c[3] == 0);
+    nb[6] = twrap_f ? cb - g.sT * (g.L[3] - 1) : cb + g.sT;
+    nb[7] = twrap_b ? cb + g.sT * (g.L[3] - 1) : cb - g.sT;
 }
 
 // checkerboard index of coordinates (its parity is implied by the coordinates)
@@ -368,6 +428,13 @@ struct SpinorRef<LQCD_F64> {
         return s;
     }
     template <typename R>
+    __device__ __forceinline__ Sp<R> load_scaled(int cb, R &scale) const
+    {
+        scale = (R)1;
+        return load<R>(cb);
+    }
+    static constexpr bool has_norm = false;
+    template <typename R>
     __device__ __forceinline__ void store(int cb, const Sp<R> &s) const
     {
 #pragma unroll
@@ -408,6 +475,13 @@ struct SpinorRef<LQCD_F32> {
         for (int k = 0; k < 6; k++) v[k] = d[(size_t)k * Vh + cb];
         return unpack<R>(v);
     }
+    template <typename R>
+    __device__ __forceinline__ Sp<R> load_scaled(int cb, R &scale) const
+    {
+        scale = (R)1;
+        return load<R>(cb);
+    }
+    static constexpr bool has_norm = false;
     template <typename R>
     __device__ __forceinline__ void store(int cb, const Sp<R> &s) const
     {
@@ -450,6 +524,18 @@ struct SpinorRef<LQCD_F16N> {
         for (int k = 0; k < 3; k++) v[k] = ldg(d + (size_t)k * Vh + cb);
         return unpack<R>(v, ldg(norm + cb));
     }
+    // the stored values (value / norm) and the norm, for callers that apply
+    // the norm after a linear map
+    template <typename R>
+    __device__ __forceinline__ Sp<R> load_scaled(int cb, R &scale) const
+    {
+        uint4 v[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) v[k] = ldg(d + (size_t)k * Vh + cb);
+        scale = (R)ldg(norm + cb);
+        return unpack<R>(v, 1.0f);
+    }
+    static constexpr bool has_norm = true;
     template <typename R>
     __device__ __forceinline__ Sp<R> load_rw(int cb) const
     {
@@ -517,6 +603,13 @@ struct SpinorRef<LQCD_BF16> {
         for (int k = 0; k < 3; k++) v[k] = d[(size_t)k * Vh + cb];
         return unpack<R>(v);
     }
+    template <typename R>
+    __device__ __forceinline__ Sp<R> load_scaled(int cb, R &scale) const
+    {
+        scale = (R)1;
+        return load<R>(cb);
+    }
+    static constexpr bool has_norm = false;
     template <typename R>
     __device__ __forceinline__ void store(int cb, const Sp<R> &s) const
     {

@@ -86,7 +86,7 @@ _SIGS = {
     "lqcd_launch_count": (ctypes.c_uint64, []),
     "lqcd_set_allocator": (_i, [ALLOC_FN, FREE_FN, _vp]),
     "lqcd_kernel_timers": (_i, [_i]),
-    "lqcd_kernel_timer_read": (_i, [ctypes.c_char_p, _dp, ctypes.POINTER(ctypes.c_uint64)]),
+    "lqcd_kernel_timer_read": (_i, [ctypes.c_char_p, _dp, ctypes.POINTER(ctypes.c_uint64), _dp]),
     "lqcd_field_alloc": (_i, [ctypes.POINTER(Lattice), _i, _i, _i, _pp]),
     "lqcd_field_free": (_i, [_vp]),
     "lqcd_field_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
@@ -175,12 +175,14 @@ def kernel_timers(enable: bool):
 
 
 def kernel_timer_read(kernel_class: str):
-    """(total milliseconds, launches) of one kernel class since the timers were enabled"""
+    """(total milliseconds, launches, algorithmic bytes) of one kernel class
+    since the timers were enabled"""
     ms = ctypes.c_double()
     n = ctypes.c_uint64()
-    _check(lib().lqcd_kernel_timer_read(kernel_class.encode(), ctypes.byref(ms), ctypes.byref(n)),
+    nb = ctypes.c_double()
+    _check(lib().lqcd_kernel_timer_read(kernel_class.encode(), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(nb)),
            "kernel_timer_read")
-    return ms.value, n.value
+    return ms.value, n.value, nb.value
 
 
 # ---------------------------------------------------------------- torch plumbing

@@ -160,3 +160,20 @@ def test_fp32_forces_close_to_oracle(which):
     err = np.max(np.abs((Ph - P.download()) / coeff - F))
     assert err < 5e-6 * np.abs(F).max(), err
     assert err > 0  # it really ran in FP32
+
+
+@pytest.mark.parametrize("sloppy", [lqcd.F32, lqcd.F16N])
+def test_cg_mixed_tight_tolerance(sloppy):
+    """Solving to 1e-12 needs the float-float residual of the reliable updates
+    to be accurate to ~1e-13 of |b|; the oracle's FP64 operator checks it."""
+    dims = (8, 6, 6, 12)
+    kappa = 0.156
+    Uh = orc.gauge_start(dims, seed=2, eps=0.3)
+    b = inputs.random_spinor(dims, 23, parity=0)
+    U, Us = upload_gauge(Uh, dims, sloppy)
+    bf = upload_half(b, dims, 0)
+    x = lqcd.spinor_field(dims, 0)
+    rc, info = lqcd.cg_solve(x, U, bf, kappa, lqcd.cg_params(tol=1e-12, sloppy=sloppy, delta=0.05), U_sloppy=Us)
+    assert rc == lqcd.OK and info.true_rel_res <= 1e-12
+    r = b - orc.mdagm(dims, Uh, kappa, full_from_half(x.download(), dims, 0))
+    assert np.linalg.norm(r) <= 1.05e-12 * np.linalg.norm(b)
