@@ -263,6 +263,7 @@ def run_reference(args):
 def config_block(args, sloppy):
     c = dict(WORKLOAD)
     c["dims"] = list(args.dims)
+    c["nsteps"] = args.nsteps
     c["solver"] = ("fp64 CG" if sloppy == "f64" else
                    f"reliable-update mixed CG: {sloppy} spinors + 12-real {sloppy} links, fp32 math, "
                    f"fp64 residual/dots, delta {args.delta}")
@@ -290,7 +291,7 @@ def run_ours(args):
     wl = WORKLOAD
     cg = lqcd.cg_params(tol=wl["cg_tol"], maxiter=20000, sloppy=sloppy, delta=args.delta)
     force_prec = lqcd.PREC_NAMES[args.force_prec]
-    params = lqcd.hmc_params(wl["beta"], wl["kappa"], wl["tau"], wl["nsteps"], lqcd.OMELYAN, n_flavors=2, cg=cg,
+    params = lqcd.hmc_params(wl["beta"], wl["kappa"], wl["tau"], args.nsteps, lqcd.OMELYAN, n_flavors=2, cg=cg,
                              force_prec=force_prec)
 
     U = lqcd.gauge_field(dims)
@@ -349,7 +350,7 @@ def run_ours(args):
         U64 = lqcd.gauge_field(dims)
         lqcd.gauge_start(U64, SEED, EPS, chain=rank)
         st64 = lqcd.HmcState(U64, seed=SEED, chain=rank, traj0=args.warmup)
-        p64 = lqcd.hmc_params(wl["beta"], wl["kappa"], wl["tau"], wl["nsteps"], lqcd.OMELYAN, n_flavors=2,
+        p64 = lqcd.hmc_params(wl["beta"], wl["kappa"], wl["tau"], args.nsteps, lqcd.OMELYAN, n_flavors=2,
                               cg=lqcd.cg_params(tol=wl["cg_tol"], maxiter=20000, sloppy=lqcd.F64))
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -432,6 +433,8 @@ def main(argv=None):
     ap.add_argument("--delta", type=float, default=0.003)
     ap.add_argument("--force-prec", choices=("f64", "f32"), default="f32")
     ap.add_argument("--dims", type=int, nargs=4, default=WORKLOAD["dims"])
+    ap.add_argument("--nsteps", type=int, default=WORKLOAD["nsteps"],
+                    help="MD steps per trajectory (16 for the benchmarked workload)")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")

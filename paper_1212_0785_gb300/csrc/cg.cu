@@ -417,8 +417,6 @@ lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, con
                                                                Vh);
             LQCD_LAUNCHED();
             LQCD_TRY(true_residual_df(ws, kappa, &rr_true, s));
-            // the FP64 solution is the float-float one rounded
-            LQCD_TRY((convert_spinor<PREC_DF, LQCD_F64, double>(x, ws.xdf.f, s)));
         } else {
             LQCD_TRY(true_residual(ws, x, U, b, kappa, &rr_true, s));
         }
@@ -426,6 +424,10 @@ lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, con
         if (!std::isfinite(rr_true)) {
             set_error("cg: non-finite true residual");
             return finish(LQCD_ENUMERIC);
+        }
+        if (mixed && (rr_true <= h.stop2 || h.reason == PAUSE_MAXITER || h.iter >= prm.maxiter)) {
+            // the FP64 solution is the float-float one rounded
+            LQCD_TRY((convert_spinor<PREC_DF, LQCD_F64, double>(x, ws.xdf.f, s)));
         }
         if (rr_true <= h.stop2) return finish(LQCD_OK);
         if (h.reason == PAUSE_MAXITER || h.iter >= prm.maxiter) {

@@ -80,15 +80,17 @@ __device__ __forceinline__ Sp<R> dslash_site(const SpinorRef<SP> &in, const Gaug
     return acc;
 }
 
+// |s|^2 of one site, summed in the working precision (an FP32 kernel stays off
+// the FP64 pipe); the sums over sites are FP64
 template <typename R>
 __device__ __forceinline__ double sp_norm2(const Sp<R> &s)
 {
-    double n = 0;
+    R n = R(0);
 #pragma unroll
     for (int a = 0; a < 4; a++)
 #pragma unroll
-        for (int b = 0; b < 3; b++) n += (double)norm2(s.c[a][b]);
-    return n;
+        for (int b = 0; b < 3; b++) n = n + norm2(s.c[a][b]);
+    return (double)n;
 }
 
 // ---------------------------------------------------------------- kernels
