@@ -297,6 +297,29 @@ lqcd_status lqcd_kinetic_energy(const lqcd_field *P, double *out, void *stream);
  * same kind.  out: host. */
 lqcd_status lqcd_spinor_dot(const lqcd_field *a, const lqcd_field *b, double *out, void *stream);
 
+/* ------------------------------------------------------------ allocation-free plaquette */
+
+/* Largest lattice (sites) lqcd_plaquette_noalloc accepts. */
+#define LQCD_NOALLOC_MAX_SITES 16777216
+
+/* Mean plaquette like lqcd_plaquette, for callers that cannot let the library
+ * allocate device memory: code on a thread that must not call back into the
+ * allocator hook (for instance a hook that enters the Python interpreter), or
+ * a program that fixes its device memory up front.  The paper has no
+ * counterpart of this call.
+ *   U       F64 gauge field of at most LQCD_NOALLOC_MAX_SITES sites; larger
+ *           lattices return LQCD_EINVAL (use lqcd_plaquette).
+ *   out_dev device pointer to one double, written asynchronously on stream.
+ * It allocates nothing: the per-block partial sums live in one fixed array of
+ * LQCD_NOALLOC_MAX_SITES/256 doubles (512 KiB) per device, held by every
+ * device that loads the library until the process exits.  The first call on a
+ * device looks up that array's device address; make that first call before
+ * any stream capture.  All calls on a device share the array and each call
+ * overwrites the part it reads, so calls whose kernels may overlap on the
+ * device (different streams without ordering) race and must be serialised by
+ * the caller. */
+lqcd_status lqcd_plaquette_noalloc(const lqcd_field *U, double *out_dev, void *stream);
+
 /* ------------------------------------------------------------ HMC driver */
 
 typedef struct {

@@ -733,6 +733,17 @@ lqcd_status plaquette_sum(const lqcd_field *U, double *dst_dev, DevBuf &part, cu
     return reduce_partials((double *)part.p, nb, 1, dst_dev, s);
 }
 
+// block partials of the plaquette sum into caller-provided memory (nblocks
+// from plaquette_partial_blocks)
+int plaquette_partial_blocks(const lqcd_field *U) { return nblocks_for(2L * U->Vh, RB); }
+
+lqcd_status plaquette_partials_launch(const lqcd_field *U, double *partials, int nblocks, cudaStream_t s)
+{
+    plaquette_kernel<<<nblocks, RB, 0, s>>>(gauge_ref<LQCD_F64>(U), make_geo(U->lat), partials, nblocks);
+    LQCD_LAUNCHED();
+    return LQCD_OK;
+}
+
 lqcd_status kinetic_sum(const lqcd_field *P, double *dst_dev, DevBuf &part, cudaStream_t s)
 {
     long n = (long)P->Vh * 64;

@@ -108,6 +108,7 @@ _SIGS = {
     "lqcd_link_update": (_i, [_vp, _vp, _d, _vp, _vp]),
     "lqcd_reunitarize": (_i, [_vp, _dp, _vp]),
     "lqcd_plaquette": (_i, [_vp, _dp, _vp]),
+    "lqcd_plaquette_noalloc": (_i, [_vp, _vp, _vp]),
     "lqcd_kinetic_energy": (_i, [_vp, _dp, _vp]),
     "lqcd_spinor_dot": (_i, [_vp, _vp, _dp, _vp]),
     "lqcd_hmc_state_create": (_i, [_vp, _u32, _u32, _u32, _pp]),
