@@ -268,6 +268,7 @@ def config_block(args, sloppy):
                    f"reliable-update mixed CG: {sloppy} spinors + 12-real {sloppy} links, fp32 math, "
                    f"fp64 residual/dots, delta {args.delta}")
     c["forces"] = f"{getattr(args, 'force_prec', 'f64')} arithmetic"
+    c["initial_guess"] = "previous solution (chronological)" if getattr(args, "chrono", 0) else "zero"
     c["parallelism"] = f"replicas{args.gpus}" if args.gpus > 1 else "single_gpu"
     c["l2"] = "inputs larger than L2 (FP64 links 1.21 GB, spinors 0.2 GB)"
     return c
@@ -292,7 +293,7 @@ def run_ours(args):
     cg = lqcd.cg_params(tol=wl["cg_tol"], maxiter=20000, sloppy=sloppy, delta=args.delta)
     force_prec = lqcd.PREC_NAMES[args.force_prec]
     params = lqcd.hmc_params(wl["beta"], wl["kappa"], wl["tau"], args.nsteps, lqcd.OMELYAN, n_flavors=2, cg=cg,
-                             force_prec=force_prec)
+                             force_prec=force_prec, chrono=bool(args.chrono))
 
     U = lqcd.gauge_field(dims)
     lqcd.gauge_start(U, SEED, EPS, chain=rank)
@@ -351,7 +352,8 @@ def run_ours(args):
         lqcd.gauge_start(U64, SEED, EPS, chain=rank)
         st64 = lqcd.HmcState(U64, seed=SEED, chain=rank, traj0=args.warmup)
         p64 = lqcd.hmc_params(wl["beta"], wl["kappa"], wl["tau"], args.nsteps, lqcd.OMELYAN, n_flavors=2,
-                              cg=lqcd.cg_params(tol=wl["cg_tol"], maxiter=20000, sloppy=lqcd.F64))
+                              cg=lqcd.cg_params(tol=wl["cg_tol"], maxiter=20000, sloppy=lqcd.F64),
+                              chrono=bool(args.chrono))
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -432,6 +434,9 @@ def main(argv=None):
     ap.add_argument("--sloppy", choices=("f32", "f16n", "bf16"), default="f16n")
     ap.add_argument("--delta", type=float, default=0.003)
     ap.add_argument("--force-prec", choices=("f64", "f32"), default="f32")
+    ap.add_argument("--chrono", type=int, choices=(0, 1), default=1,
+                    help="start each solve after the first of a trajectory from the previous solution "
+                         "(both the mixed and the FP64 path)")
     ap.add_argument("--dims", type=int, nargs=4, default=WORKLOAD["dims"])
     ap.add_argument("--nsteps", type=int, default=WORKLOAD["nsteps"],
                     help="MD steps per trajectory (16 for the benchmarked workload)")

@@ -224,6 +224,8 @@ typedef struct {
     double delta;         /* reliable-update threshold: recompute the true residual when the
                              sloppy |r| drops below delta * max |r| since the last update */
     int max_restarts;     /* FP64 CG only: restarts allowed when the true residual fails */
+    int guess;            /* 0: start from x0 = 0; 1: x holds the initial guess on entry (its
+                             residual is recomputed accurately before the first iteration) */
 } lqcd_cg_params;
 
 typedef struct {
@@ -234,7 +236,7 @@ typedef struct {
 } lqcd_cg_info;
 
 /* Solve Mhat^dag Mhat x = b on the even sites (the matrix inversion of the
- * paper's Sec. 6, done there by QUDA), x0 = 0.  x, b: EVEN F64 spinors.
+ * paper's Sec. 6, done there by QUDA), from x0 = 0 or from x (params->guess).  x, b: EVEN F64 spinors.
  * U: F64/18 master links; for a mixed solve also pass the sloppy 12-real
  * copy U_sloppy in the matching precision (NULL for FP64).
  * Returns LQCD_ENOCONV (x holds the last iterate) when maxiter is reached. */
@@ -330,6 +332,9 @@ typedef struct {
     lqcd_cg_params cg;          /* solver of every force and action evaluation */
     int reunitarize;            /* 1: reunitarize the links after the accept/reject */
     int metropolis;             /* 1: accept iff u < exp(-dH); 0: always accept */
+    int chrono;                 /* 1: every solve after the first of a trajectory starts from the
+                                   previous solution (a chronological initial guess, paper Sec. 6.2);
+                                   reversibility then holds to the solver tolerance only */
     lqcd_prec force_prec;       /* arithmetic of the molecular dynamics: LQCD_F64, or LQCD_F32: both
                                    forces in FP32 from an FP32 12-real copy of the links (increments
                                    accumulated into the FP64 momenta) and the link update's

@@ -342,7 +342,7 @@ lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, con
     LQCD_TRY(spinor_dot_dev(b, b, (double *)ws.scalars.p, ws.partials, s));
     LQCD_TRY(read_scalars((double *)ws.scalars.p, g_pinned.d, 1, s));
     double bb = g_pinned.d[0];
-    LQCD_CUDA(cudaMemsetAsync(x->data, 0, x->bytes, s));
+    if (!prm.guess) LQCD_CUDA(cudaMemsetAsync(x->data, 0, x->bytes, s));
     lqcd_cg_info inf{0, 0, 0.0, 0.0};
     auto finish = [&](lqcd_status st) {
         inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
@@ -354,12 +354,14 @@ lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, con
         return finish(LQCD_ENUMERIC);
     }
     if (bb == 0.0) {
+        LQCD_CUDA(cudaMemsetAsync(x->data, 0, x->bytes, s));
         LQCD_CUDA(cudaStreamSynchronize(s));
         return finish(LQCD_OK);
     }
 
     lqcd_field *P, *R, *T, *TMP, *XS;
     const lqcd_field *UU;
+    double rr0 = bb;
     if (mixed) {
         LQCD_REQUIRE(Us && Us->kind == LQCD_GAUGE && Us->prec == prm.sloppy && Us->recon == 12,
                      "cg: mixed solve needs a 12-real link copy in the sloppy precision");
@@ -367,22 +369,42 @@ lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, con
                                                                    gauge_ref<LQCD_F64>(U), Vh);
         LQCD_LAUNCHED();
         LQCD_TRY((convert_spinor<LQCD_F64, PREC_DF, double>(ws.bdf.f, b, s)));
-        LQCD_CUDA(cudaMemsetAsync(ws.xdf.f->data, 0, ws.xdf.f->bytes, s));
-        LQCD_TRY(lqcd_field_copy(ws.rs.f, b, s));
-        LQCD_TRY(lqcd_field_copy(ws.ps.f, b, s));
         LQCD_CUDA(cudaMemsetAsync(ws.xs.f->data, 0, ws.xs.f->bytes, s));
+        if (prm.guess) { // r = b - A x0, accurately
+            LQCD_TRY((convert_spinor<LQCD_F64, PREC_DF, double>(ws.xdf.f, x, s)));
+            LQCD_TRY(true_residual_df(ws, kappa, &rr0, s));
+            LQCD_TRY(df_to_sloppy(ws.rs.f, ws.rdf.f, s));
+            LQCD_TRY(lqcd_field_copy(ws.ps.f, ws.rs.f, s));
+        } else {
+            LQCD_CUDA(cudaMemsetAsync(ws.xdf.f->data, 0, ws.xdf.f->bytes, s));
+            LQCD_TRY(lqcd_field_copy(ws.rs.f, b, s));
+            LQCD_TRY(lqcd_field_copy(ws.ps.f, b, s));
+        }
         P = ws.ps.f, R = ws.rs.f, T = ws.ts.f, TMP = ws.tmpos.f, XS = ws.xs.f, UU = Us;
     } else {
-        LQCD_CUDA(cudaMemcpyAsync(ws.r64.f->data, b->data, b->bytes, cudaMemcpyDeviceToDevice, s));
-        LQCD_CUDA(cudaMemcpyAsync(ws.p64.f->data, b->data, b->bytes, cudaMemcpyDeviceToDevice, s));
+        if (prm.guess) {
+            LQCD_TRY(true_residual(ws, x, U, b, kappa, &rr0, s));
+        } else {
+            LQCD_CUDA(cudaMemcpyAsync(ws.r64.f->data, b->data, b->bytes, cudaMemcpyDeviceToDevice, s));
+        }
+        LQCD_CUDA(cudaMemcpyAsync(ws.p64.f->data, ws.r64.f->data, b->bytes, cudaMemcpyDeviceToDevice, s));
         P = ws.p64.f, R = ws.r64.f, T = ws.t64a.f, TMP = ws.tmpo64.f, XS = x, UU = U;
+    }
+    inf.true_rel_res = std::sqrt(rr0 / bb);
+    if (!std::isfinite(rr0)) {
+        set_error("cg: the initial residual is not finite");
+        return finish(LQCD_ENUMERIC);
+    }
+    if (rr0 <= prm.tol * prm.tol * bb) { // the guess already solves the system
+        LQCD_CUDA(cudaStreamSynchronize(s));
+        return finish(LQCD_OK);
     }
     CgScalars &h = *g_pinned.sc;
     h = CgScalars{};
-    h.rr = bb;
+    h.rr = rr0;
     h.stop2 = prm.tol * prm.tol * bb;
     h.delta2 = mixed ? prm.delta * prm.delta : 0.0;
-    h.maxrr2 = bb;
+    h.maxrr2 = rr0;
     h.maxiter = prm.maxiter;
     CgScalars *sc = (CgScalars *)ws.sc.p;
     LQCD_CUDA(cudaMemcpyAsync(sc, &h, sizeof(CgScalars), cudaMemcpyHostToDevice, s));

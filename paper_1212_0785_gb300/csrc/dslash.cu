@@ -80,17 +80,17 @@ __device__ __forceinline__ Sp<R> dslash_site(const SpinorRef<SP> &in, const Gaug
     return acc;
 }
 
-// |s|^2 of one site, summed in the working precision (an FP32 kernel stays off
-// the FP64 pipe); the sums over sites are FP64
+// |s|^2 of one site in the working precision (an FP32 kernel stays off the
+// FP64 pipe); the sums over sites are FP64
 template <typename R>
-__device__ __forceinline__ double sp_norm2(const Sp<R> &s)
+__device__ __forceinline__ R sp_norm2(const Sp<R> &s)
 {
     R n = R(0);
 #pragma unroll
     for (int a = 0; a < 4; a++)
 #pragma unroll
         for (int b = 0; b < 3; b++) n = n + norm2(s.c[a][b]);
-    return (double)n;
+    return n;
 }
 
 // ---------------------------------------------------------------- kernels
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(DS_BLOCK) dslash_xpay_kernel(SpinorRef<SP> out
 {
     if (skip && *skip) return;
     int cb = blockIdx.x * DS_BLOCK + threadIdx.x;
-    double n2[1] = {0.0};
+    R n2 = R(0);
     if (cb < g.Vh) {
         Sp<R> d = dslash_site<R, SP, GP, DAG>(in, U, g, cb, out_par);
         Sp<R> xv = x.template load_rw<R>(cb);
@@ -121,9 +121,9 @@ __global__ void __launch_bounds__(DS_BLOCK) dslash_xpay_kernel(SpinorRef<SP> out
 #pragma unroll
             for (int k = 0; k < 3; k++) d.c[a][k] = xv.c[a][k] + b * d.c[a][k];
         out.store(cb, d);
-        n2[0] = sp_norm2(d);
+        n2 = sp_norm2(d);
     }
-    if (partials) block_sum_store<1, DS_BLOCK>(n2, partials, nblocks);
+    if (partials) block_sum_store_wp<DS_BLOCK>(n2, partials);
 }
 
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, lqcd_prec XP>
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(DS_BLOCK) dslash_cg_kernel(SpinorRef<SP> in, G
     if (sc->pause) return;
     const R alpha = (R)sc->alpha;
     int cb = blockIdx.x * DS_BLOCK + threadIdx.x;
-    double n2[1] = {0.0};
+    R n2 = R(0);
     if (cb < g.Vh) {
         Sp<R> ap = dslash_site<R, SP, GP, DAG>(in, U, g, cb, out_par);
         {
@@ -164,9 +164,9 @@ __global__ void __launch_bounds__(DS_BLOCK) dslash_cg_kernel(SpinorRef<SP> in, G
 #pragma unroll
             for (int k = 0; k < 3; k++) rv.c[a][k] = rv.c[a][k] - alpha * ap.c[a][k];
         r.store(cb, rv);
-        n2[0] = sp_norm2(rv);
+        n2 = sp_norm2(rv);
     }
-    block_sum_store<1, DS_BLOCK>(n2, partials, nblocks);
+    block_sum_store_wp<DS_BLOCK>(n2, partials);
 }
 
 // ---------------------------------------------------------------- float-float kernel

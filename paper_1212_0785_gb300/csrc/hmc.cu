@@ -49,6 +49,7 @@ struct lqcd_hmc_state {
     CgWorkspace ws;
     DevBuf part, scal;
     double H0 = 0;
+    bool have_guess = false; // X holds a solution for the current phi
     // statistics of the current trajectory
     int cg_iters = 0, n_solves = 0, cg_failures = 0;
     double cg_res_max = 0;
@@ -96,7 +97,10 @@ static lqcd_field *sloppy_links(lqcd_hmc_state *st, const lqcd_hmc_params *p)
 static lqcd_status solve(lqcd_hmc_state *st, const lqcd_hmc_params *p, cudaStream_t s)
 {
     lqcd_cg_info info{};
-    lqcd_status rc = cg_solve_ws(st->ws, st->X.f, st->U, sloppy_links(st, p), st->phi.f, p->kappa, p->cg, &info, s);
+    lqcd_cg_params cg = p->cg;
+    cg.guess = (p->chrono && st->have_guess) ? 1 : 0;
+    lqcd_status rc = cg_solve_ws(st->ws, st->X.f, st->U, sloppy_links(st, p), st->phi.f, p->kappa, cg, &info, s);
+    st->have_guess = (rc == LQCD_OK || rc == LQCD_ENOCONV);
     st->cg_iters += info.iters;
     st->n_solves++;
     st->cg_res_max = std::max(st->cg_res_max, info.true_rel_res);
@@ -159,6 +163,7 @@ static double hamiltonian_from(const lqcd_hmc_state *st, const lqcd_hmc_params *
 
 static lqcd_status refresh(lqcd_hmc_state *st, const lqcd_hmc_params *p, double *H0, cudaStream_t s)
 {
+    st->have_guess = false; // a new phi: the last solution is no guess for it
     LQCD_TRY(ensure_sloppy(st, p, s));
     LQCD_TRY(momentum_refresh_dev(st->P.f, st->seed, st->chain, st->traj, s));
     double *d = (double *)st->scal.p;

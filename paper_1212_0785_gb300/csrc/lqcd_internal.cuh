@@ -810,6 +810,27 @@ __device__ __forceinline__ void block_sum_store(double (&v)[N], double *partials
     }
 }
 
+// The same for one value held in the kernel's working precision R: the warp
+// sums run in R (an FP32 kernel stays off the FP64 pipe), the warp totals are
+// summed in FP64.  Thread 0 writes partials[blockIdx.x].
+template <int BLOCK, typename R>
+__device__ __forceinline__ void block_sum_store_wp(R v, double *partials)
+{
+    static_assert(BLOCK % 32 == 0 && BLOCK <= 1024, "block size");
+    __shared__ double sh[BLOCK / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = (double)v;
+    __syncthreads();
+    if (warp == 0) {
+        double x = lane < BLOCK / 32 ? sh[lane] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+        if (lane == 0) partials[blockIdx.x] = x;
+    }
+}
+
 // Fixed-order sum of partials[k * nblocks + i] over i, by one block of 1024
 // threads; result in sums[k] (shared by the whole block after the call).
 template <int N>

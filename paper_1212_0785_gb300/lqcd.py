@@ -46,7 +46,7 @@ class Lattice(ctypes.Structure):
 
 class CgParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("sloppy", ctypes.c_int),
-                ("delta", ctypes.c_double), ("max_restarts", ctypes.c_int)]
+                ("delta", ctypes.c_double), ("max_restarts", ctypes.c_int), ("guess", ctypes.c_int)]
 
 
 class CgInfo(ctypes.Structure):
@@ -58,7 +58,7 @@ class HmcParams(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("kappa", ctypes.c_double), ("tau", ctypes.c_double),
                 ("nsteps", ctypes.c_int), ("integrator", ctypes.c_int), ("n_flavors", ctypes.c_int),
                 ("cg", CgParams), ("reunitarize", ctypes.c_int), ("metropolis", ctypes.c_int),
-                ("force_prec", ctypes.c_int)]
+                ("chrono", ctypes.c_int), ("force_prec", ctypes.c_int)]
 
 
 class TrajInfo(ctypes.Structure):
@@ -348,8 +348,8 @@ def mhat(out: Field, U: Field, inp: Field, kappa, dagger=False, stream=None):
     _check(lib().lqcd_mhat(out.h, U.h, inp.h, kappa, int(dagger), _s(stream)), "mhat")
 
 
-def cg_params(tol=1e-10, maxiter=10000, sloppy=F64, delta=0.1, max_restarts=3) -> CgParams:
-    return CgParams(tol, maxiter, sloppy, delta, max_restarts)
+def cg_params(tol=1e-10, maxiter=10000, sloppy=F64, delta=0.1, max_restarts=3, guess=False) -> CgParams:
+    return CgParams(tol, maxiter, sloppy, delta, max_restarts, int(guess))
 
 
 def cg_solve(x: Field, U: Field, b: Field, kappa, params: CgParams | None = None, U_sloppy: Field | None = None,
@@ -410,9 +410,9 @@ def spinor_dot(a: Field, b: Field, stream=None) -> float:
 # ---------------------------------------------------------------- HMC
 
 def hmc_params(beta, kappa, tau=1.0, nsteps=10, integrator=LEAPFROG, n_flavors=2, cg=None, reunitarize=True,
-               metropolis=True, force_prec=F64) -> HmcParams:
+               metropolis=True, force_prec=F64, chrono=False) -> HmcParams:
     return HmcParams(beta, kappa, tau, nsteps, integrator, n_flavors, cg or cg_params(), int(reunitarize),
-                     int(metropolis), int(force_prec))
+                     int(metropolis), int(chrono), int(force_prec))
 
 
 class HmcState:

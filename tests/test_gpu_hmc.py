@@ -101,3 +101,19 @@ def test_mixed_trajectory_fp32_forces_close_to_fp64():
     assert gm["accepted"] == g64["accepted"] == 1
     assert np.max(np.abs(Um - U64)) < 1e-5
     assert gm["cg_true_rel_res_max"] <= 1e-10
+
+
+@pytest.mark.parametrize("sloppy", [lqcd.F64, lqcd.F16N])
+def test_chronological_guess_trajectory(sloppy):
+    """solves after the first of a trajectory start from the previous solution:
+    the same trajectory to the solver tolerance, fewer CG iterations, and the
+    final Hamiltonian solve starts converged"""
+    Uh = orc.gauge_start(DIMS, seed=1, eps=0.3)
+    cg = lqcd.cg_params(tol=1e-12, sloppy=sloppy, delta=0.01)
+    base = dict(beta=5.6, kappa=0.156, tau=0.5, nsteps=8, integrator=lqcd.OMELYAN, cg=cg)
+    U0, (g0,) = _run_gpu(Uh, lqcd.hmc_params(**base), 1, 1)
+    U1, (g1,) = _run_gpu(Uh, lqcd.hmc_params(**base, chrono=True), 1, 1)
+    assert abs(g1["dH"] - g0["dH"]) < 1e-7, (g1["dH"], g0["dH"])
+    assert np.max(np.abs(U1 - U0)) < 1e-9
+    assert g1["cg_iters"] < 0.85 * g0["cg_iters"], (g1["cg_iters"], g0["cg_iters"])
+    assert g1["n_solves"] == g0["n_solves"] == 18 and g1["cg_true_rel_res_max"] <= 1e-12

@@ -177,3 +177,33 @@ def test_cg_mixed_tight_tolerance(sloppy):
     assert rc == lqcd.OK and info.true_rel_res <= 1e-12
     r = b - orc.mdagm(dims, Uh, kappa, full_from_half(x.download(), dims, 0))
     assert np.linalg.norm(r) <= 1.05e-12 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("sloppy", [lqcd.F64, lqcd.F16N])
+def test_cg_warm_start(sloppy):
+    """x on entry as the initial guess: the exact solution needs no iteration,
+    a perturbed one converges in fewer iterations than x0 = 0 to the same true
+    residual"""
+    dims = (8, 6, 6, 12)
+    kappa = 0.156
+    Uh = orc.gauge_start(dims, seed=2, eps=0.3)
+    bh = inputs.random_spinor(dims, 24, parity=0)
+    xr, _, _, _ = orc.cg(dims, Uh, kappa, bh, tol=1e-13)
+    if sloppy == lqcd.F64:
+        U, Us = lqcd.gauge_field(dims).upload(Uh), None
+    else:
+        U, Us = upload_gauge(Uh, dims, sloppy)
+    b = upload_half(bh, dims, 0)
+    prm = dict(tol=1e-10, sloppy=sloppy, delta=0.01)
+    x = lqcd.spinor_field(dims, 0)
+    rc, cold = lqcd.cg_solve(x, U, b, kappa, lqcd.cg_params(**prm), U_sloppy=Us)
+    assert rc == lqcd.OK
+    x.upload(half(xr, dims, 0))
+    rc, exact = lqcd.cg_solve(x, U, b, kappa, lqcd.cg_params(**prm, guess=True), U_sloppy=Us)
+    assert rc == lqcd.OK and exact.iters == 0 and exact.true_rel_res <= 1e-10
+    noise = 1e-4 * inputs.random_spinor(dims, 25, parity=0)
+    x.upload(half(xr + noise, dims, 0))
+    rc, warm = lqcd.cg_solve(x, U, b, kappa, lqcd.cg_params(**prm, guess=True), U_sloppy=Us)
+    assert rc == lqcd.OK and warm.true_rel_res <= 1e-10 and 0 < warm.iters < cold.iters
+    r = bh - orc.mdagm(dims, Uh, kappa, full_from_half(x.download(), dims, 0))
+    assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(bh)
