@@ -425,12 +425,94 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------- batched chains
+
+CHAINS64 = [(8, 8, 8, 8)] * 32 + [(12, 12, 12, 12)] * 24 + [(16, 16, 16, 32)] * 8
+
+
+def run_chains(args):
+    """64 independent chains of uneven volume (32 at 8^4, 24 at 12^4, 8 at
+    16^3x32), beta in [5.6, 5.9] and kappa in [0.150, 0.157] spread over the
+    chains, Philox seed 100 + i, start eps 0.3, leapfrog 10 steps, tau 1,
+    FP16+norm mixed solver, FP32 MD; all chains advanced together (their
+    solves in shared launches) against the same chains one after another."""
+    import torch
+
+    from paper_1212_0785_gb300 import lqcd
+
+    torch.cuda.set_device(0)
+    n = len(CHAINS64)
+    betas = np.linspace(5.6, 5.9, n)
+    kappas = np.linspace(0.150, 0.157, n)
+    cg = lqcd.cg_params(tol=1e-10, maxiter=20000, sloppy=lqcd.F16N, delta=args.delta)
+    params = [lqcd.hmc_params(float(betas[i]), float(kappas[i]), 1.0, 10, lqcd.LEAPFROG, cg=cg,
+                              force_prec=lqcd.F32, chrono=bool(args.chrono)) for i in range(n)]
+
+    def make():
+        fields, states = [], []
+        for i, dims in enumerate(CHAINS64):
+            U = lqcd.gauge_field(dims)
+            lqcd.gauge_start(U, 100 + i, 0.3)
+            fields.append(U)
+            states.append(lqcd.HmcState(U, seed=100 + i, chain=i))
+        return fields, states
+
+    stream = torch.cuda.current_stream()
+    fields, states = make()
+    batch = lqcd.Batch(states)
+    for _ in range(args.warmup):
+        batch.trajectory(params)
+    torch.cuda.synchronize()
+    launches0 = lqcd.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [batch.trajectory(params) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    launches = lqcd.launch_count() - launches0
+    batch.close()
+    # the same chains, one trajectory after another, each alone
+    fields2, states2 = make()
+    for i in range(n):
+        states2[i].trajectory(params[i])
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for i in range(n):
+            states2[i].trajectory(params[i])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) / 1e3
+    sites = sum(int(np.prod(d)) for d in CHAINS64)
+    line = {"metric": "chain-trajectories/s", "value": n * args.steps / t_batch, "unit": "chain-trajectories/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 math (f16n solver storage, f32 forces); f64 master fields, residuals, dH",
+            "data": "synthetic",
+            "config": {"workload": "chains64_8^4x32_12^4x24_16^3x32x8", "chains": n, "sites_total": sites,
+                       "beta": [5.6, 5.9], "kappa": [0.150, 0.157], "integrator": "leapfrog", "nsteps": 10,
+                       "tau": 1.0, "start_eps": 0.3, "initial_guess": "chronological" if args.chrono else "zero"},
+            "gpu_launches": launches,
+            "sequential": {"value": n * args.steps / t_seq, "ms_per_step": t_seq / args.steps * 1e3},
+            "batched_speedup": t_seq / t_batch,
+            "physics": {"acceptance": float(np.mean([f["accepted"] for it in infos for f in it])),
+                        "cg_iters_per_chain_traj": float(np.mean([f["cg_iters"] for it in infos for f in it])),
+                        "cg_true_rel_res_max": max(f["cg_true_rel_res_max"] for it in infos for f in it)}}
+    print(json.dumps(line))
+    for st in states + states2:
+        st.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=("hmc32", "chains64"), default="hmc32",
+                    help="hmc32: the 32^3x64 trajectory (default); chains64: 64 batched chains")
     ap.add_argument("--sloppy", choices=("f32", "f16n", "bf16"), default="f16n")
     ap.add_argument("--delta", type=float, default=0.003)
     ap.add_argument("--force-prec", choices=("f64", "f32"), default="f32")
@@ -446,6 +528,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "chains64":
+        return run_chains(args)
     return run_ours(args)
 
 

@@ -388,6 +388,37 @@ lqcd_status lqcd_md_step(lqcd_hmc_state *s, const lqcd_hmc_params *p, void *stre
 lqcd_status lqcd_hmc_trajectory(lqcd_hmc_state *s, const lqcd_hmc_params *p, lqcd_traj_info *info,
                                 void *stream);
 
+/* ------------------------------------------------------------ batched solves and chains */
+
+/* n independent mixed-precision solves Mhat^dag Mhat x[i] = b[i] (each on its
+ * own lattice, links U[i] with sloppy copy U_sloppy[i], kappa[i]) with shared
+ * launches: every kernel of a CG iteration covers all systems that have not
+ * converged, each system reading its own geometry, fields and scalars.  Each
+ * system's iterates equal those of lqcd_cg_solve on it alone.  params (one
+ * for all) must be mixed precision (sloppy F32, F16N or BF16); info[i]
+ * receives system i's result.  Returns the first non-OK status of a system
+ * (LQCD_ENOCONV if one hit maxiter) after all finished.  Small lattices, each
+ * filling a few SMs alone, fill the GPU together. */
+lqcd_status lqcd_cg_solve_batch(int n, lqcd_field *const *x, const lqcd_field *const *U,
+                                const lqcd_field *const *U_sloppy, const lqcd_field *const *b, const double *kappa,
+                                const lqcd_cg_params *params, lqcd_cg_info *info, void *stream);
+
+/* A batch of independent Markov chains (each an lqcd_hmc_state, on lattices of
+ * any size) advanced together: per molecular-dynamics force evaluation every
+ * chain's solve runs in shared launches (lqcd_cg_solve_batch's engine, each
+ * chunk of iterations replayed as a CUDA graph).  The batch borrows the states;
+ * they must outlive it. */
+typedef struct lqcd_batch lqcd_batch;
+lqcd_status lqcd_batch_create(lqcd_hmc_state *const *chains, int n, lqcd_batch **out);
+lqcd_status lqcd_batch_destroy(lqcd_batch *batch);
+
+/* One trajectory of every chain; params[i] and info[i] belong to chain i.  All
+ * chains must share integrator, nsteps, tau, solver and force precision (beta,
+ * kappa, seeds differ freely), have two flavours and a mixed-precision solver.
+ * Each chain's trajectory equals lqcd_hmc_trajectory on that chain alone. */
+lqcd_status lqcd_batch_trajectory(lqcd_batch *batch, const lqcd_hmc_params *params, lqcd_traj_info *info,
+                                  void *stream);
+
 #ifdef __cplusplus
 }
 #endif

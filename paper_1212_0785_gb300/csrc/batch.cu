@@ -1,0 +1,398 @@
+// batch.cu -- many CG solves at once.
+//
+// Independent systems Mhat^dag Mhat x_i = b_i (each on its own lattice, gauge
+// field and kappa: the solves of a batch of Markov chains, or the right-hand
+// sides of queued solve requests) share their launches: each kernel of a CG
+// iteration runs over the union of the systems' sites, every block belonging to
+// one system (a block -> system map) and reading that system's geometry,
+// fields and scalars from a descriptor table.  Small lattices, which alone fill
+// a few of the 152 SMs, then fill the GPU together, and the launch count per
+// iteration does not grow with the number of systems.  Per-system arithmetic
+// is that of the single-system kernels (same block size, same reduction order),
+// so every system's iterates are bitwise those of its solve alone.
+//
+// A chunk of iterations is captured once as a CUDA graph and replayed while the
+// set of systems is unchanged; a system whose device pause flag is raised (a
+// reliable update, convergence, maxiter) is handled by its own CgRun between
+// chunks, and leaves the batch when done.  Systems can be added between chunks.
+#include <algorithm>
+
+#include "batch.cuh"
+#include "dslash_site.cuh"
+
+namespace lqcd {
+
+constexpr int BCHUNK = 4;
+
+// ---------------------------------------------------------------- kernels
+
+// step 0: tmp = D_oe p; step 2: tmp = D_oe^dag-hop t
+template <lqcd_prec SP, bool DAG>
+__global__ void __launch_bounds__(DS_BLOCK) batch_dslash_plain(const SysDesc<SP> *sys, const int2 *bmap)
+{
+    const int2 m = bmap[blockIdx.x];
+    const SysDesc<SP> &d = sys[m.x];
+    if (d.sc->pause) return;
+    int cb = m.y * DS_BLOCK + threadIdx.x;
+    if (cb >= d.g.Vh) return;
+    const SpinorRef<SP> &in = DAG ? d.t : d.p;
+    d.tmp.store(cb, dslash_site<float, SP, SP, DAG>(in, d.U, d.g, cb, 1));
+}
+
+// step 1: t = p - kappa^2 D_eo tmp, block sums of |t|^2
+template <lqcd_prec SP>
+__global__ void __launch_bounds__(DS_BLOCK) batch_dslash_xpay(const SysDesc<SP> *sys, const int2 *bmap)
+{
+    const int2 m = bmap[blockIdx.x];
+    const SysDesc<SP> &d = sys[m.x];
+    if (d.sc->pause) return;
+    int cb = m.y * DS_BLOCK + threadIdx.x;
+    float n2 = 0.f;
+    if (cb < d.g.Vh) {
+        Sp<float> v = dslash_site<float, SP, SP, false>(d.tmp, d.U, d.g, cb, 0);
+        Sp<float> pv = d.p.template load_rw<float>(cb);
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) v.c[a][k] = pv.c[a][k] + d.b * v.c[a][k];
+        d.t.store(cb, v);
+        n2 = sp_norm2(v);
+    }
+    // the partial of block m.y of this system, as in the single-system kernel
+    double *part = d.partials;
+    __shared__ double sh[DS_BLOCK / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) n2 += __shfl_down_sync(0xffffffffu, n2, off);
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = (double)n2;
+    __syncthreads();
+    if (warp == 0) {
+        double x = lane < DS_BLOCK / 32 ? sh[lane] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+        if (lane == 0) part[m.y] = x;
+    }
+}
+
+// step 3: Ap = t - kappa^2 D_eo^dag-hop tmp; xs += alpha p; r -= alpha Ap; block sums of |r|^2
+template <lqcd_prec SP>
+__global__ void __launch_bounds__(DS_BLOCK) batch_dslash_cg(const SysDesc<SP> *sys, const int2 *bmap)
+{
+    const int2 m = bmap[blockIdx.x];
+    const SysDesc<SP> &d = sys[m.x];
+    if (d.sc->pause) return;
+    const float alpha = (float)d.sc->alpha;
+    int cb = m.y * DS_BLOCK + threadIdx.x;
+    float n2 = 0.f;
+    if (cb < d.g.Vh) {
+        Sp<float> ap = dslash_site<float, SP, SP, true>(d.tmp, d.U, d.g, cb, 0);
+        {
+            Sp<float> tv = d.t.template load_rw<float>(cb);
+#pragma unroll
+            for (int a = 0; a < 4; a++)
+#pragma unroll
+                for (int k = 0; k < 3; k++) ap.c[a][k] = tv.c[a][k] + d.b * ap.c[a][k];
+        }
+        Sp<float> pv = d.p.template load_rw<float>(cb);
+        {
+            Sp<float> xv = d.xs.template load_rw<float>(cb);
+#pragma unroll
+            for (int a = 0; a < 4; a++)
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    xv.c[a][k].re += alpha * pv.c[a][k].re;
+                    xv.c[a][k].im += alpha * pv.c[a][k].im;
+                }
+            d.xs.store(cb, xv);
+        }
+        Sp<float> rv = d.r.template load_rw<float>(cb);
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) rv.c[a][k] = rv.c[a][k] - alpha * ap.c[a][k];
+        d.r.store(cb, rv);
+        n2 = sp_norm2(rv);
+    }
+    double *part = d.partials;
+    __shared__ double sh[DS_BLOCK / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) n2 += __shfl_down_sync(0xffffffffu, n2, off);
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = (double)n2;
+    __syncthreads();
+    if (warp == 0) {
+        double x = lane < DS_BLOCK / 32 ? sh[lane] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+        if (lane == 0) part[m.y] = x;
+    }
+}
+
+// one block per system: pAp and alpha (step 1b), or rr_new, beta and the pause
+// decision (step 3b) -- the logic of cg_pap_kernel / cg_rr_kernel
+template <lqcd_prec SP, bool RR>
+__global__ void batch_scalars(const SysDesc<SP> *sys)
+{
+    const SysDesc<SP> &d = sys[blockIdx.x];
+    CgScalars *sc = d.sc;
+    if (sc->pause) return;
+    double s[1];
+    final_sum_block<1>(d.partials, d.nblocks, s);
+    if (threadIdx.x != 0) return;
+    if (!RR) {
+        double pAp = s[0];
+        sc->pAp = pAp;
+        if (!(pAp > 0.0) || !isfinite(pAp)) {
+            sc->alpha = 0.0;
+            sc->pause = 1;
+            sc->reason = PAUSE_NONFINITE;
+        } else {
+            sc->alpha = sc->rr / pAp;
+        }
+        return;
+    }
+    double rr_new = s[0];
+    sc->rr_new = rr_new;
+    sc->iter += 1;
+    int reason = PAUSE_NONE;
+    if (!isfinite(rr_new))
+        reason = PAUSE_NONFINITE;
+    else if (rr_new <= sc->stop2)
+        reason = PAUSE_CONVERGED;
+    else if (sc->delta2 > 0.0 && rr_new < sc->delta2 * sc->maxrr2)
+        reason = PAUSE_RELIABLE;
+    else if (sc->iter >= sc->maxiter)
+        reason = PAUSE_MAXITER;
+    if (reason != PAUSE_NONE) {
+        sc->pause = 1;
+        sc->reason = reason;
+    } else {
+        sc->beta = rr_new / sc->rr;
+        sc->rr = rr_new;
+        sc->maxrr2 = fmax(sc->maxrr2, rr_new);
+    }
+}
+
+// step 4: p = r + beta p
+template <lqcd_prec SP>
+__global__ void __launch_bounds__(DS_BLOCK) batch_p_update(const SysDesc<SP> *sys, const int2 *bmap)
+{
+    const int2 m = bmap[blockIdx.x];
+    const SysDesc<SP> &d = sys[m.x];
+    if (d.sc->pause) return;
+    int cb = m.y * DS_BLOCK + threadIdx.x;
+    if (cb >= d.g.Vh) return;
+    float beta = (float)d.sc->beta;
+    Sp<float> pv = d.p.template load_rw<float>(cb);
+    Sp<float> rv = d.r.template load_rw<float>(cb);
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int k = 0; k < 3; k++) pv.c[a][k] = rv.c[a][k] + beta * pv.c[a][k];
+    d.p.store(cb, pv);
+}
+
+// ---------------------------------------------------------------- host side
+
+template <lqcd_prec SP>
+static SysDesc<SP> make_desc(const CgRun &r)
+{
+    SysDesc<SP> d;
+    d.g = make_geo(r.x->lat);
+    d.p = spinor_ref<SP>(r.P);
+    d.r = spinor_ref<SP>(r.R);
+    d.t = spinor_ref<SP>(r.T);
+    d.tmp = spinor_ref<SP>(r.TMP);
+    d.xs = spinor_ref<LQCD_F32>(r.XS);
+    d.U = gauge_ref<SP>(r.UU);
+    d.b = (float)(-r.k2);
+    d.sc = r.sc;
+    d.partials = (double *)r.ws->partials.p;
+    d.nblocks = dslash_blocks(r.Vh);
+    return d;
+}
+
+BatchSolver::~BatchSolver() { release(); }
+
+void BatchSolver::drop_graph()
+{
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+}
+
+template <lqcd_prec SP>
+lqcd_status BatchSolver::enqueue_chunk(cudaStream_t s)
+{
+    const SysDesc<SP> *d = (const SysDesc<SP> *)descs.p;
+    const int2 *bm = (const int2 *)bmap.p;
+    int n = (int)active.size();
+    for (int k = 0; k < BCHUNK; k++) {
+        batch_dslash_plain<SP, false><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
+        batch_dslash_xpay<SP><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
+        batch_scalars<SP, false><<<n, 1024, 0, s>>>(d);
+        batch_dslash_plain<SP, true><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
+        batch_dslash_cg<SP><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
+        batch_scalars<SP, true><<<n, 1024, 0, s>>>(d);
+        batch_p_update<SP><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
+    }
+    LQCD_CUDA(cudaGetLastError());
+    return LQCD_OK;
+}
+
+template <lqcd_prec SP>
+lqcd_status BatchSolver::build_tables(cudaStream_t s)
+{
+    std::vector<SysDesc<SP>> hd;
+    std::vector<int2> hb;
+    for (size_t i = 0; i < active.size(); i++) {
+        const CgRun &r = *active[i];
+        hd.push_back(make_desc<SP>(r));
+        int nb = dslash_blocks(r.Vh);
+        for (int k = 0; k < nb; k++) hb.push_back(make_int2((int)i, k));
+    }
+    nblocks_total = (int)hb.size();
+    if (descs.bytes < hd.size() * sizeof(SysDesc<SP>)) LQCD_TRY(descs.alloc(hd.size() * sizeof(SysDesc<SP>), s));
+    if (bmap.bytes < hb.size() * sizeof(int2)) LQCD_TRY(bmap.alloc(hb.size() * sizeof(int2), s));
+    LQCD_CUDA(cudaMemcpyAsync(descs.p, hd.data(), hd.size() * sizeof(SysDesc<SP>), cudaMemcpyHostToDevice, s));
+    LQCD_CUDA(cudaMemcpyAsync(bmap.p, hb.data(), hb.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    LQCD_CUDA(cudaStreamSynchronize(s)); // host vectors go out of scope
+    drop_graph();
+    if (use_graph) {
+        // capture on a private stream (the caller's may be the legacy default
+        // stream, which cannot be captured); the graph is launched on s
+        if (!capture_stream) LQCD_CUDA(cudaStreamCreateWithFlags(&capture_stream, cudaStreamNonBlocking));
+        LQCD_CUDA(cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
+        lqcd_status rc = enqueue_chunk<SP>(capture_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(capture_stream, &g);
+        if (rc != LQCD_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        LQCD_CUDA(e);
+        graph = g;
+        LQCD_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    }
+    return LQCD_OK;
+}
+
+template <lqcd_prec SP>
+lqcd_status BatchSolver::run_all(std::vector<CgRun *> &runs, cudaStream_t s)
+{
+    active.clear();
+    for (CgRun *r : runs)
+        if (!r->done) active.push_back(r);
+    bool changed = true;
+    while (!active.empty()) {
+        if (changed) {
+            LQCD_TRY(build_tables<SP>(s));
+            changed = false;
+        }
+        if (use_graph) {
+            LQCD_CUDA(cudaGraphLaunch(exec, s));
+            g_launches.fetch_add(7 * BCHUNK, std::memory_order_relaxed);
+        } else {
+            LQCD_TRY(enqueue_chunk<SP>(s));
+            g_launches.fetch_add(7 * BCHUNK, std::memory_order_relaxed);
+        }
+        // read every active system's scalars (they are not contiguous: one copy each)
+        if (pinned_n < active.size()) {
+            if (pinned_h) cudaFreeHost(pinned_h);
+            pinned_h = nullptr;
+            pinned_n = 0;
+            LQCD_CUDA(cudaMallocHost((void **)&pinned_h, sizeof(CgScalars) * active.size()));
+            pinned_n = active.size();
+        }
+        for (size_t i = 0; i < active.size(); i++)
+            LQCD_CUDA(cudaMemcpyAsync(&pinned_h[i], active[i]->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+        LQCD_CUDA(cudaStreamSynchronize(s));
+        std::vector<CgRun *> still;
+        for (size_t i = 0; i < active.size(); i++) {
+            CgRun *r = active[i];
+            if (pinned_h[i].pause) r->on_pause(pinned_h[i], s);
+            if (r->done)
+                changed = true;
+            else
+                still.push_back(r);
+        }
+        active.swap(still);
+    }
+    return LQCD_OK;
+}
+
+BatchSolver::BatchSolver() = default;
+
+lqcd_status BatchSolver::solve(std::vector<CgRun *> &runs, cudaStream_t s)
+{
+    if (runs.empty()) return LQCD_OK;
+    lqcd_prec p = runs[0]->prm.sloppy;
+    for (CgRun *r : runs)
+        LQCD_REQUIRE(r->prm.sloppy == p, "batched solve: every system must use the same sloppy precision");
+    switch (p) {
+    case LQCD_F16N: return run_all<LQCD_F16N>(runs, s);
+    case LQCD_F32: return run_all<LQCD_F32>(runs, s);
+    case LQCD_BF16: return run_all<LQCD_BF16>(runs, s);
+    default: set_error("batched solve: the sloppy precision must be F32, F16N or BF16"); return LQCD_EINVAL;
+    }
+}
+
+void BatchSolver::release()
+{
+    drop_graph();
+    if (capture_stream) cudaStreamDestroy(capture_stream);
+    capture_stream = nullptr;
+    if (pinned_h) cudaFreeHost(pinned_h);
+    pinned_h = nullptr;
+    pinned_n = 0;
+}
+
+} // namespace lqcd
+
+using namespace lqcd;
+
+// ---------------------------------------------------------------- C ABI: batched solve
+
+extern "C" lqcd_status lqcd_cg_solve_batch(int n, lqcd_field *const *x, const lqcd_field *const *U,
+                                           const lqcd_field *const *U_sloppy, const lqcd_field *const *b,
+                                           const double *kappa, const lqcd_cg_params *params, lqcd_cg_info *info,
+                                           void *stream)
+{
+    LQCD_REQUIRE(n >= 0 && (n == 0 || (x && U && U_sloppy && b && kappa && params)), "cg_solve_batch: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<std::unique_ptr<CgWorkspace>> wss;
+    std::vector<CgRun> runs(n);
+    std::vector<CgRun *> ptrs;
+    DevBuf scal;
+    LQCD_TRY(scal.alloc(sizeof(CgScalars) * std::max(n, 1), s));
+    for (int i = 0; i < n; i++) {
+        LQCD_REQUIRE(x[i] && U[i] && U_sloppy[i] && b[i], "cg_solve_batch: NULL field in system %d", i);
+        LQCD_REQUIRE(x[i]->kind == LQCD_SPINOR_EVEN && b[i]->kind == LQCD_SPINOR_EVEN && x[i]->prec == LQCD_F64 &&
+                         b[i]->prec == LQCD_F64 && x[i] != b[i],
+                     "cg_solve_batch: system %d needs distinct EVEN FP64 x and b", i);
+        LQCD_REQUIRE(U[i]->kind == LQCD_GAUGE && U[i]->prec == LQCD_F64 && same_lattice(U[i]->lat, x[i]->lat) &&
+                         same_lattice(U[i]->lat, b[i]->lat) && same_lattice(U[i]->lat, U_sloppy[i]->lat),
+                     "cg_solve_batch: system %d has inconsistent fields", i);
+        LQCD_REQUIRE(params->sloppy != LQCD_F64 && params->delta > 0 && params->delta < 1 && params->tol > 0 &&
+                         params->maxiter > 0,
+                     "cg_solve_batch: needs a mixed-precision solver (sloppy F32/F16N/BF16, 0 < delta < 1)");
+        wss.emplace_back(new CgWorkspace());
+        LQCD_TRY(wss.back()->ensure(x[i]->lat, params->sloppy, s));
+        CgRun &r = runs[i];
+        r.ws = wss.back().get(), r.x = x[i], r.U = U[i], r.Us = U_sloppy[i], r.b = b[i], r.kappa = kappa[i];
+        r.prm = *params;
+        r.start(s, (CgScalars *)scal.p + i);
+        ptrs.push_back(&r);
+    }
+    BatchSolver bs;
+    lqcd_status rc = bs.solve(ptrs, s);
+    cudaStreamSynchronize(s);
+    bs.release();
+    lqcd_status worst = rc;
+    for (int i = 0; i < n; i++) {
+        if (info) info[i] = runs[i].inf;
+        if (worst == LQCD_OK && runs[i].status != LQCD_OK) worst = runs[i].status;
+    }
+    return worst;
+}

@@ -328,151 +328,210 @@ static lqcd_status true_residual(CgWorkspace &ws, const lqcd_field *x, const lqc
     return LQCD_OK;
 }
 
-lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, const lqcd_field *Us,
-                        const lqcd_field *b, double kappa, const lqcd_cg_params &prm, lqcd_cg_info *info,
-                        cudaStream_t s)
-{
-    auto t_start = std::chrono::steady_clock::now();
-    const bool mixed = prm.sloppy != LQCD_F64;
-    LQCD_TRY(ws.ensure(x->lat, prm.sloppy, s));
-    LQCD_TRY(pinned());
-    int Vh = x->Vh;
-    double k2 = kappa * kappa;
+// ---------------------------------------------------------------- one solve as a state machine
 
-    LQCD_TRY(spinor_dot_dev(b, b, (double *)ws.scalars.p, ws.partials, s));
-    LQCD_TRY(read_scalars((double *)ws.scalars.p, g_pinned.d, 1, s));
-    double bb = g_pinned.d[0];
+lqcd_status CgRun::fail(lqcd_status st)
+{
+    done = true;
+    status = st;
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+}
+
+lqcd_status CgRun::succeed()
+{
+    done = true;
+    status = LQCD_OK;
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return LQCD_OK;
+}
+
+lqcd_status CgRun::start(cudaStream_t s, CgScalars *sc_dev)
+{
+    t0 = std::chrono::steady_clock::now();
+    sc = sc_dev;
+    done = false;
+    status = LQCD_OK;
+    inf = lqcd_cg_info{0, 0, 0.0, 0.0};
+    mixed = prm.sloppy != LQCD_F64;
+    lqcd_status rc = start_impl(s);
+    if (rc != LQCD_OK) return fail(rc);
+    return LQCD_OK;
+}
+
+lqcd_status CgRun::start_impl(cudaStream_t s)
+{
+    CgWorkspace &w = *ws;
+    LQCD_TRY(w.ensure(x->lat, prm.sloppy, s));
+    LQCD_TRY(pinned());
+    Vh = x->Vh;
+    k2 = kappa * kappa;
+    LQCD_TRY(spinor_dot_dev(b, b, (double *)w.scalars.p, w.partials, s));
+    LQCD_TRY(read_scalars((double *)w.scalars.p, g_pinned.d, 1, s));
+    bb = g_pinned.d[0];
     if (!prm.guess) LQCD_CUDA(cudaMemsetAsync(x->data, 0, x->bytes, s));
-    lqcd_cg_info inf{0, 0, 0.0, 0.0};
-    auto finish = [&](lqcd_status st) {
-        inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-        if (info) *info = inf;
-        return st;
-    };
     if (!std::isfinite(bb)) {
         set_error("cg: |b|^2 is not finite");
-        return finish(LQCD_ENUMERIC);
+        return LQCD_ENUMERIC;
     }
     if (bb == 0.0) {
         LQCD_CUDA(cudaMemsetAsync(x->data, 0, x->bytes, s));
         LQCD_CUDA(cudaStreamSynchronize(s));
-        return finish(LQCD_OK);
+        succeed();
+        return LQCD_OK;
     }
-
-    lqcd_field *P, *R, *T, *TMP, *XS;
-    const lqcd_field *UU;
     double rr0 = bb;
     if (mixed) {
         LQCD_REQUIRE(Us && Us->kind == LQCD_GAUGE && Us->prec == prm.sloppy && Us->recon == 12,
                      "cg: mixed solve needs a 12-real link copy in the sloppy precision");
-        split_gauge_kernel<<<nblocks_for(8L * Vh, BB), BB, 0, s>>>(gauge_ref<PREC_DF>(ws.Udf.f),
+        split_gauge_kernel<<<nblocks_for(8L * Vh, BB), BB, 0, s>>>(gauge_ref<PREC_DF>(w.Udf.f),
                                                                    gauge_ref<LQCD_F64>(U), Vh);
         LQCD_LAUNCHED();
-        LQCD_TRY((convert_spinor<LQCD_F64, PREC_DF, double>(ws.bdf.f, b, s)));
-        LQCD_CUDA(cudaMemsetAsync(ws.xs.f->data, 0, ws.xs.f->bytes, s));
+        LQCD_TRY((convert_spinor<LQCD_F64, PREC_DF, double>(w.bdf.f, b, s)));
+        LQCD_CUDA(cudaMemsetAsync(w.xs.f->data, 0, w.xs.f->bytes, s));
         if (prm.guess) { // r = b - A x0, accurately
-            LQCD_TRY((convert_spinor<LQCD_F64, PREC_DF, double>(ws.xdf.f, x, s)));
-            LQCD_TRY(true_residual_df(ws, kappa, &rr0, s));
-            LQCD_TRY(df_to_sloppy(ws.rs.f, ws.rdf.f, s));
-            LQCD_TRY(lqcd_field_copy(ws.ps.f, ws.rs.f, s));
+            LQCD_TRY((convert_spinor<LQCD_F64, PREC_DF, double>(w.xdf.f, x, s)));
+            LQCD_TRY(true_residual_df(w, kappa, &rr0, s));
+            LQCD_TRY(df_to_sloppy(w.rs.f, w.rdf.f, s));
+            LQCD_TRY(lqcd_field_copy(w.ps.f, w.rs.f, s));
         } else {
-            LQCD_CUDA(cudaMemsetAsync(ws.xdf.f->data, 0, ws.xdf.f->bytes, s));
-            LQCD_TRY(lqcd_field_copy(ws.rs.f, b, s));
-            LQCD_TRY(lqcd_field_copy(ws.ps.f, b, s));
+            LQCD_CUDA(cudaMemsetAsync(w.xdf.f->data, 0, w.xdf.f->bytes, s));
+            LQCD_TRY(lqcd_field_copy(w.rs.f, b, s));
+            LQCD_TRY(lqcd_field_copy(w.ps.f, b, s));
         }
-        P = ws.ps.f, R = ws.rs.f, T = ws.ts.f, TMP = ws.tmpos.f, XS = ws.xs.f, UU = Us;
+        P = w.ps.f, R = w.rs.f, T = w.ts.f, TMP = w.tmpos.f, XS = w.xs.f, UU = Us;
     } else {
         if (prm.guess) {
-            LQCD_TRY(true_residual(ws, x, U, b, kappa, &rr0, s));
+            LQCD_TRY(true_residual(w, x, U, b, kappa, &rr0, s));
         } else {
-            LQCD_CUDA(cudaMemcpyAsync(ws.r64.f->data, b->data, b->bytes, cudaMemcpyDeviceToDevice, s));
+            LQCD_CUDA(cudaMemcpyAsync(w.r64.f->data, b->data, b->bytes, cudaMemcpyDeviceToDevice, s));
         }
-        LQCD_CUDA(cudaMemcpyAsync(ws.p64.f->data, ws.r64.f->data, b->bytes, cudaMemcpyDeviceToDevice, s));
-        P = ws.p64.f, R = ws.r64.f, T = ws.t64a.f, TMP = ws.tmpo64.f, XS = x, UU = U;
+        LQCD_CUDA(cudaMemcpyAsync(w.p64.f->data, w.r64.f->data, b->bytes, cudaMemcpyDeviceToDevice, s));
+        P = w.p64.f, R = w.r64.f, T = w.t64a.f, TMP = w.tmpo64.f, XS = x, UU = U;
     }
     inf.true_rel_res = std::sqrt(rr0 / bb);
     if (!std::isfinite(rr0)) {
         set_error("cg: the initial residual is not finite");
-        return finish(LQCD_ENUMERIC);
+        return LQCD_ENUMERIC;
     }
     if (rr0 <= prm.tol * prm.tol * bb) { // the guess already solves the system
         LQCD_CUDA(cudaStreamSynchronize(s));
-        return finish(LQCD_OK);
+        succeed();
+        return LQCD_OK;
     }
-    CgScalars &h = *g_pinned.sc;
-    h = CgScalars{};
-    h.rr = rr0;
-    h.stop2 = prm.tol * prm.tol * bb;
-    h.delta2 = mixed ? prm.delta * prm.delta : 0.0;
-    h.maxrr2 = rr0;
-    h.maxiter = prm.maxiter;
-    CgScalars *sc = (CgScalars *)ws.sc.p;
-    LQCD_CUDA(cudaMemcpyAsync(sc, &h, sizeof(CgScalars), cudaMemcpyHostToDevice, s));
-    LQCD_CUDA(cudaStreamSynchronize(s)); // h is reused below
+    h0 = CgScalars{};
+    h0.rr = rr0;
+    h0.stop2 = prm.tol * prm.tol * bb;
+    h0.delta2 = mixed ? prm.delta * prm.delta : 0.0;
+    h0.maxrr2 = rr0;
+    h0.maxiter = prm.maxiter;
+    LQCD_CUDA(cudaMemcpyAsync(sc, &h0, sizeof(CgScalars), cudaMemcpyHostToDevice, s));
+    LQCD_CUDA(cudaStreamSynchronize(s)); // h0 may be rewritten before the copy otherwise
+    return LQCD_OK;
+}
 
-    double *partials = (double *)ws.partials.p;
+lqcd_status CgRun::iterate(cudaStream_t s)
+{
+    double *partials = (double *)ws->partials.p;
     int nbd = dslash_blocks(Vh);
     const int *skip = &sc->pause;
-    double rr_true = bb;
-    for (;;) {
-        for (int k = 0; k < CG_CHUNK; k++) {
-            LQCD_TRY(dslash_plain(TMP, UU, P, 0, skip, s));
-            LQCD_TRY(dslash_xpay(T, UU, TMP, 0, P, -k2, partials, skip, s));
-            cg_pap_kernel<<<1, 1024, 0, s>>>(partials, nbd, sc);
-            LQCD_LAUNCHED();
-            LQCD_TRY(dslash_plain(TMP, UU, T, 1, skip, s));
-            LQCD_TRY(dslash_cg(UU, TMP, 1, T, -k2, XS, R, P, partials, sc, s));
-            cg_rr_kernel<<<1, 1024, 0, s>>>(partials, nbd, sc);
-            LQCD_LAUNCHED();
-            LQCD_TRY(launch_p_update(P, R, sc, s));
-        }
-        LQCD_CUDA(cudaMemcpyAsync(&h, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
-        LQCD_CUDA(cudaStreamSynchronize(s));
-        if (!h.pause) continue;
-        inf.iters = h.iter;
-        if (h.reason == PAUSE_NONFINITE) {
-            set_error("cg: non-finite value after %d iterations", h.iter);
-            return finish(LQCD_ENUMERIC);
-        }
-        if (mixed) {
-            accum_df_kernel<<<nblocks_for(Vh, BB), BB, 0, s>>>(spinor_ref<PREC_DF>(ws.xdf.f), spinor_ref<LQCD_F32>(XS),
-                                                               Vh);
-            LQCD_LAUNCHED();
-            LQCD_TRY(true_residual_df(ws, kappa, &rr_true, s));
-        } else {
-            LQCD_TRY(true_residual(ws, x, U, b, kappa, &rr_true, s));
-        }
-        inf.true_rel_res = std::sqrt(rr_true / bb);
-        if (!std::isfinite(rr_true)) {
-            set_error("cg: non-finite true residual");
-            return finish(LQCD_ENUMERIC);
-        }
-        if (mixed && (rr_true <= h.stop2 || h.reason == PAUSE_MAXITER || h.iter >= prm.maxiter)) {
-            // the FP64 solution is the float-float one rounded
-            LQCD_TRY((convert_spinor<PREC_DF, LQCD_F64, double>(x, ws.xdf.f, s)));
-        }
-        if (rr_true <= h.stop2) return finish(LQCD_OK);
-        if (h.reason == PAUSE_MAXITER || h.iter >= prm.maxiter) {
-            set_error("cg: no convergence in %d iterations (true |r|/|b| = %.3e)", h.iter, inf.true_rel_res);
-            return finish(LQCD_ENOCONV);
-        }
-        inf.restarts++;
-        double beta;
-        if (mixed) { // reliable update: continue with the accurate residual
-            LQCD_TRY(df_to_sloppy(ws.rs.f, ws.rdf.f, s));
-            beta = rr_true / h.rr;
-        } else { // the iterated residual lied: restart from the true one
-            if (inf.restarts > prm.max_restarts) {
-                set_error("cg: true residual %.3e above tolerance after %d restarts", inf.true_rel_res,
-                          prm.max_restarts);
-                return finish(LQCD_ENOCONV);
-            }
-            beta = 0.0;
-        }
-        cg_set_kernel<<<1, 1, 0, s>>>(sc, rr_true, beta, rr_true);
-        LQCD_LAUNCHED();
-        LQCD_TRY(launch_p_update(P, R, sc, s));
+    LQCD_TRY(dslash_plain(TMP, UU, P, 0, skip, s));
+    LQCD_TRY(dslash_xpay(T, UU, TMP, 0, P, -k2, partials, skip, s));
+    cg_pap_kernel<<<1, 1024, 0, s>>>(partials, nbd, sc);
+    LQCD_LAUNCHED();
+    LQCD_TRY(dslash_plain(TMP, UU, T, 1, skip, s));
+    LQCD_TRY(dslash_cg(UU, TMP, 1, T, -k2, XS, R, P, partials, sc, s));
+    cg_rr_kernel<<<1, 1024, 0, s>>>(partials, nbd, sc);
+    LQCD_LAUNCHED();
+    return launch_p_update(P, R, sc, s);
+}
+
+lqcd_status CgRun::on_pause(const CgScalars &h, cudaStream_t s)
+{
+    lqcd_status rc = on_pause_impl(h, s);
+    if (rc != LQCD_OK && !done) return fail(rc);
+    return rc;
+}
+
+lqcd_status CgRun::on_pause_impl(const CgScalars &h, cudaStream_t s)
+{
+    CgWorkspace &w = *ws;
+    inf.iters = h.iter;
+    if (h.reason == PAUSE_NONFINITE) {
+        set_error("cg: non-finite value after %d iterations", h.iter);
+        return fail(LQCD_ENUMERIC);
     }
+    if (mixed) {
+        accum_df_kernel<<<nblocks_for(Vh, BB), BB, 0, s>>>(spinor_ref<PREC_DF>(w.xdf.f), spinor_ref<LQCD_F32>(XS),
+                                                           Vh);
+        LQCD_LAUNCHED();
+        LQCD_TRY(true_residual_df(w, kappa, &rr_true, s));
+    } else {
+        LQCD_TRY(true_residual(w, x, U, b, kappa, &rr_true, s));
+    }
+    inf.true_rel_res = std::sqrt(rr_true / bb);
+    if (!std::isfinite(rr_true)) {
+        set_error("cg: non-finite true residual");
+        return fail(LQCD_ENUMERIC);
+    }
+    if (mixed && (rr_true <= h.stop2 || h.reason == PAUSE_MAXITER || h.iter >= prm.maxiter)) {
+        // the FP64 solution is the float-float one rounded
+        LQCD_TRY((convert_spinor<PREC_DF, LQCD_F64, double>(x, w.xdf.f, s)));
+    }
+    if (rr_true <= h.stop2) return succeed();
+    if (h.reason == PAUSE_MAXITER || h.iter >= prm.maxiter) {
+        set_error("cg: no convergence in %d iterations (true |r|/|b| = %.3e)", h.iter, inf.true_rel_res);
+        return fail(LQCD_ENOCONV);
+    }
+    inf.restarts++;
+    double beta;
+    if (mixed) { // reliable update: continue with the accurate residual
+        LQCD_TRY(df_to_sloppy(w.rs.f, w.rdf.f, s));
+        beta = rr_true / h.rr;
+    } else { // the iterated residual lied: restart from the true one
+        if (inf.restarts > prm.max_restarts) {
+            set_error("cg: true residual %.3e above tolerance after %d restarts", inf.true_rel_res,
+                      prm.max_restarts);
+            return fail(LQCD_ENOCONV);
+        }
+        beta = 0.0;
+    }
+    cg_set_kernel<<<1, 1, 0, s>>>(sc, rr_true, beta, rr_true);
+    LQCD_LAUNCHED();
+    return launch_p_update(P, R, sc, s);
+}
+
+lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, const lqcd_field *Us,
+                        const lqcd_field *b, double kappa, const lqcd_cg_params &prm, lqcd_cg_info *info,
+                        cudaStream_t s)
+{
+    LQCD_TRY(ws.ensure(x->lat, prm.sloppy, s));
+    CgRun run;
+    run.ws = &ws, run.x = x, run.U = U, run.Us = Us, run.b = b, run.kappa = kappa, run.prm = prm;
+    run.start(s, (CgScalars *)ws.sc.p);
+    CgScalars &h = *g_pinned.sc;
+    while (!run.done) {
+        for (int k = 0; k < CG_CHUNK; k++) {
+            lqcd_status rc = run.iterate(s);
+            if (rc != LQCD_OK) {
+                run.fail(rc);
+                break;
+            }
+        }
+        if (run.done) break;
+        lqcd_status rc = [&]() -> lqcd_status {
+            LQCD_CUDA(cudaMemcpyAsync(&h, run.sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+            LQCD_CUDA(cudaStreamSynchronize(s));
+            return LQCD_OK;
+        }();
+        if (rc != LQCD_OK) {
+            run.fail(rc);
+            break;
+        }
+        if (h.pause) run.on_pause(h, s);
+    }
+    if (info) *info = run.inf;
+    return run.status;
 }
 
 } // namespace lqcd

@@ -1,6 +1,8 @@
 // cg.cuh -- CG work space shared between the solver and the HMC driver.
 #pragma once
 
+#include <chrono>
+
 #include "dslash.cuh"
 
 namespace lqcd {
@@ -18,6 +20,42 @@ struct CgWorkspace {
     FieldPtr Udf, xdf, bdf, rdf, t1df, t2df, tmpodf;
     DevBuf sc, partials, scalars;
     lqcd_status ensure(const lqcd_lattice &lat, lqcd_prec sloppy, cudaStream_t s);
+};
+
+// One solve as a resumable state machine: start() does everything before the
+// first iteration, iterate() enqueues one iteration (no-op kernels while the
+// device pause flag is set), on_pause() handles a pause read back from the
+// device (reliable update, true-residual check, convergence, maxiter).  The
+// single-system solve loops over it; the multi-system solver (batch.cu) runs
+// many of them with shared launches.
+struct CgRun {
+    // inputs
+    CgWorkspace *ws = nullptr;
+    lqcd_field *x = nullptr;
+    const lqcd_field *U = nullptr, *Us = nullptr, *b = nullptr;
+    double kappa = 0;
+    lqcd_cg_params prm{};
+    // state
+    bool mixed = false, done = false;
+    lqcd_status status = LQCD_OK;
+    double bb = 0, rr_true = 0, k2 = 0;
+    int Vh = 0;
+    lqcd_field *P = nullptr, *R = nullptr, *T = nullptr, *TMP = nullptr, *XS = nullptr;
+    const lqcd_field *UU = nullptr;
+    CgScalars *sc = nullptr; // device scalars of this solve
+    CgScalars h0{};
+    lqcd_cg_info inf{};
+    std::chrono::steady_clock::time_point t0;
+
+    lqcd_status start(cudaStream_t s, CgScalars *sc_dev);
+    lqcd_status iterate(cudaStream_t s);
+    lqcd_status on_pause(const CgScalars &h, cudaStream_t s);
+    lqcd_status fail(lqcd_status st);
+    lqcd_status succeed();
+
+  private:
+    lqcd_status start_impl(cudaStream_t s);
+    lqcd_status on_pause_impl(const CgScalars &h, cudaStream_t s);
 };
 
 lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, const lqcd_field *Us,

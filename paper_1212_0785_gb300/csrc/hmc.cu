@@ -8,6 +8,7 @@
 #include <chrono>
 #include <cmath>
 
+#include "batch.cuh"
 #include "cg.cuh"
 #include "su3_device.cuh"
 
@@ -366,6 +367,212 @@ lqcd_status lqcd_hmc_trajectory(lqcd_hmc_state *s, const lqcd_hmc_params *p, lqc
         return LQCD_ENUMERIC;
     }
     return LQCD_OK;
+}
+
+} // extern "C"
+
+// ================================================================== batched chains
+
+struct lqcd_batch {
+    std::vector<lqcd_hmc_state *> chains;
+    lqcd::BatchSolver bs;
+    lqcd::DevBuf scal; // one CgScalars slot per chain
+};
+
+namespace lqcd {
+
+static lqcd_status check_batch_params(const lqcd_batch *B, const lqcd_hmc_params *p)
+{
+    LQCD_REQUIRE(p != nullptr, "batch: params is NULL");
+    for (size_t i = 0; i < B->chains.size(); i++) {
+        LQCD_TRY(check_params(&p[i]));
+        LQCD_REQUIRE(p[i].n_flavors == 2, "batch: every chain needs two Wilson flavours");
+        LQCD_REQUIRE(p[i].cg.sloppy != LQCD_F64, "batch: the batched solver is the mixed-precision one");
+        LQCD_REQUIRE(p[i].integrator == p[0].integrator && p[i].nsteps == p[0].nsteps && p[i].tau == p[0].tau &&
+                         p[i].cg.sloppy == p[0].cg.sloppy && p[i].force_prec == p[0].force_prec,
+                     "batch: chains must share integrator, nsteps, tau, solver precision and force precision");
+    }
+    return LQCD_OK;
+}
+
+// every chain's solve of phi for its current links, with shared launches
+static lqcd_status batch_solve(lqcd_batch *B, const lqcd_hmc_params *p, cudaStream_t s)
+{
+    size_t n = B->chains.size();
+    std::vector<CgRun> runs(n);
+    std::vector<CgRun *> ptrs;
+    for (size_t i = 0; i < n; i++) {
+        lqcd_hmc_state *st = B->chains[i];
+        CgRun &r = runs[i];
+        r.ws = &st->ws, r.x = st->X.f, r.U = st->U, r.Us = sloppy_links(st, &p[i]), r.b = st->phi.f;
+        r.kappa = p[i].kappa;
+        r.prm = p[i].cg;
+        r.prm.guess = (p[i].chrono && st->have_guess) ? 1 : 0;
+        LQCD_TRY(st->ws.ensure(st->U->lat, r.prm.sloppy, s));
+        r.start(s, (CgScalars *)B->scal.p + i);
+        ptrs.push_back(&r);
+    }
+    LQCD_TRY(B->bs.solve(ptrs, s));
+    for (size_t i = 0; i < n; i++) {
+        lqcd_hmc_state *st = B->chains[i];
+        const CgRun &r = runs[i];
+        st->cg_iters += r.inf.iters;
+        st->n_solves++;
+        st->cg_res_max = std::max(st->cg_res_max, r.inf.true_rel_res);
+        st->have_guess = (r.status == LQCD_OK || r.status == LQCD_ENOCONV);
+        if (r.status == LQCD_ENOCONV)
+            st->cg_failures++;
+        else if (r.status != LQCD_OK)
+            return r.status;
+    }
+    return LQCD_OK;
+}
+
+static lqcd_status batch_kick(lqcd_batch *B, const lqcd_hmc_params *p, double c, cudaStream_t s)
+{
+    size_t n = B->chains.size();
+    for (size_t i = 0; i < n; i++) {
+        lqcd_hmc_state *st = B->chains[i];
+        LQCD_TRY(gauge_force_dev(st->P.f, st->U, st->Uf.f, p[i].beta, c, p[i].force_prec, s));
+    }
+    LQCD_TRY(batch_solve(B, p, s));
+    for (size_t i = 0; i < n; i++) {
+        lqcd_hmc_state *st = B->chains[i];
+        if (p[i].force_prec == LQCD_F32) {
+            LQCD_TRY(ensure_f32_temps(st));
+            LQCD_TRY(fermion_force_dev(st->P.f, st->U, st->Uf.f, st->X.f, p[i].kappa, c, st->Ao32.f, st->Ye32.f,
+                                       st->Bo32.f, st->X32.f, s));
+        } else {
+            LQCD_TRY(fermion_force_dev(st->P.f, st->U, nullptr, st->X.f, p[i].kappa, c, st->Ao.f, st->Ye.f,
+                                       st->Bo.f, nullptr, s));
+        }
+    }
+    return LQCD_OK;
+}
+
+static lqcd_status batch_drift(lqcd_batch *B, const lqcd_hmc_params *p, double c, cudaStream_t s)
+{
+    for (size_t i = 0; i < B->chains.size(); i++) LQCD_TRY(drift(B->chains[i], &p[i], c, s));
+    return LQCD_OK;
+}
+
+static lqcd_status batch_integrate(lqcd_batch *B, const lqcd_hmc_params *p, cudaStream_t s)
+{
+    double dt = p[0].tau / p[0].nsteps;
+    int n = p[0].nsteps;
+    if (p[0].integrator == LQCD_LEAPFROG) {
+        LQCD_TRY(batch_kick(B, p, 0.5 * dt, s));
+        for (int k = 0; k < n; k++) {
+            LQCD_TRY(batch_drift(B, p, dt, s));
+            LQCD_TRY(batch_kick(B, p, k == n - 1 ? 0.5 * dt : dt, s));
+        }
+    } else {
+        const double lam = OMELYAN_LAMBDA;
+        LQCD_TRY(batch_kick(B, p, lam * dt, s));
+        for (int k = 0; k < n; k++) {
+            LQCD_TRY(batch_drift(B, p, 0.5 * dt, s));
+            LQCD_TRY(batch_kick(B, p, (1.0 - 2.0 * lam) * dt, s));
+            LQCD_TRY(batch_drift(B, p, 0.5 * dt, s));
+            LQCD_TRY(batch_kick(B, p, k == n - 1 ? lam * dt : 2.0 * lam * dt, s));
+        }
+    }
+    return LQCD_OK;
+}
+
+} // namespace lqcd
+
+extern "C" {
+
+lqcd_status lqcd_batch_create(lqcd_hmc_state *const *chains, int n, lqcd_batch **out)
+{
+    LQCD_REQUIRE(chains && out && n > 0, "batch_create: needs at least one chain");
+    for (int i = 0; i < n; i++) {
+        LQCD_REQUIRE(chains[i], "batch_create: chain %d is NULL", i);
+        for (int j = 0; j < i; j++) LQCD_REQUIRE(chains[i] != chains[j], "batch_create: chain %d repeated", i);
+    }
+    lqcd_batch *B = new lqcd_batch();
+    B->chains.assign(chains, chains + n);
+    lqcd_status rc = B->scal.alloc(sizeof(CgScalars) * n, nullptr);
+    if (rc != LQCD_OK) {
+        delete B;
+        return rc;
+    }
+    *out = B;
+    return LQCD_OK;
+}
+
+lqcd_status lqcd_batch_destroy(lqcd_batch *B)
+{
+    cudaDeviceSynchronize();
+    delete B;
+    return LQCD_OK;
+}
+
+lqcd_status lqcd_batch_trajectory(lqcd_batch *B, const lqcd_hmc_params *params, lqcd_traj_info *info, void *stream)
+{
+    LQCD_REQUIRE(B, "batch_trajectory: NULL batch");
+    LQCD_TRY(check_batch_params(B, params));
+    cudaStream_t s = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    size_t n = B->chains.size();
+    std::vector<double> H0(n, 0.0), H1(n, 0.0);
+    for (size_t i = 0; i < n; i++) {
+        lqcd_hmc_state *st = B->chains[i];
+        reset_stats(st);
+        LQCD_CUDA(cudaMemcpyAsync(st->Ubak.f->data, st->U->data, st->U->bytes, cudaMemcpyDeviceToDevice, s));
+        LQCD_TRY(refresh(st, &params[i], &H0[i], s));
+    }
+    lqcd_status rc = batch_integrate(B, params, s);
+    if (rc == LQCD_OK) {
+        for (size_t i = 0; i < n; i++) LQCD_TRY(hamiltonian_parts(B->chains[i], s));
+        rc = batch_solve(B, params, s);
+    }
+    for (size_t i = 0; i < n; i++) {
+        lqcd_hmc_state *st = B->chains[i];
+        const lqcd_hmc_params *p = &params[i];
+        double *d = (double *)st->scal.p;
+        double h[3] = {0, 0, 0};
+        if (rc == LQCD_OK) {
+            // kinetic and plaquette sums were taken before the batched solve; add phi^dag X
+            LQCD_TRY(spinor_dot_dev(st->phi.f, st->X.f, d + 2, st->part, s));
+            LQCD_TRY(read_scalars(d, h, 3, s));
+            H1[i] = hamiltonian_from(st, p, h);
+        }
+        double dH = H1[i] - H0[i];
+        metropolis_uniform_kernel<<<1, 1, 0, s>>>(d + 3, st->seed, st->chain, st->traj);
+        LQCD_LAUNCHED();
+        double u = 0;
+        LQCD_TRY(read_scalars(d + 3, &u, 1, s));
+        bool accept = rc == LQCD_OK && std::isfinite(dH) && (!p->metropolis || u < std::exp(-dH));
+        if (!accept)
+            LQCD_CUDA(cudaMemcpyAsync(st->U->data, st->Ubak.f->data, st->U->bytes, cudaMemcpyDeviceToDevice, s));
+        double maxdev = 0;
+        if (p->reunitarize) {
+            LQCD_TRY(reunitarize_dev(st->U, d + 4, st->part, s));
+            LQCD_TRY(read_scalars(d + 4, &maxdev, 1, s));
+        }
+        LQCD_TRY(plaquette_sum(st->U, d + 5, st->part, s));
+        double plaq_sum = 0;
+        LQCD_TRY(read_scalars(d + 5, &plaq_sum, 1, s));
+        if (info) {
+            lqcd_traj_info &f = info[i];
+            f.dH = dH;
+            f.H0 = H0[i];
+            f.H1 = H1[i];
+            f.plaq = plaq_sum / (6.0 * 2.0 * st->U->Vh);
+            f.u = u;
+            f.max_unitarity_dev = maxdev;
+            f.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            f.cg_true_rel_res_max = st->cg_res_max;
+            f.accepted = accept ? 1 : 0;
+            f.cg_iters = st->cg_iters;
+            f.n_solves = st->n_solves;
+            f.cg_failures = st->cg_failures;
+            f.traj = st->traj;
+        }
+        st->traj++;
+    }
+    return rc;
 }
 
 } // extern "C"

@@ -119,6 +119,10 @@ _SIGS = {
     "lqcd_hmc_hamiltonian": (_i, [_vp, ctypes.POINTER(HmcParams), _dp, _vp]),
     "lqcd_md_step": (_i, [_vp, ctypes.POINTER(HmcParams), _vp]),
     "lqcd_hmc_trajectory": (_i, [_vp, ctypes.POINTER(HmcParams), ctypes.POINTER(TrajInfo), _vp]),
+    "lqcd_cg_solve_batch": (_i, [_i, _pp, _pp, _pp, _pp, _dp, ctypes.POINTER(CgParams), ctypes.POINTER(CgInfo), _vp]),
+    "lqcd_batch_create": (_i, [_pp, _i, _pp]),
+    "lqcd_batch_destroy": (_i, [_vp]),
+    "lqcd_batch_trajectory": (_i, [_vp, ctypes.POINTER(HmcParams), ctypes.POINTER(TrajInfo), _vp]),
 }
 
 _lock = threading.Lock()
@@ -465,6 +469,58 @@ class HmcState:
     def close(self):
         if self.h:
             lib().lqcd_hmc_state_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- batches
+
+def _ptrs(fields):
+    arr = (ctypes.c_void_p * max(1, len(fields)))()
+    for i, f in enumerate(fields):
+        arr[i] = f.h.value if isinstance(f.h, ctypes.c_void_p) else f.h
+    return arr
+
+
+def cg_solve_batch(xs, Us, U_sloppys, bs, kappas, params: CgParams, stream=None, check=True):
+    """n independent mixed solves with shared launches; returns (status, [CgInfo])"""
+    n = len(xs)
+    infos = (CgInfo * max(1, n))()
+    k = (ctypes.c_double * max(1, n))(*kappas)
+    rc = lib().lqcd_cg_solve_batch(n, _ptrs(xs), _ptrs(Us), _ptrs(U_sloppys), _ptrs(bs), k, ctypes.byref(params),
+                                   infos, _s(stream))
+    if check and rc not in (OK, ENOCONV):
+        _check(rc, "cg_solve_batch")
+    return rc, [infos[i] for i in range(n)]
+
+
+class Batch:
+    """Chains (HmcState) advanced together, their solves in shared launches."""
+
+    def __init__(self, states):
+        self.states = list(states)
+        arr = (ctypes.c_void_p * len(self.states))(*[s.h.value for s in self.states])
+        h = ctypes.c_void_p()
+        _check(lib().lqcd_batch_create(arr, len(self.states), ctypes.byref(h)), "batch_create")
+        self.h = h
+
+    def trajectory(self, params, stream=None):
+        n = len(self.states)
+        if isinstance(params, HmcParams):
+            params = [params] * n
+        parr = (HmcParams * n)(*params)
+        infos = (TrajInfo * n)()
+        _check(lib().lqcd_batch_trajectory(self.h, parr, infos, _s(stream)), "batch_trajectory")
+        return [infos[i].as_dict() for i in range(n)]
+
+    def close(self):
+        if self.h:
+            lib().lqcd_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
