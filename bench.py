@@ -170,7 +170,7 @@ def kernel_source_hash() -> str:
     valid for the kernel it was taken on"""
     h = hashlib.sha256()
     base = os.path.join(HERE, "paper_1212_0785_gb300", "csrc")
-    for name in ("dslash.cu", "spin.cuh", "lqcd_internal.cuh", "dslash.cuh"):
+    for name in ("dslash.cu", "dslash_site.cuh", "spin.cuh", "lqcd_internal.cuh", "dslash.cuh"):
         with open(os.path.join(base, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -504,6 +504,100 @@ def run_chains(args):
         st.close()
     return 0
 
+SERVICE_LATS = [(8, 8, 8, 8), (16, 16, 16, 32), (24, 24, 24, 48), (32, 32, 32, 64)]
+
+
+def _serve(lqcd, fields, arrivals, reqs, params):
+    """submit reqs at their arrival times (s after the start) to a fresh
+    service; returns (results, makespan s, launches)"""
+    svc = lqcd.Service(params)
+    ids = [svc.add_gauge(U) for U in fields]
+    # warm-up: one single-RHS request per gauge makes its link copies and work space
+    for gid in ids:
+        t = svc.submit(gid, 0.15, (0, 0, 0, 0), 1)
+        svc.wait(t)
+        svc.release(t)
+    launches0 = lqcd.launch_count()
+    pending, results = {}, {}
+    t0 = time.perf_counter()
+    i = 0
+    while i < len(reqs) or pending:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and arrivals[i] <= now:
+            g, kappa, site = reqs[i]
+            pending[svc.submit(ids[g], kappa, site, 12)] = i
+            i += 1
+        for t in list(pending):
+            r = svc.poll(t)
+            if r is not None:
+                results[pending.pop(t)] = r
+                svc.release(t)
+        time.sleep(2e-4)
+    makespan = time.perf_counter() - t0
+    launches = lqcd.launch_count() - launches0
+    svc.close()
+    return [results[k] for k in range(len(reqs))], makespan, launches
+
+
+def run_service(args):
+    """Point-source solve requests (12 spin-colour right-hand sides each) of the
+    full Wilson operator on resident gauge fields of 8^4, 16^3x32, 24^3x48 and
+    32^3x64 (start exp(i 0.15 H), Philox seed 200 + k), volume uniform over the
+    four, kappa uniform in [0.150, 0.158], source site uniform, Poisson
+    arrivals at 200/s; mixed FP16+norm CG to full |r|/|b| <= 1e-10.  The
+    continuously batched service against the same service admitting one
+    request at a time (FIFO)."""
+    import torch
+
+    from paper_1212_0785_gb300 import lqcd
+
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(7)
+    n = args.requests
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n))
+    arrivals -= arrivals[0]
+    reqs = []
+    for _ in range(n):
+        g = int(rng.integers(len(SERVICE_LATS)))
+        site = tuple(int(rng.integers(L)) for L in SERVICE_LATS[g])
+        reqs.append((g, float(rng.uniform(0.150, 0.158)), site))
+    fields = []
+    for k, dims in enumerate(SERVICE_LATS):
+        U = lqcd.gauge_field(dims)
+        lqcd.gauge_start(U, 200 + k, 0.15)
+        fields.append(U)
+    sloppy = lqcd.PREC_NAMES[args.sloppy]
+    prm = lqcd.service_params(tol=1e-10, sloppy=sloppy, delta=args.delta, hbm_budget=args.hbm_budget << 30)
+    clocks = ClockSampler(0)
+    clocks.start()
+    res, span, launches = _serve(lqcd, fields, arrivals, reqs, prm)
+    clk = clocks.stop()
+    fifo_prm = lqcd.service_params(tol=1e-10, sloppy=sloppy, delta=args.delta, hbm_budget=args.hbm_budget << 30,
+                                   max_active_rhs=12)
+    fres, fspan, _ = _serve(lqcd, fields, arrivals, reqs, fifo_prm)
+
+    def stats(rs, sp):
+        lat = np.array([r["latency_s"] for r in rs])
+        return {"solves_per_s": len(rs) / sp, "rhs_per_s": 12 * len(rs) / sp, "makespan_s": sp,
+                "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+                "queue_p50_s": float(np.percentile([r["queue_s"] for r in rs], 50)),
+                "true_rel_res_max": max(r["true_rel_res_max"] for r in rs),
+                "failed": sum(r["status"] != lqcd.OK for r in rs)}
+
+    ours, fifo = stats(res, span), stats(fres, fspan)
+    line = {"metric": "solves/s", "value": ours["solves_per_s"], "unit": "solves/s (12 point-source RHS each)",
+            "n_gpus": 1, "steps": n, "warmup": len(SERVICE_LATS), "ms_per_step": span / n * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 math (f16n solver storage); f64 residual check and solutions", "data": "synthetic",
+            "config": {"workload": "solve_service_8^4_16^3x32_24^3x48_32^3x64", "requests": n,
+                       "arrival_rate_per_s": args.rate, "rhs_per_request": 12, "kappa": [0.150, 0.158],
+                       "tol_full_M": 1e-10, "hbm_budget_gib": args.hbm_budget, "start_eps": 0.15},
+            "latency_p50_s": ours["latency_p50_s"], "latency_p99_s": ours["latency_p99_s"],
+            "service": ours, "fifo": fifo, "gpu_launches": launches, "clocks": clk,
+            "iters_per_rhs": float(np.mean([r["iters"] / 12 for r in res]))}
+    print(json.dumps(line))
+    return 0
+
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
@@ -511,8 +605,12 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("hmc32", "chains64"), default="hmc32",
-                    help="hmc32: the 32^3x64 trajectory (default); chains64: 64 batched chains")
+    ap.add_argument("--workload", choices=("hmc32", "chains64", "service"), default="hmc32",
+                    help="hmc32: the 32^3x64 trajectory (default); chains64: 64 batched chains; "
+                         "service: Poisson-arriving point-source solves")
+    ap.add_argument("--requests", type=int, default=40, help="service: number of requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="service: mean arrivals per second")
+    ap.add_argument("--hbm-budget", type=int, default=96, help="service: admission budget, GiB")
     ap.add_argument("--sloppy", choices=("f32", "f16n", "bf16"), default="f16n")
     ap.add_argument("--delta", type=float, default=0.003)
     ap.add_argument("--force-prec", choices=("f64", "f32"), default="f32")
@@ -530,6 +628,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "chains64":
         return run_chains(args)
+    if args.workload == "service":
+        return run_service(args)
     return run_ours(args)
 
 

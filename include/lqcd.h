@@ -419,6 +419,75 @@ lqcd_status lqcd_batch_destroy(lqcd_batch *batch);
 lqcd_status lqcd_batch_trajectory(lqcd_batch *batch, const lqcd_hmc_params *params, lqcd_traj_info *info,
                                   void *stream);
 
+/* ------------------------------------------------------------ solve service */
+
+/* A service for solves of the full Wilson-Dirac operator, M x = b with
+ * M = 1 - kappa D, on gauge fields kept resident on the device.  Requests are
+ * submitted at any time from any host thread and run on a worker thread of the
+ * service with its own stream: it admits queued requests in arrival order
+ * while the device memory of the admitted work fits hbm_budget (a request
+ * alone is always admitted), and advances all admitted right-hand sides
+ * together, one chunk of CG iterations at a time, in shared launches (the
+ * engine of lqcd_cg_solve_batch); right-hand sides join and leave between
+ * chunks (continuous batching).  The paper keeps all fields resident and
+ * manages device memory itself (Sec. 5); admission by footprint is this
+ * library's analogue for many concurrent solves.
+ *
+ * Each right-hand side is even-odd reduced: b'_e = b_e + kappa D_eo b_o,
+ * Mhat^dag Mhat x_e = Mhat^dag b'_e by the mixed-precision CG of
+ * lqcd_cg_solve, x_o = b_o + kappa D_oe x_e.  The residual reported is that of
+ * the full operator, |b - M x| / |b|, recomputed in FP64 after the
+ * reconstruction; if it is above cg.tol the solve continues from x_e with a
+ * tighter normal-equation tolerance (at most 3 times, then LQCD_ENOCONV).
+ * Each right-hand side's result does not depend on what else runs with it. */
+typedef struct lqcd_service lqcd_service;
+
+typedef struct {
+    lqcd_cg_params cg;  /* tol = target full |r|/|b|; sloppy F32, F16N or BF16; guess ignored */
+    size_t hbm_budget;  /* bytes of device memory the admitted requests may hold */
+    int max_active_rhs; /* admit no request that would make more right-hand sides run at once (<= 0: no limit) */
+} lqcd_service_params;
+
+/* A point-source request: nrhs unit sources b = delta(x, site) delta(spin*3 +
+ * colour, k) for k = 0 .. nrhs-1 (nrhs <= 12, the spin-colour components in
+ * order). */
+typedef struct {
+    int gauge;    /* id from lqcd_service_add_gauge */
+    double kappa;
+    int site[4];  /* x, y, z, t of the source */
+    int nrhs;     /* 1 .. 12 */
+} lqcd_solve_req;
+
+typedef struct {
+    lqcd_status status;      /* first non-OK status of a right-hand side, else LQCD_OK */
+    int nrhs;
+    int iters;               /* CG iterations summed over the right-hand sides */
+    int refinements;         /* continuations after a full-residual miss, summed */
+    double true_rel_res_max; /* max over the right-hand sides of |b - M x| / |b| */
+    double queue_s;          /* submit -> admission, seconds (host clock) */
+    double latency_s;        /* submit -> result, seconds (host clock) */
+} lqcd_solve_result;
+
+/* Creates a service on the current device and starts its worker thread. */
+lqcd_status lqcd_service_create(const lqcd_service_params *params, lqcd_service **out);
+/* Registers an F64 gauge field (borrowed: it must outlive the service and not
+ * change while the service exists); *id receives its id.  Its sloppy and
+ * float-float link copies are made on the first request that uses it. */
+lqcd_status lqcd_service_add_gauge(lqcd_service *svc, lqcd_field *U, int *id);
+/* Queues a request; *ticket identifies it.  Returns at once. */
+lqcd_status lqcd_solve_submit(lqcd_service *svc, const lqcd_solve_req *req, uint64_t *ticket);
+/* LQCD_EAGAIN while the request runs; LQCD_OK with *result once done (the
+ * request's own failure is in result->status). */
+lqcd_status lqcd_solve_poll(lqcd_service *svc, uint64_t ticket, lqcd_solve_result *result);
+/* The solution halves x_e, x_o (F64 fields owned by the service) of
+ * right-hand side k of a finished request, valid until lqcd_solve_release. */
+lqcd_status lqcd_solve_solution(lqcd_service *svc, uint64_t ticket, int k, lqcd_field **x_even,
+                                lqcd_field **x_odd);
+/* Frees a finished request's solutions (LQCD_EAGAIN while it runs). */
+lqcd_status lqcd_solve_release(lqcd_service *svc, uint64_t ticket);
+/* Finishes all submitted requests, stops the worker and frees everything. */
+lqcd_status lqcd_service_destroy(lqcd_service *svc);
+
 #ifdef __cplusplus
 }
 #endif

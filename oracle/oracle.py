@@ -339,3 +339,24 @@ def hmc_trajectory(dims, U, beta, kappa, tau, nsteps, integrator=LEAPFROG, n_fla
                                    n_flavors, cg_tol, cg_maxiter, seed, chain, traj, int(reunit),
                                    int(metropolis), _ptr(info)))
     return U, dict(zip(TRAJ_KEYS, info.tolist()))
+
+
+def wilson(dims, U, kappa, psi, t_bc=-1) -> np.ndarray:
+    """The full Wilson operator M psi = psi - kappa D psi (Sec. 6.2: the Wilson
+    fermions the trajectories run)."""
+    return psi - kappa * dslash(dims, U, psi, t_bc=t_bc)
+
+
+def wilson_solve(dims, U, kappa, b, tol=1e-12, maxiter=10000, t_bc=-1):
+    """M x = b for a full-lattice source b through the even-odd reduction the
+    Krylov solver of Sec. 6 runs on: b'_e = b_e + kappa D_eo b_o, the normal
+    equations Mhat^dag Mhat x_e = Mhat^dag b'_e by CG, then x_o = b_o + kappa
+    D_oe x_e.  Returns (x, converged, cg iterations)."""
+    par = parity(dims)
+    even = (par == 0)[:, None, None]
+    b_e, b_o = np.where(even, b, 0), np.where(even, 0, b)
+    bp = b_e + kappa * dslash(dims, U, b_o, out_parity=0, t_bc=t_bc)
+    src = mhat(dims, U, kappa, bp, dagger=True, t_bc=t_bc)
+    x_e, conv, iters, _ = cg(dims, U, kappa, src, tol=tol, maxiter=maxiter, t_bc=t_bc)
+    x_o = b_o + kappa * dslash(dims, U, x_e, out_parity=1, t_bc=t_bc)
+    return np.where(even, x_e, x_o), conv, iters

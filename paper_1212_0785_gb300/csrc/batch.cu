@@ -192,6 +192,14 @@ __global__ void __launch_bounds__(DS_BLOCK) batch_p_update(const SysDesc<SP> *sy
     d.p.store(cb, pv);
 }
 
+// after a chunk: every system's scalars into one array (one copy to the host)
+template <lqcd_prec SP>
+__global__ void batch_gather_scalars(const SysDesc<SP> *sys, CgScalars *out, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = *sys[i].sc;
+}
+
 // ---------------------------------------------------------------- host side
 
 template <lqcd_prec SP>
@@ -237,6 +245,7 @@ lqcd_status BatchSolver::enqueue_chunk(cudaStream_t s)
         batch_scalars<SP, true><<<n, 1024, 0, s>>>(d);
         batch_p_update<SP><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
     }
+    batch_gather_scalars<SP><<<nblocks_for(n, 128), 128, 0, s>>>(d, (CgScalars *)gathered.p, n);
     LQCD_CUDA(cudaGetLastError());
     return LQCD_OK;
 }
@@ -255,6 +264,7 @@ lqcd_status BatchSolver::build_tables(cudaStream_t s)
     nblocks_total = (int)hb.size();
     if (descs.bytes < hd.size() * sizeof(SysDesc<SP>)) LQCD_TRY(descs.alloc(hd.size() * sizeof(SysDesc<SP>), s));
     if (bmap.bytes < hb.size() * sizeof(int2)) LQCD_TRY(bmap.alloc(hb.size() * sizeof(int2), s));
+    if (gathered.bytes < hd.size() * sizeof(CgScalars)) LQCD_TRY(gathered.alloc(hd.size() * sizeof(CgScalars), s));
     LQCD_CUDA(cudaMemcpyAsync(descs.p, hd.data(), hd.size() * sizeof(SysDesc<SP>), cudaMemcpyHostToDevice, s));
     LQCD_CUDA(cudaMemcpyAsync(bmap.p, hb.data(), hb.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
     LQCD_CUDA(cudaStreamSynchronize(s)); // host vectors go out of scope
@@ -284,42 +294,68 @@ lqcd_status BatchSolver::run_all(std::vector<CgRun *> &runs, cudaStream_t s)
     active.clear();
     for (CgRun *r : runs)
         if (!r->done) active.push_back(r);
-    bool changed = true;
-    while (!active.empty()) {
-        if (changed) {
-            LQCD_TRY(build_tables<SP>(s));
-            changed = false;
-        }
-        if (use_graph) {
-            LQCD_CUDA(cudaGraphLaunch(exec, s));
-            g_launches.fetch_add(7 * BCHUNK, std::memory_order_relaxed);
-        } else {
-            LQCD_TRY(enqueue_chunk<SP>(s));
-            g_launches.fetch_add(7 * BCHUNK, std::memory_order_relaxed);
-        }
-        // read every active system's scalars (they are not contiguous: one copy each)
-        if (pinned_n < active.size()) {
-            if (pinned_h) cudaFreeHost(pinned_h);
-            pinned_h = nullptr;
-            pinned_n = 0;
-            LQCD_CUDA(cudaMallocHost((void **)&pinned_h, sizeof(CgScalars) * active.size()));
-            pinned_n = active.size();
-        }
-        for (size_t i = 0; i < active.size(); i++)
-            LQCD_CUDA(cudaMemcpyAsync(&pinned_h[i], active[i]->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
-        LQCD_CUDA(cudaStreamSynchronize(s));
-        std::vector<CgRun *> still;
-        for (size_t i = 0; i < active.size(); i++) {
-            CgRun *r = active[i];
-            if (pinned_h[i].pause) r->on_pause(pinned_h[i], s);
-            if (r->done)
-                changed = true;
-            else
-                still.push_back(r);
-        }
-        active.swap(still);
+    changed = true;
+    while (!active.empty()) LQCD_TRY(chunk<SP>(s));
+    return LQCD_OK;
+}
+
+// one chunk of iterations of every active system, then the pauses; done
+// systems leave `active`
+template <lqcd_prec SP>
+lqcd_status BatchSolver::chunk(cudaStream_t s)
+{
+    if (changed) {
+        LQCD_TRY(build_tables<SP>(s));
+        changed = false;
+    }
+    if (use_graph) {
+        LQCD_CUDA(cudaGraphLaunch(exec, s));
+        g_launches.fetch_add(7 * BCHUNK + 1, std::memory_order_relaxed);
+    } else {
+        LQCD_TRY(enqueue_chunk<SP>(s));
+        g_launches.fetch_add(7 * BCHUNK + 1, std::memory_order_relaxed);
+    }
+    // read every active system's scalars (gathered by the chunk's last kernel)
+    if (pinned_n < active.size()) {
+        if (pinned_h) cudaFreeHost(pinned_h);
+        pinned_h = nullptr;
+        pinned_n = 0;
+        LQCD_CUDA(cudaMallocHost((void **)&pinned_h, sizeof(CgScalars) * active.size()));
+        pinned_n = active.size();
+    }
+    LQCD_CUDA(cudaMemcpyAsync(pinned_h, gathered.p, sizeof(CgScalars) * active.size(), cudaMemcpyDeviceToHost, s));
+    LQCD_CUDA(cudaStreamSynchronize(s));
+    std::vector<CgRun *> still;
+    for (size_t i = 0; i < active.size(); i++) {
+        CgRun *r = active[i];
+        if (pinned_h[i].pause) r->on_pause(pinned_h[i], s);
+        if (r->done)
+            changed = true;
+        else
+            still.push_back(r);
+    }
+    active.swap(still);
+    return LQCD_OK;
+}
+
+lqcd_status BatchSolver::add(CgRun *r)
+{
+    if (!r->done) {
+        active.push_back(r);
+        changed = true;
     }
     return LQCD_OK;
+}
+
+lqcd_status BatchSolver::step(lqcd_prec p, cudaStream_t s)
+{
+    if (active.empty()) return LQCD_OK;
+    switch (p) {
+    case LQCD_F16N: return chunk<LQCD_F16N>(s);
+    case LQCD_F32: return chunk<LQCD_F32>(s);
+    case LQCD_BF16: return chunk<LQCD_BF16>(s);
+    default: set_error("batched solve: the sloppy precision must be F32, F16N or BF16"); return LQCD_EINVAL;
+    }
 }
 
 BatchSolver::BatchSolver() = default;

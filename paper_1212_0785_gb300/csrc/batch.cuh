@@ -28,7 +28,7 @@ struct SysDesc {
 struct BatchSolver {
     bool use_graph = true;
     std::vector<CgRun *> active;
-    DevBuf descs, bmap;
+    DevBuf descs, bmap, gathered;
     int nblocks_total = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -41,13 +41,21 @@ struct BatchSolver {
     BatchSolver(const BatchSolver &) = delete;
     BatchSolver &operator=(const BatchSolver &) = delete;
 
+    bool changed = true;
+
     lqcd_status solve(std::vector<CgRun *> &runs, cudaStream_t s);
+    // continuous use: add started runs between steps; step runs one chunk of
+    // all active runs (all with sloppy precision p) and drops finished ones
+    lqcd_status add(CgRun *r);
+    lqcd_status step(lqcd_prec p, cudaStream_t s);
     void release();
 
   private:
     void drop_graph();
     template <lqcd_prec SP>
     lqcd_status run_all(std::vector<CgRun *> &runs, cudaStream_t s);
+    template <lqcd_prec SP>
+    lqcd_status chunk(cudaStream_t s);
     template <lqcd_prec SP>
     lqcd_status build_tables(cudaStream_t s);
     template <lqcd_prec SP>

@@ -256,13 +256,23 @@ lqcd_status CgWorkspace::ensure(const lqcd_lattice &l, lqcd_prec sl, cudaStream_
         LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F64, 0, &tmpo64.f));
         LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &p64.f));
     } else {
-        LQCD_TRY(field_alloc_df(&lat, LQCD_GAUGE, &Udf.f));
+        if (temps_only) {
+            LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &rdf.f));
+            LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &t1df.f));
+            LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &t2df.f));
+            LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_ODD, &tmpodf.f));
+            ready = true;
+            return LQCD_OK;
+        }
+        if (!udf_ext) LQCD_TRY(field_alloc_df(&lat, LQCD_GAUGE, &Udf.f));
         LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &xdf.f));
         LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &bdf.f));
-        LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &rdf.f));
-        LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &t1df.f));
-        LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &t2df.f));
-        LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_ODD, &tmpodf.f));
+        if (!tmp_from) {
+            LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &rdf.f));
+            LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &t1df.f));
+            LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &t2df.f));
+            LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_ODD, &tmpodf.f));
+        }
         LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F32, 0, &xs.f));
         LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, sl, 0, &rs.f));
         LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, sl, 0, &ps.f));
@@ -276,6 +286,15 @@ lqcd_status CgWorkspace::ensure(const lqcd_lattice &l, lqcd_prec sl, cudaStream_
     LQCD_TRY(scalars.alloc(8 * sizeof(double), s));
     ready = true;
     return LQCD_OK;
+}
+
+size_t CgWorkspace::bytes() const
+{
+    size_t n = sc.bytes + partials.bytes + scalars.bytes;
+    for (const FieldPtr *f : {&r64, &t64a, &t64b, &tmpo64, &p64, &xs, &rs, &ps, &ts, &tmpos, &Udf, &xdf, &bdf, &rdf,
+                              &t1df, &t2df, &tmpodf})
+        if (f->f) n += f->f->bytes + f->f->norm_bytes;
+    return n;
 }
 
 static lqcd_status launch_p_update(lqcd_field *p, lqcd_field *r, const CgScalars *sc, cudaStream_t s)
@@ -296,13 +315,13 @@ static lqcd_status launch_p_update(lqcd_field *p, lqcd_field *r, const CgScalars
 static lqcd_status true_residual_df(CgWorkspace &ws, double kappa, double *rr, cudaStream_t s)
 {
     double k2 = kappa * kappa;
-    LQCD_TRY(dslash_plain(ws.tmpodf.f, ws.Udf.f, ws.xdf.f, 0, nullptr, s));
-    LQCD_TRY(dslash_xpay(ws.t1df.f, ws.Udf.f, ws.tmpodf.f, 0, ws.xdf.f, -k2, nullptr, nullptr, s));
-    LQCD_TRY(dslash_plain(ws.tmpodf.f, ws.Udf.f, ws.t1df.f, 1, nullptr, s));
-    LQCD_TRY(dslash_xpay(ws.t2df.f, ws.Udf.f, ws.tmpodf.f, 1, ws.t1df.f, -k2, nullptr, nullptr, s));
+    LQCD_TRY(dslash_plain(ws.tmpo(), ws.udf(), ws.xdf.f, 0, nullptr, s));
+    LQCD_TRY(dslash_xpay(ws.t1(), ws.udf(), ws.tmpo(), 0, ws.xdf.f, -k2, nullptr, nullptr, s));
+    LQCD_TRY(dslash_plain(ws.tmpo(), ws.udf(), ws.t1(), 1, nullptr, s));
+    LQCD_TRY(dslash_xpay(ws.t2(), ws.udf(), ws.tmpo(), 1, ws.t1(), -k2, nullptr, nullptr, s));
     int Vh = ws.xdf.f->Vh, nb = nblocks_for(Vh, BB);
-    residual_df_kernel<<<nb, BB, 0, s>>>(spinor_ref<PREC_DF>(ws.rdf.f), spinor_ref<PREC_DF>(ws.bdf.f),
-                                         spinor_ref<PREC_DF>(ws.t2df.f), (double *)ws.partials.p, nb, Vh);
+    residual_df_kernel<<<nb, BB, 0, s>>>(spinor_ref<PREC_DF>(ws.rdf_()), spinor_ref<PREC_DF>(ws.bdf.f),
+                                         spinor_ref<PREC_DF>(ws.t2()), (double *)ws.partials.p, nb, Vh);
     LQCD_LAUNCHED();
     LQCD_TRY(reduce_partials((double *)ws.partials.p, nb, 1, (double *)ws.scalars.p, s));
     LQCD_TRY(pinned());
@@ -325,6 +344,15 @@ static lqcd_status true_residual(CgWorkspace &ws, const lqcd_field *x, const lqc
     LQCD_TRY(pinned());
     LQCD_TRY(read_scalars((double *)ws.scalars.p, g_pinned.d, 1, s));
     *rr = g_pinned.d[0];
+    return LQCD_OK;
+}
+
+// float-float copy of FP64 links (for owners that share one copy among solves)
+lqcd_status split_links(lqcd_field *Udf, const lqcd_field *U, cudaStream_t s)
+{
+    split_gauge_kernel<<<nblocks_for(8L * U->Vh, BB), BB, 0, s>>>(gauge_ref<PREC_DF>(Udf), gauge_ref<LQCD_F64>(U),
+                                                                    U->Vh);
+    LQCD_LAUNCHED();
     return LQCD_OK;
 }
 
@@ -384,15 +412,17 @@ lqcd_status CgRun::start_impl(cudaStream_t s)
     if (mixed) {
         LQCD_REQUIRE(Us && Us->kind == LQCD_GAUGE && Us->prec == prm.sloppy && Us->recon == 12,
                      "cg: mixed solve needs a 12-real link copy in the sloppy precision");
-        split_gauge_kernel<<<nblocks_for(8L * Vh, BB), BB, 0, s>>>(gauge_ref<PREC_DF>(w.Udf.f),
-                                                                   gauge_ref<LQCD_F64>(U), Vh);
-        LQCD_LAUNCHED();
+        if (!w.udf_ext) { // the float-float links of this solve
+            split_gauge_kernel<<<nblocks_for(8L * Vh, BB), BB, 0, s>>>(gauge_ref<PREC_DF>(w.Udf.f),
+                                                                       gauge_ref<LQCD_F64>(U), Vh);
+            LQCD_LAUNCHED();
+        }
         LQCD_TRY((convert_spinor<LQCD_F64, PREC_DF, double>(w.bdf.f, b, s)));
         LQCD_CUDA(cudaMemsetAsync(w.xs.f->data, 0, w.xs.f->bytes, s));
         if (prm.guess) { // r = b - A x0, accurately
             LQCD_TRY((convert_spinor<LQCD_F64, PREC_DF, double>(w.xdf.f, x, s)));
             LQCD_TRY(true_residual_df(w, kappa, &rr0, s));
-            LQCD_TRY(df_to_sloppy(w.rs.f, w.rdf.f, s));
+            LQCD_TRY(df_to_sloppy(w.rs.f, w.rdf_(), s));
             LQCD_TRY(lqcd_field_copy(w.ps.f, w.rs.f, s));
         } else {
             LQCD_CUDA(cudaMemsetAsync(w.xdf.f->data, 0, w.xdf.f->bytes, s));
@@ -486,7 +516,7 @@ lqcd_status CgRun::on_pause_impl(const CgScalars &h, cudaStream_t s)
     inf.restarts++;
     double beta;
     if (mixed) { // reliable update: continue with the accurate residual
-        LQCD_TRY(df_to_sloppy(w.rs.f, w.rdf.f, s));
+        LQCD_TRY(df_to_sloppy(w.rs.f, w.rdf_(), s));
         beta = rr_true / h.rr;
     } else { // the iterated residual lied: restart from the true one
         if (inf.restarts > prm.max_restarts) {

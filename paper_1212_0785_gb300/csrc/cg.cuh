@@ -19,7 +19,20 @@ struct CgWorkspace {
     // temporaries in float-float storage, and the float-float link copy
     FieldPtr Udf, xdf, bdf, rdf, t1df, t2df, tmpodf;
     DevBuf sc, partials, scalars;
+    // Optional sharing for many right-hand sides on one lattice: the
+    // float-float links kept current by the owner (no per-solve split), and
+    // the transient float-float fields of another workspace (used only while a
+    // pause is handled, which the owner serialises on one stream).
+    const lqcd_field *udf_ext = nullptr;
+    CgWorkspace *tmp_from = nullptr;
+    bool temps_only = false; // allocate only the transient float-float fields (a tmp_from owner)
+    const lqcd_field *udf() const { return udf_ext ? udf_ext : Udf.f; }
+    lqcd_field *rdf_() const { return tmp_from ? tmp_from->rdf.f : rdf.f; }
+    lqcd_field *t1() const { return tmp_from ? tmp_from->t1df.f : t1df.f; }
+    lqcd_field *t2() const { return tmp_from ? tmp_from->t2df.f : t2df.f; }
+    lqcd_field *tmpo() const { return tmp_from ? tmp_from->tmpodf.f : tmpodf.f; }
     lqcd_status ensure(const lqcd_lattice &lat, lqcd_prec sloppy, cudaStream_t s);
+    size_t bytes() const;
 };
 
 // One solve as a resumable state machine: start() does everything before the
@@ -57,6 +70,8 @@ struct CgRun {
     lqcd_status start_impl(cudaStream_t s);
     lqcd_status on_pause_impl(const CgScalars &h, cudaStream_t s);
 };
+
+lqcd_status split_links(lqcd_field *Udf, const lqcd_field *U, cudaStream_t s);
 
 lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, const lqcd_field *Us,
                         const lqcd_field *b, double kappa, const lqcd_cg_params &prm, lqcd_cg_info *info,

@@ -1,0 +1,495 @@
+// service.cu -- a continuous-batching service for Wilson-Dirac solves.
+//
+// Requests arrive at any time (lqcd_solve_submit) for point-source solves of
+// the full Wilson operator M x = b on gauge fields kept resident on the device.
+// A worker thread admits queued requests in arrival order while the device
+// memory their work needs fits a budget (the paper keeps fields resident and
+// manages device memory itself, Sec. 5; here admission replaces spilling), sets
+// up each right-hand side, and advances every admitted right-hand side
+// together, one graph-captured chunk of CG iterations at a time, with the
+// multi-system engine of batch.cu: right-hand sides of new requests join
+// between chunks as memory frees up, finished ones leave.  Each solve is
+// even-odd reduced: b'_e = b_e + kappa D_eo b_o, CG on Mhat^dag Mhat y =
+// Mhat^dag b'_e, x_e = y, x_o = b_o + kappa D_oe x_e; the residual reported is
+// that of the full M, |b - M x| / |b|, recomputed in FP64, and a solve whose
+// full residual misses the tolerance continues from its solution with a
+// tighter normal-equation tolerance.  Every right-hand side gives the same
+// result alone or in any mix (per-system arithmetic does not depend on the
+// batch).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+
+#include "batch.cuh"
+
+namespace lqcd {
+
+using Clock = std::chrono::steady_clock;
+
+// unit point source: component comp (spin*3 + colour) at checkerboard site cb
+__global__ void point_source_kernel(double2 *f, int Vh, int cb, int comp)
+{
+    f[(size_t)comp * Vh + cb] = make_double2(1.0, 0.0);
+}
+
+// |a - b|^2 block partials (FP64)
+__global__ void __launch_bounds__(256) diff_norm_kernel(SpinorRef<LQCD_F64> a, SpinorRef<LQCD_F64> b, double *partials,
+                                                        int Vh)
+{
+    int cb = blockIdx.x * 256 + threadIdx.x;
+    double n2[1] = {0.0};
+    if (cb < Vh) {
+        Sp<double> av = a.load_rw<double>(cb), bv = b.load_rw<double>(cb);
+#pragma unroll
+        for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) n2[0] += norm2(av.c[s][c] - bv.c[s][c]);
+    }
+    block_sum_store<1, 256>(n2, partials, (int)gridDim.x);
+}
+
+struct SvcGauge {
+    lqcd_field *U = nullptr; // borrowed FP64 links
+    FieldPtr Us, Udf;         // sloppy copy and float-float copy shared by every solve on it
+    CgWorkspace shared;       // transient float-float fields shared by its solves
+    FieldPtr be, bo, bp, src, tmpo, mxe; // set-up and check temporaries (used one solve at a time)
+    DevBuf part, scal;
+    bool ready = false;
+};
+
+struct SvcRhs {
+    int comp = 0;
+    std::unique_ptr<CgWorkspace> ws{new CgWorkspace()};
+    FieldPtr y, xo; // the solution halves
+    CgRun run;
+    int refinements = 0;
+    double tol_n = 0;
+    bool finalized = false;
+    double rel_res = 0;
+    int iters = 0;
+    lqcd_status status = LQCD_OK;
+};
+
+struct SvcRequest {
+    uint64_t ticket = 0;
+    lqcd_solve_req req{};
+    Clock::time_point t_submit, t_admit, t_done;
+    std::vector<std::unique_ptr<SvcRhs>> rhs;
+    size_t bytes = 0;
+    bool admitted = false, done = false;
+    lqcd_solve_result result{};
+};
+
+} // namespace lqcd
+
+using namespace lqcd;
+
+struct lqcd_service {
+    lqcd_service_params prm{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<std::unique_ptr<SvcGauge>> gauges;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<SvcRequest *> queue;
+    std::unordered_map<uint64_t, std::unique_ptr<SvcRequest>> reqs;
+    std::vector<SvcRequest *> running;
+    uint64_t next_ticket = 1;
+    size_t bytes_in_use = 0;
+    bool stop = false;
+    BatchSolver bs;
+    std::thread worker;
+    lqcd_status fatal = LQCD_OK;
+    std::string fatal_msg;
+};
+
+namespace lqcd {
+
+// device bytes one right-hand side holds while admitted (float-float solution
+// and source, FP32 solution increment, four sloppy vectors, the FP64 solution
+// halves and the reduction partials)
+static size_t rhs_bytes(const lqcd_lattice &lat, lqcd_prec sloppy)
+{
+    size_t Vh = (size_t)make_geo(lat).Vh;
+    double s = sloppy == LQCD_F32 ? 96 : (sloppy == LQCD_F16N ? 52 : 48);
+    return (size_t)(Vh * (2 * 192 + 96 + 4 * s + 2 * 192) + 65536);
+}
+
+static lqcd_status gauge_setup(lqcd_service *S, SvcGauge &g)
+{
+    if (g.ready) return LQCD_OK;
+    cudaStream_t s = S->stream;
+    const lqcd_lattice &lat = g.U->lat;
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_GAUGE, S->prm.cg.sloppy, 12, &g.Us.f));
+    LQCD_TRY(lqcd_field_copy(g.Us.f, g.U, s));
+    LQCD_TRY(field_alloc_df(&lat, LQCD_GAUGE, &g.Udf.f));
+    LQCD_TRY(split_links(g.Udf.f, g.U, s));
+    g.shared.temps_only = true;
+    LQCD_TRY(g.shared.ensure(lat, S->prm.cg.sloppy, s));
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &g.be.f));
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F64, 0, &g.bo.f));
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &g.bp.f));
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &g.src.f));
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F64, 0, &g.tmpo.f));
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &g.mxe.f));
+    LQCD_TRY(g.part.alloc(sizeof(double) * (nblocks_for(make_geo(lat).Vh, 256) + 1), s));
+    LQCD_TRY(g.scal.alloc(sizeof(double) * 4, s));
+    g.ready = true;
+    return LQCD_OK;
+}
+
+// b_e, b_o of the point source of component comp at the request's site
+static lqcd_status make_source(SvcGauge &g, const lqcd_solve_req &q, int comp, cudaStream_t s)
+{
+    const lqcd_lattice &lat = g.U->lat;
+    const int *c = q.site;
+    int lex = c[0] + lat.dims[0] * (c[1] + lat.dims[1] * (c[2] + lat.dims[2] * c[3]));
+    int par = (c[0] + c[1] + c[2] + c[3]) & 1;
+    LQCD_CUDA(cudaMemsetAsync(g.be.f->data, 0, g.be.f->bytes, s));
+    LQCD_CUDA(cudaMemsetAsync(g.bo.f->data, 0, g.bo.f->bytes, s));
+    point_source_kernel<<<1, 1, 0, s>>>((double2 *)(par ? g.bo.f : g.be.f)->data, g.be.f->Vh, lex >> 1, comp);
+    LQCD_LAUNCHED();
+    return LQCD_OK;
+}
+
+// start (or restart from its solution) one right-hand side's normal-equation solve
+static lqcd_status rhs_start(lqcd_service *S, SvcGauge &g, SvcRequest &r, SvcRhs &h, bool warm)
+{
+    cudaStream_t s = S->stream;
+    LQCD_TRY(make_source(g, r.req, h.comp, s));
+    // b'_e = b_e + kappa D_eo b_o;  src = Mhat^dag b'_e
+    LQCD_TRY(dslash_xpay(g.bp.f, g.U, g.bo.f, 0, g.be.f, r.req.kappa, nullptr, nullptr, s));
+    LQCD_TRY(mhat_apply(g.src.f, g.U, g.bp.f, r.req.kappa, 1, g.tmpo.f, nullptr, s));
+    h.run = CgRun();
+    h.run.ws = h.ws.get(), h.run.x = h.y.f, h.run.U = g.U, h.run.Us = g.Us.f, h.run.b = g.src.f;
+    h.run.kappa = r.req.kappa;
+    h.run.prm = S->prm.cg;
+    h.run.prm.tol = h.tol_n;
+    h.run.prm.guess = warm ? 1 : 0;
+    // start() has read src (into the solve's own float-float source) before it
+    // returns; a failure leaves the run done with its status
+    h.run.start(s, (CgScalars *)h.ws->sc.p);
+    if (!h.run.done) S->bs.add(&h.run);
+    return LQCD_OK;
+}
+
+static lqcd_status admit(lqcd_service *S, SvcRequest &r)
+{
+    SvcGauge &g = *S->gauges[r.req.gauge];
+    LQCD_TRY(gauge_setup(S, g));
+    const lqcd_lattice &lat = g.U->lat;
+    for (int k = 0; k < r.req.nrhs; k++) {
+        std::unique_ptr<SvcRhs> h(new SvcRhs());
+        h->comp = k;
+        h->tol_n = S->prm.cg.tol / 30.0;
+        h->ws->udf_ext = g.Udf.f;
+        h->ws->tmp_from = &g.shared;
+        LQCD_TRY(h->ws->ensure(lat, S->prm.cg.sloppy, S->stream));
+        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &h->y.f));
+        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F64, 0, &h->xo.f));
+        LQCD_TRY(rhs_start(S, g, r, *h, false));
+        r.rhs.push_back(std::move(h));
+    }
+    return LQCD_OK;
+}
+
+// |a - b|^2 of two FP64 fields of one parity, added to *acc
+static lqcd_status add_diff_norm(SvcGauge &g, const lqcd_field *a, const lqcd_field *b, double *acc, cudaStream_t s)
+{
+    int Vh = a->Vh, nb = nblocks_for(Vh, 256);
+    diff_norm_kernel<<<nb, 256, 0, s>>>(spinor_ref<LQCD_F64>(a), spinor_ref<LQCD_F64>(b), (double *)g.part.p, Vh);
+    LQCD_LAUNCHED();
+    LQCD_TRY(reduce_partials((double *)g.part.p, nb, 1, (double *)g.scal.p, s));
+    double v = 0;
+    LQCD_TRY(read_scalars((double *)g.scal.p, &v, 1, s));
+    *acc += v;
+    return LQCD_OK;
+}
+
+// x_o = b_o + kappa D_oe y and the full residual |b - M x| / |b| (|b| = 1);
+// a miss continues from x_e with a tighter normal-equation tolerance
+static lqcd_status rhs_check(lqcd_service *S, SvcGauge &g, SvcRequest &r, SvcRhs &h, bool *restarted)
+{
+    cudaStream_t s = S->stream;
+    const double kappa = r.req.kappa;
+    *restarted = false;
+    h.iters += h.run.inf.iters;
+    if (h.run.status != LQCD_OK) {
+        h.status = h.run.status;
+        h.finalized = true;
+        return LQCD_OK;
+    }
+    LQCD_TRY(make_source(g, r.req, h.comp, s));
+    LQCD_TRY(dslash_xpay(h.xo.f, g.U, h.y.f, 0, g.bo.f, kappa, nullptr, nullptr, s));
+    // (M x)_e = x_e - kappa D_eo x_o,  (M x)_o = x_o - kappa D_oe x_e
+    LQCD_TRY(dslash_xpay(g.mxe.f, g.U, h.xo.f, 0, h.y.f, -kappa, nullptr, nullptr, s));
+    LQCD_TRY(dslash_xpay(g.tmpo.f, g.U, h.y.f, 0, h.xo.f, -kappa, nullptr, nullptr, s));
+    double rr = 0;
+    LQCD_TRY(add_diff_norm(g, g.be.f, g.mxe.f, &rr, s));
+    LQCD_TRY(add_diff_norm(g, g.bo.f, g.tmpo.f, &rr, s));
+    h.rel_res = std::sqrt(rr);
+    if (!std::isfinite(h.rel_res)) {
+        h.status = LQCD_ENUMERIC;
+        h.finalized = true;
+        return LQCD_OK;
+    }
+    if (h.rel_res <= S->prm.cg.tol || h.refinements >= 3) {
+        h.status = h.rel_res <= S->prm.cg.tol ? LQCD_OK : LQCD_ENOCONV;
+        h.finalized = true;
+        return LQCD_OK;
+    }
+    // the full residual scales roughly like the normal-equation one: aim at half the tolerance
+    h.refinements++;
+    h.tol_n *= std::min(0.1, std::max(1e-3, 0.5 * S->prm.cg.tol / h.rel_res));
+    LQCD_TRY(rhs_start(S, g, r, h, true));
+    if (h.run.done) return rhs_check(S, g, r, h, restarted);
+    *restarted = true;
+    return LQCD_OK;
+}
+
+static void finish_request(lqcd_service *S, SvcRequest &r, lqcd_status st)
+{
+    r.t_done = Clock::now();
+    lqcd_solve_result &o = r.result;
+    o.status = st;
+    o.nrhs = r.req.nrhs;
+    o.iters = 0;
+    o.refinements = 0;
+    o.true_rel_res_max = 0;
+    for (auto &h : r.rhs) {
+        o.iters += h->iters;
+        o.refinements += h->refinements;
+        o.true_rel_res_max = std::max(o.true_rel_res_max, h->rel_res);
+        if (o.status == LQCD_OK && h->status != LQCD_OK) o.status = h->status;
+        h->ws.reset(); // the solver fields go; the solution halves stay until release
+    }
+    o.queue_s = std::chrono::duration<double>(r.t_admit - r.t_submit).count();
+    o.latency_s = std::chrono::duration<double>(r.t_done - r.t_submit).count();
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->bytes_in_use -= r.bytes;
+    r.bytes = (size_t)r.req.nrhs * 2 * 192 * (size_t)make_geo(S->gauges[r.req.gauge]->U->lat).Vh;
+    S->bytes_in_use += r.bytes; // the solutions until lqcd_solve_release
+    r.done = true;
+    S->cv.notify_all();
+}
+
+static lqcd_status worker_step(lqcd_service *S)
+{
+    // admit in arrival order while the budget allows (a request alone always runs)
+    std::vector<SvcRequest *> admitted;
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        while (!S->queue.empty()) {
+            SvcRequest *r = S->queue.front();
+            size_t need = r->bytes;
+            bool alone = S->running.empty() && admitted.empty();
+            bool fits = S->bytes_in_use + need <= S->prm.hbm_budget;
+            bool rhs_ok = S->prm.max_active_rhs <= 0 ||
+                          (int)S->bs.active.size() + r->req.nrhs <= S->prm.max_active_rhs;
+            if (!alone && !(fits && rhs_ok)) break;
+            S->queue.pop_front();
+            S->bytes_in_use += need;
+            r->admitted = true;
+            r->t_admit = Clock::now();
+            admitted.push_back(r);
+        }
+        if (admitted.empty() && S->running.empty()) {
+            if (S->stop) return LQCD_OK;
+            S->cv.wait_for(lk, std::chrono::milliseconds(50));
+            return LQCD_OK;
+        }
+    }
+    for (SvcRequest *r : admitted) {
+        lqcd_status rc = admit(S, *r);
+        if (rc != LQCD_OK) {
+            for (auto &h : r->rhs) {
+                h->finalized = true;
+                h->status = rc;
+            }
+            finish_request(S, *r, rc);
+            continue;
+        }
+        S->running.push_back(r);
+    }
+    LQCD_TRY(S->bs.step(S->prm.cg.sloppy, S->stream));
+    std::vector<SvcRequest *> still;
+    for (SvcRequest *r : S->running) {
+        SvcGauge &g = *S->gauges[r->req.gauge];
+        bool all = true;
+        for (auto &h : r->rhs) {
+            if (h->finalized) continue;
+            if (!h->run.done) {
+                all = false;
+                continue;
+            }
+            bool restarted = false;
+            LQCD_TRY(rhs_check(S, g, *r, *h, &restarted));
+            if (!h->finalized) all = false;
+        }
+        if (all)
+            finish_request(S, *r, LQCD_OK);
+        else
+            still.push_back(r);
+    }
+    S->running.swap(still);
+    return LQCD_OK;
+}
+
+static void worker_main(lqcd_service *S)
+{
+    cudaSetDevice(S->device);
+    for (;;) {
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            if (S->stop && S->queue.empty() && S->running.empty()) break;
+        }
+        lqcd_status rc = worker_step(S);
+        if (rc != LQCD_OK) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->fatal = rc;
+            S->fatal_msg = lqcd_last_error();
+            for (SvcRequest *r : S->running) {
+                r->done = true;
+                r->result.status = rc;
+            }
+            for (SvcRequest *r : S->queue) {
+                r->done = true;
+                r->result.status = rc;
+            }
+            S->running.clear();
+            S->queue.clear();
+            S->cv.notify_all();
+            break;
+        }
+    }
+    cudaStreamSynchronize(S->stream);
+}
+
+} // namespace lqcd
+
+extern "C" {
+
+lqcd_status lqcd_service_create(const lqcd_service_params *params, lqcd_service **out)
+{
+    LQCD_REQUIRE(params && out, "service_create: NULL argument");
+    LQCD_REQUIRE(params->cg.sloppy != LQCD_F64 && params->cg.tol > 0 && params->cg.maxiter > 0 &&
+                     params->cg.delta > 0 && params->cg.delta < 1,
+                 "service_create: needs a mixed-precision solver (sloppy F32/F16N/BF16, 0 < delta < 1)");
+    LQCD_REQUIRE(params->hbm_budget > 0, "service_create: hbm_budget must be positive");
+    lqcd_service *S = new lqcd_service();
+    S->prm = *params;
+    cudaError_t e = cudaGetDevice(&S->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete S;
+        return cuda_fail(e, "service stream", __FILE__, __LINE__);
+    }
+    S->worker = std::thread(worker_main, S);
+    *out = S;
+    return LQCD_OK;
+}
+
+lqcd_status lqcd_service_add_gauge(lqcd_service *S, lqcd_field *U, int *id)
+{
+    LQCD_REQUIRE(S && U && id, "service_add_gauge: NULL argument");
+    LQCD_REQUIRE(U->kind == LQCD_GAUGE && U->prec == LQCD_F64, "service_add_gauge: U must be an F64 gauge field");
+    std::lock_guard<std::mutex> lk(S->mu);
+    std::unique_ptr<SvcGauge> g(new SvcGauge());
+    g->U = U;
+    S->gauges.push_back(std::move(g));
+    *id = (int)S->gauges.size() - 1;
+    return LQCD_OK;
+}
+
+lqcd_status lqcd_solve_submit(lqcd_service *S, const lqcd_solve_req *req, uint64_t *ticket)
+{
+    LQCD_REQUIRE(S && req && ticket, "solve_submit: NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->fatal != LQCD_OK) {
+        set_error("solve_submit: the service stopped after an error: %s", S->fatal_msg.c_str());
+        return S->fatal;
+    }
+    LQCD_REQUIRE(req->gauge >= 0 && req->gauge < (int)S->gauges.size(), "solve_submit: unknown gauge %d", req->gauge);
+    LQCD_REQUIRE(req->nrhs >= 1 && req->nrhs <= 12, "solve_submit: nrhs must lie in 1..12");
+    const lqcd_lattice &lat = S->gauges[req->gauge]->U->lat;
+    for (int mu = 0; mu < 4; mu++)
+        LQCD_REQUIRE(req->site[mu] >= 0 && req->site[mu] < lat.dims[mu], "solve_submit: source site outside the lattice");
+    std::unique_ptr<SvcRequest> r(new SvcRequest());
+    r->ticket = S->next_ticket++;
+    r->req = *req;
+    r->t_submit = Clock::now();
+    r->bytes = (size_t)req->nrhs * rhs_bytes(lat, S->prm.cg.sloppy);
+    *ticket = r->ticket;
+    S->queue.push_back(r.get());
+    S->reqs[r->ticket] = std::move(r);
+    S->cv.notify_all();
+    return LQCD_OK;
+}
+
+lqcd_status lqcd_solve_poll(lqcd_service *S, uint64_t ticket, lqcd_solve_result *out)
+{
+    LQCD_REQUIRE(S && out, "solve_poll: NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    LQCD_REQUIRE(it != S->reqs.end(), "solve_poll: unknown ticket %llu", (unsigned long long)ticket);
+    if (!it->second->done) return LQCD_EAGAIN;
+    *out = it->second->result;
+    return LQCD_OK;
+}
+
+lqcd_status lqcd_solve_solution(lqcd_service *S, uint64_t ticket, int k, lqcd_field **x_even, lqcd_field **x_odd)
+{
+    LQCD_REQUIRE(S && x_even && x_odd, "solve_solution: NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    LQCD_REQUIRE(it != S->reqs.end(), "solve_solution: unknown ticket");
+    SvcRequest &r = *it->second;
+    if (!r.done) return LQCD_EAGAIN;
+    LQCD_REQUIRE(k >= 0 && k < (int)r.rhs.size(), "solve_solution: right-hand side %d not available", k);
+    *x_even = r.rhs[k]->y.f;
+    *x_odd = r.rhs[k]->xo.f;
+    return LQCD_OK;
+}
+
+lqcd_status lqcd_solve_release(lqcd_service *S, uint64_t ticket)
+{
+    LQCD_REQUIRE(S, "solve_release: NULL service");
+    std::unique_ptr<SvcRequest> r;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->reqs.find(ticket);
+        LQCD_REQUIRE(it != S->reqs.end(), "solve_release: unknown ticket");
+        if (!it->second->done) return LQCD_EAGAIN;
+        S->bytes_in_use -= it->second->bytes;
+        r = std::move(it->second);
+        S->reqs.erase(it);
+        S->cv.notify_all();
+    }
+    return LQCD_OK; // r's fields are freed here
+}
+
+lqcd_status lqcd_service_destroy(lqcd_service *S)
+{
+    if (!S) return LQCD_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        S->cv.notify_all();
+    }
+    if (S->worker.joinable()) S->worker.join();
+    S->bs.release();
+    S->reqs.clear();
+    S->gauges.clear();
+    if (S->stream) cudaStreamDestroy(S->stream);
+    delete S;
+    return LQCD_OK;
+}
+
+} // extern "C"

@@ -61,6 +61,24 @@ class HmcParams(ctypes.Structure):
                 ("chrono", ctypes.c_int), ("force_prec", ctypes.c_int)]
 
 
+class ServiceParams(ctypes.Structure):
+    _fields_ = [("cg", CgParams), ("hbm_budget", ctypes.c_size_t), ("max_active_rhs", ctypes.c_int)]
+
+
+class SolveReq(ctypes.Structure):
+    _fields_ = [("gauge", ctypes.c_int), ("kappa", ctypes.c_double), ("site", ctypes.c_int * 4),
+                ("nrhs", ctypes.c_int)]
+
+
+class SolveResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("nrhs", ctypes.c_int), ("iters", ctypes.c_int),
+                ("refinements", ctypes.c_int), ("true_rel_res_max", ctypes.c_double), ("queue_s", ctypes.c_double),
+                ("latency_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class TrajInfo(ctypes.Structure):
     _fields_ = [("dH", ctypes.c_double), ("H0", ctypes.c_double), ("H1", ctypes.c_double),
                 ("plaq", ctypes.c_double), ("u", ctypes.c_double), ("max_unitarity_dev", ctypes.c_double),
@@ -123,6 +141,13 @@ _SIGS = {
     "lqcd_batch_create": (_i, [_pp, _i, _pp]),
     "lqcd_batch_destroy": (_i, [_vp]),
     "lqcd_batch_trajectory": (_i, [_vp, ctypes.POINTER(HmcParams), ctypes.POINTER(TrajInfo), _vp]),
+    "lqcd_service_create": (_i, [ctypes.POINTER(ServiceParams), _pp]),
+    "lqcd_service_add_gauge": (_i, [_vp, _vp, ctypes.POINTER(ctypes.c_int)]),
+    "lqcd_solve_submit": (_i, [_vp, ctypes.POINTER(SolveReq), ctypes.POINTER(ctypes.c_uint64)]),
+    "lqcd_solve_poll": (_i, [_vp, ctypes.c_uint64, ctypes.POINTER(SolveResult)]),
+    "lqcd_solve_solution": (_i, [_vp, ctypes.c_uint64, _i, _pp, _pp]),
+    "lqcd_solve_release": (_i, [_vp, ctypes.c_uint64]),
+    "lqcd_service_destroy": (_i, [_vp]),
 }
 
 _lock = threading.Lock()
@@ -522,6 +547,80 @@ class Batch:
         if self.h:
             lib().lqcd_batch_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- solve service
+
+def service_params(tol=1e-10, maxiter=20000, sloppy=F16N, delta=0.003, hbm_budget=64 << 30,
+                   max_active_rhs=0) -> ServiceParams:
+    return ServiceParams(cg_params(tol=tol, maxiter=maxiter, sloppy=sloppy, delta=delta), int(hbm_budget),
+                         int(max_active_rhs))
+
+
+class Service:
+    """Point-source Wilson-Dirac solves on resident gauge fields, continuously
+    batched by the library's worker thread."""
+
+    def __init__(self, params: ServiceParams):
+        install_torch_allocator()
+        h = ctypes.c_void_p()
+        _check(lib().lqcd_service_create(ctypes.byref(params), ctypes.byref(h)), "service_create")
+        self.h = h
+        self.gauges = {}
+
+    def add_gauge(self, U: Field) -> int:
+        gid = ctypes.c_int()
+        _check(lib().lqcd_service_add_gauge(self.h, U.h, ctypes.byref(gid)), "service_add_gauge")
+        self.gauges[gid.value] = U
+        return gid.value
+
+    def submit(self, gauge, kappa, site, nrhs=12) -> int:
+        req = SolveReq(int(gauge), float(kappa), (ctypes.c_int * 4)(*[int(c) for c in site]), int(nrhs))
+        t = ctypes.c_uint64()
+        _check(lib().lqcd_solve_submit(self.h, ctypes.byref(req), ctypes.byref(t)), "solve_submit")
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else the result as a dict"""
+        r = SolveResult()
+        rc = lib().lqcd_solve_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(r))
+        if rc == EAGAIN:
+            return None
+        _check(rc, "solve_poll")
+        return r.as_dict()
+
+    def wait(self, ticket, timeout=600.0):
+        import time
+        t0 = time.perf_counter()
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                return r
+            if time.perf_counter() - t0 > timeout:
+                raise TimeoutError(f"solve {ticket} not done after {timeout} s")
+            time.sleep(2e-4)
+
+    def solution(self, ticket, k):
+        """(x_e, x_o) of right-hand side k as borrowed F64 fields"""
+        e, o = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().lqcd_solve_solution(self.h, ctypes.c_uint64(ticket), int(k), ctypes.byref(e), ctypes.byref(o)),
+               "solve_solution")
+        return e.value, o.value
+
+    def release(self, ticket):
+        _check(lib().lqcd_solve_release(self.h, ctypes.c_uint64(ticket)), "solve_release")
+
+    def close(self):
+        if self.h:
+            rc = lib().lqcd_service_destroy(self.h)
+            self.h = None
+            _check(rc, "service_destroy")
 
     def __del__(self):
         try:
