@@ -268,7 +268,9 @@ def config_block(args, sloppy):
                    f"reliable-update mixed CG: {sloppy} spinors + 12-real {sloppy} links, fp32 math, "
                    f"fp64 residual/dots, delta {args.delta}")
     c["forces"] = f"{getattr(args, 'force_prec', 'f64')} arithmetic"
-    c["initial_guess"] = "previous solution (chronological)" if getattr(args, "chrono", 0) else "zero"
+    k = int(getattr(args, "chrono", 0))
+    c["initial_guess"] = {0: "zero", 1: "previous solution (chronological)"}.get(
+        k, f"extrapolated through the last {k} solutions (chronological)")
     c["parallelism"] = f"replicas{args.gpus}" if args.gpus > 1 else "single_gpu"
     c["l2"] = "inputs larger than L2 (FP64 links 1.21 GB, spinors 0.2 GB)"
     return c
@@ -293,7 +295,7 @@ def run_ours(args):
     cg = lqcd.cg_params(tol=wl["cg_tol"], maxiter=20000, sloppy=sloppy, delta=args.delta)
     force_prec = lqcd.PREC_NAMES[args.force_prec]
     params = lqcd.hmc_params(wl["beta"], wl["kappa"], wl["tau"], args.nsteps, lqcd.OMELYAN, n_flavors=2, cg=cg,
-                             force_prec=force_prec, chrono=bool(args.chrono))
+                             force_prec=force_prec, chrono=int(args.chrono))
 
     U = lqcd.gauge_field(dims)
     lqcd.gauge_start(U, SEED, EPS, chain=rank)
@@ -353,7 +355,7 @@ def run_ours(args):
         st64 = lqcd.HmcState(U64, seed=SEED, chain=rank, traj0=args.warmup)
         p64 = lqcd.hmc_params(wl["beta"], wl["kappa"], wl["tau"], args.nsteps, lqcd.OMELYAN, n_flavors=2,
                               cg=lqcd.cg_params(tol=wl["cg_tol"], maxiter=20000, sloppy=lqcd.F64),
-                              chrono=bool(args.chrono))
+                              chrono=int(args.chrono))
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -446,7 +448,7 @@ def run_chains(args):
     kappas = np.linspace(0.150, 0.157, n)
     cg = lqcd.cg_params(tol=1e-10, maxiter=20000, sloppy=lqcd.F16N, delta=args.delta)
     params = [lqcd.hmc_params(float(betas[i]), float(kappas[i]), 1.0, 10, lqcd.LEAPFROG, cg=cg,
-                              force_prec=lqcd.F32, chrono=bool(args.chrono)) for i in range(n)]
+                              force_prec=lqcd.F32, chrono=int(args.chrono)) for i in range(n)]
 
     def make():
         fields, states = [], []
@@ -492,7 +494,8 @@ def run_chains(args):
             "data": "synthetic",
             "config": {"workload": "chains64_8^4x32_12^4x24_16^3x32x8", "chains": n, "sites_total": sites,
                        "beta": [5.6, 5.9], "kappa": [0.150, 0.157], "integrator": "leapfrog", "nsteps": 10,
-                       "tau": 1.0, "start_eps": 0.3, "initial_guess": "chronological" if args.chrono else "zero"},
+                       "tau": 1.0, "start_eps": 0.3, "initial_guess": {0: "zero", 1: "previous solution"}.get(
+                           args.chrono, f"extrapolated through the last {args.chrono} solutions")},
             "gpu_launches": launches,
             "sequential": {"value": n * args.steps / t_seq, "ms_per_step": t_seq / args.steps * 1e3},
             "batched_speedup": t_seq / t_batch,
@@ -614,9 +617,10 @@ def main(argv=None):
     ap.add_argument("--sloppy", choices=("f32", "f16n", "bf16"), default="f16n")
     ap.add_argument("--delta", type=float, default=0.003)
     ap.add_argument("--force-prec", choices=("f64", "f32"), default="f32")
-    ap.add_argument("--chrono", type=int, choices=(0, 1), default=1,
-                    help="start each solve after the first of a trajectory from the previous solution "
-                         "(both the mixed and the FP64 path)")
+    ap.add_argument("--chrono", type=int, choices=(0, 1, 2, 3, 4), default=3,
+                    help="initial guess of each solve after the first of a trajectory: 0 zero, 1 the previous "
+                         "solution, k >= 2 extrapolated through the last k solutions (both the mixed and the "
+                         "FP64 path)")
     ap.add_argument("--dims", type=int, nargs=4, default=WORKLOAD["dims"])
     ap.add_argument("--nsteps", type=int, default=WORKLOAD["nsteps"],
                     help="MD steps per trajectory (16 for the benchmarked workload)")

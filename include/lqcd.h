@@ -332,14 +332,18 @@ typedef struct {
     lqcd_cg_params cg;          /* solver of every force and action evaluation */
     int reunitarize;            /* 1: reunitarize the links after the accept/reject */
     int metropolis;             /* 1: accept iff u < exp(-dH); 0: always accept */
-    int chrono;                 /* 1: every solve after the first of a trajectory starts from the
-                                   previous solution (a chronological initial guess, paper Sec. 6.2);
-                                   reversibility then holds to the solver tolerance only */
+    int chrono;                 /* chronological initial guess (paper Sec. 6.2) for every solve after
+                                   the first of a trajectory: 0 none (x0 = 0); 1 the previous
+                                   solution; k = 2..4 the polynomial through the last k solutions
+                                   at their molecular-dynamics times, extrapolated to the current
+                                   time (a solve at the previous solve's time starts from its
+                                   solution).  Reversibility then holds to the solver tolerance only */
     lqcd_prec force_prec;       /* arithmetic of the molecular dynamics: LQCD_F64, or LQCD_F32: both
                                    forces in FP32 from an FP32 12-real copy of the links (increments
                                    accumulated into the FP64 momenta) and the link update's
-                                   exponential by Cayley-Hamilton in FP32, re-unitarized in FP64
-                                   before the FP64 product with the FP64 links */
+                                   exponential by Cayley-Hamilton in FP32, re-unitarized and
+                                   multiplied onto the FP64 links in float-float arithmetic
+                                   (~48 bits: the links stay in SU(3) to ~1e-14 per update) */
 } lqcd_hmc_params;
 
 typedef struct {

@@ -37,9 +37,34 @@ __global__ void metropolis_uniform_kernel(double *out, uint32_t seed, uint32_t c
     out[0] = u52(x.x, x.y);
 }
 
+// out = sum_{i<m} w_i x_i over n double2 elements (m <= 4)
+__global__ void combine_kernel(double2 *out, const double2 *x0, const double2 *x1, const double2 *x2,
+                               const double2 *x3, double w0, double w1, double w2, double w3, int m, size_t n)
+{
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 a = x0[i];
+    double2 r = make_double2(w0 * a.x, w0 * a.y);
+    if (m > 1) {
+        a = x1[i];
+        r.x += w1 * a.x, r.y += w1 * a.y;
+    }
+    if (m > 2) {
+        a = x2[i];
+        r.x += w2 * a.x, r.y += w2 * a.y;
+    }
+    if (m > 3) {
+        a = x3[i];
+        r.x += w3 * a.x, r.y += w3 * a.y;
+    }
+    out[i] = r;
+}
+
 } // namespace lqcd
 
 using namespace lqcd;
+
+constexpr int CHRONO_MAX = 4;
 
 struct lqcd_hmc_state {
     lqcd_field *U = nullptr; // borrowed
@@ -51,6 +76,13 @@ struct lqcd_hmc_state {
     DevBuf part, scal;
     double H0 = 0;
     bool have_guess = false; // X holds a solution for the current phi
+    // solutions of this trajectory's solves and the molecular-dynamics times
+    // (sum of the drifts since the refresh) of their links, for the
+    // extrapolated initial guess; hist[(head - 1) mod CHRONO_MAX] is the latest
+    double md_time = 0;
+    FieldPtr hist[CHRONO_MAX];
+    double hist_t[CHRONO_MAX] = {0, 0, 0, 0};
+    int n_hist = 0, head = 0;
     // statistics of the current trajectory
     int cg_iters = 0, n_solves = 0, cg_failures = 0;
     double cg_res_max = 0;
@@ -70,6 +102,7 @@ static lqcd_status check_params(const lqcd_hmc_params *p)
                      "hmc: cg delta must lie in (0, 1) for a mixed solve");
     }
     LQCD_REQUIRE(p->force_prec == LQCD_F64 || p->force_prec == LQCD_F32, "hmc: force_prec must be F64 or F32");
+    LQCD_REQUIRE(p->chrono >= 0 && p->chrono <= CHRONO_MAX, "hmc: chrono must lie in 0..%d", CHRONO_MAX);
     return LQCD_OK;
 }
 
@@ -95,13 +128,67 @@ static lqcd_field *sloppy_links(lqcd_hmc_state *st, const lqcd_hmc_params *p)
     return (p->n_flavors == 2 && p->cg.sloppy != LQCD_F64) ? st->Us.f : nullptr;
 }
 
+// The initial guess of the next solve, in X; returns whether there is one.
+// chrono 1: the previous solution (already in X).  chrono k >= 2: the
+// polynomial through the last k solutions at their molecular-dynamics times,
+// evaluated at the current time (Lagrange form); the trajectory's solves come
+// at evenly spaced times, so this is the extrapolation x_n ~ 2 x_{n-1} -
+// x_{n-2} (k = 2), 3 x_{n-1} - 3 x_{n-2} + x_{n-3} (k = 3), ...  A solve at the
+// time of the previous one (the action at the end of the trajectory) starts
+// from the previous solution.
+static lqcd_status prepare_guess(lqcd_hmc_state *st, const lqcd_hmc_params *p, cudaStream_t s, int *guess)
+{
+    *guess = (p->chrono && st->have_guess) ? 1 : 0;
+    if (!*guess || p->chrono < 2 || st->n_hist < 2) return LQCD_OK;
+    const int latest = (st->head + CHRONO_MAX - 1) % CHRONO_MAX;
+    if (st->hist_t[latest] == st->md_time) return LQCD_OK;
+    int idx[CHRONO_MAX], m = 0;
+    const int kmax = std::min(p->chrono, CHRONO_MAX);
+    for (int k = 0; k < st->n_hist && m < kmax; k++) {
+        int i = (st->head + CHRONO_MAX - 1 - k) % CHRONO_MAX;
+        bool dup = false;
+        for (int j = 0; j < m; j++) dup = dup || st->hist_t[idx[j]] == st->hist_t[i];
+        if (!dup) idx[m++] = i;
+    }
+    if (m < 2) return LQCD_OK;
+    double w[CHRONO_MAX] = {0, 0, 0, 0};
+    const double2 *x[CHRONO_MAX] = {nullptr, nullptr, nullptr, nullptr};
+    for (int a = 0; a < m; a++) {
+        double l = 1.0;
+        for (int b = 0; b < m; b++)
+            if (b != a)
+                l *= (st->md_time - st->hist_t[idx[b]]) / (st->hist_t[idx[a]] - st->hist_t[idx[b]]);
+        w[a] = l;
+        x[a] = (const double2 *)st->hist[idx[a]].f->data;
+    }
+    size_t n = st->X.f->bytes / sizeof(double2);
+    combine_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((double2 *)st->X.f->data, x[0], x[1], x[2], x[3],
+                                                               w[0], w[1], w[2], w[3], m, n);
+    LQCD_LAUNCHED();
+    return LQCD_OK;
+}
+
+// record a solve's solution for later guesses
+static lqcd_status record_solution(lqcd_hmc_state *st, const lqcd_hmc_params *p, bool ok, cudaStream_t s)
+{
+    st->have_guess = ok;
+    if (!ok || p->chrono < 2) return LQCD_OK;
+    lqcd_field *&slot = st->hist[st->head].f;
+    if (!slot) LQCD_TRY(lqcd_field_alloc(&st->U->lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &slot));
+    LQCD_CUDA(cudaMemcpyAsync(slot->data, st->X.f->data, st->X.f->bytes, cudaMemcpyDeviceToDevice, s));
+    st->hist_t[st->head] = st->md_time;
+    st->head = (st->head + 1) % CHRONO_MAX;
+    st->n_hist = std::min(st->n_hist + 1, CHRONO_MAX);
+    return LQCD_OK;
+}
+
 static lqcd_status solve(lqcd_hmc_state *st, const lqcd_hmc_params *p, cudaStream_t s)
 {
     lqcd_cg_info info{};
     lqcd_cg_params cg = p->cg;
-    cg.guess = (p->chrono && st->have_guess) ? 1 : 0;
+    LQCD_TRY(prepare_guess(st, p, s, &cg.guess));
     lqcd_status rc = cg_solve_ws(st->ws, st->X.f, st->U, sloppy_links(st, p), st->phi.f, p->kappa, cg, &info, s);
-    st->have_guess = (rc == LQCD_OK || rc == LQCD_ENOCONV);
+    LQCD_TRY(record_solution(st, p, rc == LQCD_OK || rc == LQCD_ENOCONV, s));
     st->cg_iters += info.iters;
     st->n_solves++;
     st->cg_res_max = std::max(st->cg_res_max, info.true_rel_res);
@@ -144,6 +231,7 @@ static lqcd_status kick(lqcd_hmc_state *st, const lqcd_hmc_params *p, double c, 
 static lqcd_status drift(lqcd_hmc_state *st, const lqcd_hmc_params *p, double c, cudaStream_t s)
 {
     bool fast = p->force_prec == LQCD_F32;
+    st->md_time += c;
     return link_update_dev(st->U, st->P.f, c, sloppy_links(st, p), fast ? st->Uf.f : nullptr, fast, s);
 }
 
@@ -165,6 +253,8 @@ static double hamiltonian_from(const lqcd_hmc_state *st, const lqcd_hmc_params *
 static lqcd_status refresh(lqcd_hmc_state *st, const lqcd_hmc_params *p, double *H0, cudaStream_t s)
 {
     st->have_guess = false; // a new phi: the last solution is no guess for it
+    st->n_hist = 0;
+    st->md_time = 0;
     LQCD_TRY(ensure_sloppy(st, p, s));
     LQCD_TRY(momentum_refresh_dev(st->P.f, st->seed, st->chain, st->traj, s));
     double *d = (double *)st->scal.p;
@@ -407,7 +497,7 @@ static lqcd_status batch_solve(lqcd_batch *B, const lqcd_hmc_params *p, cudaStre
         r.ws = &st->ws, r.x = st->X.f, r.U = st->U, r.Us = sloppy_links(st, &p[i]), r.b = st->phi.f;
         r.kappa = p[i].kappa;
         r.prm = p[i].cg;
-        r.prm.guess = (p[i].chrono && st->have_guess) ? 1 : 0;
+        LQCD_TRY(prepare_guess(st, &p[i], s, &r.prm.guess));
         LQCD_TRY(st->ws.ensure(st->U->lat, r.prm.sloppy, s));
         r.start(s, (CgScalars *)B->scal.p + i);
         ptrs.push_back(&r);
@@ -419,7 +509,7 @@ static lqcd_status batch_solve(lqcd_batch *B, const lqcd_hmc_params *p, cudaStre
         st->cg_iters += r.inf.iters;
         st->n_solves++;
         st->cg_res_max = std::max(st->cg_res_max, r.inf.true_rel_res);
-        st->have_guess = (r.status == LQCD_OK || r.status == LQCD_ENOCONV);
+        LQCD_TRY(record_solution(st, &p[i], r.status == LQCD_OK || r.status == LQCD_ENOCONV, s));
         if (r.status == LQCD_ENOCONV)
             st->cg_failures++;
         else if (r.status != LQCD_OK)

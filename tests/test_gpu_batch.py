@@ -66,7 +66,7 @@ def test_batched_solve_edge_cases():
                             [0.15, 0.15], lqcd.cg_params())
 
 
-@pytest.mark.parametrize("chrono", [False, True])
+@pytest.mark.parametrize("chrono", [0, 1, 3])
 def test_batched_chains_equal_solo_chains(chrono):
     specs = [((4, 4, 4, 4), 5.6, 0.150, 1), ((6, 4, 2, 10), 5.7, 0.153, 2), ((8, 6, 6, 12), 5.9, 0.157, 3)]
     cg = lqcd.cg_params(tol=1e-10, sloppy=lqcd.F16N, delta=0.01)

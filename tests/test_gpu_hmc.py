@@ -117,3 +117,40 @@ def test_chronological_guess_trajectory(sloppy):
     assert np.max(np.abs(U1 - U0)) < 1e-9
     assert g1["cg_iters"] < 0.85 * g0["cg_iters"], (g1["cg_iters"], g0["cg_iters"])
     assert g1["n_solves"] == g0["n_solves"] == 18 and g1["cg_true_rel_res_max"] <= 1e-12
+
+
+@pytest.mark.parametrize("order", [2, 3, 4])
+def test_extrapolated_guess_trajectory(order):
+    """chrono k >= 2 starts each solve from the extrapolation through the last
+    k solutions: the same trajectory to the solver tolerance, fewer iterations
+    than the previous-solution guess, every solve within tolerance"""
+    Uh = orc.gauge_start(DIMS, seed=1, eps=0.3)
+    cg = lqcd.cg_params(tol=1e-12, sloppy=lqcd.F16N, delta=0.01)
+    base = dict(beta=5.6, kappa=0.156, tau=0.5, nsteps=8, integrator=lqcd.OMELYAN, cg=cg)
+    U0, (g0,) = _run_gpu(Uh, lqcd.hmc_params(**base), 1, 1)
+    U1, (g1,) = _run_gpu(Uh, lqcd.hmc_params(**base, chrono=1), 1, 1)
+    Uk, (gk,) = _run_gpu(Uh, lqcd.hmc_params(**base, chrono=order), 1, 1)
+    assert abs(gk["dH"] - g0["dH"]) < 1e-7, (gk["dH"], g0["dH"])
+    assert np.max(np.abs(Uk - U0)) < 1e-9
+    assert gk["cg_iters"] < g1["cg_iters"], (gk["cg_iters"], g1["cg_iters"])
+    assert gk["n_solves"] == 18 and gk["cg_true_rel_res_max"] <= 1e-12 and gk["cg_failures"] == 0
+
+
+def test_extrapolated_guess_md_steps_and_leapfrog():
+    """separate md_step calls (two solves at the same links between steps) and
+    the leapfrog spacing give the same trajectory as the zero guess"""
+    Uh = orc.gauge_start(DIMS, seed=2, eps=0.3)
+    cg = lqcd.cg_params(tol=1e-12, sloppy=lqcd.F16N, delta=0.01)
+    for integ in (lqcd.LEAPFROG, lqcd.OMELYAN):
+        out = []
+        for k in (0, 3):
+            p = lqcd.hmc_params(5.6, 0.156, 0.5, 4, integ, cg=cg, chrono=k)
+            U = lqcd.gauge_field(DIMS).upload(Uh)
+            st = lqcd.HmcState(U, seed=4, chain=0)
+            st.refresh(p)
+            for _ in range(4):
+                st.md_step(p)
+            out.append((U.download(), st.hamiltonian(p)))
+            st.close()
+        assert np.max(np.abs(out[1][0] - out[0][0])) < 1e-9
+        assert abs(out[1][1] - out[0][1]) < 1e-7
