@@ -348,6 +348,11 @@ static lqcd_status true_residual(CgWorkspace &ws, const lqcd_field *x, const lqc
 }
 
 // float-float copy of FP64 links (for owners that share one copy among solves)
+lqcd_status df_to_f64(lqcd_field *dst, const lqcd_field *src_df, cudaStream_t s)
+{
+    return convert_spinor<PREC_DF, LQCD_F64, double>(dst, src_df, s);
+}
+
 lqcd_status split_links(lqcd_field *Udf, const lqcd_field *U, cudaStream_t s)
 {
     split_gauge_kernel<<<nblocks_for(8L * U->Vh, BB), BB, 0, s>>>(gauge_ref<PREC_DF>(Udf), gauge_ref<LQCD_F64>(U),

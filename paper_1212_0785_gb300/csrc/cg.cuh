@@ -72,6 +72,8 @@ struct CgRun {
 };
 
 lqcd_status split_links(lqcd_field *Udf, const lqcd_field *U, cudaStream_t s);
+// FP64 copy of a float-float spinor field (rounded hi + lo)
+lqcd_status df_to_f64(lqcd_field *dst, const lqcd_field *src_df, cudaStream_t s);
 
 lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, const lqcd_field *Us,
                         const lqcd_field *b, double kappa, const lqcd_cg_params &prm, lqcd_cg_info *info,

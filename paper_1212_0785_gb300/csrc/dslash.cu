@@ -97,9 +97,10 @@ __global__ void __launch_bounds__(DS_BLOCK) dslash_cg_kernel(SpinorRef<SP> in, G
 //
 // The float-float products of the mixed solver's accurate residual are long
 // chains of dependent FP32 operations, so this kernel spreads each output
-// site over three threads, one per colour row a of the result: every thread
-// projects the whole neighbour half spinor (L1 serves the repeated loads) and
-// multiplies it by row a of U (column a of U^dag), accumulating exact leading
+// site over three threads, one per colour a.  Each thread first projects
+// colour a of the eight neighbour spinors onto half spinors and leaves them in
+// shared memory; after one barrier it multiplies all three colours of each
+// half spinor by row a of U (column a of U^dag), accumulating exact leading
 // products with a single normalisation per dot product.
 
 constexpr int DF_SITES = 64; // sites per block; blockDim = (64, 3)
@@ -148,27 +149,74 @@ __device__ __forceinline__ void acc_hop(DfAcc (&ar)[4], DfAcc (&ai)[4], const Cx
     }
 }
 
+// colour a of (1 + S gamma_mu) psi at site nb, rows 0 and 1 (the table above project())
+template <int MU, int S>
+__device__ __forceinline__ void project_colour_df(const SpinorRef<PREC_DF> &in, int nb, int a, Cx<Df> &h0,
+                                                  Cx<Df> &h1)
+{
+    Cx<Df> p[4];
+#pragma unroll
+    for (int sp = 0; sp < 4; sp++) {
+        float4 v = ldg(in.d + (size_t)(sp * 3 + a) * in.Vh + nb);
+        p[sp] = Cx<Df>{Df(v.x, v.y), Df(v.z, v.w)};
+    }
+    if (MU == 0) {
+        h0 = p[0] + s_i<S>(p[3]);
+        h1 = p[1] + s_i<S>(p[2]);
+    } else if (MU == 1) {
+        h0 = p[0] - s_1<S>(p[3]);
+        h1 = p[1] + s_1<S>(p[2]);
+    } else if (MU == 2) {
+        h0 = p[0] + s_i<S>(p[2]);
+        h1 = p[1] - s_i<S>(p[3]);
+    } else {
+        h0 = p[0] + s_1<S>(p[2]);
+        h1 = p[1] + s_1<S>(p[3]);
+    }
+}
+
+// the projected half spinors of one block: [hop][row][colour][site], hop 2 mu
+// forward, 2 mu + 1 backward (48 KiB)
+struct DfHalves {
+    float4 h[8][2][3][DF_SITES];
+};
+
 template <int MU, int FS, int BS>
-__device__ __forceinline__ void hop_dir_df(DfAcc (&ar)[4], DfAcc (&ai)[4], const SpinorRef<PREC_DF> &in,
-                                           const GaugeRef<PREC_DF> &U, const Geo &g, int cb, int out_par, int a,
-                                           int nf, int nbk, bool wrap_f, bool wrap_b)
+__device__ __forceinline__ void project_dir_df(DfHalves &sh, const SpinorRef<PREC_DF> &in, int x, int a, int nf,
+                                               int nbk)
+{
+    Cx<Df> h0, h1;
+    project_colour_df<MU, FS>(in, nf, a, h0, h1);
+    sh.h[2 * MU][0][a][x] = df_from<Df>(h0);
+    sh.h[2 * MU][1][a][x] = df_from<Df>(h1);
+    project_colour_df<MU, BS>(in, nbk, a, h0, h1);
+    sh.h[2 * MU + 1][0][a][x] = df_from<Df>(h0);
+    sh.h[2 * MU + 1][1][a][x] = df_from<Df>(h1);
+}
+
+__device__ __forceinline__ Cx<Df> df_cx(float4 v) { return Cx<Df>{Df(v.x, v.y), Df(v.z, v.w)}; }
+
+template <int MU, int FS, int BS>
+__device__ __forceinline__ void hop_dir_df(DfAcc (&ar)[4], DfAcc (&ai)[4], const DfHalves &sh,
+                                           const GaugeRef<PREC_DF> &U, const Geo &g, int cb, int out_par, int x,
+                                           int a, int nbk, bool wrap_f, bool wrap_b)
 {
     const bool antip = (MU == 3) && g.t_bc < 0;
     { // forward: row a of U_mu(x)
-        Hs<Df> h = project<MU, FS>(in.template load<Df>(nf));
         DfAcc r0, i0, r1, i1;
 #pragma unroll
         for (int b = 0; b < 3; b++) {
             float4 w = ldg(U.d + U.idx(MU, out_par, a * 3 + b, cb));
             Df ur(w.x, w.y), ui(w.z, w.w);
-            r0.add_prod(ur, h.c[0][b].re);
-            r0.sub_prod(ui, h.c[0][b].im);
-            i0.add_prod(ur, h.c[0][b].im);
-            i0.add_prod(ui, h.c[0][b].re);
-            r1.add_prod(ur, h.c[1][b].re);
-            r1.sub_prod(ui, h.c[1][b].im);
-            i1.add_prod(ur, h.c[1][b].im);
-            i1.add_prod(ui, h.c[1][b].re);
+            const Cx<Df> h0 = df_cx(sh.h[2 * MU][0][b][x]), h1 = df_cx(sh.h[2 * MU][1][b][x]);
+            r0.add_prod(ur, h0.re);
+            r0.sub_prod(ui, h0.im);
+            i0.add_prod(ur, h0.im);
+            i0.add_prod(ui, h0.re);
+            r1.add_prod(ur, h1.re);
+            r1.sub_prod(ui, h1.im);
+            i1.add_prod(ur, h1.im);
+            i1.add_prod(ui, h1.re);
         }
         Cx<Df> v0{r0.value(), i0.value()}, v1{r1.value(), i1.value()};
         if (antip && wrap_f) {
@@ -178,20 +226,20 @@ __device__ __forceinline__ void hop_dir_df(DfAcc (&ar)[4], DfAcc (&ai)[4], const
         acc_hop<MU, FS>(ar, ai, v0, v1);
     }
     { // backward: column a of U_mu(x - mu), conjugated
-        Hs<Df> h = project<MU, BS>(in.template load<Df>(nbk));
         DfAcc r0, i0, r1, i1;
 #pragma unroll
         for (int b = 0; b < 3; b++) {
             float4 w = ldg(U.d + U.idx(MU, 1 - out_par, b * 3 + a, nbk));
             Df ur(w.x, w.y), ui(w.z, w.w);
-            r0.add_prod(ur, h.c[0][b].re);
-            r0.add_prod(ui, h.c[0][b].im);
-            i0.add_prod(ur, h.c[0][b].im);
-            i0.sub_prod(ui, h.c[0][b].re);
-            r1.add_prod(ur, h.c[1][b].re);
-            r1.add_prod(ui, h.c[1][b].im);
-            i1.add_prod(ur, h.c[1][b].im);
-            i1.sub_prod(ui, h.c[1][b].re);
+            const Cx<Df> h0 = df_cx(sh.h[2 * MU + 1][0][b][x]), h1 = df_cx(sh.h[2 * MU + 1][1][b][x]);
+            r0.add_prod(ur, h0.re);
+            r0.add_prod(ui, h0.im);
+            i0.add_prod(ur, h0.im);
+            i0.sub_prod(ui, h0.re);
+            r1.add_prod(ur, h1.re);
+            r1.add_prod(ui, h1.im);
+            i1.add_prod(ur, h1.im);
+            i1.sub_prod(ui, h1.re);
         }
         Cx<Df> v0{r0.value(), i0.value()}, v1{r1.value(), i1.value()};
         if (antip && wrap_b) {
@@ -202,26 +250,36 @@ __device__ __forceinline__ void hop_dir_df(DfAcc (&ar)[4], DfAcc (&ai)[4], const
     }
 }
 
+// 4 blocks of 192 threads per SM (80 registers, 4 x 48 KiB of half spinors)
 template <bool DAG, bool XPAY>
-__global__ void __launch_bounds__(DF_SITES * 3) dslash_df_kernel(SpinorRef<PREC_DF> out, SpinorRef<PREC_DF> in,
+__global__ void __launch_bounds__(DF_SITES * 3, 4) dslash_df_kernel(SpinorRef<PREC_DF> out, SpinorRef<PREC_DF> in,
                                                                  GaugeRef<PREC_DF> U, Geo g, int out_par,
                                                                  SpinorRef<PREC_DF> x, Df b, const int *skip)
 {
-    if (skip && *skip) return;
-    const int a = threadIdx.y;
-    const int cb = blockIdx.x * DF_SITES + threadIdx.x;
-    if (cb >= g.Vh) return;
+    __shared__ DfHalves sh;
+    if (skip && *skip) return; // the same for the whole block
+    const int tx = threadIdx.x, a = threadIdx.y;
+    const int cb = blockIdx.x * DF_SITES + tx;
+    const bool live = cb < g.Vh;
     int c[4], nb[8];
-    bool tf, tb;
-    cb_coords(g, cb, out_par, c);
-    cb_neighbours(g, cb, c, nb, tf, tb);
-    DfAcc ar[4], ai[4];
+    bool tf = false, tb = false;
     constexpr int FS = DAG ? +1 : -1;
     constexpr int BS = -FS;
-    hop_dir_df<0, FS, BS>(ar, ai, in, U, g, cb, out_par, a, nb[0], nb[1], false, false);
-    hop_dir_df<1, FS, BS>(ar, ai, in, U, g, cb, out_par, a, nb[2], nb[3], false, false);
-    hop_dir_df<2, FS, BS>(ar, ai, in, U, g, cb, out_par, a, nb[4], nb[5], false, false);
-    hop_dir_df<3, FS, BS>(ar, ai, in, U, g, cb, out_par, a, nb[6], nb[7], tf, tb);
+    if (live) {
+        cb_coords(g, cb, out_par, c);
+        cb_neighbours(g, cb, c, nb, tf, tb);
+        project_dir_df<0, FS, BS>(sh, in, tx, a, nb[0], nb[1]);
+        project_dir_df<1, FS, BS>(sh, in, tx, a, nb[2], nb[3]);
+        project_dir_df<2, FS, BS>(sh, in, tx, a, nb[4], nb[5]);
+        project_dir_df<3, FS, BS>(sh, in, tx, a, nb[6], nb[7]);
+    }
+    __syncthreads();
+    if (!live) return;
+    DfAcc ar[4], ai[4];
+    hop_dir_df<0, FS, BS>(ar, ai, sh, U, g, cb, out_par, tx, a, nb[1], false, false);
+    hop_dir_df<1, FS, BS>(ar, ai, sh, U, g, cb, out_par, tx, a, nb[3], false, false);
+    hop_dir_df<2, FS, BS>(ar, ai, sh, U, g, cb, out_par, tx, a, nb[5], false, false);
+    hop_dir_df<3, FS, BS>(ar, ai, sh, U, g, cb, out_par, tx, a, nb[7], tf, tb);
 #pragma unroll
     for (int sp = 0; sp < 4; sp++) {
         Cx<Df> v{ar[sp].value(), ai[sp].value()};

@@ -23,34 +23,83 @@
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <set>
 #include <string>
 #include <thread>
 #include <unordered_map>
 
 #include "batch.cuh"
+#include "df64.cuh"
+#include "dslash_site.cuh"
 
 namespace lqcd {
 
 using Clock = std::chrono::steady_clock;
 
-// unit point source: component comp (spin*3 + colour) at checkerboard site cb
-__global__ void point_source_kernel(double2 *f, int Vh, int cb, int comp)
+// one element of a point source: component comp (spin*3 + colour) at
+// checkerboard site cb set to v, in FP64 or float-float storage
+__global__ void point_set_kernel(double2 *f, int Vh, int cb, int comp, double v)
 {
-    f[(size_t)comp * Vh + cb] = make_double2(1.0, 0.0);
+    f[(size_t)comp * Vh + cb] = make_double2(v, 0.0);
+}
+__global__ void point_set_df_kernel(float4 *f, int Vh, int cb, int comp, float v)
+{
+    f[(size_t)comp * Vh + cb] = make_float4(v, 0.f, 0.f, 0.f);
 }
 
-// |a - b|^2 block partials (FP64)
-__global__ void __launch_bounds__(256) diff_norm_kernel(SpinorRef<LQCD_F64> a, SpinorRef<LQCD_F64> b, double *partials,
-                                                        int Vh)
+// out = x + b D in at the listed output sites only (FP64; x may be absent).
+// A point source and the operators applied to it are non-zero on a few dozen
+// sites, so the set-up of a right-hand side touches only those.
+template <bool DAG>
+__global__ void hop_sites_kernel(SpinorRef<LQCD_F64> out, SpinorRef<LQCD_F64> in, GaugeRef<LQCD_F64> U, Geo g,
+                                 int out_par, SpinorRef<LQCD_F64> x, double b, const int *sites, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int cb = sites[i];
+    Sp<double> d = dslash_site<double, LQCD_F64, LQCD_F64, DAG>(in, U, g, cb, out_par);
+    if (x.d) {
+        Sp<double> xv = x.load_rw<double>(cb);
+#pragma unroll
+        for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) d.c[s][c] = xv.c[s][c] + b * d.c[s][c];
+    } else {
+#pragma unroll
+        for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) d.c[s][c] = b * d.c[s][c];
+    }
+    out.store(cb, d);
+}
+
+__global__ void zero_sites_kernel(SpinorRef<LQCD_F64> f, const int *sites, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Sp<double> z;
+#pragma unroll
+    for (int s = 0; s < 4; s++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) z.c[s][c] = Cx<double>{0.0, 0.0};
+    f.store(sites[i], z);
+}
+
+// block partials of |y - b_e|^2 for a float-float field y and the even part
+// b_e of a unit point source (component comp at site src_cb; src_cb < 0: none)
+__global__ void __launch_bounds__(256) point_residual_kernel(SpinorRef<PREC_DF> y, int src_cb, int comp,
+                                                             double *partials, int Vh)
 {
     int cb = blockIdx.x * 256 + threadIdx.x;
     double n2[1] = {0.0};
     if (cb < Vh) {
-        Sp<double> av = a.load_rw<double>(cb), bv = b.load_rw<double>(cb);
 #pragma unroll
-        for (int s = 0; s < 4; s++)
-#pragma unroll
-            for (int c = 0; c < 3; c++) n2[0] += norm2(av.c[s][c] - bv.c[s][c]);
+        for (int k = 0; k < 12; k++) {
+            float4 v = y.d[(size_t)k * Vh + cb];
+            double re = (double)v.x + (double)v.y, im = (double)v.z + (double)v.w;
+            if (cb == src_cb && k == comp) re -= 1.0;
+            n2[0] += re * re + im * im;
+        }
     }
     block_sum_store<1, 256>(n2, partials, (int)gridDim.x);
 }
@@ -59,7 +108,9 @@ struct SvcGauge {
     lqcd_field *U = nullptr; // borrowed FP64 links
     FieldPtr Us, Udf;         // sloppy copy and float-float copy shared by every solve on it
     CgWorkspace shared;       // transient float-float fields shared by its solves
-    FieldPtr be, bo, bp, src, tmpo, mxe; // set-up and check temporaries (used one solve at a time)
+    // set-up (FP64, zero outside the few sites a set-up writes, cleared after
+    // each use) and check (float-float) temporaries, used one solve at a time
+    FieldPtr bo, bp, to, src, bo_df, xo_df, mxe_df;
     DevBuf part, scal;
     bool ready = false;
 };
@@ -80,6 +131,10 @@ struct SvcRhs {
 struct SvcRequest {
     uint64_t ticket = 0;
     lqcd_solve_req req{};
+    // the source's parity and checkerboard index, and the checkerboard sites
+    // of b'_e (S1), of D_oe^dag b'_e (T, odd) and of Mhat^dag b'_e (S2)
+    int par = 0, cb = 0, n1 = 0, nt = 0, n2 = 0;
+    DevBuf sites; // S1, T, S2 in a row
     Clock::time_point t_submit, t_admit, t_done;
     std::vector<std::unique_ptr<SvcRhs>> rhs;
     size_t bytes = 0;
@@ -133,49 +188,107 @@ static lqcd_status gauge_setup(lqcd_service *S, SvcGauge &g)
     LQCD_TRY(split_links(g.Udf.f, g.U, s));
     g.shared.temps_only = true;
     LQCD_TRY(g.shared.ensure(lat, S->prm.cg.sloppy, s));
-    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &g.be.f));
     LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F64, 0, &g.bo.f));
     LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &g.bp.f));
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F64, 0, &g.to.f));
     LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &g.src.f));
-    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F64, 0, &g.tmpo.f));
-    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &g.mxe.f));
+    LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_ODD, &g.bo_df.f));
+    LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_ODD, &g.xo_df.f));
+    LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &g.mxe_df.f));
+    for (lqcd_field *f : {g.bo.f, g.bp.f, g.to.f, g.src.f, g.bo_df.f})
+        LQCD_CUDA(cudaMemsetAsync(f->data, 0, f->bytes, s));
     LQCD_TRY(g.part.alloc(sizeof(double) * (nblocks_for(make_geo(lat).Vh, 256) + 1), s));
     LQCD_TRY(g.scal.alloc(sizeof(double) * 4, s));
     g.ready = true;
     return LQCD_OK;
 }
 
-// b_e, b_o of the point source of component comp at the request's site
-static lqcd_status make_source(SvcGauge &g, const lqcd_solve_req &q, int comp, cudaStream_t s)
+// the site lists of a request's source (host; periodic neighbours)
+static lqcd_status source_sites(SvcRequest &r, const lqcd_lattice &lat, cudaStream_t s)
 {
-    const lqcd_lattice &lat = g.U->lat;
-    const int *c = q.site;
-    int lex = c[0] + lat.dims[0] * (c[1] + lat.dims[1] * (c[2] + lat.dims[2] * c[3]));
-    int par = (c[0] + c[1] + c[2] + c[3]) & 1;
-    LQCD_CUDA(cudaMemsetAsync(g.be.f->data, 0, g.be.f->bytes, s));
-    LQCD_CUDA(cudaMemsetAsync(g.bo.f->data, 0, g.bo.f->bytes, s));
-    point_source_kernel<<<1, 1, 0, s>>>((double2 *)(par ? g.bo.f : g.be.f)->data, g.be.f->Vh, lex >> 1, comp);
+    const int *L = lat.dims;
+    auto lex = [&](const int *c) { return c[0] + L[0] * (c[1] + L[1] * (c[2] + L[2] * c[3])); };
+    auto neighbours = [&](int i, std::set<int> &out) {
+        int c[4] = {i % L[0], (i / L[0]) % L[1], (i / (L[0] * L[1])) % L[2], i / (L[0] * L[1] * L[2])};
+        for (int mu = 0; mu < 4; mu++)
+            for (int d : {1, L[mu] - 1}) {
+                int n[4] = {c[0], c[1], c[2], c[3]};
+                n[mu] = (n[mu] + d) % L[mu];
+                out.insert(lex(n));
+            }
+    };
+    int src = lex(r.req.site);
+    r.par = (r.req.site[0] + r.req.site[1] + r.req.site[2] + r.req.site[3]) & 1;
+    r.cb = src >> 1;
+    std::set<int> s1, t, s2;
+    if (r.par == 0)
+        s1.insert(src);
+    else
+        neighbours(src, s1);
+    for (int i : s1) neighbours(i, t);
+    s2 = s1;
+    for (int i : t) neighbours(i, s2);
+    std::vector<int> all;
+    for (const std::set<int> *set : {&s1, &t, &s2})
+        for (int i : *set) all.push_back(i >> 1);
+    r.n1 = (int)s1.size(), r.nt = (int)t.size(), r.n2 = (int)s2.size();
+    LQCD_TRY(r.sites.alloc(all.size() * sizeof(int), s));
+    // pageable source: the copy has taken the host data when the call returns
+    LQCD_CUDA(cudaMemcpyAsync(r.sites.p, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    return LQCD_OK;
+}
+
+template <bool DAG>
+static lqcd_status hop_sites(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, const lqcd_field *x,
+                             double b, const int *sites, int n, cudaStream_t s)
+{
+    SpinorRef<LQCD_F64> xr = x ? spinor_ref<LQCD_F64>(x) : SpinorRef<LQCD_F64>{nullptr, in->Vh};
+    hop_sites_kernel<DAG><<<nblocks_for(n, 64), 64, 0, s>>>(spinor_ref<LQCD_F64>(out), spinor_ref<LQCD_F64>(in),
+                                                            gauge_ref<LQCD_F64>(U), make_geo(U->lat),
+                                                            out->kind == LQCD_SPINOR_EVEN ? 0 : 1, xr, b, sites, n);
     LQCD_LAUNCHED();
     return LQCD_OK;
 }
 
-// start (or restart from its solution) one right-hand side's normal-equation solve
+static lqcd_status zero_sites(lqcd_field *f, const int *sites, int n, cudaStream_t s)
+{
+    zero_sites_kernel<<<nblocks_for(n, 64), 64, 0, s>>>(spinor_ref<LQCD_F64>(f), sites, n);
+    LQCD_LAUNCHED();
+    return LQCD_OK;
+}
+
+// start (or restart from its solution) one right-hand side's normal-equation
+// solve: b'_e = b_e + kappa D_eo b_o and src = Mhat^dag b'_e on their few
+// non-zero sites, then the solver's start, then the temporaries cleared
 static lqcd_status rhs_start(lqcd_service *S, SvcGauge &g, SvcRequest &r, SvcRhs &h, bool warm)
 {
     cudaStream_t s = S->stream;
-    LQCD_TRY(make_source(g, r.req, h.comp, s));
-    // b'_e = b_e + kappa D_eo b_o;  src = Mhat^dag b'_e
-    LQCD_TRY(dslash_xpay(g.bp.f, g.U, g.bo.f, 0, g.be.f, r.req.kappa, nullptr, nullptr, s));
-    LQCD_TRY(mhat_apply(g.src.f, g.U, g.bp.f, r.req.kappa, 1, g.tmpo.f, nullptr, s));
+    const double kappa = r.req.kappa;
+    const int *s1 = (const int *)r.sites.p, *t = s1 + r.n1, *s2 = t + r.nt;
+    const int Vh = g.bp.f->Vh;
+    if (r.par == 0) {
+        point_set_kernel<<<1, 1, 0, s>>>((double2 *)g.bp.f->data, Vh, r.cb, h.comp, 1.0);
+    } else {
+        point_set_kernel<<<1, 1, 0, s>>>((double2 *)g.bo.f->data, Vh, r.cb, h.comp, 1.0);
+        LQCD_LAUNCHED();
+        LQCD_TRY(hop_sites<false>(g.bp.f, g.U, g.bo.f, nullptr, kappa, s1, r.n1, s));
+        point_set_kernel<<<1, 1, 0, s>>>((double2 *)g.bo.f->data, Vh, r.cb, h.comp, 0.0);
+    }
+    LQCD_LAUNCHED();
+    LQCD_TRY(hop_sites<true>(g.to.f, g.U, g.bp.f, nullptr, 1.0, t, r.nt, s));
+    LQCD_TRY(hop_sites<true>(g.src.f, g.U, g.to.f, g.bp.f, -kappa * kappa, s2, r.n2, s));
     h.run = CgRun();
     h.run.ws = h.ws.get(), h.run.x = h.y.f, h.run.U = g.U, h.run.Us = g.Us.f, h.run.b = g.src.f;
-    h.run.kappa = r.req.kappa;
+    h.run.kappa = kappa;
     h.run.prm = S->prm.cg;
     h.run.prm.tol = h.tol_n;
     h.run.prm.guess = warm ? 1 : 0;
-    // start() has read src (into the solve's own float-float source) before it
-    // returns; a failure leaves the run done with its status
+    // start() copies src into the solve's own float-float source before any
+    // later work on this stream; a failure leaves the run done with its status
     h.run.start(s, (CgScalars *)h.ws->sc.p);
+    LQCD_TRY(zero_sites(g.bp.f, s1, r.n1, s));
+    LQCD_TRY(zero_sites(g.to.f, t, r.nt, s));
+    LQCD_TRY(zero_sites(g.src.f, s2, r.n2, s));
     if (!h.run.done) S->bs.add(&h.run);
     return LQCD_OK;
 }
@@ -185,10 +298,11 @@ static lqcd_status admit(lqcd_service *S, SvcRequest &r)
     SvcGauge &g = *S->gauges[r.req.gauge];
     LQCD_TRY(gauge_setup(S, g));
     const lqcd_lattice &lat = g.U->lat;
+    LQCD_TRY(source_sites(r, lat, S->stream));
     for (int k = 0; k < r.req.nrhs; k++) {
         std::unique_ptr<SvcRhs> h(new SvcRhs());
         h->comp = k;
-        h->tol_n = S->prm.cg.tol / 30.0;
+        h->tol_n = S->prm.cg.tol / 10.0;
         h->ws->udf_ext = g.Udf.f;
         h->ws->tmp_from = &g.shared;
         LQCD_TRY(h->ws->ensure(lat, S->prm.cg.sloppy, S->stream));
@@ -200,21 +314,11 @@ static lqcd_status admit(lqcd_service *S, SvcRequest &r)
     return LQCD_OK;
 }
 
-// |a - b|^2 of two FP64 fields of one parity, added to *acc
-static lqcd_status add_diff_norm(SvcGauge &g, const lqcd_field *a, const lqcd_field *b, double *acc, cudaStream_t s)
-{
-    int Vh = a->Vh, nb = nblocks_for(Vh, 256);
-    diff_norm_kernel<<<nb, 256, 0, s>>>(spinor_ref<LQCD_F64>(a), spinor_ref<LQCD_F64>(b), (double *)g.part.p, Vh);
-    LQCD_LAUNCHED();
-    LQCD_TRY(reduce_partials((double *)g.part.p, nb, 1, (double *)g.scal.p, s));
-    double v = 0;
-    LQCD_TRY(read_scalars((double *)g.scal.p, &v, 1, s));
-    *acc += v;
-    return LQCD_OK;
-}
-
-// x_o = b_o + kappa D_oe y and the full residual |b - M x| / |b| (|b| = 1);
-// a miss continues from x_e with a tighter normal-equation tolerance
+// x_o = b_o + kappa D_oe x_e and the full residual |b - M x| / |b| (|b| = 1),
+// both from the solver's float-float solution with float-float links and
+// arithmetic; a miss continues from x_e with a tighter normal-equation
+// tolerance.  The odd rows of b - M x are b_o - x_o + kappa D_oe x_e, zero by
+// the definition of x_o up to its rounding, so the even rows are the residual.
 static lqcd_status rhs_check(lqcd_service *S, SvcGauge &g, SvcRequest &r, SvcRhs &h, bool *restarted)
 {
     cudaStream_t s = S->stream;
@@ -226,14 +330,26 @@ static lqcd_status rhs_check(lqcd_service *S, SvcGauge &g, SvcRequest &r, SvcRhs
         h.finalized = true;
         return LQCD_OK;
     }
-    LQCD_TRY(make_source(g, r.req, h.comp, s));
-    LQCD_TRY(dslash_xpay(h.xo.f, g.U, h.y.f, 0, g.bo.f, kappa, nullptr, nullptr, s));
-    // (M x)_e = x_e - kappa D_eo x_o,  (M x)_o = x_o - kappa D_oe x_e
-    LQCD_TRY(dslash_xpay(g.mxe.f, g.U, h.xo.f, 0, h.y.f, -kappa, nullptr, nullptr, s));
-    LQCD_TRY(dslash_xpay(g.tmpo.f, g.U, h.y.f, 0, h.xo.f, -kappa, nullptr, nullptr, s));
+    const lqcd_field *xdf = h.ws->xdf.f;
+    const int Vh = xdf->Vh;
+    if (r.par == 1) {
+        point_set_df_kernel<<<1, 1, 0, s>>>((float4 *)g.bo_df.f->data, Vh, r.cb, h.comp, 1.f);
+        LQCD_LAUNCHED();
+    }
+    LQCD_TRY(dslash_xpay(g.xo_df.f, g.Udf.f, xdf, 0, g.bo_df.f, kappa, nullptr, nullptr, s));
+    LQCD_TRY(dslash_xpay(g.mxe_df.f, g.Udf.f, g.xo_df.f, 0, xdf, -kappa, nullptr, nullptr, s));
+    if (r.par == 1) {
+        point_set_df_kernel<<<1, 1, 0, s>>>((float4 *)g.bo_df.f->data, Vh, r.cb, h.comp, 0.f);
+        LQCD_LAUNCHED();
+    }
+    int nb = nblocks_for(Vh, 256);
+    point_residual_kernel<<<nb, 256, 0, s>>>(spinor_ref<PREC_DF>(g.mxe_df.f), r.par == 0 ? r.cb : -1, h.comp,
+                                             (double *)g.part.p, Vh);
+    LQCD_LAUNCHED();
+    LQCD_TRY(reduce_partials((double *)g.part.p, nb, 1, (double *)g.scal.p, s));
+    LQCD_TRY(df_to_f64(h.xo.f, g.xo_df.f, s));
     double rr = 0;
-    LQCD_TRY(add_diff_norm(g, g.be.f, g.mxe.f, &rr, s));
-    LQCD_TRY(add_diff_norm(g, g.bo.f, g.tmpo.f, &rr, s));
+    LQCD_TRY(read_scalars((double *)g.scal.p, &rr, 1, s));
     h.rel_res = std::sqrt(rr);
     if (!std::isfinite(h.rel_res)) {
         h.status = LQCD_ENUMERIC;
