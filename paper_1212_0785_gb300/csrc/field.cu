@@ -631,10 +631,11 @@ __device__ __forceinline__ M3<Df> reunit_rows_df(const M3<float> &e)
 // in float-float arithmetic (~48 bits, on the FP32 pipes), so that the FP64
 // links stay in SU(3) to ~1e-14 per update; otherwise everything in FP64.  The
 // new links are also written to the 12-real copies Us (solver precision) and
-// Uf (FP32) when those are given.
+// Uf (FP32) and to the float-float copy Udf (the solver's accurate residual)
+// when those are given.
 template <lqcd_prec PS, bool FAST>
 __global__ void link_update_kernel(GaugeRef<LQCD_F64> U, MomRef P, double c, GaugeRef<PS> Us, GaugeRef<LQCD_F32> Uf,
-                                   int Vh, int write_sloppy, int write_f32)
+                                   GaugeRef<PREC_DF> Udf, int Vh, int write_sloppy, int write_f32)
 {
     long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (t >= 8L * Vh) return;
@@ -664,13 +665,16 @@ __global__ void link_update_kernel(GaugeRef<LQCD_F64> U, MomRef P, double c, Gau
                     im.add_prod(E.e[i][k].re, u.e[k][j].im);
                     im.add_prod(E.e[i][k].im, u.e[k][j].re);
                 }
-                nu.e[i][j] = cx<double>((double)re.value(), (double)im.value());
+                const Df vr = re.value(), vi = im.value();
+                nu.e[i][j] = cx<double>((double)vr, (double)vi);
+                if (Udf.d) Udf.d[Udf.idx(mu, par, i * 3 + j, cb)] = make_float4(vr.hi, vr.lo, vi.hi, vi.lo);
             }
     } else {
         double p[8];
         for (int a = 0; a < 8; a++) p[a] = P.d[P.idx(mu, par, a, cb)];
         M3<double> E = expi_cayley_hamilton(herm_from_coeffs(p, c));
         nu = m3_mul(E, U.load<double>(mu, par, cb));
+        if (Udf.d) Udf.store(mu, par, cb, nu);
     }
     U.store(mu, par, cb, nu);
     if (write_sloppy || write_f32) {
@@ -845,8 +849,9 @@ lqcd_status reunitarize_dev(lqcd_field *U, double *dst_dev, DevBuf &part, cudaSt
 
 template <bool FAST>
 static lqcd_status launch_link_update(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *Us, lqcd_field *Uf,
-                                      cudaStream_t s)
+                                      lqcd_field *Udf, cudaStream_t s)
 {
+    GaugeRef<PREC_DF> ud = Udf ? gauge_ref<PREC_DF>(Udf) : GaugeRef<PREC_DF>{nullptr, U->Vh};
     long n = 8L * U->Vh;
     int nb = nblocks_for(n, 128);
     GaugeRef<LQCD_F32> uf = Uf ? gauge_ref<LQCD_F32>(Uf) : GaugeRef<LQCD_F32>{nullptr, U->Vh};
@@ -854,15 +859,15 @@ static lqcd_status launch_link_update(lqcd_field *U, const lqcd_field *P, double
     switch (Us ? Us->prec : LQCD_F32) {
     case LQCD_F32:
         link_update_kernel<LQCD_F32, FAST><<<nb, 128, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c,
-                                                              Us ? gauge_ref<LQCD_F32>(Us) : uf, uf, U->Vh, Us ? 1 : 0, wf);
+                                                              Us ? gauge_ref<LQCD_F32>(Us) : uf, uf, ud, U->Vh, Us ? 1 : 0, wf);
         break;
     case LQCD_F16N:
         link_update_kernel<LQCD_F16N, FAST><<<nb, 128, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c,
-                                                               gauge_ref<LQCD_F16N>(Us), uf, U->Vh, 1, wf);
+                                                               gauge_ref<LQCD_F16N>(Us), uf, ud, U->Vh, 1, wf);
         break;
     case LQCD_BF16:
         link_update_kernel<LQCD_BF16, FAST><<<nb, 128, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c,
-                                                               gauge_ref<LQCD_BF16>(Us), uf, U->Vh, 1, wf);
+                                                               gauge_ref<LQCD_BF16>(Us), uf, ud, U->Vh, 1, wf);
         break;
     default: set_error("sloppy link copy must be 12-real F32/F16N/BF16"); return LQCD_EINVAL;
     }
@@ -871,10 +876,10 @@ static lqcd_status launch_link_update(lqcd_field *U, const lqcd_field *P, double
 }
 
 lqcd_status link_update_dev(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *Us, lqcd_field *Uf, bool fast,
-                            cudaStream_t s)
+                            cudaStream_t s, lqcd_field *Udf)
 {
     KernelTimer kt(K_LINK_UPDATE, s);
-    return fast ? launch_link_update<true>(U, P, c, Us, Uf, s) : launch_link_update<false>(U, P, c, Us, Uf, s);
+    return fast ? launch_link_update<true>(U, P, c, Us, Uf, Udf, s) : launch_link_update<false>(U, P, c, Us, Uf, Udf, s);
 }
 
 lqcd_status momentum_refresh_dev(lqcd_field *P, uint32_t seed, uint32_t chain, uint32_t traj, cudaStream_t s)
@@ -1110,7 +1115,7 @@ lqcd_status lqcd_link_update(lqcd_field *U, const lqcd_field *P, double c, lqcd_
     if (U_sloppy)
         LQCD_REQUIRE(U_sloppy->kind == LQCD_GAUGE && U_sloppy->recon == 12 && same_lattice(U->lat, U_sloppy->lat),
                      "link_update: U_sloppy must be a 12-real gauge field on the same lattice");
-    return link_update_dev(U, P, c, U_sloppy, nullptr, false, (cudaStream_t)stream);
+    return link_update_dev(U, P, c, U_sloppy, nullptr, false, (cudaStream_t)stream, nullptr);
 }
 
 lqcd_status lqcd_reunitarize(lqcd_field *U, double *max_dev_out, void *stream)

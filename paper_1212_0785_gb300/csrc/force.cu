@@ -45,7 +45,58 @@ __device__ __forceinline__ void m3_acc(M3<R> &a, const M3<R> &b)
         for (int j = 0; j < 3; j++) a.e[i][j] = a.e[i][j] + b.e[i][j];
 }
 
-// staple sum A_mu(x): U_mu(x) A_mu(x) = sum of the 6 plaquettes starting with the link
+// coordinates c shifted by s (+1 or -1) in direction D, periodic
+template <int D>
+__device__ __forceinline__ void shift(const Geo &g, const int c[4], int s, int o[4])
+{
+#pragma unroll
+    for (int k = 0; k < 4; k++) o[k] = c[k];
+    int v = c[D] + s;
+    o[D] = v == g.L[D] ? 0 : (v < 0 ? g.L[D] - 1 : v);
+}
+
+// staple sum A_mu(x): U_mu(x) A_mu(x) = sum of the 6 plaquettes starting with
+// the link.  MU is a compile-time constant so every coordinate array is
+// indexed by constants (no local memory).
+template <int MU, typename R, lqcd_prec GP>
+__device__ __forceinline__ void gauge_force_link(MomRef &P, const GaugeRef<GP> &U, const Geo &g, int par, int cb,
+                                                 const int c[4], double cf)
+{
+    int cpm[4];
+    shift<MU>(g, c, +1, cpm);
+    const int cb_pm = coords_cb(g, cpm);
+    M3<R> A;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) A.e[i][j] = cx<R>(0, 0);
+#pragma unroll
+    for (int k = 1; k < 4; k++) {
+        const int nu = (MU + k) & 3;
+        int cpn[4], cmn[4], cpmmn[4];
+        switch (nu) { // nu is a constant after unrolling
+        case 0: shift<0>(g, c, +1, cpn), shift<0>(g, c, -1, cmn), shift<0>(g, cpm, -1, cpmmn); break;
+        case 1: shift<1>(g, c, +1, cpn), shift<1>(g, c, -1, cmn), shift<1>(g, cpm, -1, cpmmn); break;
+        case 2: shift<2>(g, c, +1, cpn), shift<2>(g, c, -1, cmn), shift<2>(g, cpm, -1, cpmmn); break;
+        default: shift<3>(g, c, +1, cpn), shift<3>(g, c, -1, cmn), shift<3>(g, cpm, -1, cpmmn); break;
+        }
+        const int cb_pn = coords_cb(g, cpn), cb_mn = coords_cb(g, cmn), cb_pmmn = coords_cb(g, cpmmn);
+        // upper: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+        M3<R> up = m3_mul_dag(U.template load<R>(nu, 1 - par, cb_pm), U.template load<R>(MU, 1 - par, cb_pn));
+        up = m3_mul_dag(up, U.template load<R>(nu, par, cb));
+        m3_acc(A, up);
+        // lower: U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu) = (U_mu(x-nu) U_nu(x+mu-nu))^dag U_nu(x-nu)
+        M3<R> lo = m3_mul(U.template load<R>(MU, 1 - par, cb_mn), U.template load<R>(nu, par, cb_pmmn));
+        lo = m3_dag_mul(lo, U.template load<R>(nu, 1 - par, cb_mn));
+        m3_acc(A, lo);
+    }
+    M3<R> W = m3_mul(U.template load<R>(MU, par, cb), A);
+    R gl[8];
+    im_tr_lambda(W, gl);
+#pragma unroll
+    for (int a = 0; a < 8; a++) P.d[P.idx(MU, par, a, cb)] -= cf * (double)gl[a];
+}
+
 template <typename R, lqcd_prec GP>
 __global__ void __launch_bounds__(FB) gauge_force_kernel(MomRef P, GaugeRef<GP> U, Geo g, double cf)
 {
@@ -55,33 +106,12 @@ __global__ void __launch_bounds__(FB) gauge_force_kernel(MomRef P, GaugeRef<GP> 
     link_of_thread(t, g.Vh, mu, par, cb);
     int c[4];
     cb_coords(g, cb, par, c);
-    int cpm[4] = {c[0], c[1], c[2], c[3]};
-    cpm[mu] = (c[mu] + 1 == g.L[mu]) ? 0 : c[mu] + 1;
-    int cb_pm = coords_cb(g, cpm);
-    M3<R> A;
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) A.e[i][j] = cx<R>(0, 0);
-    for (int nu = 0; nu < 4; nu++) {
-        if (nu == mu) continue;
-        int cb_pn = step_cb(g, c, nu, +1);
-        int cb_mn = step_cb(g, c, nu, -1);
-        int cb_pmmn = step_cb(g, cpm, nu, -1);
-        // upper: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
-        M3<R> up = m3_mul_dag(U.template load<R>(nu, 1 - par, cb_pm), U.template load<R>(mu, 1 - par, cb_pn));
-        up = m3_mul_dag(up, U.template load<R>(nu, par, cb));
-        m3_acc(A, up);
-        // lower: U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu) = (U_mu(x-nu) U_nu(x+mu-nu))^dag U_nu(x-nu)
-        M3<R> lo = m3_mul(U.template load<R>(mu, 1 - par, cb_mn), U.template load<R>(nu, par, cb_pmmn));
-        lo = m3_dag_mul(lo, U.template load<R>(nu, 1 - par, cb_mn));
-        m3_acc(A, lo);
+    switch (mu) {
+    case 0: gauge_force_link<0, R, GP>(P, U, g, par, cb, c, cf); break;
+    case 1: gauge_force_link<1, R, GP>(P, U, g, par, cb, c, cf); break;
+    case 2: gauge_force_link<2, R, GP>(P, U, g, par, cb, c, cf); break;
+    default: gauge_force_link<3, R, GP>(P, U, g, par, cb, c, cf); break;
     }
-    M3<R> W = m3_mul(U.template load<R>(mu, par, cb), A);
-    R gl[8];
-    im_tr_lambda(W, gl);
-#pragma unroll
-    for (int a = 0; a < 8; a++) P.d[P.idx(mu, par, a, cb)] -= cf * (double)gl[a];
 }
 
 // Fermion force on link (x, mu), x of parity par:

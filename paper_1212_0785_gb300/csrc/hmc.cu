@@ -19,7 +19,7 @@ lqcd_status plaquette_sum(const lqcd_field *U, double *dst_dev, DevBuf &part, cu
 lqcd_status kinetic_sum(const lqcd_field *P, double *dst_dev, DevBuf &part, cudaStream_t s);
 lqcd_status reunitarize_dev(lqcd_field *U, double *dst_dev, DevBuf &part, cudaStream_t s);
 lqcd_status link_update_dev(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *Us, lqcd_field *Uf, bool fast,
-                            cudaStream_t s);
+                            cudaStream_t s, lqcd_field *Udf);
 lqcd_status momentum_refresh_dev(lqcd_field *P, uint32_t seed, uint32_t chain, uint32_t traj, cudaStream_t s);
 lqcd_status eta_refresh_dev(lqcd_field *E, uint32_t seed, uint32_t chain, uint32_t traj, cudaStream_t s);
 lqcd_status gauge_force_dev(lqcd_field *P, const lqcd_field *U, const lqcd_field *Uf, double beta, double coeff,
@@ -72,6 +72,7 @@ struct lqcd_hmc_state {
     FieldPtr P, eta, phi, X, Ao, Ye, Bo, Ubak, Us;
     FieldPtr Ao32, Ye32, Bo32, X32; // FP32 fermion-force temporaries (allocated on first use)
     FieldPtr Uf;                    // FP32 12-real link copy for the FP32 molecular dynamics
+    FieldPtr Udf; // float-float link copy of the mixed solver, kept current by every link update
     CgWorkspace ws;
     DevBuf part, scal;
     double H0 = 0;
@@ -80,6 +81,8 @@ struct lqcd_hmc_state {
     // (sum of the drifts since the refresh) of their links, for the
     // extrapolated initial guess; hist[(head - 1) mod CHRONO_MAX] is the latest
     double md_time = 0;
+    bool last_ok = false; // the last solve converged, at molecular-dynamics time last_t
+    double last_t = -1;
     FieldPtr hist[CHRONO_MAX];
     double hist_t[CHRONO_MAX] = {0, 0, 0, 0};
     int n_hist = 0, head = 0;
@@ -120,6 +123,9 @@ static lqcd_status ensure_sloppy(lqcd_hmc_state *st, const lqcd_hmc_params *p, c
         st->Us.f = nullptr;
     }
     if (!st->Us.f) LQCD_TRY(lqcd_field_alloc(&st->U->lat, LQCD_GAUGE, p->cg.sloppy, 12, &st->Us.f));
+    if (!st->Udf.f) LQCD_TRY(field_alloc_df(&st->U->lat, LQCD_GAUGE, &st->Udf.f));
+    LQCD_TRY(split_links(st->Udf.f, st->U, s));
+    st->ws.udf_ext = st->Udf.f;
     return lqcd_field_copy(st->Us.f, st->U, s);
 }
 
@@ -188,6 +194,8 @@ static lqcd_status solve(lqcd_hmc_state *st, const lqcd_hmc_params *p, cudaStrea
     lqcd_cg_params cg = p->cg;
     LQCD_TRY(prepare_guess(st, p, s, &cg.guess));
     lqcd_status rc = cg_solve_ws(st->ws, st->X.f, st->U, sloppy_links(st, p), st->phi.f, p->kappa, cg, &info, s);
+    st->last_ok = rc == LQCD_OK;
+    st->last_t = st->md_time;
     LQCD_TRY(record_solution(st, p, rc == LQCD_OK || rc == LQCD_ENOCONV, s));
     st->cg_iters += info.iters;
     st->n_solves++;
@@ -232,7 +240,8 @@ static lqcd_status drift(lqcd_hmc_state *st, const lqcd_hmc_params *p, double c,
 {
     bool fast = p->force_prec == LQCD_F32;
     st->md_time += c;
-    return link_update_dev(st->U, st->P.f, c, sloppy_links(st, p), fast ? st->Uf.f : nullptr, fast, s);
+    return link_update_dev(st->U, st->P.f, c, sloppy_links(st, p), fast ? st->Uf.f : nullptr, fast, s,
+                           sloppy_links(st, p) ? st->Udf.f : nullptr);
 }
 
 // scalars[0] = plaquette sum, [1] = sum p^2, [2] = fermion term
@@ -271,12 +280,20 @@ static lqcd_status refresh(lqcd_hmc_state *st, const lqcd_hmc_params *p, double 
     return LQCD_OK;
 }
 
-static lqcd_status hamiltonian(lqcd_hmc_state *st, const lqcd_hmc_params *p, double *H, cudaStream_t s)
+// H of the current fields.  reuse_last (inside a trajectory, right after the
+// last kick): the last solve was of the same system and converged, and with a
+// chronological guess a new solve would start from its solution and stop at
+// once, so its solution is used as it is (counted as a solve of 0 iterations).
+static lqcd_status hamiltonian(lqcd_hmc_state *st, const lqcd_hmc_params *p, double *H, cudaStream_t s,
+                               bool reuse_last = false)
 {
     double *d = (double *)st->scal.p;
     LQCD_TRY(hamiltonian_parts(st, s));
     if (p->n_flavors == 2) {
-        LQCD_TRY(solve(st, p, s));
+        if (reuse_last && p->chrono && st->have_guess && st->last_ok && st->last_t == st->md_time)
+            st->n_solves++;
+        else
+            LQCD_TRY(solve(st, p, s));
         LQCD_TRY(spinor_dot_dev(st->phi.f, st->X.f, d + 2, st->part, s));
     }
     double h[3] = {0, 0, 0};
@@ -418,7 +435,7 @@ lqcd_status lqcd_hmc_trajectory(lqcd_hmc_state *s, const lqcd_hmc_params *p, lqc
     double H0 = 0, H1 = 0;
     lqcd_status rc = refresh(s, p, &H0, st);
     if (rc == LQCD_OK) rc = integrate(s, p, st);
-    if (rc == LQCD_OK) rc = hamiltonian(s, p, &H1, st);
+    if (rc == LQCD_OK) rc = hamiltonian(s, p, &H1, st, true);
     double dH = H1 - H0;
     double *d = (double *)s->scal.p;
     metropolis_uniform_kernel<<<1, 1, 0, st>>>(d + 3, s->seed, s->chain, s->traj);
@@ -486,13 +503,20 @@ static lqcd_status check_batch_params(const lqcd_batch *B, const lqcd_hmc_params
 }
 
 // every chain's solve of phi for its current links, with shared launches
-static lqcd_status batch_solve(lqcd_batch *B, const lqcd_hmc_params *p, cudaStream_t s)
+// (reuse_last: as in hamiltonian())
+static lqcd_status batch_solve(lqcd_batch *B, const lqcd_hmc_params *p, cudaStream_t s, bool reuse_last = false)
 {
     size_t n = B->chains.size();
     std::vector<CgRun> runs(n);
     std::vector<CgRun *> ptrs;
+    std::vector<bool> reused(n, false);
     for (size_t i = 0; i < n; i++) {
         lqcd_hmc_state *st = B->chains[i];
+        if (reuse_last && p[i].chrono && st->have_guess && st->last_ok && st->last_t == st->md_time) {
+            reused[i] = true;
+            st->n_solves++;
+            continue;
+        }
         CgRun &r = runs[i];
         r.ws = &st->ws, r.x = st->X.f, r.U = st->U, r.Us = sloppy_links(st, &p[i]), r.b = st->phi.f;
         r.kappa = p[i].kappa;
@@ -504,8 +528,11 @@ static lqcd_status batch_solve(lqcd_batch *B, const lqcd_hmc_params *p, cudaStre
     }
     LQCD_TRY(B->bs.solve(ptrs, s));
     for (size_t i = 0; i < n; i++) {
+        if (reused[i]) continue;
         lqcd_hmc_state *st = B->chains[i];
         const CgRun &r = runs[i];
+        st->last_ok = r.status == LQCD_OK;
+        st->last_t = st->md_time;
         st->cg_iters += r.inf.iters;
         st->n_solves++;
         st->cg_res_max = std::max(st->cg_res_max, r.inf.true_rel_res);
@@ -615,7 +642,7 @@ lqcd_status lqcd_batch_trajectory(lqcd_batch *B, const lqcd_hmc_params *params, 
     lqcd_status rc = batch_integrate(B, params, s);
     if (rc == LQCD_OK) {
         for (size_t i = 0; i < n; i++) LQCD_TRY(hamiltonian_parts(B->chains[i], s));
-        rc = batch_solve(B, params, s);
+        rc = batch_solve(B, params, s, true);
     }
     for (size_t i = 0; i < n; i++) {
         lqcd_hmc_state *st = B->chains[i];
