@@ -671,6 +671,29 @@ static void fermion_force_fields(const geom *g, const double *U, double kappa, c
     free(t);
 }
 
+/* The fields of the force term -2 Re[Y^dag (d Mhat) X] for given even-site
+ * X and Y (the standard term has Y = Mhat X): A = (X_e, Doe X_e),
+ * B = (Y_e, Deo^dag Y_e), full lattice. */
+static void fermion_force_fields_xy(const geom *g, const double *U, const double *X, const double *Y, double *A,
+                                    double *B)
+{
+    long n = g->V * 24;
+    double *Xe = malloc(sizeof(double) * n);
+    double *Ye = malloc(sizeof(double) * n);
+    double *t = malloc(sizeof(double) * n);
+    memcpy(Xe, X, sizeof(double) * n);
+    mask_parity(g, Xe, 0);
+    memcpy(Ye, Y, sizeof(double) * n);
+    mask_parity(g, Ye, 0);
+    dslash_full(g, U, Xe, t, 0, 1);
+    for (long k = 0; k < n; k++) A[k] = Xe[k] + t[k];
+    dslash_full(g, U, Ye, t, 1, 1);
+    for (long k = 0; k < n; k++) B[k] = Ye[k] + t[k];
+    free(Xe);
+    free(Ye);
+    free(t);
+}
+
 /* Fermion force coefficients at one link (x, mu):
  *   Q1 = sum_spin [s U_mu(x) A(x+mu)] [(1 - gamma_mu) B(x)]^dag
  *   Q2 = sum_spin A(x) [s U_mu(x) (1 + gamma_mu) B(x+mu)]^dag
@@ -775,7 +798,7 @@ static void philox_gauss2(uint32_t seed, uint32_t chain, uint32_t site, uint32_t
     gz[1] = r * sin(th);
 }
 
-enum { PURPOSE_GAUGE = 0, PURPOSE_MOM = 1, PURPOSE_ETA = 2, PURPOSE_METRO = 3 };
+enum { PURPOSE_GAUGE = 0, PURPOSE_MOM = 1, PURPOSE_ETA = 2, PURPOSE_METRO = 3, PURPOSE_ETA_H = 4 };
 
 void or_uniform2(uint32_t seed, uint32_t chain, uint32_t site, uint32_t j, uint32_t purpose, uint32_t traj,
                  double *u)
@@ -1008,6 +1031,31 @@ int or_momentum_refresh(const int *dims, uint32_t seed, uint32_t chain, uint32_t
 /* eta on even sites, each real ~ N(0, 1/2): Philox purpose 2, counter
  * (site, j, 2, traj), j = 0..11 giving reals k = 2j, 2j+1 in [spin][color][re,im]
  * order.  Odd sites are zero. */
+static void eta_refresh_purpose(const geom *g, uint32_t seed, uint32_t chain, uint32_t purpose, uint32_t traj,
+                                double *eta)
+{
+    memset(eta, 0, sizeof(double) * 24 * g->V);
+    for (long x = 0; x < g->V; x++) {
+        if (site_parity(g, x) != 0) continue;
+        for (int j = 0; j < 12; j++) {
+            double z[2];
+            philox_gauss2(seed, chain, (uint32_t)x, j, purpose, traj, z);
+            eta[x * 24 + 2 * j] = z[0] * sqrt(0.5);
+            eta[x * 24 + 2 * j + 1] = z[1] * sqrt(0.5);
+        }
+    }
+}
+
+/* the second pseudofermion's eta of the Hasenbusch action: as or_eta_refresh
+ * with Philox purpose 4 */
+int or_eta_refresh_h(const int *dims, uint32_t seed, uint32_t chain, uint32_t traj, double *eta)
+{
+    geom g;
+    if (geom_init(&g, dims, -1)) return -1;
+    eta_refresh_purpose(&g, seed, chain, PURPOSE_ETA_H, traj, eta);
+    return 0;
+}
+
 int or_eta_refresh(const int *dims, uint32_t seed, uint32_t chain, uint32_t traj, double *eta)
 {
     geom g;
@@ -1256,5 +1304,280 @@ int or_hmc_trajectory(const int *dims, int t_bc, double *U, double beta, double 
     free(U0);
     free(eta);
     free(phi);
+    return 0;
+}
+
+/* --------------------------------------------- Hasenbusch action, nested integration
+ *
+ * Mass preconditioning (the production feature named with the chronological
+ * guess in Sec. 6.2) splits det(Mhat^dag Mhat) with W = Mhat(kappa_h),
+ * kappa_h < kappa, into two pseudofermion actions:
+ *   heavy  S_h = phi_h^dag (W^dag W)^-1 phi_h,
+ *   ratio  S_r = chi^dag (Mhat^dag Mhat)^-1 chi,  chi = W^dag phi_r,
+ * whose Gaussian integrals give det(W^dag W) and det(Mhat^dag Mhat)/det(W^dag W).
+ * With X_r = (Mhat^dag Mhat)^-1 chi,
+ *   dS_r = -2 Re[(Mhat X_r)^dag dMhat X_r] + 2 Re[phi_r^dag dW X_r],
+ * i.e. the standard force term of (X_r, Y = Mhat X_r, kappa) minus the term
+ * of (X_r, Y = phi_r, kappa_h).  Refresh: phi_h = W^dag eta_h, and
+ * phi_r = W^-dag Mhat^dag eta = W (W^dag W)^-1 Mhat^dag eta, so that
+ * S_h = |eta_h|^2 and S_r = |eta|^2 at the start.
+ *
+ * Nested integration (Sexton-Weingarten): with gauge_substeps m >= 2 the
+ * gauge action (and the heavy action if heavy_inner) moves on an inner level
+ * that integrates each drift of the outer level in m steps of the same scheme
+ * (leapfrog or Omelyan 2MN); the fermion actions stay on the outer level of
+ * nsteps steps.  Kicks are applied as they come (none merged). */
+
+enum { TERM_GAUGE = 1, TERM_FERMION = 2, TERM_HEAVY = 4 };
+
+typedef struct {
+    double beta, kappa, kappa_h, tau;
+    int nsteps, integrator, n_flavors, gauge_substeps, heavy_inner;
+    double cg_tol;
+    int cg_maxiter;
+} hb_params;
+
+/* P <- P - c F_xy with F_xy the force of -2 Re[Y^dag dMhat(kappa) X] */
+static void add_force_xy(const geom *g, const double *U, double kappa, const double *X, const double *Y, double *P,
+                         double c)
+{
+    double *A = malloc(sizeof(double) * 24 * g->V);
+    double *B = malloc(sizeof(double) * 24 * g->V);
+    fermion_force_fields_xy(g, U, X, Y, A, B);
+    double f[8];
+    for (long x = 0; x < g->V; x++)
+        for (int mu = 0; mu < 4; mu++) {
+            fermion_force_link(g, U, kappa, A, B, x, mu, f);
+            for (int a = 0; a < 8; a++) P[(x * 4 + mu) * 8 + a] -= c * f[a];
+        }
+    free(A);
+    free(B);
+}
+
+/* X = (Mhat(kappa)^dag Mhat(kappa))^-1 b and Y = Mhat(kappa) X */
+static void solve_xy(const geom *g, const double *U, double kappa, const double *b, double *X, double *Y,
+                     const hb_params *hp, md_stats *st)
+{
+    int it;
+    double rel;
+    if (cg_solve(g, U, kappa, b, X, hp->cg_tol, hp->cg_maxiter, &it, &rel)) st->cg_fail++;
+    st->cg_iters += it;
+    st->n_solves++;
+    if (Y) mhat(g, U, kappa, X, Y, 0);
+}
+
+/* P <- P - c F of the selected action terms */
+static void hb_kick(const geom *g, const double *U, double *P, const hb_params *hp, const double *phi,
+                    const double *phi_h, int terms, double c, md_stats *st)
+{
+    if (terms & TERM_GAUGE) {
+        double f[8];
+        for (long x = 0; x < g->V; x++)
+            for (int mu = 0; mu < 4; mu++) {
+                gauge_force_link(g, U, hp->beta, x, mu, f);
+                for (int a = 0; a < 8; a++) P[(x * 4 + mu) * 8 + a] -= c * f[a];
+            }
+    }
+    if (hp->n_flavors != 2) return;
+    long n = 24 * g->V;
+    double *X = malloc(sizeof(double) * n), *Y = malloc(sizeof(double) * n), *chi = malloc(sizeof(double) * n);
+    if (terms & TERM_FERMION) {
+        if (hp->kappa_h == 0) {
+            solve_xy(g, U, hp->kappa, phi, X, Y, hp, st);
+            add_force_xy(g, U, hp->kappa, X, Y, P, c);
+        } else {
+            mhat(g, U, hp->kappa_h, phi, chi, 1);
+            solve_xy(g, U, hp->kappa, chi, X, Y, hp, st);
+            add_force_xy(g, U, hp->kappa, X, Y, P, c);
+            add_force_xy(g, U, hp->kappa_h, X, phi, P, -c);
+        }
+    }
+    if ((terms & TERM_HEAVY) && hp->kappa_h != 0) {
+        solve_xy(g, U, hp->kappa_h, phi_h, X, Y, hp, st);
+        add_force_xy(g, U, hp->kappa_h, X, Y, P, c);
+    }
+    free(X);
+    free(Y);
+    free(chi);
+}
+
+static int hb_levels(const hb_params *hp) { return hp->gauge_substeps >= 2 ? 2 : 1; }
+
+static int hb_terms(const hb_params *hp, int level)
+{
+    if (hb_levels(hp) == 1) return TERM_GAUGE | TERM_FERMION | TERM_HEAVY;
+    if (level == 0) return TERM_FERMION | (hp->heavy_inner ? 0 : TERM_HEAVY);
+    return TERM_GAUGE | (hp->heavy_inner ? TERM_HEAVY : 0);
+}
+
+static void hb_integrate(const geom *g, double *U, double *P, const hb_params *hp, const double *phi,
+                         const double *phi_h, int level, double t, md_stats *st);
+
+/* the drift of one level: the next level's integration, or the link update */
+static void hb_inner(const geom *g, double *U, double *P, const hb_params *hp, const double *phi,
+                     const double *phi_h, int level, double t, md_stats *st)
+{
+    if (level + 1 < hb_levels(hp))
+        hb_integrate(g, U, P, hp, phi, phi_h, level + 1, t, st);
+    else
+        drift(g, U, P, t);
+}
+
+static void hb_integrate(const geom *g, double *U, double *P, const hb_params *hp, const double *phi,
+                         const double *phi_h, int level, double t, md_stats *st)
+{
+    const int n = level == 0 ? hp->nsteps : hp->gauge_substeps;
+    const int terms = hb_terms(hp, level);
+    const double h = t / n;
+    const double lam = 0.1931833275037836;
+    for (int s = 0; s < n; s++) {
+        if (hp->integrator == 0) {
+            hb_kick(g, U, P, hp, phi, phi_h, terms, 0.5 * h, st);
+            hb_inner(g, U, P, hp, phi, phi_h, level, h, st);
+            hb_kick(g, U, P, hp, phi, phi_h, terms, 0.5 * h, st);
+        } else {
+            hb_kick(g, U, P, hp, phi, phi_h, terms, lam * h, st);
+            hb_inner(g, U, P, hp, phi, phi_h, level, 0.5 * h, st);
+            hb_kick(g, U, P, hp, phi, phi_h, terms, (1.0 - 2.0 * lam) * h, st);
+            hb_inner(g, U, P, hp, phi, phi_h, level, 0.5 * h, st);
+            hb_kick(g, U, P, hp, phi, phi_h, terms, lam * h, st);
+        }
+    }
+}
+
+/* S_f of the current links: phi^dag (Mhat^dag Mhat)^-1 phi, or S_r + S_h */
+static double hb_fermion_action(const geom *g, const double *U, const hb_params *hp, const double *phi,
+                                const double *phi_h, md_stats *st)
+{
+    long n = 24 * g->V;
+    double *X = malloc(sizeof(double) * n), *chi = malloc(sizeof(double) * n);
+    double S;
+    if (hp->kappa_h == 0) {
+        solve_xy(g, U, hp->kappa, phi, X, NULL, hp, st);
+        S = dot_re(g, phi, X);
+    } else {
+        mhat(g, U, hp->kappa_h, phi, chi, 1);
+        solve_xy(g, U, hp->kappa, chi, X, NULL, hp, st);
+        S = dot_re(g, chi, X);
+        solve_xy(g, U, hp->kappa_h, phi_h, X, NULL, hp, st);
+        S += dot_re(g, phi_h, X);
+    }
+    free(X);
+    free(chi);
+    return S;
+}
+
+/* The ratio action S_r and its force coefficients F[V][4][8] (NULL: none)
+ * for a given phi_r: the pieces of the Hasenbusch trajectory, for tests. */
+int or_hasenbusch_ratio(const int *dims, int t_bc, const double *U, double kappa, double kappa_h,
+                        const double *phi_r, double tol, int maxiter, double *S, double *F)
+{
+    geom g;
+    if (geom_init(&g, dims, t_bc)) return -1;
+    hb_params hp = {0, kappa, kappa_h, 0, 0, 0, 2, 0, 0, tol, maxiter};
+    md_stats st = {0, 0, 0};
+    long n = 24 * g.V;
+    double *X = malloc(sizeof(double) * n), *Y = malloc(sizeof(double) * n), *chi = malloc(sizeof(double) * n);
+    mhat(&g, U, kappa_h, phi_r, chi, 1);
+    solve_xy(&g, U, kappa, chi, X, Y, &hp, &st);
+    *S = dot_re(&g, chi, X);
+    if (F) {
+        double *P = calloc(g.V * 32, sizeof(double));
+        add_force_xy(&g, U, kappa, X, Y, P, -1.0);
+        add_force_xy(&g, U, kappa_h, X, phi_r, P, 1.0);
+        memcpy(F, P, sizeof(double) * g.V * 32);
+        free(P);
+    }
+    free(X);
+    free(Y);
+    free(chi);
+    return st.cg_fail ? 1 : 0;
+}
+
+/* The Hasenbusch refresh: phi_h = W^dag eta_h, phi_r = W (W^dag W)^-1 Mhat^dag eta
+ * for given eta, eta_h (even sites). */
+int or_hasenbusch_refresh(const int *dims, int t_bc, const double *U, double kappa, double kappa_h,
+                          const double *eta, const double *eta_h, double tol, int maxiter, double *phi_r,
+                          double *phi_h)
+{
+    geom g;
+    if (geom_init(&g, dims, t_bc)) return -1;
+    hb_params hp = {0, kappa, kappa_h, 0, 0, 0, 2, 0, 0, tol, maxiter};
+    md_stats st = {0, 0, 0};
+    long n = 24 * g.V;
+    double *t = malloc(sizeof(double) * n), *z = malloc(sizeof(double) * n);
+    mhat(&g, U, kappa_h, eta_h, phi_h, 1);
+    mhat(&g, U, kappa, eta, t, 1);
+    solve_xy(&g, U, kappa_h, t, z, phi_r, &hp, &st);
+    free(t);
+    free(z);
+    return st.cg_fail ? 1 : 0;
+}
+
+/* One HMC trajectory with the Hasenbusch action (kappa_h > 0) and/or the nested
+ * integrator (gauge_substeps >= 2); kappa_h = 0 and gauge_substeps <= 1 give
+ * the trajectory of or_hmc_trajectory with unmerged kicks.  The second eta
+ * comes from Philox purpose 4.  info_out as or_hmc_trajectory. */
+int or_hmc_trajectory_hb(const int *dims, int t_bc, double *U, double beta, double kappa, double kappa_h,
+                         double tau, int nsteps, int integrator, int n_flavors, int gauge_substeps, int heavy_inner,
+                         double cg_tol, int cg_maxiter, uint32_t seed, uint32_t chain, uint32_t traj, int do_reunit,
+                         int do_metropolis, double *info_out)
+{
+    geom g;
+    if (geom_init(&g, dims, t_bc)) return -1;
+    hb_params hp = {beta, kappa, kappa_h, tau, nsteps, integrator, n_flavors, gauge_substeps, heavy_inner,
+                    cg_tol, cg_maxiter};
+    md_stats st = {0, 0, 0};
+    long nl = g.V * 4 * 18, ns = g.V * 24;
+    double *P = malloc(sizeof(double) * g.V * 32);
+    double *U0 = malloc(sizeof(double) * nl);
+    double *eta = malloc(sizeof(double) * ns), *eta_h = malloc(sizeof(double) * ns);
+    double *phi = calloc(ns, sizeof(double)), *phi_h = calloc(ns, sizeof(double));
+    memcpy(U0, U, sizeof(double) * nl);
+    or_momentum_refresh(dims, seed, chain, traj, P);
+    double H0 = or_kinetic(dims, P) + beta * (6.0 * g.V - plaq_sum(&g, U));
+    if (n_flavors == 2) {
+        eta_refresh_purpose(&g, seed, chain, PURPOSE_ETA, traj, eta);
+        H0 += dot_re(&g, eta, eta);
+        if (kappa_h == 0) {
+            mhat(&g, U, kappa, eta, phi, 1);
+        } else {
+            eta_refresh_purpose(&g, seed, chain, PURPOSE_ETA_H, traj, eta_h);
+            H0 += dot_re(&g, eta_h, eta_h);
+            double *t = malloc(sizeof(double) * ns), *z = malloc(sizeof(double) * ns);
+            mhat(&g, U, kappa_h, eta_h, phi_h, 1);
+            mhat(&g, U, kappa, eta, t, 1);
+            solve_xy(&g, U, kappa_h, t, z, phi, &hp, &st);
+            free(t);
+            free(z);
+        }
+    }
+    hb_integrate(&g, U, P, &hp, phi, phi_h, 0, tau, &st);
+    double H1 = or_kinetic(dims, P) + beta * (6.0 * g.V - plaq_sum(&g, U));
+    if (n_flavors == 2) H1 += hb_fermion_action(&g, U, &hp, phi, phi_h, &st);
+    double dH = H1 - H0;
+    double u[2];
+    philox_uniform2(seed, chain, 0, 0, PURPOSE_METRO, traj, u);
+    int accept = 1;
+    if (do_metropolis) accept = isfinite(dH) && (u[0] < exp(-dH));
+    if (!accept) memcpy(U, U0, sizeof(double) * nl);
+    double maxdev = 0;
+    if (do_reunit) or_reunitarize(dims, U, &maxdev);
+    info_out[0] = dH;
+    info_out[1] = accept;
+    info_out[2] = plaq_sum(&g, U) / (6.0 * g.V);
+    info_out[3] = (double)st.cg_iters;
+    info_out[4] = H0;
+    info_out[5] = H1;
+    info_out[6] = u[0];
+    info_out[7] = maxdev;
+    info_out[8] = st.n_solves;
+    info_out[9] = st.cg_fail;
+    free(P);
+    free(U0);
+    free(eta);
+    free(eta_h);
+    free(phi);
+    free(phi_h);
     return 0;
 }

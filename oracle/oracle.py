@@ -87,6 +87,11 @@ def _declare(L):
         "or_hamiltonian": (_i, [_ip, _i, _dp, _dp, _dp, _d, _d, _i, _d, _i, _dp]),
         "or_hmc_trajectory": (_i, [_ip, _i, _dp, _d, _d, _d, _i, _i, _i, _d, _i,
                                    _u32, _u32, _u32, _i, _i, _dp]),
+        "or_eta_refresh_h": (_i, [_ip, _u32, _u32, _u32, _dp]),
+        "or_hasenbusch_ratio": (_i, [_ip, _i, _dp, _d, _d, _dp, _d, _i, _dp, _dp]),
+        "or_hasenbusch_refresh": (_i, [_ip, _i, _dp, _d, _d, _dp, _dp, _d, _i, _dp, _dp]),
+        "or_hmc_trajectory_hb": (_i, [_ip, _i, _dp, _d, _d, _d, _d, _i, _i, _i, _i, _i, _d, _i,
+                                      _u32, _u32, _u32, _i, _i, _dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -338,6 +343,48 @@ def hmc_trajectory(dims, U, beta, kappa, tau, nsteps, integrator=LEAPFROG, n_fla
     _check(lib().or_hmc_trajectory(_dims(dims), t_bc, _ptr(U), beta, kappa, tau, nsteps, integrator,
                                    n_flavors, cg_tol, cg_maxiter, seed, chain, traj, int(reunit),
                                    int(metropolis), _ptr(info)))
+    return U, dict(zip(TRAJ_KEYS, info.tolist()))
+
+
+def eta_refresh_h(dims, seed, traj, chain=0) -> np.ndarray:
+    """the Hasenbusch action's second eta (Philox purpose 4)"""
+    eta = new_spinor(dims)
+    _check(lib().or_eta_refresh_h(_dims(dims), seed, chain, traj, _ptr(eta)))
+    return eta
+
+
+def hasenbusch_ratio(dims, U, kappa, kappa_h, phi_r, tol=1e-12, maxiter=10000, force=True, t_bc=-1):
+    """S_r = chi^dag (Mhat^dag Mhat)^-1 chi, chi = W^dag phi_r with W = Mhat(kappa_h),
+    and its force coefficients (V, 4, 8) (Sec. 6.2: mass preconditioning)"""
+    S = ctypes.c_double()
+    F = new_momentum(dims) if force else None
+    rc = lib().or_hasenbusch_ratio(_dims(dims), t_bc, _ptr(U), kappa, kappa_h, _ptr(phi_r), tol, maxiter,
+                                   ctypes.byref(S), _ptr(F) if force else None)
+    if rc < 0:
+        raise ValueError("bad geometry")
+    return S.value, F
+
+
+def hasenbusch_refresh(dims, U, kappa, kappa_h, eta, eta_h, tol=1e-12, maxiter=10000, t_bc=-1):
+    """(phi_r, phi_h) = (W (W^dag W)^-1 Mhat^dag eta, W^dag eta_h)"""
+    phi_r, phi_h = new_spinor(dims), new_spinor(dims)
+    rc = lib().or_hasenbusch_refresh(_dims(dims), t_bc, _ptr(U), kappa, kappa_h, _ptr(eta), _ptr(eta_h), tol,
+                                     maxiter, _ptr(phi_r), _ptr(phi_h))
+    if rc < 0:
+        raise ValueError("bad geometry")
+    return phi_r, phi_h
+
+
+def hmc_trajectory_hb(dims, U, beta, kappa, kappa_h, tau, nsteps, integrator=LEAPFROG, n_flavors=2,
+                      gauge_substeps=0, heavy_inner=False, cg_tol=1e-10, cg_maxiter=10000, seed=1, chain=0, traj=0,
+                      reunit=True, metropolis=True, t_bc=-1):
+    """one trajectory with the Hasenbusch action (kappa_h > 0) and the nested
+    integrator (gauge_substeps >= 2); returns (U_new, info dict)"""
+    U = U.copy()
+    info = np.zeros(10)
+    _check(lib().or_hmc_trajectory_hb(_dims(dims), t_bc, _ptr(U), beta, kappa, kappa_h, tau, nsteps, integrator,
+                                      n_flavors, gauge_substeps, int(heavy_inner), cg_tol, cg_maxiter, seed, chain,
+                                      traj, int(reunit), int(metropolis), _ptr(info)))
     return U, dict(zip(TRAJ_KEYS, info.tolist()))
 
 
