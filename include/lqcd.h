@@ -344,6 +344,18 @@ typedef struct {
                                    exponential by Cayley-Hamilton in FP32, re-unitarized and
                                    multiplied onto the FP64 links in float-float arithmetic
                                    (~48 bits: the links stay in SU(3) to ~1e-14 per update) */
+    double hasenbusch_kappa;    /* 0: one pseudofermion with Mhat(kappa).  In (0, kappa): mass
+                                   preconditioning (paper Sec. 6.2) with W = Mhat(hasenbusch_kappa):
+                                   a heavy action phi_h^dag (W^dag W)^-1 phi_h and a ratio action
+                                   chi^dag (Mhat^dag Mhat)^-1 chi, chi = W^dag phi; refresh
+                                   phi_h = W^dag eta_h (eta_h from Philox purpose 4) and
+                                   phi = W (W^dag W)^-1 Mhat^dag eta (one solve) */
+    int gauge_substeps;         /* <= 1: every force on one time scale.  m >= 2: nested integration
+                                   (Sexton-Weingarten): the gauge force (and the heavy action if
+                                   heavy_inner) on an inner level integrating each drift of the
+                                   outer level in m steps of the same scheme; the fermion actions
+                                   on the outer level of nsteps steps */
+    int heavy_inner;            /* with gauge_substeps >= 2: the heavy action on the inner level */
 } lqcd_hmc_params;
 
 typedef struct {

@@ -558,7 +558,8 @@ __global__ void momentum_refresh_kernel(MomRef P, Geo g, int V, uint32_t seed, u
     }
 }
 
-__global__ void eta_refresh_kernel(SpinorRef<LQCD_F64> E, Geo g, uint32_t seed, uint32_t chain, uint32_t traj)
+__global__ void eta_refresh_kernel(SpinorRef<LQCD_F64> E, Geo g, uint32_t seed, uint32_t chain, uint32_t traj,
+                                   uint32_t purpose)
 {
     int cb = blockIdx.x * blockDim.x + threadIdx.x;
     if (cb >= g.Vh) return;
@@ -569,7 +570,7 @@ __global__ void eta_refresh_kernel(SpinorRef<LQCD_F64> E, Geo g, uint32_t seed, 
     Sp<double> v;
     for (int j = 0; j < 12; j++) { // complex component j = spin*3 + colour
         double g0, g1;
-        philox_gauss2(seed, chain, (uint32_t)lex, (uint32_t)j, 2u, traj, g0, g1);
+        philox_gauss2(seed, chain, (uint32_t)lex, (uint32_t)j, purpose, traj, g0, g1);
         v.c[j / 3][j % 3] = cx<double>(g0 * s, g1 * s);
     }
     E.store(cb, v);
@@ -891,10 +892,12 @@ lqcd_status momentum_refresh_dev(lqcd_field *P, uint32_t seed, uint32_t chain, u
     return LQCD_OK;
 }
 
-lqcd_status eta_refresh_dev(lqcd_field *E, uint32_t seed, uint32_t chain, uint32_t traj, cudaStream_t s)
+lqcd_status eta_refresh_dev(lqcd_field *E, uint32_t seed, uint32_t chain, uint32_t traj, cudaStream_t s,
+                            uint32_t purpose)
 {
     Geo g = make_geo(E->lat);
-    eta_refresh_kernel<<<nblocks_for(g.Vh, 128), 128, 0, s>>>(spinor_ref<LQCD_F64>(E), g, seed, chain, traj);
+    eta_refresh_kernel<<<nblocks_for(g.Vh, 128), 128, 0, s>>>(spinor_ref<LQCD_F64>(E), g, seed, chain, traj,
+                                                              purpose);
     LQCD_LAUNCHED();
     return LQCD_OK;
 }
@@ -1104,7 +1107,7 @@ lqcd_status lqcd_momentum_refresh(lqcd_field *P, uint32_t seed, uint32_t chain, 
 lqcd_status lqcd_eta_refresh(lqcd_field *eta, uint32_t seed, uint32_t chain, uint32_t traj, void *stream)
 {
     LQCD_REQUIRE(eta && eta->kind == LQCD_SPINOR_EVEN && eta->prec == LQCD_F64, "eta_refresh needs an even F64 spinor");
-    return eta_refresh_dev(eta, seed, chain, traj, (cudaStream_t)stream);
+    return eta_refresh_dev(eta, seed, chain, traj, (cudaStream_t)stream, 2u);
 }
 
 lqcd_status lqcd_link_update(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *U_sloppy, void *stream)

@@ -200,12 +200,14 @@ lqcd_status gauge_force_dev(lqcd_field *P, const lqcd_field *U, const lqcd_field
     return LQCD_OK;
 }
 
-// A_o = Doe X_e, Y_e = Mhat X_e = X_e - kappa^2 Deo A_o, B_o = Doe^dag-hop Y_e, then the link kernel.
-// The temporaries' precision (F64 or F32) sets the arithmetic; for F32 the
-// links come from the FP32 12-real copy Uf and X is rounded into Xc first.
+// A_o = Doe X_e, Y_e = Mhat X_e = X_e - kappa^2 Deo A_o, B_o = Doe^dag-hop Y_e, then the link kernel:
+// P -= coeff F with F the force of -2 Re[Y^dag dMhat X].  Y (optional) replaces
+// Mhat X (the second term of the Hasenbusch ratio action).  The temporaries'
+// precision (F64 or F32) sets the arithmetic; for F32 the links come from the
+// FP32 12-real copy Uf and X (and Y) are rounded into Xc (Ye) first.
 lqcd_status fermion_force_dev(lqcd_field *P, const lqcd_field *U, const lqcd_field *Uf, const lqcd_field *X,
                               double kappa, double coeff, lqcd_field *Ao, lqcd_field *Ye, lqcd_field *Bo, lqcd_field *Xc,
-                              cudaStream_t s)
+                              cudaStream_t s, const lqcd_field *Y)
 {
     const lqcd_field *Xa = X;
     const lqcd_field *L = Ao->prec == LQCD_F32 ? Uf : U;
@@ -214,8 +216,16 @@ lqcd_status fermion_force_dev(lqcd_field *P, const lqcd_field *U, const lqcd_fie
         Xa = Xc;
     }
     LQCD_TRY(dslash_plain(Ao, L, Xa, 0, nullptr, s));
-    LQCD_TRY(dslash_xpay(Ye, L, Ao, 0, Xa, -kappa * kappa, nullptr, nullptr, s));
-    LQCD_TRY(dslash_plain(Bo, L, Ye, 1, nullptr, s));
+    const lqcd_field *Ya = Ye;
+    if (Y) {
+        if (Y->prec != Ye->prec)
+            LQCD_TRY(lqcd_field_copy(Ye, Y, s));
+        else
+            Ya = Y;
+    } else {
+        LQCD_TRY(dslash_xpay(Ye, L, Ao, 0, Xa, -kappa * kappa, nullptr, nullptr, s));
+    }
+    LQCD_TRY(dslash_plain(Bo, L, Ya, 1, nullptr, s));
     Geo g = make_geo(U->lat);
     KernelTimer kt(K_FERMION_FORCE, s);
     int nb = nblocks_for(8L * g.Vh, FB);
@@ -223,11 +233,11 @@ lqcd_status fermion_force_dev(lqcd_field *P, const lqcd_field *U, const lqcd_fie
     if (Ao->prec == LQCD_F32)
         fermion_force_kernel<float, LQCD_F32, LQCD_F32><<<nb, FB, 0, s>>>(
             mom_ref(P), gauge_ref<LQCD_F32>(Uf), g, spinor_ref<LQCD_F32>(Xa), spinor_ref<LQCD_F32>(Ao),
-            spinor_ref<LQCD_F32>(Ye), spinor_ref<LQCD_F32>(Bo), cf);
+            spinor_ref<LQCD_F32>(Ya), spinor_ref<LQCD_F32>(Bo), cf);
     else
         fermion_force_kernel<double, LQCD_F64, LQCD_F64><<<nb, FB, 0, s>>>(
             mom_ref(P), gauge_ref<LQCD_F64>(U), g, spinor_ref<LQCD_F64>(Xa), spinor_ref<LQCD_F64>(Ao),
-            spinor_ref<LQCD_F64>(Ye), spinor_ref<LQCD_F64>(Bo), cf);
+            spinor_ref<LQCD_F64>(Ya), spinor_ref<LQCD_F64>(Bo), cf);
     LQCD_LAUNCHED();
     return LQCD_OK;
 }
@@ -279,7 +289,7 @@ lqcd_status lqcd_fermion_force_ex(lqcd_field *P, const lqcd_field *U, const lqcd
         LQCD_TRY(lqcd_field_alloc(&U->lat, LQCD_GAUGE, LQCD_F32, 12, &Uf.f));
         LQCD_TRY(lqcd_field_copy(Uf.f, U, s));
     }
-    LQCD_TRY(fermion_force_dev(P, U, Uf.f, X_e, kappa, coeff, Ao.f, Ye.f, Bo.f, Xc.f, s));
+    LQCD_TRY(fermion_force_dev(P, U, Uf.f, X_e, kappa, coeff, Ao.f, Ye.f, Bo.f, Xc.f, s, nullptr));
     LQCD_CUDA(cudaStreamSynchronize(s)); // temporaries are freed on return
     return LQCD_OK;
 }

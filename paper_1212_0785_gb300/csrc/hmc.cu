@@ -1,7 +1,9 @@
 // hmc.cu -- Hybrid Monte Carlo driver: refresh, molecular dynamics with merged
-// kicks (leapfrog or Omelyan 2MN), Hamiltonian, Metropolis and
-// reunitarization, every field operation on the device (paper Sec. 1: the
-// whole trajectory runs on the accelerator; Sec. 6.2: Nf = 2 Wilson HMC).
+// kicks (leapfrog or Omelyan 2MN, optionally nested on two time scales),
+// Hamiltonian, Metropolis and reunitarization, every field operation on the
+// device (paper Sec. 1: the whole trajectory runs on the accelerator; Sec. 6.2:
+// Nf = 2 Wilson HMC, with mass preconditioning and chronological guesses among
+// its production features).
 //
 // The host only sequences kernels and reads back the scalars it must decide
 // on (solver convergence, dH and the Metropolis uniform, the plaquette).
@@ -21,12 +23,13 @@ lqcd_status reunitarize_dev(lqcd_field *U, double *dst_dev, DevBuf &part, cudaSt
 lqcd_status link_update_dev(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *Us, lqcd_field *Uf, bool fast,
                             cudaStream_t s, lqcd_field *Udf);
 lqcd_status momentum_refresh_dev(lqcd_field *P, uint32_t seed, uint32_t chain, uint32_t traj, cudaStream_t s);
-lqcd_status eta_refresh_dev(lqcd_field *E, uint32_t seed, uint32_t chain, uint32_t traj, cudaStream_t s);
+lqcd_status eta_refresh_dev(lqcd_field *E, uint32_t seed, uint32_t chain, uint32_t traj, cudaStream_t s,
+                            uint32_t purpose);
 lqcd_status gauge_force_dev(lqcd_field *P, const lqcd_field *U, const lqcd_field *Uf, double beta, double coeff,
                             lqcd_prec arith, cudaStream_t s);
 lqcd_status fermion_force_dev(lqcd_field *P, const lqcd_field *U, const lqcd_field *Uf, const lqcd_field *X,
                               double kappa, double coeff, lqcd_field *Ao, lqcd_field *Ye, lqcd_field *Bo, lqcd_field *Xc,
-                              cudaStream_t s);
+                              cudaStream_t s, const lqcd_field *Y);
 
 constexpr double OMELYAN_LAMBDA = 0.1931833275037836;
 
@@ -66,32 +69,64 @@ using namespace lqcd;
 
 constexpr int CHRONO_MAX = 4;
 
+// One pseudofermion action of the trajectory: its field, the last solution of
+// its solve and what the chronological guess of its next solve needs.
+struct PfTerm {
+    lqcd::FieldPtr phi, X;
+    lqcd::FieldPtr chi; // ratio action: the right-hand side W^dag phi of its solve
+    bool have_guess = false; // X holds a solution for the current phi
+    bool last_ok = false;    // the last solve converged, at molecular-dynamics time last_t
+    double last_t = -1;
+    // solutions of this trajectory's solves and the molecular-dynamics times
+    // (sum of the drifts since the refresh) of their links;
+    // hist[(head - 1) mod CHRONO_MAX] is the latest
+    lqcd::FieldPtr hist[CHRONO_MAX];
+    double hist_t[CHRONO_MAX] = {0, 0, 0, 0};
+    int n_hist = 0, head = 0;
+    void reset()
+    {
+        have_guess = last_ok = false;
+        n_hist = 0;
+    }
+};
+
+// pseudofermion terms: the fermion action (the ratio action when mass
+// preconditioned) and the heavy Hasenbusch action
+enum { PF_MAIN = 0, PF_HEAVY = 1 };
+// force terms of a time-scale level
+enum { TERM_GAUGE = 1, TERM_FERMION = 2, TERM_HEAVY = 4 };
+
 struct lqcd_hmc_state {
     lqcd_field *U = nullptr; // borrowed
     uint32_t seed = 0, chain = 0, traj = 0;
-    FieldPtr P, eta, phi, X, Ao, Ye, Bo, Ubak, Us;
-    FieldPtr Ao32, Ye32, Bo32, X32; // FP32 fermion-force temporaries (allocated on first use)
-    FieldPtr Uf;                    // FP32 12-real link copy for the FP32 molecular dynamics
-    FieldPtr Udf; // float-float link copy of the mixed solver, kept current by every link update
-    CgWorkspace ws;
-    DevBuf part, scal;
+    lqcd::FieldPtr P, eta, Ao, Ye, Bo, Ubak, Us;
+    lqcd::FieldPtr eta_h, z;                // Hasenbusch refresh (allocated on first use)
+    lqcd::FieldPtr Ao32, Ye32, Bo32, X32;   // FP32 fermion-force temporaries (allocated on first use)
+    lqcd::FieldPtr Uf;                      // FP32 12-real link copy for the FP32 molecular dynamics
+    lqcd::FieldPtr Udf; // float-float link copy of the mixed solver, kept current by every link update
+    PfTerm pf[2];
+    lqcd::CgWorkspace ws;
+    lqcd::DevBuf part, scal;
     double H0 = 0;
-    bool have_guess = false; // X holds a solution for the current phi
-    // solutions of this trajectory's solves and the molecular-dynamics times
-    // (sum of the drifts since the refresh) of their links, for the
-    // extrapolated initial guess; hist[(head - 1) mod CHRONO_MAX] is the latest
     double md_time = 0;
-    bool last_ok = false; // the last solve converged, at molecular-dynamics time last_t
-    double last_t = -1;
-    FieldPtr hist[CHRONO_MAX];
-    double hist_t[CHRONO_MAX] = {0, 0, 0, 0};
-    int n_hist = 0, head = 0;
+    double pending[2] = {0, 0}; // kick coefficients of each level not yet applied
     // statistics of the current trajectory
     int cg_iters = 0, n_solves = 0, cg_failures = 0;
     double cg_res_max = 0;
 };
 
 namespace lqcd {
+
+static bool hasenbusch(const lqcd_hmc_params *p) { return p->n_flavors == 2 && p->hasenbusch_kappa != 0.0; }
+static int n_levels(const lqcd_hmc_params *p) { return p->gauge_substeps >= 2 ? 2 : 1; }
+
+// the force terms integrated on a level
+static int level_terms(const lqcd_hmc_params *p, int level)
+{
+    if (n_levels(p) == 1) return TERM_GAUGE | TERM_FERMION | TERM_HEAVY;
+    if (level == 0) return TERM_FERMION | (p->heavy_inner ? 0 : TERM_HEAVY);
+    return TERM_GAUGE | (p->heavy_inner ? TERM_HEAVY : 0);
+}
 
 static lqcd_status check_params(const lqcd_hmc_params *p)
 {
@@ -103,9 +138,12 @@ static lqcd_status check_params(const lqcd_hmc_params *p)
         LQCD_REQUIRE(p->cg.tol > 0 && p->cg.maxiter > 0, "hmc: cg tol and maxiter must be positive");
         LQCD_REQUIRE(p->cg.sloppy == LQCD_F64 || (p->cg.delta > 0 && p->cg.delta < 1),
                      "hmc: cg delta must lie in (0, 1) for a mixed solve");
+        LQCD_REQUIRE(p->hasenbusch_kappa >= 0 && p->hasenbusch_kappa < p->kappa,
+                     "hmc: hasenbusch_kappa must be 0 (off) or lie in (0, kappa)");
     }
     LQCD_REQUIRE(p->force_prec == LQCD_F64 || p->force_prec == LQCD_F32, "hmc: force_prec must be F64 or F32");
     LQCD_REQUIRE(p->chrono >= 0 && p->chrono <= CHRONO_MAX, "hmc: chrono must lie in 0..%d", CHRONO_MAX);
+    LQCD_REQUIRE(p->gauge_substeps >= 0, "hmc: gauge_substeps must be >= 0");
     return LQCD_OK;
 }
 
@@ -129,31 +167,44 @@ static lqcd_status ensure_sloppy(lqcd_hmc_state *st, const lqcd_hmc_params *p, c
     return lqcd_field_copy(st->Us.f, st->U, s);
 }
 
+static lqcd_status ensure_hasenbusch(lqcd_hmc_state *st)
+{
+    if (st->eta_h.f) return LQCD_OK;
+    const lqcd_lattice &lat = st->U->lat;
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->eta_h.f));
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->z.f));
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->pf[PF_MAIN].chi.f));
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->pf[PF_HEAVY].phi.f));
+    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->pf[PF_HEAVY].X.f));
+    return LQCD_OK;
+}
+
 static lqcd_field *sloppy_links(lqcd_hmc_state *st, const lqcd_hmc_params *p)
 {
     return (p->n_flavors == 2 && p->cg.sloppy != LQCD_F64) ? st->Us.f : nullptr;
 }
 
-// The initial guess of the next solve, in X; returns whether there is one.
-// chrono 1: the previous solution (already in X).  chrono k >= 2: the
+// The initial guess of term t's next solve, in its X; returns whether there
+// is one.  chrono 1: the previous solution (already in X).  chrono k >= 2: the
 // polynomial through the last k solutions at their molecular-dynamics times,
 // evaluated at the current time (Lagrange form); the trajectory's solves come
 // at evenly spaced times, so this is the extrapolation x_n ~ 2 x_{n-1} -
 // x_{n-2} (k = 2), 3 x_{n-1} - 3 x_{n-2} + x_{n-3} (k = 3), ...  A solve at the
 // time of the previous one (the action at the end of the trajectory) starts
 // from the previous solution.
-static lqcd_status prepare_guess(lqcd_hmc_state *st, const lqcd_hmc_params *p, cudaStream_t s, int *guess)
+static lqcd_status prepare_guess(lqcd_hmc_state *st, PfTerm &t, const lqcd_hmc_params *p, cudaStream_t s,
+                                 int *guess)
 {
-    *guess = (p->chrono && st->have_guess) ? 1 : 0;
-    if (!*guess || p->chrono < 2 || st->n_hist < 2) return LQCD_OK;
-    const int latest = (st->head + CHRONO_MAX - 1) % CHRONO_MAX;
-    if (st->hist_t[latest] == st->md_time) return LQCD_OK;
+    *guess = (p->chrono && t.have_guess) ? 1 : 0;
+    if (!*guess || p->chrono < 2 || t.n_hist < 2) return LQCD_OK;
+    const int latest = (t.head + CHRONO_MAX - 1) % CHRONO_MAX;
+    if (t.hist_t[latest] == st->md_time) return LQCD_OK;
     int idx[CHRONO_MAX], m = 0;
     const int kmax = std::min(p->chrono, CHRONO_MAX);
-    for (int k = 0; k < st->n_hist && m < kmax; k++) {
-        int i = (st->head + CHRONO_MAX - 1 - k) % CHRONO_MAX;
+    for (int k = 0; k < t.n_hist && m < kmax; k++) {
+        int i = (t.head + CHRONO_MAX - 1 - k) % CHRONO_MAX;
         bool dup = false;
-        for (int j = 0; j < m; j++) dup = dup || st->hist_t[idx[j]] == st->hist_t[i];
+        for (int j = 0; j < m; j++) dup = dup || t.hist_t[idx[j]] == t.hist_t[i];
         if (!dup) idx[m++] = i;
     }
     if (m < 2) return LQCD_OK;
@@ -162,41 +213,37 @@ static lqcd_status prepare_guess(lqcd_hmc_state *st, const lqcd_hmc_params *p, c
     for (int a = 0; a < m; a++) {
         double l = 1.0;
         for (int b = 0; b < m; b++)
-            if (b != a)
-                l *= (st->md_time - st->hist_t[idx[b]]) / (st->hist_t[idx[a]] - st->hist_t[idx[b]]);
+            if (b != a) l *= (st->md_time - t.hist_t[idx[b]]) / (t.hist_t[idx[a]] - t.hist_t[idx[b]]);
         w[a] = l;
-        x[a] = (const double2 *)st->hist[idx[a]].f->data;
+        x[a] = (const double2 *)t.hist[idx[a]].f->data;
     }
-    size_t n = st->X.f->bytes / sizeof(double2);
-    combine_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((double2 *)st->X.f->data, x[0], x[1], x[2], x[3],
-                                                               w[0], w[1], w[2], w[3], m, n);
+    size_t n = t.X.f->bytes / sizeof(double2);
+    combine_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((double2 *)t.X.f->data, x[0], x[1], x[2], x[3], w[0],
+                                                               w[1], w[2], w[3], m, n);
     LQCD_LAUNCHED();
     return LQCD_OK;
 }
 
-// record a solve's solution for later guesses
-static lqcd_status record_solution(lqcd_hmc_state *st, const lqcd_hmc_params *p, bool ok, cudaStream_t s)
+// record a solve's outcome and solution for later guesses
+static lqcd_status record_solution(lqcd_hmc_state *st, PfTerm &t, const lqcd_hmc_params *p, lqcd_status rc,
+                                   cudaStream_t s)
 {
-    st->have_guess = ok;
+    const bool ok = rc == LQCD_OK || rc == LQCD_ENOCONV;
+    t.have_guess = ok;
+    t.last_ok = rc == LQCD_OK;
+    t.last_t = st->md_time;
     if (!ok || p->chrono < 2) return LQCD_OK;
-    lqcd_field *&slot = st->hist[st->head].f;
+    lqcd_field *&slot = t.hist[t.head].f;
     if (!slot) LQCD_TRY(lqcd_field_alloc(&st->U->lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &slot));
-    LQCD_CUDA(cudaMemcpyAsync(slot->data, st->X.f->data, st->X.f->bytes, cudaMemcpyDeviceToDevice, s));
-    st->hist_t[st->head] = st->md_time;
-    st->head = (st->head + 1) % CHRONO_MAX;
-    st->n_hist = std::min(st->n_hist + 1, CHRONO_MAX);
+    LQCD_CUDA(cudaMemcpyAsync(slot->data, t.X.f->data, t.X.f->bytes, cudaMemcpyDeviceToDevice, s));
+    t.hist_t[t.head] = st->md_time;
+    t.head = (t.head + 1) % CHRONO_MAX;
+    t.n_hist = std::min(t.n_hist + 1, CHRONO_MAX);
     return LQCD_OK;
 }
 
-static lqcd_status solve(lqcd_hmc_state *st, const lqcd_hmc_params *p, cudaStream_t s)
+static lqcd_status count_solve(lqcd_hmc_state *st, lqcd_status rc, const lqcd_cg_info &info)
 {
-    lqcd_cg_info info{};
-    lqcd_cg_params cg = p->cg;
-    LQCD_TRY(prepare_guess(st, p, s, &cg.guess));
-    lqcd_status rc = cg_solve_ws(st->ws, st->X.f, st->U, sloppy_links(st, p), st->phi.f, p->kappa, cg, &info, s);
-    st->last_ok = rc == LQCD_OK;
-    st->last_t = st->md_time;
-    LQCD_TRY(record_solution(st, p, rc == LQCD_OK || rc == LQCD_ENOCONV, s));
     st->cg_iters += info.iters;
     st->n_solves++;
     st->cg_res_max = std::max(st->cg_res_max, info.true_rel_res);
@@ -205,6 +252,18 @@ static lqcd_status solve(lqcd_hmc_state *st, const lqcd_hmc_params *p, cudaStrea
         return LQCD_OK; // the trajectory goes on; the failure is reported in its info
     }
     return rc;
+}
+
+// X_t = (Mhat(kappa)^dag Mhat(kappa))^-1 b with the term's chronological guess
+static lqcd_status solve(lqcd_hmc_state *st, PfTerm &t, const lqcd_hmc_params *p, double kappa,
+                         const lqcd_field *b, cudaStream_t s)
+{
+    lqcd_cg_info info{};
+    lqcd_cg_params cg = p->cg;
+    LQCD_TRY(prepare_guess(st, t, p, s, &cg.guess));
+    lqcd_status rc = cg_solve_ws(st->ws, t.X.f, st->U, sloppy_links(st, p), b, kappa, cg, &info, s);
+    LQCD_TRY(record_solution(st, t, p, rc, s));
+    return count_solve(st, rc, info);
 }
 
 static lqcd_status ensure_f32_temps(lqcd_hmc_state *st)
@@ -218,26 +277,75 @@ static lqcd_status ensure_f32_temps(lqcd_hmc_state *st)
     return LQCD_OK;
 }
 
-// P <- P - c F(U)
-static lqcd_status kick(lqcd_hmc_state *st, const lqcd_hmc_params *p, double c, cudaStream_t s)
+// P <- P - c F with F the force of -2 Re[Y^dag dMhat(kappa) X] (Y = Mhat X if Y is NULL)
+static lqcd_status fermion_force(lqcd_hmc_state *st, const lqcd_hmc_params *p, const lqcd_field *X,
+                                 const lqcd_field *Y, double kappa, double c, cudaStream_t s)
 {
-    LQCD_TRY(gauge_force_dev(st->P.f, st->U, st->Uf.f, p->beta, c, p->force_prec, s));
-    if (p->n_flavors == 2) {
-        LQCD_TRY(solve(st, p, s));
-        if (p->force_prec == LQCD_F32) {
-            LQCD_TRY(ensure_f32_temps(st));
-            LQCD_TRY(fermion_force_dev(st->P.f, st->U, st->Uf.f, st->X.f, p->kappa, c, st->Ao32.f, st->Ye32.f,
-                                       st->Bo32.f, st->X32.f, s));
+    if (p->force_prec == LQCD_F32) {
+        LQCD_TRY(ensure_f32_temps(st));
+        return fermion_force_dev(st->P.f, st->U, st->Uf.f, X, kappa, c, st->Ao32.f, st->Ye32.f, st->Bo32.f,
+                                 st->X32.f, s, Y);
+    }
+    return fermion_force_dev(st->P.f, st->U, nullptr, X, kappa, c, st->Ao.f, st->Ye.f, st->Bo.f, nullptr, s, Y);
+}
+
+// the ratio action's right-hand side chi = W^dag phi_r in FP64 (exact: the
+// action) or in the precision of the forces (fast: a force evaluation)
+static lqcd_status ratio_rhs(lqcd_hmc_state *st, const lqcd_hmc_params *p, bool exact, cudaStream_t s)
+{
+    PfTerm &t = st->pf[PF_MAIN];
+    if (exact || p->force_prec != LQCD_F32)
+        return mhat_apply(t.chi.f, st->U, t.phi.f, p->hasenbusch_kappa, 1, st->Ao.f, nullptr, s);
+    LQCD_TRY(ensure_f32_temps(st));
+    LQCD_TRY(lqcd_field_copy(st->X32.f, t.phi.f, s));
+    LQCD_TRY(mhat_apply(st->Ye32.f, st->Uf.f, st->X32.f, p->hasenbusch_kappa, 1, st->Ao32.f, nullptr, s));
+    return lqcd_field_copy(t.chi.f, st->Ye32.f, s);
+}
+
+// P <- P - c F of the given force terms at the current links
+static lqcd_status apply_forces(lqcd_hmc_state *st, const lqcd_hmc_params *p, int terms, double c, cudaStream_t s)
+{
+    if (terms & TERM_GAUGE) LQCD_TRY(gauge_force_dev(st->P.f, st->U, st->Uf.f, p->beta, c, p->force_prec, s));
+    if (p->n_flavors != 2) return LQCD_OK;
+    if (terms & TERM_FERMION) {
+        PfTerm &t = st->pf[PF_MAIN];
+        if (!hasenbusch(p)) {
+            LQCD_TRY(solve(st, t, p, p->kappa, t.phi.f, s));
+            LQCD_TRY(fermion_force(st, p, t.X.f, nullptr, p->kappa, c, s));
         } else {
-            LQCD_TRY(fermion_force_dev(st->P.f, st->U, nullptr, st->X.f, p->kappa, c, st->Ao.f, st->Ye.f, st->Bo.f,
-                                       nullptr, s));
+            LQCD_TRY(ratio_rhs(st, p, false, s));
+            LQCD_TRY(solve(st, t, p, p->kappa, t.chi.f, s));
+            LQCD_TRY(fermion_force(st, p, t.X.f, nullptr, p->kappa, c, s));
+            LQCD_TRY(fermion_force(st, p, t.X.f, t.phi.f, p->hasenbusch_kappa, -c, s));
         }
+    }
+    if ((terms & TERM_HEAVY) && hasenbusch(p)) {
+        PfTerm &t = st->pf[PF_HEAVY];
+        LQCD_TRY(solve(st, t, p, p->hasenbusch_kappa, t.phi.f, s));
+        LQCD_TRY(fermion_force(st, p, t.X.f, nullptr, p->hasenbusch_kappa, c, s));
+    }
+    return LQCD_OK;
+}
+
+// Kicks are queued per level and applied when the links are about to change
+// (or at the end), so kicks of adjacent steps at the same links merge into
+// one force evaluation with the summed coefficient.
+static void kick(lqcd_hmc_state *st, int level, double c) { st->pending[level] += c; }
+
+static lqcd_status flush_kicks(lqcd_hmc_state *st, const lqcd_hmc_params *p, cudaStream_t s)
+{
+    for (int l = 0; l < n_levels(p); l++) {
+        if (st->pending[l] == 0.0) continue;
+        const double c = st->pending[l];
+        st->pending[l] = 0.0;
+        LQCD_TRY(apply_forces(st, p, level_terms(p, l), c, s));
     }
     return LQCD_OK;
 }
 
 static lqcd_status drift(lqcd_hmc_state *st, const lqcd_hmc_params *p, double c, cudaStream_t s)
 {
+    LQCD_TRY(flush_kicks(st, p, s));
     bool fast = p->force_prec == LQCD_F32;
     st->md_time += c;
     return link_update_dev(st->U, st->P.f, c, sloppy_links(st, p), fast ? st->Uf.f : nullptr, fast, s,
@@ -261,68 +369,128 @@ static double hamiltonian_from(const lqcd_hmc_state *st, const lqcd_hmc_params *
 
 static lqcd_status refresh(lqcd_hmc_state *st, const lqcd_hmc_params *p, double *H0, cudaStream_t s)
 {
-    st->have_guess = false; // a new phi: the last solution is no guess for it
-    st->n_hist = 0;
+    for (PfTerm &t : st->pf) t.reset(); // new pseudofermions: old solutions are no guesses
     st->md_time = 0;
+    st->pending[0] = st->pending[1] = 0;
     LQCD_TRY(ensure_sloppy(st, p, s));
     LQCD_TRY(momentum_refresh_dev(st->P.f, st->seed, st->chain, st->traj, s));
     double *d = (double *)st->scal.p;
     LQCD_TRY(hamiltonian_parts(st, s));
+    double h[4] = {0, 0, 0, 0};
     if (p->n_flavors == 2) {
-        LQCD_TRY(eta_refresh_dev(st->eta.f, st->seed, st->chain, st->traj, s));
-        LQCD_TRY(mhat_apply(st->phi.f, st->U, st->eta.f, p->kappa, 1, st->Ao.f, nullptr, s));
+        PfTerm &t = st->pf[PF_MAIN];
+        LQCD_TRY(eta_refresh_dev(st->eta.f, st->seed, st->chain, st->traj, s, 2u));
+        if (!hasenbusch(p)) {
+            LQCD_TRY(mhat_apply(t.phi.f, st->U, st->eta.f, p->kappa, 1, st->Ao.f, nullptr, s));
+        } else {
+            // phi_h = W^dag eta_h;  phi_r = W (W^dag W)^-1 Mhat^dag eta
+            LQCD_TRY(ensure_hasenbusch(st));
+            const double kh = p->hasenbusch_kappa;
+            LQCD_TRY(eta_refresh_dev(st->eta_h.f, st->seed, st->chain, st->traj, s, 4u));
+            LQCD_TRY(mhat_apply(st->pf[PF_HEAVY].phi.f, st->U, st->eta_h.f, kh, 1, st->Ao.f, nullptr, s));
+            LQCD_TRY(mhat_apply(t.chi.f, st->U, st->eta.f, p->kappa, 1, st->Ao.f, nullptr, s));
+            lqcd_cg_info info{};
+            lqcd_cg_params cg = p->cg;
+            cg.guess = 0;
+            lqcd_status rc = cg_solve_ws(st->ws, st->z.f, st->U, sloppy_links(st, p), t.chi.f, kh, cg, &info, s);
+            LQCD_TRY(count_solve(st, rc, info));
+            LQCD_TRY(mhat_apply(t.phi.f, st->U, st->z.f, kh, 0, st->Ao.f, nullptr, s));
+            LQCD_TRY(spinor_dot_dev(st->eta_h.f, st->eta_h.f, d + 3, st->part, s));
+        }
         LQCD_TRY(spinor_dot_dev(st->eta.f, st->eta.f, d + 2, st->part, s));
     }
-    double h[3] = {0, 0, 0};
-    LQCD_TRY(read_scalars(d, h, 3, s));
+    LQCD_TRY(read_scalars(d, h, hasenbusch(p) ? 4 : 3, s));
+    h[2] += h[3];
     st->H0 = hamiltonian_from(st, p, h);
     if (H0) *H0 = st->H0;
     return LQCD_OK;
 }
 
+// the term's solution is reusable for the action at the current links: a
+// chronological guess would start from it and stop at once
+static bool reusable(const lqcd_hmc_state *st, const PfTerm &t, const lqcd_hmc_params *p)
+{
+    return p->chrono && t.have_guess && t.last_ok && t.last_t == st->md_time;
+}
+
 // H of the current fields.  reuse_last (inside a trajectory, right after the
-// last kick): the last solve was of the same system and converged, and with a
-// chronological guess a new solve would start from its solution and stop at
-// once, so its solution is used as it is (counted as a solve of 0 iterations).
+// last kicks): a term whose last solve was of the same system and converged
+// uses that solution as it is (counted as a solve of 0 iterations).
 static lqcd_status hamiltonian(lqcd_hmc_state *st, const lqcd_hmc_params *p, double *H, cudaStream_t s,
                                bool reuse_last = false)
 {
     double *d = (double *)st->scal.p;
     LQCD_TRY(hamiltonian_parts(st, s));
+    double h[4] = {0, 0, 0, 0};
     if (p->n_flavors == 2) {
-        if (reuse_last && p->chrono && st->have_guess && st->last_ok && st->last_t == st->md_time)
-            st->n_solves++;
-        else
-            LQCD_TRY(solve(st, p, s));
-        LQCD_TRY(spinor_dot_dev(st->phi.f, st->X.f, d + 2, st->part, s));
+        PfTerm &t = st->pf[PF_MAIN];
+        if (!hasenbusch(p)) {
+            if (reuse_last && reusable(st, t, p))
+                st->n_solves++;
+            else
+                LQCD_TRY(solve(st, t, p, p->kappa, t.phi.f, s));
+            LQCD_TRY(spinor_dot_dev(t.phi.f, t.X.f, d + 2, st->part, s));
+        } else {
+            // the ratio action needs chi in FP64; the forces may have used FP32
+            const bool exact_chi = p->force_prec != LQCD_F32;
+            if (reuse_last && exact_chi && reusable(st, t, p)) {
+                st->n_solves++;
+            } else {
+                LQCD_TRY(ratio_rhs(st, p, true, s));
+                LQCD_TRY(solve(st, t, p, p->kappa, t.chi.f, s));
+            }
+            LQCD_TRY(spinor_dot_dev(t.chi.f, t.X.f, d + 2, st->part, s));
+            PfTerm &th = st->pf[PF_HEAVY];
+            if (reuse_last && reusable(st, th, p))
+                st->n_solves++;
+            else
+                LQCD_TRY(solve(st, th, p, p->hasenbusch_kappa, th.phi.f, s));
+            LQCD_TRY(spinor_dot_dev(th.phi.f, th.X.f, d + 3, st->part, s));
+        }
     }
-    double h[3] = {0, 0, 0};
-    LQCD_TRY(read_scalars(d, h, 3, s));
+    LQCD_TRY(read_scalars(d, h, hasenbusch(p) ? 4 : 3, s));
+    h[2] += h[3];
     *H = hamiltonian_from(st, p, h);
     return LQCD_OK;
 }
 
-static lqcd_status integrate(lqcd_hmc_state *st, const lqcd_hmc_params *p, cudaStream_t s)
+static lqcd_status integrate_level(lqcd_hmc_state *st, const lqcd_hmc_params *p, int level, double t, int n,
+                                   cudaStream_t s);
+
+// a drift of a level: the next level's integration, or the link update
+static lqcd_status inner(lqcd_hmc_state *st, const lqcd_hmc_params *p, int level, double t, cudaStream_t s)
 {
-    double dt = p->tau / p->nsteps;
-    int n = p->nsteps;
-    if (p->integrator == LQCD_LEAPFROG) {
-        LQCD_TRY(kick(st, p, 0.5 * dt, s));
-        for (int k = 0; k < n; k++) {
-            LQCD_TRY(drift(st, p, dt, s));
-            LQCD_TRY(kick(st, p, k == n - 1 ? 0.5 * dt : dt, s));
-        }
-    } else {
-        const double lam = OMELYAN_LAMBDA;
-        LQCD_TRY(kick(st, p, lam * dt, s));
-        for (int k = 0; k < n; k++) {
-            LQCD_TRY(drift(st, p, 0.5 * dt, s));
-            LQCD_TRY(kick(st, p, (1.0 - 2.0 * lam) * dt, s));
-            LQCD_TRY(drift(st, p, 0.5 * dt, s));
-            LQCD_TRY(kick(st, p, k == n - 1 ? lam * dt : 2.0 * lam * dt, s));
+    if (level + 1 < n_levels(p)) return integrate_level(st, p, level + 1, t, p->gauge_substeps, s);
+    return drift(st, p, t, s);
+}
+
+// n steps of the scheme over time t on one level (Sexton-Weingarten nesting:
+// the inner level integrates each drift of the outer one)
+static lqcd_status integrate_level(lqcd_hmc_state *st, const lqcd_hmc_params *p, int level, double t, int n,
+                                   cudaStream_t s)
+{
+    const double h = t / n;
+    for (int k = 0; k < n; k++) {
+        if (p->integrator == LQCD_LEAPFROG) {
+            kick(st, level, 0.5 * h);
+            LQCD_TRY(inner(st, p, level, h, s));
+            kick(st, level, 0.5 * h);
+        } else {
+            const double lam = OMELYAN_LAMBDA;
+            kick(st, level, lam * h);
+            LQCD_TRY(inner(st, p, level, 0.5 * h, s));
+            kick(st, level, (1.0 - 2.0 * lam) * h);
+            LQCD_TRY(inner(st, p, level, 0.5 * h, s));
+            kick(st, level, lam * h);
         }
     }
     return LQCD_OK;
+}
+
+static lqcd_status integrate(lqcd_hmc_state *st, const lqcd_hmc_params *p, double t, int n, cudaStream_t s)
+{
+    LQCD_TRY(integrate_level(st, p, 0, t, n, s));
+    return flush_kicks(st, p, s);
 }
 
 static void reset_stats(lqcd_hmc_state *st)
@@ -348,8 +516,8 @@ lqcd_status lqcd_hmc_state_create(lqcd_field *U, uint32_t seed, uint32_t chain, 
     lqcd_status rc = LQCD_OK;
     if (rc == LQCD_OK) rc = lqcd_field_alloc(&lat, LQCD_MOMENTUM, LQCD_F64, 0, &st->P.f);
     if (rc == LQCD_OK) rc = lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->eta.f);
-    if (rc == LQCD_OK) rc = lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->phi.f);
-    if (rc == LQCD_OK) rc = lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->X.f);
+    if (rc == LQCD_OK) rc = lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->pf[PF_MAIN].phi.f);
+    if (rc == LQCD_OK) rc = lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->pf[PF_MAIN].X.f);
     if (rc == LQCD_OK) rc = lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F64, 0, &st->Ao.f);
     if (rc == LQCD_OK) rc = lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->Ye.f);
     if (rc == LQCD_OK) rc = lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F64, 0, &st->Bo.f);
@@ -375,7 +543,7 @@ lqcd_status lqcd_hmc_state_fields(lqcd_hmc_state *s, lqcd_field **U, lqcd_field 
     LQCD_REQUIRE(s, "hmc_state_fields: NULL state");
     if (U) *U = s->U;
     if (P) *P = s->P.f;
-    if (phi) *phi = s->phi.f;
+    if (phi) *phi = s->pf[PF_MAIN].phi.f;
     return LQCD_OK;
 }
 
@@ -398,6 +566,7 @@ lqcd_status lqcd_hmc_hamiltonian(lqcd_hmc_state *s, const lqcd_hmc_params *p, do
 {
     LQCD_REQUIRE(s && H, "hmc_hamiltonian: NULL argument");
     LQCD_TRY(check_params(p));
+    LQCD_REQUIRE(!hasenbusch(p) || s->eta_h.f, "hmc_hamiltonian: no Hasenbusch refresh has been done");
     LQCD_TRY(ensure_sloppy(s, p, (cudaStream_t)stream));
     return hamiltonian(s, p, H, (cudaStream_t)stream);
 }
@@ -406,22 +575,11 @@ lqcd_status lqcd_md_step(lqcd_hmc_state *s, const lqcd_hmc_params *p, void *stre
 {
     LQCD_REQUIRE(s, "md_step: NULL state");
     LQCD_TRY(check_params(p));
+    LQCD_REQUIRE(!hasenbusch(p) || s->eta_h.f, "md_step: no Hasenbusch refresh has been done");
     cudaStream_t st = (cudaStream_t)stream;
     LQCD_TRY(ensure_sloppy(s, p, st));
-    double dt = p->tau / p->nsteps;
-    if (p->integrator == LQCD_LEAPFROG) {
-        LQCD_TRY(kick(s, p, 0.5 * dt, st));
-        LQCD_TRY(drift(s, p, dt, st));
-        LQCD_TRY(kick(s, p, 0.5 * dt, st));
-    } else {
-        const double lam = OMELYAN_LAMBDA;
-        LQCD_TRY(kick(s, p, lam * dt, st));
-        LQCD_TRY(drift(s, p, 0.5 * dt, st));
-        LQCD_TRY(kick(s, p, (1.0 - 2.0 * lam) * dt, st));
-        LQCD_TRY(drift(s, p, 0.5 * dt, st));
-        LQCD_TRY(kick(s, p, lam * dt, st));
-    }
-    return LQCD_OK;
+    s->pending[0] = s->pending[1] = 0;
+    return integrate(s, p, p->tau / p->nsteps, 1, st);
 }
 
 lqcd_status lqcd_hmc_trajectory(lqcd_hmc_state *s, const lqcd_hmc_params *p, lqcd_traj_info *info, void *stream)
@@ -434,24 +592,24 @@ lqcd_status lqcd_hmc_trajectory(lqcd_hmc_state *s, const lqcd_hmc_params *p, lqc
     LQCD_CUDA(cudaMemcpyAsync(s->Ubak.f->data, s->U->data, s->U->bytes, cudaMemcpyDeviceToDevice, st));
     double H0 = 0, H1 = 0;
     lqcd_status rc = refresh(s, p, &H0, st);
-    if (rc == LQCD_OK) rc = integrate(s, p, st);
+    if (rc == LQCD_OK) rc = integrate(s, p, p->tau, p->nsteps, st);
     if (rc == LQCD_OK) rc = hamiltonian(s, p, &H1, st, true);
     double dH = H1 - H0;
     double *d = (double *)s->scal.p;
-    metropolis_uniform_kernel<<<1, 1, 0, st>>>(d + 3, s->seed, s->chain, s->traj);
+    metropolis_uniform_kernel<<<1, 1, 0, st>>>(d + 4, s->seed, s->chain, s->traj);
     LQCD_LAUNCHED();
     double u = 0;
-    LQCD_TRY(read_scalars(d + 3, &u, 1, st));
+    LQCD_TRY(read_scalars(d + 4, &u, 1, st));
     bool accept = rc == LQCD_OK && std::isfinite(dH) && (!p->metropolis || u < std::exp(-dH));
     if (!accept) LQCD_CUDA(cudaMemcpyAsync(s->U->data, s->Ubak.f->data, s->U->bytes, cudaMemcpyDeviceToDevice, st));
     double maxdev = 0;
     if (p->reunitarize) {
-        LQCD_TRY(reunitarize_dev(s->U, d + 4, s->part, st));
-        LQCD_TRY(read_scalars(d + 4, &maxdev, 1, st));
+        LQCD_TRY(reunitarize_dev(s->U, d + 5, s->part, st));
+        LQCD_TRY(read_scalars(d + 5, &maxdev, 1, st));
     }
-    LQCD_TRY(plaquette_sum(s->U, d + 5, s->part, st));
+    LQCD_TRY(plaquette_sum(s->U, d + 6, s->part, st));
     double plaq_sum = 0;
-    LQCD_TRY(read_scalars(d + 5, &plaq_sum, 1, st));
+    LQCD_TRY(read_scalars(d + 6, &plaq_sum, 1, st));
     if (info) {
         info->dH = dH;
         info->H0 = H0;
@@ -495,6 +653,8 @@ static lqcd_status check_batch_params(const lqcd_batch *B, const lqcd_hmc_params
         LQCD_TRY(check_params(&p[i]));
         LQCD_REQUIRE(p[i].n_flavors == 2, "batch: every chain needs two Wilson flavours");
         LQCD_REQUIRE(p[i].cg.sloppy != LQCD_F64, "batch: the batched solver is the mixed-precision one");
+        LQCD_REQUIRE(!hasenbusch(&p[i]) && n_levels(&p[i]) == 1,
+                     "batch: chains run one pseudofermion on one time scale (no hasenbusch_kappa, gauge_substeps)");
         LQCD_REQUIRE(p[i].integrator == p[0].integrator && p[i].nsteps == p[0].nsteps && p[i].tau == p[0].tau &&
                          p[i].cg.sloppy == p[0].cg.sloppy && p[i].force_prec == p[0].force_prec,
                      "batch: chains must share integrator, nsteps, tau, solver precision and force precision");
@@ -512,16 +672,17 @@ static lqcd_status batch_solve(lqcd_batch *B, const lqcd_hmc_params *p, cudaStre
     std::vector<bool> reused(n, false);
     for (size_t i = 0; i < n; i++) {
         lqcd_hmc_state *st = B->chains[i];
-        if (reuse_last && p[i].chrono && st->have_guess && st->last_ok && st->last_t == st->md_time) {
+        PfTerm &t = st->pf[PF_MAIN];
+        if (reuse_last && reusable(st, t, &p[i])) {
             reused[i] = true;
             st->n_solves++;
             continue;
         }
         CgRun &r = runs[i];
-        r.ws = &st->ws, r.x = st->X.f, r.U = st->U, r.Us = sloppy_links(st, &p[i]), r.b = st->phi.f;
+        r.ws = &st->ws, r.x = t.X.f, r.U = st->U, r.Us = sloppy_links(st, &p[i]), r.b = t.phi.f;
         r.kappa = p[i].kappa;
         r.prm = p[i].cg;
-        LQCD_TRY(prepare_guess(st, &p[i], s, &r.prm.guess));
+        LQCD_TRY(prepare_guess(st, t, &p[i], s, &r.prm.guess));
         LQCD_TRY(st->ws.ensure(st->U->lat, r.prm.sloppy, s));
         r.start(s, (CgScalars *)B->scal.p + i);
         ptrs.push_back(&r);
@@ -531,16 +692,8 @@ static lqcd_status batch_solve(lqcd_batch *B, const lqcd_hmc_params *p, cudaStre
         if (reused[i]) continue;
         lqcd_hmc_state *st = B->chains[i];
         const CgRun &r = runs[i];
-        st->last_ok = r.status == LQCD_OK;
-        st->last_t = st->md_time;
-        st->cg_iters += r.inf.iters;
-        st->n_solves++;
-        st->cg_res_max = std::max(st->cg_res_max, r.inf.true_rel_res);
-        LQCD_TRY(record_solution(st, &p[i], r.status == LQCD_OK || r.status == LQCD_ENOCONV, s));
-        if (r.status == LQCD_ENOCONV)
-            st->cg_failures++;
-        else if (r.status != LQCD_OK)
-            return r.status;
+        LQCD_TRY(record_solution(st, st->pf[PF_MAIN], &p[i], r.status, s));
+        LQCD_TRY(count_solve(st, r.status, r.inf));
     }
     return LQCD_OK;
 }
@@ -555,14 +708,7 @@ static lqcd_status batch_kick(lqcd_batch *B, const lqcd_hmc_params *p, double c,
     LQCD_TRY(batch_solve(B, p, s));
     for (size_t i = 0; i < n; i++) {
         lqcd_hmc_state *st = B->chains[i];
-        if (p[i].force_prec == LQCD_F32) {
-            LQCD_TRY(ensure_f32_temps(st));
-            LQCD_TRY(fermion_force_dev(st->P.f, st->U, st->Uf.f, st->X.f, p[i].kappa, c, st->Ao32.f, st->Ye32.f,
-                                       st->Bo32.f, st->X32.f, s));
-        } else {
-            LQCD_TRY(fermion_force_dev(st->P.f, st->U, nullptr, st->X.f, p[i].kappa, c, st->Ao.f, st->Ye.f,
-                                       st->Bo.f, nullptr, s));
-        }
+        LQCD_TRY(fermion_force(st, &p[i], st->pf[PF_MAIN].X.f, nullptr, p[i].kappa, c, s));
     }
     return LQCD_OK;
 }
@@ -651,26 +797,26 @@ lqcd_status lqcd_batch_trajectory(lqcd_batch *B, const lqcd_hmc_params *params, 
         double h[3] = {0, 0, 0};
         if (rc == LQCD_OK) {
             // kinetic and plaquette sums were taken before the batched solve; add phi^dag X
-            LQCD_TRY(spinor_dot_dev(st->phi.f, st->X.f, d + 2, st->part, s));
+            LQCD_TRY(spinor_dot_dev(st->pf[PF_MAIN].phi.f, st->pf[PF_MAIN].X.f, d + 2, st->part, s));
             LQCD_TRY(read_scalars(d, h, 3, s));
             H1[i] = hamiltonian_from(st, p, h);
         }
         double dH = H1[i] - H0[i];
-        metropolis_uniform_kernel<<<1, 1, 0, s>>>(d + 3, st->seed, st->chain, st->traj);
+        metropolis_uniform_kernel<<<1, 1, 0, s>>>(d + 4, st->seed, st->chain, st->traj);
         LQCD_LAUNCHED();
         double u = 0;
-        LQCD_TRY(read_scalars(d + 3, &u, 1, s));
+        LQCD_TRY(read_scalars(d + 4, &u, 1, s));
         bool accept = rc == LQCD_OK && std::isfinite(dH) && (!p->metropolis || u < std::exp(-dH));
         if (!accept)
             LQCD_CUDA(cudaMemcpyAsync(st->U->data, st->Ubak.f->data, st->U->bytes, cudaMemcpyDeviceToDevice, s));
         double maxdev = 0;
         if (p->reunitarize) {
-            LQCD_TRY(reunitarize_dev(st->U, d + 4, st->part, s));
-            LQCD_TRY(read_scalars(d + 4, &maxdev, 1, s));
+            LQCD_TRY(reunitarize_dev(st->U, d + 5, st->part, s));
+            LQCD_TRY(read_scalars(d + 5, &maxdev, 1, s));
         }
-        LQCD_TRY(plaquette_sum(st->U, d + 5, st->part, s));
+        LQCD_TRY(plaquette_sum(st->U, d + 6, st->part, s));
         double plaq_sum = 0;
-        LQCD_TRY(read_scalars(d + 5, &plaq_sum, 1, s));
+        LQCD_TRY(read_scalars(d + 6, &plaq_sum, 1, s));
         if (info) {
             lqcd_traj_info &f = info[i];
             f.dH = dH;

@@ -58,7 +58,8 @@ class HmcParams(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("kappa", ctypes.c_double), ("tau", ctypes.c_double),
                 ("nsteps", ctypes.c_int), ("integrator", ctypes.c_int), ("n_flavors", ctypes.c_int),
                 ("cg", CgParams), ("reunitarize", ctypes.c_int), ("metropolis", ctypes.c_int),
-                ("chrono", ctypes.c_int), ("force_prec", ctypes.c_int)]
+                ("chrono", ctypes.c_int), ("force_prec", ctypes.c_int), ("hasenbusch_kappa", ctypes.c_double),
+                ("gauge_substeps", ctypes.c_int), ("heavy_inner", ctypes.c_int)]
 
 
 class ServiceParams(ctypes.Structure):
@@ -439,9 +440,11 @@ def spinor_dot(a: Field, b: Field, stream=None) -> float:
 # ---------------------------------------------------------------- HMC
 
 def hmc_params(beta, kappa, tau=1.0, nsteps=10, integrator=LEAPFROG, n_flavors=2, cg=None, reunitarize=True,
-               metropolis=True, force_prec=F64, chrono=False) -> HmcParams:
+               metropolis=True, force_prec=F64, chrono=False, hasenbusch_kappa=0.0, gauge_substeps=0,
+               heavy_inner=False) -> HmcParams:
     return HmcParams(beta, kappa, tau, nsteps, integrator, n_flavors, cg or cg_params(), int(reunitarize),
-                     int(metropolis), int(chrono), int(force_prec))
+                     int(metropolis), int(chrono), int(force_prec), float(hasenbusch_kappa), int(gauge_substeps),
+                     int(heavy_inner))
 
 
 class HmcState:
