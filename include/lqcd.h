@@ -124,6 +124,8 @@ uint64_t lqcd_launch_count(void);
  * link, input, output and fused-epilogue field element counted once; 0 for
  * the other classes).  Output pointers may be NULL. */
 lqcd_status lqcd_kernel_timers(int enable);
+/* The same with one class timed (the others run without events). */
+lqcd_status lqcd_kernel_timers_only(const char *kernel_class);
 lqcd_status lqcd_kernel_timer_read(const char *kernel_class, double *total_ms, uint64_t *launches,
                                    double *algorithmic_bytes);
 
@@ -208,6 +210,19 @@ lqcd_status lqcd_eta_refresh(lqcd_field *eta, uint32_t seed, uint32_t chain, uin
  * spinors of precision q (q in F32, F16N, BF16; FP32 arithmetic). */
 lqcd_status lqcd_dslash(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int dagger, void *stream);
 
+/* The FP16+norm hopping term has a second form for lattices with Lx/2 * Ly a
+ * multiple of 128: each block of 128 output sites stages its +-z and +-t
+ * neighbour spinors and the links it needs from them in shared memory with
+ * bulk asynchronous copies (the TMA engine of sm_90+) before computing;
+ * results are bitwise those of the first form.  It is on by default;
+ * lqcd_dslash_staging(0) switches it off, (1) on, (-1) queries; returns the
+ * previous setting (process-wide).  A block's wait for its copies is bounded:
+ * if one ever gives up, lqcd_dslash_check (which synchronises stream) returns
+ * LQCD_ETIMEOUT once and the results since the last check are invalid; every
+ * CG solve makes that check before it returns. */
+int lqcd_dslash_staging(int enable);
+lqcd_status lqcd_dslash_check(void *stream);
+
 /* out_e = Mhat in_e = in_e - kappa^2 Deo Doe in_e (dagger: Mhat^dag).  EVEN
  * spinors, precision rules as lqcd_dslash.  Uses one temporary odd spinor. */
 lqcd_status lqcd_mhat(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, double kappa, int dagger,
@@ -280,6 +295,15 @@ lqcd_status lqcd_fermion_force_ex(lqcd_field *P, const lqcd_field *U, const lqcd
  * (Morningstar & Peardon 2004).  If U_sloppy is not NULL it receives the
  * 12-real copy of the new links in its precision. */
 lqcd_status lqcd_link_update(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *U_sloppy, void *stream);
+
+/* The same with the arithmetic chosen: LQCD_F64 as lqcd_link_update;
+ * LQCD_F32 (the FP32 molecular dynamics of lqcd_hmc_params.force_prec): the
+ * exponential by Cayley-Hamilton in FP32, re-unitarized (Gram-Schmidt) and
+ * multiplied onto the FP64 links in float-float arithmetic, so the new links
+ * differ from exp(i c P) U by the FP32 exponential's error (~1e-7) but stay in
+ * SU(3) to ~1e-14. */
+lqcd_status lqcd_link_update_ex(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *U_sloppy, lqcd_prec arith,
+                                void *stream);
 
 /* Reunitarization (paper Sec. 1): rows 0, 1 by Gram-Schmidt, row 2 =
  * conj(row0 x row1).  max_dev_out (host, may be NULL) receives the maximum

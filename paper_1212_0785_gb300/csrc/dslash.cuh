@@ -27,7 +27,11 @@ struct CgScalars {
 
 enum { PAUSE_NONE = 0, PAUSE_CONVERGED = 1, PAUSE_RELIABLE = 2, PAUSE_MAXITER = 3, PAUSE_NONFINITE = 4 };
 
-constexpr int DS_BLOCK = 128;
+#ifndef LQCD_DS_BLOCK
+#define LQCD_DS_BLOCK 128
+#endif
+// threads per block of the hopping-term kernels (one output site each)
+constexpr int DS_BLOCK = LQCD_DS_BLOCK;
 
 inline int dslash_blocks(int Vh) { return nblocks_for(Vh, DS_BLOCK); }
 
@@ -47,5 +51,17 @@ lqcd_status dslash_xpay(lqcd_field *out, const lqcd_field *U, const lqcd_field *
 lqcd_status dslash_cg(const lqcd_field *U, const lqcd_field *in, int dagger, const lqcd_field *t, double b,
                       lqcd_field *xs, lqcd_field *r, const lqcd_field *p, double *partials, const CgScalars *sc,
                       cudaStream_t s);
+
+// LQCD_ETIMEOUT (and the flag cleared) if a staged hopping-term block gave up
+// waiting for its operands since the last check; synchronises s
+lqcd_status dslash_staging_check(cudaStream_t s);
+// switch the staged FP16+norm kernels on (1) or off (0), or query (< 0);
+// returns the previous setting
+int dslash_staging_set(int enable);
+
+// out = D in, or x + b D in if x is given, with float-float fields and links
+// (precision code 4; dslash_df.cu)
+lqcd_status dslash_df_launch(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int dagger,
+                             const lqcd_field *x, double b, const int *skip, cudaStream_t s);
 
 } // namespace lqcd

@@ -50,6 +50,17 @@ __device__ __forceinline__ void hop_dir(Sp<R> &acc, const SpinorRef<SP> &in, con
     }
 }
 
+// One hop from values already loaded: the stored spinor psi with its
+// per-site scale sc (norm, or 1), the link u (U_mu(x) forward, U_mu(x - mu)
+// backward), the boundary sign flip.  The same arithmetic as hop_dir.
+template <int MU, int S, bool FWD, typename R>
+__device__ __forceinline__ void hop_values(Sp<R> &acc, const Sp<R> &psi, R sc, const M3<R> &u, bool flip)
+{
+    Hs<R> uh = FWD ? mul_link(u, project<MU, S>(psi)) : mul_link_dag(u, project<MU, S>(psi));
+    scale_hs(uh, flip ? -sc : sc);
+    accumulate<MU, S>(acc, uh);
+}
+
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
 __device__ __forceinline__ Sp<R> dslash_site(const SpinorRef<SP> &in, const GaugeRef<GP> &U, const Geo &g, int cb,
                                              int out_par)

@@ -39,7 +39,7 @@ lqcd_status cuda_fail(cudaError_t e, const char *what, const char *file, int lin
 static const char *k_class_names[K_NCLASS] = {"dslash_f64",  "dslash_f32",  "dslash_f16n",   "dslash_bf16",
                                               "dslash_df64", "gauge_force", "fermion_force", "link_update"};
 static std::mutex g_timer_mu;
-static std::atomic<bool> g_timers_on{false};
+static std::atomic<uint32_t> g_timer_mask{0}; // bit k: class k is timed
 static std::vector<cudaEvent_t> g_event_pool;
 struct PendingTiming {
     int cls;
@@ -68,7 +68,7 @@ static cudaEvent_t pool_event()
 
 KernelTimer::KernelTimer(int c, cudaStream_t st, double nbytes) : cls(c), s(st), bytes(nbytes)
 {
-    if (!g_timers_on.load(std::memory_order_relaxed)) return;
+    if (!((g_timer_mask.load(std::memory_order_relaxed) >> c) & 1u)) return;
     std::lock_guard<std::mutex> lk(g_timer_mu);
     a = pool_event();
     b = pool_event();
@@ -628,12 +628,13 @@ __device__ __forceinline__ M3<Df> reunit_rows_df(const M3<float> &e)
 }
 
 // U <- exp(i c P) U.  FAST (the mixed-precision trajectory): the exponential
-// by Cayley-Hamilton in FP32, re-unitarized and multiplied onto the FP64 links
-// in float-float arithmetic (~48 bits, on the FP32 pipes), so that the FP64
-// links stay in SU(3) to ~1e-14 per update; otherwise everything in FP64.  The
-// new links are also written to the 12-real copies Us (solver precision) and
-// Uf (FP32) and to the float-float copy Udf (the solver's accurate residual)
-// when those are given.
+// by Cayley-Hamilton in FP32, re-unitarized and multiplied onto the links in
+// float-float arithmetic (~48 bits, on the FP32 pipes), so that the FP64 links
+// stay in SU(3) to ~1e-14 per update; otherwise everything in FP64.  The new
+// links are also written to the 12-real copies Us (solver precision) and Uf
+// (FP32) and to the float-float copy Udf (the solver's accurate residual) when
+// those are given; a given Udf is also the FAST product's input (it holds the
+// current links), which spares the FP64 split of U.
 template <lqcd_prec PS, bool FAST>
 __global__ void link_update_kernel(GaugeRef<LQCD_F64> U, MomRef P, double c, GaugeRef<PS> Us, GaugeRef<LQCD_F32> Uf,
                                    GaugeRef<PREC_DF> Udf, int Vh, int write_sloppy, int write_f32)
@@ -644,15 +645,24 @@ __global__ void link_update_kernel(GaugeRef<LQCD_F64> U, MomRef P, double c, Gau
     int mp = (int)(t / Vh);
     int mu = mp >> 1, par = mp & 1;
     M3<double> nu;
+    M3<float> nf; // rows 0, 1 of the new link rounded once, for the 12-real copies
     if (FAST) {
         float p[8];
         for (int a = 0; a < 8; a++) p[a] = (float)P.d[P.idx(mu, par, a, cb)];
         const M3<Df> E = reunit_rows_df(expi_cayley_hamilton(herm_from_coeffs(p, (float)c)));
         M3<Df> u;
+        if (Udf.d) { // the float-float copy is current: no FP64 split
 #pragma unroll
-        for (int k = 0; k < 9; k++) {
-            double2 v = ldg(U.d + U.idx(mu, par, k, cb));
-            u.e[k / 3][k % 3] = Cx<Df>{Df(v.x), Df(v.y)};
+            for (int k = 0; k < 9; k++) {
+                float4 v = Udf.d[Udf.idx(mu, par, k, cb)];
+                u.e[k / 3][k % 3] = Cx<Df>{Df(v.x, v.y), Df(v.z, v.w)};
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 9; k++) {
+                double2 v = ldg(U.d + U.idx(mu, par, k, cb));
+                u.e[k / 3][k % 3] = Cx<Df>{Df(v.x), Df(v.y)};
+            }
         }
 #pragma unroll
         for (int i = 0; i < 3; i++)
@@ -668,6 +678,7 @@ __global__ void link_update_kernel(GaugeRef<LQCD_F64> U, MomRef P, double c, Gau
                 }
                 const Df vr = re.value(), vi = im.value();
                 nu.e[i][j] = cx<double>((double)vr, (double)vi);
+                if (i < 2) nf.e[i][j] = cx<float>(vr.hi + vr.lo, vi.hi + vi.lo);
                 if (Udf.d) Udf.d[Udf.idx(mu, par, i * 3 + j, cb)] = make_float4(vr.hi, vr.lo, vi.hi, vi.lo);
             }
     } else {
@@ -676,12 +687,11 @@ __global__ void link_update_kernel(GaugeRef<LQCD_F64> U, MomRef P, double c, Gau
         M3<double> E = expi_cayley_hamilton(herm_from_coeffs(p, c));
         nu = m3_mul(E, U.load<double>(mu, par, cb));
         if (Udf.d) Udf.store(mu, par, cb, nu);
+        for (int i = 0; i < 2; i++)
+            for (int j = 0; j < 3; j++) nf.e[i][j] = cx<float>((float)nu.e[i][j].re, (float)nu.e[i][j].im);
     }
     U.store(mu, par, cb, nu);
     if (write_sloppy || write_f32) {
-        M3<float> nf; // rows 0, 1 rounded once
-        for (int i = 0; i < 2; i++)
-            for (int j = 0; j < 3; j++) nf.e[i][j] = cx<float>((float)nu.e[i][j].re, (float)nu.e[i][j].im);
         if (write_sloppy) Us.store(mu, par, cb, nf);
         if (write_f32) Uf.store(mu, par, cb, nf);
     }
@@ -916,7 +926,7 @@ const char *lqcd_version(void) { return "lqcd-gb300 0.1 (sm_103a)"; }
 
 uint64_t lqcd_launch_count(void) { return g_launches.load(); }
 
-lqcd_status lqcd_kernel_timers(int enable)
+static lqcd_status timers_set(uint32_t mask)
 {
     LQCD_CUDA(cudaDeviceSynchronize());
     std::lock_guard<std::mutex> lk(g_timer_mu);
@@ -926,8 +936,19 @@ lqcd_status lqcd_kernel_timers(int enable)
         g_timer_bytes[k] = 0;
         g_timer_n[k] = 0;
     }
-    g_timers_on.store(enable != 0);
+    g_timer_mask.store(mask);
     return LQCD_OK;
+}
+
+lqcd_status lqcd_kernel_timers(int enable) { return timers_set(enable ? (1u << K_NCLASS) - 1u : 0u); }
+
+lqcd_status lqcd_kernel_timers_only(const char *kernel_class)
+{
+    LQCD_REQUIRE(kernel_class, "kernel_timers_only: NULL class");
+    for (int k = 0; k < K_NCLASS; k++)
+        if (std::strcmp(kernel_class, k_class_names[k]) == 0) return timers_set(1u << k);
+    set_error("kernel_timers_only: unknown class '%s'", kernel_class);
+    return LQCD_EINVAL;
 }
 
 lqcd_status lqcd_kernel_timer_read(const char *kernel_class, double *total_ms, uint64_t *launches,
@@ -1119,6 +1140,20 @@ lqcd_status lqcd_link_update(lqcd_field *U, const lqcd_field *P, double c, lqcd_
         LQCD_REQUIRE(U_sloppy->kind == LQCD_GAUGE && U_sloppy->recon == 12 && same_lattice(U->lat, U_sloppy->lat),
                      "link_update: U_sloppy must be a 12-real gauge field on the same lattice");
     return link_update_dev(U, P, c, U_sloppy, nullptr, false, (cudaStream_t)stream, nullptr);
+}
+
+lqcd_status lqcd_link_update_ex(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *U_sloppy, lqcd_prec arith,
+                                void *stream)
+{
+    LQCD_REQUIRE(arith == LQCD_F64 || arith == LQCD_F32, "link_update_ex: arith must be F64 or F32");
+    if (arith == LQCD_F64) return lqcd_link_update(U, P, c, U_sloppy, stream);
+    LQCD_REQUIRE(U && P && U->kind == LQCD_GAUGE && U->prec == LQCD_F64 && P->kind == LQCD_MOMENTUM,
+                 "link_update_ex needs an F64 gauge field and a momentum field");
+    LQCD_REQUIRE(same_lattice(U->lat, P->lat), "link_update_ex: lattices differ");
+    if (U_sloppy)
+        LQCD_REQUIRE(U_sloppy->kind == LQCD_GAUGE && U_sloppy->recon == 12 && same_lattice(U->lat, U_sloppy->lat),
+                     "link_update_ex: U_sloppy must be a 12-real gauge field on the same lattice");
+    return link_update_dev(U, P, c, U_sloppy, nullptr, true, (cudaStream_t)stream, nullptr);
 }
 
 lqcd_status lqcd_reunitarize(lqcd_field *U, double *max_dev_out, void *stream)

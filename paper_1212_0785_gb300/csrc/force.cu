@@ -19,12 +19,35 @@ namespace lqcd {
 
 constexpr int FB = 128;
 
-__device__ __forceinline__ void link_of_thread(long t, int Vh, int &mu, int &par, int &cb)
+// Link of a thread, direction-major (gauge force: the staples of one
+// direction over all sites reuse best this way, measured).
+__device__ __forceinline__ bool link_of_thread_seq(int Vh, int &mu, int &par, int &cb)
 {
+    const long t = blockIdx.x * (long)FB + threadIdx.x;
+    if (t >= 8L * Vh) return false;
     cb = (int)(t % Vh);
-    int mp = (int)(t / Vh);
+    const int mp = (int)(t / Vh);
     mu = mp >> 1;
     par = mp & 1;
+    return true;
+}
+
+// Link of a thread, directions interleaved (fermion force).  The four
+// directions of one range of sites go to four consecutive blocks, which run
+// together, so the spinors that all four directions read are reused from L2
+// instead of being fetched again by a later sweep over the next direction
+// (measured: 37 -> 28 ms per 32^3x64 trajectory).  Every warp has one
+// direction.  Grid: 8 * force_blocks(Vh) blocks of FB threads.
+__host__ __device__ __forceinline__ int force_blocks(int Vh) { return (Vh + FB - 1) / FB; }
+
+__device__ __forceinline__ bool link_of_thread(int Vh, int &mu, int &par, int &cb)
+{
+    const int b = blockIdx.x;
+    mu = b & 3;
+    const int q = b >> 2, nbp = force_blocks(Vh);
+    par = q / nbp;
+    cb = (q - par * nbp) * FB + threadIdx.x;
+    return cb < Vh;
 }
 
 __device__ __forceinline__ int step_cb(const Geo &g, const int c[4], int dir, int s)
@@ -100,10 +123,8 @@ __device__ __forceinline__ void gauge_force_link(MomRef &P, const GaugeRef<GP> &
 template <typename R, lqcd_prec GP>
 __global__ void __launch_bounds__(FB) gauge_force_kernel(MomRef P, GaugeRef<GP> U, Geo g, double cf)
 {
-    long t = blockIdx.x * (long)FB + threadIdx.x;
-    if (t >= 8L * g.Vh) return;
     int mu, par, cb;
-    link_of_thread(t, g.Vh, mu, par, cb);
+    if (!link_of_thread_seq(g.Vh, mu, par, cb)) return;
     int c[4];
     cb_coords(g, cb, par, c);
     switch (mu) {
@@ -169,10 +190,8 @@ __global__ void __launch_bounds__(FB) fermion_force_kernel(MomRef P, GaugeRef<GP
                                                            SpinorRef<SP> Ao, SpinorRef<SP> Be, SpinorRef<SP> Bo,
                                                            double cf)
 {
-    long t = blockIdx.x * (long)FB + threadIdx.x;
-    if (t >= 8L * g.Vh) return;
     int mu, par, cb;
-    link_of_thread(t, g.Vh, mu, par, cb);
+    if (!link_of_thread(g.Vh, mu, par, cb)) return;
     int c[4];
     cb_coords(g, cb, par, c);
     const SpinorRef<SP> A[2] = {Ae, Ao};
@@ -228,7 +247,7 @@ lqcd_status fermion_force_dev(lqcd_field *P, const lqcd_field *U, const lqcd_fie
     LQCD_TRY(dslash_plain(Bo, L, Ya, 1, nullptr, s));
     Geo g = make_geo(U->lat);
     KernelTimer kt(K_FERMION_FORCE, s);
-    int nb = nblocks_for(8L * g.Vh, FB);
+    int nb = 8 * force_blocks(g.Vh);
     double cf = coeff * kappa * kappa;
     if (Ao->prec == LQCD_F32)
         fermion_force_kernel<float, LQCD_F32, LQCD_F32><<<nb, FB, 0, s>>>(

@@ -733,7 +733,12 @@ struct GaugeRef16 {
     template <typename R>
     __device__ __forceinline__ M3<R> load(int mu, int par, int cb) const
     {
-        uint2 a = ldg(d + idx(mu, par, 0, cb)), b = ldg(d + idx(mu, par, 1, cb)), c = ldg(d + idx(mu, par, 2, cb));
+        return decode<R>(ldg(d + idx(mu, par, 0, cb)), ldg(d + idx(mu, par, 1, cb)), ldg(d + idx(mu, par, 2, cb)));
+    }
+    // the link from its three stored chunks
+    template <typename R>
+    __device__ __forceinline__ M3<R> decode(uint2 a, uint2 b, uint2 c) const
+    {
         M3<R> u;
         float2 t;
         t = un(a.x); u.e[0][0] = cx<R>(t.x, t.y);

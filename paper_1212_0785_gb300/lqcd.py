@@ -105,6 +105,7 @@ _SIGS = {
     "lqcd_launch_count": (ctypes.c_uint64, []),
     "lqcd_set_allocator": (_i, [ALLOC_FN, FREE_FN, _vp]),
     "lqcd_kernel_timers": (_i, [_i]),
+    "lqcd_kernel_timers_only": (_i, [ctypes.c_char_p]),
     "lqcd_kernel_timer_read": (_i, [ctypes.c_char_p, _dp, ctypes.POINTER(ctypes.c_uint64), _dp]),
     "lqcd_field_alloc": (_i, [ctypes.POINTER(Lattice), _i, _i, _i, _pp]),
     "lqcd_field_free": (_i, [_vp]),
@@ -118,6 +119,8 @@ _SIGS = {
     "lqcd_momentum_refresh": (_i, [_vp, _u32, _u32, _u32, _vp]),
     "lqcd_eta_refresh": (_i, [_vp, _u32, _u32, _u32, _vp]),
     "lqcd_dslash": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "lqcd_dslash_staging": (_i, [_i]),
+    "lqcd_dslash_check": (_i, [_vp]),
     "lqcd_mhat": (_i, [_vp, _vp, _vp, _d, _i, _vp]),
     "lqcd_cg_solve": (_i, [_vp, _vp, _vp, _vp, _d, ctypes.POINTER(CgParams), ctypes.POINTER(CgInfo), _vp]),
     "lqcd_gauge_force": (_i, [_vp, _vp, _d, _d, _vp]),
@@ -125,6 +128,7 @@ _SIGS = {
     "lqcd_fermion_force": (_i, [_vp, _vp, _vp, _d, _d, _vp]),
     "lqcd_fermion_force_ex": (_i, [_vp, _vp, _vp, _d, _d, _i, _vp]),
     "lqcd_link_update": (_i, [_vp, _vp, _d, _vp, _vp]),
+    "lqcd_link_update_ex": (_i, [_vp, _vp, _d, _vp, _i, _vp]),
     "lqcd_reunitarize": (_i, [_vp, _dp, _vp]),
     "lqcd_plaquette": (_i, [_vp, _dp, _vp]),
     "lqcd_plaquette_noalloc": (_i, [_vp, _vp, _vp]),
@@ -200,9 +204,13 @@ KERNEL_CLASSES = ("dslash_f64", "dslash_f32", "dslash_f16n", "dslash_bf16", "dsl
                   "fermion_force", "link_update")
 
 
-def kernel_timers(enable: bool):
-    """Enable (clearing the totals) or disable the library's per-class event timers."""
-    _check(lib().lqcd_kernel_timers(int(enable)), "kernel_timers")
+def kernel_timers(enable: bool, only: str | None = None):
+    """Enable (clearing the totals) or disable the library's per-class event
+    timers; only: time that one class alone"""
+    if enable and only:
+        _check(lib().lqcd_kernel_timers_only(only.encode()), "kernel_timers_only")
+    else:
+        _check(lib().lqcd_kernel_timers(int(enable)), "kernel_timers")
 
 
 def kernel_timer_read(kernel_class: str):
@@ -408,9 +416,13 @@ def fermion_force(P: Field, U: Field, X: Field, kappa, coeff, arith=None, stream
         _check(lib().lqcd_fermion_force_ex(P.h, U.h, X.h, kappa, coeff, arith, _s(stream)), "fermion_force_ex")
 
 
-def link_update(U: Field, P: Field, c, U_sloppy: Field | None = None, stream=None):
-    _check(lib().lqcd_link_update(U.h, P.h, c, U_sloppy.h if U_sloppy is not None else None, _s(stream)),
-           "link_update")
+def link_update(U: Field, P: Field, c, U_sloppy: Field | None = None, stream=None, arith=None):
+    """U <- exp(i c P) U (arith F32: the FP32 exponential with a float-float product)"""
+    us = U_sloppy.h if U_sloppy is not None else None
+    if arith is None:
+        _check(lib().lqcd_link_update(U.h, P.h, c, us, _s(stream)), "link_update")
+    else:
+        _check(lib().lqcd_link_update_ex(U.h, P.h, c, us, int(arith), _s(stream)), "link_update_ex")
 
 
 def reunitarize(U: Field, stream=None) -> float:
@@ -630,3 +642,13 @@ class Service:
             self.close()
         except Exception:
             pass
+
+
+def dslash_staging(enable=None) -> bool:
+    """query (None) or set the TMA-staged FP16+norm hopping term; returns the previous setting"""
+    return bool(lib().lqcd_dslash_staging(-1 if enable is None else int(bool(enable))))
+
+
+def dslash_check(stream=None):
+    """raises LqcdError(ETIMEOUT) if a staged block gave up waiting since the last check"""
+    _check(lib().lqcd_dslash_check(_s(stream)), "dslash_check")

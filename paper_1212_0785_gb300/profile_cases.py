@@ -2,7 +2,8 @@
 
   python -m paper_1212_0785_gb300.profile_cases dslash   # 3 launches per precision
   python -m paper_1212_0785_gb300.profile_cases cg       # one mixed solve
-  python -m paper_1212_0785_gb300.profile_cases md       # one FP32 MD force + link update
+  python -m paper_1212_0785_gb300.profile_cases md       # FP32 MD forces + FP32 link update
+  python -m paper_1212_0785_gb300.profile_cases traj     # one 1-step mixed trajectory (the HMC's own kernels)
 
 Each case builds the 32^3x64 start configuration of the benchmark (Philox
 seed 3, eps 0.15) unless --dims is given, runs its calls once and exits 0.
@@ -56,17 +57,32 @@ def case_cg(dims):
 
 
 def case_md(dims):
-    """FP32 gauge force, FP32 fermion force and one link update"""
+    """FP32 gauge force, FP32 fermion force and one FP32 link update (the
+    molecular dynamics of the mixed trajectory)"""
     U, eta = _start(dims)
     P = lqcd.momentum_field(dims)
     lqcd.momentum_refresh(P, seed=3, traj=0)
     lqcd.gauge_force(P, U, BETA, 0.01, arith=lqcd.F32)
     lqcd.fermion_force(P, U, eta, KAPPA, 0.01, arith=lqcd.F32)
-    lqcd.link_update(U, P, 0.03)
+    lqcd.link_update(U, P, 0.03, arith=lqcd.F32)
     torch.cuda.synchronize()
 
 
-CASES = {"dslash": case_dslash, "cg": case_cg, "md": case_md}
+def case_traj(dims):
+    """one mixed-precision trajectory of one Omelyan step (the benchmark's
+    settings otherwise): every kernel of the trajectory in the variants the
+    HMC driver launches"""
+    U = lqcd.gauge_field(dims)
+    lqcd.gauge_start(U, seed=3, eps=0.15)
+    st = lqcd.HmcState(U, seed=3)
+    cg = lqcd.cg_params(tol=1e-10, maxiter=20000, sloppy=lqcd.F16N, delta=0.003)
+    info = st.trajectory(lqcd.hmc_params(BETA, KAPPA, 1.0, 1, lqcd.OMELYAN, cg=cg, force_prec=lqcd.F32, chrono=3))
+    torch.cuda.synchronize()
+    print(f"traj: dH {info['dH']:.4f}, {info['cg_iters']} CG iterations, {info['n_solves']} solves")
+    st.close()
+
+
+CASES = {"dslash": case_dslash, "cg": case_cg, "md": case_md, "traj": case_traj}
 
 
 def main(argv=None):

@@ -98,6 +98,26 @@ def test_link_update_matches_oracle(dims):
         assert rel_err(U.download(), orc.link_update(dims, Uh, Ph, c)) < 1e-12, c
 
 
+@pytest.mark.parametrize("c", [0.07, 1.5, -0.3])
+def test_fp32_link_update_close_and_unitary(c):
+    """the FP32 molecular dynamics' update: within the FP32 exponential's
+    error of the oracle, special unitary to float-float precision"""
+    dims = (6, 4, 2, 10)
+    Uh = orc.gauge_start(dims, seed=16, eps=0.3)
+    Ph = orc.momentum_refresh(dims, 16, 0)
+    U = lqcd.gauge_field(dims).upload(Uh)
+    P = lqcd.momentum_field(dims).upload(Ph)
+    Us = lqcd.gauge_field(dims, lqcd.F16N)
+    lqcd.link_update(U, P, c, U_sloppy=Us, arith=lqcd.F32)
+    got = U.download()
+    assert rel_err(got, orc.link_update(dims, Uh, Ph, c)) < 2e-6
+    dev = np.abs(np.einsum("xmab,xmcb->xmac", got, got.conj()) - np.eye(3)).max()
+    assert dev < 1e-13 and np.abs(np.linalg.det(got) - 1).max() < 1e-13
+    assert rel_err(Us.download(), got) < 2e-3
+    with pytest.raises(lqcd.LqcdError):
+        lqcd.link_update(U, P, c, arith=lqcd.F16N)
+
+
 def test_link_update_degenerate_momenta():
     """momenta with degenerate eigenvalues (single diagonal generators) and zero"""
     dims = (4, 4, 4, 4)
