@@ -805,6 +805,83 @@ __global__ void __launch_bounds__(RB) dot_kernel(const double *a, const double *
 // number of blocks for the flat reductions: a fixed function of n only
 static int flat_blocks(long n) { return (int)std::min<long>(1184, std::max<long>(1, (n + RB * 8 - 1) / (RB * 8))); }
 
+// The plaquette sum from float-float links (~48 bits per product, FP64
+// accumulation): the FP32 pipes instead of the FP64 one.  Re Tr(a b^dag) with
+// a = U_mu(x) U_nu(x+mu), b = U_nu(x) U_mu(x+nu), as plaquette_kernel.
+__device__ __forceinline__ M3<Df> df_link(const GaugeRef<PREC_DF> &U, int mu, int par, int cb)
+{
+    M3<Df> u;
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        float4 v = ldg(U.d + U.idx(mu, par, k, cb));
+        u.e[k / 3][k % 3] = Cx<Df>{Df(v.x, v.y), Df(v.z, v.w)};
+    }
+    return u;
+}
+
+__device__ __forceinline__ M3<Df> df_mul(const M3<Df> &a, const M3<Df> &b)
+{
+    M3<Df> r;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            DfAcc re, im;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                re.add_prod(a.e[i][k].re, b.e[k][j].re);
+                re.sub_prod(a.e[i][k].im, b.e[k][j].im);
+                im.add_prod(a.e[i][k].re, b.e[k][j].im);
+                im.add_prod(a.e[i][k].im, b.e[k][j].re);
+            }
+            r.e[i][j] = Cx<Df>{re.value(), im.value()};
+        }
+    return r;
+}
+
+__global__ void __launch_bounds__(RB) plaquette_df_kernel(GaugeRef<PREC_DF> U, Geo g, double *partials, int nblocks)
+{
+    int t = blockIdx.x * RB + threadIdx.x;
+    double acc[1] = {0.0};
+    if (t < 2 * g.Vh) {
+        int par = t / g.Vh, cb = t % g.Vh;
+        int c[4];
+        cb_coords(g, cb, par, c);
+        for (int mu = 0; mu < 3; mu++) {
+            int cm[4] = {c[0], c[1], c[2], c[3]};
+            cm[mu] = (c[mu] + 1 == g.L[mu]) ? 0 : c[mu] + 1;
+            int cb_m = coords_cb(g, cm);
+            for (int nu = mu + 1; nu < 4; nu++) {
+                int cn[4] = {c[0], c[1], c[2], c[3]};
+                cn[nu] = (c[nu] + 1 == g.L[nu]) ? 0 : c[nu] + 1;
+                int cb_n = coords_cb(g, cn);
+                M3<Df> a = df_mul(df_link(U, mu, par, cb), df_link(U, nu, 1 - par, cb_m));
+                M3<Df> b = df_mul(df_link(U, nu, par, cb), df_link(U, mu, 1 - par, cb_n));
+                DfAcc tr;
+#pragma unroll
+                for (int i = 0; i < 3; i++)
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        tr.add_prod(a.e[i][k].re, b.e[i][k].re);
+                        tr.add_prod(a.e[i][k].im, b.e[i][k].im);
+                    }
+                acc[0] += (double)tr.value() * (1.0 / 3.0);
+            }
+        }
+    }
+    block_sum_store<1, RB>(acc, partials, nblocks);
+}
+
+lqcd_status plaquette_sum_df(const lqcd_field *Udf, double *dst_dev, DevBuf &part, cudaStream_t s)
+{
+    Geo g = make_geo(Udf->lat);
+    int nb = nblocks_for(2L * g.Vh, RB);
+    if (part.bytes < sizeof(double) * nb) LQCD_TRY(part.alloc(sizeof(double) * nb, s));
+    plaquette_df_kernel<<<nb, RB, 0, s>>>(gauge_ref<PREC_DF>(Udf), g, (double *)part.p, nb);
+    LQCD_LAUNCHED();
+    return reduce_partials((double *)part.p, nb, 1, dst_dev, s);
+}
+
 lqcd_status plaquette_sum(const lqcd_field *U, double *dst_dev, DevBuf &part, cudaStream_t s)
 {
     Geo g = make_geo(U->lat);

@@ -18,6 +18,7 @@ namespace lqcd {
 
 // defined in field.cu / force.cu
 lqcd_status plaquette_sum(const lqcd_field *U, double *dst_dev, DevBuf &part, cudaStream_t s);
+lqcd_status plaquette_sum_df(const lqcd_field *Udf, double *dst_dev, DevBuf &part, cudaStream_t s);
 lqcd_status kinetic_sum(const lqcd_field *P, double *dst_dev, DevBuf &part, cudaStream_t s);
 lqcd_status reunitarize_dev(lqcd_field *U, double *dst_dev, DevBuf &part, cudaStream_t s);
 lqcd_status link_update_dev(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *Us, lqcd_field *Uf, bool fast,
@@ -352,11 +353,17 @@ static lqcd_status drift(lqcd_hmc_state *st, const lqcd_hmc_params *p, double c,
                            sloppy_links(st, p) ? st->Udf.f : nullptr);
 }
 
-// scalars[0] = plaquette sum, [1] = sum p^2, [2] = fermion term
-static lqcd_status hamiltonian_parts(lqcd_hmc_state *st, cudaStream_t s)
+// scalars[0] = plaquette sum, [1] = sum p^2, [2] = fermion term.  With the
+// mixed solver the float-float link copy is current (split at the refresh,
+// written by every link update), and the plaquette comes from it on the FP32
+// pipes instead of the FP64 one.
+static lqcd_status hamiltonian_parts(lqcd_hmc_state *st, const lqcd_hmc_params *p, cudaStream_t s)
 {
     double *d = (double *)st->scal.p;
-    LQCD_TRY(plaquette_sum(st->U, d + 0, st->part, s));
+    if (sloppy_links(st, p) && st->Udf.f)
+        LQCD_TRY(plaquette_sum_df(st->Udf.f, d + 0, st->part, s));
+    else
+        LQCD_TRY(plaquette_sum(st->U, d + 0, st->part, s));
     LQCD_TRY(kinetic_sum(st->P.f, d + 1, st->part, s));
     return LQCD_OK;
 }
@@ -375,7 +382,7 @@ static lqcd_status refresh(lqcd_hmc_state *st, const lqcd_hmc_params *p, double 
     LQCD_TRY(ensure_sloppy(st, p, s));
     LQCD_TRY(momentum_refresh_dev(st->P.f, st->seed, st->chain, st->traj, s));
     double *d = (double *)st->scal.p;
-    LQCD_TRY(hamiltonian_parts(st, s));
+    LQCD_TRY(hamiltonian_parts(st, p, s));
     double h[4] = {0, 0, 0, 0};
     if (p->n_flavors == 2) {
         PfTerm &t = st->pf[PF_MAIN];
@@ -420,7 +427,7 @@ static lqcd_status hamiltonian(lqcd_hmc_state *st, const lqcd_hmc_params *p, dou
                                bool reuse_last = false)
 {
     double *d = (double *)st->scal.p;
-    LQCD_TRY(hamiltonian_parts(st, s));
+    LQCD_TRY(hamiltonian_parts(st, p, s));
     double h[4] = {0, 0, 0, 0};
     if (p->n_flavors == 2) {
         PfTerm &t = st->pf[PF_MAIN];
@@ -787,7 +794,7 @@ lqcd_status lqcd_batch_trajectory(lqcd_batch *B, const lqcd_hmc_params *params, 
     }
     lqcd_status rc = batch_integrate(B, params, s);
     if (rc == LQCD_OK) {
-        for (size_t i = 0; i < n; i++) LQCD_TRY(hamiltonian_parts(B->chains[i], s));
+        for (size_t i = 0; i < n; i++) LQCD_TRY(hamiltonian_parts(B->chains[i], &params[i], s));
         rc = batch_solve(B, params, s, true);
     }
     for (size_t i = 0; i < n; i++) {

@@ -154,3 +154,22 @@ def test_extrapolated_guess_md_steps_and_leapfrog():
             st.close()
         assert np.max(np.abs(out[1][0] - out[0][0])) < 1e-9
         assert abs(out[1][1] - out[0][1]) < 1e-7
+
+
+def test_mixed_hamiltonian_plaquette_from_float_float_links():
+    """with the mixed solver the Hamiltonians take the plaquette from the
+    float-float link copy: H0 and H after MD steps agree with the FP64 path's"""
+    Uh = orc.gauge_start((6, 4, 4, 8), seed=9, eps=0.4)
+    cg64 = lqcd.cg_params(tol=1e-12)
+    cgmx = lqcd.cg_params(tol=1e-12, sloppy=lqcd.F16N, delta=0.01)
+    out = []
+    for cg in (cg64, cgmx):
+        U = lqcd.gauge_field((6, 4, 4, 8)).upload(Uh)
+        st = lqcd.HmcState(U, seed=9)
+        p = lqcd.hmc_params(5.7, 0.15, 0.4, 2, lqcd.LEAPFROG, cg=cg)
+        h0 = st.refresh(p)
+        st.md_step(p)
+        out.append((h0, st.hamiltonian(p)))
+        st.close()
+    assert abs(out[1][0] - out[0][0]) < 1e-10 * abs(out[0][0])
+    assert abs(out[1][1] - out[0][1]) < 1e-6 * abs(out[0][1])
