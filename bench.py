@@ -479,6 +479,13 @@ def run_chains(args):
     torch.cuda.synchronize()
     t_batch = e0.elapsed_time(e1) / 1e3
     launches = lqcd.launch_count() - launches0
+    # per-class kernel time of one more batched trajectory (every class timed)
+    lqcd.kernel_timers(True)
+    batch.trajectory(params)
+    torch.cuda.synchronize()
+    kernel_time = {k: {"ms": v[0], "launches": v[1]} for k in lqcd.KERNEL_CLASSES
+                   for v in [lqcd.kernel_timer_read(k)] if v[1]}
+    lqcd.kernel_timers(False)
     batch.close()
     # the same chains, one trajectory after another, each alone
     fields2, states2 = make()
@@ -503,6 +510,7 @@ def run_chains(args):
                        "tau": 1.0, "start_eps": 0.3, "initial_guess": {0: "zero", 1: "previous solution"}.get(
                            args.chrono, f"extrapolated through the last {args.chrono} solutions")},
             "gpu_launches": launches,
+            "kernel_time_per_batch_traj": kernel_time,
             "sequential": {"value": n * args.steps / t_seq, "ms_per_step": t_seq / args.steps * 1e3},
             "batched_speedup": t_seq / t_batch,
             "physics": {"acceptance": float(np.mean([f["accepted"] for it in infos for f in it])),

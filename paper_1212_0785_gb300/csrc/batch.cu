@@ -325,10 +325,37 @@ lqcd_status BatchSolver::chunk(cudaStream_t s)
     }
     LQCD_CUDA(cudaMemcpyAsync(pinned_h, gathered.p, sizeof(CgScalars) * active.size(), cudaMemcpyDeviceToHost, s));
     LQCD_CUDA(cudaStreamSynchronize(s));
-    std::vector<CgRun *> still;
+    // Pauses: the systems with their own float-float temporaries enqueue
+    // their accurate residuals together and share one read-back; a system
+    // that borrows another workspace's temporaries (the solve service) is
+    // handled alone, since the next system's residual would overwrite them.
+    std::vector<CgRun *> paused;
     for (size_t i = 0; i < active.size(); i++) {
         CgRun *r = active[i];
-        if (pinned_h[i].pause) r->on_pause(pinned_h[i], s);
+        if (!pinned_h[i].pause) continue;
+        if (r->ws->tmp_from) {
+            r->on_pause(pinned_h[i], s);
+        } else {
+            r->pause_begin(pinned_h[i], s);
+            if (!r->done) paused.push_back(r);
+        }
+    }
+    if (!paused.empty()) {
+        if (pinned_rr_n < paused.size()) {
+            if (pinned_rr) cudaFreeHost(pinned_rr);
+            pinned_rr = nullptr;
+            pinned_rr_n = 0;
+            LQCD_CUDA(cudaMallocHost((void **)&pinned_rr, sizeof(double) * paused.size()));
+            pinned_rr_n = paused.size();
+        }
+        for (size_t j = 0; j < paused.size(); j++)
+            LQCD_CUDA(cudaMemcpyAsync(&pinned_rr[j], paused[j]->pause_result_dev(), sizeof(double),
+                                      cudaMemcpyDeviceToHost, s));
+        LQCD_CUDA(cudaStreamSynchronize(s));
+        for (size_t j = 0; j < paused.size(); j++) paused[j]->pause_end(pinned_rr[j], s);
+    }
+    std::vector<CgRun *> still;
+    for (CgRun *r : active) {
         if (r->done)
             changed = true;
         else
@@ -382,6 +409,9 @@ void BatchSolver::release()
     if (pinned_h) cudaFreeHost(pinned_h);
     pinned_h = nullptr;
     pinned_n = 0;
+    if (pinned_rr) cudaFreeHost(pinned_rr);
+    pinned_rr = nullptr;
+    pinned_rr_n = 0;
 }
 
 } // namespace lqcd

@@ -35,6 +35,8 @@ struct BatchSolver {
     cudaStream_t capture_stream = nullptr;
     CgScalars *pinned_h = nullptr;
     size_t pinned_n = 0;
+    double *pinned_rr = nullptr; // accurate |r|^2 of the systems paused in one chunk
+    size_t pinned_rr_n = 0;
 
     BatchSolver();
     ~BatchSolver();

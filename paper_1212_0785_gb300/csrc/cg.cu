@@ -311,8 +311,9 @@ static lqcd_status launch_p_update(lqcd_field *p, lqcd_field *r, const CgScalars
 }
 
 // accurate residual r = b - A x of the mixed solve in float-float arithmetic
-// (x, b, links in float-float storage); |r|^2 in *rr
-static lqcd_status true_residual_df(CgWorkspace &ws, double kappa, double *rr, cudaStream_t s)
+// (x, b, links in float-float storage); |r|^2 into ws.scalars[0] (device),
+// not read back
+static lqcd_status residual_df_enqueue(CgWorkspace &ws, double kappa, cudaStream_t s)
 {
     double k2 = kappa * kappa;
     LQCD_TRY(dslash_plain(ws.tmpo(), ws.udf(), ws.xdf.f, 0, nullptr, s));
@@ -323,7 +324,13 @@ static lqcd_status true_residual_df(CgWorkspace &ws, double kappa, double *rr, c
     residual_df_kernel<<<nb, BB, 0, s>>>(spinor_ref<PREC_DF>(ws.rdf_()), spinor_ref<PREC_DF>(ws.bdf.f),
                                          spinor_ref<PREC_DF>(ws.t2()), (double *)ws.partials.p, nb, Vh);
     LQCD_LAUNCHED();
-    LQCD_TRY(reduce_partials((double *)ws.partials.p, nb, 1, (double *)ws.scalars.p, s));
+    return reduce_partials((double *)ws.partials.p, nb, 1, (double *)ws.scalars.p, s);
+}
+
+// the same, read back: |r|^2 in *rr
+static lqcd_status true_residual_df(CgWorkspace &ws, double kappa, double *rr, cudaStream_t s)
+{
+    LQCD_TRY(residual_df_enqueue(ws, kappa, s));
     LQCD_TRY(pinned());
     LQCD_TRY(read_scalars((double *)ws.scalars.p, g_pinned.d, 1, s));
     *rr = g_pinned.d[0];
@@ -490,20 +497,54 @@ lqcd_status CgRun::on_pause(const CgScalars &h, cudaStream_t s)
 
 lqcd_status CgRun::on_pause_impl(const CgScalars &h, cudaStream_t s)
 {
+    if (!mixed) {
+        inf.iters = h.iter;
+        if (h.reason == PAUSE_NONFINITE) {
+            set_error("cg: non-finite value after %d iterations", h.iter);
+            return fail(LQCD_ENUMERIC);
+        }
+        LQCD_TRY(true_residual(*ws, x, U, b, kappa, &rr_true, s));
+        return pause_decide(h, s);
+    }
+    LQCD_TRY(pause_begin(h, s));
+    if (done) return status;
+    LQCD_TRY(pinned());
+    LQCD_TRY(read_scalars(pause_result_dev(), g_pinned.d, 1, s));
+    return pause_end(g_pinned.d[0], s);
+}
+
+// mixed solve, first half of a pause: accumulate the FP32 increment into the
+// float-float solution and enqueue its accurate residual (read by the caller)
+lqcd_status CgRun::pause_begin(const CgScalars &h, cudaStream_t s)
+{
     CgWorkspace &w = *ws;
     inf.iters = h.iter;
+    hp = h;
     if (h.reason == PAUSE_NONFINITE) {
         set_error("cg: non-finite value after %d iterations", h.iter);
         return fail(LQCD_ENUMERIC);
     }
-    if (mixed) {
-        accum_df_kernel<<<nblocks_for(Vh, BB), BB, 0, s>>>(spinor_ref<PREC_DF>(w.xdf.f), spinor_ref<LQCD_F32>(XS),
-                                                           Vh);
-        LQCD_LAUNCHED();
-        LQCD_TRY(true_residual_df(w, kappa, &rr_true, s));
-    } else {
-        LQCD_TRY(true_residual(w, x, U, b, kappa, &rr_true, s));
-    }
+    accum_df_kernel<<<nblocks_for(Vh, BB), BB, 0, s>>>(spinor_ref<PREC_DF>(w.xdf.f), spinor_ref<LQCD_F32>(XS), Vh);
+    LQCD_LAUNCHED();
+    lqcd_status rc = residual_df_enqueue(w, kappa, s);
+    if (rc != LQCD_OK) return fail(rc);
+    return LQCD_OK;
+}
+
+double *CgRun::pause_result_dev() const { return (double *)ws->scalars.p; }
+
+// second half: the decision on the accurate |r|^2
+lqcd_status CgRun::pause_end(double rr, cudaStream_t s)
+{
+    rr_true = rr;
+    lqcd_status rc = pause_decide(hp, s);
+    if (rc != LQCD_OK && !done) return fail(rc);
+    return rc;
+}
+
+lqcd_status CgRun::pause_decide(const CgScalars &h, cudaStream_t s)
+{
+    CgWorkspace &w = *ws;
     inf.true_rel_res = std::sqrt(rr_true / bb);
     if (!std::isfinite(rr_true)) {
         set_error("cg: non-finite true residual");

@@ -63,12 +63,21 @@ struct CgRun {
     lqcd_status start(cudaStream_t s, CgScalars *sc_dev);
     lqcd_status iterate(cudaStream_t s);
     lqcd_status on_pause(const CgScalars &h, cudaStream_t s);
+    // a mixed solve's pause in two halves, so that many solves' accurate
+    // residuals can be enqueued before one read-back: pause_begin enqueues
+    // (unless it fails: then done), pause_result_dev is where |r|^2 lands,
+    // pause_end takes it and finishes the pause
+    lqcd_status pause_begin(const CgScalars &h, cudaStream_t s);
+    double *pause_result_dev() const;
+    lqcd_status pause_end(double rr, cudaStream_t s);
     lqcd_status fail(lqcd_status st);
     lqcd_status succeed();
 
   private:
+    CgScalars hp{}; // the pause being handled
     lqcd_status start_impl(cudaStream_t s);
     lqcd_status on_pause_impl(const CgScalars &h, cudaStream_t s);
+    lqcd_status pause_decide(const CgScalars &h, cudaStream_t s);
 };
 
 lqcd_status split_links(lqcd_field *Udf, const lqcd_field *U, cudaStream_t s);
