@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "batch.cuh"
+#include "dslash_df.cuh"
 #include "dslash_site.cuh"
 
 namespace lqcd {
@@ -200,6 +201,63 @@ __global__ void batch_gather_scalars(const SysDesc<SP> *sys, CgScalars *out, int
     if (i < n) out[i] = *sys[i].sc;
 }
 
+// ---------------------------------------------------------------- reliable updates of many systems
+//
+// The accurate residual r = b - Mhat^dag Mhat x of every paused system in
+// float-float, with shared launches: x += x_s, the four float-float hops,
+// r = b - t with block partials, and one fixed-order final sum per system.
+// Each block runs exactly the code and block decomposition of the
+// single-system kernels (cg.cu, dslash_df.cu), so the results are bitwise
+// theirs.
+
+struct DfSys {
+    Geo g;
+    SpinorRef<PREC_DF> xdf, bdf, rdf, t1, t2, tmpo;
+    GaugeRef<PREC_DF> U;
+    SpinorRef<LQCD_F32> xs;
+    Df mk2; // -kappa^2
+    double *partials, *scalars;
+    int nb; // blocks of CG_BLOCK sites
+};
+
+__global__ void __launch_bounds__(CG_BLOCK) batch_accum_df_kernel(const DfSys *sys, const int2 *bmap)
+{
+    const int2 m = bmap[blockIdx.x];
+    const DfSys &d = sys[m.x];
+    const int cb = m.y * CG_BLOCK + threadIdx.x;
+    if (cb < d.g.Vh) accum_df_site(d.xdf, d.xs, cb);
+}
+
+template <int STEP>
+__global__ void __launch_bounds__(DF_SITES * 3, 4) batch_df_hop_kernel(const DfSys *sys, const int2 *bmap)
+{
+    __shared__ DfHalves sh;
+    const int2 m = bmap[blockIdx.x];
+    const DfSys &d = sys[m.x];
+    if (STEP == 0) df_hop_block<false, false>(sh, d.tmpo, d.xdf, d.U, d.g, 1, d.xdf, Df(0), m.y);
+    if (STEP == 1) df_hop_block<false, true>(sh, d.t1, d.tmpo, d.U, d.g, 0, d.xdf, d.mk2, m.y);
+    if (STEP == 2) df_hop_block<true, false>(sh, d.tmpo, d.t1, d.U, d.g, 1, d.t1, Df(0), m.y);
+    if (STEP == 3) df_hop_block<true, true>(sh, d.t2, d.tmpo, d.U, d.g, 0, d.t1, d.mk2, m.y);
+}
+
+__global__ void __launch_bounds__(CG_BLOCK) batch_residual_df_kernel(const DfSys *sys, const int2 *bmap)
+{
+    const int2 m = bmap[blockIdx.x];
+    const DfSys &d = sys[m.x];
+    const int cb = m.y * CG_BLOCK + threadIdx.x;
+    double n2[1] = {0.0};
+    if (cb < d.g.Vh) n2[0] = residual_df_site(d.rdf, d.bdf, d.t2, cb);
+    block_sum_store<1, CG_BLOCK>(n2, d.partials, d.nb, m.y);
+}
+
+__global__ void batch_final_sum_kernel(const DfSys *sys)
+{
+    const DfSys &d = sys[blockIdx.x];
+    double sums[1];
+    final_sum_block<1>(d.partials, d.nb, sums);
+    if (threadIdx.x == 0) d.scalars[0] = sums[0];
+}
+
 // ---------------------------------------------------------------- host side
 
 template <lqcd_prec SP>
@@ -333,14 +391,13 @@ lqcd_status BatchSolver::chunk(cudaStream_t s)
     for (size_t i = 0; i < active.size(); i++) {
         CgRun *r = active[i];
         if (!pinned_h[i].pause) continue;
-        if (r->ws->tmp_from) {
+        if (r->ws->tmp_from)
             r->on_pause(pinned_h[i], s);
-        } else {
-            r->pause_begin(pinned_h[i], s);
-            if (!r->done) paused.push_back(r);
-        }
+        else if (r->pause_record(pinned_h[i]))
+            paused.push_back(r);
     }
     if (!paused.empty()) {
+        LQCD_TRY(residuals_df(paused, s));
         if (pinned_rr_n < paused.size()) {
             if (pinned_rr) cudaFreeHost(pinned_rr);
             pinned_rr = nullptr;
@@ -362,6 +419,59 @@ lqcd_status BatchSolver::chunk(cudaStream_t s)
             still.push_back(r);
     }
     active.swap(still);
+    return LQCD_OK;
+}
+
+// the accurate residuals of the paused systems with shared launches (their
+// |r|^2 land in each system's pause_result_dev)
+lqcd_status BatchSolver::residuals_df(const std::vector<CgRun *> &runs, cudaStream_t s)
+{
+    std::vector<DfSys> hd;
+    std::vector<int2> hdf, hbb;
+    for (size_t i = 0; i < runs.size(); i++) {
+        const CgRun &r = *runs[i];
+        CgWorkspace &w = *r.ws;
+        DfSys d;
+        d.g = make_geo(r.x->lat);
+        d.xdf = spinor_ref<PREC_DF>(w.xdf.f);
+        d.bdf = spinor_ref<PREC_DF>(w.bdf.f);
+        d.rdf = spinor_ref<PREC_DF>(w.rdf_());
+        d.t1 = spinor_ref<PREC_DF>(w.t1());
+        d.t2 = spinor_ref<PREC_DF>(w.t2());
+        d.tmpo = spinor_ref<PREC_DF>(w.tmpo());
+        d.U = gauge_ref<PREC_DF>(w.udf());
+        d.xs = spinor_ref<LQCD_F32>(r.XS);
+        d.mk2 = Df(-(r.kappa * r.kappa));
+        d.partials = (double *)w.partials.p;
+        d.scalars = r.pause_result_dev();
+        d.nb = nblocks_for(d.g.Vh, CG_BLOCK);
+        hd.push_back(d);
+        for (int k = 0; k < nblocks_for(d.g.Vh, DF_SITES); k++) hdf.push_back(make_int2((int)i, k));
+        for (int k = 0; k < d.nb; k++) hbb.push_back(make_int2((int)i, k));
+    }
+    if (df_descs.bytes < hd.size() * sizeof(DfSys)) LQCD_TRY(df_descs.alloc(hd.size() * sizeof(DfSys), s));
+    if (df_map.bytes < hdf.size() * sizeof(int2)) LQCD_TRY(df_map.alloc(hdf.size() * sizeof(int2), s));
+    if (bb_map.bytes < hbb.size() * sizeof(int2)) LQCD_TRY(bb_map.alloc(hbb.size() * sizeof(int2), s));
+    // pageable sources: the copies have taken the host data when they return
+    LQCD_CUDA(cudaMemcpyAsync(df_descs.p, hd.data(), hd.size() * sizeof(DfSys), cudaMemcpyHostToDevice, s));
+    LQCD_CUDA(cudaMemcpyAsync(df_map.p, hdf.data(), hdf.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    LQCD_CUDA(cudaMemcpyAsync(bb_map.p, hbb.data(), hbb.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    const DfSys *d = (const DfSys *)df_descs.p;
+    const int2 *mdf = (const int2 *)df_map.p, *mbb = (const int2 *)bb_map.p;
+    const int ndf = (int)hdf.size(), nbb = (int)hbb.size();
+    const dim3 dfb(DF_SITES, 3);
+    batch_accum_df_kernel<<<nbb, CG_BLOCK, 0, s>>>(d, mbb);
+    {
+        KernelTimer kt(K_DSLASH_DF64, s, 4.0 * 1536.0 * (double)ndf * DF_SITES);
+        batch_df_hop_kernel<0><<<ndf, dfb, 0, s>>>(d, mdf);
+        batch_df_hop_kernel<1><<<ndf, dfb, 0, s>>>(d, mdf);
+        batch_df_hop_kernel<2><<<ndf, dfb, 0, s>>>(d, mdf);
+        batch_df_hop_kernel<3><<<ndf, dfb, 0, s>>>(d, mdf);
+    }
+    batch_residual_df_kernel<<<nbb, CG_BLOCK, 0, s>>>(d, mbb);
+    batch_final_sum_kernel<<<(unsigned)hd.size(), 1024, 0, s>>>(d);
+    LQCD_CUDA(cudaGetLastError());
+    g_launches.fetch_add(8, std::memory_order_relaxed);
     return LQCD_OK;
 }
 

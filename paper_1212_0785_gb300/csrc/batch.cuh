@@ -29,6 +29,7 @@ struct BatchSolver {
     bool use_graph = true;
     std::vector<CgRun *> active;
     DevBuf descs, bmap, gathered;
+    DevBuf df_descs, df_map, bb_map; // the paused systems' reliable updates
     int nblocks_total = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -54,6 +55,7 @@ struct BatchSolver {
 
   private:
     void drop_graph();
+    lqcd_status residuals_df(const std::vector<CgRun *> &runs, cudaStream_t s);
     template <lqcd_prec SP>
     lqcd_status run_all(std::vector<CgRun *> &runs, cudaStream_t s);
     template <lqcd_prec SP>

@@ -21,11 +21,12 @@
 #include <cmath>
 
 #include "cg.cuh"
+#include "dslash_df.cuh"
 #include "df64.cuh"
 
 namespace lqcd {
 
-constexpr int BB = 256;
+constexpr int BB = CG_BLOCK;
 constexpr int CG_CHUNK = 4;
 
 __global__ void cg_pap_kernel(const double *partials, int nb, CgScalars *sc)
@@ -143,17 +144,7 @@ __global__ void accum_df_kernel(SpinorRef<PREC_DF> x, SpinorRef<LQCD_F32> xs, in
 {
     int cb = blockIdx.x * BB + threadIdx.x;
     if (cb >= Vh) return;
-    Sp<Df> xv = x.load_rw<Df>(cb);
-    Sp<float> dv = xs.load_rw<float>(cb);
-#pragma unroll
-    for (int a = 0; a < 4; a++)
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            xv.c[a][k].re += Df(dv.c[a][k].re, 0.f);
-            xv.c[a][k].im += Df(dv.c[a][k].im, 0.f);
-        }
-    x.store(cb, xv);
-    xs.store(cb, sp_zero<float>());
+    accum_df_site(x, xs, cb);
 }
 
 // r = b - t in float-float; block partials of |r|^2 from the leading parts
@@ -162,19 +153,7 @@ __global__ void __launch_bounds__(BB) residual_df_kernel(SpinorRef<PREC_DF> r, S
 {
     int cb = blockIdx.x * BB + threadIdx.x;
     double n2[1] = {0.0};
-    if (cb < Vh) {
-        Sp<Df> bv = b.load_rw<Df>(cb), tv = t.load_rw<Df>(cb);
-        float acc = 0.f;
-#pragma unroll
-        for (int a = 0; a < 4; a++)
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                bv.c[a][k] = bv.c[a][k] - tv.c[a][k];
-                acc += bv.c[a][k].re.hi * bv.c[a][k].re.hi + bv.c[a][k].im.hi * bv.c[a][k].im.hi;
-            }
-        r.store(cb, bv);
-        n2[0] = acc;
-    }
+    if (cb < Vh) n2[0] = residual_df_site(r, b, t, cb);
     block_sum_store<1, BB>(n2, partials, nb);
 }
 
@@ -515,15 +494,22 @@ lqcd_status CgRun::on_pause_impl(const CgScalars &h, cudaStream_t s)
 
 // mixed solve, first half of a pause: accumulate the FP32 increment into the
 // float-float solution and enqueue its accurate residual (read by the caller)
-lqcd_status CgRun::pause_begin(const CgScalars &h, cudaStream_t s)
+bool CgRun::pause_record(const CgScalars &h)
 {
-    CgWorkspace &w = *ws;
     inf.iters = h.iter;
     hp = h;
     if (h.reason == PAUSE_NONFINITE) {
         set_error("cg: non-finite value after %d iterations", h.iter);
-        return fail(LQCD_ENUMERIC);
+        fail(LQCD_ENUMERIC);
+        return false;
     }
+    return true;
+}
+
+lqcd_status CgRun::pause_begin(const CgScalars &h, cudaStream_t s)
+{
+    CgWorkspace &w = *ws;
+    if (!pause_record(h)) return status;
     accum_df_kernel<<<nblocks_for(Vh, BB), BB, 0, s>>>(spinor_ref<PREC_DF>(w.xdf.f), spinor_ref<LQCD_F32>(XS), Vh);
     LQCD_LAUNCHED();
     lqcd_status rc = residual_df_enqueue(w, kappa, s);

@@ -7,6 +7,10 @@
 
 namespace lqcd {
 
+// threads per block of the solver's vector kernels (its block partial sums
+// are laid out by it)
+constexpr int CG_BLOCK = 256;
+
 // Fields and scalars of one solver, reusable across solves on one lattice.
 struct CgWorkspace {
     lqcd_lattice lat{};
@@ -70,6 +74,9 @@ struct CgRun {
     lqcd_status pause_begin(const CgScalars &h, cudaStream_t s);
     double *pause_result_dev() const;
     lqcd_status pause_end(double rr, cudaStream_t s);
+    // pause_begin without its kernels, for a caller that runs them for many
+    // solves at once (batch.cu); false if the pause failed the solve
+    bool pause_record(const CgScalars &h);
     lqcd_status fail(lqcd_status st);
     lqcd_status succeed();
 

@@ -1,169 +1,10 @@
-// dslash_df.cu -- the hopping term in float-float arithmetic (~48
-// significant bits on the FP32 pipes) for the mixed solver's accurate
-// residual b - Mhat^dag Mhat x: GB300 runs FP64 at a small fraction of its FP32
-// rate, so the reliable updates use float-float storage and arithmetic.
-#include "df64.cuh"
-#include "dslash.cuh"
-#include "spin.cuh"
+// dslash_df.cu -- the hopping term in float-float arithmetic for the mixed
+// solver's accurate residual b - Mhat^dag Mhat x: GB300 runs FP64 at a small
+// fraction of its FP32 rate, so the reliable updates use float-float storage
+// and arithmetic (device code in dslash_df.cuh).
+#include "dslash_df.cuh"
 
 namespace lqcd {
-
-// ---------------------------------------------------------------- float-float kernel
-//
-// The float-float products of the mixed solver's accurate residual are long
-// chains of dependent FP32 operations, so this kernel spreads each output
-// site over three threads, one per colour a.  Each thread first projects
-// colour a of the eight neighbour spinors onto half spinors and leaves them in
-// shared memory; after one barrier it multiplies all three colours of each
-// half spinor by row a of U (column a of U^dag), accumulating exact leading
-// products with a single normalisation per dot product.
-
-constexpr int DF_SITES = 64; // sites per block; blockDim = (64, 3)
-
-// acc += k v with k in {+1, -1, +i, -i} (kind 0..3)
-template <int KIND>
-__device__ __forceinline__ void acc_c(DfAcc &ar, DfAcc &ai, const Cx<Df> &v)
-{
-    if (KIND == 0) {
-        ar.add(v.re);
-        ai.add(v.im);
-    } else if (KIND == 1) {
-        ar.add(-v.re);
-        ai.add(-v.im);
-    } else if (KIND == 2) { // +i v = (-im, re)
-        ar.add(-v.im);
-        ai.add(v.re);
-    } else { // -i v = (im, -re)
-        ar.add(v.im);
-        ai.add(-v.re);
-    }
-}
-
-// rows 2, 3 of (1 + S gamma_mu) from the projected rows (v0, v1): see the table above project()
-template <int MU, int S>
-__device__ __forceinline__ void acc_hop(DfAcc (&ar)[4], DfAcc (&ai)[4], const Cx<Df> &v0, const Cx<Df> &v1)
-{
-    acc_c<0>(ar[0], ai[0], v0);
-    acc_c<0>(ar[1], ai[1], v1);
-    constexpr int MI = S > 0 ? 3 : 2; // -S i
-    constexpr int PI = S > 0 ? 2 : 3; // +S i
-    constexpr int P1 = S > 0 ? 0 : 1; // +S
-    constexpr int M1 = S > 0 ? 1 : 0; // -S
-    if (MU == 0) {
-        acc_c<MI>(ar[2], ai[2], v1);
-        acc_c<MI>(ar[3], ai[3], v0);
-    } else if (MU == 1) {
-        acc_c<P1>(ar[2], ai[2], v1);
-        acc_c<M1>(ar[3], ai[3], v0);
-    } else if (MU == 2) {
-        acc_c<MI>(ar[2], ai[2], v0);
-        acc_c<PI>(ar[3], ai[3], v1);
-    } else {
-        acc_c<P1>(ar[2], ai[2], v0);
-        acc_c<P1>(ar[3], ai[3], v1);
-    }
-}
-
-// colour a of (1 + S gamma_mu) psi at site nb, rows 0 and 1 (the table above project())
-template <int MU, int S>
-__device__ __forceinline__ void project_colour_df(const SpinorRef<PREC_DF> &in, int nb, int a, Cx<Df> &h0,
-                                                  Cx<Df> &h1)
-{
-    Cx<Df> p[4];
-#pragma unroll
-    for (int sp = 0; sp < 4; sp++) {
-        float4 v = ldg(in.d + (size_t)(sp * 3 + a) * in.Vh + nb);
-        p[sp] = Cx<Df>{Df(v.x, v.y), Df(v.z, v.w)};
-    }
-    if (MU == 0) {
-        h0 = p[0] + s_i<S>(p[3]);
-        h1 = p[1] + s_i<S>(p[2]);
-    } else if (MU == 1) {
-        h0 = p[0] - s_1<S>(p[3]);
-        h1 = p[1] + s_1<S>(p[2]);
-    } else if (MU == 2) {
-        h0 = p[0] + s_i<S>(p[2]);
-        h1 = p[1] - s_i<S>(p[3]);
-    } else {
-        h0 = p[0] + s_1<S>(p[2]);
-        h1 = p[1] + s_1<S>(p[3]);
-    }
-}
-
-// the projected half spinors of one block: [hop][row][colour][site], hop 2 mu
-// forward, 2 mu + 1 backward (48 KiB)
-struct DfHalves {
-    float4 h[8][2][3][DF_SITES];
-};
-
-template <int MU, int FS, int BS>
-__device__ __forceinline__ void project_dir_df(DfHalves &sh, const SpinorRef<PREC_DF> &in, int x, int a, int nf,
-                                               int nbk)
-{
-    Cx<Df> h0, h1;
-    project_colour_df<MU, FS>(in, nf, a, h0, h1);
-    sh.h[2 * MU][0][a][x] = df_from<Df>(h0);
-    sh.h[2 * MU][1][a][x] = df_from<Df>(h1);
-    project_colour_df<MU, BS>(in, nbk, a, h0, h1);
-    sh.h[2 * MU + 1][0][a][x] = df_from<Df>(h0);
-    sh.h[2 * MU + 1][1][a][x] = df_from<Df>(h1);
-}
-
-__device__ __forceinline__ Cx<Df> df_cx(float4 v) { return Cx<Df>{Df(v.x, v.y), Df(v.z, v.w)}; }
-
-template <int MU, int FS, int BS>
-__device__ __forceinline__ void hop_dir_df(DfAcc (&ar)[4], DfAcc (&ai)[4], const DfHalves &sh,
-                                           const GaugeRef<PREC_DF> &U, const Geo &g, int cb, int out_par, int x,
-                                           int a, int nbk, bool wrap_f, bool wrap_b)
-{
-    const bool antip = (MU == 3) && g.t_bc < 0;
-    { // forward: row a of U_mu(x)
-        DfAcc r0, i0, r1, i1;
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            float4 w = ldg(U.d + U.idx(MU, out_par, a * 3 + b, cb));
-            Df ur(w.x, w.y), ui(w.z, w.w);
-            const Cx<Df> h0 = df_cx(sh.h[2 * MU][0][b][x]), h1 = df_cx(sh.h[2 * MU][1][b][x]);
-            r0.add_prod(ur, h0.re);
-            r0.sub_prod(ui, h0.im);
-            i0.add_prod(ur, h0.im);
-            i0.add_prod(ui, h0.re);
-            r1.add_prod(ur, h1.re);
-            r1.sub_prod(ui, h1.im);
-            i1.add_prod(ur, h1.im);
-            i1.add_prod(ui, h1.re);
-        }
-        Cx<Df> v0{r0.value(), i0.value()}, v1{r1.value(), i1.value()};
-        if (antip && wrap_f) {
-            v0 = -v0;
-            v1 = -v1;
-        }
-        acc_hop<MU, FS>(ar, ai, v0, v1);
-    }
-    { // backward: column a of U_mu(x - mu), conjugated
-        DfAcc r0, i0, r1, i1;
-#pragma unroll
-        for (int b = 0; b < 3; b++) {
-            float4 w = ldg(U.d + U.idx(MU, 1 - out_par, b * 3 + a, nbk));
-            Df ur(w.x, w.y), ui(w.z, w.w);
-            const Cx<Df> h0 = df_cx(sh.h[2 * MU + 1][0][b][x]), h1 = df_cx(sh.h[2 * MU + 1][1][b][x]);
-            r0.add_prod(ur, h0.re);
-            r0.add_prod(ui, h0.im);
-            i0.add_prod(ur, h0.im);
-            i0.sub_prod(ui, h0.re);
-            r1.add_prod(ur, h1.re);
-            r1.add_prod(ui, h1.im);
-            i1.add_prod(ur, h1.im);
-            i1.sub_prod(ui, h1.re);
-        }
-        Cx<Df> v0{r0.value(), i0.value()}, v1{r1.value(), i1.value()};
-        if (antip && wrap_b) {
-            v0 = -v0;
-            v1 = -v1;
-        }
-        acc_hop<MU, BS>(ar, ai, v0, v1);
-    }
-}
 
 // 4 blocks of 192 threads per SM (80 registers, 4 x 48 KiB of half spinors)
 template <bool DAG, bool XPAY>
@@ -173,39 +14,7 @@ __global__ void __launch_bounds__(DF_SITES * 3, 4) dslash_df_kernel(SpinorRef<PR
 {
     __shared__ DfHalves sh;
     if (skip && *skip) return; // the same for the whole block
-    const int tx = threadIdx.x, a = threadIdx.y;
-    const int cb = blockIdx.x * DF_SITES + tx;
-    const bool live = cb < g.Vh;
-    int c[4], nb[8];
-    bool tf = false, tb = false;
-    constexpr int FS = DAG ? +1 : -1;
-    constexpr int BS = -FS;
-    if (live) {
-        cb_coords(g, cb, out_par, c);
-        cb_neighbours(g, cb, c, nb, tf, tb);
-        project_dir_df<0, FS, BS>(sh, in, tx, a, nb[0], nb[1]);
-        project_dir_df<1, FS, BS>(sh, in, tx, a, nb[2], nb[3]);
-        project_dir_df<2, FS, BS>(sh, in, tx, a, nb[4], nb[5]);
-        project_dir_df<3, FS, BS>(sh, in, tx, a, nb[6], nb[7]);
-    }
-    __syncthreads();
-    if (!live) return;
-    DfAcc ar[4], ai[4];
-    hop_dir_df<0, FS, BS>(ar, ai, sh, U, g, cb, out_par, tx, a, nb[1], false, false);
-    hop_dir_df<1, FS, BS>(ar, ai, sh, U, g, cb, out_par, tx, a, nb[3], false, false);
-    hop_dir_df<2, FS, BS>(ar, ai, sh, U, g, cb, out_par, tx, a, nb[5], false, false);
-    hop_dir_df<3, FS, BS>(ar, ai, sh, U, g, cb, out_par, tx, a, nb[7], tf, tb);
-#pragma unroll
-    for (int sp = 0; sp < 4; sp++) {
-        Cx<Df> v{ar[sp].value(), ai[sp].value()};
-        size_t k = (size_t)(sp * 3 + a) * out.Vh + cb;
-        if (XPAY) {
-            float4 xv = x.d[k];
-            Cx<Df> xc{Df(xv.x, xv.y), Df(xv.z, xv.w)};
-            v = xc + b * v;
-        }
-        out.d[k] = df_from<Df>(v);
-    }
+    df_hop_block<DAG, XPAY>(sh, out, in, U, g, out_par, x, b, blockIdx.x);
 }
 
 lqcd_status dslash_df_launch(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int dagger,

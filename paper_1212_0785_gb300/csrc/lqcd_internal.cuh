@@ -789,7 +789,7 @@ __host__ inline MomRef mom_ref(const lqcd_field *f) { return {reinterpret_cast<d
 // writes partials[k * nblocks + blockIdx.x].  Every thread of the block must
 // call it (inactive threads pass zeros).
 template <int N, int BLOCK>
-__device__ __forceinline__ void block_sum_store(double (&v)[N], double *partials, int nblocks)
+__device__ __forceinline__ void block_sum_store(double (&v)[N], double *partials, int nblocks, int slot)
 {
     static_assert(BLOCK % 32 == 0 && BLOCK <= 1024, "block size");
     __shared__ double sh[N][BLOCK / 32];
@@ -810,9 +810,16 @@ __device__ __forceinline__ void block_sum_store(double (&v)[N], double *partials
             double x = lane < BLOCK / 32 ? sh[k][lane] : 0.0;
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-            if (lane == 0) partials[(size_t)k * nblocks + blockIdx.x] = x;
+            if (lane == 0) partials[(size_t)k * nblocks + slot] = x;
         }
     }
+}
+
+// the block's sums of v into partials[k * nblocks + blockIdx.x]
+template <int N, int BLOCK>
+__device__ __forceinline__ void block_sum_store(double (&v)[N], double *partials, int nblocks)
+{
+    block_sum_store<N, BLOCK>(v, partials, nblocks, (int)blockIdx.x);
 }
 
 // The same for one value held in the kernel's working precision R: the warp
