@@ -51,6 +51,16 @@ __device__ __forceinline__ Df operator+(Df a, Df b)
 
 __device__ __forceinline__ Df operator-(Df a) { return Df(-a.hi, -a.lo); }
 
+// a + b with the same error as operator+, left unnormalised (the pair is
+// only ever an operand of the exact products below)
+__device__ __forceinline__ Df df_add_raw(Df a, Df b)
+{
+    float s = a.hi + b.hi;
+    float v = s - a.hi;
+    float e = (a.hi - (s - v)) + (b.hi - v);
+    return Df(s, e + (a.lo + b.lo));
+}
+
 __device__ __forceinline__ Df operator-(Df a, Df b) { return a + (-b); }
 
 __device__ __forceinline__ Df operator*(Df a, Df b)
@@ -85,6 +95,20 @@ struct DfAcc {
         s = t;
     }
     __device__ __forceinline__ void sub_prod(Df a, Df b) { add_prod(Df(-a.hi, -a.lo), b); }
+    // the first product of a sum: nothing to add it to, so no two-sum
+    __device__ __forceinline__ void set_prod(Df a, Df b)
+    {
+        s = a.hi * b.hi;
+        float e = fmaf(a.hi, b.hi, -s);
+        e = fmaf(a.hi, b.lo, e);
+        c = fmaf(a.lo, b.hi, e);
+    }
+    __device__ __forceinline__ void set_neg_prod(Df a, Df b) { set_prod(Df(-a.hi, -a.lo), b); }
+    __device__ __forceinline__ void set(Df a)
+    {
+        s = a.hi;
+        c = a.lo;
+    }
     __device__ __forceinline__ void add(Df a)
     {
         float t = s + a.hi;
@@ -93,6 +117,10 @@ struct DfAcc {
         s = t;
     }
     __device__ __forceinline__ Df value() const { return df_fast_two_sum_any(s, c); }
+    // the pair as it stands, not normalised: exact to the bits of c, and a
+    // valid operand of add, add_prod and set_prod, which never assume |c| <
+    // ulp(s)
+    __device__ __forceinline__ Df raw() const { return Df(s, c); }
     // |s| >= |c| holds unless the sum cancelled; normalise with a full two-sum
     __device__ __forceinline__ static Df df_fast_two_sum_any(float a, float b)
     {

@@ -21,48 +21,49 @@ namespace lqcd {
 
 constexpr int DF_SITES = 64; // sites per block; blockDim = (64, 3)
 
-// acc += k v with k in {+1, -1, +i, -i} (kind 0..3)
-template <int KIND>
+// acc += k v with k in {+1, -1, +i, -i} (kind 0..3); FIRST: acc = k v
+template <int KIND, bool FIRST>
 __device__ __forceinline__ void acc_c(DfAcc &ar, DfAcc &ai, const Cx<Df> &v)
 {
-    if (KIND == 0) {
-        ar.add(v.re);
-        ai.add(v.im);
-    } else if (KIND == 1) {
-        ar.add(-v.re);
-        ai.add(-v.im);
-    } else if (KIND == 2) { // +i v = (-im, re)
-        ar.add(-v.im);
-        ai.add(v.re);
-    } else { // -i v = (im, -re)
-        ar.add(v.im);
-        ai.add(-v.re);
+    const Df r = KIND == 0 ? v.re : KIND == 1 ? -v.re : KIND == 2 ? -v.im : v.im;
+    const Df i = KIND == 0 ? v.im : KIND == 1 ? -v.im : KIND == 2 ? v.re : -v.re;
+    if (FIRST) {
+        ar.set(r);
+        ai.set(i);
+    } else {
+        ar.add(r);
+        ai.add(i);
     }
 }
 
 // rows 2, 3 of (1 + S gamma_mu) from the projected rows (v0, v1): see the table above project()
-template <int MU, int S>
+template <int MU, int S, bool FIRST>
 __device__ __forceinline__ void acc_hop(DfAcc (&ar)[4], DfAcc (&ai)[4], const Cx<Df> &v0, const Cx<Df> &v1)
 {
-    acc_c<0>(ar[0], ai[0], v0);
-    acc_c<0>(ar[1], ai[1], v1);
+    acc_c<0, FIRST>(ar[0], ai[0], v0);
+    acc_c<0, FIRST>(ar[1], ai[1], v1);
     constexpr int MI = S > 0 ? 3 : 2; // -S i
     constexpr int PI = S > 0 ? 2 : 3; // +S i
     constexpr int P1 = S > 0 ? 0 : 1; // +S
     constexpr int M1 = S > 0 ? 1 : 0; // -S
     if (MU == 0) {
-        acc_c<MI>(ar[2], ai[2], v1);
-        acc_c<MI>(ar[3], ai[3], v0);
+        acc_c<MI, FIRST>(ar[2], ai[2], v1);
+        acc_c<MI, FIRST>(ar[3], ai[3], v0);
     } else if (MU == 1) {
-        acc_c<P1>(ar[2], ai[2], v1);
-        acc_c<M1>(ar[3], ai[3], v0);
+        acc_c<P1, FIRST>(ar[2], ai[2], v1);
+        acc_c<M1, FIRST>(ar[3], ai[3], v0);
     } else if (MU == 2) {
-        acc_c<MI>(ar[2], ai[2], v0);
-        acc_c<PI>(ar[3], ai[3], v1);
+        acc_c<MI, FIRST>(ar[2], ai[2], v0);
+        acc_c<PI, FIRST>(ar[3], ai[3], v1);
     } else {
-        acc_c<P1>(ar[2], ai[2], v0);
-        acc_c<P1>(ar[3], ai[3], v1);
+        acc_c<P1, FIRST>(ar[2], ai[2], v0);
+        acc_c<P1, FIRST>(ar[3], ai[3], v1);
     }
+}
+
+__device__ __forceinline__ Cx<Df> cx_add_raw(const Cx<Df> &a, const Cx<Df> &b)
+{
+    return Cx<Df>{df_add_raw(a.re, b.re), df_add_raw(a.im, b.im)};
 }
 
 // colour a of (1 + S gamma_mu) psi at site nb, rows 0 and 1 (the table above project())
@@ -76,18 +77,19 @@ __device__ __forceinline__ void project_colour_df(const SpinorRef<PREC_DF> &in, 
         float4 v = ldg(in.d + (size_t)(sp * 3 + a) * in.Vh + nb);
         p[sp] = Cx<Df>{Df(v.x, v.y), Df(v.z, v.w)};
     }
+    // sums left unnormalised: they only enter the exact link products
     if (MU == 0) {
-        h0 = p[0] + s_i<S>(p[3]);
-        h1 = p[1] + s_i<S>(p[2]);
+        h0 = cx_add_raw(p[0], s_i<S>(p[3]));
+        h1 = cx_add_raw(p[1], s_i<S>(p[2]));
     } else if (MU == 1) {
-        h0 = p[0] - s_1<S>(p[3]);
-        h1 = p[1] + s_1<S>(p[2]);
+        h0 = cx_add_raw(p[0], -s_1<S>(p[3]));
+        h1 = cx_add_raw(p[1], s_1<S>(p[2]));
     } else if (MU == 2) {
-        h0 = p[0] + s_i<S>(p[2]);
-        h1 = p[1] - s_i<S>(p[3]);
+        h0 = cx_add_raw(p[0], s_i<S>(p[2]));
+        h1 = cx_add_raw(p[1], -s_i<S>(p[3]));
     } else {
-        h0 = p[0] + s_1<S>(p[2]);
-        h1 = p[1] + s_1<S>(p[3]);
+        h0 = cx_add_raw(p[0], s_1<S>(p[2]));
+        h1 = cx_add_raw(p[1], s_1<S>(p[3]));
     }
 }
 
@@ -112,6 +114,8 @@ __device__ __forceinline__ void project_dir_df(DfHalves &sh, const SpinorRef<PRE
 
 __device__ __forceinline__ Cx<Df> df_cx(float4 v) { return Cx<Df>{Df(v.x, v.y), Df(v.z, v.w)}; }
 
+// Each dot product starts from its first exact product and its sums reach the
+// output rows unnormalised; only the output is normalised.
 template <int MU, int FS, int BS>
 __device__ __forceinline__ void hop_dir_df(DfAcc (&ar)[4], DfAcc (&ai)[4], const DfHalves &sh,
                                            const GaugeRef<PREC_DF> &U, const Geo &g, int cb, int out_par, int x,
@@ -125,21 +129,28 @@ __device__ __forceinline__ void hop_dir_df(DfAcc (&ar)[4], DfAcc (&ai)[4], const
             float4 w = ldg(U.d + U.idx(MU, out_par, a * 3 + b, cb));
             Df ur(w.x, w.y), ui(w.z, w.w);
             const Cx<Df> h0 = df_cx(sh.h[2 * MU][0][b][x]), h1 = df_cx(sh.h[2 * MU][1][b][x]);
-            r0.add_prod(ur, h0.re);
+            if (b == 0) {
+                r0.set_prod(ur, h0.re);
+                i0.set_prod(ur, h0.im);
+                r1.set_prod(ur, h1.re);
+                i1.set_prod(ur, h1.im);
+            } else {
+                r0.add_prod(ur, h0.re);
+                i0.add_prod(ur, h0.im);
+                r1.add_prod(ur, h1.re);
+                i1.add_prod(ur, h1.im);
+            }
             r0.sub_prod(ui, h0.im);
-            i0.add_prod(ur, h0.im);
             i0.add_prod(ui, h0.re);
-            r1.add_prod(ur, h1.re);
             r1.sub_prod(ui, h1.im);
-            i1.add_prod(ur, h1.im);
             i1.add_prod(ui, h1.re);
         }
-        Cx<Df> v0{r0.value(), i0.value()}, v1{r1.value(), i1.value()};
+        Cx<Df> v0{r0.raw(), i0.raw()}, v1{r1.raw(), i1.raw()};
         if (antip && wrap_f) {
             v0 = -v0;
             v1 = -v1;
         }
-        acc_hop<MU, FS>(ar, ai, v0, v1);
+        acc_hop<MU, FS, MU == 0>(ar, ai, v0, v1);
     }
     { // backward: column a of U_mu(x - mu), conjugated
         DfAcc r0, i0, r1, i1;
@@ -148,21 +159,28 @@ __device__ __forceinline__ void hop_dir_df(DfAcc (&ar)[4], DfAcc (&ai)[4], const
             float4 w = ldg(U.d + U.idx(MU, 1 - out_par, b * 3 + a, nbk));
             Df ur(w.x, w.y), ui(w.z, w.w);
             const Cx<Df> h0 = df_cx(sh.h[2 * MU + 1][0][b][x]), h1 = df_cx(sh.h[2 * MU + 1][1][b][x]);
-            r0.add_prod(ur, h0.re);
+            if (b == 0) {
+                r0.set_prod(ur, h0.re);
+                i0.set_prod(ur, h0.im);
+                r1.set_prod(ur, h1.re);
+                i1.set_prod(ur, h1.im);
+            } else {
+                r0.add_prod(ur, h0.re);
+                i0.add_prod(ur, h0.im);
+                r1.add_prod(ur, h1.re);
+                i1.add_prod(ur, h1.im);
+            }
             r0.add_prod(ui, h0.im);
-            i0.add_prod(ur, h0.im);
             i0.sub_prod(ui, h0.re);
-            r1.add_prod(ur, h1.re);
             r1.add_prod(ui, h1.im);
-            i1.add_prod(ur, h1.im);
             i1.sub_prod(ui, h1.re);
         }
-        Cx<Df> v0{r0.value(), i0.value()}, v1{r1.value(), i1.value()};
+        Cx<Df> v0{r0.raw(), i0.raw()}, v1{r1.raw(), i1.raw()};
         if (antip && wrap_b) {
             v0 = -v0;
             v1 = -v1;
         }
-        acc_hop<MU, BS>(ar, ai, v0, v1);
+        acc_hop<MU, BS, false>(ar, ai, v0, v1);
     }
 }
 
