@@ -417,7 +417,11 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": (f"f32 math ({args.sloppy} storage in the solver, {args.force_prec} forces); f64 master "
                       f"links/momenta, residuals, dots, link update, dH"),
-            "data": "synthetic", "config": config_block(args, args.sloppy), "gpu_launches": launches,
+            "data": "synthetic",
+            "config": dict(config_block(args, args.sloppy),
+                           dslash_form={0: "gathered", 1: "tma_staged_t", 2: "prefetched_links"}.get(
+                               lqcd.dslash_staging(), "?")),
+            "gpu_launches": launches,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "fp64_gpu_path": fp64,
             "physics": {"acceptance": float(np.mean(acc)), "dH": [i["dH"] for i in infos],
                         "plaquette": [i["plaq"] for i in infos],

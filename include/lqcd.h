@@ -210,17 +210,21 @@ lqcd_status lqcd_eta_refresh(lqcd_field *eta, uint32_t seed, uint32_t chain, uin
  * spinors of precision q (q in F32, F16N, BF16; FP32 arithmetic). */
 lqcd_status lqcd_dslash(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int dagger, void *stream);
 
-/* The FP16+norm hopping term has a second form for lattices with Lx/2 * Ly a
- * multiple of 128: each block of 128 output sites stages its +-z and +-t
- * neighbour spinors and the links it needs from them in shared memory with
- * bulk asynchronous copies (the TMA engine of sm_90+) before computing;
- * results are bitwise those of the first form.  It is on by default;
- * lqcd_dslash_staging(0) switches it off, (1) on, (-1) queries; returns the
- * previous setting (process-wide).  A block's wait for its copies is bounded:
- * if one ever gives up, lqcd_dslash_check (which synchronises stream) returns
- * LQCD_ETIMEOUT once and the results since the last check are invalid; every
- * CG solve makes that check before it returns. */
-int lqcd_dslash_staging(int enable);
+/* The FP16+norm hopping term comes in three forms with bitwise-equal results:
+ *   0  every operand gathered by its thread;
+ *   1  (lattices with Lx/2 * Ly a multiple of 128) each block of 128 output
+ *      sites first stages its +-t neighbour spinors and the links it needs
+ *      from them in shared memory with bulk asynchronous copies (the TMA engine
+ *      of sm_90+); elsewhere form 0 runs;
+ *   2  (the default) each thread first starts asynchronous copies (cp.async)
+ *      of its eight links into shared memory, then gathers the neighbour
+ *      spinors and waits for each direction's links only when it needs them.
+ * lqcd_dslash_staging(mode) selects the form (0, 1, 2; -1 queries) and returns
+ * the previous one (process-wide).  A form-1 block's wait for its copies is
+ * bounded: if one ever gives up, lqcd_dslash_check (which synchronises stream)
+ * returns LQCD_ETIMEOUT once and the results since the last check are invalid;
+ * every CG solve makes that check before it returns. */
+int lqcd_dslash_staging(int mode);
 lqcd_status lqcd_dslash_check(void *stream);
 
 /* out_e = Mhat in_e = in_e - kappa^2 Deo Doe in_e (dagger: Mhat^dag).  EVEN

@@ -27,9 +27,27 @@ constexpr int BCHUNK = 4;
 
 // ---------------------------------------------------------------- kernels
 
+// D (DAG: D^dag) at site cb of one system: FP16+norm with the links
+// prefetched into shared memory (the single-field default), else gathered;
+// both give the same bits
+template <lqcd_prec SP, bool DAG>
+__device__ __forceinline__ Sp<float> sys_site(const SpinorRef<SP> &in, const GaugeRef<SP> &U, const Geo &g, int cb,
+                                              int out_par)
+{
+    if constexpr (SP == LQCD_F16N)
+        return prefetch_site<float, DAG>(in, U, g, cb, out_par);
+    else
+        return dslash_site<float, SP, SP, DAG>(in, U, g, cb, out_par);
+}
+
+// 7 blocks of 128 per SM for the FP16+norm kernels (72 registers, 24 KiB of
+// prefetched links each)
+template <lqcd_prec SP>
+constexpr int min_blocks() { return SP == LQCD_F16N ? 7 : 1; }
+
 // step 0: tmp = D_oe p; step 2: tmp = D_oe^dag-hop t
 template <lqcd_prec SP, bool DAG>
-__global__ void __launch_bounds__(DS_BLOCK) batch_dslash_plain(const SysDesc<SP> *sys, const int2 *bmap)
+__global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP>()) batch_dslash_plain(const SysDesc<SP> *sys, const int2 *bmap)
 {
     const int2 m = bmap[blockIdx.x];
     const SysDesc<SP> &d = sys[m.x];
@@ -37,12 +55,12 @@ __global__ void __launch_bounds__(DS_BLOCK) batch_dslash_plain(const SysDesc<SP>
     int cb = m.y * DS_BLOCK + threadIdx.x;
     if (cb >= d.g.Vh) return;
     const SpinorRef<SP> &in = DAG ? d.t : d.p;
-    d.tmp.store(cb, dslash_site<float, SP, SP, DAG>(in, d.U, d.g, cb, 1));
+    d.tmp.store(cb, sys_site<SP, DAG>(in, d.U, d.g, cb, 1));
 }
 
 // step 1: t = p - kappa^2 D_eo tmp, block sums of |t|^2
 template <lqcd_prec SP>
-__global__ void __launch_bounds__(DS_BLOCK) batch_dslash_xpay(const SysDesc<SP> *sys, const int2 *bmap)
+__global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP>()) batch_dslash_xpay(const SysDesc<SP> *sys, const int2 *bmap)
 {
     const int2 m = bmap[blockIdx.x];
     const SysDesc<SP> &d = sys[m.x];
@@ -50,7 +68,7 @@ __global__ void __launch_bounds__(DS_BLOCK) batch_dslash_xpay(const SysDesc<SP> 
     int cb = m.y * DS_BLOCK + threadIdx.x;
     float n2 = 0.f;
     if (cb < d.g.Vh) {
-        Sp<float> v = dslash_site<float, SP, SP, false>(d.tmp, d.U, d.g, cb, 0);
+        Sp<float> v = sys_site<SP, false>(d.tmp, d.U, d.g, cb, 0);
         Sp<float> pv = d.p.template load_rw<float>(cb);
 #pragma unroll
         for (int a = 0; a < 4; a++)
@@ -77,7 +95,7 @@ __global__ void __launch_bounds__(DS_BLOCK) batch_dslash_xpay(const SysDesc<SP> 
 
 // step 3: Ap = t - kappa^2 D_eo^dag-hop tmp; xs += alpha p; r -= alpha Ap; block sums of |r|^2
 template <lqcd_prec SP>
-__global__ void __launch_bounds__(DS_BLOCK) batch_dslash_cg(const SysDesc<SP> *sys, const int2 *bmap)
+__global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP>()) batch_dslash_cg(const SysDesc<SP> *sys, const int2 *bmap)
 {
     const int2 m = bmap[blockIdx.x];
     const SysDesc<SP> &d = sys[m.x];
@@ -86,7 +104,7 @@ __global__ void __launch_bounds__(DS_BLOCK) batch_dslash_cg(const SysDesc<SP> *s
     int cb = m.y * DS_BLOCK + threadIdx.x;
     float n2 = 0.f;
     if (cb < d.g.Vh) {
-        Sp<float> ap = dslash_site<float, SP, SP, true>(d.tmp, d.U, d.g, cb, 0);
+        Sp<float> ap = sys_site<SP, true>(d.tmp, d.U, d.g, cb, 0);
         {
             Sp<float> tv = d.t.template load_rw<float>(cb);
 #pragma unroll

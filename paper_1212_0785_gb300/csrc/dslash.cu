@@ -22,30 +22,33 @@ namespace lqcd {
 
 // ---------------------------------------------------------------- kernels
 
-// Sp of D in at site cb.  STAGED (FP16+norm, geometry from staging_fits):
-// the block stages its far operands first; every thread of the block calls it.
-// (The other precisions' STAGED instances are never launched.)
-template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, bool STAGED>
+// Sp of D in at site cb.  FORM 1 (staged; FP16+norm, geometry from
+// staging_fits): the block stages its far operands first, and every thread of
+// the block calls it.  FORM 2 (FP16+norm): the thread prefetches its links.
+// (The other precisions' FORM 1, 2 instances are never launched.)
+template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, int FORM>
 __device__ __forceinline__ Sp<R> site_value(const SpinorRef<SP> &in, const GaugeRef<GP> &U, const Geo &g, int cb,
                                             int out_par)
 {
-    if constexpr (STAGED && SP == LQCD_F16N && GP == LQCD_F16N)
+    if constexpr (FORM == 1 && SP == LQCD_F16N && GP == LQCD_F16N)
         return staged_site<R, DAG>(in, U, g, cb, out_par);
+    else if constexpr (FORM == 2 && SP == LQCD_F16N && GP == LQCD_F16N)
+        return prefetch_site<R, DAG>(in, U, g, cb, out_par);
     else
         return dslash_site<R, SP, GP, DAG>(in, U, g, cb, out_par);
 }
 
-template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, bool STAGED>
+template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, int FORM>
 __device__ __forceinline__ void plain_body(SpinorRef<SP> out, SpinorRef<SP> in, GaugeRef<GP> U,
                                                                  Geo g, int out_par, const int *skip)
 {
     if (skip && *skip) return;
     int cb = blockIdx.x * DS_BLOCK + threadIdx.x;
-    if (!(STAGED && SP == LQCD_F16N) && cb >= g.Vh) return;
-    out.store(cb, site_value<R, SP, GP, DAG, STAGED>(in, U, g, cb, out_par));
+    if (!(FORM == 1 && SP == LQCD_F16N) && cb >= g.Vh) return;
+    out.store(cb, site_value<R, SP, GP, DAG, FORM>(in, U, g, cb, out_par));
 }
 
-template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, bool STAGED>
+template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, int FORM>
 __device__ __forceinline__ void xpay_body(SpinorRef<SP> out, SpinorRef<SP> in, GaugeRef<GP> U,
                                                                 Geo g, int out_par, SpinorRef<SP> x, R b,
                                                                 double *partials, int nblocks, const int *skip)
@@ -53,8 +56,8 @@ __device__ __forceinline__ void xpay_body(SpinorRef<SP> out, SpinorRef<SP> in, G
     if (skip && *skip) return;
     int cb = blockIdx.x * DS_BLOCK + threadIdx.x;
     R n2 = R(0);
-    if ((STAGED && SP == LQCD_F16N) || cb < g.Vh) {
-        Sp<R> d = site_value<R, SP, GP, DAG, STAGED>(in, U, g, cb, out_par);
+    if ((FORM == 1 && SP == LQCD_F16N) || cb < g.Vh) {
+        Sp<R> d = site_value<R, SP, GP, DAG, FORM>(in, U, g, cb, out_par);
         Sp<R> xv = x.template load_rw<R>(cb);
 #pragma unroll
         for (int a = 0; a < 4; a++)
@@ -66,7 +69,7 @@ __device__ __forceinline__ void xpay_body(SpinorRef<SP> out, SpinorRef<SP> in, G
     if (partials) block_sum_store_wp<DS_BLOCK>(n2, partials);
 }
 
-template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, lqcd_prec XP, bool STAGED>
+template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, lqcd_prec XP, int FORM>
 __device__ __forceinline__ void cg_body(SpinorRef<SP> in, GaugeRef<GP> U, Geo g, int out_par,
                                                               SpinorRef<SP> t, R b, SpinorRef<XP> xs, SpinorRef<SP> r,
                                                               SpinorRef<SP> p, double *partials, int nblocks,
@@ -76,8 +79,8 @@ __device__ __forceinline__ void cg_body(SpinorRef<SP> in, GaugeRef<GP> U, Geo g,
     const R alpha = (R)sc->alpha;
     int cb = blockIdx.x * DS_BLOCK + threadIdx.x;
     R n2 = R(0);
-    if ((STAGED && SP == LQCD_F16N) || cb < g.Vh) {
-        Sp<R> ap = site_value<R, SP, GP, DAG, STAGED>(in, U, g, cb, out_par);
+    if ((FORM == 1 && SP == LQCD_F16N) || cb < g.Vh) {
+        Sp<R> ap = site_value<R, SP, GP, DAG, FORM>(in, U, g, cb, out_par);
         {
             Sp<R> tv = t.template load_rw<R>(cb);
 #pragma unroll
@@ -115,21 +118,21 @@ template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
 __global__ void __launch_bounds__(DS_BLOCK) dslash_plain_kernel(SpinorRef<SP> out, SpinorRef<SP> in, GaugeRef<GP> U,
                                                                  Geo g, int out_par, const int *skip)
 {
-    plain_body<R, SP, GP, DAG, false>(out, in, U, g, out_par, skip);
+    plain_body<R, SP, GP, DAG, 0>(out, in, U, g, out_par, skip);
 }
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
 __global__ void __launch_bounds__(DS_BLOCK, 7) dslash_plain_staged_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
                                                                            GaugeRef<GP> U, Geo g, int out_par,
                                                                            const int *skip)
 {
-    plain_body<R, SP, GP, DAG, true>(out, in, U, g, out_par, skip);
+    plain_body<R, SP, GP, DAG, 1>(out, in, U, g, out_par, skip);
 }
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
 __global__ void __launch_bounds__(DS_BLOCK) dslash_xpay_kernel(SpinorRef<SP> out, SpinorRef<SP> in, GaugeRef<GP> U,
                                                                 Geo g, int out_par, SpinorRef<SP> x, R b,
                                                                 double *partials, int nblocks, const int *skip)
 {
-    xpay_body<R, SP, GP, DAG, false>(out, in, U, g, out_par, x, b, partials, nblocks, skip);
+    xpay_body<R, SP, GP, DAG, 0>(out, in, U, g, out_par, x, b, partials, nblocks, skip);
 }
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
 __global__ void __launch_bounds__(DS_BLOCK, 7) dslash_xpay_staged_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(DS_BLOCK, 7) dslash_xpay_staged_kernel(SpinorR
                                                                           SpinorRef<SP> x, R b, double *partials,
                                                                           int nblocks, const int *skip)
 {
-    xpay_body<R, SP, GP, DAG, true>(out, in, U, g, out_par, x, b, partials, nblocks, skip);
+    xpay_body<R, SP, GP, DAG, 1>(out, in, U, g, out_par, x, b, partials, nblocks, skip);
 }
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, lqcd_prec XP>
 __global__ void __launch_bounds__(DS_BLOCK) dslash_cg_kernel(SpinorRef<SP> in, GaugeRef<GP> U, Geo g, int out_par,
@@ -145,7 +148,7 @@ __global__ void __launch_bounds__(DS_BLOCK) dslash_cg_kernel(SpinorRef<SP> in, G
                                                               SpinorRef<SP> p, double *partials, int nblocks,
                                                               const CgScalars *sc)
 {
-    cg_body<R, SP, GP, DAG, XP, false>(in, U, g, out_par, t, b, xs, r, p, partials, nblocks, sc);
+    cg_body<R, SP, GP, DAG, XP, 0>(in, U, g, out_par, t, b, xs, r, p, partials, nblocks, sc);
 }
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, lqcd_prec XP>
 __global__ void __launch_bounds__(DS_BLOCK, 7) dslash_cg_staged_kernel(SpinorRef<SP> in, GaugeRef<GP> U, Geo g,
@@ -154,7 +157,33 @@ __global__ void __launch_bounds__(DS_BLOCK, 7) dslash_cg_staged_kernel(SpinorRef
                                                                         SpinorRef<SP> p, double *partials,
                                                                         int nblocks, const CgScalars *sc)
 {
-    cg_body<R, SP, GP, DAG, XP, true>(in, U, g, out_par, t, b, xs, r, p, partials, nblocks, sc);
+    cg_body<R, SP, GP, DAG, XP, 1>(in, U, g, out_par, t, b, xs, r, p, partials, nblocks, sc);
+}
+
+// FP16+norm with prefetched links (7 blocks of 128 per SM, 24 KiB each)
+template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
+__global__ void __launch_bounds__(DS_BLOCK, 7) dslash_plain_prefetch_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
+                                                                             GaugeRef<GP> U, Geo g, int out_par,
+                                                                             const int *skip)
+{
+    plain_body<R, SP, GP, DAG, 2>(out, in, U, g, out_par, skip);
+}
+template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
+__global__ void __launch_bounds__(DS_BLOCK, 7) dslash_xpay_prefetch_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
+                                                                            GaugeRef<GP> U, Geo g, int out_par,
+                                                                            SpinorRef<SP> x, R b, double *partials,
+                                                                            int nblocks, const int *skip)
+{
+    xpay_body<R, SP, GP, DAG, 2>(out, in, U, g, out_par, x, b, partials, nblocks, skip);
+}
+template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, lqcd_prec XP>
+__global__ void __launch_bounds__(DS_BLOCK, 7) dslash_cg_prefetch_kernel(SpinorRef<SP> in, GaugeRef<GP> U, Geo g,
+                                                                          int out_par, SpinorRef<SP> t, R b,
+                                                                          SpinorRef<XP> xs, SpinorRef<SP> r,
+                                                                          SpinorRef<SP> p, double *partials,
+                                                                          int nblocks, const CgScalars *sc)
+{
+    cg_body<R, SP, GP, DAG, XP, 2>(in, U, g, out_par, t, b, xs, r, p, partials, nblocks, sc);
 }
 
 // ---------------------------------------------------------------- dispatch
@@ -188,20 +217,25 @@ struct ArithOf<PREC_DF> {
     using type = Df;
 };
 
-// the staged FP16+norm kernels: on unless switched off by lqcd_dslash_staging(0)
-static std::atomic<int> g_staging{1};
+// the FP16+norm form: 2 prefetched links (default), 1 staged, 0 gathered
+static std::atomic<int> g_staging{2};
 
 template <lqcd_prec P, lqcd_prec GP>
-static bool use_staging(const Geo &g)
+static int use_staging(const Geo &g)
 {
-    return P == LQCD_F16N && GP == LQCD_F16N && g_staging.load(std::memory_order_relaxed) && staging_fits(g);
+    if (P != LQCD_F16N || GP != LQCD_F16N) return 0;
+    const int f = g_staging.load(std::memory_order_relaxed);
+    if (f == 2) return 2;
+    return f == 1 && staging_fits(g) ? 1 : 0;
 }
 
-// launch K<STAGED> with the staged variant where it applies
-#define LQCD_LAUNCH_STAGED(staged, kern, targs, grid, args)                                                          \
+// launch kernel K in the form chosen by use_staging
+#define LQCD_LAUNCH_STAGED(form, kern, targs, grid, args)                                                            \
     do {                                                                                                             \
-        if (staged)                                                                                                  \
+        if (form == 1)                                                                                               \
             kern##_staged_kernel<LQCD_UNPAREN targs><<<grid, DS_BLOCK, 0, s>>> args;                                 \
+        else if (form == 2)                                                                                          \
+            kern##_prefetch_kernel<LQCD_UNPAREN targs><<<grid, DS_BLOCK, 0, s>>> args;                               \
         else                                                                                                         \
             kern##_kernel<LQCD_UNPAREN targs><<<grid, DS_BLOCK, 0, s>>> args;                                        \
     } while (0)
@@ -214,7 +248,7 @@ static void launch_plain(lqcd_field *out, const lqcd_field *U, const lqcd_field 
     using R = typename ArithOf<P>::type;
     Geo g = make_geo(in->lat);
     int nb = dslash_blocks(g.Vh);
-    const bool st = use_staging<P, GP>(g);
+    const int st = use_staging<P, GP>(g);
     if (dagger)
         LQCD_LAUNCH_STAGED(st, dslash_plain, (R, P, GP, true), nb,
                            (spinor_ref<P>(out), spinor_ref<P>(in), gauge_ref<GP>(U), g, out_parity(out), skip));
@@ -230,7 +264,7 @@ static void launch_xpay(lqcd_field *out, const lqcd_field *U, const lqcd_field *
     using R = typename ArithOf<P>::type;
     Geo g = make_geo(in->lat);
     int nb = dslash_blocks(g.Vh);
-    const bool st = use_staging<P, GP>(g);
+    const int st = use_staging<P, GP>(g);
     if (dagger)
         LQCD_LAUNCH_STAGED(st, dslash_xpay, (R, P, GP, true), nb,
                            (spinor_ref<P>(out), spinor_ref<P>(in), gauge_ref<GP>(U), g, out_parity(out),
@@ -250,7 +284,7 @@ static void launch_cg(const lqcd_field *U, const lqcd_field *in, int dagger, con
     Geo g = make_geo(in->lat);
     int nb = dslash_blocks(g.Vh);
     int op = out_parity(t);
-    const bool st = use_staging<P, P>(g);
+    const int st = use_staging<P, P>(g);
     if (dagger)
         LQCD_LAUNCH_STAGED(st, dslash_cg, (R, P, P, true, XP), nb,
                            (spinor_ref<P>(in), gauge_ref<P>(U), g, op, spinor_ref<P>(t), (R)b, spinor_ref<XP>(xs),
@@ -275,7 +309,7 @@ lqcd_status dslash_staging_check(cudaStream_t s)
 
 int dslash_staging_set(int enable)
 {
-    return enable < 0 ? g_staging.load() : g_staging.exchange(enable ? 1 : 0);
+    return enable < 0 ? g_staging.load() : g_staging.exchange(enable >= 2 ? 2 : enable ? 1 : 0);
 }
 
 lqcd_status dslash_plain(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int dagger, const int *skip,

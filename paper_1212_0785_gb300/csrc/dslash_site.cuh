@@ -2,6 +2,7 @@
 // single-field kernels (dslash.cu) and the multi-system kernels (batch.cu).
 #pragma once
 
+#include "dslash.cuh"
 #include "spin.cuh"
 
 namespace lqcd {
@@ -91,6 +92,86 @@ __device__ __forceinline__ R sp_norm2(const Sp<R> &s)
 #pragma unroll
         for (int b = 0; b < 3; b++) n = n + norm2(s.c[a][b]);
     return n;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// ---------------------------------------------------------------- prefetched links
+//
+// The other form that keeps the link loads off the critical path: each thread
+// first starts asynchronous copies (cp.async, 8 bytes each) of its own eight
+// links into shared memory, one commit group per direction, then walks the
+// directions gathering the neighbour spinors as usual and waits for a
+// direction's group only when it needs that direction's links.  Each thread
+// reads back only what it copied, so no block barrier is involved; tail
+// threads past Vh take no part.  Same arithmetic, same order as dslash_site.
+// Blocks of DS_BLOCK threads (the single-field kernels of dslash.cu and the
+// multi-system kernels of batch.cu).
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+struct LinkPrefetch {
+    uint2 u[4][2][3][DS_BLOCK]; // [mu][forward, backward][chunk][thread]: 24 KiB
+};
+
+template <typename R, bool DAG>
+__device__ __forceinline__ Sp<R> prefetch_site(const SpinorRef<LQCD_F16N> &in, const GaugeRef<LQCD_F16N> &U,
+                                               const Geo &g, int cb, int out_par)
+{
+    __shared__ LinkPrefetch lp;
+    const int i = threadIdx.x;
+    int c[4], nb[8];
+    bool tf, tb;
+    cb_coords(g, cb, out_par, c);
+    cb_neighbours(g, cb, c, nb, tf, tb);
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            cp_async8(&lp.u[mu][0][k][i], U.d + U.idx(mu, out_par, k, cb));
+            cp_async8(&lp.u[mu][1][k][i], U.d + U.idx(mu, 1 - out_par, k, nb[2 * mu + 1]));
+        }
+        cp_async_commit();
+    }
+    constexpr int FS = DAG ? +1 : -1;
+    constexpr int BS = -FS;
+    const bool antip = g.t_bc < 0;
+    Sp<R> acc = sp_zero<R>();
+    R sc;
+    Sp<R> psi;
+#define LQCD_PF_LINK(mu, f) U.template decode<R>(lp.u[mu][f][0][i], lp.u[mu][f][1][i], lp.u[mu][f][2][i])
+    psi = in.template load_scaled<R>(nb[0], sc);
+    cp_async_wait<3>();
+    hop_values<0, FS, true>(acc, psi, sc, LQCD_PF_LINK(0, 0), false);
+    psi = in.template load_scaled<R>(nb[1], sc);
+    hop_values<0, BS, false>(acc, psi, sc, LQCD_PF_LINK(0, 1), false);
+    psi = in.template load_scaled<R>(nb[2], sc);
+    cp_async_wait<2>();
+    hop_values<1, FS, true>(acc, psi, sc, LQCD_PF_LINK(1, 0), false);
+    psi = in.template load_scaled<R>(nb[3], sc);
+    hop_values<1, BS, false>(acc, psi, sc, LQCD_PF_LINK(1, 1), false);
+    psi = in.template load_scaled<R>(nb[4], sc);
+    cp_async_wait<1>();
+    hop_values<2, FS, true>(acc, psi, sc, LQCD_PF_LINK(2, 0), false);
+    psi = in.template load_scaled<R>(nb[5], sc);
+    hop_values<2, BS, false>(acc, psi, sc, LQCD_PF_LINK(2, 1), false);
+    psi = in.template load_scaled<R>(nb[6], sc);
+    cp_async_wait<0>();
+    hop_values<3, FS, true>(acc, psi, sc, LQCD_PF_LINK(3, 0), antip && tf);
+    psi = in.template load_scaled<R>(nb[7], sc);
+    hop_values<3, BS, false>(acc, psi, sc, LQCD_PF_LINK(3, 1), antip && tb);
+#undef LQCD_PF_LINK
+    return acc;
 }
 
 } // namespace lqcd

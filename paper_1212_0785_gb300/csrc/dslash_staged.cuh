@@ -41,8 +41,6 @@ constexpr uint32_t STAGE_BYTES = NSR * (3 * ST_SITES * 16 + ST_SITES * 4) + (NUF
 // host; this header belongs to dslash.cu alone)
 static __device__ int g_stage_timeout = 0;
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint32_t bar)
 {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(

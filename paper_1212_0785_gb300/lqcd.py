@@ -644,9 +644,16 @@ class Service:
             pass
 
 
-def dslash_staging(enable=None) -> bool:
-    """query (None) or set the TMA-staged FP16+norm hopping term; returns the previous setting"""
-    return bool(lib().lqcd_dslash_staging(-1 if enable is None else int(bool(enable))))
+DSLASH_GATHER, DSLASH_STAGED, DSLASH_PREFETCH = 0, 1, 2
+
+
+def dslash_staging(mode=None) -> int:
+    """query (None) or select the form of the FP16+norm hopping term: 0
+    gathered, 1 TMA-staged +-t operands, 2 prefetched links (the default);
+    returns the previous form"""
+    if mode is not None and int(mode) not in (0, 1, 2):
+        raise ValueError("dslash form must be 0, 1 or 2")
+    return int(lib().lqcd_dslash_staging(-1 if mode is None else int(mode)))
 
 
 def dslash_check(stream=None):
