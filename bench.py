@@ -427,6 +427,8 @@ def run_ours(args):
                         "plaquette": [i["plaq"] for i in infos],
                         "cg_iters_per_traj": float(np.mean([i["cg_iters"] for i in infos])),
                         "solves_per_traj": float(np.mean([i["n_solves"] for i in infos])),
+                        "accurate_residuals_per_traj": float(np.mean([i["cg_accurate_residuals"] for i in infos])),
+                        "failed_checks_per_traj": float(np.mean([i["cg_failed_checks"] for i in infos])),
                         "cg_true_rel_res_max": max(i["cg_true_rel_res_max"] for i in infos)},
             "kernel_time_per_traj": kernel_share,
         }

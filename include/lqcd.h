@@ -252,6 +252,10 @@ typedef struct {
     int restarts;         /* FP64 restarts / mixed reliable updates */
     double true_rel_res;  /* |b - A x| / |b| in FP64 at exit */
     double seconds;       /* wall time of the call */
+    int accurate_residuals; /* accurate (FP64 or float-float) residuals b - A x computed: of the
+                               initial guess, at every reliable update or restart, at the end */
+    int failed_checks;    /* times the iterated residual met the tolerance and the accurate one
+                             did not (the solve then went on) */
 } lqcd_cg_info;
 
 /* Solve Mhat^dag Mhat x = b on the even sites (the matrix inversion of the
@@ -398,6 +402,8 @@ typedef struct {
     int n_solves;
     int cg_failures;
     uint32_t traj;             /* trajectory counter used for the random numbers */
+    int cg_accurate_residuals; /* summed lqcd_cg_info.accurate_residuals of the solves */
+    int cg_failed_checks;      /* summed lqcd_cg_info.failed_checks of the solves */
 } lqcd_traj_info;
 
 /* State of one Markov chain on the device: borrows the caller's FP64 gauge

@@ -371,7 +371,7 @@ lqcd_status CgRun::start(cudaStream_t s, CgScalars *sc_dev)
     sc = sc_dev;
     done = false;
     status = LQCD_OK;
-    inf = lqcd_cg_info{0, 0, 0.0, 0.0};
+    inf = lqcd_cg_info{0, 0, 0.0, 0.0, 0, 0};
     mixed = prm.sloppy != LQCD_F64;
     lqcd_status rc = start_impl(s);
     if (rc != LQCD_OK) return fail(rc);
@@ -411,6 +411,7 @@ lqcd_status CgRun::start_impl(cudaStream_t s)
         LQCD_TRY((convert_spinor<LQCD_F64, PREC_DF, double>(w.bdf.f, b, s)));
         LQCD_CUDA(cudaMemsetAsync(w.xs.f->data, 0, w.xs.f->bytes, s));
         if (prm.guess) { // r = b - A x0, accurately
+            inf.accurate_residuals++;
             LQCD_TRY((convert_spinor<LQCD_F64, PREC_DF, double>(w.xdf.f, x, s)));
             LQCD_TRY(true_residual_df(w, kappa, &rr0, s));
             LQCD_TRY(df_to_sloppy(w.rs.f, w.rdf_(), s));
@@ -423,6 +424,7 @@ lqcd_status CgRun::start_impl(cudaStream_t s)
         P = w.ps.f, R = w.rs.f, T = w.ts.f, TMP = w.tmpos.f, XS = w.xs.f, UU = Us;
     } else {
         if (prm.guess) {
+            inf.accurate_residuals++;
             LQCD_TRY(true_residual(w, x, U, b, kappa, &rr0, s));
         } else {
             LQCD_CUDA(cudaMemcpyAsync(w.r64.f->data, b->data, b->bytes, cudaMemcpyDeviceToDevice, s));
@@ -532,6 +534,8 @@ lqcd_status CgRun::pause_decide(const CgScalars &h, cudaStream_t s)
 {
     CgWorkspace &w = *ws;
     inf.true_rel_res = std::sqrt(rr_true / bb);
+    inf.accurate_residuals++;
+    if (h.reason == PAUSE_CONVERGED && !(rr_true <= h.stop2)) inf.failed_checks++;
     if (!std::isfinite(rr_true)) {
         set_error("cg: non-finite true residual");
         return fail(LQCD_ENUMERIC);

@@ -112,7 +112,7 @@ struct lqcd_hmc_state {
     double md_time = 0;
     double pending[2] = {0, 0}; // kick coefficients of each level not yet applied
     // statistics of the current trajectory
-    int cg_iters = 0, n_solves = 0, cg_failures = 0;
+    int cg_iters = 0, n_solves = 0, cg_failures = 0, cg_accurate = 0, cg_failed_checks = 0;
     double cg_res_max = 0;
 };
 
@@ -246,6 +246,8 @@ static lqcd_status record_solution(lqcd_hmc_state *st, PfTerm &t, const lqcd_hmc
 static lqcd_status count_solve(lqcd_hmc_state *st, lqcd_status rc, const lqcd_cg_info &info)
 {
     st->cg_iters += info.iters;
+    st->cg_accurate += info.accurate_residuals;
+    st->cg_failed_checks += info.failed_checks;
     st->n_solves++;
     st->cg_res_max = std::max(st->cg_res_max, info.true_rel_res);
     if (rc == LQCD_ENOCONV) {
@@ -502,7 +504,7 @@ static lqcd_status integrate(lqcd_hmc_state *st, const lqcd_hmc_params *p, doubl
 
 static void reset_stats(lqcd_hmc_state *st)
 {
-    st->cg_iters = st->n_solves = st->cg_failures = 0;
+    st->cg_iters = st->n_solves = st->cg_failures = st->cg_accurate = st->cg_failed_checks = 0;
     st->cg_res_max = 0;
 }
 
@@ -630,6 +632,8 @@ lqcd_status lqcd_hmc_trajectory(lqcd_hmc_state *s, const lqcd_hmc_params *p, lqc
         info->cg_iters = s->cg_iters;
         info->n_solves = s->n_solves;
         info->cg_failures = s->cg_failures;
+        info->cg_accurate_residuals = s->cg_accurate;
+        info->cg_failed_checks = s->cg_failed_checks;
         info->traj = s->traj;
     }
     s->traj++;
@@ -838,6 +842,8 @@ lqcd_status lqcd_batch_trajectory(lqcd_batch *B, const lqcd_hmc_params *params, 
             f.cg_iters = st->cg_iters;
             f.n_solves = st->n_solves;
             f.cg_failures = st->cg_failures;
+            f.cg_accurate_residuals = st->cg_accurate;
+            f.cg_failed_checks = st->cg_failed_checks;
             f.traj = st->traj;
         }
         st->traj++;

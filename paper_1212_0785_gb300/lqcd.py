@@ -51,7 +51,7 @@ class CgParams(ctypes.Structure):
 
 class CgInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("true_rel_res", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("accurate_residuals", ctypes.c_int), ("failed_checks", ctypes.c_int)]
 
 
 class HmcParams(ctypes.Structure):
@@ -85,7 +85,8 @@ class TrajInfo(ctypes.Structure):
                 ("plaq", ctypes.c_double), ("u", ctypes.c_double), ("max_unitarity_dev", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("cg_true_rel_res_max", ctypes.c_double),
                 ("accepted", ctypes.c_int), ("cg_iters", ctypes.c_int), ("n_solves", ctypes.c_int),
-                ("cg_failures", ctypes.c_int), ("traj", ctypes.c_uint32)]
+                ("cg_failures", ctypes.c_int), ("traj", ctypes.c_uint32), ("cg_accurate_residuals", ctypes.c_int),
+                ("cg_failed_checks", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

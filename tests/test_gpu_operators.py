@@ -207,3 +207,9 @@ def test_cg_warm_start(sloppy):
     assert rc == lqcd.OK and warm.true_rel_res <= 1e-10 and 0 < warm.iters < cold.iters
     r = bh - orc.mdagm(dims, Uh, kappa, full_from_half(x.download(), dims, 0))
     assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(bh)
+    # accurate residuals: one per restart (reliable update or failed check) and
+    # one at the end, plus one of the guess; a guess that solves takes just that
+    assert cold.accurate_residuals == cold.restarts + 1 and warm.accurate_residuals == warm.restarts + 2
+    assert exact.accurate_residuals == 1 and exact.restarts == 0
+    for info in (cold, exact, warm):
+        assert 0 <= info.failed_checks <= info.restarts
