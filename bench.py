@@ -351,6 +351,36 @@ def run_ours(args):
                         "GB_per_s": (v[2] / (v[0] * 1e-3) / 1e9) if v[2] else None}
                     for k, v in timers.items() if v[1]}
 
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        host_in = torch.empty(V * 4 * 9 * 2, dtype=torch.float64, pin_memory=True).numpy()
+        host_out = torch.empty(V * 4 * 9 * 2, dtype=torch.float64, pin_memory=True).numpy()
+        hin = host_in.view(np.complex128).reshape(V, 4, 3, 3)
+        hout = host_out.view(np.complex128).reshape(V, 4, 3, 3)
+        U.download(out=hin)
+        # one untimed round trip first: the transfer staging buffers are
+        # allocated once, like every other buffer before the timed region
+        U.upload(hin)
+        state.trajectory(params)
+        U.download(out=hout)
+        hin, hout = hout, hin
+        torch.cuda.synchronize()
+        barrier(dist, local)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            U.upload(hin)
+            info = state.trajectory(params)
+            U.download(out=hout)
+            hin, hout = hout, hin
+        e1.record(stream)
+        torch.cuda.synchronize()
+        te = max_over_ranks(dist, e0.elapsed_time(e1) / 1e3, dev)
+        nb = V * 4 * 18 * 8
+        e2e = {"value": sum_over_ranks(dist, float(args.e2e_steps), dev) / te, "unit": "trajectories/s",
+               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 96, "steps": args.e2e_steps}
+
     # FP64 GPU path beside it: same start, same chain, same trajectory counters
     # as the first timed mixed trajectories, so dH differences measure the
     # error of the mixed path
@@ -380,30 +410,6 @@ def run_ours(args):
                                           if same_start else None)}
         st64.close()
         del U64
-
-    # end to end through the public API with host buffers
-    e2e = None
-    if args.e2e_steps > 0:
-        host_in = torch.empty(V * 4 * 9 * 2, dtype=torch.float64, pin_memory=True).numpy()
-        host_out = torch.empty(V * 4 * 9 * 2, dtype=torch.float64, pin_memory=True).numpy()
-        hin = host_in.view(np.complex128).reshape(V, 4, 3, 3)
-        hout = host_out.view(np.complex128).reshape(V, 4, 3, 3)
-        U.download(out=hin)
-        torch.cuda.synchronize()
-        barrier(dist, local)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.e2e_steps):
-            U.upload(hin)
-            info = state.trajectory(params)
-            U.download(out=hout)
-            hin, hout = hout, hin
-        e1.record(stream)
-        torch.cuda.synchronize()
-        te = max_over_ranks(dist, e0.elapsed_time(e1) / 1e3, dev)
-        nb = V * 4 * 18 * 8
-        e2e = {"value": sum_over_ranks(dist, float(args.e2e_steps), dev) / te, "unit": "trajectories/s",
-               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 96, "steps": args.e2e_steps}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
