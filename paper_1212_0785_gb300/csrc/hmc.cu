@@ -649,10 +649,39 @@ lqcd_status lqcd_hmc_trajectory(lqcd_hmc_state *s, const lqcd_hmc_params *p, lqc
 
 // ================================================================== batched chains
 
+// Streams over which the chains' per-chain kernels (forces, link updates) are
+// spread: a small lattice's kernel fills a fraction of the GPU, so the chains
+// run side by side.  Created on first use; each chain's kernels stay in order
+// on one stream, and the caller's stream waits for all of them.
+struct ChainStreams {
+    static constexpr int N = 8;
+    cudaStream_t st[N] = {};
+    cudaEvent_t fork = nullptr, join[N] = {};
+    lqcd_status ensure()
+    {
+        if (fork) return LQCD_OK;
+        LQCD_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        for (int k = 0; k < N; k++) {
+            LQCD_CUDA(cudaStreamCreateWithFlags(&st[k], cudaStreamNonBlocking));
+            LQCD_CUDA(cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming));
+        }
+        return LQCD_OK;
+    }
+    ~ChainStreams()
+    {
+        for (int k = 0; k < N; k++) {
+            if (st[k]) cudaStreamDestroy(st[k]);
+            if (join[k]) cudaEventDestroy(join[k]);
+        }
+        if (fork) cudaEventDestroy(fork);
+    }
+};
+
 struct lqcd_batch {
     std::vector<lqcd_hmc_state *> chains;
     lqcd::BatchSolver bs;
     lqcd::DevBuf scal; // one CgScalars slot per chain
+    ChainStreams cs;
 };
 
 namespace lqcd {
@@ -709,25 +738,41 @@ static lqcd_status batch_solve(lqcd_batch *B, const lqcd_hmc_params *p, cudaStre
     return LQCD_OK;
 }
 
+// f(i, stream) for every chain i, chain i on chain stream i mod N, all after
+// the work already on s and before the work later enqueued on s
+template <class F>
+static lqcd_status per_chain(lqcd_batch *B, cudaStream_t s, F f)
+{
+    ChainStreams &cs = B->cs;
+    LQCD_TRY(cs.ensure());
+    LQCD_CUDA(cudaEventRecord(cs.fork, s));
+    const int ns = (int)std::min<size_t>(ChainStreams::N, B->chains.size());
+    for (int k = 0; k < ns; k++) LQCD_CUDA(cudaStreamWaitEvent(cs.st[k], cs.fork, 0));
+    lqcd_status rc = LQCD_OK;
+    for (size_t i = 0; i < B->chains.size() && rc == LQCD_OK; i++) rc = f(i, cs.st[i % ChainStreams::N]);
+    for (int k = 0; k < ns; k++) { // joined also after a failure
+        LQCD_CUDA(cudaEventRecord(cs.join[k], cs.st[k]));
+        LQCD_CUDA(cudaStreamWaitEvent(s, cs.join[k], 0));
+    }
+    return rc;
+}
+
 static lqcd_status batch_kick(lqcd_batch *B, const lqcd_hmc_params *p, double c, cudaStream_t s)
 {
-    size_t n = B->chains.size();
-    for (size_t i = 0; i < n; i++) {
+    LQCD_TRY(per_chain(B, s, [&](size_t i, cudaStream_t cst) {
         lqcd_hmc_state *st = B->chains[i];
-        LQCD_TRY(gauge_force_dev(st->P.f, st->U, st->Uf.f, p[i].beta, c, p[i].force_prec, s));
-    }
+        return gauge_force_dev(st->P.f, st->U, st->Uf.f, p[i].beta, c, p[i].force_prec, cst);
+    }));
     LQCD_TRY(batch_solve(B, p, s));
-    for (size_t i = 0; i < n; i++) {
+    return per_chain(B, s, [&](size_t i, cudaStream_t cst) {
         lqcd_hmc_state *st = B->chains[i];
-        LQCD_TRY(fermion_force(st, &p[i], st->pf[PF_MAIN].X.f, nullptr, p[i].kappa, c, s));
-    }
-    return LQCD_OK;
+        return fermion_force(st, &p[i], st->pf[PF_MAIN].X.f, nullptr, p[i].kappa, c, cst);
+    });
 }
 
 static lqcd_status batch_drift(lqcd_batch *B, const lqcd_hmc_params *p, double c, cudaStream_t s)
 {
-    for (size_t i = 0; i < B->chains.size(); i++) LQCD_TRY(drift(B->chains[i], &p[i], c, s));
-    return LQCD_OK;
+    return per_chain(B, s, [&](size_t i, cudaStream_t cst) { return drift(B->chains[i], &p[i], c, cst); });
 }
 
 static lqcd_status batch_integrate(lqcd_batch *B, const lqcd_hmc_params *p, cudaStream_t s)
