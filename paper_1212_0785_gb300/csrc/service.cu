@@ -113,11 +113,16 @@ struct SvcGauge {
     FieldPtr bo, bp, to, src, bo_df, xo_df, mxe_df;
     DevBuf part, scal;
     bool ready = false;
+    // solver work spaces of finished right-hand sides, reused by the next
+    // ones (at most one request's worth, kept outside the admission budget)
+    std::vector<std::unique_ptr<CgWorkspace>> idle;
 };
+
+constexpr size_t IDLE_WS_MAX = 12;
 
 struct SvcRhs {
     int comp = 0;
-    std::unique_ptr<CgWorkspace> ws{new CgWorkspace()};
+    std::unique_ptr<CgWorkspace> ws;
     FieldPtr y, xo; // the solution halves
     CgRun run;
     int refinements = 0;
@@ -303,6 +308,12 @@ static lqcd_status admit(lqcd_service *S, SvcRequest &r)
         std::unique_ptr<SvcRhs> h(new SvcRhs());
         h->comp = k;
         h->tol_n = S->prm.cg.tol / 10.0;
+        if (!g.idle.empty()) {
+            h->ws = std::move(g.idle.back());
+            g.idle.pop_back();
+        } else {
+            h->ws.reset(new CgWorkspace());
+        }
         h->ws->udf_ext = g.Udf.f;
         h->ws->tmp_from = &g.shared;
         LQCD_TRY(h->ws->ensure(lat, S->prm.cg.sloppy, S->stream));
@@ -384,7 +395,11 @@ static void finish_request(lqcd_service *S, SvcRequest &r, lqcd_status st)
         o.refinements += h->refinements;
         o.true_rel_res_max = std::max(o.true_rel_res_max, h->rel_res);
         if (o.status == LQCD_OK && h->status != LQCD_OK) o.status = h->status;
-        h->ws.reset(); // the solver fields go; the solution halves stay until release
+        // the solver fields go back to the gauge field's pool (or are freed);
+        // the solution halves stay until release
+        SvcGauge &g = *S->gauges[r.req.gauge];
+        if (h->ws && g.idle.size() < IDLE_WS_MAX) g.idle.push_back(std::move(h->ws));
+        h->ws.reset();
     }
     o.queue_s = std::chrono::duration<double>(r.t_admit - r.t_submit).count();
     o.latency_s = std::chrono::duration<double>(r.t_done - r.t_submit).count();
