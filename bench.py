@@ -367,6 +367,8 @@ def run_ours(args):
         hin, hout = hout, hin
         torch.cuda.synchronize()
         barrier(dist, local)
+        eclk = ClockSampler(gpu_index)
+        eclk.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.e2e_steps):
@@ -376,10 +378,12 @@ def run_ours(args):
             hin, hout = hout, hin
         e1.record(stream)
         torch.cuda.synchronize()
+        e2e_clk = eclk.stop()
         te = max_over_ranks(dist, e0.elapsed_time(e1) / 1e3, dev)
         nb = V * 4 * 18 * 8
         e2e = {"value": sum_over_ranks(dist, float(args.e2e_steps), dev) / te, "unit": "trajectories/s",
-               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 96, "steps": args.e2e_steps}
+               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb + 96, "steps": args.e2e_steps,
+               "clocks": e2e_clk}
 
     # FP64 GPU path beside it: same start, same chain, same trajectory counters
     # as the first timed mixed trajectories, so dH differences measure the
@@ -651,7 +655,7 @@ def main(argv=None):
     ap.add_argument("--nsteps", type=int, default=WORKLOAD["nsteps"],
                     help="MD steps per trajectory (16 for the benchmarked workload)")
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
     if args.impl == "reference":
