@@ -135,24 +135,90 @@ __global__ void __launch_bounds__(FB) gauge_force_kernel(MomRef P, GaugeRef<GP> 
     }
 }
 
+// FP32 fermion force: each thread first starts asynchronous 16-byte copies
+// (cp.async) of B(x), B(x+mu) and U_mu(x) (one group) and of A(x+mu) (a
+// second) into shared memory, so their DRAM latencies overlap instead of
+// following one another; A(x) is loaded as before.  The arithmetic is
+// unchanged.  Slots: [0, 6) B(x), [6, 12) B(x+mu), [12, 15) U_mu(x),
+// [15, 21) A(x+mu), each [slot][thread].
+constexpr int FF_SLOTS = 21;
+
+__device__ __forceinline__ void ff_cp16(float4 *dst, const float4 *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+
+// a 12-real FP32 link from its three stored chunks (as GaugeRef<F32>::load)
+template <typename R>
+__device__ __forceinline__ M3<R> ff_link(float4 a, float4 b, float4 c)
+{
+    M3<R> u;
+    u.e[0][0] = cx<R>(a.x, a.y);
+    u.e[0][1] = cx<R>(a.z, a.w);
+    u.e[0][2] = cx<R>(b.x, b.y);
+    u.e[1][0] = cx<R>(b.z, b.w);
+    u.e[1][1] = cx<R>(c.x, c.y);
+    u.e[1][2] = cx<R>(c.z, c.w);
+    reconstruct_row2(u);
+    return u;
+}
+
 // Fermion force on link (x, mu), x of parity par:
 //   Q = sum_spin [s U A(x+mu)] [(1 - gamma_mu) B(x)]^dag - A(x) [s U (1 + gamma_mu) B(x+mu)]^dag
 // A = (A_e, A_o), B = (B_e, B_o) full-lattice spinors split by parity.
 template <int MU, typename R, lqcd_prec SP, lqcd_prec GP>
 __device__ __forceinline__ void fermion_force_link(MomRef &P, const GaugeRef<GP> &U, const Geo &g, int par,
                                                    int cb, const int c[4], const SpinorRef<SP> (&A)[2],
-                                                   const SpinorRef<SP> (&B)[2], double cf)
+                                                   const SpinorRef<SP> (&B)[2], double cf,
+                                                   float4 (*pf)[FB] = nullptr)
 {
     int cy[4] = {c[0], c[1], c[2], c[3]};
     bool wrap = (c[MU] + 1 == g.L[MU]);
     cy[MU] = wrap ? 0 : c[MU] + 1;
     int cby = coords_cb(g, cy);
     R s = (MU == 3 && wrap && g.t_bc < 0) ? (R)-1 : (R)1;
-    M3<R> u = U.template load<R>(MU, par, cb);
-    Sp<R> Ay = A[1 - par].template load_rw<R>(cby);
-    Sp<R> Ax = A[par].template load_rw<R>(cb);
-    Sp<R> Bx = B[par].template load_rw<R>(cb);
-    Sp<R> By = B[1 - par].template load_rw<R>(cby);
+    M3<R> u;
+    Sp<R> Ay, Ax, Bx, By;
+    if constexpr (SP == LQCD_F32 && GP == LQCD_F32) {
+        const int i = threadIdx.x;
+        const size_t Vh = (size_t)g.Vh;
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            ff_cp16(&pf[k][i], B[par].d + k * Vh + cb);
+            ff_cp16(&pf[6 + k][i], B[1 - par].d + k * Vh + cby);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; k++) ff_cp16(&pf[12 + k][i], U.d + U.idx(MU, par, k, cb));
+        asm volatile("cp.async.commit_group;" ::: "memory");
+#pragma unroll
+        for (int k = 0; k < 6; k++) ff_cp16(&pf[15 + k][i], A[1 - par].d + k * Vh + cby);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        Ax = A[par].template load_rw<R>(cb);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        {
+            float4 v[6], w[6];
+#pragma unroll
+            for (int k = 0; k < 6; k++) v[k] = pf[k][i], w[k] = pf[6 + k][i];
+            Bx = B[par].template unpack<R>(v);
+            By = B[1 - par].template unpack<R>(w);
+        }
+        u = ff_link<R>(pf[12][i], pf[13][i], pf[14][i]);
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        {
+            float4 v[6];
+#pragma unroll
+            for (int k = 0; k < 6; k++) v[k] = pf[15 + k][i];
+            Ay = A[1 - par].template unpack<R>(v);
+        }
+    } else {
+        u = U.template load<R>(MU, par, cb);
+        Ay = A[1 - par].template load_rw<R>(cby);
+        Ax = A[par].template load_rw<R>(cb);
+        Bx = B[par].template load_rw<R>(cb);
+        By = B[1 - par].template load_rw<R>(cby);
+    }
     // w1 = (1 - gamma) B(x) as a full spinor
     Sp<R> w1 = sp_zero<R>();
     accumulate<MU, -1>(w1, project<MU, -1>(Bx));
@@ -196,11 +262,12 @@ __global__ void __launch_bounds__(FB) fermion_force_kernel(MomRef P, GaugeRef<GP
     cb_coords(g, cb, par, c);
     const SpinorRef<SP> A[2] = {Ae, Ao};
     const SpinorRef<SP> B[2] = {Be, Bo};
+    __shared__ float4 pf[SP == LQCD_F32 && GP == LQCD_F32 ? FF_SLOTS : 1][FB];
     switch (mu) {
-    case 0: fermion_force_link<0, R, SP, GP>(P, U, g, par, cb, c, A, B, cf); break;
-    case 1: fermion_force_link<1, R, SP, GP>(P, U, g, par, cb, c, A, B, cf); break;
-    case 2: fermion_force_link<2, R, SP, GP>(P, U, g, par, cb, c, A, B, cf); break;
-    default: fermion_force_link<3, R, SP, GP>(P, U, g, par, cb, c, A, B, cf); break;
+    case 0: fermion_force_link<0, R, SP, GP>(P, U, g, par, cb, c, A, B, cf, pf); break;
+    case 1: fermion_force_link<1, R, SP, GP>(P, U, g, par, cb, c, A, B, cf, pf); break;
+    case 2: fermion_force_link<2, R, SP, GP>(P, U, g, par, cb, c, A, B, cf, pf); break;
+    default: fermion_force_link<3, R, SP, GP>(P, U, g, par, cb, c, A, B, cf, pf); break;
     }
 }
 
