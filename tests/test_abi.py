@@ -70,3 +70,29 @@ def test_allocator_hook_validation(L):
     a = lqcd.ALLOC_FN(lambda n, s, c: None)
     assert L.lqcd_set_allocator(a, lqcd.FREE_FN(), None) == lqcd.EINVAL
     assert L.lqcd_set_allocator(lqcd.ALLOC_FN(), lqcd.FREE_FN(), None) == lqcd.OK
+
+
+def test_dslash_form_switch_is_host_state(L):
+    """the FP16+norm hopping-term form is a process-wide host setting: set,
+    query and restore need no device; values above 2 select form 2"""
+    prev = lqcd.dslash_staging()
+    try:
+        assert prev in (lqcd.DSLASH_GATHER, lqcd.DSLASH_STAGED, lqcd.DSLASH_PREFETCH)
+        lqcd.dslash_staging(lqcd.DSLASH_GATHER)
+        assert lqcd.dslash_staging(lqcd.DSLASH_STAGED) == lqcd.DSLASH_GATHER
+        assert lqcd.dslash_staging() == lqcd.DSLASH_STAGED
+        assert L.lqcd_dslash_staging(7) == lqcd.DSLASH_STAGED and lqcd.dslash_staging() == lqcd.DSLASH_PREFETCH
+        with pytest.raises(ValueError):
+            lqcd.dslash_staging(-2)
+    finally:
+        lqcd.dslash_staging(prev)
+
+
+def test_info_structs_carry_the_solver_counters():
+    """lqcd_cg_info and lqcd_traj_info end with the accurate-residual and
+    failed-check counters (appended, so the earlier fields keep their offsets)"""
+    names = [f for f, _ in lqcd.CgInfo._fields_]
+    assert names[:4] == ["iters", "restarts", "true_rel_res", "seconds"]
+    assert names[4:] == ["accurate_residuals", "failed_checks"]
+    tnames = [f for f, _ in lqcd.TrajInfo._fields_]
+    assert tnames[-3:] == ["traj", "cg_accurate_residuals", "cg_failed_checks"]
