@@ -425,8 +425,9 @@ def run_ours(args):
             "metric": "trajectories/s", "value": value, "unit": "trajectories/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": (f"f32 math ({args.sloppy} storage in the solver, {args.force_prec} forces); f64 master "
-                      f"links/momenta, residuals, dots, link update, dH"),
+            "dtype": "f32",
+            "dtype_detail": (f"f32 math ({args.sloppy} storage in the solver, {args.force_prec} forces); f64 master "
+                             f"links/momenta, residuals, dots, link update, dH"),
             "data": "synthetic",
             "config": dict(config_block(args, args.sloppy),
                            dslash_form={0: "gathered", 1: "tma_staged_t", 2: "prefetched_links"}.get(
@@ -519,7 +520,7 @@ def run_chains(args):
     line = {"metric": "chain-trajectories/s", "value": n * args.steps / t_batch, "unit": "chain-trajectories/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 math (f16n solver storage, f32 forces); f64 master fields, residuals, dH",
+            "dtype": "f32", "dtype_detail": "f32 math (f16n solver storage, f32 forces); f64 master fields, residuals, dH",
             "data": "synthetic",
             "config": {"workload": "chains64_8^4x32_12^4x24_16^3x32x8", "chains": n, "sites_total": sites,
                        "beta": [5.6, 5.9], "kappa": [0.150, 0.157], "integrator": "leapfrog", "nsteps": 10,
@@ -621,7 +622,8 @@ def run_service(args):
     line = {"metric": "solves/s", "value": ours["solves_per_s"], "unit": "solves/s (12 point-source RHS each)",
             "n_gpus": 1, "steps": n, "warmup": len(SERVICE_LATS), "ms_per_step": span / n * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 math (f16n solver storage); f64 residual check and solutions", "data": "synthetic",
+            "dtype": "f32", "dtype_detail": "f32 math (f16n solver storage); f64 residual check and solutions",
+            "data": "synthetic",
             "config": {"workload": "solve_service_8^4_16^3x32_24^3x48_32^3x64", "requests": n,
                        "arrival_rate_per_s": args.rate, "rhs_per_request": 12, "kappa": [0.150, 0.158],
                        "tol_full_M": 1e-10, "hbm_budget_gib": args.hbm_budget, "start_eps": 0.15},
