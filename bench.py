@@ -170,7 +170,7 @@ def kernel_source_hash() -> str:
     valid for the kernel it was taken on"""
     h = hashlib.sha256()
     base = os.path.join(HERE, "paper_1212_0785_gb300", "csrc")
-    for name in ("dslash.cu", "dslash_site.cuh", "dslash_staged.cuh", "spin.cuh", "lqcd_internal.cuh", "dslash.cuh"):
+    for name in ("dslash.cu", "dslash_site.cuh", "spin.cuh", "lqcd_internal.cuh", "dslash.cuh"):
         with open(os.path.join(base, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -197,45 +197,121 @@ def stored_traffic(kernel: str):
 
 # ---------------------------------------------------------------- oracle baseline
 
-def oracle_sample(dims=ORACLE_SAMPLE_DIMS, wl=WORKLOAD):
-    """Time the FP64 CPU oracle on the operations of one MD force evaluation of
-    the workload at a reduced volume with the same recipe, and derive the time
-    of one full trajectory at the workload's volume:
-      t_traj = (2n+1) (t_solve + t_gauge_force + t_fermion_force) + t_solve
-               + 2n t_link_update,   scaled by V_workload / V_sample.
-    The CG iteration count of the sample solve is that of the oracle itself."""
+def host_cpu() -> dict:
+    """core count and CPU model of the host the oracle runs on"""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "model": model or platform.processor() or "unknown",
+            "arch": platform.machine()}
+
+
+def oracle_sample(dims=ORACLE_SAMPLE_DIMS, wl=WORKLOAD, openmp=True):
+    """Time the FP64 CPU oracle (its OpenMP or its serial build) on the
+    operations of one MD force evaluation of the workload at a reduced volume
+    with the same recipe: one CG solve to the workload's tolerance from a zero
+    guess (time per iteration), the gauge force, the fermion force and a link
+    update."""
     from oracle import oracle as orc
 
-    beta, kappa, n = wl["beta"], wl["kappa"], wl["nsteps"]
+    prev = orc.use_openmp(openmp)
+    try:
+        beta, kappa, n = wl["beta"], wl["kappa"], wl["nsteps"]
+        U = orc.gauge_start(dims, SEED, EPS)
+        eta = orc.eta_refresh(dims, SEED, 0)
+        phi = orc.mhat(dims, U, kappa, eta, dagger=True)
+        P = orc.momentum_refresh(dims, SEED, 0)
+        t0 = time.perf_counter()
+        X, conv, iters, _ = orc.cg(dims, U, kappa, phi, tol=wl["cg_tol"])
+        t1 = time.perf_counter()
+        orc.gauge_force(dims, U, beta)
+        t2 = time.perf_counter()
+        orc.fermion_force(dims, U, kappa, X)
+        t3 = time.perf_counter()
+        orc.link_update(dims, U, P, 0.5 * wl["tau"] / n)
+        t4 = time.perf_counter()
+        threads = orc.num_threads()
+    finally:
+        orc.use_openmp(prev == "openmp")
+    return {"dims": list(dims), "threads": threads, "cg_iters": iters, "sample_cpu_s": t4 - t0,
+            "parts_s": {"cg_iteration": (t1 - t0) / max(iters, 1), "gauge_force": t2 - t1,
+                        "fermion_force": t3 - t2, "link_update": t4 - t3},
+            "scale": float(np.prod(wl["dims"])) / float(np.prod(dims))}
+
+
+def derived_traj_s(sample, cg_iters_per_traj, wl=WORKLOAD) -> float:
+    """one trajectory of the workload from the sample's per-part times:
+    (2n+1) force evaluations (merged Omelyan kicks), 2n link updates and the
+    given number of CG iterations, scaled by the volume ratio"""
+    n, p = wl["nsteps"], sample["parts_s"]
+    t = (cg_iters_per_traj * p["cg_iteration"] + (2 * n + 1) * (p["gauge_force"] + p["fermion_force"])
+         + 2 * n * p["link_update"])
+    return t * sample["scale"]
+
+
+def oracle_trajectory_4(gpu_traj=None):
+    """a full oracle trajectory at 4^4 with the workload's recipe (beta,
+    kappa, Omelyan 16 steps, tau 1, start seed 3 eps 0.15), timed on the serial
+    and the OpenMP build; with gpu_traj (the library's trajectory of the same
+    4^4 chain in the benchmark's mixed configuration: dH, H0, plaquette,
+    links) the per-result differences against the oracle"""
+    from oracle import oracle as orc
+
+    dims, wl = (4, 4, 4, 4), WORKLOAD
     U = orc.gauge_start(dims, SEED, EPS)
-    eta = orc.eta_refresh(dims, SEED, 0)
-    phi = orc.mhat(dims, U, kappa, eta, dagger=True)
-    P = orc.momentum_refresh(dims, SEED, 0)
-    t0 = time.perf_counter()
-    X, conv, iters, _ = orc.cg(dims, U, kappa, phi, tol=wl["cg_tol"])
-    t1 = time.perf_counter()
-    orc.gauge_force(dims, U, beta)
-    t2 = time.perf_counter()
-    orc.fermion_force(dims, U, kappa, X)
-    t3 = time.perf_counter()
-    orc.link_update(dims, U, P, 0.5 * wl["tau"] / n)
-    t4 = time.perf_counter()
-    t_solve, t_gf, t_ff, t_lu = t1 - t0, t2 - t1, t3 - t2, t4 - t3
-    scale = float(np.prod(wl["dims"])) / float(np.prod(dims))
-    t_traj = ((2 * n + 1) * (t_solve + t_gf + t_ff) + t_solve + 2 * n * t_lu) * scale
-    return {"t_traj_derived_s": t_traj, "sample_cpu_s": t4 - t0, "cg_iters": iters,
-            "parts_s": {"cg_solve": t_solve, "gauge_force": t_gf, "fermion_force": t_ff, "link_update": t_lu},
-            "scale": scale}
+    out = {}
+    for variant in (False, True):
+        prev = orc.use_openmp(variant)
+        t0 = time.perf_counter()
+        Uo, o = orc.hmc_trajectory(dims, U, wl["beta"], wl["kappa"], wl["tau"], wl["nsteps"],
+                                   integrator=orc.OMELYAN, seed=SEED, traj=0, cg_tol=wl["cg_tol"])
+        out["openmp_s" if variant else "serial_s"] = time.perf_counter() - t0
+        out["openmp_threads" if variant else "serial_threads"] = orc.num_threads()
+        orc.use_openmp(prev == "openmp")
+    out["oracle"] = {"dH": o["dH"], "accepted": int(o["accepted"]), "plaq": o["plaq"], "cg_iters": o["cg_iters"]}
+    if gpu_traj is not None:
+        g, Ug = gpu_traj
+        out["mixed_gpu_minus_oracle"] = {"dH": g["dH"] - o["dH"], "H0_rel": (g["H0"] - o["H0"]) / o["H0"],
+                                         "plaq": g["plaq"] - o["plaq"], "links_max": float(np.max(np.abs(Ug - Uo))),
+                                         "accept_same": g["accepted"] == int(o["accepted"]),
+                                         "tolerances": {"dH": 1.8e-3, "H0_rel": 1e-12, "plaq": 1e-7,
+                                                        "links_max": 1e-4}}
+    return out
 
 
-def cpu_baseline_block(sample) -> dict:
-    d = "x".join(str(v) for v in ORACLE_SAMPLE_DIMS)
-    return {"value": 1.0 / sample["t_traj_derived_s"], "unit": "trajectories/s", "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 oracle, single thread: one CG solve to 1e-10 ({sample['cg_iters']} iterations), "
-                       f"gauge force, fermion force and link update at {d} with the 32^3x64 recipe "
-                       f"({sample['sample_cpu_s']:.1f} s), derived to one 33-force-evaluation trajectory "
-                       f"and scaled by volume x{sample['scale']:.1f}"),
-            "parts_s": sample["parts_s"]}
+def cpu_baseline_block(omp, serial, cg_iters_per_traj, iters_source, traj4=None) -> dict:
+    d = "x".join(str(v) for v in omp["dims"])
+    t_omp = derived_traj_s(omp, cg_iters_per_traj)
+    t_ser = derived_traj_s(serial, cg_iters_per_traj)
+    blk = {"value": 1.0 / t_omp, "unit": "trajectories/s", "cores": omp["threads"], "kind": "oracle",
+           "sample": (f"FP64 oracle (OpenMP build, {omp['threads']} threads): one CG solve to 1e-10 "
+                      f"({omp['cg_iters']} iterations from a zero guess), gauge force, fermion force and link "
+                      f"update at {d} with the 32^3x64 recipe ({omp['sample_cpu_s']:.1f} s), derived to one "
+                      f"trajectory of 33 force evaluations, 32 link updates and {cg_iters_per_traj:.0f} CG "
+                      f"iterations ({iters_source}), scaled by volume x{omp['scale']:.1f}"),
+           "derived": True, "host": host_cpu(),
+           "single_thread": {"value": 1.0 / t_ser, "cores": 1, "sample_cpu_s": serial["sample_cpu_s"],
+                             "parts_s": serial["parts_s"]},
+           "parts_s": omp["parts_s"]}
+    if traj4 is not None:
+        blk["full_trajectory_4^4"] = traj4
+    return blk
 
 
 def run_reference(args):
@@ -244,30 +320,34 @@ def run_reference(args):
         return 0
     samples = []
     for k in range(args.warmup + args.steps):
-        s = oracle_sample()
+        s = oracle_sample(openmp=True)
         if k >= args.warmup:
             samples.append(s)
-    t = float(np.mean([s["t_traj_derived_s"] for s in samples]))
+    # the oracle's own iteration count: its zero-guess solve at the sample
+    # volume, for each of the trajectory's 34 solves
+    iters = 34 * samples[-1]["cg_iters"]
+    t = float(np.mean([derived_traj_s(s, iters) for s in samples]))
     value = 1.0 / t
-    cb = cpu_baseline_block(samples[-1])
+    serial = oracle_sample(openmp=False)
+    cb = cpu_baseline_block(samples[-1], serial, iters, "the oracle's own: 34 zero-guess solves")
     cb["value"] = value
     line = {"metric": "trajectories/s", "value": value, "unit": "trajectories/s", "impl": "reference",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_block(args, "f64"), "cpu_baseline": cb,
+            "data": "synthetic", "config": config_block(args, "f64", "f64"), "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "trajectories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-def config_block(args, sloppy):
+def config_block(args, sloppy, force_prec):
     c = dict(WORKLOAD)
     c["dims"] = list(args.dims)
     c["nsteps"] = args.nsteps
     c["solver"] = ("fp64 CG" if sloppy == "f64" else
                    f"reliable-update mixed CG: {sloppy} spinors + 12-real {sloppy} links, fp32 math, "
-                   f"fp64 residual/dots, delta {args.delta}")
-    c["forces"] = f"{getattr(args, 'force_prec', 'f64')} arithmetic"
+                   f"float-float residual/solution, fp64 dot sums, delta {args.delta}")
+    c["forces"] = f"{force_prec} arithmetic"
     k = int(getattr(args, "chrono", 0))
     c["initial_guess"] = {0: "zero", 1: "previous solution (chronological)"}.get(
         k, f"extrapolated through the last {k} solutions (chronological)")
@@ -300,8 +380,8 @@ def run_ours(args):
     U = lqcd.gauge_field(dims)
     lqcd.gauge_start(U, SEED, EPS, chain=rank)
     state = lqcd.HmcState(U, seed=SEED, chain=rank)
-    for _ in range(args.warmup):
-        state.trajectory(params)
+    warm = [state.trajectory(params) for _ in range(args.warmup)]
+    warm_rejected = all(i["accepted"] == 0 for i in warm)
     torch.cuda.synchronize()
     barrier(dist, local)
 
@@ -391,11 +471,15 @@ def run_ours(args):
     fp64 = None
     if args.fp64_steps > 0:
         U64 = lqcd.gauge_field(dims)
-        lqcd.gauge_start(U64, SEED, EPS, chain=rank)
-        st64 = lqcd.HmcState(U64, seed=SEED, chain=rank, traj0=args.warmup)
         p64 = lqcd.hmc_params(wl["beta"], wl["kappa"], wl["tau"], args.nsteps, lqcd.OMELYAN, n_flavors=2,
                               cg=lqcd.cg_params(tol=wl["cg_tol"], maxiter=20000, sloppy=lqcd.F64),
                               chrono=int(args.chrono))
+        lqcd.gauge_start(U64, SEED, EPS, chain=rank)
+        st64 = lqcd.HmcState(U64, seed=SEED, chain=rank, traj0=args.warmup)
+        for _ in range(args.fp64_warmup):  # allocations and first launches, then the same start again
+            st64.trajectory(p64)
+        lqcd.gauge_start(U64, SEED, EPS, chain=rank)
+        st64.traj = args.warmup
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -403,9 +487,14 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         t64 = e0.elapsed_time(e1) / 1e3
-        # the mixed chain's first timed trajectory against the FP64 chain's first
-        same_start = all(i["accepted"] == 0 for i in infos[:args.fp64_steps]) or args.warmup == 0
+        # the mixed chain's timed trajectories against the FP64 chain's, from
+        # the same links and trajectory counters (hence the same momenta and
+        # pseudofermions) as long as neither chain accepted a trajectory
+        same_start = (all(i["accepted"] == 0 for i in infos[:args.fp64_steps])
+                      and all(i["accepted"] == 0 for i in i64[:-1]) and
+                      (args.warmup == 0 or warm_rejected))
         fp64 = {"trajectories_per_s": args.fp64_steps / t64, "s_per_traj": t64 / args.fp64_steps,
+                "steps": args.fp64_steps, "warmup": args.fp64_warmup,
                 "cg_iters_per_traj": float(np.mean([i["cg_iters"] for i in i64])),
                 "dH": [i["dH"] for i in i64], "mixed_speedup": value / world / (args.fp64_steps / t64),
                 "mixed_minus_fp64_dH": ([m["dH"] - f["dH"] for m, f in zip(infos, i64)]
@@ -417,7 +506,21 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_block(oracle_sample())
+        traj4 = None
+        if args.nsteps == WORKLOAD["nsteps"]:
+            # the benchmark's mixed configuration on a 4^4 lattice with the same
+            # recipe, for the per-result differences against the oracle
+            U4 = lqcd.gauge_field((4, 4, 4, 4))
+            lqcd.gauge_start(U4, SEED, EPS)
+            st4 = lqcd.HmcState(U4, seed=SEED)
+            g4 = st4.trajectory(params)
+            traj4 = oracle_trajectory_4((g4, U4.download()))
+            st4.close()
+        if fp64:
+            iters, src = fp64["cg_iters_per_traj"], "measured on the FP64 GPU path of this run"
+        else:
+            iters, src = float(np.mean([i["cg_iters"] for i in infos])), "measured on the mixed GPU path of this run"
+        cpu = cpu_baseline_block(oracle_sample(openmp=True), oracle_sample(openmp=False), iters, src, traj4)
 
     if rank == 0:
         acc = [i["accepted"] for i in infos]
@@ -429,9 +532,8 @@ def run_ours(args):
             "dtype_detail": (f"f32 math ({args.sloppy} storage in the solver, {args.force_prec} forces); f64 master "
                              f"links/momenta, residuals, dots, link update, dH"),
             "data": "synthetic",
-            "config": dict(config_block(args, args.sloppy),
-                           dslash_form={0: "gathered", 1: "tma_staged_t", 2: "prefetched_links"}.get(
-                               lqcd.dslash_staging(), "?")),
+            "config": dict(config_block(args, args.sloppy, args.force_prec),
+                           dslash_form={0: "gathered", 1: "prefetched_links"}.get(lqcd.dslash_form(), "?")),
             "gpu_launches": launches,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "fp64_gpu_path": fp64,
             "physics": {"acceptance": float(np.mean(acc)), "dH": [i["dH"] for i in infos],
@@ -447,6 +549,97 @@ def run_ours(args):
     state.close()
     if dist is not None:
         dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------- plain FP64 path, 16^3x32
+
+FP64_16 = {"workload": "nf2_wilson_hmc_fp64_16x16x16x32", "dims": [16, 16, 16, 32], "beta": 5.6, "kappa": 0.1575,
+           "start": "exp(i*0.2*H), H Gell-Mann Gaussians from Philox seed 2", "integrator": "leapfrog",
+           "nsteps": 20, "tau": 1.0, "cg_tol": 1e-10, "seed": 2, "eps": 0.2}
+FP64_FLOP_PER_SITE = 1320  # one half hopping term per output site
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA/clock/SM x 2 flop x max SM clock
+
+
+def run_fp64_16(args):
+    """Config 2: the plain FP64 GPU path (FP64 hopping term, FP64 CG on
+    Mhat^dag Mhat to 1e-10, FP64 forces and link update) on 16^3x32, beta 5.6,
+    kappa 0.1575, start exp(i 0.2 H) from Philox seed 2, leapfrog with 20 steps,
+    tau 1, 10 trajectories with plaquette and acceptance logged; beside it one
+    full trajectory of the FP64 oracle on all host cores."""
+    import torch
+
+    from paper_1212_0785_gb300 import lqcd
+
+    torch.cuda.set_device(0)
+    wl = FP64_16
+    dims = tuple(wl["dims"])
+    steps = args.steps if args.steps is not None else 10
+    stream = torch.cuda.current_stream()
+    cg = lqcd.cg_params(tol=wl["cg_tol"], maxiter=20000, sloppy=lqcd.F64)
+    params = lqcd.hmc_params(wl["beta"], wl["kappa"], wl["tau"], wl["nsteps"], lqcd.LEAPFROG, cg=cg,
+                             chrono=int(args.chrono))
+    U = lqcd.gauge_field(dims)
+    lqcd.gauge_start(U, wl["seed"], wl["eps"])
+    st = lqcd.HmcState(U, seed=wl["seed"])
+    warm = [st.trajectory(params) for _ in range(args.warmup)]
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    lqcd.kernel_timers(True, only="dslash_f64")
+    launches0 = lqcd.launch_count()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [st.trajectory(params) for _ in range(steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = lqcd.launch_count() - launches0
+    t = e0.elapsed_time(e1) / 1e3
+    ms, n, nbytes = lqcd.kernel_timer_read("dslash_f64")
+    lqcd.kernel_timers(False)
+    Vh = int(np.prod(dims)) // 2
+    flops = FP64_FLOP_PER_SITE * Vh * n
+    achieved = flops / (ms * 1e-3) / 1e12 if n else None
+    roofline = {"kernel": "dslash_f64", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clock x 2 flop x 2.07 GHz",
+                "hbm_GB_per_s": nbytes / (ms * 1e-3) / 1e9 if n else None,
+                "avg_launch_us": ms / n * 1e3 if n else None, "launches": n}
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import oracle as orc
+
+        prev = orc.use_openmp(True)
+        Uo = orc.gauge_start(dims, wl["seed"], wl["eps"])
+        t0 = time.perf_counter()
+        _, o = orc.hmc_trajectory(dims, Uo, wl["beta"], wl["kappa"], wl["tau"], wl["nsteps"],
+                                  integrator=orc.LEAPFROG, seed=wl["seed"], traj=0, cg_tol=wl["cg_tol"])
+        t_or = time.perf_counter() - t0
+        threads = orc.num_threads()
+        orc.use_openmp(prev == "openmp")
+        cpu = {"value": 1.0 / t_or, "unit": "trajectories/s", "cores": threads, "kind": "oracle",
+               "sample": f"one full FP64 oracle trajectory at 16^3x32 (OpenMP build, {threads} threads, "
+                         f"{t_or:.1f} s, {o['cg_iters']:.0f} CG iterations from zero guesses)",
+               "derived": False, "host": host_cpu(),
+               "oracle_traj0": {"dH": o["dH"], "accepted": int(o["accepted"]), "plaq": o["plaq"]},
+               "gpu_traj0_minus_oracle": ({"dH": warm[0]["dH"] - o["dH"], "plaq": warm[0]["plaq"] - o["plaq"]}
+                                          if warm else None)}
+    line = {"metric": "trajectories/s", "value": steps / t, "unit": "trajectories/s", "n_gpus": 1, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": t / steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(wl, solver="fp64 CG", forces="f64 arithmetic", parallelism="single_gpu",
+                           initial_guess={0: "zero", 1: "previous solution"}.get(
+                               args.chrono, f"extrapolated through the last {args.chrono} solutions"),
+                           l2="inputs larger than L2 (FP64 links 151 MB)"),
+            "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "physics": {"acceptance": float(np.mean([i["accepted"] for i in infos])),
+                        "plaquette": [i["plaq"] for i in infos], "dH": [i["dH"] for i in infos],
+                        "accepted": [i["accepted"] for i in infos],
+                        "cg_iters_per_traj": float(np.mean([i["cg_iters"] for i in infos])),
+                        "cg_true_rel_res_max": max(i["cg_true_rel_res_max"] for i in infos)}}
+    print(json.dumps(line))
+    st.close()
     return 0
 
 
@@ -637,12 +830,13 @@ def run_service(args):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 5; 10 trajectories for fp64_16x32, 2 for chains64)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("hmc32", "chains64", "service"), default="hmc32",
-                    help="hmc32: the 32^3x64 trajectory (default); chains64: 64 batched chains; "
-                         "service: Poisson-arriving point-source solves")
+    ap.add_argument("--workload", choices=("hmc32", "fp64_16x32", "chains64", "service"), default="hmc32",
+                    help="hmc32: the 32^3x64 trajectory (default); fp64_16x32: the plain FP64 path on 16^3x32; "
+                         "chains64: 64 batched chains; service: Poisson-arriving point-source solves")
     ap.add_argument("--requests", type=int, default=40, help="service: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="service: mean arrivals per second")
     ap.add_argument("--hbm-budget", type=int, default=96, help="service: admission budget, GiB")
@@ -656,12 +850,20 @@ def main(argv=None):
     ap.add_argument("--dims", type=int, nargs=4, default=WORKLOAD["dims"])
     ap.add_argument("--nsteps", type=int, default=WORKLOAD["nsteps"],
                     help="MD steps per trajectory (16 for the benchmarked workload)")
-    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="timed trajectories of the plain FP64 GPU path (0: skip it)")
+    ap.add_argument("--fp64-warmup", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
+    if args.steps is None and args.workload in ("hmc32", "service"):
+        args.steps = 5
+    elif args.steps is None and args.workload == "chains64":
+        args.steps = 2
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "fp64_16x32":
+        return run_fp64_16(args)
     if args.workload == "chains64":
         return run_chains(args)
     if args.workload == "service":

@@ -72,7 +72,8 @@ typedef enum {
     LQCD_ENUMERIC = 4, /* non-finite value in a reduction (dH, residual) */
     LQCD_ECUDA = 5,    /* a CUDA runtime call failed; message from cudaGetErrorString */
     LQCD_EAGAIN = 6,   /* result not ready yet (asynchronous solve) */
-    LQCD_ETIMEOUT = 7  /* a bounded device-side wait gave up */
+    LQCD_ETIMEOUT = 7  /* a bounded wait gave up (reserved: no kernel of this library waits on
+                          another kernel, so no call returns it today) */
 } lqcd_status;
 
 typedef struct {
@@ -138,7 +139,11 @@ lqcd_status lqcd_set_allocator(lqcd_alloc_fn alloc, lqcd_free_fn free_fn, void *
 
 /* ------------------------------------------------------------ fields */
 
-/* Allocate a field on the current device (contents undefined).
+/* Allocate a field on the current device (contents undefined).  The paper's
+ * memory manager (Sec. 5) allocates device memory for a field on first use,
+ * from a pool, and keeps it resident; here the caller allocates each field
+ * once through the allocator hook and it stays resident until
+ * lqcd_field_free. 
  *   kind/prec/link_recon combinations:
  *     LQCD_GAUGE:       (F64, 18) master links; (F32|F16N|BF16, 12) compressed
  *                       copies storing rows 0, 1 (row 2 = conj(row0 x row1)).
@@ -155,6 +160,8 @@ lqcd_status lqcd_set_allocator(lqcd_alloc_fn alloc, lqcd_free_fn free_fn, void *
  * Errors: LQCD_EINVAL (bad lattice / combination), LQCD_ENOMEM. */
 lqcd_status lqcd_field_alloc(const lqcd_lattice *lat, lqcd_kind kind, lqcd_prec prec, int link_recon,
                              lqcd_field **out);
+/* Releases the field's device memory through the hook it was allocated with
+ * (Sec. 5: the memory manager returns a field's memory to its pool). */
 lqcd_status lqcd_field_free(lqcd_field *f);
 
 /* Bytes of device memory the field holds. */
@@ -164,7 +171,9 @@ lqcd_status lqcd_field_bytes(const lqcd_field *f, size_t *bytes);
  * none), for callers that share memory with another library. */
 lqcd_status lqcd_field_data(const lqcd_field *f, void **data_dev, void **norm_dev);
 
-/* Copy a host array in the canonical FP64 layout into the field (converting
+/* Host <-> device transfer of a field (Sec. 5: the memory manager moves a
+ * field between host and device memory when a kernel needs it on the device
+ * or the host reads it).  Copy a host array in the canonical FP64 layout into the field (converting
  * to the field's precision; gauge 12-real copies keep rows 0 and 1), or the
  * field out to such an array (compressed gauge fields are expanded by
  * reconstructing row 2).  Synchronous with respect to the host buffer: the
@@ -204,28 +213,25 @@ lqcd_status lqcd_eta_refresh(lqcd_field *eta, uint32_t seed, uint32_t chain, uin
 
 /* ------------------------------------------------------------ operators */
 
-/* Half hopping term: out = D_{p' p} in, p the parity of `in`, p' = 1 - p the
+/* Half hopping term of the Wilson operator (Sec. 6.2: the Nf = 2 Wilson
+ * fermions of the paper's runs; Sec. 6: the even-odd preconditioned operator
+ * whose inversion the paper hands to QUDA is Mhat = 1 - kappa^2 Deo Doe, built
+ * from these two halves).
+ * out = D_{p' p} in, p the parity of `in`, p' = 1 - p the
  * parity of `out` (EVEN/ODD kinds).  dagger != 0 applies D^dag = gamma5 D gamma5.
  * Precisions: U F64/18 with F64 spinors, or U 12-real of precision q with
  * spinors of precision q (q in F32, F16N, BF16; FP32 arithmetic). */
 lqcd_status lqcd_dslash(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int dagger, void *stream);
 
-/* The FP16+norm hopping term comes in three forms with bitwise-equal results:
+/* The FP16+norm hopping term comes in two forms with bitwise-equal results:
  *   0  every operand gathered by its thread;
- *   1  (lattices with Lx/2 * Ly a multiple of 128) each block of 128 output
- *      sites first stages its +-t neighbour spinors and the links it needs
- *      from them in shared memory with bulk asynchronous copies (the TMA engine
- *      of sm_90+); elsewhere form 0 runs;
- *   2  (the default) each thread first starts asynchronous copies (cp.async)
+ *   1  (the default) each thread first starts asynchronous copies (cp.async)
  *      of its eight links into shared memory, then gathers the neighbour
  *      spinors and waits for each direction's links only when it needs them.
- * lqcd_dslash_staging(mode) selects the form (0, 1, 2; -1 queries) and returns
- * the previous one (process-wide).  A form-1 block's wait for its copies is
- * bounded: if one ever gives up, lqcd_dslash_check (which synchronises stream)
- * returns LQCD_ETIMEOUT once and the results since the last check are invalid;
- * every CG solve makes that check before it returns. */
-int lqcd_dslash_staging(int mode);
-lqcd_status lqcd_dslash_check(void *stream);
+ * lqcd_dslash_form(form) selects the form (0, 1; a negative value queries)
+ * and returns the previous one (process-wide); an unknown form returns -1,
+ * leaves the setting unchanged and sets lqcd_last_error. */
+int lqcd_dslash_form(int form);
 
 /* out_e = Mhat in_e = in_e - kappa^2 Deo Doe in_e (dagger: Mhat^dag).  EVEN
  * spinors, precision rules as lqcd_dslash.  Uses one temporary odd spinor. */
@@ -238,8 +244,11 @@ typedef struct {
     double tol;           /* stop when the true |r| <= tol |b| (r = b - Mhat^dag Mhat x) */
     int maxiter;          /* total iteration cap (LQCD_ENOCONV when reached) */
     lqcd_prec sloppy;     /* LQCD_F64: plain FP64 CG.  F32/F16N/BF16: reliable-update mixed
-                             CG with that sloppy storage (FP32 arithmetic, FP64 dot products,
-                             FP64 residual recomputation and solution accumulation) */
+                             CG with that sloppy storage (FP32 arithmetic, FP64 sums of the dot
+                             products).  Its accurate solution, source, links and residual are
+                             held in float-float storage (a pair of FP32 numbers, ~48
+                             significant bits) and the residual b - A x is recomputed and the
+                             solution accumulated in float-float arithmetic, not FP64 */
     double delta;         /* reliable-update threshold: recompute the true residual when the
                              sloppy |r| drops below delta * max |r| since the last update */
     int max_restarts;     /* FP64 CG only: restarts allowed when the true residual fails */
@@ -250,7 +259,10 @@ typedef struct {
 typedef struct {
     int iters;            /* CG iterations (sloppy iterations for the mixed solver) */
     int restarts;         /* FP64 restarts / mixed reliable updates */
-    double true_rel_res;  /* |b - A x| / |b| in FP64 at exit */
+    double true_rel_res;  /* |b - A x| / |b| at exit, recomputed accurately: in FP64 by the FP64
+                             solve; in float-float arithmetic (~48 bits) from the float-float
+                             solution by the mixed solve (the FP64 x returned is that solution
+                             rounded) */
     double seconds;       /* wall time of the call */
     int accurate_residuals; /* accurate (FP64 or float-float) residuals b - A x computed: of the
                                initial guess, at every reliable update or restart, at the end */
@@ -426,7 +438,9 @@ lqcd_status lqcd_hmc_refresh(lqcd_hmc_state *s, const lqcd_hmc_params *p, double
 /* H = T + S_g + S_f for the state's current (U, P, phi) (S_f by a CG solve). */
 lqcd_status lqcd_hmc_hamiltonian(lqcd_hmc_state *s, const lqcd_hmc_params *p, double *H, void *stream);
 
-/* One molecular-dynamics step of length tau/nsteps with the state's phi, as
+/* One molecular-dynamics step (Sec. 1: the momentum updates with their force
+ * terms, and the link update by the exponential of SU(3) matrices, are among
+ * the HMC parts the paper moves to the GPU) of length tau/nsteps with the state's phi, as
  * a whole step (leapfrog: kick dt/2, drift dt, kick dt/2; Omelyan:
  * lambda dt, dt/2, (1-2 lambda) dt, dt/2, lambda dt). */
 lqcd_status lqcd_md_step(lqcd_hmc_state *s, const lqcd_hmc_params *p, void *stream);

@@ -38,6 +38,13 @@
  * Even/odd fields are full-lattice arrays whose other-parity sites are ignored
  * on input and written as zero on output.
  *
+ * Built twice from this one source: plainly (serial), and with -fopenmp, where
+ * the pragmas split the loops over sites whose iterations write disjoint
+ * outputs (hopping term, forces, link update, refresh, start configuration,
+ * reunitarization with its exact max) across threads.  Every sum (dot
+ * products, plaquette, kinetic energy) stays a serial loop in site order, so
+ * both builds give bitwise the same results.
+ *
  * Build with -ffp-contract=off so the same source rounds identically on every host.
  */
 #include <complex.h>
@@ -360,6 +367,15 @@ static void gamma_init(void)
     G_ready = 1;
 }
 
+/* threads the site loops use: omp_get_max_threads() in the OpenMP build, 1 in
+ * the serial one */
+#ifdef _OPENMP
+#include <omp.h>
+int or_num_threads(void) { return omp_get_max_threads(); }
+#else
+int or_num_threads(void) { return 1; }
+#endif
+
 /* Copy of one gamma matrix (0..3 = gamma_1..gamma_4, 4 = gamma_5), row-major
  * [4][4][re,im]. */
 void or_gamma(int which, double *out32)
@@ -458,6 +474,8 @@ static void dslash_full(const geom *g, const double *U, const double *in, double
         apply_g5(g, in, tmp);
         src = tmp;
     }
+    gamma_init();
+    #pragma omp parallel for schedule(static)
     for (long x = 0; x < g->V; x++) {
         cplx r[12];
         if (out_parity >= 0 && site_parity(g, x) != out_parity) {
@@ -905,6 +923,7 @@ int or_gauge_force(const int *dims, const double *U, double beta, double *F)
 {
     geom g;
     if (geom_init(&g, dims, -1)) return -1;
+    #pragma omp parallel for schedule(static)
     for (long x = 0; x < g.V; x++)
         for (int mu = 0; mu < 4; mu++) gauge_force_link(&g, U, beta, x, mu, F + (x * 4 + mu) * 8);
     return 0;
@@ -930,7 +949,9 @@ int or_fermion_force(const int *dims, int t_bc, const double *U, double kappa, c
     double *A = malloc(sizeof(double) * 24 * g.V);
     double *B = malloc(sizeof(double) * 24 * g.V);
     fermion_force_fields(&g, U, kappa, X, A, B);
+    gamma_init();
     if (n < 0) {
+        #pragma omp parallel for schedule(static)
         for (long x = 0; x < g.V; x++)
             for (int mu = 0; mu < 4; mu++) fermion_force_link(&g, U, kappa, A, B, x, mu, F + (x * 4 + mu) * 8);
     } else {
@@ -1078,6 +1099,7 @@ int or_link_update(const int *dims, double *U, const double *P, double c)
 {
     geom g;
     if (geom_init(&g, dims, -1)) return -1;
+    #pragma omp parallel for schedule(static)
     for (long x = 0; x < g.V; x++)
         for (int mu = 0; mu < 4; mu++) {
             mat3 H = algebra_to_mat(P + (x * 4 + mu) * 8);
@@ -1095,6 +1117,7 @@ int or_reunitarize(const int *dims, double *U, double *maxdev)
     geom g;
     if (geom_init(&g, dims, -1)) return -1;
     double m = 0;
+#pragma omp parallel for schedule(static) reduction(max : m)
     for (long x = 0; x < g.V; x++)
         for (int mu = 0; mu < 4; mu++) {
             mat3 u = link_get(U, x, mu);
@@ -1138,9 +1161,10 @@ typedef struct {
 static void kick(const geom *g, const double *U, double *P, const double *phi, const md_params *mp, double c,
                  md_stats *st)
 {
-    double f[8];
+    #pragma omp parallel for schedule(static)
     for (long x = 0; x < g->V; x++)
         for (int mu = 0; mu < 4; mu++) {
+            double f[8];
             gauge_force_link(g, U, mp->beta, x, mu, f);
             for (int a = 0; a < 8; a++) P[(x * 4 + mu) * 8 + a] -= c * f[a];
         }
@@ -1154,8 +1178,11 @@ static void kick(const geom *g, const double *U, double *P, const double *phi, c
         st->cg_iters += it;
         st->n_solves++;
         fermion_force_fields(g, U, mp->kappa, X, A, B);
+        gamma_init();
+        #pragma omp parallel for schedule(static)
         for (long x = 0; x < g->V; x++)
             for (int mu = 0; mu < 4; mu++) {
+                double f[8];
                 fermion_force_link(g, U, mp->kappa, A, B, x, mu, f);
                 for (int a = 0; a < 8; a++) P[(x * 4 + mu) * 8 + a] -= c * f[a];
             }
@@ -1167,6 +1194,7 @@ static void kick(const geom *g, const double *U, double *P, const double *phi, c
 
 static void drift(const geom *g, double *U, const double *P, double c)
 {
+    #pragma omp parallel for schedule(static)
     for (long x = 0; x < g->V; x++)
         for (int mu = 0; mu < 4; mu++) {
             mat3 H = algebra_to_mat(P + (x * 4 + mu) * 8);
@@ -1344,9 +1372,11 @@ static void add_force_xy(const geom *g, const double *U, double kappa, const dou
     double *A = malloc(sizeof(double) * 24 * g->V);
     double *B = malloc(sizeof(double) * 24 * g->V);
     fermion_force_fields_xy(g, U, X, Y, A, B);
-    double f[8];
+    gamma_init();
+    #pragma omp parallel for schedule(static)
     for (long x = 0; x < g->V; x++)
         for (int mu = 0; mu < 4; mu++) {
+            double f[8];
             fermion_force_link(g, U, kappa, A, B, x, mu, f);
             for (int a = 0; a < 8; a++) P[(x * 4 + mu) * 8 + a] -= c * f[a];
         }
@@ -1371,9 +1401,10 @@ static void hb_kick(const geom *g, const double *U, double *P, const hb_params *
                     const double *phi_h, int terms, double c, md_stats *st)
 {
     if (terms & TERM_GAUGE) {
-        double f[8];
+        #pragma omp parallel for schedule(static)
         for (long x = 0; x < g->V; x++)
             for (int mu = 0; mu < 4; mu++) {
+                double f[8];
                 gauge_force_link(g, U, hp->beta, x, mu, f);
                 for (int a = 0; a < 8; a++) P[(x * 4 + mu) * 8 + a] -= c * f[a];
             }

@@ -22,32 +22,53 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lqcd_oracle.c")
-_LIB = os.path.join(_HERE, "liblqcd_oracle.so")
+_LIBS = {"serial": os.path.join(_HERE, "liblqcd_oracle.so"),
+         "openmp": os.path.join(_HERE, "liblqcd_oracle_omp.so")}
 _lock = threading.Lock()
-_lib = None
+_loaded = {}
+_variant = "serial"
 
 CFLAGS = ["-O2", "-fPIC", "-shared", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math"]
 
 
-def build(force: bool = False) -> str:
-    """Compile lqcd_oracle.c into liblqcd_oracle.so next to it (gcc)."""
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
-    os.replace(tmp, _LIB)
-    return _LIB
+def build(force: bool = False, variant: str = "serial") -> str:
+    """Compile lqcd_oracle.c into liblqcd_oracle.so (serial) or
+    liblqcd_oracle_omp.so (the same source with -fopenmp) next to it (gcc)."""
+    out = _LIBS[variant]
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    extra = ["-fopenmp"] if variant == "openmp" else []
+    subprocess.check_call(["gcc", *CFLAGS, *extra, _SRC, "-o", tmp, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
+def use_openmp(on: bool) -> str:
+    """Select the build every call below goes to (the OpenMP build spreads the
+    site loops over OMP_NUM_THREADS threads, bitwise the same results);
+    returns the previous selection."""
+    global _variant
+    prev = _variant
+    _variant = "openmp" if on else "serial"
+    return prev
 
 
 def lib():
-    global _lib
     with _lock:
-        if _lib is None:
-            build()
-            _lib = ctypes.CDLL(_LIB)
-            _declare(_lib)
-    return _lib
+        L = _loaded.get(_variant)
+        if L is None:
+            build(variant=_variant)
+            L = ctypes.CDLL(_LIBS[_variant])
+            _declare(L)
+            _loaded[_variant] = L
+    return L
+
+
+def num_threads() -> int:
+    """threads the selected build's site loops use"""
+    return int(lib().or_num_threads())
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -59,6 +80,7 @@ _i, _d, _u32, _l = ctypes.c_int, ctypes.c_double, ctypes.c_uint32, ctypes.c_long
 
 def _declare(L):
     sig = {
+        "or_num_threads": (_i, []),
         "or_gamma": (None, [_i, _dp]),
         "or_philox4x32_10": (None, [_up, _up, _up]),
         "or_uniform2": (None, [_u32] * 6 + [_dp]),

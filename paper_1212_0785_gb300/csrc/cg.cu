@@ -597,7 +597,6 @@ lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, con
         if (h.pause) run.on_pause(h, s);
     }
     if (info) *info = run.inf;
-    if (run.status == LQCD_OK || run.status == LQCD_ENOCONV) LQCD_TRY(dslash_staging_check(s));
     return run.status;
 }
 

@@ -16,23 +16,19 @@
 #include "df64.cuh"
 #include "dslash.cuh"
 #include "dslash_site.cuh"
-#include "dslash_staged.cuh"
 
 namespace lqcd {
 
 // ---------------------------------------------------------------- kernels
 
-// Sp of D in at site cb.  FORM 1 (staged; FP16+norm, geometry from
-// staging_fits): the block stages its far operands first, and every thread of
-// the block calls it.  FORM 2 (FP16+norm): the thread prefetches its links.
-// (The other precisions' FORM 1, 2 instances are never launched.)
+// Sp of D in at site cb.  FORM 1 (FP16+norm): the thread prefetches its
+// links into shared memory first.  FORM 0: every operand gathered by its
+// thread.  (The other precisions' FORM 1 instances are never launched.)
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, int FORM>
 __device__ __forceinline__ Sp<R> site_value(const SpinorRef<SP> &in, const GaugeRef<GP> &U, const Geo &g, int cb,
                                             int out_par)
 {
     if constexpr (FORM == 1 && SP == LQCD_F16N && GP == LQCD_F16N)
-        return staged_site<R, DAG>(in, U, g, cb, out_par);
-    else if constexpr (FORM == 2 && SP == LQCD_F16N && GP == LQCD_F16N)
         return prefetch_site<R, DAG>(in, U, g, cb, out_par);
     else
         return dslash_site<R, SP, GP, DAG>(in, U, g, cb, out_par);
@@ -44,7 +40,7 @@ __device__ __forceinline__ void plain_body(SpinorRef<SP> out, SpinorRef<SP> in, 
 {
     if (skip && *skip) return;
     int cb = blockIdx.x * DS_BLOCK + threadIdx.x;
-    if (!(FORM == 1 && SP == LQCD_F16N) && cb >= g.Vh) return;
+    if (cb >= g.Vh) return;
     out.store(cb, site_value<R, SP, GP, DAG, FORM>(in, U, g, cb, out_par));
 }
 
@@ -56,7 +52,7 @@ __device__ __forceinline__ void xpay_body(SpinorRef<SP> out, SpinorRef<SP> in, G
     if (skip && *skip) return;
     int cb = blockIdx.x * DS_BLOCK + threadIdx.x;
     R n2 = R(0);
-    if ((FORM == 1 && SP == LQCD_F16N) || cb < g.Vh) {
+    if (cb < g.Vh) {
         Sp<R> d = site_value<R, SP, GP, DAG, FORM>(in, U, g, cb, out_par);
         Sp<R> xv = x.template load_rw<R>(cb);
 #pragma unroll
@@ -79,7 +75,7 @@ __device__ __forceinline__ void cg_body(SpinorRef<SP> in, GaugeRef<GP> U, Geo g,
     const R alpha = (R)sc->alpha;
     int cb = blockIdx.x * DS_BLOCK + threadIdx.x;
     R n2 = R(0);
-    if ((FORM == 1 && SP == LQCD_F16N) || cb < g.Vh) {
+    if (cb < g.Vh) {
         Sp<R> ap = site_value<R, SP, GP, DAG, FORM>(in, U, g, cb, out_par);
         {
             Sp<R> tv = t.template load_rw<R>(cb);
@@ -112,8 +108,8 @@ __device__ __forceinline__ void cg_body(SpinorRef<SP> in, GaugeRef<GP> U, Geo g,
     block_sum_store_wp<DS_BLOCK>(n2, partials);
 }
 
-// The kernels: unstaged, and staged (FP16+norm; 7 blocks of 128 per SM, which
-// its 19.6 KiB of staged operands allow) with the same bodies.
+// The kernels: gathered operands, and (FP16+norm) prefetched links with the
+// same bodies (7 blocks of 128 per SM, 24 KiB of shared memory each).
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
 __global__ void __launch_bounds__(DS_BLOCK) dslash_plain_kernel(SpinorRef<SP> out, SpinorRef<SP> in, GaugeRef<GP> U,
                                                                  Geo g, int out_par, const int *skip)
@@ -121,26 +117,11 @@ __global__ void __launch_bounds__(DS_BLOCK) dslash_plain_kernel(SpinorRef<SP> ou
     plain_body<R, SP, GP, DAG, 0>(out, in, U, g, out_par, skip);
 }
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
-__global__ void __launch_bounds__(DS_BLOCK, 7) dslash_plain_staged_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
-                                                                           GaugeRef<GP> U, Geo g, int out_par,
-                                                                           const int *skip)
-{
-    plain_body<R, SP, GP, DAG, 1>(out, in, U, g, out_par, skip);
-}
-template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
 __global__ void __launch_bounds__(DS_BLOCK) dslash_xpay_kernel(SpinorRef<SP> out, SpinorRef<SP> in, GaugeRef<GP> U,
                                                                 Geo g, int out_par, SpinorRef<SP> x, R b,
                                                                 double *partials, int nblocks, const int *skip)
 {
     xpay_body<R, SP, GP, DAG, 0>(out, in, U, g, out_par, x, b, partials, nblocks, skip);
-}
-template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
-__global__ void __launch_bounds__(DS_BLOCK, 7) dslash_xpay_staged_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
-                                                                          GaugeRef<GP> U, Geo g, int out_par,
-                                                                          SpinorRef<SP> x, R b, double *partials,
-                                                                          int nblocks, const int *skip)
-{
-    xpay_body<R, SP, GP, DAG, 1>(out, in, U, g, out_par, x, b, partials, nblocks, skip);
 }
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, lqcd_prec XP>
 __global__ void __launch_bounds__(DS_BLOCK) dslash_cg_kernel(SpinorRef<SP> in, GaugeRef<GP> U, Geo g, int out_par,
@@ -150,23 +131,13 @@ __global__ void __launch_bounds__(DS_BLOCK) dslash_cg_kernel(SpinorRef<SP> in, G
 {
     cg_body<R, SP, GP, DAG, XP, 0>(in, U, g, out_par, t, b, xs, r, p, partials, nblocks, sc);
 }
-template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, lqcd_prec XP>
-__global__ void __launch_bounds__(DS_BLOCK, 7) dslash_cg_staged_kernel(SpinorRef<SP> in, GaugeRef<GP> U, Geo g,
-                                                                        int out_par, SpinorRef<SP> t, R b,
-                                                                        SpinorRef<XP> xs, SpinorRef<SP> r,
-                                                                        SpinorRef<SP> p, double *partials,
-                                                                        int nblocks, const CgScalars *sc)
-{
-    cg_body<R, SP, GP, DAG, XP, 1>(in, U, g, out_par, t, b, xs, r, p, partials, nblocks, sc);
-}
 
-// FP16+norm with prefetched links (7 blocks of 128 per SM, 24 KiB each)
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
 __global__ void __launch_bounds__(DS_BLOCK, 7) dslash_plain_prefetch_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
                                                                              GaugeRef<GP> U, Geo g, int out_par,
                                                                              const int *skip)
 {
-    plain_body<R, SP, GP, DAG, 2>(out, in, U, g, out_par, skip);
+    plain_body<R, SP, GP, DAG, 1>(out, in, U, g, out_par, skip);
 }
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
 __global__ void __launch_bounds__(DS_BLOCK, 7) dslash_xpay_prefetch_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
@@ -174,7 +145,7 @@ __global__ void __launch_bounds__(DS_BLOCK, 7) dslash_xpay_prefetch_kernel(Spino
                                                                             SpinorRef<SP> x, R b, double *partials,
                                                                             int nblocks, const int *skip)
 {
-    xpay_body<R, SP, GP, DAG, 2>(out, in, U, g, out_par, x, b, partials, nblocks, skip);
+    xpay_body<R, SP, GP, DAG, 1>(out, in, U, g, out_par, x, b, partials, nblocks, skip);
 }
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, lqcd_prec XP>
 __global__ void __launch_bounds__(DS_BLOCK, 7) dslash_cg_prefetch_kernel(SpinorRef<SP> in, GaugeRef<GP> U, Geo g,
@@ -183,7 +154,7 @@ __global__ void __launch_bounds__(DS_BLOCK, 7) dslash_cg_prefetch_kernel(SpinorR
                                                                           SpinorRef<SP> p, double *partials,
                                                                           int nblocks, const CgScalars *sc)
 {
-    cg_body<R, SP, GP, DAG, XP, 2>(in, U, g, out_par, t, b, xs, r, p, partials, nblocks, sc);
+    cg_body<R, SP, GP, DAG, XP, 1>(in, U, g, out_par, t, b, xs, r, p, partials, nblocks, sc);
 }
 
 // ---------------------------------------------------------------- dispatch
@@ -217,24 +188,20 @@ struct ArithOf<PREC_DF> {
     using type = Df;
 };
 
-// the FP16+norm form: 2 prefetched links (default), 1 staged, 0 gathered
-static std::atomic<int> g_staging{2};
+// the FP16+norm form: 1 prefetched links (default), 0 gathered
+static std::atomic<int> g_form{1};
 
 template <lqcd_prec P, lqcd_prec GP>
-static int use_staging(const Geo &g)
+static int use_form(const Geo &)
 {
     if (P != LQCD_F16N || GP != LQCD_F16N) return 0;
-    const int f = g_staging.load(std::memory_order_relaxed);
-    if (f == 2) return 2;
-    return f == 1 && staging_fits(g) ? 1 : 0;
+    return g_form.load(std::memory_order_relaxed);
 }
 
-// launch kernel K in the form chosen by use_staging
-#define LQCD_LAUNCH_STAGED(form, kern, targs, grid, args)                                                            \
+// launch kernel K in the form chosen by use_form
+#define LQCD_LAUNCH_FORM(form, kern, targs, grid, args)                                                              \
     do {                                                                                                             \
         if (form == 1)                                                                                               \
-            kern##_staged_kernel<LQCD_UNPAREN targs><<<grid, DS_BLOCK, 0, s>>> args;                                 \
-        else if (form == 2)                                                                                          \
             kern##_prefetch_kernel<LQCD_UNPAREN targs><<<grid, DS_BLOCK, 0, s>>> args;                               \
         else                                                                                                         \
             kern##_kernel<LQCD_UNPAREN targs><<<grid, DS_BLOCK, 0, s>>> args;                                        \
@@ -248,12 +215,12 @@ static void launch_plain(lqcd_field *out, const lqcd_field *U, const lqcd_field 
     using R = typename ArithOf<P>::type;
     Geo g = make_geo(in->lat);
     int nb = dslash_blocks(g.Vh);
-    const int st = use_staging<P, GP>(g);
+    const int st = use_form<P, GP>(g);
     if (dagger)
-        LQCD_LAUNCH_STAGED(st, dslash_plain, (R, P, GP, true), nb,
+        LQCD_LAUNCH_FORM(st, dslash_plain, (R, P, GP, true), nb,
                            (spinor_ref<P>(out), spinor_ref<P>(in), gauge_ref<GP>(U), g, out_parity(out), skip));
     else
-        LQCD_LAUNCH_STAGED(st, dslash_plain, (R, P, GP, false), nb,
+        LQCD_LAUNCH_FORM(st, dslash_plain, (R, P, GP, false), nb,
                            (spinor_ref<P>(out), spinor_ref<P>(in), gauge_ref<GP>(U), g, out_parity(out), skip));
 }
 
@@ -264,13 +231,13 @@ static void launch_xpay(lqcd_field *out, const lqcd_field *U, const lqcd_field *
     using R = typename ArithOf<P>::type;
     Geo g = make_geo(in->lat);
     int nb = dslash_blocks(g.Vh);
-    const int st = use_staging<P, GP>(g);
+    const int st = use_form<P, GP>(g);
     if (dagger)
-        LQCD_LAUNCH_STAGED(st, dslash_xpay, (R, P, GP, true), nb,
+        LQCD_LAUNCH_FORM(st, dslash_xpay, (R, P, GP, true), nb,
                            (spinor_ref<P>(out), spinor_ref<P>(in), gauge_ref<GP>(U), g, out_parity(out),
                             spinor_ref<P>(x), (R)b, partials, nb, skip));
     else
-        LQCD_LAUNCH_STAGED(st, dslash_xpay, (R, P, GP, false), nb,
+        LQCD_LAUNCH_FORM(st, dslash_xpay, (R, P, GP, false), nb,
                            (spinor_ref<P>(out), spinor_ref<P>(in), gauge_ref<GP>(U), g, out_parity(out),
                             spinor_ref<P>(x), (R)b, partials, nb, skip));
 }
@@ -284,32 +251,25 @@ static void launch_cg(const lqcd_field *U, const lqcd_field *in, int dagger, con
     Geo g = make_geo(in->lat);
     int nb = dslash_blocks(g.Vh);
     int op = out_parity(t);
-    const int st = use_staging<P, P>(g);
+    const int st = use_form<P, P>(g);
     if (dagger)
-        LQCD_LAUNCH_STAGED(st, dslash_cg, (R, P, P, true, XP), nb,
+        LQCD_LAUNCH_FORM(st, dslash_cg, (R, P, P, true, XP), nb,
                            (spinor_ref<P>(in), gauge_ref<P>(U), g, op, spinor_ref<P>(t), (R)b, spinor_ref<XP>(xs),
                             spinor_ref<P>(r), spinor_ref<P>(p), partials, nb, sc));
     else
-        LQCD_LAUNCH_STAGED(st, dslash_cg, (R, P, P, false, XP), nb,
+        LQCD_LAUNCH_FORM(st, dslash_cg, (R, P, P, false, XP), nb,
                            (spinor_ref<P>(in), gauge_ref<P>(U), g, op, spinor_ref<P>(t), (R)b, spinor_ref<XP>(xs),
                             spinor_ref<P>(r), spinor_ref<P>(p), partials, nb, sc));
 }
 
-lqcd_status dslash_staging_check(cudaStream_t s)
+int dslash_form_set(int form)
 {
-    int flag = 0, zero = 0;
-    LQCD_CUDA(cudaMemcpyFromSymbolAsync(&flag, g_stage_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
-    LQCD_CUDA(cudaStreamSynchronize(s));
-    if (!flag) return LQCD_OK;
-    LQCD_CUDA(cudaMemcpyToSymbolAsync(g_stage_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
-    LQCD_CUDA(cudaStreamSynchronize(s));
-    set_error("dslash: a block's wait for its staged operands gave up; the results since the last check are invalid");
-    return LQCD_ETIMEOUT;
-}
-
-int dslash_staging_set(int enable)
-{
-    return enable < 0 ? g_staging.load() : g_staging.exchange(enable >= 2 ? 2 : enable ? 1 : 0);
+    if (form < 0) return g_form.load();
+    if (form > 1) {
+        set_error("dslash_form: unknown form %d (0 gathered, 1 prefetched links)", form);
+        return -1;
+    }
+    return g_form.exchange(form);
 }
 
 lqcd_status dslash_plain(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int dagger, const int *skip,
@@ -410,8 +370,6 @@ lqcd_status lqcd_mhat(lqcd_field *out, const lqcd_field *U, const lqcd_field *in
     return LQCD_OK;
 }
 
-int lqcd_dslash_staging(int enable) { return dslash_staging_set(enable); }
-
-lqcd_status lqcd_dslash_check(void *stream) { return dslash_staging_check((cudaStream_t)stream); }
+int lqcd_dslash_form(int form) { return dslash_form_set(form); }
 
 } // extern "C"

@@ -52,12 +52,9 @@ lqcd_status dslash_cg(const lqcd_field *U, const lqcd_field *in, int dagger, con
                       lqcd_field *xs, lqcd_field *r, const lqcd_field *p, double *partials, const CgScalars *sc,
                       cudaStream_t s);
 
-// LQCD_ETIMEOUT (and the flag cleared) if a staged hopping-term block gave up
-// waiting for its operands since the last check; synchronises s
-lqcd_status dslash_staging_check(cudaStream_t s);
-// switch the staged FP16+norm kernels on (1) or off (0), or query (< 0);
-// returns the previous setting
-int dslash_staging_set(int enable);
+// the FP16+norm hopping-term form: 1 prefetched links (default), 0 gathered;
+// returns the previous form (form < 0: query; -1 and an error for an unknown form)
+int dslash_form_set(int form);
 
 // out = D in, or x + b D in if x is given, with float-float fields and links
 // (precision code 4; dslash_df.cu)

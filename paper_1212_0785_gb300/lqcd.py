@@ -120,8 +120,7 @@ _SIGS = {
     "lqcd_momentum_refresh": (_i, [_vp, _u32, _u32, _u32, _vp]),
     "lqcd_eta_refresh": (_i, [_vp, _u32, _u32, _u32, _vp]),
     "lqcd_dslash": (_i, [_vp, _vp, _vp, _i, _vp]),
-    "lqcd_dslash_staging": (_i, [_i]),
-    "lqcd_dslash_check": (_i, [_vp]),
+    "lqcd_dslash_form": (_i, [_i]),
     "lqcd_mhat": (_i, [_vp, _vp, _vp, _d, _i, _vp]),
     "lqcd_cg_solve": (_i, [_vp, _vp, _vp, _vp, _d, ctypes.POINTER(CgParams), ctypes.POINTER(CgInfo), _vp]),
     "lqcd_gauge_force": (_i, [_vp, _vp, _d, _d, _vp]),
@@ -645,18 +644,12 @@ class Service:
             pass
 
 
-DSLASH_GATHER, DSLASH_STAGED, DSLASH_PREFETCH = 0, 1, 2
+DSLASH_GATHER, DSLASH_PREFETCH = 0, 1
 
 
-def dslash_staging(mode=None) -> int:
+def dslash_form(form=None) -> int:
     """query (None) or select the form of the FP16+norm hopping term: 0
-    gathered, 1 TMA-staged +-t operands, 2 prefetched links (the default);
-    returns the previous form"""
-    if mode is not None and int(mode) not in (0, 1, 2):
-        raise ValueError("dslash form must be 0, 1 or 2")
-    return int(lib().lqcd_dslash_staging(-1 if mode is None else int(mode)))
-
-
-def dslash_check(stream=None):
-    """raises LqcdError(ETIMEOUT) if a staged block gave up waiting since the last check"""
-    _check(lib().lqcd_dslash_check(_s(stream)), "dslash_check")
+    gathered, 1 prefetched links (the default); returns the previous form"""
+    if form is not None and int(form) not in (0, 1):
+        raise ValueError("dslash form must be 0 or 1")
+    return int(lib().lqcd_dslash_form(-1 if form is None else int(form)))

@@ -74,18 +74,20 @@ def test_allocator_hook_validation(L):
 
 def test_dslash_form_switch_is_host_state(L):
     """the FP16+norm hopping-term form is a process-wide host setting: set,
-    query and restore need no device; values above 2 select form 2"""
-    prev = lqcd.dslash_staging()
+    query and restore need no device; an unknown form is refused and changes
+    nothing"""
+    prev = lqcd.dslash_form()
     try:
-        assert prev in (lqcd.DSLASH_GATHER, lqcd.DSLASH_STAGED, lqcd.DSLASH_PREFETCH)
-        lqcd.dslash_staging(lqcd.DSLASH_GATHER)
-        assert lqcd.dslash_staging(lqcd.DSLASH_STAGED) == lqcd.DSLASH_GATHER
-        assert lqcd.dslash_staging() == lqcd.DSLASH_STAGED
-        assert L.lqcd_dslash_staging(7) == lqcd.DSLASH_STAGED and lqcd.dslash_staging() == lqcd.DSLASH_PREFETCH
+        assert prev in (lqcd.DSLASH_GATHER, lqcd.DSLASH_PREFETCH)
+        lqcd.dslash_form(lqcd.DSLASH_GATHER)
+        assert lqcd.dslash_form(lqcd.DSLASH_PREFETCH) == lqcd.DSLASH_GATHER
+        assert lqcd.dslash_form() == lqcd.DSLASH_PREFETCH
+        assert L.lqcd_dslash_form(7) == -1 and lqcd.dslash_form() == lqcd.DSLASH_PREFETCH
+        assert b"unknown form" in L.lqcd_last_error()
         with pytest.raises(ValueError):
-            lqcd.dslash_staging(-2)
+            lqcd.dslash_form(2)
     finally:
-        lqcd.dslash_staging(prev)
+        lqcd.dslash_form(prev)
 
 
 def test_info_structs_carry_the_solver_counters():

@@ -60,7 +60,11 @@ def test_reference_arm_prints_one_json_line():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == "trajectories/s" and d["higher_is_better"] is True
-    assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    cb = d["cpu_baseline"]
+    assert d["value"] > 0 and cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
+    assert cb["single_thread"]["cores"] == 1 and cb["single_thread"]["value"] > 0
+    assert cb["host"]["nproc"] == os.cpu_count() and cb["host"]["model"]
+    assert d["config"]["forces"] == "f64 arithmetic" and d["config"]["solver"] == "fp64 CG"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["config"]["workload"] == "nf2_wilson_hmc_32x32x32x64"
 
@@ -70,6 +74,13 @@ def test_reference_arm_other_ranks_do_nothing():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "0"], capture_output=True, text=True, env=env, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_derived_trajectory_counts_every_part():
+    sample = {"parts_s": {"cg_iteration": 1.0, "gauge_force": 10.0, "fermion_force": 100.0, "link_update": 1000.0},
+              "scale": 2.0}
+    # 16 Omelyan steps: 33 force evaluations, 32 link updates
+    assert bench.derived_traj_s(sample, 7) == 2.0 * (7 + 33 * 110.0 + 32 * 1000.0)
 
 
 def test_stored_traffic_is_dropped_when_the_kernel_changed(tmp_path, monkeypatch):

@@ -1,0 +1,75 @@
+"""The two forms of the FP16+norm hopping term -- every operand gathered by
+its thread (0), and each thread's links prefetched into shared memory by
+cp.async (1, the default) -- give bitwise the same results on full and
+ragged last blocks, across the z and t boundaries, for both boundary
+conditions, both parities, D and D^dag, the axpy/CG epilogues and a whole
+mixed solve; and they match the oracle to FP16 accuracy."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1212_0785_gb300 import inputs, lqcd
+from tests.gpu_util import full_from_half, half, rel_err
+
+pytestmark = pytest.mark.gpu
+
+# Vh = 512, 576 (whole blocks of 128), 432 and 1728 (a ragged last block)
+DIMS = [(16, 16, 4, 4), (32, 8, 4, 6), (6, 6, 4, 6), (8, 6, 6, 12)]
+FORMS = (lqcd.DSLASH_GATHER, lqcd.DSLASH_PREFETCH)
+F16N_TOL = 3e-3  # FP16+norm storage rounding, derived in the design doc section 7a
+
+
+@pytest.fixture
+def form():
+    prev = lqcd.dslash_form()
+    yield
+    lqcd.dslash_form(prev)
+
+
+def _fields(dims, t_bc, seed):
+    Uh = inputs.random_gauge(dims, seed, spread=0.5)
+    U = lqcd.gauge_field(dims, t_bc=t_bc).upload(Uh)
+    Us = lqcd.gauge_field(dims, lqcd.F16N, t_bc=t_bc).copy_from(U)
+    return Uh, U, Us
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("t_bc", [-1, 1])
+def test_forms_dslash_bitwise(dims, t_bc, form):
+    Uh, U, Us = _fields(dims, t_bc, 50)
+    for par in (0, 1):
+        psi = inputs.random_spinor(dims, 51 + par, parity=par)
+        inp = lqcd.spinor_field(dims, par, lqcd.F16N, t_bc=t_bc).copy_from(
+            lqcd.spinor_field(dims, par, t_bc=t_bc).upload(half(psi, dims, par)))
+        for dag in (False, True):
+            outs = []
+            for f in FORMS:
+                lqcd.dslash_form(f)
+                out = lqcd.spinor_field(dims, 1 - par, lqcd.F16N, t_bc=t_bc)
+                lqcd.dslash(out, Us, inp, dag)
+                outs.append(out.download())
+            assert np.array_equal(outs[0], outs[1]), (par, dag)
+            ref = orc.dslash(dims, Uh, full_from_half(inp.download(), dims, par), dagger=dag, t_bc=t_bc)
+            assert rel_err(outs[1], half(ref, dims, 1 - par)) < F16N_TOL
+
+
+@pytest.mark.parametrize("dims", DIMS[1:2] + DIMS[3:])
+def test_forms_mhat_and_mixed_solve_bitwise(dims, form):
+    Uh, U, Us = _fields(dims, -1, 60)
+    eta = inputs.random_spinor(dims, 61, parity=0)
+    b = lqcd.spinor_field(dims, 0).upload(half(eta, dims, 0))
+    b16 = lqcd.spinor_field(dims, 0, lqcd.F16N).copy_from(b)
+    res = []
+    for f in FORMS:
+        lqcd.dslash_form(f)
+        m = lqcd.spinor_field(dims, 0, lqcd.F16N)
+        lqcd.mhat(m, Us, b16, 0.155, True)
+        x = lqcd.spinor_field(dims, 0)
+        rc, info = lqcd.cg_solve(x, U, b, 0.155, lqcd.cg_params(tol=1e-11, sloppy=lqcd.F16N, delta=0.01),
+                                 U_sloppy=Us)
+        assert rc == lqcd.OK
+        res.append((m.download(), x.download(), info.iters, info.restarts))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1]) and res[0][2:] == res[1][2:]
+    r = half(eta, dims, 0) - half(orc.mdagm(dims, Uh, 0.155, full_from_half(res[1][1], dims, 0)), dims, 0)
+    assert np.linalg.norm(r) <= 1.01e-11 * np.linalg.norm(half(eta, dims, 0))
