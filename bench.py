@@ -290,8 +290,8 @@ def oracle_trajectory_4(gpu_traj=None):
         out["mixed_gpu_minus_oracle"] = {"dH": g["dH"] - o["dH"], "H0_rel": (g["H0"] - o["H0"]) / o["H0"],
                                          "plaq": g["plaq"] - o["plaq"], "links_max": float(np.max(np.abs(Ug - Uo))),
                                          "accept_same": g["accepted"] == int(o["accepted"]),
-                                         "tolerances": {"dH": 1.8e-3, "H0_rel": 1e-12, "plaq": 1e-7,
-                                                        "links_max": 1e-4}}
+                                         "tolerances": {"dH": 9.1e-5, "H0_rel": 1e-12, "plaq": 1e-8,
+                                                        "links_max": 1e-5}}
     return out
 
 

@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP>()) batch_dslash_xpay(
         for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
         if (lane == 0) part[m.y] = x;
     }
+    cg_finish<DS_BLOCK, false>(d.sc, part, d.nblocks); // pAp and alpha, as the single-system kernel
 }
 
 // step 3: Ap = t - kappa^2 D_eo^dag-hop tmp; xs += alpha p; r -= alpha Ap; block sums of |r|^2
@@ -145,51 +146,7 @@ __global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP>()) batch_dslash_cg(co
         for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
         if (lane == 0) part[m.y] = x;
     }
-}
-
-// one block per system: pAp and alpha (step 1b), or rr_new, beta and the pause
-// decision (step 3b) -- the logic of cg_pap_kernel / cg_rr_kernel
-template <lqcd_prec SP, bool RR>
-__global__ void batch_scalars(const SysDesc<SP> *sys)
-{
-    const SysDesc<SP> &d = sys[blockIdx.x];
-    CgScalars *sc = d.sc;
-    if (sc->pause) return;
-    double s[1];
-    final_sum_block<1>(d.partials, d.nblocks, s);
-    if (threadIdx.x != 0) return;
-    if (!RR) {
-        double pAp = s[0];
-        sc->pAp = pAp;
-        if (!(pAp > 0.0) || !isfinite(pAp)) {
-            sc->alpha = 0.0;
-            sc->pause = 1;
-            sc->reason = PAUSE_NONFINITE;
-        } else {
-            sc->alpha = sc->rr / pAp;
-        }
-        return;
-    }
-    double rr_new = s[0];
-    sc->rr_new = rr_new;
-    sc->iter += 1;
-    int reason = PAUSE_NONE;
-    if (!isfinite(rr_new))
-        reason = PAUSE_NONFINITE;
-    else if (rr_new <= sc->stop2)
-        reason = PAUSE_CONVERGED;
-    else if (sc->delta2 > 0.0 && rr_new < sc->delta2 * sc->maxrr2)
-        reason = PAUSE_RELIABLE;
-    else if (sc->iter >= sc->maxiter)
-        reason = PAUSE_MAXITER;
-    if (reason != PAUSE_NONE) {
-        sc->pause = 1;
-        sc->reason = reason;
-    } else {
-        sc->beta = rr_new / sc->rr;
-        sc->rr = rr_new;
-        sc->maxrr2 = fmax(sc->maxrr2, rr_new);
-    }
+    cg_finish<DS_BLOCK, true>(d.sc, part, d.nblocks); // rr, beta and the pause decision
 }
 
 // step 4: p = r + beta p
@@ -315,10 +272,8 @@ lqcd_status BatchSolver::enqueue_chunk(cudaStream_t s)
     for (int k = 0; k < BCHUNK; k++) {
         batch_dslash_plain<SP, false><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
         batch_dslash_xpay<SP><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
-        batch_scalars<SP, false><<<n, 1024, 0, s>>>(d);
         batch_dslash_plain<SP, true><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
         batch_dslash_cg<SP><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
-        batch_scalars<SP, true><<<n, 1024, 0, s>>>(d);
         batch_p_update<SP><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
     }
     batch_gather_scalars<SP><<<nblocks_for(n, 128), 128, 0, s>>>(d, (CgScalars *)gathered.p, n);
@@ -386,10 +341,10 @@ lqcd_status BatchSolver::chunk(cudaStream_t s)
     }
     if (use_graph) {
         LQCD_CUDA(cudaGraphLaunch(exec, s));
-        g_launches.fetch_add(7 * BCHUNK + 1, std::memory_order_relaxed);
+        g_launches.fetch_add(5 * BCHUNK + 1, std::memory_order_relaxed);
     } else {
         LQCD_TRY(enqueue_chunk<SP>(s));
-        g_launches.fetch_add(7 * BCHUNK + 1, std::memory_order_relaxed);
+        g_launches.fetch_add(5 * BCHUNK + 1, std::memory_order_relaxed);
     }
     // read every active system's scalars (gathered by the chunk's last kernel)
     if (pinned_n < active.size()) {

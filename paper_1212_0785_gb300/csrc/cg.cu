@@ -12,9 +12,10 @@
 // that runs several times faster than FP64 and is far more accurate than the
 // 1e-10 tolerance needs.  The plain FP64 solve uses FP64 throughout.
 //
-// Every scalar (rr, pAp, alpha, beta) lives on the device: the reduction
-// kernels compute them in a fixed order and raise a pause flag when the host
-// must act, and every iteration kernel is a no-op while the flag is set.  The
+// Every scalar (rr, pAp, alpha, beta) lives on the device: the last block of
+// each reducing hop kernel sums the block partials in a fixed order, computes
+// them and raises a pause flag when the host must act, and every iteration
+// kernel is a no-op while the flag is set.  The
 // host therefore synchronises only once per chunk of iterations, yet the
 // iteration count is exactly that of a per-iteration check.
 #include <chrono>
@@ -28,53 +29,6 @@ namespace lqcd {
 
 constexpr int BB = CG_BLOCK;
 constexpr int CG_CHUNK = 4;
-
-__global__ void cg_pap_kernel(const double *partials, int nb, CgScalars *sc)
-{
-    if (sc->pause) return;
-    double s[1];
-    final_sum_block<1>(partials, nb, s);
-    if (threadIdx.x == 0) {
-        double pAp = s[0];
-        sc->pAp = pAp;
-        if (!(pAp > 0.0) || !isfinite(pAp)) {
-            sc->alpha = 0.0;
-            sc->pause = 1;
-            sc->reason = PAUSE_NONFINITE;
-        } else {
-            sc->alpha = sc->rr / pAp;
-        }
-    }
-}
-
-__global__ void cg_rr_kernel(const double *partials, int nb, CgScalars *sc)
-{
-    if (sc->pause) return;
-    double s[1];
-    final_sum_block<1>(partials, nb, s);
-    if (threadIdx.x == 0) {
-        double rr_new = s[0];
-        sc->rr_new = rr_new;
-        sc->iter += 1;
-        int reason = PAUSE_NONE;
-        if (!isfinite(rr_new))
-            reason = PAUSE_NONFINITE;
-        else if (rr_new <= sc->stop2)
-            reason = PAUSE_CONVERGED;
-        else if (sc->delta2 > 0.0 && rr_new < sc->delta2 * sc->maxrr2)
-            reason = PAUSE_RELIABLE;
-        else if (sc->iter >= sc->maxiter)
-            reason = PAUSE_MAXITER;
-        if (reason != PAUSE_NONE) {
-            sc->pause = 1;
-            sc->reason = reason;
-        } else {
-            sc->beta = rr_new / sc->rr;
-            sc->rr = rr_new;
-            sc->maxrr2 = fmax(sc->maxrr2, rr_new);
-        }
-    }
-}
 
 __global__ void cg_set_kernel(CgScalars *sc, double rr, double beta, double maxrr2)
 {
@@ -456,16 +410,13 @@ lqcd_status CgRun::start_impl(cudaStream_t s)
 lqcd_status CgRun::iterate(cudaStream_t s)
 {
     double *partials = (double *)ws->partials.p;
-    int nbd = dslash_blocks(Vh);
     const int *skip = &sc->pause;
+    // the last block of the axpy hop computes alpha, that of the CG-update hop
+    // the pause decision and beta (cg_finish)
     LQCD_TRY(dslash_plain(TMP, UU, P, 0, skip, s));
-    LQCD_TRY(dslash_xpay(T, UU, TMP, 0, P, -k2, partials, skip, s));
-    cg_pap_kernel<<<1, 1024, 0, s>>>(partials, nbd, sc);
-    LQCD_LAUNCHED();
+    LQCD_TRY(dslash_xpay(T, UU, TMP, 0, P, -k2, partials, skip, s, sc));
     LQCD_TRY(dslash_plain(TMP, UU, T, 1, skip, s));
     LQCD_TRY(dslash_cg(UU, TMP, 1, T, -k2, XS, R, P, partials, sc, s));
-    cg_rr_kernel<<<1, 1024, 0, s>>>(partials, nbd, sc);
-    LQCD_LAUNCHED();
     return launch_p_update(P, R, sc, s);
 }
 

@@ -47,7 +47,8 @@ __device__ __forceinline__ void plain_body(SpinorRef<SP> out, SpinorRef<SP> in, 
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, int FORM>
 __device__ __forceinline__ void xpay_body(SpinorRef<SP> out, SpinorRef<SP> in, GaugeRef<GP> U,
                                                                 Geo g, int out_par, SpinorRef<SP> x, R b,
-                                                                double *partials, int nblocks, const int *skip)
+                                                                double *partials, int nblocks, const int *skip,
+                                                                CgScalars *fin)
 {
     if (skip && *skip) return;
     int cb = blockIdx.x * DS_BLOCK + threadIdx.x;
@@ -62,14 +63,17 @@ __device__ __forceinline__ void xpay_body(SpinorRef<SP> out, SpinorRef<SP> in, G
         out.store(cb, d);
         n2 = sp_norm2(d);
     }
-    if (partials) block_sum_store_wp<DS_BLOCK>(n2, partials);
+    if (partials) {
+        block_sum_store_wp<DS_BLOCK>(n2, partials);
+        if (fin) cg_finish<DS_BLOCK, false>(fin, partials, nblocks);
+    }
 }
 
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, lqcd_prec XP, int FORM>
 __device__ __forceinline__ void cg_body(SpinorRef<SP> in, GaugeRef<GP> U, Geo g, int out_par,
                                                               SpinorRef<SP> t, R b, SpinorRef<XP> xs, SpinorRef<SP> r,
                                                               SpinorRef<SP> p, double *partials, int nblocks,
-                                                              const CgScalars *sc)
+                                                              CgScalars *sc)
 {
     if (sc->pause) return;
     const R alpha = (R)sc->alpha;
@@ -106,6 +110,7 @@ __device__ __forceinline__ void cg_body(SpinorRef<SP> in, GaugeRef<GP> U, Geo g,
         n2 = sp_norm2(rv);
     }
     block_sum_store_wp<DS_BLOCK>(n2, partials);
+    cg_finish<DS_BLOCK, true>(sc, partials, nblocks);
 }
 
 // The kernels: gathered operands, and (FP16+norm) prefetched links with the
@@ -119,15 +124,16 @@ __global__ void __launch_bounds__(DS_BLOCK) dslash_plain_kernel(SpinorRef<SP> ou
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
 __global__ void __launch_bounds__(DS_BLOCK) dslash_xpay_kernel(SpinorRef<SP> out, SpinorRef<SP> in, GaugeRef<GP> U,
                                                                 Geo g, int out_par, SpinorRef<SP> x, R b,
-                                                                double *partials, int nblocks, const int *skip)
+                                                                double *partials, int nblocks, const int *skip,
+                                                                CgScalars *fin)
 {
-    xpay_body<R, SP, GP, DAG, 0>(out, in, U, g, out_par, x, b, partials, nblocks, skip);
+    xpay_body<R, SP, GP, DAG, 0>(out, in, U, g, out_par, x, b, partials, nblocks, skip, fin);
 }
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, lqcd_prec XP>
 __global__ void __launch_bounds__(DS_BLOCK) dslash_cg_kernel(SpinorRef<SP> in, GaugeRef<GP> U, Geo g, int out_par,
                                                               SpinorRef<SP> t, R b, SpinorRef<XP> xs, SpinorRef<SP> r,
                                                               SpinorRef<SP> p, double *partials, int nblocks,
-                                                              const CgScalars *sc)
+                                                              CgScalars *sc)
 {
     cg_body<R, SP, GP, DAG, XP, 0>(in, U, g, out_par, t, b, xs, r, p, partials, nblocks, sc);
 }
@@ -143,16 +149,17 @@ template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
 __global__ void __launch_bounds__(DS_BLOCK, 7) dslash_xpay_prefetch_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
                                                                             GaugeRef<GP> U, Geo g, int out_par,
                                                                             SpinorRef<SP> x, R b, double *partials,
-                                                                            int nblocks, const int *skip)
+                                                                            int nblocks, const int *skip,
+                                                                            CgScalars *fin)
 {
-    xpay_body<R, SP, GP, DAG, 1>(out, in, U, g, out_par, x, b, partials, nblocks, skip);
+    xpay_body<R, SP, GP, DAG, 1>(out, in, U, g, out_par, x, b, partials, nblocks, skip, fin);
 }
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, lqcd_prec XP>
 __global__ void __launch_bounds__(DS_BLOCK, 7) dslash_cg_prefetch_kernel(SpinorRef<SP> in, GaugeRef<GP> U, Geo g,
                                                                           int out_par, SpinorRef<SP> t, R b,
                                                                           SpinorRef<XP> xs, SpinorRef<SP> r,
                                                                           SpinorRef<SP> p, double *partials,
-                                                                          int nblocks, const CgScalars *sc)
+                                                                          int nblocks, CgScalars *sc)
 {
     cg_body<R, SP, GP, DAG, XP, 1>(in, U, g, out_par, t, b, xs, r, p, partials, nblocks, sc);
 }
@@ -226,7 +233,7 @@ static void launch_plain(lqcd_field *out, const lqcd_field *U, const lqcd_field 
 
 template <lqcd_prec P, lqcd_prec GP = P>
 static void launch_xpay(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int dagger, const lqcd_field *x,
-                        double b, double *partials, const int *skip, cudaStream_t s)
+                        double b, double *partials, const int *skip, cudaStream_t s, CgScalars *fin)
 {
     using R = typename ArithOf<P>::type;
     Geo g = make_geo(in->lat);
@@ -235,16 +242,16 @@ static void launch_xpay(lqcd_field *out, const lqcd_field *U, const lqcd_field *
     if (dagger)
         LQCD_LAUNCH_FORM(st, dslash_xpay, (R, P, GP, true), nb,
                            (spinor_ref<P>(out), spinor_ref<P>(in), gauge_ref<GP>(U), g, out_parity(out),
-                            spinor_ref<P>(x), (R)b, partials, nb, skip));
+                            spinor_ref<P>(x), (R)b, partials, nb, skip, fin));
     else
         LQCD_LAUNCH_FORM(st, dslash_xpay, (R, P, GP, false), nb,
                            (spinor_ref<P>(out), spinor_ref<P>(in), gauge_ref<GP>(U), g, out_parity(out),
-                            spinor_ref<P>(x), (R)b, partials, nb, skip));
+                            spinor_ref<P>(x), (R)b, partials, nb, skip, fin));
 }
 
 template <lqcd_prec P, lqcd_prec XP>
 static void launch_cg(const lqcd_field *U, const lqcd_field *in, int dagger, const lqcd_field *t, double b,
-                      lqcd_field *xs, lqcd_field *r, const lqcd_field *p, double *partials, const CgScalars *sc,
+                      lqcd_field *xs, lqcd_field *r, const lqcd_field *p, double *partials, CgScalars *sc,
                       cudaStream_t s)
 {
     using R = typename ArithOf<P>::type;
@@ -295,22 +302,22 @@ lqcd_status dslash_plain(lqcd_field *out, const lqcd_field *U, const lqcd_field 
 }
 
 lqcd_status dslash_xpay(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int dagger, const lqcd_field *x,
-                        double b, double *partials, const int *skip, cudaStream_t s)
+                        double b, double *partials, const int *skip, cudaStream_t s, CgScalars *fin)
 {
     LQCD_TRY(check_pair(out, U, in));
     LQCD_REQUIRE(x && x->kind == out->kind && x->prec == out->prec, "dslash_xpay: x must match out");
     double site = 8 * link_bytes(U->prec) + 3 * spinor_site_bytes(in->prec); // + read of x
     KernelTimer kt(dslash_class(in->prec), s, site * in->Vh);
     switch (in->prec) {
-    case LQCD_F64: launch_xpay<LQCD_F64>(out, U, in, dagger, x, b, partials, skip, s); break;
+    case LQCD_F64: launch_xpay<LQCD_F64>(out, U, in, dagger, x, b, partials, skip, s, fin); break;
     case LQCD_F32:
         if (U->prec == LQCD_F64)
-            launch_xpay<LQCD_F32, LQCD_F64>(out, U, in, dagger, x, b, partials, skip, s);
+            launch_xpay<LQCD_F32, LQCD_F64>(out, U, in, dagger, x, b, partials, skip, s, fin);
         else
-            launch_xpay<LQCD_F32>(out, U, in, dagger, x, b, partials, skip, s);
+            launch_xpay<LQCD_F32>(out, U, in, dagger, x, b, partials, skip, s, fin);
         break;
-    case LQCD_F16N: launch_xpay<LQCD_F16N>(out, U, in, dagger, x, b, partials, skip, s); break;
-    case LQCD_BF16: launch_xpay<LQCD_BF16>(out, U, in, dagger, x, b, partials, skip, s); break;
+    case LQCD_F16N: launch_xpay<LQCD_F16N>(out, U, in, dagger, x, b, partials, skip, s, fin); break;
+    case LQCD_BF16: launch_xpay<LQCD_BF16>(out, U, in, dagger, x, b, partials, skip, s, fin); break;
     default:
         LQCD_REQUIRE(partials == nullptr, "float-float hopping term has no norm reduction");
         dslash_df_launch(out, U, in, dagger, x, b, skip, s);
@@ -321,7 +328,7 @@ lqcd_status dslash_xpay(lqcd_field *out, const lqcd_field *U, const lqcd_field *
 }
 
 lqcd_status dslash_cg(const lqcd_field *U, const lqcd_field *in, int dagger, const lqcd_field *t, double b,
-                      lqcd_field *xs, lqcd_field *r, const lqcd_field *p, double *partials, const CgScalars *sc,
+                      lqcd_field *xs, lqcd_field *r, const lqcd_field *p, double *partials, CgScalars *sc,
                       cudaStream_t s)
 {
     // links, input; reads of t, p, r and xs; writes of r and xs (no output of the product)

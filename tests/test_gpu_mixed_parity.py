@@ -8,35 +8,44 @@ beta 5.8, kappa 0.1570, start exp(i 0.15 H) from Philox seed 3, CG true
 ones).  One chain of a batch of chains is held to the same bar.
 
 The tolerances follow from the FP32 molecular dynamics (the derivation is in
-the design doc, section 8a): a force evaluation carries a relative error of about
-eps_F = 30 * 2^-24 from the FP32 links, the FP32 solution and the FP32
-arithmetic; over a trajectory of length tau = 1 that moves the momenta by at
-most tau * eps_F * max|F| and the links by about half that plus 2 nsteps FP32
-exponentials, ~1e-5; the change of H1 is a sum of 32 V such random
-perturbations of size ~1e-5 weighted by |P| ~ 1, i.e. ~1e-5 sqrt(32 V).  Each
-of those estimates takes every perturbation at its bound; the dH bound is twice
-its estimate, the others about ten times theirs.  A dropped or mis-signed term
-anywhere changes dH by O(1)."""
+the design doc, section 8a).  A force evaluation rounds the links and the solution
+to FP32 and adds in FP32, so each of the 32 V momentum coefficients is moved by
+about 2^-24 |F| per evaluation, in no coherent direction; over tau = 1 with
+|F| ~ 1-3 and |P| ~ 1 that changes H1 by about 2e-7 sqrt(32 V), and every link
+entry by a few 1e-7 (with 2 nsteps FP32 exponentials of error ~1e-7 each).
+The bounds sit 5-50 times above those estimates (measured: dH 1.4e-5 at 4^4,
+1.6e-5 at 8^4; links 2.6e-7; X 1.2e-7; plaquette 1.3e-9).  A dropped or
+mis-signed term anywhere changes dH by O(1).  The first trajectory starts from
+bitwise the oracle's links, so H0 and phi agree to FP64 rounding; a chained
+trajectory starts from links that already differ by the previous trajectory's
+link error dU, which moves S_g by at most 24 beta V dU.
+"""
 import numpy as np
 import pytest
 
 from oracle import oracle as orc
 from paper_1212_0785_gb300 import lqcd
-from tests.gpu_util import full_from_half, half
+from tests.gpu_util import half
 
 pytestmark = pytest.mark.gpu
 
 BETA, KAPPA, TAU, NSTEPS, SEED, EPS = 5.8, 0.1570, 1.0, 16, 3, 0.15
-TOL_H0_REL = 1e-12      # refresh and H0 are FP64 (plaquette from float-float links, ~1e-14)
-TOL_PHI_REL = 1e-12     # phi = Mhat^dag eta in FP64
-TOL_LINKS = 1e-4        # max |U_gpu - U_oracle| over all link entries
-TOL_PLAQ = 1e-7         # mean plaquette after the trajectory
-TOL_X_REL = 1e-3        # max |X_gpu - X_oracle| / max |X_oracle| of the final solve
+TOL_H0_REL = 1e-12      # first trajectory: FP64 refresh (plaquette from float-float links, ~1e-14)
+TOL_PHI_REL = 1e-12     # phi = Mhat^dag eta in FP64, on the trajectory's start links
+TOL_LINKS = 1e-5        # max |U_gpu - U_oracle| over all link entries
+TOL_PLAQ = 1e-8         # mean plaquette after the trajectory
+TOL_X_REL = 1e-5        # max |X_gpu - X_oracle| / max |X_oracle| of the final solve
 
 
 def tol_dh(dims):
-    """|dH_gpu - dH_oracle| <= 2e-5 sqrt(32 V): 1.8e-3 at 4^4, 7.2e-3 at 8^4"""
-    return 2e-5 * np.sqrt(32 * int(np.prod(dims)))
+    """|dH_gpu - dH_oracle| <= 1e-6 sqrt(32 V): 9.1e-5 at 4^4, 3.6e-4 at 8^4"""
+    return 1e-6 * np.sqrt(32 * int(np.prod(dims)))
+
+
+def tol_h0_rel(dims, H0, dU_prev):
+    """relative H0 bound of a trajectory whose start links differ from the
+    oracle's by dU_prev (0 for the first trajectory)"""
+    return TOL_H0_REL + 24 * BETA * int(np.prod(dims)) * dU_prev / abs(H0)
 
 
 def bench_params(metropolis=True):
@@ -70,6 +79,7 @@ def run_and_compare(dims, trajs, metropolis):
     Uo = orc.gauge_start(dims, SEED, EPS)
     assert np.max(np.abs(U.download() - Uo)) < 1e-13
     errs = []
+    dU_prev = 0.0
     for traj in range(trajs):
         Uo_start = Uo
         g = st.trajectory(p)
@@ -79,8 +89,10 @@ def run_and_compare(dims, trajs, metropolis):
         e = {"dH": abs(g["dH"] - o["dH"]), "H0_rel": abs(g["H0"] - o["H0"]) / abs(o["H0"]),
              "plaq": abs(g["plaq"] - o["plaq"]), "links": float(np.max(np.abs(U.download() - Uo))),
              "phi_rel": float(np.max(np.abs(phi.download() - half(phi_or, dims, 0))) / np.max(np.abs(phi_or))),
-             "accept": (g["accepted"], int(o["accepted"])), "u": (g["u"], o["u"]), "dH_oracle": o["dH"]}
+             "accept": (g["accepted"], int(o["accepted"])), "u": (g["u"], o["u"]), "dH_oracle": o["dH"],
+             "H0_tol": tol_h0_rel(dims, o["H0"], dU_prev), "phi_tol": TOL_PHI_REL + 10 * dU_prev}
         e["X_rel"] = final_solution_error(dims, U, phi, Uo, phi_or)
+        dU_prev = e["links"]
         errs.append(e)
         print(dims, traj, e)
         assert g["cg_true_rel_res_max"] <= 1e-10 and g["cg_failures"] == 0
@@ -94,8 +106,8 @@ def check(dims, errs):
         assert e["u"][0] == e["u"][1]
         marginal = abs(e["u"][1] - np.exp(-e["dH_oracle"])) < tol_dh(dims)
         assert marginal or e["accept"][0] == e["accept"][1], e
-        assert e["H0_rel"] < TOL_H0_REL, e
-        assert e["phi_rel"] < TOL_PHI_REL, e
+        assert e["H0_rel"] < e["H0_tol"], e
+        assert e["phi_rel"] < e["phi_tol"], e
         assert e["dH"] < tol_dh(dims), e
         assert e["plaq"] < TOL_PLAQ, e
         assert e["links"] < TOL_LINKS, e
