@@ -350,7 +350,8 @@ def config_block(args, sloppy, force_prec):
     c["forces"] = f"{force_prec} arithmetic"
     k = int(getattr(args, "chrono", 0))
     c["initial_guess"] = {0: "zero", 1: "previous solution (chronological)"}.get(
-        k, f"extrapolated through the last {k} solutions (chronological)")
+        k, f"extrapolated through the last {k} solutions (chronological)"
+           + (", refined by minimal residual extrapolation" if getattr(args, "mre", 0) and sloppy != "f64" else ""))
     c["parallelism"] = f"replicas{args.gpus}" if args.gpus > 1 else "single_gpu"
     c["l2"] = "inputs larger than L2 (FP64 links 1.21 GB, spinors 0.2 GB)"
     return c
@@ -375,7 +376,7 @@ def run_ours(args):
     cg = lqcd.cg_params(tol=wl["cg_tol"], maxiter=20000, sloppy=sloppy, delta=args.delta)
     force_prec = lqcd.PREC_NAMES[args.force_prec]
     params = lqcd.hmc_params(wl["beta"], wl["kappa"], wl["tau"], args.nsteps, lqcd.OMELYAN, n_flavors=2, cg=cg,
-                             force_prec=force_prec, chrono=int(args.chrono))
+                             force_prec=force_prec, chrono=int(args.chrono), chrono_mre=args.mre)
 
     U = lqcd.gauge_field(dims)
     lqcd.gauge_start(U, SEED, EPS, chain=rank)
@@ -542,6 +543,7 @@ def run_ours(args):
                         "solves_per_traj": float(np.mean([i["n_solves"] for i in infos])),
                         "accurate_residuals_per_traj": float(np.mean([i["cg_accurate_residuals"] for i in infos])),
                         "failed_checks_per_traj": float(np.mean([i["cg_failed_checks"] for i in infos])),
+                        "guesses_refined_per_traj": float(np.mean([i["cg_guesses_refined"] for i in infos])),
                         "cg_true_rel_res_max": max(i["cg_true_rel_res_max"] for i in infos)},
             "kernel_time_per_traj": kernel_share,
         }
@@ -847,6 +849,8 @@ def main(argv=None):
                     help="initial guess of each solve after the first of a trajectory: 0 zero, 1 the previous "
                          "solution, k >= 2 extrapolated through the last k solutions (both the mixed and the "
                          "FP64 path)")
+    ap.add_argument("--mre", type=int, choices=(0, 1), default=0,
+                    help="1: refine the extrapolated guesses by minimal residual extrapolation")
     ap.add_argument("--dims", type=int, nargs=4, default=WORKLOAD["dims"])
     ap.add_argument("--nsteps", type=int, default=WORKLOAD["nsteps"],
                     help="MD steps per trajectory (16 for the benchmarked workload)")

@@ -268,6 +268,7 @@ typedef struct {
                                initial guess, at every reliable update or restart, at the end */
     int failed_checks;    /* times the iterated residual met the tolerance and the accurate one
                              did not (the solve then went on) */
+    int guess_refined;    /* 1 if the initial guess was refined by minimal residual extrapolation */
 } lqcd_cg_info;
 
 /* Solve Mhat^dag Mhat x = b on the even sites (the matrix inversion of the
@@ -400,6 +401,13 @@ typedef struct {
                                    outer level in m steps of the same scheme; the fermion actions
                                    on the outer level of nsteps steps */
     int heavy_inner;            /* with gauge_substeps >= 2: the heavy action on the inner level */
+    int chrono_mre;             /* with chrono = k >= 2 and a mixed-precision solver: 1 refines the
+                                   extrapolated guess by minimal residual extrapolation (paper Sec.
+                                   6.2, the chronological inverter of its production runs): the guess
+                                   x_L + sum_j c_j (x_j - x_{j+1}) over the last k solutions x_j whose
+                                   real coefficients c minimise |b - A x| for the current operator A;
+                                   the products A (x_j - x_{j+1}) in FP32 arithmetic, the residual of
+                                   x_L and the update in float-float.  0: the extrapolation alone */
 } lqcd_hmc_params;
 
 typedef struct {
@@ -416,6 +424,7 @@ typedef struct {
     uint32_t traj;             /* trajectory counter used for the random numbers */
     int cg_accurate_residuals; /* summed lqcd_cg_info.accurate_residuals of the solves */
     int cg_failed_checks;      /* summed lqcd_cg_info.failed_checks of the solves */
+    int cg_guesses_refined;    /* solves whose guess minimal residual extrapolation refined */
 } lqcd_traj_info;
 
 /* State of one Markov chain on the device: borrows the caller's FP64 gauge

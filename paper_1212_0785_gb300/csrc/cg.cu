@@ -127,6 +127,106 @@ __global__ void split_gauge_kernel(GaugeRef<PREC_DF> dst, GaugeRef<LQCD_F64> src
     dst.store(mp >> 1, mp & 1, cb, src.load<double>(mp >> 1, mp & 1, cb));
 }
 
+// ---------------------------------------------------------------- minimal residual extrapolation
+
+// d = a - b (FP64 solutions) rounded to FP32
+__global__ void mre_diff_kernel(SpinorRef<LQCD_F32> d, SpinorRef<LQCD_F64> a, SpinorRef<LQCD_F64> b, int Vh)
+{
+    int cb = blockIdx.x * BB + threadIdx.x;
+    if (cb >= Vh) return;
+    Sp<double> av = a.load_rw<double>(cb), bv = b.load_rw<double>(cb);
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) av.c[k][c] = av.c[k][c] - bv.c[k][c];
+    d.store(cb, av);
+}
+
+// block partials of G_ij = Re<w_i, w_j> (i <= j, row by row) and g_i = Re<w_i, r>
+// for N directions; r in float-float (its leading parts)
+template <int N>
+__global__ void __launch_bounds__(BB) mre_dots_kernel(const float4 *const *w, SpinorRef<PREC_DF> r, double *partials,
+                                                       int nb, int Vh)
+{
+    constexpr int NG = N * (N + 1) / 2, NT = NG + N;
+    int cb = blockIdx.x * BB + threadIdx.x;
+    double v[NT];
+#pragma unroll
+    for (int k = 0; k < NT; k++) v[k] = 0.0;
+    if (cb < Vh) {
+        float4 wv[N][6];
+#pragma unroll
+        for (int j = 0; j < N; j++)
+#pragma unroll
+            for (int k = 0; k < 6; k++) wv[j][k] = w[j][(size_t)k * Vh + cb];
+        Sp<float> rv = r.load_rw<float>(cb);
+        float rr[24];
+#pragma unroll
+        for (int k = 0; k < 12; k++) rr[2 * k] = rv.c[k / 3][k % 3].re, rr[2 * k + 1] = rv.c[k / 3][k % 3].im;
+        int q = 0;
+#pragma unroll
+        for (int i = 0; i < N; i++)
+#pragma unroll
+            for (int j = i; j < N; j++, q++) {
+                float a = 0.f;
+#pragma unroll
+                for (int k = 0; k < 6; k++)
+                    a += wv[i][k].x * wv[j][k].x + wv[i][k].y * wv[j][k].y + wv[i][k].z * wv[j][k].z +
+                         wv[i][k].w * wv[j][k].w;
+                v[q] = a;
+            }
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+            float a = 0.f;
+#pragma unroll
+            for (int k = 0; k < 6; k++)
+                a += wv[i][k].x * rr[4 * k] + wv[i][k].y * rr[4 * k + 1] + wv[i][k].z * rr[4 * k + 2] +
+                     wv[i][k].w * rr[4 * k + 3];
+            v[NG + i] = a;
+        }
+    }
+    block_sum_store<NT, BB>(v, partials, nb);
+}
+
+// x += sum_j c_j d_j and r -= sum_j c_j w_j in float-float; block partials of
+// |r|^2 from the leading parts
+template <int N>
+__global__ void __launch_bounds__(BB) mre_update_kernel(SpinorRef<PREC_DF> x, SpinorRef<PREC_DF> r,
+                                                         const float4 *const *d, const float4 *const *w, double c0,
+                                                         double c1, double c2, double *partials, int nb, int Vh)
+{
+    int cb = blockIdx.x * BB + threadIdx.x;
+    double n2[1] = {0.0};
+    if (cb < Vh) {
+        const Df c[3] = {Df(c0), Df(c1), Df(c2)};
+        Sp<Df> xv = x.load_rw<Df>(cb), rv = r.load_rw<Df>(cb);
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            Df *xe[4] = {&xv.c[(2 * k) / 3][(2 * k) % 3].re, &xv.c[(2 * k) / 3][(2 * k) % 3].im,
+                         &xv.c[(2 * k + 1) / 3][(2 * k + 1) % 3].re, &xv.c[(2 * k + 1) / 3][(2 * k + 1) % 3].im};
+            Df *re[4] = {&rv.c[(2 * k) / 3][(2 * k) % 3].re, &rv.c[(2 * k) / 3][(2 * k) % 3].im,
+                         &rv.c[(2 * k + 1) / 3][(2 * k + 1) % 3].re, &rv.c[(2 * k + 1) / 3][(2 * k + 1) % 3].im};
+#pragma unroll
+            for (int j = 0; j < N; j++) {
+                const float4 dv = d[j][(size_t)k * Vh + cb], wv = w[j][(size_t)k * Vh + cb];
+                const float dd[4] = {dv.x, dv.y, dv.z, dv.w}, ww[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    *xe[q] += c[j] * Df(dd[q], 0.f);
+                    *re[q] += -(c[j] * Df(ww[q], 0.f));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc += re[q]->hi * re[q]->hi;
+        }
+        x.store(cb, xv);
+        r.store(cb, rv);
+        n2[0] = acc;
+    }
+    block_sum_store<1, BB>(n2, partials, nb);
+}
+
 template <lqcd_prec PS, lqcd_prec PD, typename R>
 static lqcd_status convert_spinor(lqcd_field *dst, const lqcd_field *src, cudaStream_t s)
 {
@@ -171,10 +271,32 @@ static lqcd_status pinned()
 
 // ---------------------------------------------------------------- work space
 
+lqcd_status CgWorkspace::ensure_mre(int n, cudaStream_t s)
+{
+    n = std::min(n, MRE_MAX);
+    // the normal equations' block partials: up to 9 sums of CG_BLOCK-site blocks
+    const size_t need = 9 * (size_t)nblocks_for(make_geo(lat).Vh, BB) * sizeof(double);
+    if (partials.bytes < need) LQCD_TRY(partials.alloc(need, s));
+    if (!mre_te.f) {
+        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F32, 0, &mre_te.f));
+        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F32, 0, &mre_to.f));
+    }
+    for (; mre_n < n; mre_n++) {
+        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F32, 0, &mre_d[mre_n].f));
+        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F32, 0, &mre_w[mre_n].f));
+    }
+    return LQCD_OK;
+}
+
 lqcd_status CgWorkspace::ensure(const lqcd_lattice &l, lqcd_prec sl, cudaStream_t s)
 {
     if (ready && same_lattice(lat, l) && sloppy == sl) return LQCD_OK;
     ready = false;
+    for (FieldPtr *f : {&mre_d[0], &mre_d[1], &mre_d[2], &mre_w[0], &mre_w[1], &mre_w[2], &mre_te, &mre_to}) {
+        if (f->f) lqcd_field_free(f->f);
+        f->f = nullptr;
+    }
+    mre_n = 0;
     for (FieldPtr *f : {&r64, &t64a, &t64b, &tmpo64, &p64, &xs, &rs, &ps, &ts, &tmpos, &Udf, &xdf, &bdf, &rdf,
                         &t1df, &t2df, &tmpodf}) {
         if (f->f) lqcd_field_free(f->f);
@@ -216,7 +338,7 @@ lqcd_status CgWorkspace::ensure(const lqcd_lattice &l, lqcd_prec sl, cudaStream_
     size_t np = (size_t)std::max(std::max(dslash_blocks(Vh), nblocks_for(Vh, BB)), 2048);
     LQCD_TRY(sc.alloc(sizeof(CgScalars), s));
     LQCD_TRY(partials.alloc(np * sizeof(double), s));
-    LQCD_TRY(scalars.alloc(8 * sizeof(double), s));
+    LQCD_TRY(scalars.alloc(16 * sizeof(double), s));
     ready = true;
     return LQCD_OK;
 }
@@ -225,7 +347,8 @@ size_t CgWorkspace::bytes() const
 {
     size_t n = sc.bytes + partials.bytes + scalars.bytes;
     for (const FieldPtr *f : {&r64, &t64a, &t64b, &tmpo64, &p64, &xs, &rs, &ps, &ts, &tmpos, &Udf, &xdf, &bdf, &rdf,
-                              &t1df, &t2df, &tmpodf})
+                              &t1df, &t2df, &tmpodf, &mre_d[0], &mre_d[1], &mre_d[2], &mre_w[0], &mre_w[1],
+                              &mre_w[2], &mre_te, &mre_to})
         if (f->f) n += f->f->bytes + f->f->norm_bytes;
     return n;
 }
@@ -319,13 +442,113 @@ lqcd_status CgRun::succeed()
     return LQCD_OK;
 }
 
+// Minimal residual extrapolation (Brower, Ivanenko, Levkova, Orginos 1997,
+// the chronological inverter of the paper's Sec. 6.2): the guess x_L already
+// in x / xdf has its accurate residual r_L in rdf.  Over the directions
+// d_j = x_j - x_{j+1} of the last n_mre solutions, the real coefficients c
+// minimising |r_L - sum_j c_j A d_j| solve the normal equations G c = g,
+// G_ij = Re<A d_i, A d_j>, g_i = Re<A d_i, r_L>; the guess becomes
+// x_L + sum_j c_j d_j and its residual r_L - sum_j c_j A d_j.  The products
+// A d_j are formed in FP32 arithmetic: they multiply differences of nearby
+// solutions, so their rounding error is ~1e-7 of |r_L|, far below the solve's
+// tolerance, and the updates of x and r are float-float.  A singular or
+// ill-conditioned G leaves the guess as it was.
+lqcd_status CgRun::mre_refine(cudaStream_t s, double *rr0)
+{
+    CgWorkspace &w = *ws;
+    const int nd = std::min(n_mre - 1, CgWorkspace::MRE_MAX);
+    LQCD_TRY(w.ensure_mre(nd, s));
+    const lqcd_field *L = mre_links ? mre_links : U;
+    const int nb = nblocks_for(Vh, BB);
+    for (int j = 0; j < nd; j++) {
+        mre_diff_kernel<<<nb, BB, 0, s>>>(spinor_ref<LQCD_F32>(w.mre_d[j].f), spinor_ref<LQCD_F64>(mre_x[j]),
+                                          spinor_ref<LQCD_F64>(mre_x[j + 1]), Vh);
+        LQCD_LAUNCHED();
+        LQCD_TRY(mhat_apply(w.mre_te.f, L, w.mre_d[j].f, kappa, 0, w.mre_to.f, nullptr, s));
+        LQCD_TRY(mhat_apply(w.mre_w[j].f, L, w.mre_te.f, kappa, 1, w.mre_to.f, nullptr, s));
+    }
+    // the direction pointers in device memory (one small table after the partials' scalars)
+    const float4 *ptrs[2 * CgWorkspace::MRE_MAX];
+    for (int j = 0; j < nd; j++) {
+        ptrs[j] = (const float4 *)w.mre_d[j].f->data;
+        ptrs[CgWorkspace::MRE_MAX + j] = (const float4 *)w.mre_w[j].f->data;
+    }
+    if (w.mre_tab.bytes < sizeof(ptrs)) LQCD_TRY(w.mre_tab.alloc(sizeof(ptrs), s));
+    LQCD_CUDA(cudaMemcpyAsync(w.mre_tab.p, ptrs, sizeof(ptrs), cudaMemcpyHostToDevice, s));
+    const float4 *const *dtab = (const float4 *const *)w.mre_tab.p;
+    const float4 *const *wtab = dtab + CgWorkspace::MRE_MAX;
+    double *part = (double *)w.partials.p;
+    const int ng = nd * (nd + 1) / 2, nt = ng + nd;
+    switch (nd) {
+    case 1: mre_dots_kernel<1><<<nb, BB, 0, s>>>(wtab, spinor_ref<PREC_DF>(w.rdf_()), part, nb, Vh); break;
+    case 2: mre_dots_kernel<2><<<nb, BB, 0, s>>>(wtab, spinor_ref<PREC_DF>(w.rdf_()), part, nb, Vh); break;
+    default: mre_dots_kernel<3><<<nb, BB, 0, s>>>(wtab, spinor_ref<PREC_DF>(w.rdf_()), part, nb, Vh); break;
+    }
+    LQCD_LAUNCHED();
+    LQCD_TRY(reduce_partials(part, nb, nt, (double *)w.scalars.p, s));
+    double h[9];
+    LQCD_TRY(read_scalars((double *)w.scalars.p, h, nt, s)); // synchronises: ptrs may go out of scope
+    // G c = g by Cholesky (G symmetric positive semi-definite)
+    double G[3][3], g[3], Lc[3][3] = {}, c[3] = {0, 0, 0};
+    for (int i = 0, q = 0; i < nd; i++)
+        for (int j = i; j < nd; j++, q++) G[i][j] = G[j][i] = h[q];
+    for (int i = 0; i < nd; i++) g[i] = h[ng + i];
+    bool ok = true;
+    for (int i = 0; i < nd && ok; i++) {
+        for (int j = 0; j <= i; j++) {
+            double v = G[i][j];
+            for (int k = 0; k < j; k++) v -= Lc[i][k] * Lc[j][k];
+            if (i == j) {
+                ok = std::isfinite(v) && v > 1e-24 * G[0][0] && v > 0;
+                Lc[i][i] = ok ? std::sqrt(v) : 0.0;
+            } else {
+                Lc[i][j] = v / Lc[j][j];
+            }
+        }
+    }
+    if (!ok) return LQCD_OK; // keep the extrapolated guess
+    double y[3];
+    for (int i = 0; i < nd; i++) {
+        double v = g[i];
+        for (int k = 0; k < i; k++) v -= Lc[i][k] * y[k];
+        y[i] = v / Lc[i][i];
+    }
+    for (int i = nd - 1; i >= 0; i--) {
+        double v = y[i];
+        for (int k = i + 1; k < nd; k++) v -= Lc[k][i] * c[k];
+        c[i] = v / Lc[i][i];
+    }
+    switch (nd) {
+    case 1:
+        mre_update_kernel<1><<<nb, BB, 0, s>>>(spinor_ref<PREC_DF>(w.xdf.f), spinor_ref<PREC_DF>(w.rdf_()), dtab, wtab,
+                                               c[0], c[1], c[2], part, nb, Vh);
+        break;
+    case 2:
+        mre_update_kernel<2><<<nb, BB, 0, s>>>(spinor_ref<PREC_DF>(w.xdf.f), spinor_ref<PREC_DF>(w.rdf_()), dtab, wtab,
+                                               c[0], c[1], c[2], part, nb, Vh);
+        break;
+    default:
+        mre_update_kernel<3><<<nb, BB, 0, s>>>(spinor_ref<PREC_DF>(w.xdf.f), spinor_ref<PREC_DF>(w.rdf_()), dtab, wtab,
+                                               c[0], c[1], c[2], part, nb, Vh);
+        break;
+    }
+    LQCD_LAUNCHED();
+    LQCD_TRY(reduce_partials(part, nb, 1, (double *)w.scalars.p, s));
+    LQCD_TRY(read_scalars((double *)w.scalars.p, h, 1, s));
+    *rr0 = h[0];
+    mre_used = true;
+    inf.guess_refined = 1;
+    // the FP64 guess follows the float-float one (a solve that stops at once returns it)
+    return convert_spinor<PREC_DF, LQCD_F64, double>(x, w.xdf.f, s);
+}
+
 lqcd_status CgRun::start(cudaStream_t s, CgScalars *sc_dev)
 {
     t0 = std::chrono::steady_clock::now();
     sc = sc_dev;
     done = false;
     status = LQCD_OK;
-    inf = lqcd_cg_info{0, 0, 0.0, 0.0, 0, 0};
+    inf = lqcd_cg_info{0, 0, 0.0, 0.0, 0, 0, 0};
     mixed = prm.sloppy != LQCD_F64;
     lqcd_status rc = start_impl(s);
     if (rc != LQCD_OK) return fail(rc);
@@ -368,6 +591,7 @@ lqcd_status CgRun::start_impl(cudaStream_t s)
             inf.accurate_residuals++;
             LQCD_TRY((convert_spinor<LQCD_F64, PREC_DF, double>(w.xdf.f, x, s)));
             LQCD_TRY(true_residual_df(w, kappa, &rr0, s));
+            if (n_mre >= 2 && std::isfinite(rr0)) LQCD_TRY(mre_refine(s, &rr0));
             LQCD_TRY(df_to_sloppy(w.rs.f, w.rdf_(), s));
             LQCD_TRY(lqcd_field_copy(w.ps.f, w.rs.f, s));
         } else {
@@ -520,11 +744,16 @@ lqcd_status CgRun::pause_decide(const CgScalars &h, cudaStream_t s)
 
 lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, const lqcd_field *Us,
                         const lqcd_field *b, double kappa, const lqcd_cg_params &prm, lqcd_cg_info *info,
-                        cudaStream_t s)
+                        cudaStream_t s, const MreInput *mre)
 {
     LQCD_TRY(ws.ensure(x->lat, prm.sloppy, s));
     CgRun run;
     run.ws = &ws, run.x = x, run.U = U, run.Us = Us, run.b = b, run.kappa = kappa, run.prm = prm;
+    if (mre && prm.guess && prm.sloppy != LQCD_F64) {
+        run.n_mre = std::min(mre->n, CgWorkspace::MRE_MAX + 1);
+        for (int j = 0; j < run.n_mre; j++) run.mre_x[j] = mre->x[j];
+        run.mre_links = mre->links;
+    }
     run.start(s, (CgScalars *)ws.sc.p);
     CgScalars &h = *g_pinned.sc;
     while (!run.done) {

@@ -16,6 +16,7 @@ struct CgWorkspace {
     lqcd_lattice lat{};
     lqcd_prec sloppy = LQCD_F64;
     bool ready = false;
+    int mre_n = 0; // directions allocated
     FieldPtr r64, t64a, t64b, tmpo64;  // FP64 residual and operator temporaries (FP64 CG)
     FieldPtr p64;                      // FP64 search direction (plain FP64 CG)
     FieldPtr xs, rs, ps, ts, tmpos;    // sloppy fields (mixed CG)
@@ -23,6 +24,12 @@ struct CgWorkspace {
     // temporaries in float-float storage, and the float-float link copy
     FieldPtr Udf, xdf, bdf, rdf, t1df, t2df, tmpodf;
     DevBuf sc, partials, scalars;
+    // minimal residual extrapolation of the guess (mixed solves): FP32
+    // directions d_j, their images w_j = A d_j and the operator temporaries
+    static constexpr int MRE_MAX = 3;
+    FieldPtr mre_d[MRE_MAX], mre_w[MRE_MAX], mre_te, mre_to;
+    DevBuf mre_tab; // device table of the d_j and w_j pointers
+    lqcd_status ensure_mre(int n, cudaStream_t s);
     // Optional sharing for many right-hand sides on one lattice: the
     // float-float links kept current by the owner (no per-solve split), and
     // the transient float-float fields of another workspace (used only while a
@@ -52,6 +59,13 @@ struct CgRun {
     const lqcd_field *U = nullptr, *Us = nullptr, *b = nullptr;
     double kappa = 0;
     lqcd_cg_params prm{};
+    // optional minimal residual extrapolation of a mixed solve's guess x:
+    // the last n_mre solutions (latest first, FP64), on links mre_links
+    // (an FP32 12-real copy, or the FP64 links) for the FP32 products
+    const lqcd_field *mre_x[CgWorkspace::MRE_MAX + 1] = {};
+    int n_mre = 0;
+    const lqcd_field *mre_links = nullptr;
+    bool mre_used = false; // the guess was refined
     // state
     bool mixed = false, done = false;
     lqcd_status status = LQCD_OK;
@@ -83,6 +97,7 @@ struct CgRun {
   private:
     CgScalars hp{}; // the pause being handled
     lqcd_status start_impl(cudaStream_t s);
+    lqcd_status mre_refine(cudaStream_t s, double *rr0);
     lqcd_status on_pause_impl(const CgScalars &h, cudaStream_t s);
     lqcd_status pause_decide(const CgScalars &h, cudaStream_t s);
 };
@@ -91,9 +106,15 @@ lqcd_status split_links(lqcd_field *Udf, const lqcd_field *U, cudaStream_t s);
 // FP64 copy of a float-float spinor field (rounded hi + lo)
 lqcd_status df_to_f64(lqcd_field *dst, const lqcd_field *src_df, cudaStream_t s);
 
+// mre (optional): the minimal residual extrapolation inputs of CgRun
+struct MreInput {
+    const lqcd_field *x[CgWorkspace::MRE_MAX + 1] = {};
+    int n = 0;
+    const lqcd_field *links = nullptr;
+};
 lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, const lqcd_field *Us,
                         const lqcd_field *b, double kappa, const lqcd_cg_params &prm, lqcd_cg_info *info,
-                        cudaStream_t s);
+                        cudaStream_t s, const MreInput *mre = nullptr);
 
 // |v|^2 and Re<a,b> of FP64 fields into a device double (deterministic)
 lqcd_status spinor_dot_dev(const lqcd_field *a, const lqcd_field *b, double *dst_dev, DevBuf &part, cudaStream_t s);

@@ -210,6 +210,9 @@ lqcd_status reduce_partials(const double *partials, int nblocks, int n, double *
     case 1: final_sum_kernel<1><<<1, 1024, 0, s>>>(partials, nblocks, dst_dev); break;
     case 2: final_sum_kernel<2><<<1, 1024, 0, s>>>(partials, nblocks, dst_dev); break;
     case 3: final_sum_kernel<3><<<1, 1024, 0, s>>>(partials, nblocks, dst_dev); break;
+    case 4: final_sum_kernel<4><<<1, 1024, 0, s>>>(partials, nblocks, dst_dev); break;
+    case 5: final_sum_kernel<5><<<1, 1024, 0, s>>>(partials, nblocks, dst_dev); break;
+    case 9: final_sum_kernel<9><<<1, 1024, 0, s>>>(partials, nblocks, dst_dev); break;
     default: set_error("reduce_partials: n=%d unsupported", n); return LQCD_EINVAL;
     }
     LQCD_LAUNCHED();

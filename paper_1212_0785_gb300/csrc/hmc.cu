@@ -112,7 +112,7 @@ struct lqcd_hmc_state {
     double md_time = 0;
     double pending[2] = {0, 0}; // kick coefficients of each level not yet applied
     // statistics of the current trajectory
-    int cg_iters = 0, n_solves = 0, cg_failures = 0, cg_accurate = 0, cg_failed_checks = 0;
+    int cg_iters = 0, n_solves = 0, cg_failures = 0, cg_accurate = 0, cg_failed_checks = 0, cg_refined = 0;
     double cg_res_max = 0;
 };
 
@@ -144,6 +144,7 @@ static lqcd_status check_params(const lqcd_hmc_params *p)
     }
     LQCD_REQUIRE(p->force_prec == LQCD_F64 || p->force_prec == LQCD_F32, "hmc: force_prec must be F64 or F32");
     LQCD_REQUIRE(p->chrono >= 0 && p->chrono <= CHRONO_MAX, "hmc: chrono must lie in 0..%d", CHRONO_MAX);
+    LQCD_REQUIRE(p->chrono_mre == 0 || p->chrono_mre == 1, "hmc: chrono_mre must be 0 or 1");
     LQCD_REQUIRE(p->gauge_substeps >= 0, "hmc: gauge_substeps must be >= 0");
     return LQCD_OK;
 }
@@ -193,9 +194,13 @@ static lqcd_field *sloppy_links(lqcd_hmc_state *st, const lqcd_hmc_params *p)
 // x_{n-2} (k = 2), 3 x_{n-1} - 3 x_{n-2} + x_{n-3} (k = 3), ...  A solve at the
 // time of the previous one (the action at the end of the trajectory) starts
 // from the previous solution.
+//
+// With chrono_mre the solutions used (latest first) also go to *mre, for the
+// solver's minimal residual refinement of the extrapolated guess.
 static lqcd_status prepare_guess(lqcd_hmc_state *st, PfTerm &t, const lqcd_hmc_params *p, cudaStream_t s,
-                                 int *guess)
+                                 int *guess, MreInput *mre = nullptr)
 {
+    if (mre) mre->n = 0;
     *guess = (p->chrono && t.have_guess) ? 1 : 0;
     if (!*guess || p->chrono < 2 || t.n_hist < 2) return LQCD_OK;
     const int latest = (t.head + CHRONO_MAX - 1) % CHRONO_MAX;
@@ -222,6 +227,11 @@ static lqcd_status prepare_guess(lqcd_hmc_state *st, PfTerm &t, const lqcd_hmc_p
     combine_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((double2 *)t.X.f->data, x[0], x[1], x[2], x[3], w[0],
                                                                w[1], w[2], w[3], m, n);
     LQCD_LAUNCHED();
+    if (mre && p->chrono_mre && p->cg.sloppy != LQCD_F64) {
+        mre->n = m;
+        for (int a = 0; a < m; a++) mre->x[a] = t.hist[idx[a]].f;
+        mre->links = p->force_prec == LQCD_F32 ? st->Uf.f : nullptr; // the FP32 copy is current then
+    }
     return LQCD_OK;
 }
 
@@ -248,6 +258,7 @@ static lqcd_status count_solve(lqcd_hmc_state *st, lqcd_status rc, const lqcd_cg
     st->cg_iters += info.iters;
     st->cg_accurate += info.accurate_residuals;
     st->cg_failed_checks += info.failed_checks;
+    st->cg_refined += info.guess_refined;
     st->n_solves++;
     st->cg_res_max = std::max(st->cg_res_max, info.true_rel_res);
     if (rc == LQCD_ENOCONV) {
@@ -263,8 +274,10 @@ static lqcd_status solve(lqcd_hmc_state *st, PfTerm &t, const lqcd_hmc_params *p
 {
     lqcd_cg_info info{};
     lqcd_cg_params cg = p->cg;
-    LQCD_TRY(prepare_guess(st, t, p, s, &cg.guess));
-    lqcd_status rc = cg_solve_ws(st->ws, t.X.f, st->U, sloppy_links(st, p), b, kappa, cg, &info, s);
+    MreInput mre;
+    LQCD_TRY(prepare_guess(st, t, p, s, &cg.guess, &mre));
+    lqcd_status rc = cg_solve_ws(st->ws, t.X.f, st->U, sloppy_links(st, p), b, kappa, cg, &info, s,
+                                 mre.n >= 2 ? &mre : nullptr);
     LQCD_TRY(record_solution(st, t, p, rc, s));
     return count_solve(st, rc, info);
 }
@@ -504,7 +517,7 @@ static lqcd_status integrate(lqcd_hmc_state *st, const lqcd_hmc_params *p, doubl
 
 static void reset_stats(lqcd_hmc_state *st)
 {
-    st->cg_iters = st->n_solves = st->cg_failures = st->cg_accurate = st->cg_failed_checks = 0;
+    st->cg_iters = st->n_solves = st->cg_failures = st->cg_accurate = st->cg_failed_checks = st->cg_refined = 0;
     st->cg_res_max = 0;
 }
 
@@ -634,6 +647,7 @@ lqcd_status lqcd_hmc_trajectory(lqcd_hmc_state *s, const lqcd_hmc_params *p, lqc
         info->cg_failures = s->cg_failures;
         info->cg_accurate_residuals = s->cg_accurate;
         info->cg_failed_checks = s->cg_failed_checks;
+        info->cg_guesses_refined = s->cg_refined;
         info->traj = s->traj;
     }
     s->traj++;
@@ -722,7 +736,13 @@ static lqcd_status batch_solve(lqcd_batch *B, const lqcd_hmc_params *p, cudaStre
         r.ws = &st->ws, r.x = t.X.f, r.U = st->U, r.Us = sloppy_links(st, &p[i]), r.b = t.phi.f;
         r.kappa = p[i].kappa;
         r.prm = p[i].cg;
-        LQCD_TRY(prepare_guess(st, t, &p[i], s, &r.prm.guess));
+        MreInput mre;
+        LQCD_TRY(prepare_guess(st, t, &p[i], s, &r.prm.guess, &mre));
+        if (mre.n >= 2 && r.prm.guess) {
+            r.n_mre = std::min(mre.n, CgWorkspace::MRE_MAX + 1);
+            for (int j = 0; j < r.n_mre; j++) r.mre_x[j] = mre.x[j];
+            r.mre_links = mre.links;
+        }
         LQCD_TRY(st->ws.ensure(st->U->lat, r.prm.sloppy, s));
         r.start(s, (CgScalars *)B->scal.p + i);
         ptrs.push_back(&r);
@@ -889,6 +909,7 @@ lqcd_status lqcd_batch_trajectory(lqcd_batch *B, const lqcd_hmc_params *params, 
             f.cg_failures = st->cg_failures;
             f.cg_accurate_residuals = st->cg_accurate;
             f.cg_failed_checks = st->cg_failed_checks;
+            f.cg_guesses_refined = st->cg_refined;
             f.traj = st->traj;
         }
         st->traj++;

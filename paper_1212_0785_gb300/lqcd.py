@@ -51,7 +51,8 @@ class CgParams(ctypes.Structure):
 
 class CgInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("true_rel_res", ctypes.c_double),
-                ("seconds", ctypes.c_double), ("accurate_residuals", ctypes.c_int), ("failed_checks", ctypes.c_int)]
+                ("seconds", ctypes.c_double), ("accurate_residuals", ctypes.c_int), ("failed_checks", ctypes.c_int),
+                ("guess_refined", ctypes.c_int)]
 
 
 class HmcParams(ctypes.Structure):
@@ -59,7 +60,7 @@ class HmcParams(ctypes.Structure):
                 ("nsteps", ctypes.c_int), ("integrator", ctypes.c_int), ("n_flavors", ctypes.c_int),
                 ("cg", CgParams), ("reunitarize", ctypes.c_int), ("metropolis", ctypes.c_int),
                 ("chrono", ctypes.c_int), ("force_prec", ctypes.c_int), ("hasenbusch_kappa", ctypes.c_double),
-                ("gauge_substeps", ctypes.c_int), ("heavy_inner", ctypes.c_int)]
+                ("gauge_substeps", ctypes.c_int), ("heavy_inner", ctypes.c_int), ("chrono_mre", ctypes.c_int)]
 
 
 class ServiceParams(ctypes.Structure):
@@ -86,7 +87,7 @@ class TrajInfo(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("cg_true_rel_res_max", ctypes.c_double),
                 ("accepted", ctypes.c_int), ("cg_iters", ctypes.c_int), ("n_solves", ctypes.c_int),
                 ("cg_failures", ctypes.c_int), ("traj", ctypes.c_uint32), ("cg_accurate_residuals", ctypes.c_int),
-                ("cg_failed_checks", ctypes.c_int)]
+                ("cg_failed_checks", ctypes.c_int), ("cg_guesses_refined", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -453,10 +454,10 @@ def spinor_dot(a: Field, b: Field, stream=None) -> float:
 
 def hmc_params(beta, kappa, tau=1.0, nsteps=10, integrator=LEAPFROG, n_flavors=2, cg=None, reunitarize=True,
                metropolis=True, force_prec=F64, chrono=False, hasenbusch_kappa=0.0, gauge_substeps=0,
-               heavy_inner=False) -> HmcParams:
+               heavy_inner=False, chrono_mre=False) -> HmcParams:
     return HmcParams(beta, kappa, tau, nsteps, integrator, n_flavors, cg or cg_params(), int(reunitarize),
                      int(metropolis), int(chrono), int(force_prec), float(hasenbusch_kappa), int(gauge_substeps),
-                     int(heavy_inner))
+                     int(heavy_inner), int(chrono_mre))
 
 
 class HmcState:

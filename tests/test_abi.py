@@ -95,6 +95,6 @@ def test_info_structs_carry_the_solver_counters():
     failed-check counters (appended, so the earlier fields keep their offsets)"""
     names = [f for f, _ in lqcd.CgInfo._fields_]
     assert names[:4] == ["iters", "restarts", "true_rel_res", "seconds"]
-    assert names[4:] == ["accurate_residuals", "failed_checks"]
+    assert names[4:] == ["accurate_residuals", "failed_checks", "guess_refined"]
     tnames = [f for f, _ in lqcd.TrajInfo._fields_]
-    assert tnames[-3:] == ["traj", "cg_accurate_residuals", "cg_failed_checks"]
+    assert tnames[-4:] == ["traj", "cg_accurate_residuals", "cg_failed_checks", "cg_guesses_refined"]

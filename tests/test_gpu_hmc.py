@@ -173,3 +173,28 @@ def test_mixed_hamiltonian_plaquette_from_float_float_links():
         st.close()
     assert abs(out[1][0] - out[0][0]) < 1e-10 * abs(out[0][0])
     assert abs(out[1][1] - out[0][1]) < 1e-6 * abs(out[0][1])
+
+
+@pytest.mark.parametrize("force_prec", [lqcd.F64, lqcd.F32])
+def test_minimal_residual_guess_trajectory(force_prec):
+    """chrono 3 with the minimal residual refinement (paper Sec. 6.2): the
+    same trajectory as the zero guess to the solver tolerance (FP64 forces),
+    or to the FP32 rounding of the solution (FP32 forces); every solve with
+    two earlier solutions at distinct times refines its guess; fewer
+    iterations than the zero guess"""
+    Uh = orc.gauge_start(DIMS, seed=1, eps=0.3)
+    cg = lqcd.cg_params(tol=1e-12, sloppy=lqcd.F16N, delta=0.01)
+    base = dict(beta=5.6, kappa=0.156, tau=0.5, nsteps=8, integrator=lqcd.OMELYAN, cg=cg, force_prec=force_prec)
+    U0, (g0,) = _run_gpu(Uh, lqcd.hmc_params(**base), 1, 1)
+    Uk, (gk,) = _run_gpu(Uh, lqcd.hmc_params(**base, chrono=3), 1, 1)
+    Um, (gm,) = _run_gpu(Uh, lqcd.hmc_params(**base, chrono=3, chrono_mre=True), 1, 1)
+    print("iterations: zero guess", g0["cg_iters"], "extrapolated", gk["cg_iters"], "minimal residual",
+          gm["cg_iters"], "refined", gm["cg_guesses_refined"], "accurate residuals", gk["cg_accurate_residuals"],
+          gm["cg_accurate_residuals"])
+    tol_dh, tol_u = (1e-7, 1e-9) if force_prec == lqcd.F64 else (1e-5, 1e-6)
+    assert abs(gm["dH"] - g0["dH"]) < tol_dh, (gm["dH"], g0["dH"])
+    assert np.max(np.abs(Um - U0)) < tol_u
+    # 17 force evaluations and the final action: solves 3..17 have two earlier solutions
+    assert gm["cg_guesses_refined"] == 15 and gk["cg_guesses_refined"] == 0
+    assert gm["cg_iters"] < g0["cg_iters"]
+    assert gm["n_solves"] == 18 and gm["cg_true_rel_res_max"] <= 1e-12 and gm["cg_failures"] == 0

@@ -48,10 +48,10 @@ def tol_h0_rel(dims, H0, dU_prev):
     return TOL_H0_REL + 24 * BETA * int(np.prod(dims)) * dU_prev / abs(H0)
 
 
-def bench_params(metropolis=True):
+def bench_params(metropolis=True, mre=False):
     cg = lqcd.cg_params(tol=1e-10, maxiter=20000, sloppy=lqcd.F16N, delta=0.003)
     return lqcd.hmc_params(BETA, KAPPA, TAU, NSTEPS, lqcd.OMELYAN, n_flavors=2, cg=cg, force_prec=lqcd.F32,
-                           chrono=3, metropolis=metropolis)
+                           chrono=3, metropolis=metropolis, chrono_mre=mre)
 
 
 def final_solution_error(dims, U_gpu, phi_gpu, U_or, phi_or):
@@ -68,10 +68,10 @@ def final_solution_error(dims, U_gpu, phi_gpu, U_or, phi_or):
     return float(np.max(np.abs(x.download() - xo)) / np.max(np.abs(xo)))
 
 
-def run_and_compare(dims, trajs, metropolis):
+def run_and_compare(dims, trajs, metropolis, mre=False):
     """the GPU chain and the oracle chain from the same start, trajectory by
     trajectory; returns the list of per-result errors"""
-    p = bench_params(metropolis)
+    p = bench_params(metropolis, mre)
     U = lqcd.gauge_field(dims)
     lqcd.gauge_start(U, SEED, EPS)
     st = lqcd.HmcState(U, seed=SEED)
@@ -114,9 +114,11 @@ def check(dims, errs):
         assert e["X_rel"] < TOL_X_REL, e
 
 
-def test_benchmark_configuration_matches_oracle_4x4x4x4():
+@pytest.mark.parametrize("mre", [False, True])
+def test_benchmark_configuration_matches_oracle_4x4x4x4(mre):
+    """(with mre: the guesses refined by minimal residual extrapolation)"""
     dims = (4, 4, 4, 4)
-    errs = run_and_compare(dims, 2, metropolis=True)
+    errs = run_and_compare(dims, 2, metropolis=True, mre=mre)
     assert errs[0]["accept"] == (1, 1)  # dH 0.35 against u 0.082: the compared links moved
     check(dims, errs)
 
