@@ -19,6 +19,7 @@
 
 #include "batch.cuh"
 #include "dslash_df.cuh"
+#include "dslash_packed.cuh"
 #include "dslash_site.cuh"
 
 namespace lqcd {
@@ -27,14 +28,17 @@ constexpr int BCHUNK = 4;
 
 // ---------------------------------------------------------------- kernels
 
-// D (DAG: D^dag) at site cb of one system: FP16+norm with the links
-// prefetched into shared memory (the single-field default), else gathered;
-// both give the same bits
-template <lqcd_prec SP, bool DAG>
+// D (DAG: D^dag) at site cb of one system: FP16+norm in the hopping-term
+// form of the single-field kernels (FORM 2 packed FP32x2 arithmetic, else
+// the links prefetched into shared memory, which gives the bits of the
+// gathered form), other precisions gathered
+template <lqcd_prec SP, bool DAG, int FORM>
 __device__ __forceinline__ Sp<float> sys_site(const SpinorRef<SP> &in, const GaugeRef<SP> &U, const Geo &g, int cb,
                                               int out_par)
 {
-    if constexpr (SP == LQCD_F16N)
+    if constexpr (SP == LQCD_F16N && FORM == 2)
+        return packed_site<DAG>(in, U, g, cb, out_par);
+    else if constexpr (SP == LQCD_F16N)
         return prefetch_site<float, DAG>(in, U, g, cb, out_par);
     else
         return dslash_site<float, SP, SP, DAG>(in, U, g, cb, out_par);
@@ -46,7 +50,7 @@ template <lqcd_prec SP>
 constexpr int min_blocks() { return SP == LQCD_F16N ? 7 : 1; }
 
 // step 0: tmp = D_oe p; step 2: tmp = D_oe^dag-hop t
-template <lqcd_prec SP, bool DAG>
+template <lqcd_prec SP, bool DAG, int FORM>
 __global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP>()) batch_dslash_plain(const SysDesc<SP> *sys, const int2 *bmap)
 {
     const int2 m = bmap[blockIdx.x];
@@ -55,11 +59,11 @@ __global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP>()) batch_dslash_plain
     int cb = m.y * DS_BLOCK + threadIdx.x;
     if (cb >= d.g.Vh) return;
     const SpinorRef<SP> &in = DAG ? d.t : d.p;
-    d.tmp.store(cb, sys_site<SP, DAG>(in, d.U, d.g, cb, 1));
+    d.tmp.store(cb, sys_site<SP, DAG, FORM>(in, d.U, d.g, cb, 1));
 }
 
 // step 1: t = p - kappa^2 D_eo tmp, block sums of |t|^2
-template <lqcd_prec SP>
+template <lqcd_prec SP, int FORM>
 __global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP>()) batch_dslash_xpay(const SysDesc<SP> *sys, const int2 *bmap)
 {
     const int2 m = bmap[blockIdx.x];
@@ -68,7 +72,7 @@ __global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP>()) batch_dslash_xpay(
     int cb = m.y * DS_BLOCK + threadIdx.x;
     float n2 = 0.f;
     if (cb < d.g.Vh) {
-        Sp<float> v = sys_site<SP, false>(d.tmp, d.U, d.g, cb, 0);
+        Sp<float> v = sys_site<SP, false, FORM>(d.tmp, d.U, d.g, cb, 0);
         Sp<float> pv = d.p.template load_rw<float>(cb);
 #pragma unroll
         for (int a = 0; a < 4; a++)
@@ -95,7 +99,7 @@ __global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP>()) batch_dslash_xpay(
 }
 
 // step 3: Ap = t - kappa^2 D_eo^dag-hop tmp; xs += alpha p; r -= alpha Ap; block sums of |r|^2
-template <lqcd_prec SP>
+template <lqcd_prec SP, int FORM>
 __global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP>()) batch_dslash_cg(const SysDesc<SP> *sys, const int2 *bmap)
 {
     const int2 m = bmap[blockIdx.x];
@@ -105,7 +109,7 @@ __global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP>()) batch_dslash_cg(co
     int cb = m.y * DS_BLOCK + threadIdx.x;
     float n2 = 0.f;
     if (cb < d.g.Vh) {
-        Sp<float> ap = sys_site<SP, true>(d.tmp, d.U, d.g, cb, 0);
+        Sp<float> ap = sys_site<SP, true, FORM>(d.tmp, d.U, d.g, cb, 0);
         {
             Sp<float> tv = d.t.template load_rw<float>(cb);
 #pragma unroll
@@ -269,11 +273,19 @@ lqcd_status BatchSolver::enqueue_chunk(cudaStream_t s)
     const SysDesc<SP> *d = (const SysDesc<SP> *)descs.p;
     const int2 *bm = (const int2 *)bmap.p;
     int n = (int)active.size();
+    const bool packed = SP == LQCD_F16N && dslash_form_set(-1) == 2;
     for (int k = 0; k < BCHUNK; k++) {
-        batch_dslash_plain<SP, false><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
-        batch_dslash_xpay<SP><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
-        batch_dslash_plain<SP, true><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
-        batch_dslash_cg<SP><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
+        if (packed) {
+            batch_dslash_plain<SP, false, 2><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
+            batch_dslash_xpay<SP, 2><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
+            batch_dslash_plain<SP, true, 2><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
+            batch_dslash_cg<SP, 2><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
+        } else {
+            batch_dslash_plain<SP, false, 1><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
+            batch_dslash_xpay<SP, 1><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
+            batch_dslash_plain<SP, true, 1><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
+            batch_dslash_cg<SP, 1><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
+        }
         batch_p_update<SP><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
     }
     batch_gather_scalars<SP><<<nblocks_for(n, 128), 128, 0, s>>>(d, (CgScalars *)gathered.p, n);

@@ -645,12 +645,13 @@ class Service:
             pass
 
 
-DSLASH_GATHER, DSLASH_PREFETCH = 0, 1
+DSLASH_GATHER, DSLASH_PREFETCH, DSLASH_PACKED = 0, 1, 2
 
 
 def dslash_form(form=None) -> int:
     """query (None) or select the form of the FP16+norm hopping term: 0
-    gathered, 1 prefetched links (the default); returns the previous form"""
-    if form is not None and int(form) not in (0, 1):
-        raise ValueError("dslash form must be 0 or 1")
+    gathered, 1 prefetched links (the default), 2 prefetched links with packed
+    FP32x2 arithmetic; returns the previous form"""
+    if form is not None and int(form) not in (0, 1, 2):
+        raise ValueError("dslash form must be 0, 1 or 2")
     return int(lib().lqcd_dslash_form(-1 if form is None else int(form)))

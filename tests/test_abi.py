@@ -85,7 +85,7 @@ def test_dslash_form_switch_is_host_state(L):
         assert L.lqcd_dslash_form(7) == -1 and lqcd.dslash_form() == lqcd.DSLASH_PREFETCH
         assert b"unknown form" in L.lqcd_last_error()
         with pytest.raises(ValueError):
-            lqcd.dslash_form(2)
+            lqcd.dslash_form(3)
     finally:
         lqcd.dslash_form(prev)
 

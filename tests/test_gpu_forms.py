@@ -73,3 +73,50 @@ def test_forms_mhat_and_mixed_solve_bitwise(dims, form):
     assert np.array_equal(res[0][1], res[1][1]) and res[0][2:] == res[1][2:]
     r = half(eta, dims, 0) - half(orc.mdagm(dims, Uh, 0.155, full_from_half(res[1][1], dims, 0)), dims, 0)
     assert np.linalg.norm(r) <= 1.01e-11 * np.linalg.norm(half(eta, dims, 0))
+
+
+@pytest.mark.parametrize("dims", [DIMS[0], DIMS[3]])
+@pytest.mark.parametrize("t_bc", [-1, 1])
+def test_packed_form_matches_prefetched(dims, t_bc, form):
+    """form 2 (packed FP32x2 arithmetic) rounds its products in another order:
+    its FP32 results agree with form 1's to FP32 rounding, so the stored FP16
+    values differ by at most one FP16 step of the site norm (2^-10 relative);
+    both match the oracle to the FP16+norm bound"""
+    Uh, U, Us = _fields(dims, t_bc, 90)
+    for par in (0, 1):
+        psi = inputs.random_spinor(dims, 91 + par, parity=par)
+        inp = lqcd.spinor_field(dims, par, lqcd.F16N, t_bc=t_bc).copy_from(
+            lqcd.spinor_field(dims, par, t_bc=t_bc).upload(half(psi, dims, par)))
+        ref = orc.dslash(dims, Uh, full_from_half(inp.download(), dims, par), t_bc=t_bc)
+        for dag in (False, True):
+            outs = []
+            for f in (lqcd.DSLASH_PREFETCH, lqcd.DSLASH_PACKED):
+                lqcd.dslash_form(f)
+                out = lqcd.spinor_field(dims, 1 - par, lqcd.F16N, t_bc=t_bc)
+                lqcd.dslash(out, Us, inp, dag)
+                outs.append(out.download())
+            site_norm = np.max(np.abs(outs[0]).reshape(len(outs[0]), -1), axis=1)
+            diff = np.max(np.abs(outs[1] - outs[0]).reshape(len(outs[0]), -1), axis=1)
+            assert np.all(diff <= 2.0 ** -10 * site_norm + 1e-30), (par, dag, float(np.max(diff / site_norm)))
+            if not dag:
+                assert rel_err(outs[1], half(ref, dims, 1 - par)) < F16N_TOL
+
+
+def test_packed_form_mixed_solve_and_batch(form):
+    """a whole mixed solve in form 2 reaches the FP64 tolerance, and the
+    batched engine (which follows the form) equals the single solve bitwise"""
+    dims = DIMS[3]
+    Uh, U, Us = _fields(dims, -1, 95)
+    eta = inputs.random_spinor(dims, 96, parity=0)
+    b = lqcd.spinor_field(dims, 0).upload(half(eta, dims, 0))
+    lqcd.dslash_form(lqcd.DSLASH_PACKED)
+    prm = lqcd.cg_params(tol=1e-11, sloppy=lqcd.F16N, delta=0.01)
+    x = lqcd.spinor_field(dims, 0)
+    rc, info = lqcd.cg_solve(x, U, b, 0.155, prm, U_sloppy=Us)
+    assert rc == lqcd.OK
+    r = half(eta, dims, 0) - half(orc.mdagm(dims, Uh, 0.155, full_from_half(x.download(), dims, 0)), dims, 0)
+    assert np.linalg.norm(r) <= 1.01e-11 * np.linalg.norm(half(eta, dims, 0))
+    xb = lqcd.spinor_field(dims, 0)
+    rc, infos = lqcd.cg_solve_batch([xb], [U], [Us], [b], [0.155], prm)
+    assert rc == lqcd.OK and infos[0].iters == info.iters
+    assert np.array_equal(xb.download(), x.download())
