@@ -276,14 +276,19 @@ lqcd_status CgWorkspace::ensure_mre(int n, cudaStream_t s)
     n = std::min(n, MRE_MAX);
     // the normal equations' block partials: up to 9 sums of CG_BLOCK-site blocks
     const size_t need = 9 * (size_t)nblocks_for(make_geo(lat).Vh, BB) * sizeof(double);
-    if (partials.bytes < need) LQCD_TRY(partials.alloc(need, s));
-    if (!mre_te.f) {
-        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F32, 0, &mre_te.f));
-        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F32, 0, &mre_to.f));
+    if (partials.bytes < need) {
+        lqcd_status rc = partials.alloc(need, s);
+        if (rc != LQCD_OK) { // the old buffer is gone: the next solve rebuilds the work space
+            ready = false;
+            return rc;
+        }
     }
+    // each field only if missing, so a call that failed half way can be repeated
+    if (!mre_te.f) LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F32, 0, &mre_te.f));
+    if (!mre_to.f) LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F32, 0, &mre_to.f));
     for (; mre_n < n; mre_n++) {
-        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F32, 0, &mre_d[mre_n].f));
-        LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F32, 0, &mre_w[mre_n].f));
+        if (!mre_d[mre_n].f) LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F32, 0, &mre_d[mre_n].f));
+        if (!mre_w[mre_n].f) LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F32, 0, &mre_w[mre_n].f));
     }
     return LQCD_OK;
 }

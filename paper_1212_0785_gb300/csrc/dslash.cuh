@@ -67,7 +67,7 @@ __device__ __forceinline__ void cg_rr_step(CgScalars *sc, double rr_new)
 }
 
 // Fixed-order sum of partials[0..n) by one block of BLOCK threads: thread i
-// adds partials[i], partials[i + BLOCK], ... in that order (eight loads in
+// adds partials[i], partials[i + BLOCK], ... in that order (sixteen loads in
 // flight, read from L2 since other blocks wrote them), then the warps reduce
 // by shuffles and warp 0 adds the warp totals in warp order.  The result,
 // valid in thread 0, does not depend on which block computes it.
@@ -77,12 +77,12 @@ __device__ __forceinline__ double block_final_sum(const double *partials, int n)
     __shared__ double wsum[BLOCK / 32];
     double s = 0.0;
     int i = threadIdx.x;
-    for (; i + 7 * BLOCK < n; i += 8 * BLOCK) {
-        double v[8];
+    for (; i + 15 * BLOCK < n; i += 16 * BLOCK) {
+        double v[16];
 #pragma unroll
-        for (int k = 0; k < 8; k++) v[k] = __ldcg(partials + i + k * BLOCK);
+        for (int k = 0; k < 16; k++) v[k] = __ldcg(partials + i + k * BLOCK);
 #pragma unroll
-        for (int k = 0; k < 8; k++) s += v[k];
+        for (int k = 0; k < 16; k++) s += v[k];
     }
     for (; i < n; i += BLOCK) s += __ldcg(partials + i);
 #pragma unroll

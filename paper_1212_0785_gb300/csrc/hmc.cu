@@ -169,16 +169,22 @@ static lqcd_status ensure_sloppy(lqcd_hmc_state *st, const lqcd_hmc_params *p, c
     return lqcd_field_copy(st->Us.f, st->U, s);
 }
 
+// allocates f unless it is already there: a call that failed half way (the
+// allocator returned NULL) leaves the fields it made, and the next call makes
+// only the missing ones
+static lqcd_status ensure_field(FieldPtr &f, const lqcd_lattice &lat, lqcd_kind kind, lqcd_prec prec)
+{
+    return f.f ? LQCD_OK : lqcd_field_alloc(&lat, kind, prec, 0, &f.f);
+}
+
 static lqcd_status ensure_hasenbusch(lqcd_hmc_state *st)
 {
-    if (st->eta_h.f) return LQCD_OK;
     const lqcd_lattice &lat = st->U->lat;
-    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->eta_h.f));
-    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->z.f));
-    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->pf[PF_MAIN].chi.f));
-    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->pf[PF_HEAVY].phi.f));
-    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F64, 0, &st->pf[PF_HEAVY].X.f));
-    return LQCD_OK;
+    LQCD_TRY(ensure_field(st->eta_h, lat, LQCD_SPINOR_EVEN, LQCD_F64));
+    LQCD_TRY(ensure_field(st->z, lat, LQCD_SPINOR_EVEN, LQCD_F64));
+    LQCD_TRY(ensure_field(st->pf[PF_MAIN].chi, lat, LQCD_SPINOR_EVEN, LQCD_F64));
+    LQCD_TRY(ensure_field(st->pf[PF_HEAVY].phi, lat, LQCD_SPINOR_EVEN, LQCD_F64));
+    return ensure_field(st->pf[PF_HEAVY].X, lat, LQCD_SPINOR_EVEN, LQCD_F64);
 }
 
 static lqcd_field *sloppy_links(lqcd_hmc_state *st, const lqcd_hmc_params *p)
@@ -284,13 +290,11 @@ static lqcd_status solve(lqcd_hmc_state *st, PfTerm &t, const lqcd_hmc_params *p
 
 static lqcd_status ensure_f32_temps(lqcd_hmc_state *st)
 {
-    if (st->Ao32.f) return LQCD_OK;
     const lqcd_lattice &lat = st->U->lat;
-    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F32, 0, &st->Ao32.f));
-    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F32, 0, &st->Ye32.f));
-    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, LQCD_F32, 0, &st->Bo32.f));
-    LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F32, 0, &st->X32.f));
-    return LQCD_OK;
+    LQCD_TRY(ensure_field(st->Ao32, lat, LQCD_SPINOR_ODD, LQCD_F32));
+    LQCD_TRY(ensure_field(st->Ye32, lat, LQCD_SPINOR_EVEN, LQCD_F32));
+    LQCD_TRY(ensure_field(st->Bo32, lat, LQCD_SPINOR_ODD, LQCD_F32));
+    return ensure_field(st->X32, lat, LQCD_SPINOR_EVEN, LQCD_F32);
 }
 
 // P <- P - c F with F the force of -2 Re[Y^dag dMhat(kappa) X] (Y = Mhat X if Y is NULL)

@@ -13,8 +13,10 @@ Host arrays use the canonical layouts of include/lqcd.h as numpy arrays:
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 import re
+import time
 import threading
 
 import numpy as np
@@ -257,6 +259,32 @@ def install_torch_allocator():
     _allocator_installed = True
 
 
+def set_allocator(alloc, free):
+    """Point the library's allocator hook at Python callables alloc(nbytes,
+    stream) -> device pointer or None, and free(ptr, stream); None, None
+    restores PyTorch's caching allocator.  Fields remember the hook that made
+    them and are released through it."""
+    global _allocator_installed
+    if alloc is None:
+        _allocator_installed = False
+        install_torch_allocator()
+        return
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return alloc(int(nbytes), stream)
+        except Exception:
+            return None
+
+    def _free(ptr, stream, ctx):
+        free(int(ptr), stream)
+
+    a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+    _alloc_keep.extend([a, f])
+    _check(lib().lqcd_set_allocator(a, f, None), "set_allocator")
+    _allocator_installed = True
+
+
 def current_stream() -> int:
     return _torch().cuda.current_stream().cuda_stream
 
@@ -466,7 +494,7 @@ class HmcState:
     def __init__(self, U: Field, seed, chain=0, traj0=0):
         h = ctypes.c_void_p()
         _check(lib().lqcd_hmc_state_create(U.h, seed, chain, traj0, ctypes.byref(h)), "hmc_state_create")
-        self.h, self.U = h, U
+        self.h, self.U, self.seed, self.chain = h, U, int(seed), int(chain)
 
     def fields(self):
         u, p, phi = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
@@ -501,11 +529,33 @@ class HmcState:
     def md_step(self, params: HmcParams, stream=None):
         _check(lib().lqcd_md_step(self.h, ctypes.byref(params), _s(stream)), "md_step")
 
-    def trajectory(self, params: HmcParams, stream=None) -> dict:
+    def trajectory(self, params: HmcParams, stream=None, log=None) -> dict:
+        """One trajectory; its info as a dict.  log: a path or a text file to
+        which one JSON line with the trajectory's metrics is appended."""
         info = TrajInfo()
-        _check(lib().lqcd_hmc_trajectory(self.h, ctypes.byref(params), ctypes.byref(info), _s(stream)),
-               "hmc_trajectory")
-        return info.as_dict()
+        rc = lib().lqcd_hmc_trajectory(self.h, ctypes.byref(params), ctypes.byref(info), _s(stream))
+        d = info.as_dict()
+        if log is not None:
+            write_log_line(log, dict(d, status=int(rc), seed=self.seed, chain=self.chain, dims=list(self.U.dims),
+                                     time=time.time()))
+        _check(rc, "hmc_trajectory")
+        return d
+
+    def checkpoint(self, path):
+        """Saves what resuming this chain needs -- the FP64 links in the
+        canonical host layout, the Philox key (seed, chain) and the trajectory
+        counter -- to an .npz file.  The random numbers of every trajectory
+        follow from (seed, chain, traj) alone, so a resumed chain repeats the
+        unbroken one bit for bit."""
+        np.savez(path, U=self.U.download(), dims=np.array(self.U.dims), t_bc=self.U.t_bc, seed=self.seed,
+                 chain=self.chain, traj=self.traj)
+
+    @classmethod
+    def resume(cls, path) -> "HmcState":
+        """A new chain state (and its FP64 gauge field, state.U) from a checkpoint file."""
+        z = np.load(path)
+        U = gauge_field(tuple(int(v) for v in z["dims"]), t_bc=int(z["t_bc"])).upload(z["U"])
+        return cls(U, int(z["seed"]), int(z["chain"]), int(z["traj"]))
 
     def close(self):
         if self.h:
@@ -520,6 +570,17 @@ class HmcState:
 
 
 # ---------------------------------------------------------------- batches
+
+def write_log_line(log, record: dict):
+    """Appends record as one JSON line to log (a path or a text file)."""
+    line = json.dumps(record, sort_keys=True) + "\n"
+    if hasattr(log, "write"):
+        log.write(line)
+        log.flush()
+    else:
+        with open(log, "a") as fh:
+            fh.write(line)
+
 
 def _ptrs(fields):
     arr = (ctypes.c_void_p * max(1, len(fields)))()
