@@ -534,8 +534,8 @@ def run_ours(args):
                              f"links/momenta, residuals, dots, link update, dH"),
             "data": "synthetic",
             "config": dict(config_block(args, args.sloppy, args.force_prec),
-                           dslash_form={0: "gathered", 1: "prefetched_links", 2: "prefetched_links_packed_f32x2",
-                                        3: "prefetched_links_packed_f32x2_l2_prefetch"}.get(lqcd.dslash_form(), "?")),
+                           dslash_form={0: "gathered", 1: "prefetched_links", 2: "prefetched_links_packed_f32x2"}.get(
+                               lqcd.dslash_form(), "?")),
             "gpu_launches": launches,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "fp64_gpu_path": fp64,
             "physics": {"acceptance": float(np.mean(acc)), "dH": [i["dH"] for i in infos],

@@ -223,19 +223,17 @@ lqcd_status lqcd_eta_refresh(lqcd_field *eta, uint32_t seed, uint32_t chain, uin
  * spinors of precision q (q in F32, F16N, BF16; FP32 arithmetic). */
 lqcd_status lqcd_dslash(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int dagger, void *stream);
 
-/* The FP16+norm hopping term comes in four forms:
+/* The FP16+norm hopping term comes in three forms:
  *   0  every operand gathered by its thread;
  *   1  each thread first starts asynchronous copies (cp.async) of its eight
  *      links into shared memory, then gathers the neighbour spinors and waits
  *      for each direction's links only when it needs them;
  *   2  (the default) form 1 with the two spin rows of every projected half
- *      spinor carried as pairs in Blackwell's packed FP32x2 instructions;
- *   3  form 2 that also asks L2 for all neighbour spinors before the first hop.
- * Forms 0 and 1 give bitwise the same results, and so do forms 2 and 3; forms
- * 2 and 3 round their products in another order than 0 and 1 (agreement
- * within FP32 rounding).  The multi-system solver (lqcd_cg_solve_batch,
- * batched chains, solve service) follows the setting.
- * lqcd_dslash_form(form) selects the form (0 to 3; a negative value queries)
+ *      spinor carried as pairs in Blackwell's packed FP32x2 instructions.
+ * Forms 0 and 1 give bitwise the same results; form 2 rounds its products in
+ * another order (agreement within FP32 rounding).  The multi-system solver
+ * (lqcd_cg_solve_batch, batched chains, solve service) follows the setting.
+ * lqcd_dslash_form(form) selects the form (0, 1, 2; a negative value queries)
  * and returns the previous one (process-wide); an unknown form returns -1,
  * leaves the setting unchanged and sets lqcd_last_error. */
 int lqcd_dslash_form(int form);

@@ -29,16 +29,15 @@ constexpr int BCHUNK = 4;
 // ---------------------------------------------------------------- kernels
 
 // D (DAG: D^dag) at site cb of one system: FP16+norm in the hopping-term
-// form of the single-field kernels (FORM 2 packed FP32x2 arithmetic, FORM 3
-// the same with the neighbour spinors prefetched into L2, else the links
-// prefetched into shared memory, which gives the bits of the gathered form),
-// other precisions gathered
+// form of the single-field kernels (FORM 2 packed FP32x2 arithmetic, else
+// the links prefetched into shared memory, which gives the bits of the
+// gathered form), other precisions gathered
 template <lqcd_prec SP, bool DAG, int FORM>
 __device__ __forceinline__ Sp<float> sys_site(const SpinorRef<SP> &in, const GaugeRef<SP> &U, const Geo &g, int cb,
                                               int out_par)
 {
-    if constexpr (SP == LQCD_F16N && FORM >= 2)
-        return packed_site<DAG, FORM == 3>(in, U, g, cb, out_par);
+    if constexpr (SP == LQCD_F16N && FORM == 2)
+        return packed_site<DAG>(in, U, g, cb, out_par);
     else if constexpr (SP == LQCD_F16N)
         return prefetch_site<float, DAG>(in, U, g, cb, out_par);
     else
@@ -276,12 +275,7 @@ lqcd_status BatchSolver::enqueue_chunk(cudaStream_t s)
     int n = (int)active.size();
     const int form = SP == LQCD_F16N ? dslash_form_set(-1) : 1;
     for (int k = 0; k < BCHUNK; k++) {
-        if (form == 3) {
-            batch_dslash_plain<SP, false, 3><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
-            batch_dslash_xpay<SP, 3><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
-            batch_dslash_plain<SP, true, 3><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
-            batch_dslash_cg<SP, 3><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
-        } else if (form == 2) {
+        if (form == 2) {
             batch_dslash_plain<SP, false, 2><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
             batch_dslash_xpay<SP, 2><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);
             batch_dslash_plain<SP, true, 2><<<nblocks_total, DS_BLOCK, 0, s>>>(d, bm);

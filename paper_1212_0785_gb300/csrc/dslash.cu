@@ -34,8 +34,6 @@ __device__ __forceinline__ Sp<R> site_value(const SpinorRef<SP> &in, const Gauge
         return prefetch_site<R, DAG>(in, U, g, cb, out_par);
     else if constexpr (FORM == 2 && SP == LQCD_F16N && GP == LQCD_F16N && std::is_same<R, float>::value)
         return packed_site<DAG>(in, U, g, cb, out_par);
-    else if constexpr (FORM == 3 && SP == LQCD_F16N && GP == LQCD_F16N && std::is_same<R, float>::value)
-        return packed_site<DAG, true>(in, U, g, cb, out_par);
     else
         return dslash_site<R, SP, GP, DAG>(in, U, g, cb, out_par);
 }
@@ -196,32 +194,6 @@ __global__ void __launch_bounds__(DS_BLOCK, 7) dslash_cg_packed_kernel(SpinorRef
     cg_body<R, SP, GP, DAG, XP, 2>(in, U, g, out_par, t, b, xs, r, p, partials, nblocks, sc);
 }
 
-template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
-__global__ void __launch_bounds__(DS_BLOCK, 7) dslash_plain_packedpf_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
-                                                                           GaugeRef<GP> U, Geo g, int out_par,
-                                                                           const int *skip)
-{
-    plain_body<R, SP, GP, DAG, 3>(out, in, U, g, out_par, skip);
-}
-template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
-__global__ void __launch_bounds__(DS_BLOCK, 7) dslash_xpay_packedpf_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
-                                                                          GaugeRef<GP> U, Geo g, int out_par,
-                                                                          SpinorRef<SP> x, R b, double *partials,
-                                                                          int nblocks, const int *skip,
-                                                                          CgScalars *fin)
-{
-    xpay_body<R, SP, GP, DAG, 3>(out, in, U, g, out_par, x, b, partials, nblocks, skip, fin);
-}
-template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, lqcd_prec XP>
-__global__ void __launch_bounds__(DS_BLOCK, 7) dslash_cg_packedpf_kernel(SpinorRef<SP> in, GaugeRef<GP> U, Geo g,
-                                                                        int out_par, SpinorRef<SP> t, R b,
-                                                                        SpinorRef<XP> xs, SpinorRef<SP> r,
-                                                                        SpinorRef<SP> p, double *partials,
-                                                                        int nblocks, CgScalars *sc)
-{
-    cg_body<R, SP, GP, DAG, XP, 3>(in, U, g, out_par, t, b, xs, r, p, partials, nblocks, sc);
-}
-
 // ---------------------------------------------------------------- dispatch
 
 static int out_parity(const lqcd_field *f) { return f->kind == LQCD_SPINOR_EVEN ? 0 : 1; }
@@ -254,8 +226,7 @@ struct ArithOf<PREC_DF> {
 };
 
 // the FP16+norm form: 2 prefetched links with packed FP32x2 arithmetic
-// (default), 3 the same with the neighbour spinors prefetched into L2, 1
-// prefetched links, 0 gathered
+// (default), 1 prefetched links, 0 gathered
 static std::atomic<int> g_form{2};
 
 template <lqcd_prec P, lqcd_prec GP>
@@ -272,8 +243,6 @@ static int use_form(const Geo &)
             kern##_prefetch_kernel<LQCD_UNPAREN targs><<<grid, DS_BLOCK, 0, s>>> args;                               \
         else if (form == 2)                                                                                          \
             kern##_packed_kernel<LQCD_UNPAREN targs><<<grid, DS_BLOCK, 0, s>>> args;                                 \
-        else if (form == 3)                                                                                          \
-            kern##_packedpf_kernel<LQCD_UNPAREN targs><<<grid, DS_BLOCK, 0, s>>> args;                               \
         else                                                                                                         \
             kern##_kernel<LQCD_UNPAREN targs><<<grid, DS_BLOCK, 0, s>>> args;                                        \
     } while (0)
@@ -336,10 +305,8 @@ static void launch_cg(const lqcd_field *U, const lqcd_field *in, int dagger, con
 int dslash_form_set(int form)
 {
     if (form < 0) return g_form.load();
-    if (form > 3) {
-        set_error("dslash_form: unknown form %d (0 gathered, 1 prefetched links, 2 packed, 3 packed with L2 "
-                  "prefetch)",
-                  form);
+    if (form > 2) {
+        set_error("dslash_form: unknown form %d (0 gathered, 1 prefetched links, 2 packed)", form);
         return -1;
     }
     return g_form.exchange(form);

@@ -150,14 +150,7 @@ __device__ __forceinline__ void hop_packed(SpP &acc, const SpF &psi, float sc, c
     accumulate_p<MU, S>(acc, mul_link_p<FWD>(u, project_p<MU, S>(psi)), flip ? -sc : sc);
 }
 
-__device__ __forceinline__ void prefetch_l2(const void *p)
-{
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p)));
-}
-
-// L2PF: before the first hop, ask L2 for the eight neighbour spinors and their
-// norms (no registers held; the later loads then wait on L2, not on DRAM)
-template <bool DAG, bool L2PF = false>
+template <bool DAG>
 __device__ __forceinline__ Sp<float> packed_site(const SpinorRef<LQCD_F16N> &in, const GaugeRef<LQCD_F16N> &U,
                                                  const Geo &g, int cb, int out_par)
 {
@@ -175,14 +168,6 @@ __device__ __forceinline__ Sp<float> packed_site(const SpinorRef<LQCD_F16N> &in,
             cp_async8(&lp.u[mu][1][k][i], U.d + U.idx(mu, 1 - out_par, k, nb[2 * mu + 1]));
         }
         cp_async_commit();
-    }
-    if (L2PF) {
-#pragma unroll
-        for (int n = 2; n < 8; n++) { // the first two neighbours are loaded at once anyway
-#pragma unroll
-            for (int k = 0; k < 3; k++) prefetch_l2(in.d + (size_t)k * in.Vh + nb[n]);
-            prefetch_l2(in.norm + nb[n]);
-        }
     }
     constexpr int FS = DAG ? +1 : -1;
     constexpr int BS = -FS;

@@ -706,14 +706,13 @@ class Service:
             pass
 
 
-DSLASH_GATHER, DSLASH_PREFETCH, DSLASH_PACKED, DSLASH_PACKED_L2 = 0, 1, 2, 3
+DSLASH_GATHER, DSLASH_PREFETCH, DSLASH_PACKED = 0, 1, 2
 
 
 def dslash_form(form=None) -> int:
     """query (None) or select the form of the FP16+norm hopping term: 0
     gathered, 1 prefetched links, 2 prefetched links with packed FP32x2
-    arithmetic (the default), 3 form 2 with the neighbour spinors prefetched
-    into L2; returns the previous form"""
-    if form is not None and int(form) not in (0, 1, 2, 3):
-        raise ValueError("dslash form must be 0, 1, 2 or 3")
+    arithmetic (the default); returns the previous form"""
+    if form is not None and int(form) not in (0, 1, 2):
+        raise ValueError("dslash form must be 0, 1 or 2")
     return int(lib().lqcd_dslash_form(-1 if form is None else int(form)))

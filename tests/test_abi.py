@@ -78,14 +78,14 @@ def test_dslash_form_switch_is_host_state(L):
     nothing"""
     prev = lqcd.dslash_form()
     try:
-        assert prev in (lqcd.DSLASH_GATHER, lqcd.DSLASH_PREFETCH, lqcd.DSLASH_PACKED, lqcd.DSLASH_PACKED_L2)
+        assert prev in (lqcd.DSLASH_GATHER, lqcd.DSLASH_PREFETCH, lqcd.DSLASH_PACKED)
         lqcd.dslash_form(lqcd.DSLASH_GATHER)
         assert lqcd.dslash_form(lqcd.DSLASH_PREFETCH) == lqcd.DSLASH_GATHER
         assert lqcd.dslash_form() == lqcd.DSLASH_PREFETCH
         assert L.lqcd_dslash_form(7) == -1 and lqcd.dslash_form() == lqcd.DSLASH_PREFETCH
         assert b"unknown form" in L.lqcd_last_error()
         with pytest.raises(ValueError):
-            lqcd.dslash_form(4)
+            lqcd.dslash_form(3)
     finally:
         lqcd.dslash_form(prev)
 

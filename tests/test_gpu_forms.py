@@ -2,10 +2,9 @@
 thread (0) and each thread's links prefetched into shared memory by cp.async
 (1) give bitwise the same results on full and ragged last blocks, across the
 z and t boundaries, for both boundary conditions, both parities, D and D^dag,
-the axpy/CG epilogues and a whole mixed solve; so do the packed FP32x2 form
-(2, the default) and that form with the neighbour spinors prefetched into L2
-(3).  Forms 2 and 3 round in another order than 0 and 1 and agree with them
-to one FP16 step; all match the oracle to FP16 accuracy."""
+the axpy/CG epilogues and a whole mixed solve.  The packed FP32x2 form (2,
+the default) rounds in another order and agrees with them to one FP16 step;
+all match the oracle to FP16 accuracy."""
 import numpy as np
 import pytest
 
@@ -18,7 +17,6 @@ pytestmark = pytest.mark.gpu
 # Vh = 512, 576 (whole blocks of 128), 432 and 1728 (a ragged last block)
 DIMS = [(16, 16, 4, 4), (32, 8, 4, 6), (6, 6, 4, 6), (8, 6, 6, 12)]
 FORMS = (lqcd.DSLASH_GATHER, lqcd.DSLASH_PREFETCH)
-PACKED_FORMS = (lqcd.DSLASH_PACKED, lqcd.DSLASH_PACKED_L2)
 F16N_TOL = 3e-3  # FP16+norm storage rounding, derived in the design doc section 7a
 
 
@@ -36,10 +34,10 @@ def _fields(dims, t_bc, seed):
     return Uh, U, Us
 
 
-@pytest.mark.parametrize("forms", [FORMS, PACKED_FORMS])
 @pytest.mark.parametrize("dims", DIMS)
 @pytest.mark.parametrize("t_bc", [-1, 1])
-def test_forms_dslash_bitwise(dims, t_bc, forms, form):
+def test_forms_dslash_bitwise(dims, t_bc, form):
+    forms = FORMS
     Uh, U, Us = _fields(dims, t_bc, 50)
     for par in (0, 1):
         psi = inputs.random_spinor(dims, 51 + par, parity=par)
@@ -57,9 +55,9 @@ def test_forms_dslash_bitwise(dims, t_bc, forms, form):
             assert rel_err(outs[1], half(ref, dims, 1 - par)) < F16N_TOL
 
 
-@pytest.mark.parametrize("forms", [FORMS, PACKED_FORMS])
 @pytest.mark.parametrize("dims", DIMS[1:2] + DIMS[3:])
-def test_forms_mhat_and_mixed_solve_bitwise(dims, forms, form):
+def test_forms_mhat_and_mixed_solve_bitwise(dims, form):
+    forms = FORMS
     Uh, U, Us = _fields(dims, -1, 60)
     eta = inputs.random_spinor(dims, 61, parity=0)
     b = lqcd.spinor_field(dims, 0).upload(half(eta, dims, 0))

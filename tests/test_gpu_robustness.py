@@ -114,7 +114,9 @@ def test_nan_link_is_rejected(mixed):
     Uh[17, 2, 1, 0] = np.nan
     U = lqcd.gauge_field(DIMS).upload(Uh)
     st = lqcd.HmcState(U, seed=1)
-    p = mixed_params() if mixed else lqcd.hmc_params(5.6, 0.156, 0.5, 4, cg=lqcd.cg_params(tol=1e-10))
+    # no reunitarization after the reject, so the restored links are the uploaded bits
+    p = (mixed_params(reunitarize=False) if mixed else
+         lqcd.hmc_params(5.6, 0.156, 0.5, 4, cg=lqcd.cg_params(tol=1e-10), reunitarize=False))
     with pytest.raises(lqcd.LqcdError) as ei:
         st.trajectory(p)
     assert ei.value.status == lqcd.ENUMERIC
@@ -125,7 +127,7 @@ def test_nan_link_is_rejected(mixed):
     U2 = lqcd.gauge_field(DIMS).upload(Uh)
     st2 = lqcd.HmcState(U2, seed=1)
     with pytest.raises(lqcd.LqcdError) as ei:
-        st2.trajectory(lqcd.hmc_params(5.6, 0.0, 0.5, 4, n_flavors=0))
+        st2.trajectory(lqcd.hmc_params(5.6, 0.0, 0.5, 4, n_flavors=0, reunitarize=False))
     assert ei.value.status == lqcd.ENUMERIC
     st2.close()
     # the library stays usable
