@@ -378,6 +378,11 @@ def run_ours(args):
     params = lqcd.hmc_params(wl["beta"], wl["kappa"], wl["tau"], args.nsteps, lqcd.OMELYAN, n_flavors=2, cg=cg,
                              force_prec=force_prec, chrono=int(args.chrono), chrono_mre=args.mre)
 
+    tuned = None
+    if args.autotune:
+        # threads per block of the tunable kernels on this lattice (paper Sec. 4),
+        # before the warm-up; the timings go to --tune-file if given
+        tuned = lqcd.autotune(dims, args.tune_file)
     U = lqcd.gauge_field(dims)
     lqcd.gauge_start(U, SEED, EPS, chain=rank)
     state = lqcd.HmcState(U, seed=SEED, chain=rank)
@@ -533,7 +538,7 @@ def run_ours(args):
             "dtype_detail": (f"f32 math ({args.sloppy} storage in the solver, {args.force_prec} forces); f64 master "
                              f"links/momenta, residuals, dots, link update, dH"),
             "data": "synthetic",
-            "config": dict(config_block(args, args.sloppy, args.force_prec),
+            "config": dict(config_block(args, args.sloppy, args.force_prec), threads_per_block=tuned,
                            dslash_form={0: "gathered", 1: "prefetched_links", 2: "prefetched_links_packed_f32x2"}.get(
                                lqcd.dslash_form(), "?")),
             "gpu_launches": launches,
@@ -850,6 +855,9 @@ def main(argv=None):
                     help="initial guess of each solve after the first of a trajectory: 0 zero, 1 the previous "
                          "solution, k >= 2 extrapolated through the last k solutions (both the mixed and the "
                          "FP64 path)")
+    ap.add_argument("--autotune", type=int, choices=(0, 1), default=1,
+                    help="1: tune the threads per block of the tunable kernels on the lattice first")
+    ap.add_argument("--tune-file", default=None, help="write the autotuner's timings to this file")
     ap.add_argument("--mre", type=int, choices=(0, 1), default=0,
                     help="1: refine the extrapolated guesses by minimal residual extrapolation")
     ap.add_argument("--dims", type=int, nargs=4, default=WORKLOAD["dims"])

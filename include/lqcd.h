@@ -349,6 +349,30 @@ lqcd_status lqcd_kinetic_energy(const lqcd_field *P, double *out, void *stream);
  * same kind.  out: host. */
 lqcd_status lqcd_spinor_dot(const lqcd_field *a, const lqcd_field *b, double *out, void *stream);
 
+/* ------------------------------------------------------------ autotuning (paper Sec. 4) */
+
+/* The paper times each generated kernel over its threads-per-block settings on
+ * first use and keeps the fastest (Sec. 4).  Here that is an explicit call:
+ * lqcd_autotune times, on scratch fields of the lattice (allocated and freed
+ * inside), every candidate block size of the kernel classes whose launch shape
+ * is free -- "dslash_f16n" (the packed FP16+norm hopping term: 64, 128, 256),
+ * "gauge_force_f32", "gauge_force_f64" and "link_update_f32" (32 to 256),
+ * "fermion_force_f32" (32 to 128) -- keeps the fastest of each in a
+ * process-wide table keyed by (kernel class, lattice dims) that every later
+ * launch on that lattice reads, and writes all timings to the text file path
+ * (lines "class Lx Ly Lz Lt block ms_per_launch best"; NULL: no file).
+ * Synchronises stream.  Results do not depend on the block size of the force
+ * and link-update kernels; the hopping term's block size sets the order of
+ * its block sums, so a tuned size other than 128 changes the solver's
+ * rounding (the multi-system solver always uses 128).
+ * lqcd_autotune_load reads such a file into the table; lqcd_autotune_block
+ * returns a class's block size for a lattice (0: not tuned, the default
+ * applies); lqcd_autotune_clear empties the table. */
+lqcd_status lqcd_autotune(const lqcd_lattice *lat, const char *path, void *stream);
+lqcd_status lqcd_autotune_load(const char *path);
+lqcd_status lqcd_autotune_block(const char *kernel_class, const lqcd_lattice *lat, int *block);
+lqcd_status lqcd_autotune_clear(void);
+
 /* ------------------------------------------------------------ allocation-free plaquette */
 
 /* Largest lattice (sites) lqcd_plaquette_noalloc accepts. */

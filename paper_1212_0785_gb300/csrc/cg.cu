@@ -340,7 +340,8 @@ lqcd_status CgWorkspace::ensure(const lqcd_lattice &l, lqcd_prec sl, cudaStream_
         LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_ODD, sl, 0, &tmpos.f));
     }
     int Vh = make_geo(lat).Vh;
-    size_t np = (size_t)std::max(std::max(dslash_blocks(Vh), nblocks_for(Vh, BB)), 2048);
+    // one partial per hop block (down to the 64-thread blocks of a tuned hop) or per CG_BLOCK sites
+    size_t np = (size_t)std::max(std::max(nblocks_for(Vh, 64), nblocks_for(Vh, BB)), 2048);
     LQCD_TRY(sc.alloc(sizeof(CgScalars), s));
     LQCD_TRY(partials.alloc(np * sizeof(double), s));
     LQCD_TRY(scalars.alloc(16 * sizeof(double), s));

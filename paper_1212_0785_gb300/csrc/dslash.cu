@@ -17,6 +17,7 @@
 #include "dslash.cuh"
 #include "dslash_packed.cuh"
 #include "dslash_site.cuh"
+#include "tune.cuh"
 
 namespace lqcd {
 
@@ -26,39 +27,40 @@ namespace lqcd {
 // links into shared memory first; FORM 2 (FP16+norm): the same with packed
 // FP32x2 arithmetic.  FORM 0: every operand gathered by its thread.  (The
 // other precisions' FORM 1, 2 instances are never launched.)
-template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, int FORM>
+template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, int FORM, int BLOCK = DS_BLOCK>
 __device__ __forceinline__ Sp<R> site_value(const SpinorRef<SP> &in, const GaugeRef<GP> &U, const Geo &g, int cb,
                                             int out_par)
 {
     if constexpr (FORM == 1 && SP == LQCD_F16N && GP == LQCD_F16N)
         return prefetch_site<R, DAG>(in, U, g, cb, out_par);
     else if constexpr (FORM == 2 && SP == LQCD_F16N && GP == LQCD_F16N && std::is_same<R, float>::value)
-        return packed_site<DAG>(in, U, g, cb, out_par);
+        return packed_site<DAG, BLOCK>(in, U, g, cb, out_par);
     else
         return dslash_site<R, SP, GP, DAG>(in, U, g, cb, out_par);
 }
 
-template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, int FORM>
+// (BLOCK: threads per block of the launch; 128 except for the tuned packed kernels)
+template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, int FORM, int BLOCK = DS_BLOCK>
 __device__ __forceinline__ void plain_body(SpinorRef<SP> out, SpinorRef<SP> in, GaugeRef<GP> U,
                                                                  Geo g, int out_par, const int *skip)
 {
     if (skip && *skip) return;
-    int cb = blockIdx.x * DS_BLOCK + threadIdx.x;
+    int cb = blockIdx.x * BLOCK + threadIdx.x;
     if (cb >= g.Vh) return;
-    out.store(cb, site_value<R, SP, GP, DAG, FORM>(in, U, g, cb, out_par));
+    out.store(cb, site_value<R, SP, GP, DAG, FORM, BLOCK>(in, U, g, cb, out_par));
 }
 
-template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, int FORM>
+template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, int FORM, int BLOCK = DS_BLOCK>
 __device__ __forceinline__ void xpay_body(SpinorRef<SP> out, SpinorRef<SP> in, GaugeRef<GP> U,
                                                                 Geo g, int out_par, SpinorRef<SP> x, R b,
                                                                 double *partials, int nblocks, const int *skip,
                                                                 CgScalars *fin)
 {
     if (skip && *skip) return;
-    int cb = blockIdx.x * DS_BLOCK + threadIdx.x;
+    int cb = blockIdx.x * BLOCK + threadIdx.x;
     R n2 = R(0);
     if (cb < g.Vh) {
-        Sp<R> d = site_value<R, SP, GP, DAG, FORM>(in, U, g, cb, out_par);
+        Sp<R> d = site_value<R, SP, GP, DAG, FORM, BLOCK>(in, U, g, cb, out_par);
         Sp<R> xv = x.template load_rw<R>(cb);
 #pragma unroll
         for (int a = 0; a < 4; a++)
@@ -68,12 +70,12 @@ __device__ __forceinline__ void xpay_body(SpinorRef<SP> out, SpinorRef<SP> in, G
         n2 = sp_norm2(d);
     }
     if (partials) {
-        block_sum_store_wp<DS_BLOCK>(n2, partials);
-        if (fin) cg_finish<DS_BLOCK, false>(fin, partials, nblocks);
+        block_sum_store_wp<BLOCK>(n2, partials);
+        if (fin) cg_finish<BLOCK, false>(fin, partials, nblocks);
     }
 }
 
-template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, lqcd_prec XP, int FORM>
+template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, lqcd_prec XP, int FORM, int BLOCK = DS_BLOCK>
 __device__ __forceinline__ void cg_body(SpinorRef<SP> in, GaugeRef<GP> U, Geo g, int out_par,
                                                               SpinorRef<SP> t, R b, SpinorRef<XP> xs, SpinorRef<SP> r,
                                                               SpinorRef<SP> p, double *partials, int nblocks,
@@ -81,10 +83,10 @@ __device__ __forceinline__ void cg_body(SpinorRef<SP> in, GaugeRef<GP> U, Geo g,
 {
     if (sc->pause) return;
     const R alpha = (R)sc->alpha;
-    int cb = blockIdx.x * DS_BLOCK + threadIdx.x;
+    int cb = blockIdx.x * BLOCK + threadIdx.x;
     R n2 = R(0);
     if (cb < g.Vh) {
-        Sp<R> ap = site_value<R, SP, GP, DAG, FORM>(in, U, g, cb, out_par);
+        Sp<R> ap = site_value<R, SP, GP, DAG, FORM, BLOCK>(in, U, g, cb, out_par);
         {
             Sp<R> tv = t.template load_rw<R>(cb);
 #pragma unroll
@@ -113,8 +115,8 @@ __device__ __forceinline__ void cg_body(SpinorRef<SP> in, GaugeRef<GP> U, Geo g,
         r.store(cb, rv);
         n2 = sp_norm2(rv);
     }
-    block_sum_store_wp<DS_BLOCK>(n2, partials);
-    cg_finish<DS_BLOCK, true>(sc, partials, nblocks);
+    block_sum_store_wp<BLOCK>(n2, partials);
+    cg_finish<BLOCK, true>(sc, partials, nblocks);
 }
 
 // The kernels: gathered operands, and (FP16+norm) prefetched links with the
@@ -168,30 +170,33 @@ __global__ void __launch_bounds__(DS_BLOCK, 7) dslash_cg_prefetch_kernel(SpinorR
     cg_body<R, SP, GP, DAG, XP, 1>(in, U, g, out_par, t, b, xs, r, p, partials, nblocks, sc);
 }
 
-template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
-__global__ void __launch_bounds__(DS_BLOCK, 7) dslash_plain_packed_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
-                                                                           GaugeRef<GP> U, Geo g, int out_par,
-                                                                           const int *skip)
+// The packed form with BLOCK threads per block (64, 128 or 256, chosen per
+// lattice by the autotuner): the register budget of 7 blocks of 128 per SM
+// (72 registers), whatever the block size.
+template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 896 / BLOCK) dslash_plain_packed_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
+                                                                                  GaugeRef<GP> U, Geo g, int out_par,
+                                                                                  const int *skip)
 {
-    plain_body<R, SP, GP, DAG, 2>(out, in, U, g, out_par, skip);
+    plain_body<R, SP, GP, DAG, 2, BLOCK>(out, in, U, g, out_par, skip);
 }
-template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG>
-__global__ void __launch_bounds__(DS_BLOCK, 7) dslash_xpay_packed_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
-                                                                          GaugeRef<GP> U, Geo g, int out_par,
-                                                                          SpinorRef<SP> x, R b, double *partials,
-                                                                          int nblocks, const int *skip,
-                                                                          CgScalars *fin)
+template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 896 / BLOCK) dslash_xpay_packed_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
+                                                                                 GaugeRef<GP> U, Geo g, int out_par,
+                                                                                 SpinorRef<SP> x, R b, double *partials,
+                                                                                 int nblocks, const int *skip,
+                                                                                 CgScalars *fin)
 {
-    xpay_body<R, SP, GP, DAG, 2>(out, in, U, g, out_par, x, b, partials, nblocks, skip, fin);
+    xpay_body<R, SP, GP, DAG, 2, BLOCK>(out, in, U, g, out_par, x, b, partials, nblocks, skip, fin);
 }
-template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, lqcd_prec XP>
-__global__ void __launch_bounds__(DS_BLOCK, 7) dslash_cg_packed_kernel(SpinorRef<SP> in, GaugeRef<GP> U, Geo g,
-                                                                        int out_par, SpinorRef<SP> t, R b,
-                                                                        SpinorRef<XP> xs, SpinorRef<SP> r,
-                                                                        SpinorRef<SP> p, double *partials,
-                                                                        int nblocks, CgScalars *sc)
+template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, lqcd_prec XP, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 896 / BLOCK) dslash_cg_packed_kernel(SpinorRef<SP> in, GaugeRef<GP> U, Geo g,
+                                                                               int out_par, SpinorRef<SP> t, R b,
+                                                                               SpinorRef<XP> xs, SpinorRef<SP> r,
+                                                                               SpinorRef<SP> p, double *partials,
+                                                                               int nblocks, CgScalars *sc)
 {
-    cg_body<R, SP, GP, DAG, XP, 2>(in, U, g, out_par, t, b, xs, r, p, partials, nblocks, sc);
+    cg_body<R, SP, GP, DAG, XP, 2, BLOCK>(in, U, g, out_par, t, b, xs, r, p, partials, nblocks, sc);
 }
 
 // ---------------------------------------------------------------- dispatch
@@ -241,21 +246,52 @@ static int use_form(const Geo &)
     do {                                                                                                             \
         if (form == 1)                                                                                               \
             kern##_prefetch_kernel<LQCD_UNPAREN targs><<<grid, DS_BLOCK, 0, s>>> args;                               \
-        else if (form == 2)                                                                                          \
-            kern##_packed_kernel<LQCD_UNPAREN targs><<<grid, DS_BLOCK, 0, s>>> args;                                 \
         else                                                                                                         \
             kern##_kernel<LQCD_UNPAREN targs><<<grid, DS_BLOCK, 0, s>>> args;                                        \
     } while (0)
 #define LQCD_UNPAREN(...) __VA_ARGS__
 
+#define LQCD_UNPAREN_PK(...) __VA_ARGS__
+// launch the packed-form kernel K with bs threads per block (64, 128, 256)
+#define LQCD_LAUNCH_PACKED(bs, kern, targs, args)                                                                    \
+    do {                                                                                                             \
+        const int nbp_ = nblocks_for(g.Vh, bs);                                                                      \
+        if (bs == 64)                                                                                                \
+            kern##_packed_kernel<LQCD_UNPAREN_PK targs, 64><<<nbp_, 64, 0, s>>> args;                                \
+        else if (bs == 256)                                                                                          \
+            kern##_packed_kernel<LQCD_UNPAREN_PK targs, 256><<<nbp_, 256, 0, s>>> args;                              \
+        else                                                                                                         \
+            kern##_packed_kernel<LQCD_UNPAREN_PK targs, 128><<<nbp_, 128, 0, s>>> args;                              \
+    } while (0)
+
+// threads per block of the packed FP16+norm kernels on this lattice (the
+// autotuner's choice, else DS_BLOCK)
+static int packed_block(const lqcd_field *in)
+{
+    const int b = tuned_block(TK_HOP_F16N, in->lat, DS_BLOCK);
+    return (b == 64 || b == 128 || b == 256) ? b : DS_BLOCK;
+}
+
 template <lqcd_prec P, lqcd_prec GP = P>
 static void launch_plain(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int dagger, const int *skip,
-                         cudaStream_t s)
+                         cudaStream_t s, int bs = 0)
 {
     using R = typename ArithOf<P>::type;
     Geo g = make_geo(in->lat);
-    int nb = dslash_blocks(g.Vh);
     const int st = use_form<P, GP>(g);
+    if constexpr (P == LQCD_F16N && GP == LQCD_F16N) {
+        if (st == 2) {
+            if (bs == 0) bs = packed_block(in);
+            if (dagger)
+                LQCD_LAUNCH_PACKED(bs, dslash_plain, (R, P, GP, true),
+                                   (spinor_ref<P>(out), spinor_ref<P>(in), gauge_ref<GP>(U), g, out_parity(out), skip));
+            else
+                LQCD_LAUNCH_PACKED(bs, dslash_plain, (R, P, GP, false),
+                                   (spinor_ref<P>(out), spinor_ref<P>(in), gauge_ref<GP>(U), g, out_parity(out), skip));
+            return;
+        }
+    }
+    int nb = dslash_blocks(g.Vh);
     if (dagger)
         LQCD_LAUNCH_FORM(st, dslash_plain, (R, P, GP, true), nb,
                            (spinor_ref<P>(out), spinor_ref<P>(in), gauge_ref<GP>(U), g, out_parity(out), skip));
@@ -270,8 +306,22 @@ static void launch_xpay(lqcd_field *out, const lqcd_field *U, const lqcd_field *
 {
     using R = typename ArithOf<P>::type;
     Geo g = make_geo(in->lat);
-    int nb = dslash_blocks(g.Vh);
     const int st = use_form<P, GP>(g);
+    if constexpr (P == LQCD_F16N && GP == LQCD_F16N) {
+        if (st == 2) {
+            const int bs = packed_block(in), nb = nblocks_for(g.Vh, bs);
+            if (dagger)
+                LQCD_LAUNCH_PACKED(bs, dslash_xpay, (R, P, GP, true),
+                                   (spinor_ref<P>(out), spinor_ref<P>(in), gauge_ref<GP>(U), g, out_parity(out),
+                                    spinor_ref<P>(x), (R)b, partials, nb, skip, fin));
+            else
+                LQCD_LAUNCH_PACKED(bs, dslash_xpay, (R, P, GP, false),
+                                   (spinor_ref<P>(out), spinor_ref<P>(in), gauge_ref<GP>(U), g, out_parity(out),
+                                    spinor_ref<P>(x), (R)b, partials, nb, skip, fin));
+            return;
+        }
+    }
+    int nb = dslash_blocks(g.Vh);
     if (dagger)
         LQCD_LAUNCH_FORM(st, dslash_xpay, (R, P, GP, true), nb,
                            (spinor_ref<P>(out), spinor_ref<P>(in), gauge_ref<GP>(U), g, out_parity(out),
@@ -289,9 +339,23 @@ static void launch_cg(const lqcd_field *U, const lqcd_field *in, int dagger, con
 {
     using R = typename ArithOf<P>::type;
     Geo g = make_geo(in->lat);
-    int nb = dslash_blocks(g.Vh);
     int op = out_parity(t);
     const int st = use_form<P, P>(g);
+    if constexpr (P == LQCD_F16N) {
+        if (st == 2) {
+            const int bs = packed_block(in), nb = nblocks_for(g.Vh, bs);
+            if (dagger)
+                LQCD_LAUNCH_PACKED(bs, dslash_cg, (R, P, P, true, XP),
+                                   (spinor_ref<P>(in), gauge_ref<P>(U), g, op, spinor_ref<P>(t), (R)b,
+                                    spinor_ref<XP>(xs), spinor_ref<P>(r), spinor_ref<P>(p), partials, nb, sc));
+            else
+                LQCD_LAUNCH_PACKED(bs, dslash_cg, (R, P, P, false, XP),
+                                   (spinor_ref<P>(in), gauge_ref<P>(U), g, op, spinor_ref<P>(t), (R)b,
+                                    spinor_ref<XP>(xs), spinor_ref<P>(r), spinor_ref<P>(p), partials, nb, sc));
+            return;
+        }
+    }
+    int nb = dslash_blocks(g.Vh);
     if (dagger)
         LQCD_LAUNCH_FORM(st, dslash_cg, (R, P, P, true, XP), nb,
                            (spinor_ref<P>(in), gauge_ref<P>(U), g, op, spinor_ref<P>(t), (R)b, spinor_ref<XP>(xs),
@@ -300,6 +364,20 @@ static void launch_cg(const lqcd_field *U, const lqcd_field *in, int dagger, con
         LQCD_LAUNCH_FORM(st, dslash_cg, (R, P, P, false, XP), nb,
                            (spinor_ref<P>(in), gauge_ref<P>(U), g, op, spinor_ref<P>(t), (R)b, spinor_ref<XP>(xs),
                             spinor_ref<P>(r), spinor_ref<P>(p), partials, nb, sc));
+}
+
+// the packed plain hop with bs threads per block, for the autotuner
+lqcd_status dslash_packed_plain_block(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int bs,
+                                      cudaStream_t s)
+{
+    LQCD_TRY(check_pair(out, U, in));
+    LQCD_REQUIRE(in->prec == LQCD_F16N && U->prec == LQCD_F16N, "packed hop: FP16+norm fields only");
+    LQCD_REQUIRE(bs == 64 || bs == 128 || bs == 256, "packed hop: block size %d not compiled", bs);
+    const int prev = g_form.exchange(2);
+    launch_plain<LQCD_F16N>(out, U, in, 0, nullptr, s, bs);
+    g_form.store(prev);
+    LQCD_LAUNCHED();
+    return LQCD_OK;
 }
 
 int dslash_form_set(int form)

@@ -150,11 +150,11 @@ __device__ __forceinline__ void hop_packed(SpP &acc, const SpF &psi, float sc, c
     accumulate_p<MU, S>(acc, mul_link_p<FWD>(u, project_p<MU, S>(psi)), flip ? -sc : sc);
 }
 
-template <bool DAG>
+template <bool DAG, int BLOCK = DS_BLOCK>
 __device__ __forceinline__ Sp<float> packed_site(const SpinorRef<LQCD_F16N> &in, const GaugeRef<LQCD_F16N> &U,
                                                  const Geo &g, int cb, int out_par)
 {
-    __shared__ LinkPrefetch lp;
+    __shared__ LinkPrefetchT<BLOCK> lp;
     const int i = threadIdx.x;
     int c[4], nb[8];
     bool tf, tb;

@@ -120,9 +120,11 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-struct LinkPrefetch {
-    uint2 u[4][2][3][DS_BLOCK]; // [mu][forward, backward][chunk][thread]: 24 KiB
+template <int BLOCK>
+struct LinkPrefetchT {
+    uint2 u[4][2][3][BLOCK]; // [mu][forward, backward][chunk][thread]: 192 bytes per thread
 };
+using LinkPrefetch = LinkPrefetchT<DS_BLOCK>;
 
 template <typename R, bool DAG>
 __device__ __forceinline__ Sp<R> prefetch_site(const SpinorRef<LQCD_F16N> &in, const GaugeRef<LQCD_F16N> &U,

@@ -9,6 +9,7 @@
 
 #include "df64.cuh"
 #include "lqcd_internal.cuh"
+#include "tune.cuh"
 #include "su3_device.cuh"
 
 namespace lqcd {
@@ -940,24 +941,25 @@ lqcd_status reunitarize_dev(lqcd_field *U, double *dst_dev, DevBuf &part, cudaSt
 
 template <bool FAST>
 static lqcd_status launch_link_update(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *Us, lqcd_field *Uf,
-                                      lqcd_field *Udf, cudaStream_t s)
+                                      lqcd_field *Udf, cudaStream_t s, int bs = 128)
 {
+    LQCD_REQUIRE(bs >= 32 && bs <= 256 && bs % 32 == 0, "link update: bad block size %d", bs);
     GaugeRef<PREC_DF> ud = Udf ? gauge_ref<PREC_DF>(Udf) : GaugeRef<PREC_DF>{nullptr, U->Vh};
     long n = 8L * U->Vh;
-    int nb = nblocks_for(n, 128);
+    int nb = nblocks_for(n, bs);
     GaugeRef<LQCD_F32> uf = Uf ? gauge_ref<LQCD_F32>(Uf) : GaugeRef<LQCD_F32>{nullptr, U->Vh};
     int wf = Uf ? 1 : 0;
     switch (Us ? Us->prec : LQCD_F32) {
     case LQCD_F32:
-        link_update_kernel<LQCD_F32, FAST><<<nb, 128, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c,
+        link_update_kernel<LQCD_F32, FAST><<<nb, bs, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c,
                                                               Us ? gauge_ref<LQCD_F32>(Us) : uf, uf, ud, U->Vh, Us ? 1 : 0, wf);
         break;
     case LQCD_F16N:
-        link_update_kernel<LQCD_F16N, FAST><<<nb, 128, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c,
+        link_update_kernel<LQCD_F16N, FAST><<<nb, bs, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c,
                                                                gauge_ref<LQCD_F16N>(Us), uf, ud, U->Vh, 1, wf);
         break;
     case LQCD_BF16:
-        link_update_kernel<LQCD_BF16, FAST><<<nb, 128, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c,
+        link_update_kernel<LQCD_BF16, FAST><<<nb, bs, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c,
                                                                gauge_ref<LQCD_BF16>(Us), uf, ud, U->Vh, 1, wf);
         break;
     default: set_error("sloppy link copy must be 12-real F32/F16N/BF16"); return LQCD_EINVAL;
@@ -970,7 +972,15 @@ lqcd_status link_update_dev(lqcd_field *U, const lqcd_field *P, double c, lqcd_f
                             cudaStream_t s, lqcd_field *Udf)
 {
     KernelTimer kt(K_LINK_UPDATE, s);
-    return fast ? launch_link_update<true>(U, P, c, Us, Uf, Udf, s) : launch_link_update<false>(U, P, c, Us, Uf, Udf, s);
+    return fast ? launch_link_update<true>(U, P, c, Us, Uf, Udf, s, tuned_block(TK_LINK_UPDATE_F32, U->lat, 128))
+                : launch_link_update<false>(U, P, c, Us, Uf, Udf, s);
+}
+
+// the FP32 molecular dynamics' link update with bs threads per block
+lqcd_status link_update_block(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *Us, lqcd_field *Uf,
+                              lqcd_field *Udf, int bs, cudaStream_t s)
+{
+    return launch_link_update<true>(U, P, c, Us, Uf, Udf, s, bs);
 }
 
 lqcd_status momentum_refresh_dev(lqcd_field *P, uint32_t seed, uint32_t chain, uint32_t traj, cudaStream_t s)

@@ -14,16 +14,20 @@
 #include "dslash.cuh"
 #include "spin.cuh"
 #include "su3_device.cuh"
+#include "tune.cuh"
 
 namespace lqcd {
 
+// default threads per block of the force kernels (the autotuner's table
+// overrides it per lattice); FB_MAX bounds the launches
 constexpr int FB = 128;
+constexpr int FB_MAX = 256;
 
 // Link of a thread, direction-major (gauge force: the staples of one
 // direction over all sites reuse best this way, measured).
 __device__ __forceinline__ bool link_of_thread_seq(int Vh, int &mu, int &par, int &cb)
 {
-    const long t = blockIdx.x * (long)FB + threadIdx.x;
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (t >= 8L * Vh) return false;
     cb = (int)(t % Vh);
     const int mp = (int)(t / Vh);
@@ -37,16 +41,16 @@ __device__ __forceinline__ bool link_of_thread_seq(int Vh, int &mu, int &par, in
 // together, so the spinors that all four directions read are reused from L2
 // instead of being fetched again by a later sweep over the next direction
 // (measured: 37 -> 28 ms per 32^3x64 trajectory).  Every warp has one
-// direction.  Grid: 8 * force_blocks(Vh) blocks of FB threads.
-__host__ __device__ __forceinline__ int force_blocks(int Vh) { return (Vh + FB - 1) / FB; }
+// direction.  Grid: 8 * force_blocks(Vh, bs) blocks of bs threads.
+__host__ __device__ __forceinline__ int force_blocks(int Vh, int bs) { return (Vh + bs - 1) / bs; }
 
 __device__ __forceinline__ bool link_of_thread(int Vh, int &mu, int &par, int &cb)
 {
-    const int b = blockIdx.x;
+    const int b = blockIdx.x, bs = blockDim.x;
     mu = b & 3;
-    const int q = b >> 2, nbp = force_blocks(Vh);
+    const int q = b >> 2, nbp = force_blocks(Vh, bs);
     par = q / nbp;
-    cb = (q - par * nbp) * FB + threadIdx.x;
+    cb = (q - par * nbp) * bs + threadIdx.x;
     return cb < Vh;
 }
 
@@ -121,7 +125,7 @@ __device__ __forceinline__ void gauge_force_link(MomRef &P, const GaugeRef<GP> &
 }
 
 template <typename R, lqcd_prec GP>
-__global__ void __launch_bounds__(FB) gauge_force_kernel(MomRef P, GaugeRef<GP> U, Geo g, double cf)
+__global__ void __launch_bounds__(FB_MAX) gauge_force_kernel(MomRef P, GaugeRef<GP> U, Geo g, double cf)
 {
     int mu, par, cb;
     if (!link_of_thread_seq(g.Vh, mu, par, cb)) return;
@@ -140,8 +144,10 @@ __global__ void __launch_bounds__(FB) gauge_force_kernel(MomRef P, GaugeRef<GP> 
 // second) into shared memory, so their DRAM latencies overlap instead of
 // following one another; A(x) is loaded as before.  The arithmetic is
 // unchanged.  Slots: [0, 6) B(x), [6, 12) B(x+mu), [12, 15) U_mu(x),
-// [15, 21) A(x+mu), each [slot][thread].
+// [15, 21) A(x+mu), each [slot][thread] in dynamic shared memory (336 bytes
+// per thread, so at most FF_MAX threads per block).
 constexpr int FF_SLOTS = 21;
+constexpr int FF_MAX = 128;
 
 __device__ __forceinline__ void ff_cp16(float4 *dst, const float4 *src)
 {
@@ -172,7 +178,7 @@ template <int MU, typename R, lqcd_prec SP, lqcd_prec GP>
 __device__ __forceinline__ void fermion_force_link(MomRef &P, const GaugeRef<GP> &U, const Geo &g, int par,
                                                    int cb, const int c[4], const SpinorRef<SP> (&A)[2],
                                                    const SpinorRef<SP> (&B)[2], double cf,
-                                                   float4 (*pf)[FB] = nullptr)
+                                                   float4 *pf = nullptr)
 {
     int cy[4] = {c[0], c[1], c[2], c[3]};
     bool wrap = (c[MU] + 1 == g.L[MU]);
@@ -182,34 +188,35 @@ __device__ __forceinline__ void fermion_force_link(MomRef &P, const GaugeRef<GP>
     M3<R> u;
     Sp<R> Ay, Ax, Bx, By;
     if constexpr (SP == LQCD_F32 && GP == LQCD_F32) {
-        const int i = threadIdx.x;
+        const int i = threadIdx.x, nt = blockDim.x;
         const size_t Vh = (size_t)g.Vh;
+        auto slot = [&](int k) -> float4 & { return pf[k * nt + i]; };
 #pragma unroll
         for (int k = 0; k < 6; k++) {
-            ff_cp16(&pf[k][i], B[par].d + k * Vh + cb);
-            ff_cp16(&pf[6 + k][i], B[1 - par].d + k * Vh + cby);
+            ff_cp16(&slot(k), B[par].d + k * Vh + cb);
+            ff_cp16(&slot(6 + k), B[1 - par].d + k * Vh + cby);
         }
 #pragma unroll
-        for (int k = 0; k < 3; k++) ff_cp16(&pf[12 + k][i], U.d + U.idx(MU, par, k, cb));
+        for (int k = 0; k < 3; k++) ff_cp16(&slot(12 + k), U.d + U.idx(MU, par, k, cb));
         asm volatile("cp.async.commit_group;" ::: "memory");
 #pragma unroll
-        for (int k = 0; k < 6; k++) ff_cp16(&pf[15 + k][i], A[1 - par].d + k * Vh + cby);
+        for (int k = 0; k < 6; k++) ff_cp16(&slot(15 + k), A[1 - par].d + k * Vh + cby);
         asm volatile("cp.async.commit_group;" ::: "memory");
         Ax = A[par].template load_rw<R>(cb);
         asm volatile("cp.async.wait_group 1;" ::: "memory");
         {
             float4 v[6], w[6];
 #pragma unroll
-            for (int k = 0; k < 6; k++) v[k] = pf[k][i], w[k] = pf[6 + k][i];
+            for (int k = 0; k < 6; k++) v[k] = slot(k), w[k] = slot(6 + k);
             Bx = B[par].template unpack<R>(v);
             By = B[1 - par].template unpack<R>(w);
         }
-        u = ff_link<R>(pf[12][i], pf[13][i], pf[14][i]);
+        u = ff_link<R>(slot(12), slot(13), slot(14));
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         {
             float4 v[6];
 #pragma unroll
-            for (int k = 0; k < 6; k++) v[k] = pf[15 + k][i];
+            for (int k = 0; k < 6; k++) v[k] = slot(15 + k);
             Ay = A[1 - par].template unpack<R>(v);
         }
     } else {
@@ -252,7 +259,7 @@ __device__ __forceinline__ void fermion_force_link(MomRef &P, const GaugeRef<GP>
 }
 
 template <typename R, lqcd_prec SP, lqcd_prec GP>
-__global__ void __launch_bounds__(FB) fermion_force_kernel(MomRef P, GaugeRef<GP> U, Geo g, SpinorRef<SP> Ae,
+__global__ void __launch_bounds__(FF_MAX) fermion_force_kernel(MomRef P, GaugeRef<GP> U, Geo g, SpinorRef<SP> Ae,
                                                            SpinorRef<SP> Ao, SpinorRef<SP> Be, SpinorRef<SP> Bo,
                                                            double cf)
 {
@@ -262,7 +269,7 @@ __global__ void __launch_bounds__(FB) fermion_force_kernel(MomRef P, GaugeRef<GP
     cb_coords(g, cb, par, c);
     const SpinorRef<SP> A[2] = {Ae, Ao};
     const SpinorRef<SP> B[2] = {Be, Bo};
-    __shared__ float4 pf[SP == LQCD_F32 && GP == LQCD_F32 ? FF_SLOTS : 1][FB];
+    extern __shared__ float4 pf[]; // FF_SLOTS x blockDim.x (FP32), none otherwise
     switch (mu) {
     case 0: fermion_force_link<0, R, SP, GP>(P, U, g, par, cb, c, A, B, cf, pf); break;
     case 1: fermion_force_link<1, R, SP, GP>(P, U, g, par, cb, c, A, B, cf, pf); break;
@@ -271,19 +278,50 @@ __global__ void __launch_bounds__(FB) fermion_force_kernel(MomRef P, GaugeRef<GP
     }
 }
 
-// Uf: the FP32 12-real link copy, used (and required) when arith is F32
+// P -= cf f of the gauge force with bs threads per block; Uf: the FP32
+// 12-real link copy, used (and required) when arith is F32
+lqcd_status gauge_force_block(lqcd_field *P, const lqcd_field *U, const lqcd_field *Uf, double cf, lqcd_prec arith,
+                              int bs, cudaStream_t s)
+{
+    LQCD_REQUIRE(bs >= 32 && bs <= FB_MAX && bs % 32 == 0, "gauge force: bad block size %d", bs);
+    Geo g = make_geo(U->lat);
+    int nb = nblocks_for(8L * g.Vh, bs);
+    if (arith == LQCD_F32)
+        gauge_force_kernel<float, LQCD_F32><<<nb, bs, 0, s>>>(mom_ref(P), gauge_ref<LQCD_F32>(Uf), g, cf);
+    else
+        gauge_force_kernel<double, LQCD_F64><<<nb, bs, 0, s>>>(mom_ref(P), gauge_ref<LQCD_F64>(U), g, cf);
+    LQCD_LAUNCHED();
+    return LQCD_OK;
+}
+
 lqcd_status gauge_force_dev(lqcd_field *P, const lqcd_field *U, const lqcd_field *Uf, double beta, double coeff,
                             lqcd_prec arith, cudaStream_t s)
 {
-    Geo g = make_geo(U->lat);
     KernelTimer kt(K_GAUGE_FORCE, s);
-    int nb = nblocks_for(8L * g.Vh, FB);
-    if (arith == LQCD_F32)
-        gauge_force_kernel<float, LQCD_F32><<<nb, FB, 0, s>>>(mom_ref(P), gauge_ref<LQCD_F32>(Uf), g, coeff * beta / 6.0);
-    else
-        gauge_force_kernel<double, LQCD_F64><<<nb, FB, 0, s>>>(mom_ref(P), gauge_ref<LQCD_F64>(U), g, coeff * beta / 6.0);
+    const int bs = tuned_block(arith == LQCD_F32 ? TK_GAUGE_FORCE_F32 : TK_GAUGE_FORCE_F64, U->lat, FB);
+    return gauge_force_block(P, U, Uf, coeff * beta / 6.0, arith, bs, s);
+}
+
+// the fermion-force link kernel with bs threads per block (A = (Xe, Ao), B = (Ye, Bo))
+template <typename R, lqcd_prec SP>
+static lqcd_status fermion_link_launch(lqcd_field *P, const lqcd_field *L, const lqcd_field *Xe, const lqcd_field *Ao,
+                                       const lqcd_field *Ye, const lqcd_field *Bo, double cf, int bs, cudaStream_t s)
+{
+    LQCD_REQUIRE(bs >= 32 && bs <= FF_MAX && bs % 32 == 0, "fermion force: bad block size %d", bs);
+    Geo g = make_geo(L->lat);
+    const int nb = 8 * force_blocks(g.Vh, bs);
+    const size_t smem = SP == LQCD_F32 ? (size_t)FF_SLOTS * bs * sizeof(float4) : 0;
+    fermion_force_kernel<R, SP, SP><<<nb, bs, smem, s>>>(mom_ref(P), gauge_ref<SP>(L), g, spinor_ref<SP>(Xe),
+                                                          spinor_ref<SP>(Ao), spinor_ref<SP>(Ye), spinor_ref<SP>(Bo),
+                                                          cf);
     LQCD_LAUNCHED();
     return LQCD_OK;
+}
+
+lqcd_status fermion_force_link_block(lqcd_field *P, const lqcd_field *Uf, const lqcd_field *Xe, const lqcd_field *Ao,
+                                     const lqcd_field *Ye, const lqcd_field *Bo, double cf, int bs, cudaStream_t s)
+{
+    return fermion_link_launch<float, LQCD_F32>(P, Uf, Xe, Ao, Ye, Bo, cf, bs, s);
 }
 
 // A_o = Doe X_e, Y_e = Mhat X_e = X_e - kappa^2 Deo A_o, B_o = Doe^dag-hop Y_e, then the link kernel:
@@ -312,20 +350,12 @@ lqcd_status fermion_force_dev(lqcd_field *P, const lqcd_field *U, const lqcd_fie
         LQCD_TRY(dslash_xpay(Ye, L, Ao, 0, Xa, -kappa * kappa, nullptr, nullptr, s));
     }
     LQCD_TRY(dslash_plain(Bo, L, Ya, 1, nullptr, s));
-    Geo g = make_geo(U->lat);
     KernelTimer kt(K_FERMION_FORCE, s);
-    int nb = 8 * force_blocks(g.Vh);
-    double cf = coeff * kappa * kappa;
+    const double cf = coeff * kappa * kappa;
     if (Ao->prec == LQCD_F32)
-        fermion_force_kernel<float, LQCD_F32, LQCD_F32><<<nb, FB, 0, s>>>(
-            mom_ref(P), gauge_ref<LQCD_F32>(Uf), g, spinor_ref<LQCD_F32>(Xa), spinor_ref<LQCD_F32>(Ao),
-            spinor_ref<LQCD_F32>(Ya), spinor_ref<LQCD_F32>(Bo), cf);
-    else
-        fermion_force_kernel<double, LQCD_F64, LQCD_F64><<<nb, FB, 0, s>>>(
-            mom_ref(P), gauge_ref<LQCD_F64>(U), g, spinor_ref<LQCD_F64>(Xa), spinor_ref<LQCD_F64>(Ao),
-            spinor_ref<LQCD_F64>(Ya), spinor_ref<LQCD_F64>(Bo), cf);
-    LQCD_LAUNCHED();
-    return LQCD_OK;
+        return fermion_link_launch<float, LQCD_F32>(P, Uf, Xa, Ao, Ya, Bo, cf,
+                                                    tuned_block(TK_FERMION_FORCE_F32, U->lat, FB), s);
+    return fermion_link_launch<double, LQCD_F64>(P, U, Xa, Ao, Ya, Bo, cf, FB, s);
 }
 
 } // namespace lqcd

@@ -124,6 +124,10 @@ _SIGS = {
     "lqcd_eta_refresh": (_i, [_vp, _u32, _u32, _u32, _vp]),
     "lqcd_dslash": (_i, [_vp, _vp, _vp, _i, _vp]),
     "lqcd_dslash_form": (_i, [_i]),
+    "lqcd_autotune": (_i, [ctypes.POINTER(Lattice), ctypes.c_char_p, _vp]),
+    "lqcd_autotune_load": (_i, [ctypes.c_char_p]),
+    "lqcd_autotune_block": (_i, [ctypes.c_char_p, ctypes.POINTER(Lattice), ctypes.POINTER(ctypes.c_int)]),
+    "lqcd_autotune_clear": (_i, []),
     "lqcd_mhat": (_i, [_vp, _vp, _vp, _d, _i, _vp]),
     "lqcd_cg_solve": (_i, [_vp, _vp, _vp, _vp, _d, ctypes.POINTER(CgParams), ctypes.POINTER(CgInfo), _vp]),
     "lqcd_gauge_force": (_i, [_vp, _vp, _d, _d, _vp]),
@@ -570,6 +574,47 @@ class HmcState:
 
 
 # ---------------------------------------------------------------- batches
+
+TUNED_CLASSES = ("dslash_f16n", "gauge_force_f32", "gauge_force_f64", "fermion_force_f32", "link_update_f32")
+
+
+def autotune(dims, path=None, t_bc=-1, stream=None) -> dict:
+    """Times every candidate block size of the tunable kernel classes on a
+    lattice (paper Sec. 4), keeps the fastest for later launches on it, writes
+    the timings to path (if given); returns {class: block}."""
+    lat = lattice(dims, t_bc)
+    _check(lib().lqcd_autotune(ctypes.byref(lat), None if path is None else str(path).encode(), _s(stream)),
+           "autotune")
+    return {k: autotune_block(k, dims, t_bc) for k in TUNED_CLASSES}
+
+
+def autotune_load(path):
+    _check(lib().lqcd_autotune_load(str(path).encode()), "autotune_load")
+
+
+def autotune_block(kernel_class, dims, t_bc=-1) -> int:
+    """the tuned block size of a class on a lattice (0: not tuned)"""
+    lat = lattice(dims, t_bc)
+    b = ctypes.c_int()
+    _check(lib().lqcd_autotune_block(kernel_class.encode(), ctypes.byref(lat), ctypes.byref(b)), "autotune_block")
+    return b.value
+
+
+def autotune_clear():
+    _check(lib().lqcd_autotune_clear(), "autotune_clear")
+
+
+def read_tune_table(path) -> list[dict]:
+    """the rows of an autotune file"""
+    rows = []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, lx, ly, lz, lt, block, ms, best = line.split()
+        rows.append({"class": k, "dims": (int(lx), int(ly), int(lz), int(lt)), "block": int(block),
+                     "ms": float(ms), "best": best == "1"})
+    return rows
+
 
 def write_log_line(log, record: dict):
     """Appends record as one JSON line to log (a path or a text file)."""

@@ -98,3 +98,30 @@ def test_info_structs_carry_the_solver_counters():
     assert names[4:] == ["accurate_residuals", "failed_checks", "guess_refined"]
     tnames = [f for f, _ in lqcd.TrajInfo._fields_]
     assert tnames[-4:] == ["traj", "cg_accurate_residuals", "cg_failed_checks", "cg_guesses_refined"]
+
+
+def test_autotune_table_is_host_state(tmp_path):
+    """the threads-per-block table: a saved file loads into the process-wide
+    table (one best row per class and lattice; block sizes this build cannot
+    launch are ignored), lookups return it, clear empties it -- no device"""
+    f = tmp_path / "tune.txt"
+    f.write_text("# kernel Lx Ly Lz Lt block ms_per_launch best\n"
+                 "gauge_force_f32 8 8 8 8 64 0.10 0\n"
+                 "gauge_force_f32 8 8 8 8 96 0.08 1\n"
+                 "dslash_f16n 8 8 8 8 256 0.02 1\n"
+                 "link_update_f32 8 8 8 8 100 0.01 1\n"
+                 "no_such_kernel 8 8 8 8 64 0.01 1\n")
+    lqcd.autotune_clear()
+    try:
+        lqcd.autotune_load(f)
+        assert lqcd.autotune_block("gauge_force_f32", (8, 8, 8, 8)) == 96
+        assert lqcd.autotune_block("dslash_f16n", (8, 8, 8, 8)) == 256
+        assert lqcd.autotune_block("link_update_f32", (8, 8, 8, 8)) == 0  # 100 is not a candidate
+        assert lqcd.autotune_block("gauge_force_f32", (4, 4, 4, 4)) == 0
+        rows = lqcd.read_tune_table(f)
+        assert len(rows) == 5 and rows[1]["best"] and rows[1]["block"] == 96
+        with pytest.raises(lqcd.LqcdError):
+            lqcd.autotune_block("no_such_kernel", (8, 8, 8, 8))
+    finally:
+        lqcd.autotune_clear()
+    assert lqcd.autotune_block("gauge_force_f32", (8, 8, 8, 8)) == 0
