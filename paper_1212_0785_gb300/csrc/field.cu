@@ -9,6 +9,7 @@
 
 #include "df64.cuh"
 #include "lqcd_internal.cuh"
+#include "md_device.cuh"
 #include "tune.cuh"
 #include "su3_device.cuh"
 
@@ -582,63 +583,7 @@ __global__ void eta_refresh_kernel(SpinorRef<LQCD_F64> E, Geo g, uint32_t seed, 
 
 // ------------------------------------------------------------------ link update / reunitarize
 
-// 1/sqrt(n) in float-float for n > 0: the FP32 estimate y refined by one
-// Newton-Raphson step of the reciprocal square root, y + y (1 - n y^2) / 2
-// (relative error ~ (3/8) e^2 for an estimate of relative error e)
-__device__ __forceinline__ Df df_rsqrt(Df n)
-{
-    const float y = rsqrtf(n.hi);
-    const Df yy = Df(y, 0.f) * Df(y, 0.f);
-    const Df r = Df(1) - n * yy;
-    return Df(y, 0.f) + Df(y, 0.f) * Df(0.5f * r.hi, 0.5f * r.lo);
-}
-
-// Gram-Schmidt of rows 0 and 1 of an FP32 matrix in float-float arithmetic,
-// row 2 = conj(row0 x row1): special unitary to ~2^-46
-__device__ __forceinline__ M3<Df> reunit_rows_df(const M3<float> &e)
-{
-    M3<Df> u;
-    DfAcc n0;
-#pragma unroll
-    for (int b = 0; b < 3; b++) {
-        n0.add_prod(Df(e.e[0][b].re, 0.f), Df(e.e[0][b].re, 0.f));
-        n0.add_prod(Df(e.e[0][b].im, 0.f), Df(e.e[0][b].im, 0.f));
-    }
-    const Df s0 = df_rsqrt(n0.value());
-#pragma unroll
-    for (int b = 0; b < 3; b++) u.e[0][b] = Cx<Df>{s0 * Df(e.e[0][b].re, 0.f), s0 * Df(e.e[0][b].im, 0.f)};
-    DfAcc ore, oim; // <row0, row1>
-#pragma unroll
-    for (int b = 0; b < 3; b++) {
-        const Df r1(e.e[1][b].re, 0.f), i1(e.e[1][b].im, 0.f);
-        ore.add_prod(u.e[0][b].re, r1);
-        ore.add_prod(u.e[0][b].im, i1);
-        oim.add_prod(u.e[0][b].re, i1);
-        oim.sub_prod(u.e[0][b].im, r1);
-    }
-    const Cx<Df> ov{ore.value(), oim.value()};
-    DfAcc n1;
-#pragma unroll
-    for (int b = 0; b < 3; b++) {
-        u.e[1][b] = Cx<Df>{Df(e.e[1][b].re, 0.f), Df(e.e[1][b].im, 0.f)} - ov * u.e[0][b];
-        n1.add_prod(u.e[1][b].re, u.e[1][b].re);
-        n1.add_prod(u.e[1][b].im, u.e[1][b].im);
-    }
-    const Df s1 = df_rsqrt(n1.value());
-#pragma unroll
-    for (int b = 0; b < 3; b++) u.e[1][b] = Cx<Df>{s1 * u.e[1][b].re, s1 * u.e[1][b].im};
-    reconstruct_row2(u);
-    return u;
-}
-
-// U <- exp(i c P) U.  FAST (the mixed-precision trajectory): the exponential
-// by Cayley-Hamilton in FP32, re-unitarized and multiplied onto the links in
-// float-float arithmetic (~48 bits, on the FP32 pipes), so that the FP64 links
-// stay in SU(3) to ~1e-14 per update; otherwise everything in FP64.  The new
-// links are also written to the 12-real copies Us (solver precision) and Uf
-// (FP32) and to the float-float copy Udf (the solver's accurate residual) when
-// those are given; a given Udf is also the FAST product's input (it holds the
-// current links), which spares the FP64 split of U.
+// U <- exp(i c P) U on every link (link_update_one), one thread per link
 template <lqcd_prec PS, bool FAST>
 __global__ void link_update_kernel(GaugeRef<LQCD_F64> U, MomRef P, double c, GaugeRef<PS> Us, GaugeRef<LQCD_F32> Uf,
                                    GaugeRef<PREC_DF> Udf, int Vh, int write_sloppy, int write_f32)
@@ -647,58 +592,7 @@ __global__ void link_update_kernel(GaugeRef<LQCD_F64> U, MomRef P, double c, Gau
     if (t >= 8L * Vh) return;
     int cb = (int)(t % Vh);
     int mp = (int)(t / Vh);
-    int mu = mp >> 1, par = mp & 1;
-    M3<double> nu;
-    M3<float> nf; // rows 0, 1 of the new link rounded once, for the 12-real copies
-    if (FAST) {
-        float p[8];
-        for (int a = 0; a < 8; a++) p[a] = (float)P.d[P.idx(mu, par, a, cb)];
-        const M3<Df> E = reunit_rows_df(expi_cayley_hamilton(herm_from_coeffs(p, (float)c)));
-        M3<Df> u;
-        if (Udf.d) { // the float-float copy is current: no FP64 split
-#pragma unroll
-            for (int k = 0; k < 9; k++) {
-                float4 v = Udf.d[Udf.idx(mu, par, k, cb)];
-                u.e[k / 3][k % 3] = Cx<Df>{Df(v.x, v.y), Df(v.z, v.w)};
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 9; k++) {
-                double2 v = ldg(U.d + U.idx(mu, par, k, cb));
-                u.e[k / 3][k % 3] = Cx<Df>{Df(v.x), Df(v.y)};
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) {
-                DfAcc re, im;
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    re.add_prod(E.e[i][k].re, u.e[k][j].re);
-                    re.sub_prod(E.e[i][k].im, u.e[k][j].im);
-                    im.add_prod(E.e[i][k].re, u.e[k][j].im);
-                    im.add_prod(E.e[i][k].im, u.e[k][j].re);
-                }
-                const Df vr = re.value(), vi = im.value();
-                nu.e[i][j] = cx<double>((double)vr, (double)vi);
-                if (i < 2) nf.e[i][j] = cx<float>(vr.hi + vr.lo, vi.hi + vi.lo);
-                if (Udf.d) Udf.d[Udf.idx(mu, par, i * 3 + j, cb)] = make_float4(vr.hi, vr.lo, vi.hi, vi.lo);
-            }
-    } else {
-        double p[8];
-        for (int a = 0; a < 8; a++) p[a] = P.d[P.idx(mu, par, a, cb)];
-        M3<double> E = expi_cayley_hamilton(herm_from_coeffs(p, c));
-        nu = m3_mul(E, U.load<double>(mu, par, cb));
-        if (Udf.d) Udf.store(mu, par, cb, nu);
-        for (int i = 0; i < 2; i++)
-            for (int j = 0; j < 3; j++) nf.e[i][j] = cx<float>((float)nu.e[i][j].re, (float)nu.e[i][j].im);
-    }
-    U.store(mu, par, cb, nu);
-    if (write_sloppy || write_f32) {
-        if (write_sloppy) Us.store(mu, par, cb, nf);
-        if (write_f32) Uf.store(mu, par, cb, nf);
-    }
+    link_update_one<PS, FAST>(U, P, c, Us, Uf, Udf, mp >> 1, mp & 1, cb, write_sloppy, write_f32);
 }
 
 __global__ void reunitarize_kernel(GaugeRef<LQCD_F64> U, int Vh, double *partials)

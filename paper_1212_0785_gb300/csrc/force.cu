@@ -11,118 +11,10 @@
 // = Re(2 i c Im Tr(lambda_a W)), so
 //   gauge   F = -(i beta/12) TA(U A):  f_a = (beta / 6) Im Tr(lambda_a U A)
 //   fermion F = (i kappa^2/2) TA(Q):   f_a = -kappa^2 Im Tr(lambda_a Q).
-#include "dslash.cuh"
-#include "spin.cuh"
-#include "su3_device.cuh"
+#include "force.cuh"
 #include "tune.cuh"
 
 namespace lqcd {
-
-// default threads per block of the force kernels (the autotuner's table
-// overrides it per lattice); FB_MAX bounds the launches
-constexpr int FB = 128;
-constexpr int FB_MAX = 256;
-
-// Link of a thread, direction-major (gauge force: the staples of one
-// direction over all sites reuse best this way, measured).
-__device__ __forceinline__ bool link_of_thread_seq(int Vh, int &mu, int &par, int &cb)
-{
-    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (t >= 8L * Vh) return false;
-    cb = (int)(t % Vh);
-    const int mp = (int)(t / Vh);
-    mu = mp >> 1;
-    par = mp & 1;
-    return true;
-}
-
-// Link of a thread, directions interleaved (fermion force).  The four
-// directions of one range of sites go to four consecutive blocks, which run
-// together, so the spinors that all four directions read are reused from L2
-// instead of being fetched again by a later sweep over the next direction
-// (measured: 37 -> 28 ms per 32^3x64 trajectory).  Every warp has one
-// direction.  Grid: 8 * force_blocks(Vh, bs) blocks of bs threads.
-__host__ __device__ __forceinline__ int force_blocks(int Vh, int bs) { return (Vh + bs - 1) / bs; }
-
-__device__ __forceinline__ bool link_of_thread(int Vh, int &mu, int &par, int &cb)
-{
-    const int b = blockIdx.x, bs = blockDim.x;
-    mu = b & 3;
-    const int q = b >> 2, nbp = force_blocks(Vh, bs);
-    par = q / nbp;
-    cb = (q - par * nbp) * bs + threadIdx.x;
-    return cb < Vh;
-}
-
-__device__ __forceinline__ int step_cb(const Geo &g, const int c[4], int dir, int s)
-{
-    int d[4] = {c[0], c[1], c[2], c[3]};
-    d[dir] += s;
-    if (d[dir] == g.L[dir]) d[dir] = 0;
-    if (d[dir] < 0) d[dir] = g.L[dir] - 1;
-    return coords_cb(g, d);
-}
-
-template <typename R>
-__device__ __forceinline__ void m3_acc(M3<R> &a, const M3<R> &b)
-{
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) a.e[i][j] = a.e[i][j] + b.e[i][j];
-}
-
-// coordinates c shifted by s (+1 or -1) in direction D, periodic
-template <int D>
-__device__ __forceinline__ void shift(const Geo &g, const int c[4], int s, int o[4])
-{
-#pragma unroll
-    for (int k = 0; k < 4; k++) o[k] = c[k];
-    int v = c[D] + s;
-    o[D] = v == g.L[D] ? 0 : (v < 0 ? g.L[D] - 1 : v);
-}
-
-// staple sum A_mu(x): U_mu(x) A_mu(x) = sum of the 6 plaquettes starting with
-// the link.  MU is a compile-time constant so every coordinate array is
-// indexed by constants (no local memory).
-template <int MU, typename R, lqcd_prec GP>
-__device__ __forceinline__ void gauge_force_link(MomRef &P, const GaugeRef<GP> &U, const Geo &g, int par, int cb,
-                                                 const int c[4], double cf)
-{
-    int cpm[4];
-    shift<MU>(g, c, +1, cpm);
-    const int cb_pm = coords_cb(g, cpm);
-    M3<R> A;
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) A.e[i][j] = cx<R>(0, 0);
-#pragma unroll
-    for (int k = 1; k < 4; k++) {
-        const int nu = (MU + k) & 3;
-        int cpn[4], cmn[4], cpmmn[4];
-        switch (nu) { // nu is a constant after unrolling
-        case 0: shift<0>(g, c, +1, cpn), shift<0>(g, c, -1, cmn), shift<0>(g, cpm, -1, cpmmn); break;
-        case 1: shift<1>(g, c, +1, cpn), shift<1>(g, c, -1, cmn), shift<1>(g, cpm, -1, cpmmn); break;
-        case 2: shift<2>(g, c, +1, cpn), shift<2>(g, c, -1, cmn), shift<2>(g, cpm, -1, cpmmn); break;
-        default: shift<3>(g, c, +1, cpn), shift<3>(g, c, -1, cmn), shift<3>(g, cpm, -1, cpmmn); break;
-        }
-        const int cb_pn = coords_cb(g, cpn), cb_mn = coords_cb(g, cmn), cb_pmmn = coords_cb(g, cpmmn);
-        // upper: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
-        M3<R> up = m3_mul_dag(U.template load<R>(nu, 1 - par, cb_pm), U.template load<R>(MU, 1 - par, cb_pn));
-        up = m3_mul_dag(up, U.template load<R>(nu, par, cb));
-        m3_acc(A, up);
-        // lower: U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu) = (U_mu(x-nu) U_nu(x+mu-nu))^dag U_nu(x-nu)
-        M3<R> lo = m3_mul(U.template load<R>(MU, 1 - par, cb_mn), U.template load<R>(nu, par, cb_pmmn));
-        lo = m3_dag_mul(lo, U.template load<R>(nu, 1 - par, cb_mn));
-        m3_acc(A, lo);
-    }
-    M3<R> W = m3_mul(U.template load<R>(MU, par, cb), A);
-    R gl[8];
-    im_tr_lambda(W, gl);
-#pragma unroll
-    for (int a = 0; a < 8; a++) P.d[P.idx(MU, par, a, cb)] -= cf * (double)gl[a];
-}
 
 template <typename R, lqcd_prec GP>
 __global__ void __launch_bounds__(FB_MAX) gauge_force_kernel(MomRef P, GaugeRef<GP> U, Geo g, double cf)
@@ -137,125 +29,6 @@ __global__ void __launch_bounds__(FB_MAX) gauge_force_kernel(MomRef P, GaugeRef<
     case 2: gauge_force_link<2, R, GP>(P, U, g, par, cb, c, cf); break;
     default: gauge_force_link<3, R, GP>(P, U, g, par, cb, c, cf); break;
     }
-}
-
-// FP32 fermion force: each thread first starts asynchronous 16-byte copies
-// (cp.async) of B(x), B(x+mu) and U_mu(x) (one group) and of A(x+mu) (a
-// second) into shared memory, so their DRAM latencies overlap instead of
-// following one another; A(x) is loaded as before.  The arithmetic is
-// unchanged.  Slots: [0, 6) B(x), [6, 12) B(x+mu), [12, 15) U_mu(x),
-// [15, 21) A(x+mu), each [slot][thread] in dynamic shared memory (336 bytes
-// per thread, so at most FF_MAX threads per block).
-constexpr int FF_SLOTS = 21;
-constexpr int FF_MAX = 128;
-
-__device__ __forceinline__ void ff_cp16(float4 *dst, const float4 *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(__cvta_generic_to_global(src))
-                 : "memory");
-}
-
-// a 12-real FP32 link from its three stored chunks (as GaugeRef<F32>::load)
-template <typename R>
-__device__ __forceinline__ M3<R> ff_link(float4 a, float4 b, float4 c)
-{
-    M3<R> u;
-    u.e[0][0] = cx<R>(a.x, a.y);
-    u.e[0][1] = cx<R>(a.z, a.w);
-    u.e[0][2] = cx<R>(b.x, b.y);
-    u.e[1][0] = cx<R>(b.z, b.w);
-    u.e[1][1] = cx<R>(c.x, c.y);
-    u.e[1][2] = cx<R>(c.z, c.w);
-    reconstruct_row2(u);
-    return u;
-}
-
-// Fermion force on link (x, mu), x of parity par:
-//   Q = sum_spin [s U A(x+mu)] [(1 - gamma_mu) B(x)]^dag - A(x) [s U (1 + gamma_mu) B(x+mu)]^dag
-// A = (A_e, A_o), B = (B_e, B_o) full-lattice spinors split by parity.
-template <int MU, typename R, lqcd_prec SP, lqcd_prec GP>
-__device__ __forceinline__ void fermion_force_link(MomRef &P, const GaugeRef<GP> &U, const Geo &g, int par,
-                                                   int cb, const int c[4], const SpinorRef<SP> (&A)[2],
-                                                   const SpinorRef<SP> (&B)[2], double cf,
-                                                   float4 *pf = nullptr)
-{
-    int cy[4] = {c[0], c[1], c[2], c[3]};
-    bool wrap = (c[MU] + 1 == g.L[MU]);
-    cy[MU] = wrap ? 0 : c[MU] + 1;
-    int cby = coords_cb(g, cy);
-    R s = (MU == 3 && wrap && g.t_bc < 0) ? (R)-1 : (R)1;
-    M3<R> u;
-    Sp<R> Ay, Ax, Bx, By;
-    if constexpr (SP == LQCD_F32 && GP == LQCD_F32) {
-        const int i = threadIdx.x, nt = blockDim.x;
-        const size_t Vh = (size_t)g.Vh;
-        auto slot = [&](int k) -> float4 & { return pf[k * nt + i]; };
-#pragma unroll
-        for (int k = 0; k < 6; k++) {
-            ff_cp16(&slot(k), B[par].d + k * Vh + cb);
-            ff_cp16(&slot(6 + k), B[1 - par].d + k * Vh + cby);
-        }
-#pragma unroll
-        for (int k = 0; k < 3; k++) ff_cp16(&slot(12 + k), U.d + U.idx(MU, par, k, cb));
-        asm volatile("cp.async.commit_group;" ::: "memory");
-#pragma unroll
-        for (int k = 0; k < 6; k++) ff_cp16(&slot(15 + k), A[1 - par].d + k * Vh + cby);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        Ax = A[par].template load_rw<R>(cb);
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-        {
-            float4 v[6], w[6];
-#pragma unroll
-            for (int k = 0; k < 6; k++) v[k] = slot(k), w[k] = slot(6 + k);
-            Bx = B[par].template unpack<R>(v);
-            By = B[1 - par].template unpack<R>(w);
-        }
-        u = ff_link<R>(slot(12), slot(13), slot(14));
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        {
-            float4 v[6];
-#pragma unroll
-            for (int k = 0; k < 6; k++) v[k] = slot(15 + k);
-            Ay = A[1 - par].template unpack<R>(v);
-        }
-    } else {
-        u = U.template load<R>(MU, par, cb);
-        Ay = A[1 - par].template load_rw<R>(cby);
-        Ax = A[par].template load_rw<R>(cb);
-        Bx = B[par].template load_rw<R>(cb);
-        By = B[1 - par].template load_rw<R>(cby);
-    }
-    // w1 = (1 - gamma) B(x) as a full spinor
-    Sp<R> w1 = sp_zero<R>();
-    accumulate<MU, -1>(w1, project<MU, -1>(Bx));
-    // w2 = s U (1 + gamma) B(y): project, multiply the two rows, reconstruct
-    Sp<R> w2 = sp_zero<R>();
-    {
-        Hs<R> h = mul_link(u, project<MU, +1>(By));
-        accumulate<MU, +1>(w2, h);
-    }
-    M3<R> Q;
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-#pragma unroll
-        for (int b = 0; b < 3; b++) Q.e[a][b] = cx<R>(0, 0);
-#pragma unroll
-    for (int sp = 0; sp < 4; sp++) {
-        Cx<R> v1[3];
-#pragma unroll
-        for (int a = 0; a < 3; a++) v1[a] = u.e[a][0] * Ay.c[sp][0] + u.e[a][1] * Ay.c[sp][1] + u.e[a][2] * Ay.c[sp][2];
-#pragma unroll
-        for (int a = 0; a < 3; a++)
-#pragma unroll
-            for (int b = 0; b < 3; b++)
-                Q.e[a][b] = Q.e[a][b] + s * (v1[a] * conj(w1.c[sp][b]) - Ax.c[sp][a] * conj(w2.c[sp][b]));
-    }
-    R gl[8];
-    im_tr_lambda(Q, gl);
-    // P -= coeff * f with f_a = -kappa^2 g_a
-#pragma unroll
-    for (int a = 0; a < 8; a++) P.d[P.idx(MU, par, a, cb)] += cf * (double)gl[a];
 }
 
 template <typename R, lqcd_prec SP, lqcd_prec GP>

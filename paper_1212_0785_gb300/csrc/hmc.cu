@@ -9,9 +9,11 @@
 // on (solver convergence, dH and the Metropolis uniform, the plaquette).
 #include <chrono>
 #include <cmath>
+#include <cstring>
 
 #include "batch.cuh"
 #include "cg.cuh"
+#include "chains.cuh"
 #include "su3_device.cuh"
 
 namespace lqcd {
@@ -700,6 +702,8 @@ struct lqcd_batch {
     lqcd::BatchSolver bs;
     lqcd::DevBuf scal; // one CgScalars slot per chain
     ChainStreams cs;
+    lqcd::ChainMdTables md; // shared launches of the FP32 molecular dynamics
+    bool md_shared = false;
 };
 
 namespace lqcd {
@@ -781,8 +785,45 @@ static lqcd_status per_chain(lqcd_batch *B, cudaStream_t s, F f)
     return rc;
 }
 
+// the descriptors of the chains' FP32 molecular dynamics (after the refresh,
+// which makes every field they name); false if the batch's forces are FP64
+static lqcd_status batch_md_tables(lqcd_batch *B, const lqcd_hmc_params *p, cudaStream_t s)
+{
+    B->md_shared = p[0].force_prec == LQCD_F32;
+    if (!B->md_shared) return LQCD_OK;
+    std::vector<ChainMd> d;
+    for (size_t i = 0; i < B->chains.size(); i++) {
+        lqcd_hmc_state *st = B->chains[i];
+        LQCD_TRY(ensure_f32_temps(st));
+        ChainMd c{};
+        c.g = make_geo(st->U->lat);
+        c.P = mom_ref(st->P.f);
+        c.U = gauge_ref<LQCD_F64>(st->U);
+        c.Uf = gauge_ref<LQCD_F32>(st->Uf.f);
+        c.us = st->Us.f->data;
+        c.Udf = gauge_ref<PREC_DF>(st->Udf.f);
+        c.X = spinor_ref<LQCD_F64>(st->pf[PF_MAIN].X.f);
+        c.X32 = spinor_ref<LQCD_F32>(st->X32.f);
+        c.Ao = spinor_ref<LQCD_F32>(st->Ao32.f);
+        c.Ye = spinor_ref<LQCD_F32>(st->Ye32.f);
+        c.Bo = spinor_ref<LQCD_F32>(st->Bo32.f);
+        c.beta = p[i].beta;
+        c.kappa = p[i].kappa;
+        c.mk2 = (float)(-p[i].kappa * p[i].kappa);
+        d.push_back(c);
+    }
+    if (B->md.n == (int)d.size() && !std::memcmp(B->md.host.data(), d.data(), d.size() * sizeof(ChainMd)))
+        return LQCD_OK; // the same fields and couplings: the tables stand
+    return B->md.build(d, s);
+}
+
 static lqcd_status batch_kick(lqcd_batch *B, const lqcd_hmc_params *p, double c, cudaStream_t s)
 {
+    if (B->md_shared) { // one launch per kernel over every chain
+        LQCD_TRY(chains_gauge_force(B->md, c, s));
+        LQCD_TRY(batch_solve(B, p, s));
+        return chains_fermion_force(B->md, c, s);
+    }
     LQCD_TRY(per_chain(B, s, [&](size_t i, cudaStream_t cst) {
         lqcd_hmc_state *st = B->chains[i];
         return gauge_force_dev(st->P.f, st->U, st->Uf.f, p[i].beta, c, p[i].force_prec, cst);
@@ -796,6 +837,10 @@ static lqcd_status batch_kick(lqcd_batch *B, const lqcd_hmc_params *p, double c,
 
 static lqcd_status batch_drift(lqcd_batch *B, const lqcd_hmc_params *p, double c, cudaStream_t s)
 {
+    if (B->md_shared) {
+        for (lqcd_hmc_state *st : B->chains) st->md_time += c; // (no kicks are queued in a batch)
+        return chains_link_update(B->md, c, p[0].cg.sloppy, s);
+    }
     return per_chain(B, s, [&](size_t i, cudaStream_t cst) { return drift(B->chains[i], &p[i], c, cst); });
 }
 
@@ -865,6 +910,7 @@ lqcd_status lqcd_batch_trajectory(lqcd_batch *B, const lqcd_hmc_params *params, 
         LQCD_CUDA(cudaMemcpyAsync(st->Ubak.f->data, st->U->data, st->U->bytes, cudaMemcpyDeviceToDevice, s));
         LQCD_TRY(refresh(st, &params[i], &H0[i], s));
     }
+    LQCD_TRY(batch_md_tables(B, params, s));
     lqcd_status rc = batch_integrate(B, params, s);
     if (rc == LQCD_OK) {
         for (size_t i = 0; i < n; i++) LQCD_TRY(hamiltonian_parts(B->chains[i], &params[i], s));
