@@ -79,6 +79,11 @@ typedef enum {
 typedef struct {
     int dims[4]; /* Lx, Ly, Lz, Lt: positive and even, V < 2^31 */
     int t_bc;    /* fermion boundary factor in t: -1 antiperiodic, +1 periodic */
+    double xi0;  /* anisotropic Wilson actions (the paper's runs, Fig. 3): the gauge action weighs the
+                    plaquettes of the planes with t by beta xi0 and the spatial ones by beta / xi0;
+                    0 or 1: isotropic */
+    double nu;   /* the Wilson operator weighs its spatial hops by nu / xi0 (its t hops by 1);
+                    0 counts as 1 */
 } lqcd_lattice;
 
 typedef enum {

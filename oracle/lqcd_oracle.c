@@ -61,10 +61,24 @@ typedef struct {
     int L[4];
     long V;
     double t_bc; /* +1 periodic, -1 antiperiodic fermion boundary in t */
+    double xi0;  /* bare gauge anisotropy: plaquettes in a plane with t weigh xi0, spatial ones 1/xi0 */
+    double cs;   /* weight of the spatial hops of the Wilson operator, nu / xi0 (t hops weigh 1) */
 } geom;
+
+/* Anisotropy of every later call (the paper's runs use the anisotropic
+ * Wilson gauge and fermion actions, Fig. 3): 1, 1 is the isotropic action. */
+static double g_xi0 = 1.0, g_nu = 1.0;
+
+void or_set_anisotropy(double xi0, double nu)
+{
+    g_xi0 = xi0;
+    g_nu = nu;
+}
 
 static int geom_init(geom *g, const int *dims, int t_bc)
 {
+    g->xi0 = g_xi0;
+    g->cs = g_nu / g_xi0;
     g->V = 1;
     for (int mu = 0; mu < 4; mu++) {
         if (dims[mu] <= 0 || dims[mu] % 2 != 0) return -1;
@@ -419,6 +433,7 @@ static void dslash_site(const geom *g, const double *U, const double *psi, long 
     gamma_init();
     for (int k = 0; k < 12; k++) out[k] = 0;
     for (int mu = 0; mu < 4; mu++) {
+        const double w = mu < 3 ? g->cs : 1.0; /* the hop's weight in the anisotropic operator */
         double s;
         /* forward hop */
         long y = hop(g, x, mu, +1, &s);
@@ -438,7 +453,7 @@ static void dslash_site(const geom *g, const double *U, const double *psi, long 
                     cplx proj = (al == be ? 1.0 : 0.0) - G[mu][al][be];
                     acc += proj * v[be * 3 + a];
                 }
-                out[al * 3 + a] += s * acc;
+                out[al * 3 + a] += (s * w) * acc;
             }
         /* backward hop */
         y = hop(g, x, mu, -1, &s);
@@ -457,7 +472,7 @@ static void dslash_site(const geom *g, const double *U, const double *psi, long 
                     cplx proj = (al == be ? 1.0 : 0.0) + G[mu][al][be];
                     acc += proj * v[be * 3 + a];
                 }
-                out[al * 3 + a] += s * acc;
+                out[al * 3 + a] += (s * w) * acc;
             }
     }
 }
@@ -610,6 +625,33 @@ static mat3 plaquette_mat(const geom *g, const double *U, long x, int mu, int nu
     return mat_mul(&t, &dd);
 }
 
+/* weight of the plaquettes in plane (mu, nu) in the anisotropic gauge action:
+ * xi0 for the planes with t, 1/xi0 for the spatial ones */
+static double plane_weight(const geom *g, int mu, int nu)
+{
+    return (mu == 3 || nu == 3) ? g->xi0 : 1.0 / g->xi0;
+}
+
+/* sum_x sum_{mu<nu} w_munu Re Tr U_munu(x) / 3, and the sum of the weights */
+static double wplaq_sum(const geom *g, const double *U)
+{
+    double s = 0;
+    for (long x = 0; x < g->V; x++)
+        for (int mu = 0; mu < 4; mu++)
+            for (int nu = mu + 1; nu < 4; nu++) {
+                mat3 p = plaquette_mat(g, U, x, mu, nu);
+                s += plane_weight(g, mu, nu) * (creal(mat_trace(&p)) / 3.0);
+            }
+    return s;
+}
+static double weight_sum(const geom *g) { return g->V * (3.0 / g->xi0 + 3.0 * g->xi0); }
+
+/* S_g = beta sum_x sum_{mu<nu} w_munu (1 - Re Tr U_munu / 3) */
+static double gauge_action(const geom *g, const double *U, double beta)
+{
+    return beta * (weight_sum(g) - wplaq_sum(g, U));
+}
+
 /* sum_x sum_{mu<nu} Re Tr U_munu(x) / 3 */
 static double plaq_sum(const geom *g, const double *U)
 {
@@ -624,7 +666,8 @@ static double plaq_sum(const geom *g, const double *U)
 }
 
 /* Staple sum A_mu(x) so that U_mu(x) A_mu(x) is the sum of the 6 plaquettes
- * through the link (x, mu) that start with it. */
+ * through the link (x, mu) that start with it, each weighted by its plane's
+ * weight in the (anisotropic) gauge action. */
 static mat3 staple(const geom *g, const double *U, long x, int mu)
 {
     mat3 A = mat_zero();
@@ -638,8 +681,11 @@ static mat3 staple(const geom *g, const double *U, long x, int mu)
         mat3 b = link_get(U, xpn, mu);
         mat3 c = link_get(U, x, nu);
         mat3 bd = mat_dag(&b), cd = mat_dag(&c);
+        const double w = plane_weight(g, mu < nu ? mu : nu, mu < nu ? nu : mu);
         mat3 t = mat_mul(&a, &bd);
         t = mat_mul(&t, &cd);
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) t.m[i][j] *= w;
         A = mat_add(&A, &t);
         /* lower: U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu) */
         long xmn = hop(g, x, nu, -1, &s);
@@ -650,6 +696,8 @@ static mat3 staple(const geom *g, const double *U, long x, int mu)
         mat3 dd = mat_dag(&d), ed = mat_dag(&e);
         t = mat_mul(&dd, &ed);
         t = mat_mul(&t, &f);
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) t.m[i][j] *= w;
         A = mat_add(&A, &t);
     }
     return A;
@@ -763,6 +811,9 @@ static void fermion_force_link(const geom *g, const double *U, double kappa, con
     mat3 T = proj_ta(&Q);
     mat3 F = mat_scale(&T, I * kappa * kappa / 2.0);
     mat_to_algebra(&F, f);
+    /* the link enters the operator through its hop, weighted by the hop's weight */
+    const double w = mu < 3 ? g->cs : 1.0;
+    for (int k = 0; k < 8; k++) f[k] *= w;
 }
 
 /* ------------------------------------------------------------------- Philox */
@@ -847,7 +898,7 @@ int or_gauge_action(const int *dims, const double *U, double beta, double *S)
 {
     geom g;
     if (geom_init(&g, dims, -1)) return -1;
-    *S = beta * (6.0 * g.V - plaq_sum(&g, U));
+    *S = gauge_action(&g, U, beta);
     return 0;
 }
 
@@ -1256,7 +1307,7 @@ int or_hamiltonian(const int *dims, int t_bc, const double *U, const double *P, 
 {
     geom g;
     if (geom_init(&g, dims, t_bc)) return -1;
-    double h = or_kinetic(dims, P) + beta * (6.0 * g.V - plaq_sum(&g, U));
+    double h = or_kinetic(dims, P) + gauge_action(&g, U, beta);
     if (n_flavors == 2) {
         double S;
         int it;
@@ -1288,7 +1339,7 @@ int or_hmc_trajectory(const int *dims, int t_bc, double *U, double beta, double 
     double *phi = malloc(sizeof(double) * ns);
     memcpy(U0, U, sizeof(double) * nl);
     or_momentum_refresh(dims, seed, chain, traj, P);
-    double H0 = or_kinetic(dims, P) + beta * (6.0 * g.V - plaq_sum(&g, U));
+    double H0 = or_kinetic(dims, P) + gauge_action(&g, U, beta);
     if (n_flavors == 2) {
         or_eta_refresh(dims, seed, chain, traj, eta);
         mhat(&g, U, kappa, eta, phi, 1);
@@ -1299,7 +1350,7 @@ int or_hmc_trajectory(const int *dims, int t_bc, double *U, double beta, double 
     md_params mp = {beta, kappa, tau, nsteps, integrator, n_flavors, cg_tol, cg_maxiter};
     md_stats st = {0, 0, 0};
     md_integrate(&g, U, P, phi, &mp, &st);
-    double H1 = or_kinetic(dims, P) + beta * (6.0 * g.V - plaq_sum(&g, U));
+    double H1 = or_kinetic(dims, P) + gauge_action(&g, U, beta);
     if (n_flavors == 2) {
         double *X = malloc(sizeof(double) * ns);
         int it;
@@ -1566,7 +1617,7 @@ int or_hmc_trajectory_hb(const int *dims, int t_bc, double *U, double beta, doub
     double *phi = calloc(ns, sizeof(double)), *phi_h = calloc(ns, sizeof(double));
     memcpy(U0, U, sizeof(double) * nl);
     or_momentum_refresh(dims, seed, chain, traj, P);
-    double H0 = or_kinetic(dims, P) + beta * (6.0 * g.V - plaq_sum(&g, U));
+    double H0 = or_kinetic(dims, P) + gauge_action(&g, U, beta);
     if (n_flavors == 2) {
         eta_refresh_purpose(&g, seed, chain, PURPOSE_ETA, traj, eta);
         H0 += dot_re(&g, eta, eta);
@@ -1584,7 +1635,7 @@ int or_hmc_trajectory_hb(const int *dims, int t_bc, double *U, double beta, doub
         }
     }
     hb_integrate(&g, U, P, &hp, phi, phi_h, 0, tau, &st);
-    double H1 = or_kinetic(dims, P) + beta * (6.0 * g.V - plaq_sum(&g, U));
+    double H1 = or_kinetic(dims, P) + gauge_action(&g, U, beta);
     if (n_flavors == 2) H1 += hb_fermion_action(&g, U, &hp, phi, phi_h, &st);
     double dH = H1 - H0;
     double u[2];

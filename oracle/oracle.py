@@ -66,6 +66,23 @@ def lib():
     return L
 
 
+class anisotropy:
+    """Context in which every oracle call uses the anisotropic Wilson actions:
+    the gauge plaquettes of the planes with t weighted by xi0 and the spatial
+    ones by 1/xi0 (beta xi0 and beta / xi0), the spatial hops of the Wilson
+    operator by nu / xi0 (the t hops by 1).  (1, 1) is the isotropic action."""
+
+    def __init__(self, xi0, nu):
+        self.xi0, self.nu = float(xi0), float(nu)
+
+    def __enter__(self):
+        lib().or_set_anisotropy(self.xi0, self.nu)
+        return self
+
+    def __exit__(self, *exc):
+        lib().or_set_anisotropy(1.0, 1.0)
+
+
 def num_threads() -> int:
     """threads the selected build's site loops use"""
     return int(lib().or_num_threads())
@@ -81,6 +98,7 @@ _i, _d, _u32, _l = ctypes.c_int, ctypes.c_double, ctypes.c_uint32, ctypes.c_long
 def _declare(L):
     sig = {
         "or_num_threads": (_i, []),
+        "or_set_anisotropy": (None, [_d, _d]),
         "or_gamma": (None, [_i, _dp]),
         "or_philox4x32_10": (None, [_up, _up, _up]),
         "or_uniform2": (None, [_u32] * 6 + [_dp]),

@@ -180,27 +180,30 @@ __device__ __forceinline__ Sp<float> packed_site(const SpinorRef<LQCD_F16N> &in,
     float sc;
     SpF psi;
 #define LQCD_PK_LINK(mu, f) U.template decode<float>(lp.u[mu][f][0][i], lp.u[mu][f][1][i], lp.u[mu][f][2][i])
+    // the spatial hops' weight (anisotropic operator), folded into the norm
+#define LQCD_SP(x) (g.aniso ? (x) * (float)g.cs : (x))
     psi = load_f16_unscaled(in, nb[0], sc);
     cp_async_wait<3>();
-    hop_packed<0, FS, true>(acc, psi, sc, LQCD_PK_LINK(0, 0), false);
+    hop_packed<0, FS, true>(acc, psi, LQCD_SP(sc), LQCD_PK_LINK(0, 0), false);
     psi = load_f16_unscaled(in, nb[1], sc);
-    hop_packed<0, BS, false>(acc, psi, sc, LQCD_PK_LINK(0, 1), false);
+    hop_packed<0, BS, false>(acc, psi, LQCD_SP(sc), LQCD_PK_LINK(0, 1), false);
     psi = load_f16_unscaled(in, nb[2], sc);
     cp_async_wait<2>();
-    hop_packed<1, FS, true>(acc, psi, sc, LQCD_PK_LINK(1, 0), false);
+    hop_packed<1, FS, true>(acc, psi, LQCD_SP(sc), LQCD_PK_LINK(1, 0), false);
     psi = load_f16_unscaled(in, nb[3], sc);
-    hop_packed<1, BS, false>(acc, psi, sc, LQCD_PK_LINK(1, 1), false);
+    hop_packed<1, BS, false>(acc, psi, LQCD_SP(sc), LQCD_PK_LINK(1, 1), false);
     psi = load_f16_unscaled(in, nb[4], sc);
     cp_async_wait<1>();
-    hop_packed<2, FS, true>(acc, psi, sc, LQCD_PK_LINK(2, 0), false);
+    hop_packed<2, FS, true>(acc, psi, LQCD_SP(sc), LQCD_PK_LINK(2, 0), false);
     psi = load_f16_unscaled(in, nb[5], sc);
-    hop_packed<2, BS, false>(acc, psi, sc, LQCD_PK_LINK(2, 1), false);
+    hop_packed<2, BS, false>(acc, psi, LQCD_SP(sc), LQCD_PK_LINK(2, 1), false);
     psi = load_f16_unscaled(in, nb[6], sc);
     cp_async_wait<0>();
     hop_packed<3, FS, true>(acc, psi, sc, LQCD_PK_LINK(3, 0), antip && tf);
     psi = load_f16_unscaled(in, nb[7], sc);
     hop_packed<3, BS, false>(acc, psi, sc, LQCD_PK_LINK(3, 1), antip && tb);
 #undef LQCD_PK_LINK
+#undef LQCD_SP
     Sp<float> out;
 #pragma unroll
     for (int a = 0; a < 3; a++) {

@@ -169,8 +169,14 @@ lqcd_status check_lattice(const lqcd_lattice *lat)
     }
     LQCD_REQUIRE(V < (1LL << 31), "lattice volume %lld exceeds 2^31 - 1", V);
     LQCD_REQUIRE(lat->t_bc == 1 || lat->t_bc == -1, "t_bc must be +1 or -1 (got %d)", lat->t_bc);
+    LQCD_REQUIRE(lat->xi0 >= 0 && lat->xi0 < 1e6 && lat->nu >= 0 && lat->nu < 1e6,
+                 "anisotropy xi0 = %g, nu = %g must be finite and non-negative (0: isotropic)", lat->xi0, lat->nu);
     return LQCD_OK;
 }
+
+// the anisotropy of a lattice, 0 read as 1
+static double eff_xi0(const lqcd_lattice &l) { return l.xi0 > 0 ? l.xi0 : 1.0; }
+static double eff_nu(const lqcd_lattice &l) { return l.nu > 0 ? l.nu : 1.0; }
 
 Geo make_geo(const lqcd_lattice &lat)
 {
@@ -185,6 +191,9 @@ Geo make_geo(const lqcd_lattice &lat)
     g.dLxh = make_fastdiv((uint32_t)g.Lxh);
     g.dLy = make_fastdiv((uint32_t)lat.dims[1]);
     g.dLz = make_fastdiv((uint32_t)lat.dims[2]);
+    g.xi0 = eff_xi0(lat);
+    g.cs = eff_nu(lat) / g.xi0;
+    g.aniso = (g.xi0 != 1.0 || g.cs != 1.0) ? 1 : 0;
     return g;
 }
 
@@ -192,7 +201,7 @@ bool same_lattice(const lqcd_lattice &a, const lqcd_lattice &b)
 {
     for (int mu = 0; mu < 4; mu++)
         if (a.dims[mu] != b.dims[mu]) return false;
-    return a.t_bc == b.t_bc;
+    return a.t_bc == b.t_bc && eff_xi0(a) == eff_xi0(b) && eff_nu(a) == eff_nu(b);
 }
 
 // ------------------------------------------------------------------ scalar helpers
@@ -650,7 +659,11 @@ __global__ void max_final_kernel(const double *partials, int n, double *out)
 constexpr int RB = 256;
 
 // sum over sites of sum_{mu<nu} Re Tr U_munu(x) / 3; thread per site (both parities)
-__global__ void __launch_bounds__(RB) plaquette_kernel(GaugeRef<LQCD_F64> U, Geo g, double *partials, int nblocks)
+// sum over sites and planes mu < nu of Re Tr U_munu / 3; WEIGHTED (the
+// anisotropic gauge action): each plane times its weight, xi0 for the planes
+// with t and 1 / xi0 for the spatial ones
+__global__ void __launch_bounds__(RB) plaquette_kernel(GaugeRef<LQCD_F64> U, Geo g, double *partials, int nblocks,
+                                                       int weighted)
 {
     int t = blockIdx.x * RB + threadIdx.x;
     double acc[1] = {0.0};
@@ -673,7 +686,8 @@ __global__ void __launch_bounds__(RB) plaquette_kernel(GaugeRef<LQCD_F64> U, Geo
                 double tr = 0;
                 for (int i = 0; i < 3; i++)
                     for (int k = 0; k < 3; k++) tr += a.e[i][k].re * b.e[i][k].re + a.e[i][k].im * b.e[i][k].im;
-                acc[0] += tr * (1.0 / 3.0);
+                const double p = tr * (1.0 / 3.0);
+                acc[0] += (weighted && g.aniso) ? (nu == 3 ? g.xi0 : 1.0 / g.xi0) * p : p;
             }
         }
     }
@@ -737,7 +751,8 @@ __device__ __forceinline__ M3<Df> df_mul(const M3<Df> &a, const M3<Df> &b)
     return r;
 }
 
-__global__ void __launch_bounds__(RB) plaquette_df_kernel(GaugeRef<PREC_DF> U, Geo g, double *partials, int nblocks)
+__global__ void __launch_bounds__(RB) plaquette_df_kernel(GaugeRef<PREC_DF> U, Geo g, double *partials, int nblocks,
+                                                          int weighted)
 {
     int t = blockIdx.x * RB + threadIdx.x;
     double acc[1] = {0.0};
@@ -763,29 +778,30 @@ __global__ void __launch_bounds__(RB) plaquette_df_kernel(GaugeRef<PREC_DF> U, G
                         tr.add_prod(a.e[i][k].re, b.e[i][k].re);
                         tr.add_prod(a.e[i][k].im, b.e[i][k].im);
                     }
-                acc[0] += (double)tr.value() * (1.0 / 3.0);
+                const double p = (double)tr.value() * (1.0 / 3.0);
+                acc[0] += (weighted && g.aniso) ? (nu == 3 ? g.xi0 : 1.0 / g.xi0) * p : p;
             }
         }
     }
     block_sum_store<1, RB>(acc, partials, nblocks);
 }
 
-lqcd_status plaquette_sum_df(const lqcd_field *Udf, double *dst_dev, DevBuf &part, cudaStream_t s)
+lqcd_status plaquette_sum_df(const lqcd_field *Udf, double *dst_dev, DevBuf &part, cudaStream_t s, bool weighted)
 {
     Geo g = make_geo(Udf->lat);
     int nb = nblocks_for(2L * g.Vh, RB);
     if (part.bytes < sizeof(double) * nb) LQCD_TRY(part.alloc(sizeof(double) * nb, s));
-    plaquette_df_kernel<<<nb, RB, 0, s>>>(gauge_ref<PREC_DF>(Udf), g, (double *)part.p, nb);
+    plaquette_df_kernel<<<nb, RB, 0, s>>>(gauge_ref<PREC_DF>(Udf), g, (double *)part.p, nb, weighted ? 1 : 0);
     LQCD_LAUNCHED();
     return reduce_partials((double *)part.p, nb, 1, dst_dev, s);
 }
 
-lqcd_status plaquette_sum(const lqcd_field *U, double *dst_dev, DevBuf &part, cudaStream_t s)
+lqcd_status plaquette_sum(const lqcd_field *U, double *dst_dev, DevBuf &part, cudaStream_t s, bool weighted)
 {
     Geo g = make_geo(U->lat);
     int nb = nblocks_for(2L * g.Vh, RB);
     if (part.bytes < sizeof(double) * nb) LQCD_TRY(part.alloc(sizeof(double) * nb, s));
-    plaquette_kernel<<<nb, RB, 0, s>>>(gauge_ref<LQCD_F64>(U), g, (double *)part.p, nb);
+    plaquette_kernel<<<nb, RB, 0, s>>>(gauge_ref<LQCD_F64>(U), g, (double *)part.p, nb, weighted ? 1 : 0);
     LQCD_LAUNCHED();
     return reduce_partials((double *)part.p, nb, 1, dst_dev, s);
 }
@@ -796,7 +812,7 @@ int plaquette_partial_blocks(const lqcd_field *U) { return nblocks_for(2L * U->V
 
 lqcd_status plaquette_partials_launch(const lqcd_field *U, double *partials, int nblocks, cudaStream_t s)
 {
-    plaquette_kernel<<<nblocks, RB, 0, s>>>(gauge_ref<LQCD_F64>(U), make_geo(U->lat), partials, nblocks);
+    plaquette_kernel<<<nblocks, RB, 0, s>>>(gauge_ref<LQCD_F64>(U), make_geo(U->lat), partials, nblocks, 0);
     LQCD_LAUNCHED();
     return LQCD_OK;
 }
@@ -1159,7 +1175,7 @@ lqcd_status lqcd_plaquette(const lqcd_field *U, double *out, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     DevBuf part, res;
     LQCD_TRY(res.alloc(sizeof(double), s));
-    LQCD_TRY(plaquette_sum(U, (double *)res.p, part, s));
+    LQCD_TRY(plaquette_sum(U, (double *)res.p, part, s, false));
     double h = 0;
     LQCD_TRY(read_scalars((double *)res.p, &h, 1, s));
     *out = h / (6.0 * 2.0 * U->Vh);

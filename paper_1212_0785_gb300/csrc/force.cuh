@@ -62,6 +62,15 @@ __device__ __forceinline__ int step_cb(const Geo &g, const int c[4], int dir, in
 }
 
 template <typename R>
+__device__ __forceinline__ void m3_scale(M3<R> &a, R w)
+{
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) a.e[i][j] = w * a.e[i][j];
+}
+
+template <typename R>
 __device__ __forceinline__ void m3_acc(M3<R> &a, const M3<R> &b)
 {
 #pragma unroll
@@ -109,10 +118,15 @@ __device__ __forceinline__ void gauge_force_link(MomRef &P, const GaugeRef<GP> &
         // upper: U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
         M3<R> up = m3_mul_dag(U.template load<R>(nu, 1 - par, cb_pm), U.template load<R>(MU, 1 - par, cb_pn));
         up = m3_mul_dag(up, U.template load<R>(nu, par, cb));
-        m3_acc(A, up);
         // lower: U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu) = (U_mu(x-nu) U_nu(x+mu-nu))^dag U_nu(x-nu)
         M3<R> lo = m3_mul(U.template load<R>(MU, 1 - par, cb_mn), U.template load<R>(nu, par, cb_pmmn));
         lo = m3_dag_mul(lo, U.template load<R>(nu, 1 - par, cb_mn));
+        if (g.aniso) { // the plane's weight in the anisotropic gauge action
+            const R w = (R)((MU == 3 || nu == 3) ? g.xi0 : 1.0 / g.xi0);
+            m3_scale(up, w);
+            m3_scale(lo, w);
+        }
+        m3_acc(A, up);
         m3_acc(A, lo);
     }
     M3<R> W = m3_mul(U.template load<R>(MU, par, cb), A);
@@ -236,7 +250,8 @@ __device__ __forceinline__ void fermion_force_link(MomRef &P, const GaugeRef<GP>
     }
     R gl[8];
     im_tr_lambda(Q, gl);
-    // P -= coeff * f with f_a = -kappa^2 g_a
+    // P -= coeff * f with f_a = -kappa^2 g_a (a spatial link times its hop's weight)
+    if (MU < 3 && g.aniso) cf *= g.cs;
 #pragma unroll
     for (int a = 0; a < 8; a++) P.d[P.idx(MU, par, a, cb)] += cf * (double)gl[a];
 }

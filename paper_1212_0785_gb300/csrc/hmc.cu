@@ -19,8 +19,9 @@
 namespace lqcd {
 
 // defined in field.cu / force.cu
-lqcd_status plaquette_sum(const lqcd_field *U, double *dst_dev, DevBuf &part, cudaStream_t s);
-lqcd_status plaquette_sum_df(const lqcd_field *Udf, double *dst_dev, DevBuf &part, cudaStream_t s);
+// (weighted: the anisotropic gauge action's plane weights; false: the plaquette observable)
+lqcd_status plaquette_sum(const lqcd_field *U, double *dst_dev, DevBuf &part, cudaStream_t s, bool weighted);
+lqcd_status plaquette_sum_df(const lqcd_field *Udf, double *dst_dev, DevBuf &part, cudaStream_t s, bool weighted);
 lqcd_status kinetic_sum(const lqcd_field *P, double *dst_dev, DevBuf &part, cudaStream_t s);
 lqcd_status reunitarize_dev(lqcd_field *U, double *dst_dev, DevBuf &part, cudaStream_t s);
 lqcd_status link_update_dev(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *Us, lqcd_field *Uf, bool fast,
@@ -382,17 +383,22 @@ static lqcd_status hamiltonian_parts(lqcd_hmc_state *st, const lqcd_hmc_params *
 {
     double *d = (double *)st->scal.p;
     if (sloppy_links(st, p) && st->Udf.f)
-        LQCD_TRY(plaquette_sum_df(st->Udf.f, d + 0, st->part, s));
+        LQCD_TRY(plaquette_sum_df(st->Udf.f, d + 0, st->part, s, true));
     else
-        LQCD_TRY(plaquette_sum(st->U, d + 0, st->part, s));
+        LQCD_TRY(plaquette_sum(st->U, d + 0, st->part, s, true));
     LQCD_TRY(kinetic_sum(st->P.f, d + 1, st->part, s));
     return LQCD_OK;
 }
 
+// H = T + S_g + S_f from the sums h: h[0] the plaquette sum weighted by the
+// gauge action's plane weights, whose total over all plaquettes is
+// V (3 / xi0 + 3 xi0) (6 V when isotropic)
 static double hamiltonian_from(const lqcd_hmc_state *st, const lqcd_hmc_params *p, const double *h)
 {
     double V = 2.0 * st->U->Vh;
-    return 0.5 * h[1] + p->beta * (6.0 * V - h[0]) + (p->n_flavors == 2 ? h[2] : 0.0);
+    const Geo g = make_geo(st->U->lat);
+    const double W = g.aniso ? V * (3.0 / g.xi0 + 3.0 * g.xi0) : 6.0 * V;
+    return 0.5 * h[1] + p->beta * (W - h[0]) + (p->n_flavors == 2 ? h[2] : 0.0);
 }
 
 static lqcd_status refresh(lqcd_hmc_state *st, const lqcd_hmc_params *p, double *H0, cudaStream_t s)
@@ -635,7 +641,7 @@ lqcd_status lqcd_hmc_trajectory(lqcd_hmc_state *s, const lqcd_hmc_params *p, lqc
         LQCD_TRY(reunitarize_dev(s->U, d + 5, s->part, st));
         LQCD_TRY(read_scalars(d + 5, &maxdev, 1, st));
     }
-    LQCD_TRY(plaquette_sum(s->U, d + 6, s->part, st));
+    LQCD_TRY(plaquette_sum(s->U, d + 6, s->part, st, false));
     double plaq_sum = 0;
     LQCD_TRY(read_scalars(d + 6, &plaq_sum, 1, st));
     if (info) {
@@ -940,7 +946,7 @@ lqcd_status lqcd_batch_trajectory(lqcd_batch *B, const lqcd_hmc_params *params, 
             LQCD_TRY(reunitarize_dev(st->U, d + 5, st->part, s));
             LQCD_TRY(read_scalars(d + 5, &maxdev, 1, s));
         }
-        LQCD_TRY(plaquette_sum(st->U, d + 6, st->part, s));
+        LQCD_TRY(plaquette_sum(st->U, d + 6, st->part, s, false));
         double plaq_sum = 0;
         LQCD_TRY(read_scalars(d + 6, &plaq_sum, 1, s));
         if (info) {

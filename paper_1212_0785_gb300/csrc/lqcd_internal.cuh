@@ -175,6 +175,9 @@ struct Geo {
     int Lxh; // Lx / 2
     int Vh;
     int t_bc; // +1 / -1
+    int aniso;  // the actions are anisotropic (xi0 != 1 or cs != 1)
+    double xi0; // gauge: planes with t weigh xi0, spatial planes 1 / xi0
+    double cs;  // fermion: weight nu / xi0 of the spatial hops
     int sY, sZ, sT; // checkerboard strides of y, z, t
     FastDiv dLxh, dLy, dLz;
 };

@@ -43,7 +43,7 @@ class LqcdError(RuntimeError):
 # ---------------------------------------------------------------- structs
 
 class Lattice(ctypes.Structure):
-    _fields_ = [("dims", ctypes.c_int * 4), ("t_bc", ctypes.c_int)]
+    _fields_ = [("dims", ctypes.c_int * 4), ("t_bc", ctypes.c_int), ("xi0", ctypes.c_double), ("nu", ctypes.c_double)]
 
 
 class CgParams(ctypes.Structure):
@@ -299,30 +299,34 @@ def _s(stream):
 
 # ---------------------------------------------------------------- fields
 
-def lattice(dims, t_bc=-1) -> Lattice:
-    return Lattice((ctypes.c_int * 4)(*[int(d) for d in dims]), int(t_bc))
+def lattice(dims, t_bc=-1, xi0=1.0, nu=1.0) -> Lattice:
+    """the lattice of a field: extents, fermion boundary factor in t, and the
+    anisotropy of the actions (xi0: the gauge action's plaquettes with t weigh
+    beta xi0, the spatial ones beta / xi0; the Wilson operator's spatial hops
+    weigh nu / xi0)"""
+    return Lattice((ctypes.c_int * 4)(*[int(d) for d in dims]), int(t_bc), float(xi0), float(nu))
 
 
 class Field:
     """A device field owned by the library (lqcd_field*)."""
 
-    def __init__(self, dims, kind, prec=F64, recon=None, t_bc=-1):
+    def __init__(self, dims, kind, prec=F64, recon=None, t_bc=-1, aniso=(1.0, 1.0)):
         install_torch_allocator()
         self.dims = tuple(int(d) for d in dims)
-        self.kind, self.prec, self.t_bc = kind, prec, t_bc
+        self.kind, self.prec, self.t_bc, self.aniso = kind, prec, t_bc, tuple(float(v) for v in aniso)
         if recon is None:
             recon = (18 if prec == F64 else 12) if kind == GAUGE else 0
         self.recon = recon
         h = ctypes.c_void_p()
-        _check(lib().lqcd_field_alloc(ctypes.byref(lattice(dims, t_bc)), kind, prec, recon, ctypes.byref(h)),
-               "field_alloc")
+        _check(lib().lqcd_field_alloc(ctypes.byref(lattice(dims, t_bc, *self.aniso)), kind, prec, recon,
+                                      ctypes.byref(h)), "field_alloc")
         self.h = h
         self._owned = True
 
     @classmethod
-    def borrowed(cls, handle, dims, kind, prec=F64, t_bc=-1):
+    def borrowed(cls, handle, dims, kind, prec=F64, t_bc=-1, aniso=(1.0, 1.0)):
         f = cls.__new__(cls)
-        f.dims, f.kind, f.prec, f.t_bc = tuple(dims), kind, prec, t_bc
+        f.dims, f.kind, f.prec, f.t_bc, f.aniso = tuple(dims), kind, prec, t_bc, tuple(aniso)
         f.recon = (18 if prec == F64 else 12) if kind == GAUGE else 0
         f.h = ctypes.c_void_p(handle)
         f._owned = False
@@ -380,16 +384,18 @@ class Field:
             pass
 
 
-def gauge_field(dims, prec=F64, t_bc=-1):
-    return Field(dims, GAUGE, prec, t_bc=t_bc)
+def gauge_field(dims, prec=F64, t_bc=-1, aniso=(1.0, 1.0)):
+    """aniso = (xi0, nu): the anisotropic actions (see lattice); every field of
+    one computation carries the same"""
+    return Field(dims, GAUGE, prec, t_bc=t_bc, aniso=aniso)
 
 
-def spinor_field(dims, parity, prec=F64, t_bc=-1):
-    return Field(dims, SPINOR_EVEN if parity == 0 else SPINOR_ODD, prec, t_bc=t_bc)
+def spinor_field(dims, parity, prec=F64, t_bc=-1, aniso=(1.0, 1.0)):
+    return Field(dims, SPINOR_EVEN if parity == 0 else SPINOR_ODD, prec, t_bc=t_bc, aniso=aniso)
 
 
-def momentum_field(dims, t_bc=-1):
-    return Field(dims, MOMENTUM, F64, t_bc=t_bc)
+def momentum_field(dims, t_bc=-1, aniso=(1.0, 1.0)):
+    return Field(dims, MOMENTUM, F64, t_bc=t_bc, aniso=aniso)
 
 
 # ---------------------------------------------------------------- operations
@@ -504,9 +510,9 @@ class HmcState:
         u, p, phi = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
         _check(lib().lqcd_hmc_state_fields(self.h, ctypes.byref(u), ctypes.byref(p), ctypes.byref(phi)),
                "hmc_state_fields")
-        d, t = self.U.dims, self.U.t_bc
-        return (self.U, Field.borrowed(p.value, d, MOMENTUM, t_bc=t),
-                Field.borrowed(phi.value, d, SPINOR_EVEN, t_bc=t))
+        d, t, a = self.U.dims, self.U.t_bc, self.U.aniso
+        return (self.U, Field.borrowed(p.value, d, MOMENTUM, t_bc=t, aniso=a),
+                Field.borrowed(phi.value, d, SPINOR_EVEN, t_bc=t, aniso=a))
 
     @property
     def traj(self) -> int:
@@ -551,14 +557,16 @@ class HmcState:
         counter -- to an .npz file.  The random numbers of every trajectory
         follow from (seed, chain, traj) alone, so a resumed chain repeats the
         unbroken one bit for bit."""
-        np.savez(path, U=self.U.download(), dims=np.array(self.U.dims), t_bc=self.U.t_bc, seed=self.seed,
+        np.savez(path, U=self.U.download(), dims=np.array(self.U.dims), t_bc=self.U.t_bc,
+                 aniso=np.array(self.U.aniso), seed=self.seed,
                  chain=self.chain, traj=self.traj)
 
     @classmethod
     def resume(cls, path) -> "HmcState":
         """A new chain state (and its FP64 gauge field, state.U) from a checkpoint file."""
         z = np.load(path)
-        U = gauge_field(tuple(int(v) for v in z["dims"]), t_bc=int(z["t_bc"])).upload(z["U"])
+        U = gauge_field(tuple(int(v) for v in z["dims"]), t_bc=int(z["t_bc"]),
+                        aniso=tuple(float(v) for v in z["aniso"])).upload(z["U"])
         return cls(U, int(z["seed"]), int(z["chain"]), int(z["traj"]))
 
     def close(self):
