@@ -46,7 +46,6 @@ WORKLOAD = {
     "cg_tol": 1e-10,
 }
 SEED, EPS = 3, 0.15
-SLOPPY_BYTES = {"f64": 1536, "f32": 576, "f16n": 296, "bf16": 288}  # algorithmic bytes / half-dslash site
 ORACLE_SAMPLE_DIMS = (12, 12, 12, 24)
 
 
@@ -156,6 +155,12 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- peaks, profiles
 
+# HBM3e bandwidth of a GB300 as specified (context beside the measured copy peak)
+NOMINAL_HBM_GBS = 7900.0
+# the dominant class's launches carry events one in TIMER_EVERY inside the timed region
+TIMER_EVERY = 13
+
+
 def measured_peaks() -> dict:
     p = os.path.join(HERE, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -170,13 +175,13 @@ def kernel_source_hash() -> str:
     valid for the kernel it was taken on"""
     h = hashlib.sha256()
     base = os.path.join(HERE, "paper_1212_0785_gb300", "csrc")
-    for name in ("dslash.cu", "dslash_site.cuh", "spin.cuh", "lqcd_internal.cuh", "dslash.cuh"):
+    for name in ("dslash.cu", "dslash_site.cuh", "dslash_packed.cuh", "spin.cuh", "lqcd_internal.cuh", "dslash.cuh"):
         with open(os.path.join(base, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def stored_traffic(kernel: str):
+def stored_traffic(kernel: str, key: str = "dram_bytes_per_launch"):
     """DRAM bytes per launch from the committed ncu summary, or None if absent or stale"""
     p = os.path.join(HERE, "profiles", f"traffic_{kernel}_32x32x32x64.txt")
     if not os.path.exists(p):
@@ -190,7 +195,7 @@ def stored_traffic(kernel: str):
     if kv.get("kernel_source_sha") != kernel_source_hash():
         return None
     try:
-        return float(kv["dram_bytes_per_launch"])
+        return float(kv[key])
     except (KeyError, ValueError):
         return None
 
@@ -397,7 +402,11 @@ def run_ours(args):
     kclass = f"dslash_{args.sloppy}"
     # only the dominant class is timed inside the timed region (events on its
     # launches); the per-class breakdown comes from one more trajectory below
-    lqcd.kernel_timers(True, only=kclass)
+    plain_class = kclass + "_plain" if kclass == "dslash_f16n" else None
+    # events on one launch of the class in every TIMER_EVERY (coprime to the
+    # four hop variants of a CG iteration, so all are sampled alike): events
+    # on every launch would slow the timed trajectories themselves
+    lqcd.kernel_timers(True, only=kclass, every=TIMER_EVERY)
     launches0 = lqcd.launch_count()
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -415,23 +424,41 @@ def run_ours(args):
     value = total_traj / t_max
 
     ms, n, nbytes = lqcd.kernel_timer_read(kclass)
-    # per-class breakdown: one more trajectory with every class timed
-    lqcd.kernel_timers(True)
+    # per-class breakdown: one more trajectory with every launch of every class timed
+    lqcd.kernel_timers(True, every=1)
     state.trajectory(params)
     torch.cuda.synchronize()
     timers = {k: lqcd.kernel_timer_read(k) for k in lqcd.KERNEL_CLASSES}
     lqcd.kernel_timers(False)
+    # the plain variant's own events (outside the timed region, whose only
+    # events are the class's: nested events would add to every plain launch)
+    pms, pn, pbytes = timers[plain_class] if plain_class else (0.0, 0, 0.0)
     Vh = V // 2
     peaks = measured_peaks()
     # achieved = algorithmic bytes of the timed launches (each launch's own
     # fields: plain, axpy and CG-update variants) / their summed event time
     achieved = nbytes / (ms * 1e-3) / 1e9 if n else None
-    traffic = stored_traffic(kclass) if tuple(dims) == (32, 32, 32, 64) else None
+    full = tuple(dims) == (32, 32, 32, 64)
+    traffic = stored_traffic(kclass) if full else None
     roofline = {"kernel": kclass, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"] if achieved else None, "traffic": traffic,
-                "peak_source": peaks["source"], "algorithmic_bytes_per_launch": nbytes / n if n else None,
-                "plain_kernel_bytes_per_launch": SLOPPY_BYTES[args.sloppy] * Vh,
-                "avg_launch_us": ms / n * 1e3 if n else None, "launches": n}
+                "peak_source": peaks["source"],
+                "nominal_peak": NOMINAL_HBM_GBS,
+                "frac_of_nominal": achieved / NOMINAL_HBM_GBS if achieved else None,
+                # DRAM bytes actually moved per second (ncu traffic / live launch time)
+                "dram_achieved": traffic / (ms / n * 1e-3) / 1e9 if (traffic and n) else None,
+                "algorithmic_bytes_per_launch": nbytes / n if n else None,
+                "avg_launch_us": ms / n * 1e3 if n else None, "launches": n, "timed_one_in": TIMER_EVERY}
+    if pn:
+        # the plain hop alone (no fused epilogue), from its own event timers
+        # in the breakdown trajectory
+        p_ach = pbytes / (pms * 1e-3) / 1e9
+        p_traffic = stored_traffic(kclass, "dram_bytes_per_launch_plain") if full else None
+        roofline["plain"] = {"achieved": p_ach, "frac": p_ach / peaks["hbm_gbs"],
+                             "frac_of_nominal": p_ach / NOMINAL_HBM_GBS,
+                             "algorithmic_bytes_per_launch": pbytes / pn, "avg_launch_us": pms / pn * 1e3,
+                             "launches": pn, "traffic": p_traffic,
+                             "dram_achieved": p_traffic / (pms / pn * 1e-3) / 1e9 if p_traffic else None}
     step_ms = t_max / args.steps * 1e3
     kernel_share = {k: {"ms_per_traj": v[0], "launches_per_traj": v[1],
                         "GB_per_s": (v[2] / (v[0] * 1e-3) / 1e9) if v[2] else None}
@@ -613,7 +640,7 @@ def run_fp64_16(args):
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clock x 2 flop x 2.07 GHz",
                 "hbm_GB_per_s": nbytes / (ms * 1e-3) / 1e9 if n else None,
-                "avg_launch_us": ms / n * 1e3 if n else None, "launches": n}
+                "avg_launch_us": ms / n * 1e3 if n else None, "launches": n, "timed_one_in": TIMER_EVERY}
     cpu = None
     if not args.no_cpu_baseline:
         from oracle import oracle as orc

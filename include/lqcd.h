@@ -123,17 +123,27 @@ uint64_t lqcd_launch_count(void);
  * "dslash_f64", "dslash_f32", "dslash_f16n", "dslash_bf16" (every half
  * hopping-term launch of that storage precision, fused epilogues included),
  * "dslash_df64" (the mixed solver's float-float residual products),
- * "gauge_force", "fermion_force", "link_update".  Enabling clears the totals.
+ * "gauge_force", "fermion_force", "link_update", and "dslash_f16n_plain" (the
+ * plain FP16+norm hops alone, without fused epilogues; they are also counted
+ * in "dslash_f16n").  Enabling clears the totals.
  * lqcd_kernel_timer_read synchronises the device, then returns the summed
  * event time in milliseconds, the number of launches of one class and, for the
  * hopping-term classes, the algorithmic bytes those launches move (every
  * link, input, output and fused-epilogue field element counted once; 0 for
  * the other classes).  Output pointers may be NULL. */
 lqcd_status lqcd_kernel_timers(int enable);
-/* The same with one class timed (the others run without events). */
-lqcd_status lqcd_kernel_timers_only(const char *kernel_class);
+/* The same with only the listed classes timed (comma-separated names; the
+ * others run without events).  LQCD_EINVAL on an unknown name. */
+lqcd_status lqcd_kernel_timers_only(const char *kernel_classes);
 lqcd_status lqcd_kernel_timer_read(const char *kernel_class, double *total_ms, uint64_t *launches,
                                    double *algorithmic_bytes);
+/* Sampling: while timers are enabled, time only one launch in every `every`
+ * of each class (1, the default: all), counted from the last enable, so that
+ * the events disturb a timed run less; the totals then cover the sampled
+ * launches (launches and bytes count those, the averages stay per launch).
+ * Pick `every` coprime to any period of the launch sequence (a CG iteration
+ * cycles through four hopping-term variants).  LQCD_EINVAL if every < 1. */
+lqcd_status lqcd_kernel_timers_every(int every);
 
 /* Device allocator hook.  alloc(bytes, stream, ctx) returns device memory or
  * NULL; free(ptr, stream, ctx) releases it.  Passing NULL for both restores
@@ -182,8 +192,9 @@ lqcd_status lqcd_field_data(const lqcd_field *f, void **data_dev, void **norm_de
  * to the field's precision; gauge 12-real copies keep rows 0 and 1), or the
  * field out to such an array (compressed gauge fields are expanded by
  * reconstructing row 2).  Synchronous with respect to the host buffer: the
- * call returns after the copy completed.  Uses a temporary device buffer of
- * the host array's size. */
+ * call returns after the copy completed.  Pinned (page-locked) host memory is
+ * read or written directly by the converting kernel; pageable memory goes
+ * through a temporary device buffer of the host array's size and one copy. */
 lqcd_status lqcd_field_upload(lqcd_field *f, const double *host, void *stream);
 lqcd_status lqcd_field_download(const lqcd_field *f, double *host, void *stream);
 
@@ -360,7 +371,10 @@ lqcd_status lqcd_spinor_dot(const lqcd_field *a, const lqcd_field *b, double *ou
  * first use and keeps the fastest (Sec. 4).  Here that is an explicit call:
  * lqcd_autotune times, on scratch fields of the lattice (allocated and freed
  * inside), every candidate block size of the kernel classes whose launch shape
- * is free -- "dslash_f16n" (the packed FP16+norm hopping term: 64, 128, 256),
+ * is free -- "dslash_f16n" (the packed FP16+norm hopping term: 64, 128, 256,
+ * timed as the solver uses it, one application of Mhat^dag Mhat: two plain
+ * hops and two with the fused axpy and norm reduction, whose last block sums
+ * the block partials),
  * "gauge_force_f32", "gauge_force_f64" and "link_update_f32" (32 to 256),
  * "fermion_force_f32" (32 to 128) -- keeps the fastest of each in a
  * process-wide table keyed by (kernel class, lattice dims) that every later
@@ -532,8 +546,9 @@ lqcd_status lqcd_batch_trajectory(lqcd_batch *batch, const lqcd_hmc_params *para
  * M = 1 - kappa D, on gauge fields kept resident on the device.  Requests are
  * submitted at any time from any host thread and run on a worker thread of the
  * service with its own stream: it admits queued requests in arrival order
- * while the device memory of the admitted work fits hbm_budget (a request
- * alone is always admitted), and advances all admitted right-hand sides
+ * while the device memory of the admitted work, the unreleased solutions and
+ * the pooled idle solver work spaces fits hbm_budget (a request alone is
+ * always admitted; idle work spaces are freed to make room), and advances all admitted right-hand sides
  * together, one chunk of CG iterations at a time, in shared launches (the
  * engine of lqcd_cg_solve_batch); right-hand sides join and leave between
  * chunks (continuous batching).  The paper keeps all fields resident and
@@ -551,7 +566,7 @@ typedef struct lqcd_service lqcd_service;
 
 typedef struct {
     lqcd_cg_params cg;  /* tol = target full |r|/|b|; sloppy F32, F16N or BF16; guess ignored */
-    size_t hbm_budget;  /* bytes of device memory the admitted requests may hold */
+    size_t hbm_budget;  /* device bytes for admitted requests, unreleased solutions, idle work spaces */
     int max_active_rhs; /* admit no request that would make more right-hand sides run at once (<= 0: no limit) */
 } lqcd_service_params;
 
@@ -592,6 +607,12 @@ lqcd_status lqcd_solve_solution(lqcd_service *svc, uint64_t ticket, int k, lqcd_
                                 lqcd_field **x_odd);
 /* Frees a finished request's solutions (LQCD_EAGAIN while it runs). */
 lqcd_status lqcd_solve_release(lqcd_service *svc, uint64_t ticket);
+/* Device bytes the service holds: *counted = what hbm_budget covers (the
+ * admitted right-hand sides, the solutions not yet released and the idle
+ * solver work spaces pooled for reuse); *fixed = what each gauge field holds
+ * once it has served a request (its sloppy and float-float link copies and
+ * the temporaries its solves share), outside the budget. */
+lqcd_status lqcd_service_bytes(lqcd_service *svc, size_t *counted, size_t *fixed);
 /* Finishes all submitted requests, stops the worker and frees everything. */
 lqcd_status lqcd_service_destroy(lqcd_service *svc);
 

@@ -102,7 +102,8 @@ __global__ void chains_link_update_kernel(const ChainMd *d, const int2 *bmap, do
     int mu, par, cb;
     if (!link_seq(c.g.Vh, (long)m.y * CB + threadIdx.x, mu, par, cb)) return;
     const GaugeRef<PS> Us{reinterpret_cast<decltype(GaugeRef<PS>::d)>(c.us), c.g.Vh};
-    link_update_one<PS, true>(c.U, c.P, step, Us, c.Uf, c.Udf, mu, par, cb, 1, 1);
+    // with a float-float copy the FP64 links lag behind it (written after the molecular dynamics)
+    link_update_one<PS, true>(c.U, c.P, step, Us, c.Uf, c.Udf, mu, par, cb, 1, 1, c.Udf.d ? 0 : 1);
 }
 
 // ---------------------------------------------------------------- host

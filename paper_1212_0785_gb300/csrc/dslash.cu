@@ -264,11 +264,21 @@ static int use_form(const Geo &)
             kern##_packed_kernel<LQCD_UNPAREN_PK targs, 128><<<nbp_, 128, 0, s>>> args;                              \
     } while (0)
 
-// threads per block of the packed FP16+norm kernels on this lattice (the
-// autotuner's choice, else DS_BLOCK)
+// threads per block of the packed FP16+norm kernels on this lattice: the
+// calling thread's override while the autotuner times a candidate, else the
+// autotuner's choice, else DS_BLOCK
+static thread_local int t_packed_block = 0;
+
+int dslash_packed_block_override(int bs)
+{
+    const int prev = t_packed_block;
+    t_packed_block = bs;
+    return prev;
+}
+
 static int packed_block(const lqcd_field *in)
 {
-    const int b = tuned_block(TK_HOP_F16N, in->lat, DS_BLOCK);
+    const int b = t_packed_block ? t_packed_block : tuned_block(TK_HOP_F16N, in->lat, DS_BLOCK);
     return (b == 64 || b == 128 || b == 256) ? b : DS_BLOCK;
 }
 
@@ -367,19 +377,6 @@ static void launch_cg(const lqcd_field *U, const lqcd_field *in, int dagger, con
 }
 
 // the packed plain hop with bs threads per block, for the autotuner
-lqcd_status dslash_packed_plain_block(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int bs,
-                                      cudaStream_t s)
-{
-    LQCD_TRY(check_pair(out, U, in));
-    LQCD_REQUIRE(in->prec == LQCD_F16N && U->prec == LQCD_F16N, "packed hop: FP16+norm fields only");
-    LQCD_REQUIRE(bs == 64 || bs == 128 || bs == 256, "packed hop: block size %d not compiled", bs);
-    const int prev = g_form.exchange(2);
-    launch_plain<LQCD_F16N>(out, U, in, 0, nullptr, s, bs);
-    g_form.store(prev);
-    LQCD_LAUNCHED();
-    return LQCD_OK;
-}
-
 int dslash_form_set(int form)
 {
     if (form < 0) return g_form.load();
@@ -396,6 +393,7 @@ lqcd_status dslash_plain(lqcd_field *out, const lqcd_field *U, const lqcd_field 
     LQCD_TRY(check_pair(out, U, in));
     double site = 8 * link_bytes(U->prec) + 2 * spinor_site_bytes(in->prec);
     KernelTimer kt(dslash_class(in->prec), s, site * in->Vh);
+    KernelTimer kt_plain(in->prec == LQCD_F16N ? K_DSLASH_F16N_PLAIN : K_NCLASS, s, site * in->Vh);
     switch (in->prec) {
     case LQCD_F64: launch_plain<LQCD_F64>(out, U, in, dagger, skip, s); break;
     case LQCD_F32:

@@ -150,9 +150,9 @@ lqcd_status dslash_cg(const lqcd_field *U, const lqcd_field *in, int dagger, con
                       lqcd_field *xs, lqcd_field *r, const lqcd_field *p, double *partials, CgScalars *sc,
                       cudaStream_t s);
 
-// the FP16+norm hopping-term form: 1 prefetched links (default), 2 prefetched
-// links with packed FP32x2 arithmetic, 0 gathered; returns the previous form
-// (form < 0: query; -1 and an error for an unknown form)
+// the FP16+norm hopping-term form: 2 prefetched links with packed FP32x2
+// arithmetic (default), 1 prefetched links, 0 gathered; returns the previous
+// form (form < 0: query; -1 and an error for an unknown form)
 int dslash_form_set(int form);
 
 // out = D in, or x + b D in if x is given, with float-float fields and links

@@ -1,17 +1,23 @@
 // dslash_packed.cuh -- the FP16+norm hopping term at one output site with
-// Blackwell's packed FP32 arithmetic (fma.rn.f32x2 / mul.rn.f32x2, one
-// instruction for two FP32 lanes, each rounded as fmaf / a * b).
+// Blackwell's packed arithmetic: FP16x2 for the spin projection, FP32x2
+// (fma.rn.f32x2 / mul.rn.f32x2, one instruction for two FP32 lanes, each
+// rounded as fmaf / a * b) for the link product and the reconstruction.
 //
-// The two spin rows of a projected half spinor are carried as pairs: for
-// colour j, re[j] = (row0.re, row1.re) and im[j] = (row0.im, row1.im).  The
-// spin projection, the SU(3) matrix times half spinor and the reconstruction
-// of spin rows 0, 1 (and, for z and t, rows 2, 3) then act on both rows with
-// one packed instruction where the scalar form needs two; the x and y hops
-// reconstruct rows 2, 3 from the rows in swapped order, which stays scalar.
-// Links are prefetched into shared memory as in prefetch_site, and the
-// directions, neighbours, boundary signs and per-site norms are those of
-// dslash_site.  The products are rounded in a different order than the
-// scalar form, so the bits differ from forms 0 and 1 (within FP32 rounding).
+// Each stored word of an FP16+norm spinor is one complex component (re, im)
+// of value / norm, so a projected component (1 + S gamma_mu) psi is one FP16x2
+// add of two stored words (the factor +-i swaps the halves), rounded once to
+// FP16 -- relative error 2^-11, the size of the storage rounding itself --
+// and only the 12 projected reals, not the 24 stored ones, are widened to
+// FP32: the f16 -> f32 conversions were the busiest instructions of the FMA
+// pipe.  The two spin rows of a projected half spinor are then carried as
+// pairs: for colour j, re[j] = (row0.re, row1.re) and im[j] = (row0.im,
+// row1.im), so the SU(3) matrix times half spinor and the reconstruction of
+// spin rows 0, 1 (and, for z and t, rows 2, 3) act on both rows with one
+// packed instruction; the x and y hops reconstruct rows 2, 3 from the rows in
+// swapped order, which stays scalar.  Links are prefetched into shared memory
+// as in prefetch_site, and the directions, neighbours, boundary signs and
+// per-site norms are those of dslash_site.  The bits differ from forms 0 and
+// 1 by the FP16 rounding of the projection and the order of the FP32 products.
 #pragma once
 
 #include "dslash_site.cuh"
@@ -29,60 +35,6 @@ __device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b
 __device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-
-// the 24 stored reals of an FP16+norm site (value / norm, not rescaled)
-struct SpF {
-    float re[4][3], im[4][3];
-};
-__device__ __forceinline__ SpF load_f16_unscaled(const SpinorRef<LQCD_F16N> &in, int cb, float &nrm)
-{
-    uint4 v[3];
-#pragma unroll
-    for (int k = 0; k < 3; k++) v[k] = ldg(in.d + (size_t)k * in.Vh + cb);
-    nrm = ldg(in.norm + cb);
-    SpF p;
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const uint32_t w[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int c = 4 * k + q;
-            const float2 f = unpack_h2(w[q]);
-            p.re[c / 3][c % 3] = f.x;
-            p.im[c / 3][c % 3] = f.y;
-        }
-    }
-    return p;
-}
-
-// (1 + S gamma_mu) psi: the two rows (h0, h1) of the DeGrand-Rossi projection
-//   x: h0 = p0 + S i p3, h1 = p1 + S i p2     y: h0 = p0 - S p3, h1 = p1 + S p2
-//   z: h0 = p0 + S i p2, h1 = p1 - S i p3     t: h0 = p0 + S p2, h1 = p1 + S p3
-// with i q = (-q.im, q.re); multiplying by +-1 is exact, so each lane is the
-// scalar sum
-template <int MU, int S>
-__device__ __forceinline__ HsP project_p(const SpF &p)
-{
-    HsP h;
-#pragma unroll
-    for (int j = 0; j < 3; j++) {
-        const float2 r01 = pk(p.re[0][j], p.re[1][j]), i01 = pk(p.im[0][j], p.im[1][j]);
-        if (MU == 0) {
-            h.re[j] = fma2(pk(p.im[3][j], p.im[2][j]), bc((float)-S), r01);
-            h.im[j] = fma2(pk(p.re[3][j], p.re[2][j]), bc((float)S), i01);
-        } else if (MU == 1) {
-            h.re[j] = fma2(pk(p.re[3][j], p.re[2][j]), pk((float)-S, (float)S), r01);
-            h.im[j] = fma2(pk(p.im[3][j], p.im[2][j]), pk((float)-S, (float)S), i01);
-        } else if (MU == 2) {
-            h.re[j] = fma2(pk(p.im[2][j], p.im[3][j]), pk((float)-S, (float)S), r01);
-            h.im[j] = fma2(pk(p.re[2][j], p.re[3][j]), pk((float)S, (float)-S), i01);
-        } else {
-            h.re[j] = fma2(pk(p.re[2][j], p.re[3][j]), bc((float)S), r01);
-            h.im[j] = fma2(pk(p.im[2][j], p.im[3][j]), bc((float)S), i01);
-        }
-    }
-    return h;
-}
 
 // U h (FWD) or U^dag h, both rows at once
 template <bool FWD>
@@ -144,10 +96,46 @@ __device__ __forceinline__ void accumulate_p(SpP &acc, const HsP &o, float sc)
     }
 }
 
-template <int MU, int S, bool FWD>
-__device__ __forceinline__ void hop_packed(SpP &acc, const SpF &psi, float sc, const M3<float> &u, bool flip)
+__device__ __forceinline__ __half2 as_h2(uint32_t w) { return *reinterpret_cast<const __half2 *>(&w); }
+
+// (1 + S gamma_mu) psi straight from the stored halves: each stored word is
+// one complex component (re, im) of value / norm, and each projected
+// component is one FP16 add of two of them (i q = (-q.im, q.re): the swapped
+// pair times (-1, 1)), correctly rounded to FP16; only the 12 projected reals
+// are widened to FP32 for the link product
+template <int MU, int S>
+__device__ __forceinline__ HsP load_project_h(const SpinorRef<LQCD_F16N> &in, int cb, float &nrm)
 {
-    accumulate_p<MU, S>(acc, mul_link_p<FWD>(u, project_p<MU, S>(psi)), flip ? -sc : sc);
+    uint4 v[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) v[k] = ldg(in.d + (size_t)k * in.Vh + cb);
+    nrm = ldg(in.norm + cb);
+    const uint32_t w[12] = {v[0].x, v[0].y, v[0].z, v[0].w, v[1].x, v[1].y,
+                            v[1].z, v[1].w, v[2].x, v[2].y, v[2].z, v[2].w};
+    const __half2 pi = __floats2half2_rn((float)-S, (float)S); // S i: (re, im) -> (-S im, S re)
+    const __half2 mi = __floats2half2_rn((float)S, (float)-S); // -S i
+    HsP h;
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        const __half2 p0 = as_h2(w[j]), p1 = as_h2(w[3 + j]), p2 = as_h2(w[6 + j]), p3 = as_h2(w[9 + j]);
+        __half2 h0, h1;
+        if (MU == 0) {
+            h0 = __hfma2(__lowhigh2highlow(p3), pi, p0);
+            h1 = __hfma2(__lowhigh2highlow(p2), pi, p1);
+        } else if (MU == 1) {
+            h0 = S > 0 ? __hsub2(p0, p3) : __hadd2(p0, p3);
+            h1 = S > 0 ? __hadd2(p1, p2) : __hsub2(p1, p2);
+        } else if (MU == 2) {
+            h0 = __hfma2(__lowhigh2highlow(p2), pi, p0);
+            h1 = __hfma2(__lowhigh2highlow(p3), mi, p1);
+        } else {
+            h0 = S > 0 ? __hadd2(p0, p2) : __hsub2(p0, p2);
+            h1 = S > 0 ? __hadd2(p1, p3) : __hsub2(p1, p3);
+        }
+        h.re[j] = make_float2(__low2float(h0), __low2float(h1));
+        h.im[j] = make_float2(__high2float(h0), __high2float(h1));
+    }
+    return h;
 }
 
 template <bool DAG, int BLOCK = DS_BLOCK>
@@ -178,32 +166,35 @@ __device__ __forceinline__ Sp<float> packed_site(const SpinorRef<LQCD_F16N> &in,
 #pragma unroll
         for (int a = 0; a < 3; a++) acc.re[h][a] = acc.im[h][a] = make_float2(0.f, 0.f);
     float sc;
-    SpF psi;
 #define LQCD_PK_LINK(mu, f) U.template decode<float>(lp.u[mu][f][0][i], lp.u[mu][f][1][i], lp.u[mu][f][2][i])
-    // the spatial hops' weight (anisotropic operator), folded into the norm
-#define LQCD_SP(x) (g.aniso ? (x) * (float)g.cs : (x))
-    psi = load_f16_unscaled(in, nb[0], sc);
-    cp_async_wait<3>();
-    hop_packed<0, FS, true>(acc, psi, LQCD_SP(sc), LQCD_PK_LINK(0, 0), false);
-    psi = load_f16_unscaled(in, nb[1], sc);
-    hop_packed<0, BS, false>(acc, psi, LQCD_SP(sc), LQCD_PK_LINK(0, 1), false);
-    psi = load_f16_unscaled(in, nb[2], sc);
-    cp_async_wait<2>();
-    hop_packed<1, FS, true>(acc, psi, LQCD_SP(sc), LQCD_PK_LINK(1, 0), false);
-    psi = load_f16_unscaled(in, nb[3], sc);
-    hop_packed<1, BS, false>(acc, psi, LQCD_SP(sc), LQCD_PK_LINK(1, 1), false);
-    psi = load_f16_unscaled(in, nb[4], sc);
-    cp_async_wait<1>();
-    hop_packed<2, FS, true>(acc, psi, LQCD_SP(sc), LQCD_PK_LINK(2, 0), false);
-    psi = load_f16_unscaled(in, nb[5], sc);
-    hop_packed<2, BS, false>(acc, psi, LQCD_SP(sc), LQCD_PK_LINK(2, 1), false);
-    psi = load_f16_unscaled(in, nb[6], sc);
-    cp_async_wait<0>();
-    hop_packed<3, FS, true>(acc, psi, sc, LQCD_PK_LINK(3, 0), antip && tf);
-    psi = load_f16_unscaled(in, nb[7], sc);
-    hop_packed<3, BS, false>(acc, psi, sc, LQCD_PK_LINK(3, 1), antip && tb);
+    // the spatial hops carry the anisotropic operator's weight nu / xi0 in
+    // their scale (csf = 1 exactly when isotropic, so nothing changes there)
+    // each hop: gather and project the neighbour (its loads issued before
+    // the direction's links are waited for), multiply by the link, add
+    {
+        HsP hp;
+        hp = load_project_h<0, FS>(in, nb[0], sc);
+        cp_async_wait<3>();
+        accumulate_p<0, FS>(acc, mul_link_p<true>(LQCD_PK_LINK(0, 0), hp), sc * g.csf);
+        hp = load_project_h<0, BS>(in, nb[1], sc);
+        accumulate_p<0, BS>(acc, mul_link_p<false>(LQCD_PK_LINK(0, 1), hp), sc * g.csf);
+        hp = load_project_h<1, FS>(in, nb[2], sc);
+        cp_async_wait<2>();
+        accumulate_p<1, FS>(acc, mul_link_p<true>(LQCD_PK_LINK(1, 0), hp), sc * g.csf);
+        hp = load_project_h<1, BS>(in, nb[3], sc);
+        accumulate_p<1, BS>(acc, mul_link_p<false>(LQCD_PK_LINK(1, 1), hp), sc * g.csf);
+        hp = load_project_h<2, FS>(in, nb[4], sc);
+        cp_async_wait<1>();
+        accumulate_p<2, FS>(acc, mul_link_p<true>(LQCD_PK_LINK(2, 0), hp), sc * g.csf);
+        hp = load_project_h<2, BS>(in, nb[5], sc);
+        accumulate_p<2, BS>(acc, mul_link_p<false>(LQCD_PK_LINK(2, 1), hp), sc * g.csf);
+        hp = load_project_h<3, FS>(in, nb[6], sc);
+        cp_async_wait<0>();
+        accumulate_p<3, FS>(acc, mul_link_p<true>(LQCD_PK_LINK(3, 0), hp), (antip && tf) ? -sc : sc);
+        hp = load_project_h<3, BS>(in, nb[7], sc);
+        accumulate_p<3, BS>(acc, mul_link_p<false>(LQCD_PK_LINK(3, 1), hp), (antip && tb) ? -sc : sc);
+    }
 #undef LQCD_PK_LINK
-#undef LQCD_SP
     Sp<float> out;
 #pragma unroll
     for (int a = 0; a < 3; a++) {

@@ -31,8 +31,8 @@ __device__ __forceinline__ void hop_dir(Sp<R> &acc, const SpinorRef<SP> &in, con
         R sc;
         Sp<R> psi = in.template load_scaled<R>(nf, sc);
         Hs<R> uh = mul_link(U.template load<R>(MU, out_par, cb), project<MU, FS>(psi));
-        if (MU < 3 && g.aniso) sc = NORM ? sc * (R)g.cs : (R)g.cs; // the spatial hops' weight
-        if (NORM || (MU < 3 && g.aniso)) {
+        if (NORM) {
+            if (MU < 3) sc = sc * spatial_weight<R>(g); // 1 exactly when isotropic
             scale_hs(uh, (antip && wrap_f) ? -sc : sc);
         } else if (MU == 3) {
             if (antip && wrap_f) negate(uh);
@@ -43,8 +43,8 @@ __device__ __forceinline__ void hop_dir(Sp<R> &acc, const SpinorRef<SP> &in, con
         R sc;
         Sp<R> psi = in.template load_scaled<R>(nbk, sc);
         Hs<R> uh = mul_link_dag(U.template load<R>(MU, 1 - out_par, nbk), project<MU, BS>(psi));
-        if (MU < 3 && g.aniso) sc = NORM ? sc * (R)g.cs : (R)g.cs;
-        if (NORM || (MU < 3 && g.aniso)) {
+        if (NORM) {
+            if (MU < 3) sc = sc * spatial_weight<R>(g);
             scale_hs(uh, (antip && wrap_b) ? -sc : sc);
         } else if (MU == 3) {
             if (antip && wrap_b) negate(uh);
@@ -79,6 +79,10 @@ __device__ __forceinline__ Sp<R> dslash_site(const SpinorRef<SP> &in, const Gaug
     hop_dir<0, FS, BS, R>(acc, in, U, g, cb, out_par, nb[0], nb[1], false, false);
     hop_dir<1, FS, BS, R>(acc, in, U, g, cb, out_par, nb[2], nb[3], false, false);
     hop_dir<2, FS, BS, R>(acc, in, U, g, cb, out_par, nb[4], nb[5], false, false);
+    // the anisotropic operator weighs the spatial hops: stored spinors with a
+    // norm carry the weight in it (hop_dir), the others take it here (a
+    // uniform branch)
+    if (!SpinorRef<SP>::has_norm && g.aniso) sp_scale(acc, spatial_weight<R>(g));
     hop_dir<3, FS, BS, R>(acc, in, U, g, cb, out_par, nb[6], nb[7], tf, tb);
     return acc;
 }
@@ -153,31 +157,28 @@ __device__ __forceinline__ Sp<R> prefetch_site(const SpinorRef<LQCD_F16N> &in, c
     Sp<R> acc = sp_zero<R>();
     R sc;
     Sp<R> psi;
-    // the spatial hops' weight (anisotropic operator), folded into the norm
-#define LQCD_SP(x) (g.aniso ? (x) * (R)g.cs : (x))
 #define LQCD_PF_LINK(mu, f) U.template decode<R>(lp.u[mu][f][0][i], lp.u[mu][f][1][i], lp.u[mu][f][2][i])
     psi = in.template load_scaled<R>(nb[0], sc);
     cp_async_wait<3>();
-    hop_values<0, FS, true>(acc, psi, LQCD_SP(sc), LQCD_PF_LINK(0, 0), false);
+    hop_values<0, FS, true>(acc, psi, sc * spatial_weight<R>(g), LQCD_PF_LINK(0, 0), false);
     psi = in.template load_scaled<R>(nb[1], sc);
-    hop_values<0, BS, false>(acc, psi, LQCD_SP(sc), LQCD_PF_LINK(0, 1), false);
+    hop_values<0, BS, false>(acc, psi, sc * spatial_weight<R>(g), LQCD_PF_LINK(0, 1), false);
     psi = in.template load_scaled<R>(nb[2], sc);
     cp_async_wait<2>();
-    hop_values<1, FS, true>(acc, psi, LQCD_SP(sc), LQCD_PF_LINK(1, 0), false);
+    hop_values<1, FS, true>(acc, psi, sc * spatial_weight<R>(g), LQCD_PF_LINK(1, 0), false);
     psi = in.template load_scaled<R>(nb[3], sc);
-    hop_values<1, BS, false>(acc, psi, LQCD_SP(sc), LQCD_PF_LINK(1, 1), false);
+    hop_values<1, BS, false>(acc, psi, sc * spatial_weight<R>(g), LQCD_PF_LINK(1, 1), false);
     psi = in.template load_scaled<R>(nb[4], sc);
     cp_async_wait<1>();
-    hop_values<2, FS, true>(acc, psi, LQCD_SP(sc), LQCD_PF_LINK(2, 0), false);
+    hop_values<2, FS, true>(acc, psi, sc * spatial_weight<R>(g), LQCD_PF_LINK(2, 0), false);
     psi = in.template load_scaled<R>(nb[5], sc);
-    hop_values<2, BS, false>(acc, psi, LQCD_SP(sc), LQCD_PF_LINK(2, 1), false);
+    hop_values<2, BS, false>(acc, psi, sc * spatial_weight<R>(g), LQCD_PF_LINK(2, 1), false);
     psi = in.template load_scaled<R>(nb[6], sc);
     cp_async_wait<0>();
     hop_values<3, FS, true>(acc, psi, sc, LQCD_PF_LINK(3, 0), antip && tf);
     psi = in.template load_scaled<R>(nb[7], sc);
     hop_values<3, BS, false>(acc, psi, sc, LQCD_PF_LINK(3, 1), antip && tb);
 #undef LQCD_PF_LINK
-#undef LQCD_SP
     return acc;
 }
 

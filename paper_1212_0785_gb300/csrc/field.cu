@@ -38,10 +38,13 @@ lqcd_status cuda_fail(cudaError_t e, const char *what, const char *file, int lin
 
 // ------------------------------------------------------------------ kernel timers
 
-static const char *k_class_names[K_NCLASS] = {"dslash_f64",  "dslash_f32",  "dslash_f16n",   "dslash_bf16",
-                                              "dslash_df64", "gauge_force", "fermion_force", "link_update"};
+static const char *k_class_names[K_NCLASS] = {"dslash_f64",    "dslash_f32",  "dslash_f16n",
+                                              "dslash_bf16",   "dslash_df64", "gauge_force",
+                                              "fermion_force", "link_update", "dslash_f16n_plain"};
 static std::mutex g_timer_mu;
 static std::atomic<uint32_t> g_timer_mask{0}; // bit k: class k is timed
+static std::atomic<int> g_timer_every{1};      // time one launch in every g_timer_every of a class
+static std::atomic<uint64_t> g_timer_seen[K_NCLASS];
 static std::vector<cudaEvent_t> g_event_pool;
 struct PendingTiming {
     int cls;
@@ -71,6 +74,8 @@ static cudaEvent_t pool_event()
 KernelTimer::KernelTimer(int c, cudaStream_t st, double nbytes) : cls(c), s(st), bytes(nbytes)
 {
     if (!((g_timer_mask.load(std::memory_order_relaxed) >> c) & 1u)) return;
+    const int every = g_timer_every.load(std::memory_order_relaxed);
+    if (every > 1 && g_timer_seen[c].fetch_add(1, std::memory_order_relaxed) % (uint64_t)every != 0) return;
     std::lock_guard<std::mutex> lk(g_timer_mu);
     a = pool_event();
     b = pool_event();
@@ -194,6 +199,8 @@ Geo make_geo(const lqcd_lattice &lat)
     g.xi0 = eff_xi0(lat);
     g.cs = eff_nu(lat) / g.xi0;
     g.aniso = (g.xi0 != 1.0 || g.cs != 1.0) ? 1 : 0;
+    g.csf = (float)g.cs;
+    g.cs_lo = (float)(g.cs - (double)g.csf);
     return g;
 }
 
@@ -284,11 +291,25 @@ lqcd_status field_alloc_df(const lqcd_lattice *lat, lqcd_kind kind, lqcd_field *
 // ------------------------------------------------------------------ host layout permutation kernels
 
 // canonical gauge AoS [site][mu][row][col][re,im] <-> device SoA
+// AoS host layout of a gauge field: links in (lexicographic site, mu) order,
+// 18 doubles each (row-major complex 3x3).  A block of GA_LINKS threads moves
+// GA_LINKS consecutive links through shared memory, so the AoS side is read
+// (or written) contiguously by the whole block -- which matters when it is
+// pinned host memory accessed directly over the host link -- and each thread
+// converts its own link.
+constexpr int GA_LINKS = 128;
+
 template <lqcd_prec P>
-__global__ void gauge_from_aos(GaugeRef<P> U, const double *aos, Geo g, int V)
+__global__ void __launch_bounds__(GA_LINKS) gauge_from_aos(GaugeRef<P> U, const double *aos, Geo g, int V)
 {
-    long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (t >= 4L * V) return;
+    __shared__ double sh[GA_LINKS * 18];
+    const long t0 = (long)blockIdx.x * GA_LINKS;
+    const int nl = (int)min((long)GA_LINKS, 4L * V - t0);
+    const double *src = aos + t0 * 18;
+    for (int i = threadIdx.x; i < nl * 18; i += GA_LINKS) sh[i] = src[i];
+    __syncthreads();
+    if ((int)threadIdx.x >= nl) return;
+    const long t = t0 + threadIdx.x;
     int lex = (int)(t >> 2), mu = (int)(t & 3);
     int c[4], r = lex;
     for (int m = 0; m < 4; m++) {
@@ -296,31 +317,37 @@ __global__ void gauge_from_aos(GaugeRef<P> U, const double *aos, Geo g, int V)
         r /= g.L[m];
     }
     int par = (c[0] + c[1] + c[2] + c[3]) & 1;
-    int cb = lex >> 1;
-    const double *src = aos + ((size_t)lex * 4 + mu) * 18;
+    const double *e = sh + threadIdx.x * 18;
     M3<double> u;
-    for (int k = 0; k < 9; k++) u.e[k / 3][k % 3] = cx<double>(src[2 * k], src[2 * k + 1]);
-    U.store(mu, par, cb, u);
+    for (int k = 0; k < 9; k++) u.e[k / 3][k % 3] = cx<double>(e[2 * k], e[2 * k + 1]);
+    U.store(mu, par, lex >> 1, u);
 }
 
 template <lqcd_prec P>
-__global__ void gauge_to_aos(GaugeRef<P> U, double *aos, Geo g, int V)
+__global__ void __launch_bounds__(GA_LINKS) gauge_to_aos(GaugeRef<P> U, double *aos, Geo g, int V)
 {
-    long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (t >= 4L * V) return;
-    int lex = (int)(t >> 2), mu = (int)(t & 3);
-    int c[4], r = lex;
-    for (int m = 0; m < 4; m++) {
-        c[m] = r % g.L[m];
-        r /= g.L[m];
+    __shared__ double sh[GA_LINKS * 18];
+    const long t0 = (long)blockIdx.x * GA_LINKS;
+    const int nl = (int)min((long)GA_LINKS, 4L * V - t0);
+    if ((int)threadIdx.x < nl) {
+        const long t = t0 + threadIdx.x;
+        int lex = (int)(t >> 2), mu = (int)(t & 3);
+        int c[4], r = lex;
+        for (int m = 0; m < 4; m++) {
+            c[m] = r % g.L[m];
+            r /= g.L[m];
+        }
+        int par = (c[0] + c[1] + c[2] + c[3]) & 1;
+        M3<double> u = U.template load<double>(mu, par, lex >> 1);
+        double *e = sh + threadIdx.x * 18;
+        for (int k = 0; k < 9; k++) {
+            e[2 * k] = u.e[k / 3][k % 3].re;
+            e[2 * k + 1] = u.e[k / 3][k % 3].im;
+        }
     }
-    int par = (c[0] + c[1] + c[2] + c[3]) & 1;
-    M3<double> u = U.template load<double>(mu, par, lex >> 1);
-    double *dst = aos + ((size_t)lex * 4 + mu) * 18;
-    for (int k = 0; k < 9; k++) {
-        dst[2 * k] = u.e[k / 3][k % 3].re;
-        dst[2 * k + 1] = u.e[k / 3][k % 3].im;
-    }
+    __syncthreads();
+    double *dst = aos + t0 * 18;
+    for (int i = threadIdx.x; i < nl * 18; i += GA_LINKS) dst[i] = sh[i];
 }
 
 __global__ void mom_from_aos(MomRef P, const double *aos, Geo g, int V, int to_aos)
@@ -405,18 +432,38 @@ static size_t host_doubles(const lqcd_field *f)
     return 0;
 }
 
+// the device address of pinned (page-locked, mapped) host memory, else NULL
+static double *mapped_host(double *host)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer ? (double *)a.devicePointer : nullptr;
+}
+
+// Host <-> device with the layout change done by a kernel.  Pinned host
+// memory is read or written by that kernel directly (no device staging copy:
+// one pass over the host link); pageable memory goes through a device buffer
+// and one copy.
 static lqcd_status transfer(lqcd_field *f, double *host, bool upload, cudaStream_t s)
 {
     size_t n = host_doubles(f);
     DevBuf tmp;
-    LQCD_TRY(tmp.alloc(n * sizeof(double), s));
-    double *d = (double *)tmp.p;
+    double *d = mapped_host(host);
+    const bool staged = d == nullptr;
+    if (staged) {
+        LQCD_TRY(tmp.alloc(n * sizeof(double), s));
+        d = (double *)tmp.p;
+    }
     Geo g = make_geo(f->lat);
     int V = 2 * f->Vh;
     const int B = 256;
-    if (upload) LQCD_CUDA(cudaMemcpyAsync(d, host, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (upload && staged) LQCD_CUDA(cudaMemcpyAsync(d, host, n * sizeof(double), cudaMemcpyHostToDevice, s));
     switch (f->kind) {
     case LQCD_GAUGE: {
+        const int B = GA_LINKS;
         int nb = nblocks_for(4L * V, B);
         switch (f->prec) {
         case LQCD_F64:
@@ -469,7 +516,7 @@ static lqcd_status transfer(lqcd_field *f, double *host, bool upload, cudaStream
         break;
     }
     LQCD_LAUNCHED();
-    if (!upload) LQCD_CUDA(cudaMemcpyAsync(host, d, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (!upload && staged) LQCD_CUDA(cudaMemcpyAsync(host, d, n * sizeof(double), cudaMemcpyDeviceToHost, s));
     LQCD_CUDA(cudaStreamSynchronize(s));
     return LQCD_OK;
 }
@@ -595,13 +642,31 @@ __global__ void eta_refresh_kernel(SpinorRef<LQCD_F64> E, Geo g, uint32_t seed, 
 // U <- exp(i c P) U on every link (link_update_one), one thread per link
 template <lqcd_prec PS, bool FAST>
 __global__ void link_update_kernel(GaugeRef<LQCD_F64> U, MomRef P, double c, GaugeRef<PS> Us, GaugeRef<LQCD_F32> Uf,
-                                   GaugeRef<PREC_DF> Udf, int Vh, int write_sloppy, int write_f32)
+                                   GaugeRef<PREC_DF> Udf, int Vh, int write_sloppy, int write_f32, int write_f64)
 {
     long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (t >= 8L * Vh) return;
     int cb = (int)(t % Vh);
     int mp = (int)(t / Vh);
-    link_update_one<PS, FAST>(U, P, c, Us, Uf, Udf, mp >> 1, mp & 1, cb, write_sloppy, write_f32);
+    link_update_one<PS, FAST>(U, P, c, Us, Uf, Udf, mp >> 1, mp & 1, cb, write_sloppy, write_f32, write_f64);
+}
+
+// U = the float-float links, per link entry (double) hi + (double) lo: bitwise
+// what the link update writes when it writes the FP64 links itself
+__global__ void links_from_df_kernel(GaugeRef<LQCD_F64> U, GaugeRef<PREC_DF> Udf, int Vh)
+{
+    long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= 8L * Vh) return;
+    const int cb = (int)(t % Vh), mp = (int)(t / Vh);
+    U.store(mp >> 1, mp & 1, cb, Udf.load<double>(mp >> 1, mp & 1, cb));
+}
+
+lqcd_status links_from_df(lqcd_field *U, const lqcd_field *Udf, cudaStream_t s)
+{
+    links_from_df_kernel<<<nblocks_for(8L * U->Vh, 128), 128, 0, s>>>(gauge_ref<LQCD_F64>(U),
+                                                                        gauge_ref<PREC_DF>(Udf), U->Vh);
+    LQCD_LAUNCHED();
+    return LQCD_OK;
 }
 
 __global__ void reunitarize_kernel(GaugeRef<LQCD_F64> U, int Vh, double *partials)
@@ -851,9 +916,11 @@ lqcd_status reunitarize_dev(lqcd_field *U, double *dst_dev, DevBuf &part, cudaSt
 
 template <bool FAST>
 static lqcd_status launch_link_update(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *Us, lqcd_field *Uf,
-                                      lqcd_field *Udf, cudaStream_t s, int bs = 128)
+                                      lqcd_field *Udf, cudaStream_t s, int bs = 128, bool write_f64 = true)
 {
     LQCD_REQUIRE(bs >= 32 && bs <= 256 && bs % 32 == 0, "link update: bad block size %d", bs);
+    LQCD_REQUIRE(write_f64 || (FAST && Udf), "link update: only the float-float copy can stand in for the FP64 links");
+    const int w64 = write_f64 ? 1 : 0;
     GaugeRef<PREC_DF> ud = Udf ? gauge_ref<PREC_DF>(Udf) : GaugeRef<PREC_DF>{nullptr, U->Vh};
     long n = 8L * U->Vh;
     int nb = nblocks_for(n, bs);
@@ -862,15 +929,15 @@ static lqcd_status launch_link_update(lqcd_field *U, const lqcd_field *P, double
     switch (Us ? Us->prec : LQCD_F32) {
     case LQCD_F32:
         link_update_kernel<LQCD_F32, FAST><<<nb, bs, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c,
-                                                              Us ? gauge_ref<LQCD_F32>(Us) : uf, uf, ud, U->Vh, Us ? 1 : 0, wf);
+                                                              Us ? gauge_ref<LQCD_F32>(Us) : uf, uf, ud, U->Vh, Us ? 1 : 0, wf, w64);
         break;
     case LQCD_F16N:
         link_update_kernel<LQCD_F16N, FAST><<<nb, bs, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c,
-                                                               gauge_ref<LQCD_F16N>(Us), uf, ud, U->Vh, 1, wf);
+                                                               gauge_ref<LQCD_F16N>(Us), uf, ud, U->Vh, 1, wf, w64);
         break;
     case LQCD_BF16:
         link_update_kernel<LQCD_BF16, FAST><<<nb, bs, 0, s>>>(gauge_ref<LQCD_F64>(U), mom_ref(P), c,
-                                                               gauge_ref<LQCD_BF16>(Us), uf, ud, U->Vh, 1, wf);
+                                                               gauge_ref<LQCD_BF16>(Us), uf, ud, U->Vh, 1, wf, w64);
         break;
     default: set_error("sloppy link copy must be 12-real F32/F16N/BF16"); return LQCD_EINVAL;
     }
@@ -879,18 +946,20 @@ static lqcd_status launch_link_update(lqcd_field *U, const lqcd_field *P, double
 }
 
 lqcd_status link_update_dev(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *Us, lqcd_field *Uf, bool fast,
-                            cudaStream_t s, lqcd_field *Udf)
+                            cudaStream_t s, lqcd_field *Udf, bool write_f64 = true)
 {
     KernelTimer kt(K_LINK_UPDATE, s);
-    return fast ? launch_link_update<true>(U, P, c, Us, Uf, Udf, s, tuned_block(TK_LINK_UPDATE_F32, U->lat, 128))
+    return fast ? launch_link_update<true>(U, P, c, Us, Uf, Udf, s, tuned_block(TK_LINK_UPDATE_F32, U->lat, 128),
+                                           write_f64)
                 : launch_link_update<false>(U, P, c, Us, Uf, Udf, s);
 }
 
-// the FP32 molecular dynamics' link update with bs threads per block
+// the FP32 molecular dynamics' link update with bs threads per block, as the
+// mixed trajectory runs it (the FP64 links lag behind the float-float copy)
 lqcd_status link_update_block(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *Us, lqcd_field *Uf,
                               lqcd_field *Udf, int bs, cudaStream_t s)
 {
-    return launch_link_update<true>(U, P, c, Us, Uf, Udf, s, bs);
+    return launch_link_update<true>(U, P, c, Us, Uf, Udf, s, bs, Udf == nullptr);
 }
 
 lqcd_status momentum_refresh_dev(lqcd_field *P, uint32_t seed, uint32_t chain, uint32_t traj, cudaStream_t s)
@@ -936,19 +1005,38 @@ static lqcd_status timers_set(uint32_t mask)
         g_timer_bytes[k] = 0;
         g_timer_n[k] = 0;
     }
+    for (int k = 0; k < K_NCLASS; k++) g_timer_seen[k].store(0);
     g_timer_mask.store(mask);
     return LQCD_OK;
 }
 
 lqcd_status lqcd_kernel_timers(int enable) { return timers_set(enable ? (1u << K_NCLASS) - 1u : 0u); }
 
-lqcd_status lqcd_kernel_timers_only(const char *kernel_class)
+lqcd_status lqcd_kernel_timers_only(const char *kernel_classes)
 {
-    LQCD_REQUIRE(kernel_class, "kernel_timers_only: NULL class");
-    for (int k = 0; k < K_NCLASS; k++)
-        if (std::strcmp(kernel_class, k_class_names[k]) == 0) return timers_set(1u << k);
-    set_error("kernel_timers_only: unknown class '%s'", kernel_class);
-    return LQCD_EINVAL;
+    LQCD_REQUIRE(kernel_classes, "kernel_timers_only: NULL class");
+    uint32_t mask = 0;
+    const std::string list(kernel_classes);
+    size_t at = 0;
+    while (at <= list.size()) {
+        size_t end = list.find(',', at);
+        if (end == std::string::npos) end = list.size();
+        const std::string name = list.substr(at, end - at);
+        int cls = -1;
+        for (int k = 0; k < K_NCLASS; k++)
+            if (name == k_class_names[k]) cls = k;
+        LQCD_REQUIRE(cls >= 0, "kernel_timers_only: unknown class '%s'", name.c_str());
+        mask |= 1u << cls;
+        at = end + 1;
+    }
+    return timers_set(mask);
+}
+
+lqcd_status lqcd_kernel_timers_every(int every)
+{
+    LQCD_REQUIRE(every >= 1, "kernel_timers_every: every must be >= 1");
+    g_timer_every.store(every);
+    return LQCD_OK;
 }
 
 lqcd_status lqcd_kernel_timer_read(const char *kernel_class, double *total_ms, uint64_t *launches,

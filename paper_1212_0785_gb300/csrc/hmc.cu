@@ -25,7 +25,8 @@ lqcd_status plaquette_sum_df(const lqcd_field *Udf, double *dst_dev, DevBuf &par
 lqcd_status kinetic_sum(const lqcd_field *P, double *dst_dev, DevBuf &part, cudaStream_t s);
 lqcd_status reunitarize_dev(lqcd_field *U, double *dst_dev, DevBuf &part, cudaStream_t s);
 lqcd_status link_update_dev(lqcd_field *U, const lqcd_field *P, double c, lqcd_field *Us, lqcd_field *Uf, bool fast,
-                            cudaStream_t s, lqcd_field *Udf);
+                            cudaStream_t s, lqcd_field *Udf, bool write_f64);
+lqcd_status links_from_df(lqcd_field *U, const lqcd_field *Udf, cudaStream_t s);
 lqcd_status momentum_refresh_dev(lqcd_field *P, uint32_t seed, uint32_t chain, uint32_t traj, cudaStream_t s);
 lqcd_status eta_refresh_dev(lqcd_field *E, uint32_t seed, uint32_t chain, uint32_t traj, cudaStream_t s,
                             uint32_t purpose);
@@ -108,6 +109,7 @@ struct lqcd_hmc_state {
     lqcd::FieldPtr Ao32, Ye32, Bo32, X32;   // FP32 fermion-force temporaries (allocated on first use)
     lqcd::FieldPtr Uf;                      // FP32 12-real link copy for the FP32 molecular dynamics
     lqcd::FieldPtr Udf; // float-float link copy of the mixed solver, kept current by every link update
+    bool u_lags = false; // U (FP64) not yet written since link updates that wrote only the copies
     PfTerm pf[2];
     lqcd::CgWorkspace ws;
     lqcd::DevBuf part, scal;
@@ -371,8 +373,22 @@ static lqcd_status drift(lqcd_hmc_state *st, const lqcd_hmc_params *p, double c,
     LQCD_TRY(flush_kicks(st, p, s));
     bool fast = p->force_prec == LQCD_F32;
     st->md_time += c;
-    return link_update_dev(st->U, st->P.f, c, sloppy_links(st, p), fast ? st->Uf.f : nullptr, fast, s,
-                           sloppy_links(st, p) ? st->Udf.f : nullptr);
+    // with FP32 forces and the mixed solver the molecular dynamics reads only
+    // the link copies, so the FP64 links are written once, after it
+    // (sync_master_links), instead of at every update
+    lqcd_field *Udf = sloppy_links(st, p) ? st->Udf.f : nullptr;
+    const bool lag = fast && Udf;
+    if (lag) st->u_lags = true;
+    return link_update_dev(st->U, st->P.f, c, sloppy_links(st, p), fast ? st->Uf.f : nullptr, fast, s, Udf, !lag);
+}
+
+// the FP64 links from the float-float copy after molecular dynamics that
+// updated only the copies
+static lqcd_status sync_master_links(lqcd_hmc_state *st, cudaStream_t s)
+{
+    if (!st->u_lags) return LQCD_OK;
+    st->u_lags = false;
+    return links_from_df(st->U, st->Udf.f, s);
 }
 
 // scalars[0] = plaquette sum, [1] = sum p^2, [2] = fermion term.  With the
@@ -523,8 +539,11 @@ static lqcd_status integrate_level(lqcd_hmc_state *st, const lqcd_hmc_params *p,
 
 static lqcd_status integrate(lqcd_hmc_state *st, const lqcd_hmc_params *p, double t, int n, cudaStream_t s)
 {
-    LQCD_TRY(integrate_level(st, p, 0, t, n, s));
-    return flush_kicks(st, p, s);
+    lqcd_status rc = integrate_level(st, p, 0, t, n, s);
+    if (rc == LQCD_OK) rc = flush_kicks(st, p, s);
+    // the FP64 links hold the latest update even after a failure half way
+    const lqcd_status rs = sync_master_links(st, s);
+    return rc != LQCD_OK ? rc : rs;
 }
 
 static void reset_stats(lqcd_hmc_state *st)
@@ -844,7 +863,10 @@ static lqcd_status batch_kick(lqcd_batch *B, const lqcd_hmc_params *p, double c,
 static lqcd_status batch_drift(lqcd_batch *B, const lqcd_hmc_params *p, double c, cudaStream_t s)
 {
     if (B->md_shared) {
-        for (lqcd_hmc_state *st : B->chains) st->md_time += c; // (no kicks are queued in a batch)
+        for (lqcd_hmc_state *st : B->chains) {
+            st->md_time += c; // (no kicks are queued in a batch)
+            if (st->Udf.f) st->u_lags = true;
+        }
         return chains_link_update(B->md, c, p[0].cg.sloppy, s);
     }
     return per_chain(B, s, [&](size_t i, cudaStream_t cst) { return drift(B->chains[i], &p[i], c, cst); });
@@ -918,6 +940,10 @@ lqcd_status lqcd_batch_trajectory(lqcd_batch *B, const lqcd_hmc_params *params, 
     }
     LQCD_TRY(batch_md_tables(B, params, s));
     lqcd_status rc = batch_integrate(B, params, s);
+    for (lqcd_hmc_state *st : B->chains) { // the FP64 links from the float-float copies
+        const lqcd_status rs = sync_master_links(st, s);
+        if (rc == LQCD_OK) rc = rs;
+    }
     if (rc == LQCD_OK) {
         for (size_t i = 0; i < n; i++) LQCD_TRY(hamiltonian_parts(B->chains[i], &params[i], s));
         rc = batch_solve(B, params, s, true);

@@ -80,6 +80,7 @@ enum KernelClass {
     K_GAUGE_FORCE,
     K_FERMION_FORCE,
     K_LINK_UPDATE,
+    K_DSLASH_F16N_PLAIN, // the plain FP16+norm hops alone (also counted in K_DSLASH_F16N)
     K_NCLASS
 };
 struct KernelTimer { // RAII: events around the launches made while it lives
@@ -178,6 +179,7 @@ struct Geo {
     int aniso;  // the actions are anisotropic (xi0 != 1 or cs != 1)
     double xi0; // gauge: planes with t weigh xi0, spatial planes 1 / xi0
     double cs;  // fermion: weight nu / xi0 of the spatial hops
+    float csf, cs_lo; // cs rounded to FP32, and cs - csf (its float-float low part)
     int sY, sZ, sT; // checkerboard strides of y, z, t
     FastDiv dLxh, dLy, dLz;
 };
@@ -302,6 +304,21 @@ struct Hs { // projected half spinor: 2 spin x 3 colour
     Cx<R> c[2][3];
 };
 
+// the spatial hops' weight nu / xi0 of the anisotropic operator in the
+// working precision (1 when isotropic)
+template <typename R>
+__device__ __forceinline__ R spatial_weight(const Geo &g);
+template <>
+__device__ __forceinline__ float spatial_weight<float>(const Geo &g)
+{
+    return g.csf;
+}
+template <>
+__device__ __forceinline__ double spatial_weight<double>(const Geo &g)
+{
+    return g.cs;
+}
+
 template <typename R>
 __device__ __forceinline__ Sp<R> sp_zero()
 {
@@ -311,6 +328,16 @@ __device__ __forceinline__ Sp<R> sp_zero()
 #pragma unroll
         for (int b = 0; b < 3; b++) s.c[a][b] = cx<R>(0, 0);
     return s;
+}
+
+// s *= w, every component
+template <typename R>
+__device__ __forceinline__ void sp_scale(Sp<R> &s, R w)
+{
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) s.c[a][b] = cx<R>(w * s.c[a][b].re, w * s.c[a][b].im);
 }
 
 template <typename R>

@@ -59,14 +59,6 @@ __device__ __forceinline__ M3<Df> reunit_rows_df(const M3<float> &e)
     return u;
 }
 
-// U <- exp(i c P) U.  FAST (the mixed-precision trajectory): the exponential
-// by Cayley-Hamilton in FP32, re-unitarized and multiplied onto the links in
-// float-float arithmetic (~48 bits, on the FP32 pipes), so that the FP64 links
-// stay in SU(3) to ~1e-14 per update; otherwise everything in FP64.  The new
-// links are also written to the 12-real copies Us (solver precision) and Uf
-// (FP32) and to the float-float copy Udf (the solver's accurate residual) when
-// those are given; a given Udf is also the FAST product's input (it holds the
-// current links), which spares the FP64 split of U.
 // U_mu(x) <- exp(i c P_mu(x)) U_mu(x) for the link (mu, par, cb).  FAST (the
 // mixed-precision trajectory): the exponential by Cayley-Hamilton in FP32,
 // re-unitarized and multiplied onto the links in float-float arithmetic (~48
@@ -75,12 +67,14 @@ __device__ __forceinline__ M3<Df> reunit_rows_df(const M3<float> &e)
 // 12-real copies Us (solver precision) and Uf (FP32) and to the float-float
 // copy Udf (the solver's accurate residual) when those are given; a given Udf
 // is also the FAST product's input (it holds the current links), which spares
-// the FP64 split of U.
+// the FP64 split of U.  write_f64 0 (FAST with Udf only): the FP64 links are
+// not written; they lag behind the float-float copy until the caller converts
+// it (the molecular dynamics reads only the copies).
 template <lqcd_prec PS, bool FAST>
 __device__ __forceinline__ void link_update_one(const GaugeRef<LQCD_F64> &U, const MomRef &P, double c,
                                                 const GaugeRef<PS> &Us, const GaugeRef<LQCD_F32> &Uf,
                                                 const GaugeRef<PREC_DF> &Udf, int mu, int par, int cb,
-                                                int write_sloppy, int write_f32)
+                                                int write_sloppy, int write_f32, int write_f64 = 1)
 {
     M3<double> nu;
     M3<float> nf; // rows 0, 1 of the new link rounded once, for the 12-real copies
@@ -115,7 +109,7 @@ __device__ __forceinline__ void link_update_one(const GaugeRef<LQCD_F64> &U, con
                     im.add_prod(E.e[i][k].im, u.e[k][j].re);
                 }
                 const Df vr = re.value(), vi = im.value();
-                nu.e[i][j] = cx<double>((double)vr, (double)vi);
+                if (write_f64) nu.e[i][j] = cx<double>((double)vr, (double)vi);
                 if (i < 2) nf.e[i][j] = cx<float>(vr.hi + vr.lo, vi.hi + vi.lo);
                 if (Udf.d) Udf.d[Udf.idx(mu, par, i * 3 + j, cb)] = make_float4(vr.hi, vr.lo, vi.hi, vi.lo);
             }
@@ -128,7 +122,7 @@ __device__ __forceinline__ void link_update_one(const GaugeRef<LQCD_F64> &U, con
         for (int i = 0; i < 2; i++)
             for (int j = 0; j < 3; j++) nf.e[i][j] = cx<float>((float)nu.e[i][j].re, (float)nu.e[i][j].im);
     }
-    U.store(mu, par, cb, nu);
+    if (write_f64) U.store(mu, par, cb, nu);
     if (write_sloppy || write_f32) {
         if (write_sloppy) Us.store(mu, par, cb, nf);
         if (write_f32) Uf.store(mu, par, cb, nf);

@@ -114,8 +114,10 @@ struct SvcGauge {
     DevBuf part, scal;
     bool ready = false;
     // solver work spaces of finished right-hand sides, reused by the next
-    // ones (at most one request's worth, kept outside the admission budget)
+    // ones (at most one request's worth; their bytes count against the
+    // admission budget like those of running right-hand sides)
     std::vector<std::unique_ptr<CgWorkspace>> idle;
+    size_t fixed_bytes = 0; // the link copies and shared temporaries above, once set up
 };
 
 constexpr size_t IDLE_WS_MAX = 12;
@@ -162,7 +164,8 @@ struct lqcd_service {
     std::unordered_map<uint64_t, std::unique_ptr<SvcRequest>> reqs;
     std::vector<SvcRequest *> running;
     uint64_t next_ticket = 1;
-    size_t bytes_in_use = 0;
+    size_t bytes_in_use = 0; // admitted right-hand sides and unreleased solutions
+    size_t idle_bytes = 0;   // the gauge fields' pools of idle solver work spaces
     bool stop = false;
     BatchSolver bs;
     std::thread worker;
@@ -172,14 +175,23 @@ struct lqcd_service {
 
 namespace lqcd {
 
-// device bytes one right-hand side holds while admitted (float-float solution
-// and source, FP32 solution increment, four sloppy vectors, the FP64 solution
-// halves and the reduction partials)
+// device bytes of one right-hand side's solver work space as
+// CgWorkspace::ensure allocates it when the float-float links and temporaries
+// are the gauge field's: float-float solution and source, FP32 solution
+// increment, four sloppy vectors, the scalars and the block partials
+static size_t ws_bytes(const lqcd_lattice &lat, lqcd_prec sloppy)
+{
+    const int Vh = make_geo(lat).Vh;
+    const size_t s = sloppy == LQCD_F32 ? 96 : (sloppy == LQCD_F16N ? 52 : 48);
+    const size_t np = (size_t)std::max(std::max(nblocks_for(Vh, 64), nblocks_for(Vh, CG_BLOCK)), 2048);
+    return (size_t)Vh * (2 * 192 + 96 + 4 * s) + sizeof(CgScalars) + np * sizeof(double) + 16 * sizeof(double);
+}
+
+// device bytes one right-hand side holds while admitted: its work space and
+// the FP64 solution halves
 static size_t rhs_bytes(const lqcd_lattice &lat, lqcd_prec sloppy)
 {
-    size_t Vh = (size_t)make_geo(lat).Vh;
-    double s = sloppy == LQCD_F32 ? 96 : (sloppy == LQCD_F16N ? 52 : 48);
-    return (size_t)(Vh * (2 * 192 + 96 + 4 * s + 2 * 192) + 65536);
+    return ws_bytes(lat, sloppy) + (size_t)make_geo(lat).Vh * 2 * 192;
 }
 
 static lqcd_status gauge_setup(lqcd_service *S, SvcGauge &g)
@@ -204,6 +216,13 @@ static lqcd_status gauge_setup(lqcd_service *S, SvcGauge &g)
         LQCD_CUDA(cudaMemsetAsync(f->data, 0, f->bytes, s));
     LQCD_TRY(g.part.alloc(sizeof(double) * (nblocks_for(make_geo(lat).Vh, 256) + 1), s));
     LQCD_TRY(g.scal.alloc(sizeof(double) * 4, s));
+    size_t fixed = g.shared.bytes() + g.part.bytes + g.scal.bytes;
+    for (const FieldPtr *f : {&g.Us, &g.Udf, &g.bo, &g.bp, &g.to, &g.src, &g.bo_df, &g.xo_df, &g.mxe_df})
+        fixed += f->f->bytes + f->f->norm_bytes;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        g.fixed_bytes = fixed;
+    }
     g.ready = true;
     return LQCD_OK;
 }
@@ -311,6 +330,8 @@ static lqcd_status admit(lqcd_service *S, SvcRequest &r)
         if (!g.idle.empty()) {
             h->ws = std::move(g.idle.back());
             g.idle.pop_back();
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->idle_bytes -= ws_bytes(lat, S->prm.cg.sloppy);
         } else {
             h->ws.reset(new CgWorkspace());
         }
@@ -390,6 +411,7 @@ static void finish_request(lqcd_service *S, SvcRequest &r, lqcd_status st)
     o.iters = 0;
     o.refinements = 0;
     o.true_rel_res_max = 0;
+    size_t idle_added = 0;
     for (auto &h : r.rhs) {
         o.iters += h->iters;
         o.refinements += h->refinements;
@@ -398,12 +420,16 @@ static void finish_request(lqcd_service *S, SvcRequest &r, lqcd_status st)
         // the solver fields go back to the gauge field's pool (or are freed);
         // the solution halves stay until release
         SvcGauge &g = *S->gauges[r.req.gauge];
-        if (h->ws && g.idle.size() < IDLE_WS_MAX) g.idle.push_back(std::move(h->ws));
+        if (h->ws && h->ws->ready && g.idle.size() < IDLE_WS_MAX) {
+            g.idle.push_back(std::move(h->ws));
+            idle_added += ws_bytes(g.U->lat, S->prm.cg.sloppy);
+        }
         h->ws.reset();
     }
     o.queue_s = std::chrono::duration<double>(r.t_admit - r.t_submit).count();
     o.latency_s = std::chrono::duration<double>(r.t_done - r.t_submit).count();
     std::lock_guard<std::mutex> lk(S->mu);
+    S->idle_bytes += idle_added;
     S->bytes_in_use -= r.bytes;
     r.bytes = (size_t)r.req.nrhs * 2 * 192 * (size_t)make_geo(S->gauges[r.req.gauge]->U->lat).Vh;
     S->bytes_in_use += r.bytes; // the solutions until lqcd_solve_release
@@ -413,18 +439,47 @@ static void finish_request(lqcd_service *S, SvcRequest &r, lqcd_status st)
 
 static lqcd_status worker_step(lqcd_service *S)
 {
-    // admit in arrival order while the budget allows (a request alone always runs)
+    // admit in arrival order while the budget allows (a request alone always
+    // runs).  The budget covers the admitted right-hand sides, the unreleased
+    // solutions and the pooled idle work spaces; a request reuses its own
+    // gauge field's idle work spaces, and those of other gauge fields are
+    // freed when the request would not fit beside them.
     std::vector<SvcRequest *> admitted;
+    std::vector<std::unique_ptr<CgWorkspace>> evicted;
     {
         std::unique_lock<std::mutex> lk(S->mu);
+        std::vector<size_t> claimed(S->gauges.size(), 0);
         while (!S->queue.empty()) {
             SvcRequest *r = S->queue.front();
-            size_t need = r->bytes;
+            const size_t need = r->bytes;
+            const int gi = r->req.gauge;
+            SvcGauge &gr = *S->gauges[gi];
+            const size_t wsb = ws_bytes(gr.U->lat, S->prm.cg.sloppy);
+            // the idle work spaces this request will take (those not claimed
+            // by a request admitted before it in this pass)
+            const size_t take = std::min(gr.idle.size() - claimed[gi], (size_t)r->req.nrhs);
             bool alone = S->running.empty() && admitted.empty();
-            bool fits = S->bytes_in_use + need <= S->prm.hbm_budget;
+            bool fits = S->bytes_in_use + need <= S->prm.hbm_budget; // once the other idle work spaces are freed
             bool rhs_ok = S->prm.max_active_rhs <= 0 ||
                           (int)S->bs.active.size() + r->req.nrhs <= S->prm.max_active_rhs;
             if (!alone && !(fits && rhs_ok)) break;
+            claimed[gi] += take;
+            // free idle work spaces, other gauge fields' first, then the
+            // unclaimed ones of this gauge field, while the resident total
+            // would exceed the budget
+            auto over = [&] { return S->bytes_in_use + need + S->idle_bytes - take * wsb > S->prm.hbm_budget; };
+            for (int pass = 0; pass < 2; pass++)
+                for (size_t k = 0; k < S->gauges.size(); k++) {
+                    if ((pass == 0) == ((int)k == gi)) continue;
+                    SvcGauge &g = *S->gauges[k];
+                    const size_t b = ws_bytes(g.U->lat, S->prm.cg.sloppy);
+                    // admissions take work spaces from the back of a pool
+                    while (g.idle.size() > claimed[k] && over()) {
+                        evicted.push_back(std::move(g.idle.front()));
+                        g.idle.erase(g.idle.begin());
+                        S->idle_bytes -= b;
+                    }
+                }
             S->queue.pop_front();
             S->bytes_in_use += need;
             r->admitted = true;
@@ -437,6 +492,7 @@ static lqcd_status worker_step(lqcd_service *S)
             return LQCD_OK;
         }
     }
+    evicted.clear(); // freed before the admissions allocate
     for (SvcRequest *r : admitted) {
         lqcd_status rc = admit(S, *r);
         if (rc != LQCD_OK) {
@@ -604,6 +660,16 @@ lqcd_status lqcd_solve_release(lqcd_service *S, uint64_t ticket)
         S->cv.notify_all();
     }
     return LQCD_OK; // r's fields are freed here
+}
+
+lqcd_status lqcd_service_bytes(lqcd_service *S, size_t *counted, size_t *fixed)
+{
+    LQCD_REQUIRE(S && counted && fixed, "service_bytes: NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    *counted = S->bytes_in_use + S->idle_bytes;
+    *fixed = 0;
+    for (auto &g : S->gauges) *fixed += g->fixed_bytes;
+    return LQCD_OK;
 }
 
 lqcd_status lqcd_service_destroy(lqcd_service *S)

@@ -12,8 +12,7 @@
 namespace lqcd {
 
 // launchers with an explicit block size (dslash.cu, force.cu, field.cu)
-lqcd_status dslash_packed_plain_block(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int block,
-                                      cudaStream_t s);
+int dslash_packed_block_override(int block); // 0: the table's choice
 lqcd_status gauge_force_block(lqcd_field *P, const lqcd_field *U, const lqcd_field *Uf, double cf, lqcd_prec arith,
                               int block, cudaStream_t s);
 lqcd_status fermion_force_link_block(lqcd_field *P, const lqcd_field *Uf, const lqcd_field *Xe, const lqcd_field *Ao,
@@ -82,14 +81,16 @@ static lqcd_status time_launches(F f, int block, cudaStream_t s, double *ms)
     return rc;
 }
 
+// per_call: kernel launches f makes (the table stores time per launch)
 template <class F>
-static lqcd_status tune_one(int k, const lqcd_lattice &lat, F f, cudaStream_t s)
+static lqcd_status tune_one(int k, const lqcd_lattice &lat, F f, cudaStream_t s, int per_call = 1)
 {
     TuneEntry e;
     double best = 0;
     for (int block : CANDIDATES[k]) {
         double ms = 0;
         LQCD_TRY(time_launches(f, block, s, &ms));
+        ms /= per_call;
         e.ms.emplace_back(block, ms);
         if (e.block == 0 || ms < best) e.block = block, best = ms;
     }
@@ -146,12 +147,35 @@ lqcd_status lqcd_autotune(const lqcd_lattice *lat, const char *path, void *strea
     LQCD_TRY(lqcd_dslash(Ao.f, Uf.f, Xe.f, 0, s));
     LQCD_TRY(lqcd_field_copy(Ye.f, Xe.f, s));
     LQCD_TRY(lqcd_dslash(Bo.f, Uf.f, Ye.f, 1, s));
-    FieldPtr in16, out16;
-    LQCD_TRY(lqcd_field_alloc(lat, LQCD_SPINOR_EVEN, LQCD_F16N, 0, &in16.f));
-    LQCD_TRY(lqcd_field_copy(in16.f, he.f, s));
-    LQCD_TRY(lqcd_field_alloc(lat, LQCD_SPINOR_ODD, LQCD_F16N, 0, &out16.f));
-    LQCD_TRY(tune_one(TK_HOP_F16N, *lat,
-                      [&](int b) { return dslash_packed_plain_block(out16.f, Us.f, in16.f, b, s); }, s));
+    // the FP16+norm hopping term is timed as the solver uses it: one
+    // application of Mhat^dag Mhat, two plain hops and two with the fused
+    // axpy and norm reduction whose last block sums the block partials
+    // (cg_finish into scratch scalars; time per hop = a quarter of it)
+    FieldPtr p16, o16, t16, u16;
+    DevBuf part, fin;
+    LQCD_TRY(lqcd_field_alloc(lat, LQCD_SPINOR_EVEN, LQCD_F16N, 0, &p16.f));
+    LQCD_TRY(lqcd_field_copy(p16.f, he.f, s));
+    LQCD_TRY(lqcd_field_alloc(lat, LQCD_SPINOR_ODD, LQCD_F16N, 0, &o16.f));
+    LQCD_TRY(lqcd_field_alloc(lat, LQCD_SPINOR_EVEN, LQCD_F16N, 0, &t16.f));
+    LQCD_TRY(lqcd_field_alloc(lat, LQCD_SPINOR_EVEN, LQCD_F16N, 0, &u16.f));
+    LQCD_TRY(part.alloc(sizeof(double) * (size_t)nblocks_for(make_geo(*lat).Vh, 64), s));
+    LQCD_TRY(fin.alloc(sizeof(CgScalars), s));
+    LQCD_CUDA(cudaMemsetAsync(fin.p, 0, sizeof(CgScalars), s));
+    const int prev_form = dslash_form_set(2);
+    const double k2 = 0.15 * 0.15;
+    lqcd_status rc = tune_one(TK_HOP_F16N, *lat, [&](int b) {
+        dslash_packed_block_override(b);
+        double *pp = (double *)part.p;
+        CgScalars *fs = (CgScalars *)fin.p;
+        lqcd_status r = dslash_plain(o16.f, Us.f, p16.f, 0, nullptr, s);
+        if (r == LQCD_OK) r = dslash_xpay(t16.f, Us.f, o16.f, 0, p16.f, -k2, pp, nullptr, s, fs);
+        if (r == LQCD_OK) r = dslash_plain(o16.f, Us.f, t16.f, 1, nullptr, s);
+        if (r == LQCD_OK) r = dslash_xpay(u16.f, Us.f, o16.f, 1, t16.f, -k2, pp, nullptr, s, fs);
+        dslash_packed_block_override(0);
+        return r;
+    }, s, 4);
+    dslash_form_set(prev_form);
+    LQCD_TRY(rc);
     LQCD_TRY(tune_one(TK_GAUGE_FORCE_F32, *lat,
                       [&](int b) { return gauge_force_block(P.f, U.f, Uf.f, 1e-3, LQCD_F32, b, s); }, s));
     LQCD_TRY(tune_one(TK_GAUGE_FORCE_F64, *lat,

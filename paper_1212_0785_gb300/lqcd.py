@@ -159,7 +159,9 @@ _SIGS = {
     "lqcd_solve_poll": (_i, [_vp, ctypes.c_uint64, ctypes.POINTER(SolveResult)]),
     "lqcd_solve_solution": (_i, [_vp, ctypes.c_uint64, _i, _pp, _pp]),
     "lqcd_solve_release": (_i, [_vp, ctypes.c_uint64]),
+    "lqcd_service_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
     "lqcd_service_destroy": (_i, [_vp]),
+    "lqcd_kernel_timers_every": (_i, [_i]),
 }
 
 _lock = threading.Lock()
@@ -208,12 +210,14 @@ def launch_count() -> int:
 
 
 KERNEL_CLASSES = ("dslash_f64", "dslash_f32", "dslash_f16n", "dslash_bf16", "dslash_df64", "gauge_force",
-                  "fermion_force", "link_update")
+                  "fermion_force", "link_update", "dslash_f16n_plain")
 
 
-def kernel_timers(enable: bool, only: str | None = None):
+def kernel_timers(enable: bool, only: str | None = None, every: int = 1):
     """Enable (clearing the totals) or disable the library's per-class event
-    timers; only: time that one class alone"""
+    timers; only: time those classes alone (comma-separated names); every:
+    time one launch in every `every` of each class"""
+    _check(lib().lqcd_kernel_timers_every(int(every)), "kernel_timers_every")
     if enable and only:
         _check(lib().lqcd_kernel_timers_only(only.encode()), "kernel_timers_only")
     else:
@@ -745,6 +749,13 @@ class Service:
 
     def release(self, ticket):
         _check(lib().lqcd_solve_release(self.h, ctypes.c_uint64(ticket)), "solve_release")
+
+    def bytes(self):
+        """(counted, fixed): the device bytes hbm_budget covers, and the gauge
+        fields' link copies and shared temporaries outside it"""
+        c, f = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(lib().lqcd_service_bytes(self.h, ctypes.byref(c), ctypes.byref(f)), "service_bytes")
+        return c.value, f.value
 
     def close(self):
         if self.h:

@@ -66,6 +66,16 @@ def test_null_arguments_are_rejected(L):
     assert L.lqcd_field_free(None) == lqcd.OK
 
 
+def test_timer_class_lists_are_checked_on_the_host(L):
+    """every name of a timer-class list is checked before the device is touched"""
+    for bad in (b"bogus", b"dslash_f16n,bogus", b"dslash_f16n,", b",dslash_f16n"):
+        assert L.lqcd_kernel_timers_only(bad) == lqcd.EINVAL, bad
+    assert b"unknown class" in L.lqcd_last_error()
+    assert L.lqcd_kernel_timers_only(None) == lqcd.EINVAL
+    assert L.lqcd_kernel_timer_read(b"bogus", None, None, None) == lqcd.EINVAL
+    assert "dslash_f16n_plain" in lqcd.KERNEL_CLASSES
+
+
 def test_allocator_hook_validation(L):
     a = lqcd.ALLOC_FN(lambda n, s, c: None)
     assert L.lqcd_set_allocator(a, lqcd.FREE_FN(), None) == lqcd.EINVAL

@@ -7,8 +7,7 @@ beta 5.8, kappa 0.1570, start exp(i 0.15 H) from Philox seed 3, CG true
 (one trajectory, Metropolis off so that the compared links are the evolved
 ones).  One chain of a batch of chains is held to the same bar.
 
-The tolerances follow from the FP32 molecular dynamics (the derivation is in
-the design doc, section 8a).  A force evaluation rounds the links and the solution
+The tolerances follow from the FP32 molecular dynamics.  A force evaluation rounds the links and the solution
 to FP32 and adds in FP32, so each of the 32 V momentum coefficients is moved by
 about 2^-24 |F| per evaluation, in no coherent direction; over tau = 1 with
 |F| ~ 1-3 and |P| ~ 1 that changes H1 by about 2e-7 sqrt(32 V), and every link

@@ -9,9 +9,16 @@ from tests.gpu_util import PARITY_DIMS, full_from_half, half, rel_err, upload_ga
 
 pytestmark = pytest.mark.gpu
 
-# relative error bounds of the low-precision dslash against FP64 (storage
-# rounding of links and spinors, FP32 arithmetic): see the derivation in the
-# design notes -- FP32 ~ 2^-24 x O(10), FP16+norm ~ 2^-11, BF16 ~ 2^-8
+# max|a - b| / max|b| of the low-precision hop against FP64.  Each output
+# real is a sum of 96 link x spinor products; each factor carries a storage
+# rounding of relative size u (FP16 2^-11, BF16 2^-8, FP32 2^-24; row 2 of a
+# 12-real link, rebuilt from rows 0 and 1, up to ~3u), the packed FP16 form
+# rounds each projected component once more (u), and the output is rounded
+# to storage (u of its site norm).  As a random walk of independent
+# roundings the expected maximum over a test lattice is ~3u of max|out|; the
+# bounds sit at ~6u (FP16 3e-3, BF16 2.5e-2).  FP32 adds its 96-term
+# arithmetic (~sqrt(96) 2^-24 typical): 2e-6.  A wrong sign, a transposed
+# operand or a dropped hop moves the output by O(max|out|).
 LOWPREC_TOL = {lqcd.F32: 2e-6, lqcd.F16N: 3e-3, lqcd.BF16: 2.5e-2}
 
 

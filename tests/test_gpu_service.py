@@ -106,6 +106,63 @@ def test_admission_by_footprint():
     assert tight[2][0]["queue_s"] >= tight[0][0]["latency_s"] * 0.5
 
 
+class LiveBytes:
+    """an allocator hook over PyTorch's caching allocator that tracks the live
+    device bytes the library holds and their peak"""
+
+    def __init__(self):
+        import torch
+        self.torch, self.live, self.sizes, self.peak = torch, 0, {}, 0
+
+    def alloc(self, nbytes, stream):
+        p = self.torch.cuda.caching_allocator_alloc(nbytes)
+        self.sizes[p] = nbytes
+        self.live += nbytes
+        self.peak = max(self.peak, self.live)
+        return p
+
+    def free(self, ptr, stream):
+        self.live -= self.sizes.pop(ptr)
+        self.torch.cuda.caching_allocator_delete(ptr)
+
+
+def test_device_bytes_stay_within_budget():
+    """the idle solver work spaces pooled for reuse count against hbm_budget:
+    with a budget of one 12-source request, requests on two 8^4 gauge fields
+    in turn keep the service's device bytes (everything the library
+    allocates, less the gauge fields' fixed link copies and temporaries)
+    within the budget plus the batch engine's small tables; the first field's
+    idle work spaces are freed to admit the second's request"""
+    dims = (8, 8, 8, 8)
+    Us = [lqcd.gauge_field(dims).upload(orc.gauge_start(dims, seed=30 + k, eps=0.25)) for k in range(2)]
+    Vh = int(np.prod(dims)) // 2
+    # one right-hand side: float-float solution and source, FP32 increment,
+    # four FP16+norm vectors, the FP64 solution halves, scalars and partials
+    one = Vh * (2 * 192 + 96 + 4 * 52 + 2 * 192) + 2048 * 8 + 4096
+    budget = 12 * one + one // 2
+    tables = 1 << 20
+    live = LiveBytes()
+    lqcd.set_allocator(live.alloc, live.free)
+    try:
+        svc = lqcd.Service(lqcd.service_params(tol=TOL, hbm_budget=budget))
+        ids = [svc.add_gauge(U) for U in Us]
+        for rnd in range(2):
+            for g in ids:
+                t = svc.submit(g, 0.152 + 0.002 * g, (1, 2, 3, rnd), 12)
+                r = svc.wait(t)
+                assert r["status"] == lqcd.OK and r["true_rel_res_max"] <= TOL
+                counted, fixed = svc.bytes()
+                assert 0 < counted <= budget
+                svc.release(t)
+        counted, fixed = svc.bytes()
+        assert 0 < counted <= budget  # the idle pool of the last field
+        assert fixed > 0 and live.peak - fixed <= budget + tables, (live.peak, fixed, budget)
+        svc.close()
+        assert live.live == 0
+    finally:
+        lqcd.set_allocator(None, None)
+
+
 def test_service_rejects_bad_requests():
     gauges = _gauges()[:1]
     with pytest.raises(lqcd.LqcdError):
