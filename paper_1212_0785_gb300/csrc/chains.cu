@@ -94,8 +94,9 @@ __global__ void __launch_bounds__(CB) chains_fermion_force_kernel(const ChainMd 
 }
 
 // the FP32 molecular dynamics' link update with its copies, per link
+// (registers capped at 128 like the single-chain kernel's)
 template <lqcd_prec PS>
-__global__ void chains_link_update_kernel(const ChainMd *d, const int2 *bmap, double step)
+__global__ void __launch_bounds__(CB, 4) chains_link_update_kernel(const ChainMd *d, const int2 *bmap, double step)
 {
     const int2 m = bmap[blockIdx.x];
     const ChainMd &c = d[m.x];

@@ -47,7 +47,10 @@ __device__ __forceinline__ void plain_body(SpinorRef<SP> out, SpinorRef<SP> in, 
     if (skip && *skip) return;
     int cb = blockIdx.x * BLOCK + threadIdx.x;
     if (cb >= g.Vh) return;
-    out.store(cb, site_value<R, SP, GP, DAG, FORM, BLOCK>(in, U, g, cb, out_par));
+    if constexpr (FORM == 2 && SP == LQCD_F16N && GP == LQCD_F16N && std::is_same<R, float>::value)
+        store_packed(out, cb, packed_acc<DAG, BLOCK>(in, U, g, cb, out_par));
+    else
+        out.store(cb, site_value<R, SP, GP, DAG, FORM, BLOCK>(in, U, g, cb, out_par));
 }
 
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, int FORM, int BLOCK = DS_BLOCK>

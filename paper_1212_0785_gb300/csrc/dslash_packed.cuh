@@ -12,9 +12,9 @@
 // pipe.  The two spin rows of a projected half spinor are then carried as
 // pairs: for colour j, re[j] = (row0.re, row1.re) and im[j] = (row0.im,
 // row1.im), so the SU(3) matrix times half spinor and the reconstruction of
-// spin rows 0, 1 (and, for z and t, rows 2, 3) act on both rows with one
-// packed instruction; the x and y hops reconstruct rows 2, 3 from the rows in
-// swapped order, which stays scalar.  Links are prefetched into shared memory
+// spin rows 0, 1 and 2, 3 act on both rows with one packed instruction (the
+// x and y hops take the pairs swapped), and so does the scaling of the stored
+// output by its norm.  Links are prefetched into shared memory
 // as in prefetch_site, and the directions, neighbours, boundary signs and
 // per-site norms are those of dslash_site.  The bits differ from forms 0 and
 // 1 by the FP16 rounding of the projection and the order of the FP32 products.
@@ -35,6 +35,7 @@ __device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b
 __device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 swp(float2 a) { return make_float2(a.y, a.x); }
 
 // U h (FWD) or U^dag h, both rows at once
 template <bool FWD>
@@ -68,6 +69,8 @@ __device__ __forceinline__ HsP mul_link_p(const M3<float> &u, const HsP &h)
 // acc += sc times the reconstruction of (1 + S gamma_mu) from its rows (o0, o1):
 //   rows 0, 1 += (o0, o1);   rows 2, 3 +=
 //   x: (-S i o1, -S i o0)   y: (S o1, -S o0)   z: (-S i o0, S i o1)   t: (S o0, S o1)
+// (the x and y hops take the rows in swapped order: the pairs are swapped
+// first, so every lane is the same fmaf as in scalar form)
 template <int MU, int S>
 __device__ __forceinline__ void accumulate_p(SpP &acc, const HsP &o, float sc)
 {
@@ -77,15 +80,11 @@ __device__ __forceinline__ void accumulate_p(SpP &acc, const HsP &o, float sc)
         acc.re[0][a] = fma2(bc(sc), o.re[a], acc.re[0][a]);
         acc.im[0][a] = fma2(bc(sc), o.im[a], acc.im[0][a]);
         if (MU == 0) { // -S i (x + i y) = S y - i S x, rows swapped
-            acc.re[1][a].x = fmaf(s, o.im[a].y, acc.re[1][a].x);
-            acc.re[1][a].y = fmaf(s, o.im[a].x, acc.re[1][a].y);
-            acc.im[1][a].x = fmaf(-s, o.re[a].y, acc.im[1][a].x);
-            acc.im[1][a].y = fmaf(-s, o.re[a].x, acc.im[1][a].y);
+            acc.re[1][a] = fma2(swp(o.im[a]), bc(s), acc.re[1][a]);
+            acc.im[1][a] = fma2(swp(o.re[a]), bc(-s), acc.im[1][a]);
         } else if (MU == 1) {
-            acc.re[1][a].x = fmaf(s, o.re[a].y, acc.re[1][a].x);
-            acc.re[1][a].y = fmaf(-s, o.re[a].x, acc.re[1][a].y);
-            acc.im[1][a].x = fmaf(s, o.im[a].y, acc.im[1][a].x);
-            acc.im[1][a].y = fmaf(-s, o.im[a].x, acc.im[1][a].y);
+            acc.re[1][a] = fma2(swp(o.re[a]), pk(s, -s), acc.re[1][a]);
+            acc.im[1][a] = fma2(swp(o.im[a]), pk(s, -s), acc.im[1][a]);
         } else if (MU == 2) {
             acc.re[1][a] = fma2(o.im[a], pk(s, -s), acc.re[1][a]);
             acc.im[1][a] = fma2(o.re[a], pk(-s, s), acc.im[1][a]);
@@ -139,8 +138,8 @@ __device__ __forceinline__ HsP load_project_h(const SpinorRef<LQCD_F16N> &in, in
 }
 
 template <bool DAG, int BLOCK = DS_BLOCK>
-__device__ __forceinline__ Sp<float> packed_site(const SpinorRef<LQCD_F16N> &in, const GaugeRef<LQCD_F16N> &U,
-                                                 const Geo &g, int cb, int out_par)
+__device__ __forceinline__ SpP packed_acc(const SpinorRef<LQCD_F16N> &in, const GaugeRef<LQCD_F16N> &U,
+                                          const Geo &g, int cb, int out_par)
 {
     __shared__ LinkPrefetchT<BLOCK> lp;
     const int i = threadIdx.x;
@@ -195,6 +194,14 @@ __device__ __forceinline__ Sp<float> packed_site(const SpinorRef<LQCD_F16N> &in,
         accumulate_p<3, BS>(acc, mul_link_p<false>(LQCD_PK_LINK(3, 1), hp), (antip && tb) ? -sc : sc);
     }
 #undef LQCD_PK_LINK
+    return acc;
+}
+
+template <bool DAG, int BLOCK = DS_BLOCK>
+__device__ __forceinline__ Sp<float> packed_site(const SpinorRef<LQCD_F16N> &in, const GaugeRef<LQCD_F16N> &U,
+                                                 const Geo &g, int cb, int out_par)
+{
+    const SpP acc = packed_acc<DAG, BLOCK>(in, U, g, cb, out_par);
     Sp<float> out;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
@@ -204,6 +211,38 @@ __device__ __forceinline__ Sp<float> packed_site(const SpinorRef<LQCD_F16N> &in,
         out.c[3][a] = cx<float>(acc.re[1][a].y, acc.im[1][a].y);
     }
     return out;
+}
+
+// SpinorRef<F16N>::store of the packed accumulator: the same norm (max
+// |component|), the same products value * (1 / norm) lane by lane (FP32x2),
+// the same FP16 rounding -- bitwise the same stored site
+__device__ __forceinline__ void store_packed(const SpinorRef<LQCD_F16N> &out, int cb, const SpP &acc)
+{
+    float m = 0.f;
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            m = fmaxf(fmaxf(m, fmaxf(fabsf(acc.re[h][a].x), fabsf(acc.im[h][a].x))),
+                      fmaxf(fabsf(acc.re[h][a].y), fabsf(acc.im[h][a].y)));
+    const float inv = m > 0.f ? 1.0f / m : 0.f;
+    SpP v;
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) v.re[h][a] = mul2(acc.re[h][a], bc(inv)), v.im[h][a] = mul2(acc.im[h][a], bc(inv));
+    // component c = spin * 3 + colour: spin 2h + lane, colour a
+    uint32_t w[12];
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            w[(2 * h) * 3 + a] = pack_h2(v.re[h][a].x, v.im[h][a].x);
+            w[(2 * h + 1) * 3 + a] = pack_h2(v.re[h][a].y, v.im[h][a].y);
+        }
+#pragma unroll
+    for (int k = 0; k < 3; k++) out.d[(size_t)k * out.Vh + cb] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+    out.norm[cb] = m;
 }
 
 } // namespace lqcd

@@ -639,9 +639,12 @@ __global__ void eta_refresh_kernel(SpinorRef<LQCD_F64> E, Geo g, uint32_t seed, 
 
 // ------------------------------------------------------------------ link update / reunitarize
 
-// U <- exp(i c P) U on every link (link_update_one), one thread per link
+// U <- exp(i c P) U on every link (link_update_one), one thread per link.
+// Registers capped at 128 (two blocks of 256, four of 128 per SM): uncapped it
+// took 168 (three blocks of 128) and ran 46.4 ms per 32^3x64 trajectory, capped
+// 40.9 ms in a same-box A/B (85 registers, with spills: 41.7 ms).
 template <lqcd_prec PS, bool FAST>
-__global__ void link_update_kernel(GaugeRef<LQCD_F64> U, MomRef P, double c, GaugeRef<PS> Us, GaugeRef<LQCD_F32> Uf,
+__global__ void __launch_bounds__(256, 2) link_update_kernel(GaugeRef<LQCD_F64> U, MomRef P, double c, GaugeRef<PS> Us, GaugeRef<LQCD_F32> Uf,
                                    GaugeRef<PREC_DF> Udf, int Vh, int write_sloppy, int write_f32, int write_f64)
 {
     long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
