@@ -18,6 +18,7 @@
 // kernel is a no-op while the flag is set.  The
 // host therefore synchronises only once per chunk of iterations, yet the
 // iteration count is exactly that of a per-iteration check.
+#include <atomic>
 #include <chrono>
 #include <cmath>
 
@@ -297,6 +298,7 @@ lqcd_status CgWorkspace::ensure(const lqcd_lattice &l, lqcd_prec sl, cudaStream_
 {
     if (ready && same_lattice(lat, l) && sloppy == sl) return LQCD_OK;
     ready = false;
+    bdf_of = nullptr;
     for (FieldPtr *f : {&mre_d[0], &mre_d[1], &mre_d[2], &mre_w[0], &mre_w[1], &mre_w[2], &mre_te, &mre_to}) {
         if (f->f) lqcd_field_free(f->f);
         f->f = nullptr;
@@ -591,7 +593,12 @@ lqcd_status CgRun::start_impl(cudaStream_t s)
                                                                        gauge_ref<LQCD_F64>(U), Vh);
             LQCD_LAUNCHED();
         }
-        LQCD_TRY((convert_spinor<LQCD_F64, PREC_DF, double>(w.bdf.f, b, s)));
+        if (!(b_stamp && w.bdf_of == b && w.bdf_stamp == b_stamp)) {
+            w.bdf_of = nullptr;
+            LQCD_TRY((convert_spinor<LQCD_F64, PREC_DF, double>(w.bdf.f, b, s)));
+            w.bdf_of = b;
+            w.bdf_stamp = b_stamp;
+        }
         LQCD_CUDA(cudaMemsetAsync(w.xs.f->data, 0, w.xs.f->bytes, s));
         if (prm.guess) { // r = b - A x0, accurately
             inf.accurate_residuals++;
@@ -748,13 +755,20 @@ lqcd_status CgRun::pause_decide(const CgScalars &h, cudaStream_t s)
     return launch_p_update(P, R, sc, s);
 }
 
+uint64_t new_content_stamp()
+{
+    static std::atomic<uint64_t> next{1};
+    return next.fetch_add(1, std::memory_order_relaxed);
+}
+
 lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, const lqcd_field *Us,
                         const lqcd_field *b, double kappa, const lqcd_cg_params &prm, lqcd_cg_info *info,
-                        cudaStream_t s, const MreInput *mre)
+                        cudaStream_t s, const MreInput *mre, uint64_t b_stamp)
 {
     LQCD_TRY(ws.ensure(x->lat, prm.sloppy, s));
     CgRun run;
     run.ws = &ws, run.x = x, run.U = U, run.Us = Us, run.b = b, run.kappa = kappa, run.prm = prm;
+    run.b_stamp = b_stamp;
     if (mre && prm.guess && prm.sloppy != LQCD_F64) {
         run.n_mre = std::min(mre->n, CgWorkspace::MRE_MAX + 1);
         for (int j = 0; j < run.n_mre; j++) run.mre_x[j] = mre->x[j];

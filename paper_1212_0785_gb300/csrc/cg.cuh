@@ -23,6 +23,10 @@ struct CgWorkspace {
     // mixed CG: the accurate solution, source, residual and operator
     // temporaries in float-float storage, and the float-float link copy
     FieldPtr Udf, xdf, bdf, rdf, t1df, t2df, tmpodf;
+    // bdf holds the float-float copy of the source b with stamp bdf_stamp
+    // (0: none), so repeated solves of an unchanged source skip the split
+    const lqcd_field *bdf_of = nullptr;
+    uint64_t bdf_stamp = 0;
     DevBuf sc, partials, scalars;
     // minimal residual extrapolation of the guess (mixed solves): FP32
     // directions d_j, their images w_j = A d_j and the operator temporaries
@@ -59,6 +63,9 @@ struct CgRun {
     const lqcd_field *U = nullptr, *Us = nullptr, *b = nullptr;
     double kappa = 0;
     lqcd_cg_params prm{};
+    // nonzero: a stamp of b's contents, new whenever they change; a solve of
+    // the same b and stamp as the workspace's last reuses its float-float copy
+    uint64_t b_stamp = 0;
     // optional minimal residual extrapolation of a mixed solve's guess x:
     // the last n_mre solutions (latest first, FP64), on links mre_links
     // (an FP32 12-real copy, or the FP64 links) for the FP32 products
@@ -114,7 +121,9 @@ struct MreInput {
 };
 lqcd_status cg_solve_ws(CgWorkspace &ws, lqcd_field *x, const lqcd_field *U, const lqcd_field *Us,
                         const lqcd_field *b, double kappa, const lqcd_cg_params &prm, lqcd_cg_info *info,
-                        cudaStream_t s, const MreInput *mre = nullptr);
+                        cudaStream_t s, const MreInput *mre = nullptr, uint64_t b_stamp = 0);
+// a stamp never handed out before (for CgRun::b_stamp)
+uint64_t new_content_stamp();
 
 // |v|^2 and Re<a,b> of FP64 fields into a device double (deterministic)
 lqcd_status spinor_dot_dev(const lqcd_field *a, const lqcd_field *b, double *dst_dev, DevBuf &part, cudaStream_t s);

@@ -80,6 +80,7 @@ struct PfTerm {
     lqcd::FieldPtr phi, X;
     lqcd::FieldPtr chi; // ratio action: the right-hand side W^dag phi of its solve
     bool have_guess = false; // X holds a solution for the current phi
+    uint64_t phi_stamp = 0;  // stamp of phi's contents (new at every refresh and public entry)
     bool last_ok = false;    // the last solve converged, at molecular-dynamics time last_t
     double last_t = -1;
     // solutions of this trajectory's solves and the molecular-dynamics times
@@ -92,6 +93,7 @@ struct PfTerm {
     {
         have_guess = last_ok = false;
         n_hist = 0;
+        phi_stamp = lqcd::new_content_stamp();
     }
 };
 
@@ -287,8 +289,9 @@ static lqcd_status solve(lqcd_hmc_state *st, PfTerm &t, const lqcd_hmc_params *p
     lqcd_cg_params cg = p->cg;
     MreInput mre;
     LQCD_TRY(prepare_guess(st, t, p, s, &cg.guess, &mre));
+    // phi is constant between refreshes: its float-float copy is made once
     lqcd_status rc = cg_solve_ws(st->ws, t.X.f, st->U, sloppy_links(st, p), b, kappa, cg, &info, s,
-                                 mre.n >= 2 ? &mre : nullptr);
+                                 mre.n >= 2 ? &mre : nullptr, b == t.phi.f ? t.phi_stamp : 0);
     LQCD_TRY(record_solution(st, t, p, rc, s));
     return count_solve(st, rc, info);
 }
@@ -621,6 +624,7 @@ lqcd_status lqcd_hmc_hamiltonian(lqcd_hmc_state *s, const lqcd_hmc_params *p, do
     LQCD_TRY(check_params(p));
     LQCD_REQUIRE(!hasenbusch(p) || s->eta_h.f, "hmc_hamiltonian: no Hasenbusch refresh has been done");
     LQCD_TRY(ensure_sloppy(s, p, (cudaStream_t)stream));
+    for (PfTerm &t : s->pf) t.phi_stamp = new_content_stamp(); // the caller may have written phi
     return hamiltonian(s, p, H, (cudaStream_t)stream);
 }
 
@@ -632,6 +636,7 @@ lqcd_status lqcd_md_step(lqcd_hmc_state *s, const lqcd_hmc_params *p, void *stre
     cudaStream_t st = (cudaStream_t)stream;
     LQCD_TRY(ensure_sloppy(s, p, st));
     s->pending[0] = s->pending[1] = 0;
+    for (PfTerm &t : s->pf) t.phi_stamp = new_content_stamp(); // the caller may have written phi
     return integrate(s, p, p->tau / p->nsteps, 1, st);
 }
 
@@ -767,6 +772,7 @@ static lqcd_status batch_solve(lqcd_batch *B, const lqcd_hmc_params *p, cudaStre
         }
         CgRun &r = runs[i];
         r.ws = &st->ws, r.x = t.X.f, r.U = st->U, r.Us = sloppy_links(st, &p[i]), r.b = t.phi.f;
+        r.b_stamp = t.phi_stamp;
         r.kappa = p[i].kappa;
         r.prm = p[i].cg;
         MreInput mre;
