@@ -339,27 +339,34 @@ def run_reference(args):
     line = {"metric": "trajectories/s", "value": value, "unit": "trajectories/s", "impl": "reference",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_block(args, "f64", "f64"), "cpu_baseline": cb,
+            "data": "synthetic", "config": config_block(args), "arithmetic": arithmetic_block(args, "f64", "f64", 0),
+            "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "trajectories/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-def config_block(args, sloppy, force_prec):
+def config_block(args):
+    """The workload both arms run: the same dict for ours and the oracle's."""
     c = dict(WORKLOAD)
     c["dims"] = list(args.dims)
     c["nsteps"] = args.nsteps
-    c["solver"] = ("fp64 CG" if sloppy == "f64" else
-                   f"reliable-update mixed CG: {sloppy} spinors + 12-real {sloppy} links, fp32 math, "
-                   f"float-float residual/solution, fp64 dot sums, delta {args.delta}")
-    c["forces"] = f"{force_prec} arithmetic"
-    k = int(getattr(args, "chrono", 0))
-    c["initial_guess"] = {0: "zero", 1: "previous solution (chronological)"}.get(
-        k, f"extrapolated through the last {k} solutions (chronological)"
-           + (", refined by minimal residual extrapolation" if getattr(args, "mre", 0) and sloppy != "f64" else ""))
     c["parallelism"] = f"replicas{args.gpus}" if args.gpus > 1 else "single_gpu"
     c["l2"] = "inputs larger than L2 (FP64 links 1.21 GB, spinors 0.2 GB)"
     return c
+
+
+def arithmetic_block(args, sloppy, force_prec, chrono):
+    """How an arm computes the workload: solver storage, force precision, initial guess."""
+    a = {"solver": ("fp64 CG" if sloppy == "f64" else
+                    f"reliable-update mixed CG: {sloppy} spinors + 12-real {sloppy} links, fp32 math, "
+                    f"float-float residual/solution, fp64 dot sums, delta {args.delta}"),
+         "forces": f"{force_prec} arithmetic"}
+    k = int(chrono)
+    a["initial_guess"] = {0: "zero", 1: "previous solution (chronological)"}.get(
+        k, f"extrapolated through the last {k} solutions (chronological)"
+           + (", refined by minimal residual extrapolation" if getattr(args, "mre", 0) and sloppy != "f64" else ""))
+    return a
 
 
 # ---------------------------------------------------------------- our arm
@@ -565,9 +572,11 @@ def run_ours(args):
             "dtype_detail": (f"f32 math ({args.sloppy} storage in the solver, {args.force_prec} forces); f64 master "
                              f"links/momenta, residuals, dots, link update, dH"),
             "data": "synthetic",
-            "config": dict(config_block(args, args.sloppy, args.force_prec), threads_per_block=tuned,
-                           dslash_form={0: "gathered", 1: "prefetched_links", 2: "prefetched_links_packed_f32x2"}.get(
-                               lqcd.dslash_form(), "?")),
+            "config": config_block(args),
+            "arithmetic": arithmetic_block(args, args.sloppy, args.force_prec, args.chrono),
+            "tuning": {"threads_per_block": tuned,
+                       "dslash_form": {0: "gathered", 1: "prefetched_links", 2: "prefetched_links_packed_f32x2"}.get(
+                           lqcd.dslash_form(), "?")},
             "gpu_launches": launches,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "fp64_gpu_path": fp64,
             "physics": {"acceptance": float(np.mean(acc)), "dH": [i["dH"] for i in infos],
@@ -862,7 +871,7 @@ def run_service(args):
     return 0
 
 
-def main(argv=None):
+def parse_args(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
@@ -900,6 +909,11 @@ def main(argv=None):
         args.steps = 5
     elif args.steps is None and args.workload == "chains64":
         args.steps = 2
+    return args
+
+
+def main(argv=None):
+    args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "fp64_16x32":

@@ -64,7 +64,10 @@ def test_reference_arm_prints_one_json_line():
     assert d["value"] > 0 and cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert cb["single_thread"]["cores"] == 1 and cb["single_thread"]["value"] > 0
     assert cb["host"]["nproc"] == os.cpu_count() and cb["host"]["model"]
-    assert d["config"]["forces"] == "f64 arithmetic" and d["config"]["solver"] == "fp64 CG"
+    assert d["arithmetic"]["forces"] == "f64 arithmetic" and d["arithmetic"]["solver"] == "fp64 CG"
+    assert d["arithmetic"]["initial_guess"] == "zero"
+    # the workload block is the one the GPU arm prints with the default arguments
+    assert d["config"] == bench.config_block(bench.parse_args([]))
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["config"]["workload"] == "nf2_wilson_hmc_32x32x32x64"
 
