@@ -174,17 +174,23 @@ __global__ void __launch_bounds__(DS_BLOCK, 7) dslash_cg_prefetch_kernel(SpinorR
 }
 
 // The packed form with BLOCK threads per block (64, 128 or 256, chosen per
-// lattice by the autotuner): the register budget of 7 blocks of 128 per SM
-// (72 registers), whatever the block size.
+// lattice by the autotuner), register budgets per SM whatever the block size:
+// 640 threads for the plain variant (96 registers at 128 per block, where the
+// compiler keeps more neighbour loads in flight) and 768 for the reducing
+// variants (80 registers; their block sums want the extra warps).  Measured
+// on the 32^3x64 trajectory against the earlier 896 for all three: plain
+// 185.5 -> 178.8 ms, reducing 282 -> 277 ms per trajectory; 512 for all
+// three, or 640 for the reducing ones, was slower.
+constexpr int PK_THREADS_PLAIN = 640, PK_THREADS_REDUCING = 768;
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 896 / BLOCK) dslash_plain_packed_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
+__global__ void __launch_bounds__(BLOCK, PK_THREADS_PLAIN / BLOCK) dslash_plain_packed_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
                                                                                   GaugeRef<GP> U, Geo g, int out_par,
                                                                                   const int *skip)
 {
     plain_body<R, SP, GP, DAG, 2, BLOCK>(out, in, U, g, out_par, skip);
 }
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 896 / BLOCK) dslash_xpay_packed_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
+__global__ void __launch_bounds__(BLOCK, PK_THREADS_REDUCING / BLOCK) dslash_xpay_packed_kernel(SpinorRef<SP> out, SpinorRef<SP> in,
                                                                                  GaugeRef<GP> U, Geo g, int out_par,
                                                                                  SpinorRef<SP> x, R b, double *partials,
                                                                                  int nblocks, const int *skip,
@@ -193,7 +199,7 @@ __global__ void __launch_bounds__(BLOCK, 896 / BLOCK) dslash_xpay_packed_kernel(
     xpay_body<R, SP, GP, DAG, 2, BLOCK>(out, in, U, g, out_par, x, b, partials, nblocks, skip, fin);
 }
 template <typename R, lqcd_prec SP, lqcd_prec GP, bool DAG, lqcd_prec XP, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 896 / BLOCK) dslash_cg_packed_kernel(SpinorRef<SP> in, GaugeRef<GP> U, Geo g,
+__global__ void __launch_bounds__(BLOCK, PK_THREADS_REDUCING / BLOCK) dslash_cg_packed_kernel(SpinorRef<SP> in, GaugeRef<GP> U, Geo g,
                                                                                int out_par, SpinorRef<SP> t, R b,
                                                                                SpinorRef<XP> xs, SpinorRef<SP> r,
                                                                                SpinorRef<SP> p, double *partials,
