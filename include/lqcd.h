@@ -210,6 +210,16 @@ lqcd_status lqcd_field_copy(lqcd_field *dst, const lqcd_field *src, void *stream
 lqcd_status lqcd_philox_blocks(uint32_t *out_dev, size_t n_blocks, uint32_t c0, uint32_t c1, uint32_t c2,
                                uint32_t c3, uint32_t key0, uint32_t key1, void *stream);
 
+/* The float-float codec of the mixed solver (the Krylov solver of Sec. 6; its
+ * accurate residuals and solutions are held as unevaluated sums hi + lo of
+ * two floats in place of FP64, see lqcd_cg_params) on n doubles: pairs_dev[2i] = hi =
+ * RN_float(in[i]), pairs_dev[2i+1] = lo = RN_float(in[i] - hi), back_dev[i] =
+ * RN_double(hi + lo), exactly as the FP64 operations would give them, computed
+ * on the IEEE-754 bit patterns as the field conversions do.  All three arrays
+ * on the device (n doubles, 2n floats, n doubles), caller-owned; NULL with
+ * n > 0 is LQCD_EINVAL. */
+lqcd_status lqcd_df_split(const double *in_dev, size_t n, float *pairs_dev, double *back_dev, void *stream);
+
 /* Start configuration U_mu(x) = exp(i eps sum_a h_a T_a), h_a ~ N(0,1) from
  * Philox purpose 0 (counter (site, j, 0, 0), j = 0..15, Gaussians 2j, 2j+1 are
  * coefficient k = mu*8 + a; uniforms from 52-bit words, Box-Muller).

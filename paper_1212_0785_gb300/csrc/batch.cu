@@ -183,20 +183,21 @@ __global__ void batch_gather_scalars(const SysDesc<SP> *sys, CgScalars *out, int
 // ---------------------------------------------------------------- reliable updates of many systems
 //
 // The accurate residual r = b - Mhat^dag Mhat x of every paused system in
-// float-float, with shared launches: x += x_s, the four float-float hops,
-// r = b - t with block partials, and one fixed-order final sum per system.
+// float-float, with shared launches: x += x_s, the four float-float hops (the
+// last one forming r = b - t and its block partials), and one fixed-order
+// final sum per system.
 // Each block runs exactly the code and block decomposition of the
 // single-system kernels (cg.cu, dslash_df.cu), so the results are bitwise
 // theirs.
 
 struct DfSys {
     Geo g;
-    SpinorRef<PREC_DF> xdf, bdf, rdf, t1, t2, tmpo;
+    SpinorRef<PREC_DF> xdf, bdf, rdf, t1, tmpo;
     GaugeRef<PREC_DF> U;
     SpinorRef<LQCD_F32> xs;
     Df mk2; // -kappa^2
     double *partials, *scalars;
-    int nb; // blocks of CG_BLOCK sites
+    int nb; // blocks of DF_SITES sites: the partials of |r|^2
 };
 
 __global__ void __launch_bounds__(CG_BLOCK) batch_accum_df_kernel(const DfSys *sys, const int2 *bmap)
@@ -216,17 +217,7 @@ __global__ void __launch_bounds__(DF_SITES * 3, 4) batch_df_hop_kernel(const DfS
     if (STEP == 0) df_hop_block<false, false>(sh, d.tmpo, d.xdf, d.U, d.g, 1, d.xdf, Df(0), m.y);
     if (STEP == 1) df_hop_block<false, true>(sh, d.t1, d.tmpo, d.U, d.g, 0, d.xdf, d.mk2, m.y);
     if (STEP == 2) df_hop_block<true, false>(sh, d.tmpo, d.t1, d.U, d.g, 1, d.t1, Df(0), m.y);
-    if (STEP == 3) df_hop_block<true, true>(sh, d.t2, d.tmpo, d.U, d.g, 0, d.t1, d.mk2, m.y);
-}
-
-__global__ void __launch_bounds__(CG_BLOCK) batch_residual_df_kernel(const DfSys *sys, const int2 *bmap)
-{
-    const int2 m = bmap[blockIdx.x];
-    const DfSys &d = sys[m.x];
-    const int cb = m.y * CG_BLOCK + threadIdx.x;
-    double n2[1] = {0.0};
-    if (cb < d.g.Vh) n2[0] = residual_df_site(d.rdf, d.bdf, d.t2, cb);
-    block_sum_store<1, CG_BLOCK>(n2, d.partials, d.nb, m.y);
+    if (STEP == 3) df_hop_block<true, true, true>(sh, d.rdf, d.tmpo, d.U, d.g, 0, d.t1, d.mk2, m.y, d.bdf, d.partials);
 }
 
 __global__ void batch_final_sum_kernel(const DfSys *sys)
@@ -422,17 +413,16 @@ lqcd_status BatchSolver::residuals_df(const std::vector<CgRun *> &runs, cudaStre
         d.bdf = spinor_ref<PREC_DF>(w.bdf.f);
         d.rdf = spinor_ref<PREC_DF>(w.rdf_());
         d.t1 = spinor_ref<PREC_DF>(w.t1());
-        d.t2 = spinor_ref<PREC_DF>(w.t2());
         d.tmpo = spinor_ref<PREC_DF>(w.tmpo());
         d.U = gauge_ref<PREC_DF>(w.udf());
         d.xs = spinor_ref<LQCD_F32>(r.XS);
         d.mk2 = Df(-(r.kappa * r.kappa));
         d.partials = (double *)w.partials.p;
         d.scalars = r.pause_result_dev();
-        d.nb = nblocks_for(d.g.Vh, CG_BLOCK);
+        d.nb = nblocks_for(d.g.Vh, DF_SITES);
         hd.push_back(d);
-        for (int k = 0; k < nblocks_for(d.g.Vh, DF_SITES); k++) hdf.push_back(make_int2((int)i, k));
-        for (int k = 0; k < d.nb; k++) hbb.push_back(make_int2((int)i, k));
+        for (int k = 0; k < d.nb; k++) hdf.push_back(make_int2((int)i, k));
+        for (int k = 0; k < nblocks_for(d.g.Vh, CG_BLOCK); k++) hbb.push_back(make_int2((int)i, k));
     }
     if (df_descs.bytes < hd.size() * sizeof(DfSys)) LQCD_TRY(df_descs.alloc(hd.size() * sizeof(DfSys), s));
     if (df_map.bytes < hdf.size() * sizeof(int2)) LQCD_TRY(df_map.alloc(hdf.size() * sizeof(int2), s));
@@ -453,10 +443,9 @@ lqcd_status BatchSolver::residuals_df(const std::vector<CgRun *> &runs, cudaStre
         batch_df_hop_kernel<2><<<ndf, dfb, 0, s>>>(d, mdf);
         batch_df_hop_kernel<3><<<ndf, dfb, 0, s>>>(d, mdf);
     }
-    batch_residual_df_kernel<<<nbb, CG_BLOCK, 0, s>>>(d, mbb);
     batch_final_sum_kernel<<<(unsigned)hd.size(), 1024, 0, s>>>(d);
     LQCD_CUDA(cudaGetLastError());
-    g_launches.fetch_add(8, std::memory_order_relaxed);
+    g_launches.fetch_add(7, std::memory_order_relaxed);
     return LQCD_OK;
 }
 

@@ -102,16 +102,6 @@ __global__ void accum_df_kernel(SpinorRef<PREC_DF> x, SpinorRef<LQCD_F32> xs, in
     accum_df_site(x, xs, cb);
 }
 
-// r = b - t in float-float; block partials of |r|^2 from the leading parts
-__global__ void __launch_bounds__(BB) residual_df_kernel(SpinorRef<PREC_DF> r, SpinorRef<PREC_DF> b,
-                                                         SpinorRef<PREC_DF> t, double *partials, int nb, int Vh)
-{
-    int cb = blockIdx.x * BB + threadIdx.x;
-    double n2[1] = {0.0};
-    if (cb < Vh) n2[0] = residual_df_site(r, b, t, cb);
-    block_sum_store<1, BB>(n2, partials, nb);
-}
-
 template <lqcd_prec PS, lqcd_prec PD, typename R>
 __global__ void convert_spinor_kernel(SpinorRef<PD> dst, SpinorRef<PS> src, int Vh)
 {
@@ -305,7 +295,7 @@ lqcd_status CgWorkspace::ensure(const lqcd_lattice &l, lqcd_prec sl, cudaStream_
     }
     mre_n = 0;
     for (FieldPtr *f : {&r64, &t64a, &t64b, &tmpo64, &p64, &xs, &rs, &ps, &ts, &tmpos, &Udf, &xdf, &bdf, &rdf,
-                        &t1df, &t2df, &tmpodf}) {
+                        &t1df, &tmpodf}) {
         if (f->f) lqcd_field_free(f->f);
         f->f = nullptr;
     }
@@ -321,7 +311,6 @@ lqcd_status CgWorkspace::ensure(const lqcd_lattice &l, lqcd_prec sl, cudaStream_
         if (temps_only) {
             LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &rdf.f));
             LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &t1df.f));
-            LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &t2df.f));
             LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_ODD, &tmpodf.f));
             ready = true;
             return LQCD_OK;
@@ -332,7 +321,6 @@ lqcd_status CgWorkspace::ensure(const lqcd_lattice &l, lqcd_prec sl, cudaStream_
         if (!tmp_from) {
             LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &rdf.f));
             LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &t1df.f));
-            LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_EVEN, &t2df.f));
             LQCD_TRY(field_alloc_df(&lat, LQCD_SPINOR_ODD, &tmpodf.f));
         }
         LQCD_TRY(lqcd_field_alloc(&lat, LQCD_SPINOR_EVEN, LQCD_F32, 0, &xs.f));
@@ -355,7 +343,7 @@ size_t CgWorkspace::bytes() const
 {
     size_t n = sc.bytes + partials.bytes + scalars.bytes;
     for (const FieldPtr *f : {&r64, &t64a, &t64b, &tmpo64, &p64, &xs, &rs, &ps, &ts, &tmpos, &Udf, &xdf, &bdf, &rdf,
-                              &t1df, &t2df, &tmpodf, &mre_d[0], &mre_d[1], &mre_d[2], &mre_w[0], &mre_w[1],
+                              &t1df, &tmpodf, &mre_d[0], &mre_d[1], &mre_d[2], &mre_w[0], &mre_w[1],
                               &mre_w[2], &mre_te, &mre_to})
         if (f->f) n += f->f->bytes + f->f->norm_bytes;
     return n;
@@ -383,11 +371,9 @@ static lqcd_status residual_df_enqueue(CgWorkspace &ws, double kappa, cudaStream
     LQCD_TRY(dslash_plain(ws.tmpo(), ws.udf(), ws.xdf.f, 0, nullptr, s));
     LQCD_TRY(dslash_xpay(ws.t1(), ws.udf(), ws.tmpo(), 0, ws.xdf.f, -k2, nullptr, nullptr, s));
     LQCD_TRY(dslash_plain(ws.tmpo(), ws.udf(), ws.t1(), 1, nullptr, s));
-    LQCD_TRY(dslash_xpay(ws.t2(), ws.udf(), ws.tmpo(), 1, ws.t1(), -k2, nullptr, nullptr, s));
-    int Vh = ws.xdf.f->Vh, nb = nblocks_for(Vh, BB);
-    residual_df_kernel<<<nb, BB, 0, s>>>(spinor_ref<PREC_DF>(ws.rdf_()), spinor_ref<PREC_DF>(ws.bdf.f),
-                                         spinor_ref<PREC_DF>(ws.t2()), (double *)ws.partials.p, nb, Vh);
-    LQCD_LAUNCHED();
+    // the last term writes r = b - (t1 - kappa^2 D^dag tmpo) and its block partials of |r|^2
+    LQCD_TRY(dslash_df_residual(ws.rdf_(), ws.udf(), ws.tmpo(), ws.t1(), -k2, ws.bdf.f, (double *)ws.partials.p, s));
+    const int nb = nblocks_for(ws.xdf.f->Vh, DF_SITES);
     return reduce_partials((double *)ws.partials.p, nb, 1, (double *)ws.scalars.p, s);
 }
 

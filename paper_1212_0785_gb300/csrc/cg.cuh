@@ -22,7 +22,7 @@ struct CgWorkspace {
     FieldPtr xs, rs, ps, ts, tmpos;    // sloppy fields (mixed CG)
     // mixed CG: the accurate solution, source, residual and operator
     // temporaries in float-float storage, and the float-float link copy
-    FieldPtr Udf, xdf, bdf, rdf, t1df, t2df, tmpodf;
+    FieldPtr Udf, xdf, bdf, rdf, t1df, tmpodf;
     // bdf holds the float-float copy of the source b with stamp bdf_stamp
     // (0: none), so repeated solves of an unchanged source skip the split
     const lqcd_field *bdf_of = nullptr;
@@ -44,7 +44,6 @@ struct CgWorkspace {
     const lqcd_field *udf() const { return udf_ext ? udf_ext : Udf.f; }
     lqcd_field *rdf_() const { return tmp_from ? tmp_from->rdf.f : rdf.f; }
     lqcd_field *t1() const { return tmp_from ? tmp_from->t1df.f : t1df.f; }
-    lqcd_field *t2() const { return tmp_from ? tmp_from->t2df.f : t2df.f; }
     lqcd_field *tmpo() const { return tmp_from ? tmp_from->tmpodf.f : tmpodf.f; }
     lqcd_status ensure(const lqcd_lattice &lat, lqcd_prec sloppy, cudaStream_t s);
     size_t bytes() const;

@@ -18,18 +18,84 @@ namespace lqcd {
 // internal storage precision: float-float pairs (not part of the C ABI)
 constexpr lqcd_prec PREC_DF = (lqcd_prec)4;
 
+// Conversions between doubles and float pairs on the integer bits of the
+// IEEE-754 formats.  The direct routes -- hi = RN(d), lo = RN(d - hi): two
+// conversions, one subtraction and one more conversion on the FP64 pipe;
+// (double) hi + (double) lo: two conversions and one addition -- bound every
+// kernel that converts whole fields on a part whose FP64 rate is a small
+// fraction of its FP32 rate.  These give the same bits with at most the one
+// FP64 addition.
+//
+// Split, for d = (-1)^s 2^E (1 + f / 2^52) with -74 <= E <= 126 (so that hi
+// and every nonzero lo are normal floats):
+//   hi keeps the leading 23 of the 52 fraction bits, rounded to nearest-even
+//   on the 29 dropped bits t: away from zero iff t > 2^28, or t = 2^28 and
+//   the last kept bit is 1.  The rounding increment is added to the pattern
+//   (E + 127) << 23 | f23, so a carry out of the fraction raises the exponent
+//   as RN(d) requires.
+//   d - hi is exact: t units of 2^(E-52) with the sign of d, or, when hi went
+//   away from zero, 2^29 - t units with the opposite sign.  The integer (< 2^29)
+//   is rounded to 24 bits by the unsigned -> float conversion and scaled by
+//   the normal float 2^(E-52) exactly; d = hi gives lo = +0 as d - hi does.
+// Zero, subnormal, very small or very large d, Inf and NaN take the direct
+// route.
+__device__ __forceinline__ void df_split_bits(double d, float &hi, float &lo)
+{
+    const unsigned long long D = (unsigned long long)__double_as_longlong(d);
+    const int E = (int)((D >> 52) & 0x7ffu) - 1023;
+    if (E < -74 || E > 126) {
+        hi = __double2float_rn(d);
+        lo = __double2float_rn(d - (double)hi);
+        return;
+    }
+    const unsigned int sign = (unsigned int)(D >> 32) & 0x80000000u;
+    const unsigned int t = (unsigned int)D & 0x1fffffffu;
+    const unsigned int f23 = (unsigned int)(D >> 29) & 0x7fffffu;
+    const unsigned int away = (t > 0x10000000u) | ((t == 0x10000000u) & f23);
+    hi = __uint_as_float(sign | ((((unsigned int)(E + 127) << 23) | f23) + (away & 1u)));
+    const unsigned int m = (away & 1u) ? 0x20000000u - t : t;
+    const float mag = __uint2float_rn(m) * __uint_as_float((unsigned int)(E + 75) << 23);
+    const unsigned int lsign = m == 0u ? 0u : (away & 1u) ? sign ^ 0x80000000u : sign;
+    lo = __uint_as_float(__float_as_uint(mag) ^ lsign);
+}
+
+// a normal float widened to a double on its bits: exponent rebased by
+// 1023 - 127 = 896, fraction moved up by 52 - 23 = 29 bits (exact)
+__device__ __forceinline__ double df_widen_normal(unsigned int x)
+{
+    return __longlong_as_double((long long)((((unsigned long long)(x & 0x7fffffffu) << 29) + (896ull << 52)) |
+                                            ((unsigned long long)(x & 0x80000000u) << 32)));
+}
+
+// (double) hi + (double) lo: both widened exactly, then the one rounding
+// FP64 addition (none when lo is zero); zero, subnormal, Inf or NaN parts
+// take the direct route
+__device__ __forceinline__ double df_sum_bits(float hi, float lo)
+{
+    const unsigned int H = __float_as_uint(hi), L = __float_as_uint(lo);
+    const unsigned int eh = (H >> 23) & 0xffu, el = (L >> 23) & 0xffu;
+    const bool lo_zero = (L & 0x7fffffffu) == 0u;
+    if (eh == 0u || eh == 0xffu || el == 0xffu || (el == 0u && !lo_zero)) return (double)hi + (double)lo;
+    const double dh = df_widen_normal(H);
+    return lo_zero ? dh : dh + df_widen_normal(L);
+}
+
 struct Df {
     float hi, lo;
     Df() = default;
     __host__ __device__ __forceinline__ constexpr Df(float h, float l) : hi(h), lo(l) {}
     __host__ __device__ __forceinline__ Df(int v) : hi((float)v), lo(0.f) {}
-    // exact split of a double (one FP64 subtraction)
+    // exact split of a double: hi = RN(d), lo = RN(d - hi)
     __host__ __device__ __forceinline__ explicit Df(double d)
     {
+#ifdef __CUDA_ARCH__
+        df_split_bits(d, hi, lo);
+#else
         hi = (float)d;
         lo = (float)(d - (double)hi);
+#endif
     }
-    __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+    __device__ __forceinline__ explicit operator double() const { return df_sum_bits(hi, lo); }
     __device__ __forceinline__ explicit operator float() const { return hi + lo; }
 };
 
@@ -142,7 +208,7 @@ __device__ __forceinline__ float df_to<float>(float hi, float lo)
 template <>
 __device__ __forceinline__ double df_to<double>(float hi, float lo)
 {
-    return (double)hi + (double)lo;
+    return df_sum_bits(hi, lo);
 }
 template <>
 __device__ __forceinline__ Df df_to<Df>(float hi, float lo)

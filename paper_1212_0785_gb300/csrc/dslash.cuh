@@ -160,4 +160,10 @@ int dslash_form_set(int form);
 lqcd_status dslash_df_launch(lqcd_field *out, const lqcd_field *U, const lqcd_field *in, int dagger,
                              const lqcd_field *x, double b, const int *skip, cudaStream_t s);
 
+// the accurate residual's last float-float term: r = bsrc - (x + b D^dag in),
+// with one partial of |r|^2 per block of DF_SITES sites in partials[0 ..
+// nblocks_for(Vh, DF_SITES)) (dslash_df.cu)
+lqcd_status dslash_df_residual(lqcd_field *r, const lqcd_field *U, const lqcd_field *in, const lqcd_field *x,
+                               double b, const lqcd_field *bsrc, double *partials, cudaStream_t s);
+
 } // namespace lqcd

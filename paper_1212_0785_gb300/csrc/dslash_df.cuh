@@ -186,12 +186,16 @@ __device__ __forceinline__ void hop_dir_df(DfAcc (&ar)[4], DfAcc (&ai)[4], const
 
 // The block body: output sites blk * DF_SITES + threadIdx.x, colour
 // threadIdx.y (the kernels of dslash_df.cu and the multi-system kernels of
-// batch.cu).
-template <bool DAG, bool XPAY>
+// batch.cu).  RESID (with XPAY): the accurate residual r = b - (x + b D in)
+// is stored instead of x + b D in, each component r = b - t in float-float, and the block's partial sum of |r|^2 (leading parts) goes to
+// partials[blk]: each thread adds its colour over the four spins in FP32,
+// the threads' sums are added in FP64 in a fixed order.
+template <bool DAG, bool XPAY, bool RESID = false>
 __device__ __forceinline__ void df_hop_block(DfHalves &sh, SpinorRef<PREC_DF> out, SpinorRef<PREC_DF> in,
                                              GaugeRef<PREC_DF> U, const Geo &g, int out_par, SpinorRef<PREC_DF> x,
-                                             Df b, int blk)
+                                             Df b, int blk, SpinorRef<PREC_DF> bsrc = {}, double *partials = nullptr)
 {
+    static_assert(!RESID || XPAY, "the residual follows the last term x + b D in");
     const int tx = threadIdx.x, a = threadIdx.y;
     const int cb = blk * DF_SITES + tx;
     const bool live = cb < g.Vh;
@@ -208,30 +212,53 @@ __device__ __forceinline__ void df_hop_block(DfHalves &sh, SpinorRef<PREC_DF> ou
         project_dir_df<3, FS, BS>(sh, in, tx, a, nb[6], nb[7]);
     }
     __syncthreads();
-    if (!live) return;
-    DfAcc ar[4], ai[4];
-    hop_dir_df<0, FS, BS>(ar, ai, sh, U, g, cb, out_par, tx, a, nb[1], false, false);
-    hop_dir_df<1, FS, BS>(ar, ai, sh, U, g, cb, out_par, tx, a, nb[3], false, false);
-    hop_dir_df<2, FS, BS>(ar, ai, sh, U, g, cb, out_par, tx, a, nb[5], false, false);
-    if (g.aniso) { // the spatial hops' weight of the anisotropic operator (a uniform branch)
-        const Df w(g.csf, g.cs_lo);
+    if (!RESID && !live) return;
+    float n2 = 0.f;
+    if (live) {
+        DfAcc ar[4], ai[4];
+        hop_dir_df<0, FS, BS>(ar, ai, sh, U, g, cb, out_par, tx, a, nb[1], false, false);
+        hop_dir_df<1, FS, BS>(ar, ai, sh, U, g, cb, out_par, tx, a, nb[3], false, false);
+        hop_dir_df<2, FS, BS>(ar, ai, sh, U, g, cb, out_par, tx, a, nb[5], false, false);
+        if (g.aniso) { // the spatial hops' weight of the anisotropic operator (a uniform branch)
+            const Df w(g.csf, g.cs_lo);
+#pragma unroll
+            for (int sp = 0; sp < 4; sp++) {
+                ar[sp].set(w * ar[sp].value());
+                ai[sp].set(w * ai[sp].value());
+            }
+        }
+        hop_dir_df<3, FS, BS>(ar, ai, sh, U, g, cb, out_par, tx, a, nb[7], tf, tb);
 #pragma unroll
         for (int sp = 0; sp < 4; sp++) {
-            ar[sp].set(w * ar[sp].value());
-            ai[sp].set(w * ai[sp].value());
+            Cx<Df> v{ar[sp].value(), ai[sp].value()};
+            size_t k = (size_t)(sp * 3 + a) * out.Vh + cb;
+            if (XPAY) {
+                float4 xv = x.d[k];
+                Cx<Df> xc{Df(xv.x, xv.y), Df(xv.z, xv.w)};
+                v = xc + b * v;
+            }
+            if (RESID) {
+                const float4 bv = bsrc.d[k];
+                v = Cx<Df>{Df(bv.x, bv.y) - v.re, Df(bv.z, bv.w) - v.im};
+                n2 += v.re.hi * v.re.hi + v.im.hi * v.im.hi;
+            }
+            out.d[k] = df_from<Df>(v);
         }
     }
-    hop_dir_df<3, FS, BS>(ar, ai, sh, U, g, cb, out_par, tx, a, nb[7], tf, tb);
+    if (RESID) { // warps of 32 consecutive sites of one colour; warp sums added in warp order
+        __shared__ double wsum[DF_SITES * 3 / 32];
+        double t = n2;
 #pragma unroll
-    for (int sp = 0; sp < 4; sp++) {
-        Cx<Df> v{ar[sp].value(), ai[sp].value()};
-        size_t k = (size_t)(sp * 3 + a) * out.Vh + cb;
-        if (XPAY) {
-            float4 xv = x.d[k];
-            Cx<Df> xc{Df(xv.x, xv.y), Df(xv.z, xv.w)};
-            v = xc + b * v;
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+        const int lid = a * DF_SITES + tx;
+        if ((lid & 31) == 0) wsum[lid >> 5] = t;
+        __syncthreads();
+        if (lid == 0) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < DF_SITES * 3 / 32; w++) s += wsum[w];
+            partials[blk] = s;
         }
-        out.d[k] = df_from<Df>(v);
     }
 }
 
@@ -250,23 +277,6 @@ __device__ __forceinline__ void accum_df_site(const SpinorRef<PREC_DF> &x, const
         }
     x.store(cb, xv);
     xs.store(cb, sp_zero<float>());
-}
-
-// r = b - t in float-float; returns |r|^2 of the leading parts (FP32)
-__device__ __forceinline__ float residual_df_site(const SpinorRef<PREC_DF> &r, const SpinorRef<PREC_DF> &b,
-                                                  const SpinorRef<PREC_DF> &t, int cb)
-{
-    Sp<Df> bv = b.load_rw<Df>(cb), tv = t.load_rw<Df>(cb);
-    float acc = 0.f;
-#pragma unroll
-    for (int a = 0; a < 4; a++)
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            bv.c[a][k] = bv.c[a][k] - tv.c[a][k];
-            acc += bv.c[a][k].re.hi * bv.c[a][k].re.hi + bv.c[a][k].im.hi * bv.c[a][k].im.hi;
-        }
-    r.store(cb, bv);
-    return acc;
 }
 
 } // namespace lqcd

@@ -569,6 +569,17 @@ static void launch_spinor_convert(lqcd_field *dst, const lqcd_field *src, cudaSt
 
 // ------------------------------------------------------------------ RNG kernels
 
+// the float-float codec on n doubles: pairs[2i], pairs[2i + 1] = hi, lo of
+// in[i]; back[i] = hi + lo rounded to a double
+__global__ void df_split_kernel(const double *in, float2 *pairs, double *back, size_t n)
+{
+    size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Df v(in[i]);
+    pairs[i] = make_float2(v.hi, v.lo);
+    back[i] = (double)v;
+}
+
 __global__ void philox_blocks_kernel(uint4 *out, size_t n, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                      uint32_t k0, uint32_t k1)
 {
@@ -1196,6 +1207,16 @@ lqcd_status lqcd_philox_blocks(uint32_t *out_dev, size_t n_blocks, uint32_t c0, 
     if (n_blocks == 0) return LQCD_OK;
     philox_blocks_kernel<<<nblocks_for((long)n_blocks, 256), 256, 0, (cudaStream_t)stream>>>((uint4 *)out_dev, n_blocks,
                                                                                               c0, c1, c2, c3, key0, key1);
+    LQCD_LAUNCHED();
+    return LQCD_OK;
+}
+
+lqcd_status lqcd_df_split(const double *in_dev, size_t n, float *pairs_dev, double *back_dev, void *stream)
+{
+    LQCD_REQUIRE((in_dev && pairs_dev && back_dev) || n == 0, "df_split: NULL pointer");
+    if (n == 0) return LQCD_OK;
+    df_split_kernel<<<nblocks_for((long)n, 256), 256, 0, (cudaStream_t)stream>>>(in_dev, (float2 *)pairs_dev,
+                                                                                 back_dev, n);
     LQCD_LAUNCHED();
     return LQCD_OK;
 }

@@ -119,6 +119,7 @@ _SIGS = {
     "lqcd_field_download": (_i, [_vp, _dp, _vp]),
     "lqcd_field_copy": (_i, [_vp, _vp, _vp]),
     "lqcd_philox_blocks": (_i, [_vp, _sz, _u32, _u32, _u32, _u32, _u32, _u32, _vp]),
+    "lqcd_df_split": (_i, [_vp, _sz, _vp, _vp, _vp]),
     "lqcd_gauge_start": (_i, [_vp, _u32, _u32, _d, _vp]),
     "lqcd_momentum_refresh": (_i, [_vp, _u32, _u32, _u32, _vp]),
     "lqcd_eta_refresh": (_i, [_vp, _u32, _u32, _u32, _vp]),
@@ -403,6 +404,12 @@ def momentum_field(dims, t_bc=-1, aniso=(1.0, 1.0)):
 
 
 # ---------------------------------------------------------------- operations
+
+def df_split(in_ptr: int, n: int, pairs_ptr: int, back_ptr: int, stream=None):
+    """the float-float codec on n device doubles (lqcd_df_split)"""
+    _check(lib().lqcd_df_split(ctypes.c_void_p(in_ptr), n, ctypes.c_void_p(pairs_ptr), ctypes.c_void_p(back_ptr),
+                               _s(stream)), "df_split")
+
 
 def philox_blocks(out_ptr: int, n_blocks: int, ctr, key, stream=None):
     _check(lib().lqcd_philox_blocks(ctypes.c_void_p(out_ptr), n_blocks, *[int(c) for c in ctr],

@@ -29,6 +29,56 @@ def test_philox_blocks_bit_exact():
         assert np.array_equal(got[i], orc.philox4x32_10([(0xFFFFFFFE + i) & 0xFFFFFFFF, 0, 2, 0], (1, 2)))
 
 
+def _df_codec_inputs():
+    """doubles over the whole exponent range, with the cases the bit-level
+    split must get right: exact floats, rounding ties both ways, carries out
+    of the fraction, the edges of the range it handles itself, zeros,
+    subnormals, Inf and NaN"""
+    rng = np.random.default_rng(11)
+    n = 200_000
+    sign = rng.integers(0, 2, n, dtype=np.uint64) << np.uint64(63)
+    expo = rng.integers(0, 2047, n, dtype=np.uint64) << np.uint64(52)
+    frac = rng.integers(0, 1 << 52, n, dtype=np.uint64)
+    words = [sign | expo | frac]
+    # exponents near the split's own range [-74, 126] and typical field values
+    e = rng.integers(-80, 131, n).astype(np.uint64) + np.uint64(1023)
+    words.append(sign | (e << np.uint64(52)) | frac)
+    words.append(np.frombuffer(rng.standard_normal(n).astype(np.float64).tobytes(), dtype=np.uint64))
+    # the 29 dropped bits: exactly half (ties to even both ways), zero, all ones
+    kept = frac & ~np.uint64((1 << 29) - 1)
+    for t in (1 << 28, 0, (1 << 29) - 1, (1 << 28) - 1, (1 << 28) + 1):
+        words.append(sign | (e << np.uint64(52)) | kept | np.uint64(t))
+    # all-ones fractions: rounding carries into the exponent
+    words.append(sign | (e << np.uint64(52)) | np.uint64((1 << 52) - 1))
+    special = np.array([0.0, -0.0, 5e-324, -5e-324, 2.2250738585072014e-308, 1e-300, 1.7976931348623157e308,
+                        np.inf, -np.inf, np.nan, 2.0 ** -74, 2.0 ** -75, -(2.0 ** 126), 2.0 ** 127, 2.0 ** 128,
+                        1.0, -1.0, 1.0 + 2.0 ** -52, 3.4028235677973366e38, 1.401298464324817e-45])
+    words.append(special.view(np.uint64))
+    return np.concatenate(words).view(np.float64)
+
+
+def test_float_float_codec_matches_ieee_rounding():
+    d = _df_codec_inputs()
+    with np.errstate(over="ignore", invalid="ignore"):
+        hi = d.astype(np.float32)
+        lo = (d - hi.astype(np.float64)).astype(np.float32)
+        back = hi.astype(np.float64) + lo.astype(np.float64)
+    din = torch.from_numpy(d.copy()).cuda()
+    pairs = torch.empty(2 * d.size, dtype=torch.float32, device="cuda")
+    got_back = torch.empty(d.size, dtype=torch.float64, device="cuda")
+    lqcd.df_split(din.data_ptr(), d.size, pairs.data_ptr(), got_back.data_ptr())
+    torch.cuda.synchronize()
+    p = pairs.cpu().numpy().reshape(-1, 2)
+    gb = got_back.cpu().numpy()
+    for name, want, got in (("hi", hi, p[:, 0]), ("lo", lo, p[:, 1]), ("back", back, gb)):
+        nan = np.isnan(want)
+        assert np.array_equal(np.isnan(got), nan), name
+        iw = want.view(np.uint32 if want.dtype == np.float32 else np.uint64)
+        ig = got.view(iw.dtype)
+        bad = np.flatnonzero((iw != ig) & ~nan)
+        assert bad.size == 0, (name, d[bad[:5]], want[bad[:5]], got[bad[:5]])
+
+
 @pytest.mark.parametrize("dims", PARITY_DIMS[:3])
 def test_gauge_start_matches_oracle(dims):
     U = lqcd.gauge_field(dims)
