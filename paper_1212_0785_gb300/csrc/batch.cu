@@ -44,14 +44,15 @@ __device__ __forceinline__ Sp<float> sys_site(const SpinorRef<SP> &in, const Gau
         return dslash_site<float, SP, SP, DAG>(in, U, g, cb, out_par);
 }
 
-// 7 blocks of 128 per SM for the FP16+norm kernels (72 registers, 24 KiB of
-// prefetched links each)
-template <lqcd_prec SP>
-constexpr int min_blocks() { return SP == LQCD_F16N ? 7 : 1; }
+// blocks of 128 per SM for the FP16+norm kernels, the register budgets of the
+// single-system hop (dslash.cu): 5 for the plain steps, 6 for the reducing
+// ones (fewer spills than 7 for all; the 64 chains ran at the same rate)
+template <lqcd_prec SP, bool REDUCING>
+constexpr int min_blocks() { return SP != LQCD_F16N ? 1 : (REDUCING ? 6 : 5); }
 
 // step 0: tmp = D_oe p; step 2: tmp = D_oe^dag-hop t
 template <lqcd_prec SP, bool DAG, int FORM>
-__global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP>()) batch_dslash_plain(const SysDesc<SP> *sys, const int2 *bmap)
+__global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP, false>()) batch_dslash_plain(const SysDesc<SP> *sys, const int2 *bmap)
 {
     const int2 m = bmap[blockIdx.x];
     const SysDesc<SP> &d = sys[m.x];
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP>()) batch_dslash_plain
 
 // step 1: t = p - kappa^2 D_eo tmp, block sums of |t|^2
 template <lqcd_prec SP, int FORM>
-__global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP>()) batch_dslash_xpay(const SysDesc<SP> *sys, const int2 *bmap)
+__global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP, true>()) batch_dslash_xpay(const SysDesc<SP> *sys, const int2 *bmap)
 {
     const int2 m = bmap[blockIdx.x];
     const SysDesc<SP> &d = sys[m.x];
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP>()) batch_dslash_xpay(
 
 // step 3: Ap = t - kappa^2 D_eo^dag-hop tmp; xs += alpha p; r -= alpha Ap; block sums of |r|^2
 template <lqcd_prec SP, int FORM>
-__global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP>()) batch_dslash_cg(const SysDesc<SP> *sys, const int2 *bmap)
+__global__ void __launch_bounds__(DS_BLOCK, min_blocks<SP, true>()) batch_dslash_cg(const SysDesc<SP> *sys, const int2 *bmap)
 {
     const int2 m = bmap[blockIdx.x];
     const SysDesc<SP> &d = sys[m.x];
