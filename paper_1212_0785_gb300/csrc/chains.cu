@@ -29,12 +29,7 @@ __global__ void __launch_bounds__(CB) chains_gauge_force_kernel(const ChainMd *d
     MomRef P = c.P;
     const GaugeRef<LQCD_F32> U = c.Uf;
     const double cf = coeff * c.beta / 6.0;
-    switch (mu) {
-    case 0: gauge_force_link<0, float, LQCD_F32>(P, U, c.g, par, cb, x, cf); break;
-    case 1: gauge_force_link<1, float, LQCD_F32>(P, U, c.g, par, cb, x, cf); break;
-    case 2: gauge_force_link<2, float, LQCD_F32>(P, U, c.g, par, cb, x, cf); break;
-    default: gauge_force_link<3, float, LQCD_F32>(P, U, c.g, par, cb, x, cf); break;
-    }
+    gauge_force_link<float, LQCD_F32>(P, U, c.g, mu, par, cb, x, cf);
 }
 
 // X32 = X rounded to FP32 (the fermion force's input), per even site

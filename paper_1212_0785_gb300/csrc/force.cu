@@ -16,19 +16,17 @@
 
 namespace lqcd {
 
+// one thread per link, the four directions of a range of sites in four
+// consecutive blocks (link_of_thread), so the staple links that all four
+// directions read are shared through L2
 template <typename R, lqcd_prec GP>
 __global__ void __launch_bounds__(FB_MAX) gauge_force_kernel(MomRef P, GaugeRef<GP> U, Geo g, double cf)
 {
     int mu, par, cb;
-    if (!link_of_thread_seq(g.Vh, mu, par, cb)) return;
+    if (!link_of_thread(g.Vh, mu, par, cb)) return;
     int c[4];
     cb_coords(g, cb, par, c);
-    switch (mu) {
-    case 0: gauge_force_link<0, R, GP>(P, U, g, par, cb, c, cf); break;
-    case 1: gauge_force_link<1, R, GP>(P, U, g, par, cb, c, cf); break;
-    case 2: gauge_force_link<2, R, GP>(P, U, g, par, cb, c, cf); break;
-    default: gauge_force_link<3, R, GP>(P, U, g, par, cb, c, cf); break;
-    }
+    gauge_force_link<R, GP>(P, U, g, mu, par, cb, c, cf);
 }
 
 template <typename R, lqcd_prec SP, lqcd_prec GP>
@@ -58,7 +56,7 @@ lqcd_status gauge_force_block(lqcd_field *P, const lqcd_field *U, const lqcd_fie
 {
     LQCD_REQUIRE(bs >= 32 && bs <= FB_MAX && bs % 32 == 0, "gauge force: bad block size %d", bs);
     Geo g = make_geo(U->lat);
-    int nb = nblocks_for(8L * g.Vh, bs);
+    const int nb = 8 * force_blocks(g.Vh, bs);
     if (arith == LQCD_F32)
         gauge_force_kernel<float, LQCD_F32><<<nb, bs, 0, s>>>(mom_ref(P), gauge_ref<LQCD_F32>(Uf), g, cf);
     else
