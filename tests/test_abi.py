@@ -63,6 +63,8 @@ def test_null_arguments_are_rejected(L):
     assert L.lqcd_dslash(None, None, None, 0, None) == lqcd.EINVAL
     assert L.lqcd_plaquette(None, None, None) == lqcd.EINVAL
     assert L.lqcd_hmc_trajectory(None, None, None, None) == lqcd.EINVAL
+    assert L.lqcd_df_split(None, 4, None, None, None) == lqcd.EINVAL
+    assert L.lqcd_df_split(None, 0, None, None, None) == lqcd.OK  # nothing to do
     assert L.lqcd_field_free(None) == lqcd.OK
 
 
